@@ -1,0 +1,200 @@
+"""Octree, interaction lists and neighbour lists (oracle; test infrastructure only).
+
+Follows Section 2 of the paper (the FMM recap): boxes B^l_alpha of an octree with
+centres c^l_alpha and size a_l, levels l = 0 (root) .. L, highest active level 2
+(Table "Notation"); the interaction list I(B^l_alpha) = boxes of level l that are
+not neighbours of B^l_alpha but whose parent is a neighbour of the parent of
+B^l_alpha (M2L paragraph); the neighbour list N(B^L_alpha) = B^L_alpha and all
+its neighbours (after Eq. FMM_FinalStep).
+
+The paper uses uniform trees and leaves these conventions open; the ones taken
+here are fixed so that an independent implementation can reproduce the tree bit
+for bit:
+
+* root cube: given explicitly, or centred on the bounding box of all points
+  with side = the largest extent (1 if that is 0);
+* box index at depth D: clamp(floor((x - corner) * (2^D / side)), 0, 2^D - 1);
+  coarser levels take the index shifted right;
+* box centre c = corner + (idx + 1/2) * (side / 2^l), box size a_l = side / 2^l;
+* only boxes holding at least one source or target exist (sparse, level uniform);
+* boxes and points are ordered by Morton key (x bit above y bit above z bit),
+  points by key and then by original index;
+* "neighbour" = Chebyshev distance of box indices <= 1 (a box is its own
+  neighbour); transfer-vector index v = (di+3)*49 + (dj+3)*7 + (dk+3) with
+  (di, dj, dk) = idx(source box) - idx(target box).
+
+Everything is plain Python / numpy on float64 and int64.
+"""
+import numpy as np
+
+MAX_DEPTH = 20
+
+
+def root_cube(points, root=None):
+    """Return (corner[3], side) of the root box."""
+    if root is not None:
+        return np.array(root[:3], dtype=np.float64), float(root[3])
+    lo = points.min(axis=0)
+    hi = points.max(axis=0)
+    side = float(np.max(hi - lo))
+    if side == 0.0:
+        side = 1.0
+    corner = (lo + hi) / 2.0 - side / 2.0
+    return corner, side
+
+
+def box_index(points, corner, side, depth):
+    """Integer box coordinates (n, 3) of each point at the given depth."""
+    nb = 2 ** depth
+    scale = float(nb) / side
+    v = np.floor((points - corner) * scale)
+    v = np.clip(v, 0.0, float(nb - 1))
+    return v.astype(np.int64)
+
+
+def morton_key(idx, depth):
+    """Interleave the bits of (ix, iy, iz); x is the most significant of each triple."""
+    key = np.zeros(idx.shape[0], dtype=np.int64)
+    for b in range(depth):
+        key |= ((idx[:, 0] >> b) & 1) << (3 * b + 2)
+        key |= ((idx[:, 1] >> b) & 1) << (3 * b + 1)
+        key |= ((idx[:, 2] >> b) & 1) << (3 * b)
+    return key
+
+
+def max_occupancy(sources, targets, corner, side, depth):
+    occ = 0
+    for pts in (sources, targets):
+        if pts.shape[0] == 0:
+            continue
+        key = morton_key(box_index(pts, corner, side, depth), depth)
+        _, counts = np.unique(key, return_counts=True)
+        occ = max(occ, int(counts.max()))
+    return occ
+
+
+def occupancy_depth(sources, targets, corner, side, max_leaf):
+    """Smallest depth D whose fullest box holds <= max_leaf sources and <= max_leaf targets."""
+    for d in range(MAX_DEPTH + 1):
+        if max_occupancy(sources, targets, corner, side, d) <= max_leaf:
+            return d
+    return MAX_DEPTH
+
+
+def transfer_index(d):
+    """Index 0..342 of a box offset (di, dj, dk), each in [-3, 3]."""
+    return (d[0] + 3) * 49 + (d[1] + 3) * 7 + (d[2] + 3)
+
+
+class Tree:
+    """Sparse level-uniform octree over sources and targets, levels 0..depth.
+
+    Attributes
+    ----------
+    corner, side, depth
+    src_perm, tgt_perm : original indices of sources / targets in tree order
+    levels[l] : dict with 'idx' (n,3) int64, 'key' (n,), 'center' (n,3),
+                'parent' (n,) position of the parent box in levels[l-1]
+    src_start/src_count, tgt_start/tgt_count : point ranges of the depth-level
+                boxes inside the permuted point arrays
+    ilist[l], vlist[l] : for l >= 2, per box, the interaction-list box positions
+                (ascending) and their transfer-vector indices
+    nlist : per depth-level box, the neighbour-list box positions (ascending)
+    """
+
+    def __init__(self, sources, targets, depth, root=None):
+        sources = np.asarray(sources, dtype=np.float64).reshape(-1, 3)
+        targets = np.asarray(targets, dtype=np.float64).reshape(-1, 3)
+        allp = np.concatenate([sources, targets], axis=0)
+        self.corner, self.side = root_cube(allp, root)
+        self.depth = int(depth)
+        D = self.depth
+        sidx = box_index(sources, self.corner, self.side, D)
+        tidx = box_index(targets, self.corner, self.side, D)
+        skey = morton_key(sidx, D)
+        tkey = morton_key(tidx, D)
+        # stable sort by key, ties by original index
+        self.src_perm = np.lexsort((np.arange(len(skey)), skey))
+        self.tgt_perm = np.lexsort((np.arange(len(tkey)), tkey))
+        skey_sorted = skey[self.src_perm]
+        tkey_sorted = tkey[self.tgt_perm]
+
+        # boxes per level
+        leaf_keys = np.unique(np.concatenate([skey, tkey]))
+        self.levels = []
+        for l in range(D + 1):
+            keys_l = np.unique(leaf_keys >> (3 * (D - l)))
+            idx = np.zeros((len(keys_l), 3), dtype=np.int64)
+            for b in range(l):
+                idx[:, 0] |= ((keys_l >> (3 * b + 2)) & 1) << b
+                idx[:, 1] |= ((keys_l >> (3 * b + 1)) & 1) << b
+                idx[:, 2] |= ((keys_l >> (3 * b)) & 1) << b
+            h = self.side / float(2 ** l)
+            center = self.corner + (idx.astype(np.float64) + 0.5) * h
+            if l == 0:
+                parent = np.full(len(keys_l), -1, dtype=np.int64)
+            else:
+                pkeys = self.levels[l - 1]['key']
+                parent = np.searchsorted(pkeys, keys_l >> 3).astype(np.int64)
+            self.levels.append({'idx': idx, 'key': keys_l, 'center': center,
+                                'parent': parent, 'a': h})
+
+        lk = self.levels[D]['key']
+        self.src_start = np.searchsorted(skey_sorted, lk, side='left')
+        self.src_count = np.searchsorted(skey_sorted, lk, side='right') - self.src_start
+        self.tgt_start = np.searchsorted(tkey_sorted, lk, side='left')
+        self.tgt_count = np.searchsorted(tkey_sorted, lk, side='right') - self.tgt_start
+
+        # lists
+        self.ilist = [None] * (D + 1)
+        self.vlist = [None] * (D + 1)
+        for l in range(2, D + 1):
+            self.ilist[l], self.vlist[l] = self._interaction_lists(l)
+        self.nlist = self._neighbour_lists(D)
+
+    def _lookup(self, l):
+        return {tuple(int(c) for c in self.levels[l]['idx'][i]): i
+                for i in range(len(self.levels[l]['key']))}
+
+    def _interaction_lists(self, l):
+        lev = self.levels[l]
+        where = self._lookup(l)
+        nb = 2 ** l
+        il, vl = [], []
+        for a in range(len(lev['key'])):
+            ia = lev['idx'][a]
+            pa = ia >> 1
+            found = []
+            # children of the parent's neighbours
+            for dp in np.ndindex(3, 3, 3):
+                pn = pa + np.array(dp) - 1
+                for dc in np.ndindex(2, 2, 2):
+                    ib = pn * 2 + np.array(dc)
+                    if np.any(ib < 0) or np.any(ib >= nb):
+                        continue
+                    d = ib - ia
+                    if np.max(np.abs(d)) <= 1:
+                        continue
+                    b = where.get(tuple(int(c) for c in ib))
+                    if b is not None:
+                        found.append((lev['key'][b], b, transfer_index(d)))
+            found.sort()
+            il.append(np.array([f[1] for f in found], dtype=np.int64))
+            vl.append(np.array([f[2] for f in found], dtype=np.int64))
+        return il, vl
+
+    def _neighbour_lists(self, l):
+        lev = self.levels[l]
+        where = self._lookup(l)
+        out = []
+        for a in range(len(lev['key'])):
+            ia = lev['idx'][a]
+            found = []
+            for d in np.ndindex(3, 3, 3):
+                ib = ia + np.array(d) - 1
+                b = where.get(tuple(int(c) for c in ib))
+                if b is not None:
+                    found.append((lev['key'][b], b))
+            found.sort()
+            out.append(np.array([f[1] for f in found], dtype=np.int64))
+        return out
