@@ -1,0 +1,297 @@
+"""Benchmark of the FMM apply on one GB300 (or N independent replicas under torchrun).
+
+Workload: 262,144 points uniform on the unit sphere (sources = targets), kappa = 64,
+eps = 1e-6, complex64 charges N(0,1), one right-hand side.  The headline `value` is the
+mixed-precision apply in Mpoints*RHS/s (N_t * R / t_apply / 1e6) with inputs resident in
+HBM; `fp64_path` is the all-float64 apply on the same workload; `e2e` is the same metric
+through the public API with pinned host buffers and both copies inside the timed region.
+Every timed apply is preceded by an L2 flush (a 512 MiB write) outside its event pair.
+
+--impl reference times the CPU oracle (direct sum over all sources for a seeded subset of
+targets) on the host cores; it is the baseline arm, not the target.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="sphere262k", points=262144, surface="unit sphere", kappa=64.0, eps=1e-6,
+                nrhs=1, charges="complex64 N(0,1)")
+ORACLE_TARGETS = 2000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the float64-path measurement")
+    return ap.parse_args()
+
+
+def dist_setup(ngpus):
+    rank, world = int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if ngpus > 0 else "gloo")
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 3 + i and r[3 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def time_oracle(s, t, q, kappa, ntargets, seed):
+    from oracle import direct
+    idx = np.sort(np.random.default_rng(seed).choice(len(t), ntargets, replace=False))
+    t0 = time.perf_counter()
+    direct.direct(s, t[idx], q, kappa)
+    return time.perf_counter() - t0
+
+
+def oracle_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_0911_4114_gb300 import workloads as wl
+    s, t = wl.points("sphere262k")
+    q = wl.charges(len(s), 0, wl.rng(1, salt=1)).astype(np.complex64).astype(np.complex128)
+    for i in range(args.warmup):
+        time_oracle(s, t, q, 64.0, 200, 100 + i)
+    secs = [time_oracle(s, t, q, 64.0, ORACLE_TARGETS, 200 + i) for i in range(args.steps)]
+    value = ORACLE_TARGETS / float(np.mean(secs)) / 1e6
+    line = {"impl": "reference", "metric": "FMM apply Mpoints*RHS/s at stated rel. err; mixed vs FP64 on one GB300",
+            "value": value, "unit": "Mpoints*RHS/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, l2="n/a (host)"),
+            "cpu_baseline": {"value": value, "unit": "Mpoints*RHS/s", "cores": oracle_threads(), "kind": "oracle",
+                             "sample": f"float64 direct sum over all 262,144 sources for {ORACLE_TARGETS} seeded "
+                                       f"targets per step (exact; the FMM approximates it)"},
+            "e2e": {"value": value, "unit": "Mpoints*RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def count_launches(info):
+    lf = info["lf"]
+    n = 3  # permute in, near field, permute out
+    if lf >= 2:
+        n += 1 + 3 * (lf - 2) + (lf - 1) + 3 * (lf - 2) + 1
+    return n
+
+
+def main():
+    args = parse()
+    rank, world = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    from oracle import direct
+    from paper_0911_4114_gb300 import FmmPlan, workloads as wl
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    s, t = wl.points("sphere262k")
+    kappa, eps = 64.0, 1e-6
+    q_host = wl.charges(len(s), 0, wl.rng(1, salt=1)).astype(np.complex64)
+    q = torch.as_tensor(q_host).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(plan, steps, warmup):
+        out = torch.empty((len(t), 1), dtype=torch.complex64, device=dev)
+        q2 = q.reshape(-1, 1)
+        for _ in range(warmup):
+            plan.apply(q2, out=out)
+        torch.cuda.synchronize()
+        barrier(world)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.fill_(1.0)
+            a.record(stream)
+            plan.apply(q2, out=out)
+            b.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return allmax(float(np.mean(ms)), world), out
+
+    plans = {}
+    for precision in (("mixed",) if args.no_fp64 else ("mixed", "fp64")):
+        t0 = time.perf_counter()
+        plans[precision] = FmmPlan(s, t, kappa, eps, precision=precision)
+        plans[precision].plan_seconds = time.perf_counter() - t0
+
+    idx = np.sort(wl.rng(1, salt=2).choice(len(t), 1000, replace=False))
+    ref = direct.direct(s, t[idx], q_host.astype(np.complex128), kappa)
+    results = {}
+    with ClockSampler(local) as clk:
+        for precision, plan in plans.items():
+            ms, out = timed(plan, args.steps, args.warmup)
+            got = out[:, 0].cpu().numpy().astype(np.complex128)[idx]
+            results[precision] = dict(ms=ms, rel_err=float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+    clocks = clk.summary()
+
+    # per-stage device times of the mixed apply (library events on the apply stream)
+    mp = plans["mixed"]
+    mp.set_timing(True)
+    stage_ms = {k: 0.0 for k in ("permute_in", "near_field", "s2m", "m2m", "m2l", "l2l", "l2t", "permute_out")}
+    nst = max(3, args.steps // 2)
+    out = torch.empty((len(t), 1), dtype=torch.complex64, device=dev)
+    for _ in range(nst):
+        flush.fill_(1.0)
+        mp.apply(q.reshape(-1, 1), out=out)
+        for k, v in mp.info()["stage_ms"].items():
+            stage_ms[k] += v / nst
+    mp.set_timing(False)
+    info = mp.info()
+
+    # end to end through the public API: pinned host in, host out
+    qh = torch.as_tensor(q_host).reshape(-1, 1).pin_memory()
+    ph = torch.empty((len(t), 1), dtype=torch.complex64).pin_memory()
+    qd = torch.empty_like(qh, device=dev)
+    od = torch.empty((len(t), 1), dtype=torch.complex64, device=dev)
+    for _ in range(args.warmup):
+        qd.copy_(qh, non_blocking=True)
+        mp.apply(qd, out=od)
+        ph.copy_(od, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        qd.copy_(qh, non_blocking=True)
+        mp.apply(qd, out=od)
+        ph.copy_(od, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e = allmax(float(np.mean(e2e_ms)), world)
+
+    # CPU oracle on this host (rank 0 only), bounded sample
+    cpu = None
+    if rank == 0 and world == 1:
+        secs = time_oracle(s, t, q_host.astype(np.complex128), kappa, ORACLE_TARGETS, 300)
+        cpu = {"value": ORACLE_TARGETS / secs / 1e6, "unit": "Mpoints*RHS/s", "cores": oracle_threads(),
+               "kind": "oracle", "sample": f"float64 direct sum over all 262,144 sources for {ORACLE_TARGETS} "
+                                           f"seeded targets ({secs:.1f} s)"}
+
+    # roofline of the dominant kernel
+    stage = max(stage_ms, key=stage_ms.get)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    if stage == "near_field":
+        pairs = info["p2p_pairs"]
+        achieved = pairs / (stage_ms[stage] * 1e-3) / 1e9
+        peak = 16.0 / 3.0 * 152 * sm_max * 1e6 / 1e9     # MUFU-limited pair rate (3 MUFU ops per pair)
+        roof = {"kernel": "k_p2p_mixed", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_note": "16 MUFU ops/clk/SM x 152 SMs x max SM clock / 3 MUFU ops per pair"}
+    else:
+        roof = {"kernel": stage, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None, "stage_ms": stage_ms[stage]}
+
+    nt = len(t)
+    value = world * nt / (results["mixed"]["ms"] * 1e-3) / 1e6
+    line = {"metric": "FMM apply Mpoints*RHS/s at stated rel. err; mixed vs FP64 on one GB300",
+            "value": value, "unit": "Mpoints*RHS/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": results["mixed"]["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": dict(WORKLOAD, parallelism="replicas" if world > 1 else "single",
+                           l2="flushed before every timed apply (512 MiB write)",
+                           lf=info["lf"], levels={str(l): v for l, v in info["levels"].items()},
+                           p2p_pairs=info["p2p_pairs"]),
+            "rel_err": results["mixed"]["rel_err"],
+            "fp64_path": ({"value": world * nt / (results["fp64"]["ms"] * 1e-3) / 1e6,
+                           "ms_per_step": results["fp64"]["ms"], "rel_err": results["fp64"]["rel_err"],
+                           "lf": plans["fp64"].info()["lf"]} if "fp64" in results else None),
+            "stage_ms": stage_ms, "plan_seconds": plans["mixed"].plan_seconds,
+            "e2e": {"value": world * nt / (e2e * 1e-3) / 1e6, "unit": "Mpoints*RHS/s",
+                    "h2d_bytes_per_step": int(qh.numel() * 8), "d2h_bytes_per_step": int(ph.numel() * 8)},
+            "roofline": roof, "cpu_baseline": cpu, "gpu_launches": count_launches(info) * args.steps,
+            "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

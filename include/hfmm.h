@@ -1,0 +1,169 @@
+/*
+ * hfmm.h -- C ABI of the GB300 Fourier-basis Helmholtz FMM apply.
+ *
+ * The library computes the matrix-vector product of Eq. (HelmholtzMatrixVector)
+ * of Cecka & Darve, "Fourier Based Fast Multipole Method for the Helmholtz
+ * Equation" (arXiv 0911.4114), generalised to targets x_i that differ from the
+ * sources y_j:
+ *
+ *     phi_i = sum_{j : |x_i - y_j| > 0} q_j exp(i kappa |x_i - y_j|) / |x_i - y_j|
+ *
+ * by the multilevel FMM of Section 2 (S2M, M2M, M2L, L2L, L2T and the near
+ * field of Eq. FMM_FinalStep) on the uniform (theta, phi) Fourier quadratures
+ * of Section 3, with the band-limited modified transfer function of Algorithm
+ * BMTF and the FFT re-quadrature of Section 3.4.
+ *
+ * Conventions for every entry point:
+ *   - Point arrays are host, row-major (n, 3) float64 (x, y, z per point).
+ *   - Charge / potential arrays are DEVICE pointers, row-major (n, R) complex
+ *     (interleaved re, im) of the given dtype; R is the number of right-hand
+ *     sides.  The caller owns them; the library never keeps them.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     An apply only enqueues work on that stream: it allocates nothing and
+ *     does not synchronise.  Concurrent applies on one plan are not allowed
+ *     (they share the plan's workspace).
+ *   - Errors are returned as hfmm_status; nothing is thrown across the ABI.
+ *     hfmm_last_error() gives a thread-local message for the last failure.
+ */
+#ifndef HFMM_H
+#define HFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HFMM_MAX_LEVELS 21
+#define HFMM_N_STAGES 8
+
+typedef struct hfmm_plan_s* hfmm_plan_t;
+
+typedef enum {
+    HFMM_OK = 0,
+    HFMM_ERR_ARG = 1,      /* invalid argument (sizes, NaN, kappa <= 0, eps outside (0, 0.1], ...) */
+    HFMM_ERR_CUDA = 2,     /* a CUDA call failed (message in hfmm_last_error) */
+    HFMM_ERR_NOMEM = 3,    /* host or device allocation failed at plan time */
+    HFMM_ERR_UNSTABLE = 4, /* reserved: eps unreachable in the requested precision */
+    HFMM_ERR_TIMEOUT = 5,  /* reserved: device watchdog */
+    HFMM_ERR_STATE = 6     /* call not valid for this plan (e.g. apply on a host-only plan) */
+} hfmm_status;
+
+typedef enum { HFMM_C64 = 0, HFMM_C128 = 1 } hfmm_dtype;
+
+/* Precision policy.  FP64: every stage in float64.  MIXED: per level float32
+ * where the planner's round-off estimate allows it, float64 elsewhere; near
+ * field in float32 with compensated geometry and float64 tile accumulation. */
+typedef enum { HFMM_PREC_FP64 = 0, HFMM_PREC_MIXED = 1 } hfmm_precision;
+
+/* Level precisions reported by hfmm_query. */
+typedef enum { HFMM_LEVEL_FP64 = 0, HFMM_LEVEL_FP32 = 1 } hfmm_level_precision;
+
+typedef struct {
+    /* alpha values tried for each level, in order (Section 3.3.3: |r| = alpha sqrt(3) a_l);
+     * a 0 ends the list.  Default {0.8, 0.7, 0.6, 0}. */
+    double alpha_ladder[4];
+    /* per-level target eps_l = eps_scale * eps (default 0.25) */
+    double eps_scale;
+    /* the tree depth never exceeds the smallest depth at which no box holds more
+     * than max_leaf sources or max_leaf targets (default 64) */
+    int max_leaf;
+    /* > 0: requested depth (replaces the max_leaf rule; active levels may still stop
+     * earlier where the stability rule rejects a level).  0 = use max_leaf. */
+    int depth;
+    /* 1: root cube given by root = {corner x, corner y, corner z, side}; 0: bounding cube */
+    int has_root;
+    double root[4];
+    hfmm_precision precision;
+    /* largest number of right-hand sides an apply may use (workspace size), default 1 */
+    int max_rhs;
+    /* CUDA device ordinal (default 0); -1 builds a host-only plan (queries only, no apply) */
+    int device;
+} hfmm_options;
+
+typedef struct {
+    int64_t ns, nt;
+    double kappa, eps;
+    int occupancy_depth;   /* depth bound from max_leaf (or the requested depth) */
+    int lf;                /* deepest active level; < 2 means no far field (near field = direct sum) */
+    int64_t p2p_pairs;     /* target-source pairs of the near field */
+    /* per level l = 0..HFMM_MAX_LEVELS-1 (valid for 2 <= l <= lf) */
+    int level_nbox[HFMM_MAX_LEVELS];   /* nonempty boxes (valid for 0 <= l <= lf) */
+    int level_ell[HFMM_MAX_LEVELS];
+    int level_ntheta[HFMM_MAX_LEVELS];
+    int64_t level_K[HFMM_MAX_LEVELS];  /* stored samples per signature: sum_n N_phi(theta_n) */
+    int level_precision[HFMM_MAX_LEVELS];
+    double level_alpha[HFMM_MAX_LEVELS];
+    double level_round_est[HFMM_MAX_LEVELS];  /* round-off estimate at the level's precision */
+    int level_ilist_total[HFMM_MAX_LEVELS];   /* sum of interaction-list lengths */
+    /* device milliseconds of the last apply per stage (filled when timing is on):
+     * 0 permute-in, 1 near field, 2 S2M, 3 M2M, 4 M2L, 5 L2L, 6 L2T, 7 permute-out */
+    double stage_ms[HFMM_N_STAGES];
+    int64_t workspace_bytes;
+} hfmm_info;
+
+/* Fill *opt with the defaults listed above. */
+void hfmm_default_options(hfmm_options* opt);
+
+/* Plan stage (host, float64; Sections 2.1, 3.3, 3.4 and the tree of Section 2).
+ * sources: host (ns, 3) float64, ns >= 1.  targets: host (nt, 3) float64, nt >= 1; it
+ * may be the same pointer as sources.  kappa > 0; 0 < eps <= 0.1.  opt may be NULL.
+ * Builds the octree, the interaction and neighbour lists, the per-level truncation
+ * (Eq. EBF refined by Eq. CollinoError), N_theta (Algorithm Ntheta), N_phi(theta_n)
+ * (Algorithm Nphi) and the T^{s,LL} tables (Algorithm BMTF, 34 computed, reflected to
+ * 316), copies the points, and (device >= 0) uploads everything and allocates the apply
+ * workspace on the device.  On success *out owns all of it; release with hfmm_destroy.
+ * Errors: HFMM_ERR_ARG, HFMM_ERR_NOMEM, HFMM_ERR_CUDA. */
+hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, int64_t nt,
+                      double kappa, double eps, const hfmm_options* opt, hfmm_plan_t* out);
+
+/* Apply (device; Section 2 steps on the Section 3 quadratures).
+ * q: device (ns, nrhs) complex of dtype; phi: device (nt, nrhs) complex of dtype,
+ * overwritten with the FMM approximation of the sum above.  1 <= nrhs <= max_rhs.
+ * Enqueued on `stream`; no allocation, no synchronisation.
+ * Errors: HFMM_ERR_ARG (bad pointer/size/dtype), HFMM_ERR_STATE (host-only plan),
+ * HFMM_ERR_CUDA (launch failure). */
+hfmm_status hfmm_apply(hfmm_plan_t plan, const void* q, void* phi, int nrhs, hfmm_dtype dtype,
+                       void* stream);
+
+/* Plan summary and the per-stage times of the last timed apply.  Errors: HFMM_ERR_ARG. */
+hfmm_status hfmm_query(hfmm_plan_t plan, hfmm_info* info);
+
+/* 1: record per-stage CUDA events in later applies (read with hfmm_query after the
+ * stream is synchronised); 0: off (default).  Errors: HFMM_ERR_ARG, HFMM_ERR_STATE. */
+hfmm_status hfmm_set_timing(hfmm_plan_t plan, int on);
+
+/* Release the plan and every host/device buffer it owns.  NULL is accepted. */
+hfmm_status hfmm_destroy(hfmm_plan_t plan);
+
+/* Thread-local message describing the last failure on this thread ("" if none). */
+const char* hfmm_last_error(void);
+
+/* Read-only access to plan internals for tests (host copies).  Returns the number of
+ * elements available (copies min(count, cap) of them into out when out != NULL), or -1
+ * for an unknown request.  `level` selects the tree level; `arg` is the transfer-vector
+ * index for HFMM_GET_TABLE.  Element types: int32 for indices, int64 for permutations,
+ * float64 for the interleaved complex table. */
+typedef enum {
+    HFMM_GET_BOX_IDX = 0,      /* int32 (nbox, 3) box coordinates of `level` */
+    HFMM_GET_BOX_PARENT = 1,   /* int32 (nbox) parent position in level-1 */
+    HFMM_GET_ILIST_OFF = 2,    /* int32 (nbox+1) CSR offsets of the interaction lists */
+    HFMM_GET_ILIST_IDX = 3,    /* int32 interaction-list box positions */
+    HFMM_GET_ILIST_V = 4,      /* int32 transfer-vector indices (di+3)*49+(dj+3)*7+(dk+3) */
+    HFMM_GET_NLIST_OFF = 5,    /* int32 (nbox+1) CSR offsets of the leaf neighbour lists */
+    HFMM_GET_NLIST_IDX = 6,    /* int32 neighbour-list box positions */
+    HFMM_GET_SRC_PERM = 7,     /* int64 (ns) original index of each sorted source */
+    HFMM_GET_TGT_PERM = 8,     /* int64 (nt) original index of each sorted target */
+    HFMM_GET_NPHI = 9,         /* int32 (ntheta/2+1) N_phi(theta_n) of `level` */
+    HFMM_GET_TABLE = 10,       /* float64 (K, 2) T^{s,LL} of `level` for vector `arg` */
+    HFMM_GET_LEAF_SRC = 11,    /* int32 (nbox, 2) first sorted source and count per leaf box */
+    HFMM_GET_LEAF_TGT = 12     /* int32 (nbox, 2) first sorted target and count per leaf box */
+} hfmm_get;
+
+int64_t hfmm_debug_get(hfmm_plan_t plan, int what, int level, int64_t arg, void* out, int64_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HFMM_H */

@@ -1,0 +1,750 @@
+// C ABI of the GB300 Fourier-basis Helmholtz FMM (declared in include/hfmm.h):
+// plan creation (host planner + one upload), the device apply and the queries.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <type_traits>
+#include <string>
+#include <vector>
+
+#include "../../include/hfmm.h"
+#include "host_plan.hpp"
+#include "kernels.cuh"
+
+using namespace hfmm;
+
+namespace {
+
+thread_local std::string g_err;
+
+hfmm_status fail(hfmm_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(HFMM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+struct DevLevel {
+    int prec = kFP64;
+    int64_t K = 0;
+    int nbox = 0;
+    QuadView qv{};
+    BoxView bv{};
+    int32_t* octant = nullptr;
+    int32_t *ioff = nullptr, *iidx = nullptr, *iv = nullptr;
+    int32_t* tslot = nullptr;
+    void* table = nullptr;      // compact T^{s,LL} tables in the level precision
+    cxd* shift64 = nullptr;     // [8][K] exp(i k s.d_o), d_o = child-centre offsets of level l+1
+    cxf* shift32 = nullptr;
+    void* M = nullptr;          // nbox * Rmax * K
+    void* IL = nullptr;         // incoming, then local expansions (in place)
+};
+
+struct Requad {
+    RequadArgs args{};
+    int64_t ga_elems = 0, gb_elems = 0;
+};
+
+}  // namespace
+
+struct hfmm_plan_s {
+    HostPlan hp;
+    int device = -1;
+    int rmax = 1;
+    std::vector<void*> allocs;
+    // leaf / points
+    int64_t *src_perm = nullptr, *tgt_perm = nullptr;
+    double *sx = nullptr, *sy = nullptr, *sz = nullptr, *tx = nullptr, *ty = nullptr, *tz = nullptr;
+    int32_t *sstart = nullptr, *scount = nullptr, *tstart = nullptr, *tcount = nullptr;
+    int32_t *noff = nullptr, *nidx = nullptr;
+    P2PMixedArgs mixed{};
+    cxd *qs = nullptr, *phis = nullptr;
+    DevLevel lev[kMaxLevels];
+    Requad up[kMaxLevels];    // up[l]: level l -> l-1
+    Requad down[kMaxLevels];  // down[l]: level l -> l+1
+    void *ga = nullptr, *gb = nullptr;
+    void *tw64 = nullptr, *tw32 = nullptr;
+    int* twoff = nullptr;
+    int64_t workspace = 0;
+    bool timing = false;
+    cudaEvent_t ev[HFMM_N_STAGES + 1] = {};
+    bool ev_recorded = false;
+};
+
+namespace {
+
+template <typename T>
+hfmm_status dalloc(hfmm_plan_s* p, T** ptr, size_t count) {
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, count * sizeof(T));
+    if (e != cudaSuccess) return fail(HFMM_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    p->allocs.push_back(v);
+    p->workspace += (int64_t)(count * sizeof(T));
+    *ptr = static_cast<T*>(v);
+    return HFMM_OK;
+}
+
+template <typename T>
+hfmm_status upload(hfmm_plan_s* p, T** ptr, const std::vector<T>& host) {
+    hfmm_status s = dalloc(p, ptr, host.size());
+    if (s != HFMM_OK) return s;
+    if (!host.empty()) CK(cudaMemcpy(*ptr, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return HFMM_OK;
+}
+
+#define TRY(x)                          \
+    do {                                \
+        hfmm_status s_ = (x);           \
+        if (s_ != HFMM_OK) return s_;   \
+    } while (0)
+
+size_t cx_bytes(int prec) { return prec == kFP64 ? sizeof(cxd) : sizeof(cxf); }
+
+hfmm_status upload_level(hfmm_plan_s* P, int l) {
+    HostPlan& hp = P->hp;
+    DevLevel& d = P->lev[l];
+    const TreeLevel& T = hp.levels[l];
+    const LevelPlan& lp = hp.lp[l];
+    const Quadrature& q = lp.quad;
+    d.prec = lp.prec;
+    d.K = q.K;
+    d.nbox = (int)T.nbox();
+    // quadrature
+    std::vector<double> shat(3 * q.K), w(q.K);
+    const int half = q.ntheta / 2;
+    const double two_pi = 2.0 * 3.14159265358979323846;
+    for (int n = 0; n <= half; ++n) {
+        const double th = two_pi * n / q.ntheta;
+        const int np = q.nphi[n];
+        const double mult = (n == 0 || n == half) ? 1.0 : 2.0;
+        for (int m = 0; m < np; ++m) {
+            const double ph = two_pi * m / np;
+            const int64_t k = q.off[n] + m;
+            shat[3 * k] = std::cos(ph) * std::sin(th);
+            shat[3 * k + 1] = std::sin(ph) * std::sin(th);
+            shat[3 * k + 2] = std::cos(th);
+            w[k] = mult * (two_pi * two_pi) / ((double)q.ntheta * (double)np);
+        }
+    }
+    int* nphi;
+    int64_t* off;
+    double *dshat, *dw;
+    TRY(upload(P, &nphi, q.nphi));
+    TRY(upload(P, &off, q.off));
+    TRY(upload(P, &dshat, shat));
+    TRY(upload(P, &dw, w));
+    d.qv = QuadView{q.ntheta, half + 1, q.K, nphi, off, dshat, dw};
+    // boxes
+    double* center;
+    int32_t *idx, *parent, *cs = nullptr, *cc = nullptr;
+    TRY(upload(P, &center, T.center));
+    TRY(upload(P, &idx, T.idx));
+    TRY(upload(P, &parent, T.parent));
+    if (!T.child_start.empty()) {
+        TRY(upload(P, &cs, T.child_start));
+        TRY(upload(P, &cc, T.child_count));
+    }
+    d.bv = BoxView{d.nbox, center, idx, parent, cs, cc};
+    std::vector<int32_t> oct(d.nbox);
+    for (int b = 0; b < d.nbox; ++b)
+        oct[b] = 4 * (T.idx[3 * b] & 1) + 2 * (T.idx[3 * b + 1] & 1) + (T.idx[3 * b + 2] & 1);
+    TRY(upload(P, &d.octant, oct));
+    TRY(upload(P, &d.ioff, T.ioff));
+    TRY(upload(P, &d.iidx, T.iidx));
+    TRY(upload(P, &d.iv, T.iv));
+    // transfer tables, compact
+    std::vector<int32_t> slot(kNumTransfer, 0);
+    int ns = 0;
+    for (int v = 0; v < kNumTransfer; ++v) slot[v] = lp.table[v].empty() ? 0 : ns++;
+    TRY(upload(P, &d.tslot, slot));
+    if (d.prec == kFP64) {
+        std::vector<cxd> t((size_t)ns * q.K);
+        for (int v = 0; v < kNumTransfer; ++v)
+            if (!lp.table[v].empty())
+                for (int64_t k = 0; k < q.K; ++k)
+                    t[(size_t)slot[v] * q.K + k] = mk<double>(lp.table[v][k].real(), lp.table[v][k].imag());
+        cxd* dt;
+        TRY(upload(P, &dt, t));
+        d.table = dt;
+    } else {
+        std::vector<cxf> t((size_t)ns * q.K);
+        for (int v = 0; v < kNumTransfer; ++v)
+            if (!lp.table[v].empty())
+                for (int64_t k = 0; k < q.K; ++k)
+                    t[(size_t)slot[v] * q.K + k] =
+                        mk<float>((float)lp.table[v][k].real(), (float)lp.table[v][k].imag());
+        cxf* dt;
+        TRY(upload(P, &dt, t));
+        d.table = dt;
+    }
+    // shift tables for the child offsets of level l+1 (M2M into l, L2L out of l)
+    if (l < hp.lf) {
+        const double ac = hp.side / (double)(1u << (l + 1));
+        std::vector<cxd> s64((size_t)8 * q.K);
+        std::vector<cxf> s32((size_t)8 * q.K);
+        for (int o = 0; o < 8; ++o) {
+            const double dvec[3] = {(((o >> 2) & 1) - 0.5) * ac, (((o >> 1) & 1) - 0.5) * ac,
+                                    ((o & 1) - 0.5) * ac};
+            for (int64_t k = 0; k < q.K; ++k) {
+                const double ph = hp.kappa * (shat[3 * k] * dvec[0] + shat[3 * k + 1] * dvec[1] +
+                                              shat[3 * k + 2] * dvec[2]);
+                s64[(size_t)o * q.K + k] = mk<double>(std::cos(ph), std::sin(ph));
+                s32[(size_t)o * q.K + k] = mk<float>((float)std::cos(ph), (float)std::sin(ph));
+            }
+        }
+        TRY(upload(P, &d.shift64, s64));
+        TRY(upload(P, &d.shift32, s32));
+    }
+    // signature buffers
+    const size_t bytes = (size_t)d.nbox * P->rmax * q.K * cx_bytes(d.prec);
+    unsigned char *m, *il;
+    TRY(dalloc(P, &m, bytes));
+    TRY(dalloc(P, &il, bytes));
+    d.M = m;
+    d.IL = il;
+    return HFMM_OK;
+}
+
+Requad make_requad(const Quadrature& a, const Quadrature& b, int nbox_seq, int rmax) {
+    Requad r;
+    int big = 0;
+    for (int v : a.nphi) big = std::max(big, v);
+    for (int v : b.nphi) big = std::max(big, v);
+    r.args.big = big;
+    r.args.maxlen = std::max(big, std::max(a.ntheta, b.ntheta));
+    r.ga_elems = (int64_t)nbox_seq * rmax * (a.ntheta / 2 + 1) * big;
+    r.gb_elems = (int64_t)nbox_seq * rmax * (b.ntheta / 2 + 1) * big;
+    return r;
+}
+
+hfmm_status upload_plan(hfmm_plan_s* P) {
+    HostPlan& hp = P->hp;
+    CK(cudaSetDevice(P->device));
+    // points, sorted, SoA
+    auto soa = [&](const std::vector<double>& pts, const std::vector<int64_t>& perm, double** x, double** y,
+                   double** z) -> hfmm_status {
+        std::vector<double> a(perm.size()), b(perm.size()), c(perm.size());
+        for (size_t i = 0; i < perm.size(); ++i) {
+            a[i] = pts[3 * perm[i]];
+            b[i] = pts[3 * perm[i] + 1];
+            c[i] = pts[3 * perm[i] + 2];
+        }
+        TRY(upload(P, x, a));
+        TRY(upload(P, y, b));
+        TRY(upload(P, z, c));
+        return HFMM_OK;
+    };
+    TRY(soa(hp.src, hp.src_perm, &P->sx, &P->sy, &P->sz));
+    TRY(soa(hp.tgt, hp.tgt_perm, &P->tx, &P->ty, &P->tz));
+    TRY(upload(P, &P->src_perm, hp.src_perm));
+    TRY(upload(P, &P->tgt_perm, hp.tgt_perm));
+    TRY(upload(P, &P->sstart, hp.src_start));
+    TRY(upload(P, &P->scount, hp.src_count));
+    TRY(upload(P, &P->tstart, hp.tgt_start));
+    TRY(upload(P, &P->tcount, hp.tgt_count));
+    TRY(upload(P, &P->noff, hp.noff));
+    TRY(upload(P, &P->nidx, hp.nidx));
+    // mixed-precision near-field geometry: exact grid integers + fractional offsets
+    {
+        const int gbits = std::min(12, 10 + std::max(0, hp.lf));
+        const double cells = std::ldexp(1.0, gbits);
+        const double scale = cells / hp.side;
+        auto grid = [&](const std::vector<double>& pts, const std::vector<int64_t>& perm, const float4** g,
+                        const float4** o) -> hfmm_status {
+            std::vector<float4> gg(perm.size()), oo(perm.size());
+            for (size_t i = 0; i < perm.size(); ++i) {
+                float gv[3], ov[3];
+                for (int k = 0; k < 3; ++k) {
+                    double u = (pts[3 * perm[i] + k] - hp.corner[k]) * scale;
+                    double f = std::floor(u);
+                    f = std::min(std::max(f, 0.0), cells - 1.0);
+                    gv[k] = (float)f;
+                    ov[k] = (float)(u - f);
+                }
+                gg[i] = make_float4(gv[0], gv[1], gv[2], 0.f);
+                oo[i] = make_float4(ov[0], ov[1], ov[2], 0.f);
+            }
+            float4 *dg, *dof;
+            TRY(upload(P, &dg, gg));
+            TRY(upload(P, &dof, oo));
+            *g = dg;
+            *o = dof;
+            return HFMM_OK;
+        };
+        TRY(grid(hp.tgt, hp.tgt_perm, &P->mixed.tpt, &P->mixed.tof));
+        TRY(grid(hp.src, hp.src_perm, &P->mixed.spt, &P->mixed.sof));
+        const double tau = hp.kappa * (hp.side / cells) / (2.0 * 3.14159265358979323846);
+        P->mixed.tau_hi = (float)tau;
+        P->mixed.tau_lo = (float)(tau - (double)P->mixed.tau_hi);
+        P->mixed.inv_unit = scale;
+    }
+    TRY(dalloc(P, &P->qs, (size_t)hp.ns * P->rmax));
+    TRY(dalloc(P, &P->phis, (size_t)hp.nt * P->rmax));
+    // levels
+    for (int l = 2; l <= hp.lf; ++l) TRY(upload_level(P, l));
+    // re-quadrature passes and scratch
+    int64_t ga = 0, gb = 0;
+    std::vector<int> lengths;
+    auto add_len = [&](const Quadrature& q) {
+        for (int v : q.nphi) lengths.push_back(v);
+        lengths.push_back(q.ntheta);
+    };
+    for (int l = 3; l <= hp.lf; ++l) {
+        P->up[l] = make_requad(hp.lp[l].quad, hp.lp[l - 1].quad, P->lev[l].nbox, P->rmax);
+        P->down[l - 1] = make_requad(hp.lp[l - 1].quad, hp.lp[l].quad, P->lev[l].nbox, P->rmax);
+        for (Requad* r : {&P->up[l], &P->down[l - 1]}) {
+            ga = std::max(ga, r->ga_elems);
+            gb = std::max(gb, r->gb_elems);
+            lengths.push_back(r->args.big);
+        }
+        add_len(hp.lp[l].quad);
+        add_len(hp.lp[l - 1].quad);
+    }
+    TRY(dalloc(P, (cxd**)&P->ga, (size_t)ga));
+    TRY(dalloc(P, (cxd**)&P->gb, (size_t)gb));
+    // twiddle tables
+    int maxlen = 1;
+    for (int v : lengths) maxlen = std::max(maxlen, v);
+    std::vector<int> off(maxlen + 1, -1);
+    std::vector<cxd> t64;
+    std::vector<cxf> t32;
+    std::sort(lengths.begin(), lengths.end());
+    lengths.erase(std::unique(lengths.begin(), lengths.end()), lengths.end());
+    for (int n : lengths) {
+        if (!is_235(n)) return fail(HFMM_ERR_ARG, "internal: FFT length " + std::to_string(n) + " not 2^a3^b5^c");
+        off[n] = (int)t64.size();
+        for (int t = 0; t < n; ++t) {
+            const double ang = 2.0 * 3.14159265358979323846 * (double)t / (double)n;
+            t64.push_back(mk<double>(std::cos(ang), -std::sin(ang)));
+            t32.push_back(mk<float>((float)std::cos(ang), (float)-std::sin(ang)));
+        }
+    }
+    cxd* d64;
+    cxf* d32;
+    TRY(upload(P, &d64, t64));
+    TRY(upload(P, &d32, t32));
+    TRY(upload(P, &P->twoff, off));
+    P->tw64 = d64;
+    P->tw32 = d32;
+    for (int l = 2; l <= hp.lf; ++l) {
+        for (Requad* r : {&P->up[l], &P->down[l]}) {
+            r->args.tw.off = P->twoff;
+        }
+    }
+    for (int l = 3; l <= hp.lf; ++l) {
+        P->up[l].args.qa = P->lev[l].qv;
+        P->up[l].args.qb = P->lev[l - 1].qv;
+        P->down[l - 1].args.qa = P->lev[l - 1].qv;
+        P->down[l - 1].args.qb = P->lev[l].qv;
+        // M2M computes in the parent's precision, L2L in the child's
+        P->up[l].args.tw.pool = (P->lev[l - 1].prec == kFP64) ? P->tw64 : P->tw32;
+        P->down[l - 1].args.tw.pool = (P->lev[l].prec == kFP64) ? P->tw64 : P->tw32;
+    }
+    for (int i = 0; i <= HFMM_N_STAGES; ++i) CK(cudaEventCreate(&P->ev[i]));
+    return HFMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// apply helpers
+// ---------------------------------------------------------------------------
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// opt a kernel into more than 48 KiB of dynamic shared memory when a launch needs it
+template <typename K>
+void smem_opt_in(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename Tin, typename Tc>
+void launch_up(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
+    Requad& rq = P->up[l];
+    DevLevel& c = P->lev[l];
+    DevLevel& p = P->lev[l - 1];
+    const size_t sm = (size_t)kWarps * 2 * rq.args.maxlen * sizeof(cx<Tc>);
+    cx<Tc>* GA = (cx<Tc>*)P->ga;
+    cx<Tc>* GB = (cx<Tc>*)P->gb;
+    smem_opt_in(k_requad_rows_a<Tin, Tc, false>, sm);
+    smem_opt_in(k_requad_cols<Tc>, sm);
+    smem_opt_in(k_requad_rows_c_m2m<Tc, Tc>, sm);
+    int64_t nA = (int64_t)c.nbox * R * rq.args.qa.nrows;
+    k_requad_rows_a<Tin, Tc, false><<<nblk(nA, kWarps), 32 * kWarps, sm, st>>>(
+        rq.args, c.nbox, R, (const cx<Tin>*)c.M, nullptr, nullptr, nullptr, GA);
+    int64_t nB = (int64_t)c.nbox * R * (rq.args.big / 2);
+    k_requad_cols<Tc><<<nblk(nB, kWarps), 32 * kWarps, sm, st>>>(rq.args, c.nbox, R, GA, GB);
+    int64_t nC = (int64_t)p.nbox * R * rq.args.qb.nrows;
+    const cx<Tc>* shift = (const cx<Tc>*)(std::is_same<Tc, double>::value ? (void*)p.shift64 : (void*)p.shift32);
+    k_requad_rows_c_m2m<Tc, Tc><<<nblk(nC, kWarps), 32 * kWarps, sm, st>>>(
+        rq.args, p.nbox, R, p.bv.child_start, p.bv.child_count, c.octant, shift, GB, (cx<Tc>*)p.M);
+}
+
+template <typename Tin, typename Tc>
+void launch_down(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
+    Requad& rq = P->down[l];
+    DevLevel& p = P->lev[l];
+    DevLevel& c = P->lev[l + 1];
+    const size_t sm = (size_t)kWarps * 2 * rq.args.maxlen * sizeof(cx<Tc>);
+    cx<Tc>* GA = (cx<Tc>*)P->ga;
+    cx<Tc>* GB = (cx<Tc>*)P->gb;
+    const cx<Tc>* shift = (const cx<Tc>*)(std::is_same<Tc, double>::value ? (void*)p.shift64 : (void*)p.shift32);
+    smem_opt_in(k_requad_rows_a<Tin, Tc, true>, sm);
+    smem_opt_in(k_requad_cols<Tc>, sm);
+    smem_opt_in(k_requad_rows_c_l2l<Tc>, sm);
+    int64_t nA = (int64_t)c.nbox * R * rq.args.qa.nrows;
+    k_requad_rows_a<Tin, Tc, true><<<nblk(nA, kWarps), 32 * kWarps, sm, st>>>(
+        rq.args, c.nbox, R, (const cx<Tin>*)p.IL, c.bv.parent, c.octant, shift, GA);
+    int64_t nB = (int64_t)c.nbox * R * (rq.args.big / 2);
+    k_requad_cols<Tc><<<nblk(nB, kWarps), 32 * kWarps, sm, st>>>(rq.args, c.nbox, R, GA, GB);
+    int64_t nC = (int64_t)c.nbox * R * rq.args.qb.nrows;
+    k_requad_rows_c_l2l<Tc><<<nblk(nC, kWarps), 32 * kWarps, sm, st>>>(rq.args, c.nbox, R, GB, (cx<Tc>*)c.IL);
+}
+
+template <typename T>
+void launch_m2l(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
+    DevLevel& d = P->lev[l];
+    dim3 grid(d.nbox, nblk(d.K, 256));
+    k_m2l<T><<<grid, 256, 0, st>>>(d.nbox, d.K, d.ioff, d.iidx, d.iv, d.tslot, (const cx<T>*)d.table,
+                                   (const cx<T>*)d.M, R, (cx<T>*)d.IL);
+}
+
+template <typename T>
+void launch_s2m(hfmm_plan_s* P, int R, cudaStream_t st) {
+    const int lf = P->hp.lf;
+    DevLevel& d = P->lev[lf];
+    dim3 grid(d.nbox, nblk(d.K, kS2MThreads));
+    k_s2m<T><<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, P->sstart, P->scount, P->sx, P->sy, P->sz, P->qs, R,
+                                           P->hp.kappa / (2.0 * 3.14159265358979323846), (cx<T>*)d.M);
+}
+
+template <typename T>
+void launch_l2t(hfmm_plan_s* P, int R, cudaStream_t st) {
+    const int lf = P->hp.lf;
+    DevLevel& d = P->lev[lf];
+    k_l2t<T><<<d.nbox, kL2TThreads, 0, st>>>(d.bv, d.qv, P->tstart, P->tcount, P->tx, P->ty, P->tz,
+                                             (const cx<T>*)d.IL, R,
+                                             P->hp.kappa / (2.0 * 3.14159265358979323846), P->phis);
+}
+
+hfmm_status check_launch(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(HFMM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return HFMM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void hfmm_default_options(hfmm_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->alpha_ladder[0] = 0.8;
+    opt->alpha_ladder[1] = 0.7;
+    opt->alpha_ladder[2] = 0.6;
+    opt->alpha_ladder[3] = 0.0;
+    opt->eps_scale = 0.25;
+    opt->max_leaf = 64;
+    opt->depth = 0;
+    opt->has_root = 0;
+    opt->root[3] = 1.0;
+    opt->precision = HFMM_PREC_FP64;
+    opt->max_rhs = 1;
+    opt->device = 0;
+}
+
+const char* hfmm_last_error(void) { return g_err.c_str(); }
+
+hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, int64_t nt, double kappa,
+                      double eps, const hfmm_options* opt_in, hfmm_plan_t* out) {
+    g_err.clear();
+    if (!out) return fail(HFMM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!sources || !targets || ns < 1 || nt < 1) return fail(HFMM_ERR_ARG, "need ns >= 1, nt >= 1 and non-NULL points");
+    if (ns > INT32_MAX || nt > INT32_MAX) return fail(HFMM_ERR_ARG, "ns and nt must fit in int32");
+    if (!(kappa > 0.0) || !std::isfinite(kappa)) return fail(HFMM_ERR_ARG, "kappa must be finite and > 0");
+    if (!(eps > 0.0 && eps <= 0.1)) return fail(HFMM_ERR_ARG, "eps must be in (0, 0.1]");
+    hfmm_options opt;
+    hfmm_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    if (opt.max_rhs < 1 || opt.max_rhs > 4096) return fail(HFMM_ERR_ARG, "max_rhs must be in [1, 4096]");
+    if (opt.max_leaf < 1) return fail(HFMM_ERR_ARG, "max_leaf must be >= 1");
+    if (opt.depth < 0 || opt.depth > kTreeBits) return fail(HFMM_ERR_ARG, "depth must be in [0, 20]");
+    if (!(opt.eps_scale > 0.0 && opt.eps_scale <= 1.0)) return fail(HFMM_ERR_ARG, "eps_scale must be in (0, 1]");
+    if (opt.precision != HFMM_PREC_FP64 && opt.precision != HFMM_PREC_MIXED)
+        return fail(HFMM_ERR_ARG, "unknown precision policy");
+    std::vector<double> alphas;
+    for (int i = 0; i < 4 && opt.alpha_ladder[i] != 0.0; ++i) {
+        if (!(opt.alpha_ladder[i] >= 0.5 && opt.alpha_ladder[i] <= 1.0))
+            return fail(HFMM_ERR_ARG, "alpha values must lie in [0.5, 1]");
+        alphas.push_back(opt.alpha_ladder[i]);
+    }
+    if (alphas.empty()) return fail(HFMM_ERR_ARG, "alpha_ladder is empty");
+    for (int64_t i = 0; i < 3 * ns; ++i)
+        if (!std::isfinite(sources[i])) return fail(HFMM_ERR_ARG, "non-finite source coordinate");
+    for (int64_t i = 0; i < 3 * nt; ++i)
+        if (!std::isfinite(targets[i])) return fail(HFMM_ERR_ARG, "non-finite target coordinate");
+    if (opt.has_root) {
+        if (!(opt.root[3] > 0.0)) return fail(HFMM_ERR_ARG, "root side must be > 0");
+        for (int64_t i = 0; i < ns; ++i)
+            for (int k = 0; k < 3; ++k)
+                if (sources[3 * i + k] < opt.root[k] || sources[3 * i + k] > opt.root[k] + opt.root[3])
+                    return fail(HFMM_ERR_ARG, "a source lies outside the given root cube");
+        for (int64_t i = 0; i < nt; ++i)
+            for (int k = 0; k < 3; ++k)
+                if (targets[3 * i + k] < opt.root[k] || targets[3 * i + k] > opt.root[k] + opt.root[3])
+                    return fail(HFMM_ERR_ARG, "a target lies outside the given root cube");
+    }
+    hfmm_plan_s* P = new (std::nothrow) hfmm_plan_s();
+    if (!P) return fail(HFMM_ERR_NOMEM, "host allocation failed");
+    HostPlan& hp = P->hp;
+    try {
+        hp.src.assign(sources, sources + 3 * ns);
+        hp.tgt.assign(targets, targets + 3 * nt);
+        hp.ns = ns;
+        hp.nt = nt;
+        hp.kappa = kappa;
+        hp.eps = eps;
+        hp.eps_scale = opt.eps_scale;
+        hp.alphas = alphas;
+        hp.max_leaf = opt.max_leaf;
+        hp.depth_req = opt.depth;
+        hp.precision = opt.precision;
+        hp.has_root = opt.has_root;
+        for (int k = 0; k < 4; ++k) hp.root[k] = opt.root[k];
+        std::string e = build_host_plan(hp);
+        if (!e.empty()) {
+            delete P;
+            return fail(HFMM_ERR_ARG, e);
+        }
+    } catch (const std::bad_alloc&) {
+        delete P;
+        return fail(HFMM_ERR_NOMEM, "host allocation failed while planning");
+    } catch (const std::exception& ex) {
+        delete P;
+        return fail(HFMM_ERR_ARG, ex.what());
+    }
+    for (int l = 2; l <= hp.lf; ++l)
+        for (int v : hp.lp[l].quad.nphi)
+            if (v > 1024) {
+                delete P;
+                return fail(HFMM_ERR_ARG, "N_phi above 1024 is not supported");
+            }
+    P->rmax = opt.max_rhs;
+    P->device = opt.device;
+    if (opt.device >= 0) {
+        hfmm_status s = upload_plan(P);
+        if (s != HFMM_OK) {
+            std::string msg = g_err;
+            hfmm_destroy(P);
+            return fail(s, msg);
+        }
+    }
+    *out = P;
+    return HFMM_OK;
+}
+
+hfmm_status hfmm_destroy(hfmm_plan_t P) {
+    if (!P) return HFMM_OK;
+    if (P->device >= 0) {
+        cudaSetDevice(P->device);
+        for (void* v : P->allocs) cudaFree(v);
+        for (int i = 0; i <= HFMM_N_STAGES; ++i)
+            if (P->ev[i]) cudaEventDestroy(P->ev[i]);
+    }
+    delete P;
+    return HFMM_OK;
+}
+
+hfmm_status hfmm_set_timing(hfmm_plan_t P, int on) {
+    if (!P) return fail(HFMM_ERR_ARG, "plan is NULL");
+    if (P->device < 0) return fail(HFMM_ERR_STATE, "host-only plan");
+    P->timing = on != 0;
+    P->ev_recorded = false;
+    return HFMM_OK;
+}
+
+hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_dtype dtype, void* stream) {
+    if (!P) return fail(HFMM_ERR_ARG, "plan is NULL");
+    if (P->device < 0) return fail(HFMM_ERR_STATE, "host-only plan has no device data");
+    if (!q || !phi) return fail(HFMM_ERR_ARG, "q and phi must be device pointers");
+    if (nrhs < 1 || nrhs > P->rmax) return fail(HFMM_ERR_ARG, "nrhs must be in [1, max_rhs]");
+    if (dtype != HFMM_C64 && dtype != HFMM_C128) return fail(HFMM_ERR_ARG, "unknown dtype");
+    CK(cudaSetDevice(P->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    HostPlan& hp = P->hp;
+    const int R = nrhs;
+    const int lf = hp.lf;
+    auto mark = [&](int i) {
+        if (P->timing) cudaEventRecord(P->ev[i], st);
+    };
+    mark(0);
+    if (dtype == HFMM_C64)
+        k_permute_in<float><<<nblk(hp.ns * R, 256), 256, 0, st>>>((const cxf*)q, hp.ns, R, P->src_perm, P->qs);
+    else
+        k_permute_in<double><<<nblk(hp.ns * R, 256), 256, 0, st>>>((const cxd*)q, hp.ns, R, P->src_perm, P->qs);
+    mark(1);
+    const int nleaf = (int)hp.levels[lf].nbox();
+    if (hp.precision == HFMM_PREC_MIXED)
+        k_p2p_mixed<<<nleaf, kP2PThreads, 0, st>>>(nleaf, P->tstart, P->tcount, P->sstart, P->scount, P->noff,
+                                                   P->nidx, P->mixed, P->qs, P->phis, R);
+    else
+        k_p2p_fp64<<<nleaf, kP2PThreads, 0, st>>>(nleaf, P->tstart, P->tcount, P->sstart, P->scount, P->noff,
+                                                  P->nidx, P->tx, P->ty, P->tz, P->sx, P->sy, P->sz, P->qs,
+                                                  P->phis, R, hp.kappa);
+    mark(2);
+    if (lf >= 2) {
+        if (P->lev[lf].prec == kFP64) launch_s2m<double>(P, R, st);
+        else launch_s2m<float>(P, R, st);
+        mark(3);
+        for (int l = lf; l >= 3; --l) {
+            const int pi = P->lev[l].prec, po = P->lev[l - 1].prec;
+            if (pi == kFP64 && po == kFP64) launch_up<double, double>(P, l, R, st);
+            else if (pi == kFP64) launch_up<double, float>(P, l, R, st);
+            else launch_up<float, float>(P, l, R, st);
+        }
+        mark(4);
+        for (int l = 2; l <= lf; ++l) {
+            if (P->lev[l].prec == kFP64) launch_m2l<double>(P, l, R, st);
+            else launch_m2l<float>(P, l, R, st);
+        }
+        mark(5);
+        for (int l = 2; l < lf; ++l) {
+            const int pi = P->lev[l].prec, po = P->lev[l + 1].prec;
+            if (pi == kFP64 && po == kFP64) launch_down<double, double>(P, l, R, st);
+            else if (po == kFP64) launch_down<float, double>(P, l, R, st);
+            else launch_down<float, float>(P, l, R, st);
+        }
+        mark(6);
+        if (P->lev[lf].prec == kFP64) launch_l2t<double>(P, R, st);
+        else launch_l2t<float>(P, R, st);
+        mark(7);
+    } else {
+        for (int i = 3; i <= 7; ++i) mark(i);
+    }
+    if (dtype == HFMM_C64)
+        k_permute_out<float><<<nblk(hp.nt * R, 256), 256, 0, st>>>(P->phis, hp.nt, R, P->tgt_perm, (cxf*)phi);
+    else
+        k_permute_out<double><<<nblk(hp.nt * R, 256), 256, 0, st>>>(P->phis, hp.nt, R, P->tgt_perm, (cxd*)phi);
+    mark(8);
+    P->ev_recorded = P->timing;
+    return check_launch("hfmm_apply");
+}
+
+hfmm_status hfmm_query(hfmm_plan_t P, hfmm_info* info) {
+    if (!P || !info) return fail(HFMM_ERR_ARG, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    const HostPlan& hp = P->hp;
+    info->ns = hp.ns;
+    info->nt = hp.nt;
+    info->kappa = hp.kappa;
+    info->eps = hp.eps;
+    info->occupancy_depth = hp.occ_depth;
+    info->lf = hp.lf;
+    info->p2p_pairs = hp.p2p_pairs;
+    for (int l = 0; l <= hp.lf && l < HFMM_MAX_LEVELS; ++l) {
+        info->level_nbox[l] = (int)hp.levels[l].nbox();
+        if (l >= 2) {
+            const LevelPlan& lp = hp.lp[l];
+            info->level_ell[l] = lp.quad.ell;
+            info->level_ntheta[l] = lp.quad.ntheta;
+            info->level_K[l] = lp.quad.K;
+            info->level_precision[l] = lp.prec == kFP64 ? HFMM_LEVEL_FP64 : HFMM_LEVEL_FP32;
+            info->level_alpha[l] = lp.alpha;
+            info->level_round_est[l] = lp.est;
+            info->level_ilist_total[l] = (int)hp.levels[l].iidx.size();
+        }
+    }
+    info->workspace_bytes = P->workspace;
+    if (P->ev_recorded) {
+        if (cudaEventSynchronize(P->ev[HFMM_N_STAGES]) != cudaSuccess)
+            return fail(HFMM_ERR_CUDA, "event synchronize failed");
+        for (int i = 0; i < HFMM_N_STAGES; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, P->ev[i], P->ev[i + 1]);
+            info->stage_ms[i] = ms;
+        }
+    }
+    return HFMM_OK;
+}
+
+int64_t hfmm_debug_get(hfmm_plan_t P, int what, int level, int64_t arg, void* out, int64_t cap) {
+    if (!P) return -1;
+    const HostPlan& hp = P->hp;
+    auto give = [&](const void* src, int64_t count, size_t esz) -> int64_t {
+        if (out && count > 0) std::memcpy(out, src, (size_t)std::min(count, cap) * esz);
+        return count;
+    };
+    const bool lev_ok = level >= 0 && level <= hp.lf;
+    switch (what) {
+        case HFMM_GET_BOX_IDX:
+            if (!lev_ok) return -1;
+            return give(hp.levels[level].idx.data(), (int64_t)hp.levels[level].idx.size(), 4);
+        case HFMM_GET_BOX_PARENT:
+            if (!lev_ok) return -1;
+            return give(hp.levels[level].parent.data(), (int64_t)hp.levels[level].parent.size(), 4);
+        case HFMM_GET_ILIST_OFF:
+            if (!lev_ok || level < 2) return -1;
+            return give(hp.levels[level].ioff.data(), (int64_t)hp.levels[level].ioff.size(), 4);
+        case HFMM_GET_ILIST_IDX:
+            if (!lev_ok || level < 2) return -1;
+            return give(hp.levels[level].iidx.data(), (int64_t)hp.levels[level].iidx.size(), 4);
+        case HFMM_GET_ILIST_V:
+            if (!lev_ok || level < 2) return -1;
+            return give(hp.levels[level].iv.data(), (int64_t)hp.levels[level].iv.size(), 4);
+        case HFMM_GET_NLIST_OFF:
+            return give(hp.noff.data(), (int64_t)hp.noff.size(), 4);
+        case HFMM_GET_NLIST_IDX:
+            return give(hp.nidx.data(), (int64_t)hp.nidx.size(), 4);
+        case HFMM_GET_SRC_PERM:
+            return give(hp.src_perm.data(), (int64_t)hp.src_perm.size(), 8);
+        case HFMM_GET_TGT_PERM:
+            return give(hp.tgt_perm.data(), (int64_t)hp.tgt_perm.size(), 8);
+        case HFMM_GET_NPHI:
+            if (!lev_ok || level < 2) return -1;
+            return give(hp.lp[level].quad.nphi.data(), (int64_t)hp.lp[level].quad.nphi.size(), 4);
+        case HFMM_GET_TABLE: {
+            if (!lev_ok || level < 2 || arg < 0 || arg >= kNumTransfer) return -1;
+            const auto& t = hp.lp[level].table[arg];
+            if (t.empty()) return -1;
+            const int64_t n = (int64_t)t.size();
+            if (out) {
+                double* o = static_cast<double*>(out);
+                for (int64_t k = 0; k < std::min(n, cap / 2); ++k) {
+                    o[2 * k] = t[k].real();
+                    o[2 * k + 1] = t[k].imag();
+                }
+            }
+            return 2 * n;
+        }
+        case HFMM_GET_LEAF_SRC:
+        case HFMM_GET_LEAF_TGT: {
+            const auto& s = (what == HFMM_GET_LEAF_SRC) ? hp.src_start : hp.tgt_start;
+            const auto& c = (what == HFMM_GET_LEAF_SRC) ? hp.src_count : hp.tgt_count;
+            const int64_t n = (int64_t)s.size();
+            if (out) {
+                int32_t* o = static_cast<int32_t*>(out);
+                for (int64_t i = 0; i < std::min(n, cap / 2); ++i) {
+                    o[2 * i] = s[i];
+                    o[2 * i + 1] = c[i];
+                }
+            }
+            return 2 * n;
+        }
+        default:
+            return -1;
+    }
+}
+
+}  // extern "C"

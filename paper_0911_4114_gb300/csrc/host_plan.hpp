@@ -1,0 +1,83 @@
+// Host-side plan of the Fourier-basis FMM: tree, lists, per-level quadratures and
+// transfer tables.  Built in float64 on the host by planner.cpp; device.cu uploads it.
+#pragma once
+#include <array>
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace hfmm {
+
+using cd = std::complex<double>;
+
+constexpr int kMaxLevels = 21;
+constexpr int kTreeBits = 20;        // deepest depth the tree code supports
+constexpr int kNumTransfer = 343;    // 7^3 slots, 316 used (one buffer box)
+
+enum LevelPrec { kFP64 = 0, kFP32 = 1 };
+
+// Quadrature of one level: rows n = 0..ntheta/2 with nphi[n] points each (Section 3.4's K).
+struct Quadrature {
+    int ell = 0;
+    int ntheta = 0;
+    std::vector<int> nphi;         // ntheta/2 + 1 entries, multiples of 4
+    std::vector<int64_t> off;      // row offsets, ntheta/2 + 2 entries
+    int64_t K = 0;
+    void finalize();
+};
+
+struct LevelPlan {
+    double a = 0, alpha = 0, r = 0, r0 = 0, eps_abs = 0, est = 0;
+    int prec = kFP64;
+    Quadrature quad;
+    // T^{s,LL} for each of the 343 transfer-vector slots (empty where unused), K each
+    std::vector<std::vector<cd>> table;
+};
+
+struct TreeLevel {
+    std::vector<uint64_t> key;     // Morton keys at this level, ascending
+    std::vector<int32_t> idx;      // (n, 3) integer box coordinates
+    std::vector<int32_t> parent;   // position of the parent box in the level above
+    std::vector<double> center;    // (n, 3)
+    std::vector<int32_t> child_start, child_count;  // children in the level below (contiguous)
+    std::vector<int32_t> ioff, iidx, iv;            // interaction lists (CSR), level >= 2
+    int64_t nbox() const { return (int64_t)key.size(); }
+};
+
+struct HostPlan {
+    // inputs (copied)
+    std::vector<double> src, tgt;  // (n, 3) original order
+    int64_t ns = 0, nt = 0;
+    double kappa = 0, eps = 0, eps_l = 0;
+    // options
+    std::vector<double> alphas;
+    double eps_scale = 0.25;
+    int max_leaf = 64, depth_req = 0, precision = 0;
+    int has_root = 0;
+    double root[4] = {0, 0, 0, 1};
+    // tree
+    double corner[3] = {0, 0, 0}, side = 1;
+    int occ_depth = 0;   // depth bound (max_leaf rule or requested depth)
+    int lf = 0;          // deepest active level (tree depth used by the apply)
+    std::vector<int64_t> src_perm, tgt_perm;
+    std::vector<TreeLevel> levels;                  // 0..lf
+    std::vector<int32_t> src_start, src_count, tgt_start, tgt_count;  // per leaf box
+    std::vector<int32_t> noff, nidx;                // leaf neighbour lists (CSR)
+    int64_t p2p_pairs = 0;
+    // per level l = 2..lf
+    std::vector<LevelPlan> lp;                      // indexed by level (0, 1 unused)
+};
+
+// Builds everything on the host; returns "" on success or an error message.
+std::string build_host_plan(HostPlan& hp);
+
+// --- special functions (special.cpp) ----------------------------------------
+void sph_jn_all(int nmax, double x, double* out);     // j_0..j_nmax
+void sph_yn_all(int nmax, double x, double* out);     // y_0..y_nmax
+void bessel_jn_all(int nmax, double x, double* out);  // J_0..J_nmax (integer order)
+
+// --- helpers shared by the planner and the device-side setup -----------------
+bool is_235(int64_t k);
+int64_t round_fft(int64_t n, int64_t mult);
+}  // namespace hfmm

@@ -1,0 +1,502 @@
+// Stage kernels of the FMM apply (Section 2 of the paper on the Section 3 quadratures).
+// Signatures are stored box-major: sig[(box * R + r) * K + k], k over the half grid
+// (rows n = 0..ntheta/2, N_phi(theta_n) samples each).
+#pragma once
+#include "cx.cuh"
+#include "fft.cuh"
+
+namespace hfmm {
+
+constexpr int kWarps = 4;  // warps per CTA in the re-sampling kernels
+
+struct QuadView {
+    int ntheta;        // even
+    int nrows;         // ntheta / 2 + 1
+    int64_t K;
+    const int* nphi;   // nrows
+    const int64_t* off;  // nrows + 1
+    const double* shat;  // (K, 3)
+    const double* w;     // (K) folded quadrature weights
+};
+
+struct BoxView {
+    int nbox;
+    const double* center;      // (nbox, 3)
+    const int32_t* idx;        // (nbox, 3)
+    const int32_t* parent;
+    const int32_t* child_start;
+    const int32_t* child_count;
+};
+
+// ---------------------------------------------------------------------------
+// permutations
+// ---------------------------------------------------------------------------
+template <typename Tin>
+__global__ void k_permute_in(const cx<Tin>* __restrict__ q, int64_t n, int R,
+                             const int64_t* __restrict__ perm, cxd* __restrict__ qs) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n * R) return;
+    int64_t p = t / R;
+    int r = (int)(t - p * R);
+    qs[t] = cvt<double>(q[perm[p] * R + r]);
+}
+
+template <typename Tout>
+__global__ void k_permute_out(const cxd* __restrict__ phis, int64_t n, int R,
+                              const int64_t* __restrict__ perm, cx<Tout>* __restrict__ phi) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n * R) return;
+    int64_t p = t / R;
+    int r = (int)(t - p * R);
+    phi[perm[p] * R + r] = cvt<Tout>(phis[t]);
+}
+
+// ---------------------------------------------------------------------------
+// near field (P2P), float64: phi_i = sum_{j in N(b), R > 0} q_j exp(i k R) / R
+// one CTA per target leaf box, sources staged through shared memory
+// ---------------------------------------------------------------------------
+constexpr int kP2PThreads = 128;
+
+__global__ void k_p2p_fp64(int nbox, const int32_t* __restrict__ tstart, const int32_t* __restrict__ tcount,
+                           const int32_t* __restrict__ sstart, const int32_t* __restrict__ scount,
+                           const int32_t* __restrict__ noff, const int32_t* __restrict__ nidx,
+                           const double* __restrict__ tx, const double* __restrict__ ty,
+                           const double* __restrict__ tz, const double* __restrict__ sx,
+                           const double* __restrict__ sy, const double* __restrict__ sz,
+                           const cxd* __restrict__ qs, cxd* __restrict__ phis, int R, double kappa) {
+    __shared__ double shx[kP2PThreads], shy[kP2PThreads], shz[kP2PThreads];
+    __shared__ cxd shq[kP2PThreads * 4];
+    const int b = blockIdx.x;
+    if (b >= nbox) return;
+    const int t0 = tstart[b], tc = tcount[b];
+    for (int r0 = 0; r0 < R; r0 += 4) {
+        const int rn = min(4, R - r0);
+        for (int tb = 0; tb < tc; tb += kP2PThreads) {
+            const int ti = tb + threadIdx.x;
+            const bool active = ti < tc;
+            double x = 0, y = 0, z = 0;
+            if (active) {
+                x = tx[t0 + ti];
+                y = ty[t0 + ti];
+                z = tz[t0 + ti];
+            }
+            cxd acc[4];
+            for (int r = 0; r < 4; ++r) acc[r] = mk<double>(0, 0);
+            for (int nb = noff[b]; nb < noff[b + 1]; ++nb) {
+                const int s = nidx[nb];
+                const int s0 = sstart[s], sc = scount[s];
+                for (int sb = 0; sb < sc; sb += kP2PThreads) {
+                    const int sn = min(kP2PThreads, sc - sb);
+                    __syncthreads();
+                    if (threadIdx.x < sn) {
+                        const int j = s0 + sb + threadIdx.x;
+                        shx[threadIdx.x] = sx[j];
+                        shy[threadIdx.x] = sy[j];
+                        shz[threadIdx.x] = sz[j];
+                        for (int r = 0; r < rn; ++r) shq[threadIdx.x * 4 + r] = qs[(int64_t)j * R + r0 + r];
+                    }
+                    __syncthreads();
+                    if (active) {
+                        for (int jj = 0; jj < sn; ++jj) {
+                            const double dx = x - shx[jj], dy = y - shy[jj], dz = z - shz[jj];
+                            const double r2 = dx * dx + dy * dy + dz * dz;
+                            if (r2 == 0.0) continue;
+                            const double rr = sqrt(r2);
+                            double sn_, cs_;
+                            sincos(kappa * rr, &sn_, &cs_);
+                            const double inv = 1.0 / rr;
+                            const cxd g = mk<double>(cs_ * inv, sn_ * inv);
+                            for (int r = 0; r < rn; ++r) mac(acc[r], g, shq[jj * 4 + r]);
+                        }
+                    }
+                }
+            }
+            if (active)
+                for (int r = 0; r < rn; ++r) phis[(int64_t)(t0 + ti) * R + r0 + r] = acc[r];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// near field, mixed precision: float32 arithmetic on exactly representable grid
+// coordinates (integer part g on a 2^12 grid of the root cube, fractional part o in
+// [0,1)), squared distance kept as (A exact, B small) and one Newton step on the
+// square root, phase reduced in turns with a split constant; float64 accumulation of
+// float32 tile sums.
+// ---------------------------------------------------------------------------
+struct P2PMixedArgs {
+    const float4* tpt;   // (gx, gy, gz, 0) per sorted target
+    const float4* tof;   // (ox, oy, oz, 0)
+    const float4* spt;
+    const float4* sof;
+    float tau_hi, tau_lo;  // turns per grid unit (kappa * side / 2^12 / 2 pi), split
+    double inv_unit;       // 2^12 / side: 1 / (grid unit in length)
+};
+
+__global__ void k_p2p_mixed(int nbox, const int32_t* __restrict__ tstart, const int32_t* __restrict__ tcount,
+                            const int32_t* __restrict__ sstart, const int32_t* __restrict__ scount,
+                            const int32_t* __restrict__ noff, const int32_t* __restrict__ nidx,
+                            P2PMixedArgs a, const cxd* __restrict__ qs, cxd* __restrict__ phis, int R) {
+    __shared__ float4 shp[kP2PThreads], sho[kP2PThreads];
+    __shared__ cxf shq[kP2PThreads * 4];
+    const int b = blockIdx.x;
+    if (b >= nbox) return;
+    const int t0 = tstart[b], tc = tcount[b];
+    const float two_pi = 6.28318530717958647692f;
+    for (int r0 = 0; r0 < R; r0 += 4) {
+        const int rn = min(4, R - r0);
+        for (int tb = 0; tb < tc; tb += kP2PThreads) {
+            const int ti = tb + threadIdx.x;
+            const bool active = ti < tc;
+            float4 gp = make_float4(0, 0, 0, 0), op = gp;
+            if (active) {
+                gp = a.tpt[t0 + ti];
+                op = a.tof[t0 + ti];
+            }
+            cxd acc[4];
+            for (int r = 0; r < 4; ++r) acc[r] = mk<double>(0, 0);
+            for (int nb = noff[b]; nb < noff[b + 1]; ++nb) {
+                const int s = nidx[nb];
+                const int s0 = sstart[s], sc = scount[s];
+                for (int sb = 0; sb < sc; sb += kP2PThreads) {
+                    const int sn = min(kP2PThreads, sc - sb);
+                    __syncthreads();
+                    if (threadIdx.x < sn) {
+                        const int j = s0 + sb + threadIdx.x;
+                        shp[threadIdx.x] = a.spt[j];
+                        sho[threadIdx.x] = a.sof[j];
+                        for (int r = 0; r < rn; ++r)
+                            shq[threadIdx.x * 4 + r] = cvt<float>(qs[(int64_t)j * R + r0 + r]);
+                    }
+                    __syncthreads();
+                    if (active) {
+                        cxf tile[4];
+                        for (int r = 0; r < 4; ++r) tile[r] = mk<float>(0, 0);
+                        for (int jj = 0; jj < sn; ++jj) {
+                            const float4 sp = shp[jj], so = sho[jj];
+                            const float Dx = gp.x - sp.x, Dy = gp.y - sp.y, Dz = gp.z - sp.z;  // exact
+                            const float ex = op.x - so.x, ey = op.y - so.y, ez = op.z - so.z;
+                            const float A = fmaf(Dx, Dx, fmaf(Dy, Dy, Dz * Dz));           // exact
+                            const float B = fmaf(ex, fmaf(2.0f, Dx, ex),
+                                                 fmaf(ey, fmaf(2.0f, Dy, ey), ez * fmaf(2.0f, Dz, ez)));
+                            const float s2 = A + B;
+                            if (s2 <= 0.0f) continue;
+                            const float rho = rsqrtf(s2);
+                            const float r0f = s2 * rho;
+                            const float e = fmaf(-r0f, r0f, A);
+                            const float c = (e + B) * (0.5f * rho);
+                            // phase in turns: tau * (r0f + c), product error kept by fma
+                            const float th = a.tau_hi * r0f;
+                            float te = fmaf(a.tau_hi, r0f, -th);
+                            te = fmaf(a.tau_hi, c, te);
+                            te = fmaf(a.tau_lo, r0f, te);
+                            const float nt = rintf(th);
+                            const float f = (th - nt) + te;
+                            float sn_, cs_;
+                            __sincosf(two_pi * f, &sn_, &cs_);
+                            const cxf g = mk<float>(cs_ * rho, sn_ * rho);
+                            for (int r = 0; r < rn; ++r) mac(tile[r], g, shq[jj * 4 + r]);
+                        }
+                        for (int r = 0; r < rn; ++r) {
+                            acc[r].x += (double)tile[r].x;
+                            acc[r].y += (double)tile[r].y;
+                        }
+                    }
+                }
+            }
+            if (active)
+                for (int r = 0; r < rn; ++r)
+                    phis[(int64_t)(t0 + ti) * R + r0 + r] = a.inv_unit * acc[r];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// S2M: M_b(s_k) = sum_{j in b} q_j exp(i k s_k . (y_j - c_b)) at the leaf level
+// thread per (box, k); sources of the box staged through shared memory
+// ---------------------------------------------------------------------------
+constexpr int kS2MThreads = 128;
+
+template <typename R>
+__device__ __forceinline__ cx<R> plane_wave(double phase_turns_reduced);
+
+template <>
+__device__ __forceinline__ cxd plane_wave<double>(double t) {
+    double s, c;
+    sincospi(2.0 * t, &s, &c);
+    return mk<double>(c, s);
+}
+template <>
+__device__ __forceinline__ cxf plane_wave<float>(double t) {
+    float s, c;
+    sincospif(2.0f * (float)t, &s, &c);
+    return mk<float>(c, s);
+}
+
+// phase kappa * (s . d) in turns, reduced to [-1/2, 1/2]
+__device__ __forceinline__ double turns(double kappa_turns, const double* s, double dx, double dy, double dz) {
+    double p = kappa_turns * (s[0] * dx + s[1] * dy + s[2] * dz);
+    return p - rint(p);
+}
+
+template <typename R>
+__global__ void k_s2m(BoxView bx, QuadView qv, const int32_t* __restrict__ sstart,
+                      const int32_t* __restrict__ scount, const double* __restrict__ sx,
+                      const double* __restrict__ sy, const double* __restrict__ sz,
+                      const cxd* __restrict__ qs, int R_, double kappa_turns, cx<R>* __restrict__ M) {
+    __shared__ double shd[kS2MThreads * 3];
+    __shared__ cxd shq[kS2MThreads];
+    const int b = blockIdx.x;
+    const int64_t k = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
+    const bool active = k < qv.K;
+    double s[3] = {0, 0, 0};
+    if (active) {
+        s[0] = qv.shat[3 * k];
+        s[1] = qv.shat[3 * k + 1];
+        s[2] = qv.shat[3 * k + 2];
+    }
+    const int s0 = sstart[b], sc = scount[b];
+    const double cxx = bx.center[3 * b], cyy = bx.center[3 * b + 1], czz = bx.center[3 * b + 2];
+    for (int r = 0; r < R_; ++r) {
+        cx<R> acc = mk<R>(0, 0);
+        for (int jb = 0; jb < sc; jb += kS2MThreads) {
+            const int jn = min(kS2MThreads, sc - jb);
+            __syncthreads();
+            if (threadIdx.x < jn) {
+                const int j = s0 + jb + threadIdx.x;
+                shd[3 * threadIdx.x] = sx[j] - cxx;
+                shd[3 * threadIdx.x + 1] = sy[j] - cyy;
+                shd[3 * threadIdx.x + 2] = sz[j] - czz;
+                shq[threadIdx.x] = qs[(int64_t)j * R_ + r];
+            }
+            __syncthreads();
+            if (active)
+                for (int jj = 0; jj < jn; ++jj) {
+                    double t = turns(kappa_turns, s, shd[3 * jj], shd[3 * jj + 1], shd[3 * jj + 2]);
+                    mac(acc, plane_wave<R>(t), cvt<R>(shq[jj]));
+                }
+        }
+        if (active) M[((int64_t)b * R_ + r) * qv.K + k] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// L2T: phi_i += sum_k w_k L_b(s_k) exp(i k s_k . (c_b - x_i)); thread per target
+// ---------------------------------------------------------------------------
+constexpr int kL2TThreads = 128;
+
+template <typename R>
+__global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstart,
+                      const int32_t* __restrict__ tcount, const double* __restrict__ tx,
+                      const double* __restrict__ ty, const double* __restrict__ tz,
+                      const cx<R>* __restrict__ L, int R_, double kappa_turns, cxd* __restrict__ phis) {
+    __shared__ double shs[kL2TThreads * 3];
+    __shared__ cx<R> shl[kL2TThreads];
+    const int b = blockIdx.x;
+    const int t0 = tstart[b], tc = tcount[b];
+    if (tc == 0) return;
+    const double cxx = bx.center[3 * b], cyy = bx.center[3 * b + 1], czz = bx.center[3 * b + 2];
+    for (int r = 0; r < R_; ++r) {
+        const cx<R>* Lb = L + ((int64_t)b * R_ + r) * qv.K;
+        for (int tb = 0; tb < tc; tb += kL2TThreads) {
+            const int ti = tb + threadIdx.x;
+            const bool active = ti < tc;
+            double dx = 0, dy = 0, dz = 0;
+            if (active) {
+                dx = cxx - tx[t0 + ti];
+                dy = cyy - ty[t0 + ti];
+                dz = czz - tz[t0 + ti];
+            }
+            cx<R> acc = mk<R>(0, 0);
+            for (int64_t kb = 0; kb < qv.K; kb += kL2TThreads) {
+                const int kn = (int)min((int64_t)kL2TThreads, qv.K - kb);
+                __syncthreads();
+                if (threadIdx.x < kn) {
+                    const int64_t k = kb + threadIdx.x;
+                    shs[3 * threadIdx.x] = qv.shat[3 * k];
+                    shs[3 * threadIdx.x + 1] = qv.shat[3 * k + 1];
+                    shs[3 * threadIdx.x + 2] = qv.shat[3 * k + 2];
+                    shl[threadIdx.x] = (R)qv.w[k] * Lb[k];
+                }
+                __syncthreads();
+                if (active)
+                    for (int kk = 0; kk < kn; ++kk) {
+                        double t = turns(kappa_turns, &shs[3 * kk], dx, dy, dz);
+                        mac(acc, plane_wave<R>(t), shl[kk]);
+                    }
+            }
+            if (active) {
+                cxd& o = phis[(int64_t)(t0 + ti) * R_ + r];
+                o.x += (double)acc.x;
+                o.y += (double)acc.y;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// M2L: I_a(s_k) = sum_{b in I(a)} T^{s,LL}_{v(a,b)}(s_k) M_b(s_k); thread per (box, k)
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_m2l(int nbox, int64_t K, const int32_t* __restrict__ ioff, const int32_t* __restrict__ iidx,
+                      const int32_t* __restrict__ iv, const int32_t* __restrict__ tslot,
+                      const cx<R>* __restrict__ T, const cx<R>* __restrict__ M, int R_,
+                      cx<R>* __restrict__ I) {
+    const int a = blockIdx.x;
+    const int64_t k = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const int l0 = ioff[a], l1 = ioff[a + 1];
+    for (int r = 0; r < R_; ++r) {
+        cx<R> acc = mk<R>(0, 0);
+        for (int t = l0; t < l1; ++t) {
+            const int b = iidx[t];
+            const cx<R> tv = T[(int64_t)tslot[iv[t]] * K + k];
+            mac(acc, tv, M[((int64_t)b * R_ + r) * K + k]);
+        }
+        I[((int64_t)a * R_ + r) * K + k] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Re-quadrature (Section 3.4) in three passes through global scratch:
+//   A: rows n of quadrature a, N_phi^a(n) -> big          (step 1; optional shift pre-multiply)
+//   B: theta columns m < big/2, ntheta^a -> ntheta^b      (steps 2-4)
+//   C: rows n' of quadrature b, big -> N_phi^b(n')        (step 5; M2M: shift + child sum,
+//                                                          L2L: add the incoming I)
+// GA layout: [(seq_box * R + r) * rows_a + n] * big ; GB: [(seq_box * R + r) * rows_b + n] * big
+// ---------------------------------------------------------------------------
+struct RequadArgs {
+    QuadView qa, qb;
+    int big;
+    int maxlen;       // shared buffer length per warp
+    TwiddleView tw;
+};
+
+// Pass A.  Sequence = (box, r, n) over nbox_seq boxes.  Input signature of box `src_box(b)`:
+//   M2M: the child itself (src = box b of level a, no shift)
+//   L2L: the parent of child b (level a = parent level), times conj(shift[octant(b)])
+template <typename Tin, typename Tc, bool kShift>
+__global__ void k_requad_rows_a(RequadArgs ra, int nbox_seq, int R_, const cx<Tin>* __restrict__ in,
+                                const int32_t* __restrict__ src_box, const int32_t* __restrict__ octant,
+                                const cx<Tc>* __restrict__ shift, cx<Tc>* __restrict__ GA) {
+    extern __shared__ unsigned char smem_raw[];
+    cx<Tc>* sm = reinterpret_cast<cx<Tc>*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cx<Tc>* buf0 = sm + (size_t)warp * 2 * ra.maxlen;
+    cx<Tc>* buf1 = buf0 + ra.maxlen;
+    const int64_t seq = (int64_t)blockIdx.x * kWarps + warp;
+    const int rows = ra.qa.nrows;
+    const int64_t nseq = (int64_t)nbox_seq * R_ * rows;
+    if (seq >= nseq) return;
+    const int n = (int)(seq % rows);
+    const int64_t br = seq / rows;          // box * R + r
+    const int b = (int)(br / R_), r = (int)(br % R_);
+    const int len = ra.qa.nphi[n];
+    const int64_t o = ra.qa.off[n];
+    const int sb = kShift ? src_box[b] : b;
+    const cx<Tin>* src = in + ((int64_t)sb * R_ + r) * ra.qa.K + o;
+    const cx<Tc>* sh = kShift ? shift + (int64_t)octant[b] * ra.qa.K + o : nullptr;
+    for (int j = lane; j < len; j += 32) {
+        cx<Tc> v = cvt<Tc>(src[j]);
+        if (kShift) v = v * conj(sh[j]);
+        buf0[j] = v;
+    }
+    __syncwarp();
+    cx<Tc>* res = warp_resample(buf0, buf1, len, ra.big, ra.tw, lane);
+    cx<Tc>* dst = GA + seq * ra.big;
+    for (int j = lane; j < ra.big; j += 32) dst[j] = res[j];
+}
+
+// Pass B.  Sequence = (box, r, m), m < big/2.
+template <typename Tc>
+__global__ void k_requad_cols(RequadArgs ra, int nbox_seq, int R_, const cx<Tc>* __restrict__ GA,
+                              cx<Tc>* __restrict__ GB) {
+    extern __shared__ unsigned char smem_raw[];
+    cx<Tc>* sm = reinterpret_cast<cx<Tc>*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cx<Tc>* buf0 = sm + (size_t)warp * 2 * ra.maxlen;
+    cx<Tc>* buf1 = buf0 + ra.maxlen;
+    const int hb = ra.big / 2;
+    const int64_t seq = (int64_t)blockIdx.x * kWarps + warp;
+    const int64_t nseq = (int64_t)nbox_seq * R_ * hb;
+    if (seq >= nseq) return;
+    const int m = (int)(seq % hb);
+    const int64_t br = seq / hb;
+    const int nta = ra.qa.ntheta, ntb = ra.qb.ntheta;
+    const int ha = nta / 2, hbr = ntb / 2;
+    const cx<Tc>* ga = GA + br * (int64_t)ra.qa.nrows * ra.big;
+    for (int t = lane; t < nta; t += 32) {
+        buf0[t] = (t <= ha) ? ga[(int64_t)t * ra.big + m] : ga[(int64_t)(nta - t) * ra.big + m + hb];
+    }
+    __syncwarp();
+    cx<Tc>* res = warp_resample(buf0, buf1, nta, ntb, ra.tw, lane);
+    cx<Tc>* gb = GB + br * (int64_t)ra.qb.nrows * ra.big;
+    for (int n = lane; n <= hbr; n += 32) {
+        gb[(int64_t)n * ra.big + m] = res[n];
+        gb[(int64_t)n * ra.big + m + hb] = res[(ntb - n) % ntb];
+    }
+}
+
+// Pass C for L2L.  Sequence = (child, r, n'); L_child = anterp(...) + I_child, in place.
+template <typename Tc>
+__global__ void k_requad_rows_c_l2l(RequadArgs ra, int nbox_seq, int R_, const cx<Tc>* __restrict__ GB,
+                                    cx<Tc>* __restrict__ IL) {
+    extern __shared__ unsigned char smem_raw[];
+    cx<Tc>* sm = reinterpret_cast<cx<Tc>*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cx<Tc>* buf0 = sm + (size_t)warp * 2 * ra.maxlen;
+    cx<Tc>* buf1 = buf0 + ra.maxlen;
+    const int rows = ra.qb.nrows;
+    const int64_t seq = (int64_t)blockIdx.x * kWarps + warp;
+    const int64_t nseq = (int64_t)nbox_seq * R_ * rows;
+    if (seq >= nseq) return;
+    const int n = (int)(seq % rows);
+    const int64_t br = seq / rows;
+    const cx<Tc>* row = GB + seq * ra.big;
+    for (int j = lane; j < ra.big; j += 32) buf0[j] = row[j];
+    __syncwarp();
+    const int len = ra.qb.nphi[n];
+    cx<Tc>* res = warp_resample(buf0, buf1, ra.big, len, ra.tw, lane);
+    cx<Tc>* dst = IL + br * ra.qb.K + ra.qb.off[n];
+    for (int j = lane; j < len; j += 32) dst[j] = dst[j] + res[j];
+}
+
+// Pass C for M2M.  Sequence = (parent, r, n'); M_parent = sum_children shift * anterp(child).
+template <typename Tc, typename Tout>
+__global__ void k_requad_rows_c_m2m(RequadArgs ra, int nparent, int R_, const int32_t* __restrict__ child_start,
+                                    const int32_t* __restrict__ child_count, const int32_t* __restrict__ octant,
+                                    const cx<Tc>* __restrict__ shift, const cx<Tc>* __restrict__ GB,
+                                    cx<Tout>* __restrict__ Mp) {
+    extern __shared__ unsigned char smem_raw[];
+    cx<Tc>* sm = reinterpret_cast<cx<Tc>*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cx<Tc>* buf0 = sm + (size_t)warp * 2 * ra.maxlen;
+    cx<Tc>* buf1 = buf0 + ra.maxlen;
+    const int rows = ra.qb.nrows;
+    const int64_t seq = (int64_t)blockIdx.x * kWarps + warp;
+    const int64_t nseq = (int64_t)nparent * R_ * rows;
+    if (seq >= nseq) return;
+    const int n = (int)(seq % rows);
+    const int64_t pr = seq / rows;
+    const int p = (int)(pr / R_), r = (int)(pr % R_);
+    const int len = ra.qb.nphi[n];
+    const int64_t o = ra.qb.off[n];
+    // each lane owns outputs j = lane, lane + 32, ...: accumulate across children in registers
+    constexpr int kMaxPerLane = 32;   // len <= 1024
+    cx<Tc> acc[kMaxPerLane];
+    for (int i = 0; i < kMaxPerLane; ++i) acc[i] = mk<Tc>(0, 0);
+    const int c0 = child_start[p], cn = child_count[p];
+    for (int c = c0; c < c0 + cn; ++c) {
+        const cx<Tc>* row = GB + (((int64_t)c * R_ + r) * rows + n) * ra.big;
+        for (int j = lane; j < ra.big; j += 32) buf0[j] = row[j];
+        __syncwarp();
+        cx<Tc>* res = warp_resample(buf0, buf1, ra.big, len, ra.tw, lane);
+        const cx<Tc>* sh = shift + (int64_t)octant[c] * ra.qb.K + o;
+        for (int i = 0, j = lane; j < len; ++i, j += 32) acc[i] = acc[i] + res[j] * sh[j];
+        __syncwarp();
+    }
+    cx<Tout>* dst = Mp + ((int64_t)p * R_ + r) * ra.qb.K + o;
+    for (int i = 0, j = lane; j < len; ++i, j += 32) dst[j] = cvt<Tout>(acc[i]);
+}
+
+}  // namespace hfmm

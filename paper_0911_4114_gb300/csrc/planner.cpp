@@ -1,0 +1,632 @@
+// Host planner of the Fourier-basis FMM (float64):
+//   * octree over sources and targets, interaction lists and neighbour lists (Section 2);
+//   * per level: truncation l (Eq. EBF start, Eq. CollinoError refinement, Section 2.1),
+//     N_theta (Algorithm Ntheta), N_phi(theta_n) (Algorithm Nphi), the choice of alpha and
+//     precision by the round-off estimate of the quadrature sum;
+//   * T^{s,LL} for the 34 transfer vectors with x >= y >= 0, z >= 0 (Figure SemiOctant) by
+//     Algorithm BMTF followed by the per-row phi anterpolation of Section 3.3.2, then
+//     reflected into the other 282 of the 316 one-buffer-box vectors by index permutations.
+//
+// Conventions that the paper leaves open (identical rules are applied by the test oracle,
+// which is an independent implementation):
+//   root cube = given, or the bounding cube of all points (side = largest extent);
+//   box index at depth D = clamp(floor((x - corner) * (2^D / side)), 0, 2^D - 1);
+//   Morton order with the x bit above y above z; points by key then original index;
+//   eps_l = eps_scale * eps, absolute threshold eps_l / |r0|, d0 = -log10(eps_l);
+//   |r| = alpha sqrt(3) a_l, |r0| = 2 a_l; N^max = 2l + 64 doubled on failure;
+//   N_theta rounded up to 2 * 2^a 3^b 5^c, N_phi to 4 * 2^a 3^b 5^c; rows mirrored about
+//   theta = pi/2; re-sampling keeps |k| <= min(ceil(K/2), ceil(K'/2)) - 1.
+// Built with -ffp-contract=off so the tree arithmetic rounds exactly as written.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <stdexcept>
+
+#include "host_plan.hpp"
+
+namespace hfmm {
+
+static const double kPi = 3.14159265358979323846;
+static const double kTwoPi = 2.0 * kPi;
+static const double kFourPi2 = 4.0 * kPi * kPi;
+
+void Quadrature::finalize() {
+    off.assign(nphi.size() + 1, 0);
+    for (size_t n = 0; n < nphi.size(); ++n) off[n + 1] = off[n] + nphi[n];
+    K = off.back();
+}
+
+// ---------------------------------------------------------------------------
+// small DFT helpers: exact index reduction, twiddles from one cos/sin table
+// ---------------------------------------------------------------------------
+struct Twiddle {
+    int n;
+    std::vector<cd> w;  // w[t] = exp(-2 pi i t / n)
+    explicit Twiddle(int n_) : n(n_), w(n_) {
+        for (int t = 0; t < n; ++t) {
+            double ang = kTwoPi * (double)t / (double)n;
+            w[t] = cd(std::cos(ang), -std::sin(ang));
+        }
+    }
+    // exp(-2 pi i a b / n) for integer a, b (any sign)
+    cd fwd(int64_t a, int64_t b) const {
+        int64_t t = ((a * b) % n + n) % n;
+        return w[t];
+    }
+    cd inv(int64_t a, int64_t b) const { return std::conj(fwd(a, b)); }
+};
+
+static inline int mod(int64_t a, int64_t n) { return (int)(((a % n) + n) % n); }
+
+// Fourier coefficient of |sin(theta)| (Section 3.2)
+static double s_tilde(int64_t n) {
+    if (n & 1) return 0.0;
+    double d = (double)n;
+    return 2.0 / (kPi * (1.0 - d * d));
+}
+
+// ---------------------------------------------------------------------------
+// truncation (Section 2.1)
+// ---------------------------------------------------------------------------
+static void hankel_all(int nmax, double x, std::vector<cd>& h) {
+    std::vector<double> j(nmax + 1), y(nmax + 1);
+    sph_jn_all(nmax, x, j.data());
+    sph_yn_all(nmax, x, y.data());
+    h.resize(nmax + 1);
+    for (int n = 0; n <= nmax; ++n) h[n] = cd(j[n], y[n]);
+}
+
+static double collino(int ell, double kappa, double r, double r0) {
+    std::vector<cd> h;
+    hankel_all(ell + 1, kappa * r0, h);
+    std::vector<double> j(ell + 2);
+    sph_jn_all(ell + 1, kappa * r, j.data());
+    double best = 0.0;
+    for (int s = 0; s < 2; ++s) {
+        double sg = s == 0 ? 1.0 : -1.0;
+        cd br = h[ell + 1] * j[ell] + sg * h[ell] * j[ell + 1];
+        double v = kappa * kappa * (r * r0 / (r0 + sg * r)) * std::abs(br);
+        best = std::max(best, v);
+    }
+    return best;
+}
+
+static int choose_ell(double kappa, double r, double r0, double eps_abs, double d0) {
+    double kr = kappa * r;
+    int l = (int)std::ceil(kr + 1.8 * std::pow(d0, 2.0 / 3.0) * std::cbrt(kr));
+    l = std::max(1, l);
+    auto pass = [&](int ll) { return collino(ll, kappa, r, r0) <= eps_abs; };
+    if (pass(l)) {
+        while (l > 1 && pass(l - 1)) --l;
+    } else {
+        int start = l;
+        while (!pass(l)) {
+            ++l;
+            if (l > start + 2000) throw std::runtime_error("truncation search did not converge");
+        }
+    }
+    return l;
+}
+
+// ---------------------------------------------------------------------------
+// transfer function (Eq. TransferFn) and Algorithm BMTF
+// ---------------------------------------------------------------------------
+struct Transfer {
+    int ell;
+    double rhat[3];
+    std::vector<cd> c;  // (i k / 4 pi) i^n (2n+1) h_n(k |r0|)
+    Transfer(int ell_, double kappa, const double r0v[3]) : ell(ell_) {
+        double r0 = std::sqrt(r0v[0] * r0v[0] + r0v[1] * r0v[1] + r0v[2] * r0v[2]);
+        for (int k = 0; k < 3; ++k) rhat[k] = r0v[k] / r0;
+        std::vector<cd> h;
+        hankel_all(ell, kappa * r0, h);
+        c.resize(ell + 1);
+        const cd ipow[4] = {cd(1, 0), cd(0, 1), cd(-1, 0), cd(0, -1)};
+        cd pre(0.0, kappa / (4.0 * kPi));
+        for (int n = 0; n <= ell; ++n) c[n] = pre * ipow[n & 3] * (2.0 * n + 1.0) * h[n];
+    }
+    cd eval(double theta, double phi) const {
+        double st = std::sin(theta);
+        double s[3] = {std::cos(phi) * st, std::sin(phi) * st, std::cos(theta)};
+        double t = s[0] * rhat[0] + s[1] * rhat[1] + s[2] * rhat[2];
+        double p0 = 1.0, p1 = t;
+        cd acc = c[0];
+        if (ell >= 1) acc += c[1] * p1;
+        for (int n = 1; n < ell; ++n) {
+            double p2 = ((2.0 * n + 1.0) * t * p1 - n * p0) / (n + 1.0);
+            acc += c[n + 1] * p2;
+            p0 = p1;
+            p1 = p2;
+        }
+        return acc;
+    }
+};
+
+// theta-coefficients (freq -B..B, B = ntheta/2 - 1) of T^{s,L}(., phi) for one phi:
+// sample 1/2 T on 2l+1 theta points, DFT, convolve with F[|sin|], truncate.
+static void bmtf_coeffs(const Transfer& T, const Twiddle& tw, int ntheta, double phi,
+                        std::vector<cd>& out) {
+    const int ell = T.ell, m = 2 * ell + 1;
+    std::vector<cd> samp(m), tf(m);
+    for (int j = 0; j < m; ++j) samp[j] = 0.5 * T.eval(kTwoPi * j / m, phi);
+    for (int f = -ell; f <= ell; ++f) {
+        cd acc = 0.0;
+        for (int j = 0; j < m; ++j) acc += samp[j] * tw.fwd(j, f);
+        tf[f + ell] = acc / (double)m;
+    }
+    const int b = ntheta / 2 - 1;
+    out.assign(2 * b + 1, cd(0.0));
+    for (int n = -b; n <= b; ++n) {
+        cd acc = 0.0;
+        for (int f = -ell; f <= ell; ++f) acc += s_tilde(n - f) * tf[f + ell];
+        out[n + b] = acc;
+    }
+}
+
+static cd eval_theta(const std::vector<cd>& coef, int ntheta, int n_row) {
+    const int b = ntheta / 2 - 1;
+    cd acc = 0.0;
+    for (int f = -b; f <= b; ++f) {
+        int64_t t = mod((int64_t)f * n_row, ntheta);
+        double ang = kTwoPi * (double)t / (double)ntheta;
+        acc += coef[f + b] * cd(std::cos(ang), std::sin(ang));
+    }
+    return acc;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithms Ntheta and Nphi
+// ---------------------------------------------------------------------------
+static int m_index(int nq, int n) {
+    int a = std::abs(n);
+    return (2 * a < nq) ? nq - a : a;
+}
+
+static int choose_ntheta(int ell, double kappa, double r, double r0, double eps_abs) {
+    double r0v[3] = {0.0, 0.0, r0};
+    Transfer T(ell, kappa, r0v);
+    Twiddle tw(2 * ell + 1);
+    int nmax = 2 * ell + 64;
+    for (;;) {
+        std::vector<cd> coef;
+        bmtf_coeffs(T, tw, nmax, 0.0, coef);
+        const int b = nmax / 2 - 1;
+        std::vector<double> J(nmax + 1);
+        bessel_jn_all(nmax, kappa * r, J.data());
+        for (int nq = 2 * ell; nq <= nmax; nq += 2) {
+            double s = 0.0;
+            for (int f = -b; f <= b; ++f) s += std::abs(coef[f + b]) * std::fabs(J[m_index(nq, f)]);
+            if (s < eps_abs / kFourPi2) return nq;
+        }
+        nmax *= 2;
+    }
+}
+
+static std::vector<int> choose_nphi(int ell, double kappa, double r, double r0, int ntheta,
+                                    double eps_abs) {
+    double r0v[3] = {r0, 0.0, 0.0};
+    Transfer T(ell, kappa, r0v);
+    const int m = 2 * ell + 1;
+    Twiddle tw(m);
+    const int half = ntheta / 2;
+    // T^{s,L}(theta_n, 2 pi p / m) for rows n <= half/2
+    std::vector<std::vector<cd>> rows(half / 2 + 1, std::vector<cd>(m));
+    for (int p = 0; p < m; ++p) {
+        std::vector<cd> coef;
+        bmtf_coeffs(T, tw, ntheta, kTwoPi * p / m, coef);
+        for (int n = 0; n <= half / 2; ++n) rows[n][p] = eval_theta(coef, ntheta, n);
+    }
+    std::vector<int> nphi(half + 1, 0);
+    for (int n = 0; n <= half / 2; ++n) {
+        std::vector<double> tt(m);
+        for (int f = -ell; f <= ell; ++f) {
+            cd acc = 0.0;
+            for (int p = 0; p < m; ++p) acc += rows[n][p] * tw.fwd(p, f);
+            tt[f + ell] = std::abs(acc / (double)m);
+        }
+        double x = kappa * r * std::sin(kTwoPi * n / ntheta);
+        int nmax = 2 * ell + 64, found = 0;
+        while (!found) {
+            std::vector<double> J(nmax + 1);
+            bessel_jn_all(nmax, x, J.data());
+            for (int nq = 4; nq <= nmax; nq += 4) {
+                double s = 0.0;
+                for (int f = -ell; f <= ell; ++f) s += tt[f + ell] * std::fabs(J[m_index(nq, f)]);
+                if (s < eps_abs / kFourPi2) {
+                    found = nq;
+                    break;
+                }
+            }
+            nmax *= 2;
+        }
+        nphi[n] = found;
+    }
+    for (int n = 0; n <= half / 2; ++n) nphi[half - n] = nphi[n];
+    return nphi;
+}
+
+static double round_off_estimate(int ell, double kappa, double r0, int64_t K, double u) {
+    std::vector<cd> h;
+    hankel_all(ell, kappa * r0, h);
+    double s = 0.0;
+    for (int n = 0; n <= ell; ++n) s += (2.0 * n + 1.0) * std::norm(h[n]);
+    return u * kappa * r0 * std::sqrt(s) / std::sqrt((double)K);
+}
+
+static void plan_level(double kappa, double a, double eps_l, double alpha, LevelPlan& lp) {
+    lp.a = a;
+    lp.alpha = alpha;
+    lp.r = alpha * std::sqrt(3.0) * a;
+    lp.r0 = 2.0 * a;
+    lp.eps_abs = eps_l / lp.r0;
+    double d0 = -std::log10(eps_l);
+    Quadrature& q = lp.quad;
+    q.ell = choose_ell(kappa, lp.r, lp.r0, lp.eps_abs, d0);
+    q.ntheta = (int)round_fft(choose_ntheta(q.ell, kappa, lp.r, lp.r0, lp.eps_abs), 2);
+    std::vector<int> raw = choose_nphi(q.ell, kappa, lp.r, lp.r0, q.ntheta, lp.eps_abs);
+    q.nphi.resize(raw.size());
+    for (size_t n = 0; n < raw.size(); ++n) q.nphi[n] = (int)round_fft(raw[n], 4);
+    q.finalize();
+}
+
+// ---------------------------------------------------------------------------
+// T^{s,LL}: 34 canonical vectors by Algorithm BMTF + per-row anterpolation, 316 by reflection
+// ---------------------------------------------------------------------------
+static std::vector<cd> tsll_canonical(const LevelPlan& lp, double kappa, const int d[3]) {
+    const Quadrature& q = lp.quad;
+    const int ell = q.ell, ntheta = q.ntheta, half = ntheta / 2;
+    double r0v[3] = {d[0] * lp.a, d[1] * lp.a, d[2] * lp.a};
+    Transfer T(ell, kappa, r0v);
+    Twiddle tw(2 * ell + 1);
+    const int nfull = 4 * ((2 * ell + 1 + 3) / 4);  // even, >= 2l+2: holds the phi band |m| <= l
+    // T^{s,L}(theta_n, phi_p), p < nfull/2 directly, the rest by Eq. NumSphereSym
+    std::vector<cd> grid((size_t)(half + 1) * nfull);
+    for (int p = 0; p < nfull / 2; ++p) {
+        std::vector<cd> coef;
+        bmtf_coeffs(T, tw, ntheta, kTwoPi * p / nfull, coef);
+        for (int n = 0; n < ntheta; ++n) {
+            cd v = eval_theta(coef, ntheta, n);
+            if (n <= half) grid[(size_t)n * nfull + p] = v;
+            int nn = (ntheta - n) % ntheta;  // f(theta_nn, phi_{p + nfull/2}) = f(theta_n, phi_p)
+            if (nn <= half) grid[(size_t)nn * nfull + p + nfull / 2] = v;
+        }
+    }
+    // anterpolate each row nfull -> N_phi(theta_n)
+    Twiddle twf(nfull);
+    std::vector<cd> out((size_t)q.K);
+    for (int n = 0; n <= half; ++n) {
+        const int np = q.nphi[n];
+        const int b = std::min((nfull + 1) / 2, (np + 1) / 2) - 1;
+        std::vector<cd> spec(2 * b + 1);
+        for (int f = -b; f <= b; ++f) {
+            cd acc = 0.0;
+            for (int p = 0; p < nfull; ++p) acc += grid[(size_t)n * nfull + p] * twf.fwd(p, f);
+            spec[f + b] = acc / (double)nfull;
+        }
+        Twiddle twn(np);
+        for (int j = 0; j < np; ++j) {
+            cd acc = 0.0;
+            for (int f = -b; f <= b; ++f) acc += spec[f + b] * twn.inv(j, f);
+            out[(size_t)q.off[n] + j] = acc;
+        }
+    }
+    return out;
+}
+
+// reflect the canonical table into vector d: T_d(s) = T_canon(P F s)
+static std::vector<cd> reflect(const std::vector<cd>& canon, const Quadrature& q, const int d[3]) {
+    const int half = q.ntheta / 2;
+    const bool fx = d[0] < 0, fy = d[1] < 0, fz = d[2] < 0;
+    const bool swap = std::abs(d[0]) < std::abs(d[1]);
+    std::vector<cd> out((size_t)q.K);
+    for (int n = 0; n <= half; ++n) {
+        const int np = q.nphi[n];
+        for (int m = 0; m < np; ++m) {
+            int nn = n, mm = m;
+            if (fx) mm = mod((int64_t)np / 2 - mm, np);
+            if (fy) mm = mod(-(int64_t)mm, np);
+            if (fz) nn = half - nn;
+            if (swap) mm = mod((int64_t)np / 4 - mm, np);
+            out[(size_t)q.off[n] + m] = canon[(size_t)q.off[nn] + mm];
+        }
+    }
+    return out;
+}
+
+static void build_tables(LevelPlan& lp, double kappa) {
+    lp.table.assign(kNumTransfer, {});
+    // canonical set: x >= y >= 0, z >= 0, max >= 2
+    std::vector<std::array<int, 3>> canon;
+    for (int x = 0; x <= 3; ++x)
+        for (int y = 0; y <= x; ++y)
+            for (int z = 0; z <= 3; ++z)
+                if (std::max(x, std::max(y, z)) >= 2) canon.push_back({x, y, z});
+    std::vector<std::vector<cd>> ct(canon.size());
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int c = 0; c < (int)canon.size(); ++c) ct[c] = tsll_canonical(lp, kappa, canon[c].data());
+    for (int di = -3; di <= 3; ++di)
+        for (int dj = -3; dj <= 3; ++dj)
+            for (int dk = -3; dk <= 3; ++dk) {
+                if (std::max(std::abs(di), std::max(std::abs(dj), std::abs(dk))) < 2) continue;
+                int d[3] = {di, dj, dk};
+                std::array<int, 3> cv = {std::max(std::abs(di), std::abs(dj)),
+                                         std::min(std::abs(di), std::abs(dj)), std::abs(dk)};
+                size_t c = std::find(canon.begin(), canon.end(), cv) - canon.begin();
+                int v = (di + 3) * 49 + (dj + 3) * 7 + (dk + 3);
+                lp.table[v] = reflect(ct[c], lp.quad, d);
+            }
+}
+
+// ---------------------------------------------------------------------------
+// tree
+// ---------------------------------------------------------------------------
+static uint64_t morton(uint32_t ix, uint32_t iy, uint32_t iz, int depth) {
+    uint64_t k = 0;
+    for (int b = 0; b < depth; ++b) {
+        k |= (uint64_t)((ix >> b) & 1u) << (3 * b + 2);
+        k |= (uint64_t)((iy >> b) & 1u) << (3 * b + 1);
+        k |= (uint64_t)((iz >> b) & 1u) << (3 * b);
+    }
+    return k;
+}
+
+static void demorton(uint64_t k, int depth, int32_t out[3]) {
+    out[0] = out[1] = out[2] = 0;
+    for (int b = 0; b < depth; ++b) {
+        out[0] |= (int32_t)((k >> (3 * b + 2)) & 1u) << b;
+        out[1] |= (int32_t)((k >> (3 * b + 1)) & 1u) << b;
+        out[2] |= (int32_t)((k >> (3 * b)) & 1u) << b;
+    }
+}
+
+// keys at depth kTreeBits
+static void leaf_keys(const std::vector<double>& p, int64_t n, const double corner[3], double side,
+                      std::vector<uint64_t>& key) {
+    const double nb = (double)(1u << kTreeBits);
+    const double scale = nb / side;
+    key.resize(n);
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t c[3];
+        for (int k = 0; k < 3; ++k) {
+            double v = std::floor((p[3 * i + k] - corner[k]) * scale);
+            if (v < 0.0) v = 0.0;
+            if (v > nb - 1.0) v = nb - 1.0;
+            c[k] = (uint32_t)v;
+        }
+        key[i] = morton(c[0], c[1], c[2], kTreeBits);
+    }
+}
+
+static int max_run(std::vector<uint64_t> sorted_keys, int shift) {
+    int best = 0, run = 0;
+    for (size_t i = 0; i < sorted_keys.size(); ++i) {
+        uint64_t k = sorted_keys[i] >> shift;
+        run = (i > 0 && (sorted_keys[i - 1] >> shift) == k) ? run + 1 : 1;
+        best = std::max(best, run);
+    }
+    return best;
+}
+
+static int64_t find_key(const std::vector<uint64_t>& keys, uint64_t k) {
+    auto it = std::lower_bound(keys.begin(), keys.end(), k);
+    if (it == keys.end() || *it != k) return -1;
+    return it - keys.begin();
+}
+
+static void build_tree(HostPlan& hp) {
+    std::vector<uint64_t> ks, kt;
+    leaf_keys(hp.src, hp.ns, hp.corner, hp.side, ks);
+    leaf_keys(hp.tgt, hp.nt, hp.corner, hp.side, kt);
+    const int D = hp.lf;
+    const int shift = 3 * (kTreeBits - D);
+    // stable sort by depth-D key, ties by original index
+    auto sort_perm = [&](const std::vector<uint64_t>& k, std::vector<int64_t>& perm) {
+        perm.resize(k.size());
+        std::iota(perm.begin(), perm.end(), 0);
+        std::stable_sort(perm.begin(), perm.end(),
+                         [&](int64_t a, int64_t b) { return (k[a] >> shift) < (k[b] >> shift); });
+    };
+    sort_perm(ks, hp.src_perm);
+    sort_perm(kt, hp.tgt_perm);
+    std::vector<uint64_t> allk;
+    allk.reserve(ks.size() + kt.size());
+    for (auto k : ks) allk.push_back(k >> shift);
+    for (auto k : kt) allk.push_back(k >> shift);
+    std::sort(allk.begin(), allk.end());
+    allk.erase(std::unique(allk.begin(), allk.end()), allk.end());
+    hp.levels.assign(D + 1, TreeLevel());
+    for (int l = 0; l <= D; ++l) {
+        TreeLevel& L = hp.levels[l];
+        for (auto k : allk) {
+            uint64_t kl = k >> (3 * (D - l));
+            if (L.key.empty() || L.key.back() != kl) L.key.push_back(kl);
+        }
+        const int64_t nb = L.nbox();
+        L.idx.resize(3 * nb);
+        L.center.resize(3 * nb);
+        L.parent.assign(nb, -1);
+        const double h = hp.side / (double)(1u << l);
+        for (int64_t b = 0; b < nb; ++b) {
+            demorton(L.key[b], l, &L.idx[3 * b]);
+            for (int k = 0; k < 3; ++k)
+                L.center[3 * b + k] = hp.corner[k] + ((double)L.idx[3 * b + k] + 0.5) * h;
+            if (l > 0) L.parent[b] = (int32_t)find_key(hp.levels[l - 1].key, L.key[b] >> 3);
+        }
+        if (l > 0) {
+            TreeLevel& P = hp.levels[l - 1];
+            P.child_start.assign(P.nbox(), 0);
+            P.child_count.assign(P.nbox(), 0);
+            for (int64_t b = nb - 1; b >= 0; --b) {
+                P.child_start[L.parent[b]] = (int32_t)b;
+                P.child_count[L.parent[b]]++;
+            }
+        }
+    }
+    // leaf point ranges
+    TreeLevel& leaf = hp.levels[D];
+    const int64_t nb = leaf.nbox();
+    auto ranges = [&](const std::vector<uint64_t>& k, const std::vector<int64_t>& perm,
+                      std::vector<int32_t>& start, std::vector<int32_t>& count) {
+        start.assign(nb, 0);
+        count.assign(nb, 0);
+        int64_t b = 0;
+        for (int64_t p = 0; p < (int64_t)perm.size(); ++p) {
+            uint64_t kk = k[perm[p]] >> shift;
+            while (leaf.key[b] < kk) ++b;
+            if (count[b] == 0) start[b] = (int32_t)p;
+            count[b]++;
+        }
+        for (int64_t i = 0; i < nb; ++i)
+            if (count[i] == 0) start[i] = (i > 0) ? start[i - 1] + count[i - 1] : 0;
+    };
+    ranges(ks, hp.src_perm, hp.src_start, hp.src_count);
+    ranges(kt, hp.tgt_perm, hp.tgt_start, hp.tgt_count);
+    // interaction lists
+    for (int l = 2; l <= D; ++l) {
+        TreeLevel& L = hp.levels[l];
+        const int n1 = 1 << l;
+        L.ioff.assign(L.nbox() + 1, 0);
+        std::vector<std::vector<std::array<int64_t, 3>>> found(L.nbox());
+#pragma omp parallel for schedule(static)
+        for (int64_t a = 0; a < L.nbox(); ++a) {
+            const int32_t* ia = &L.idx[3 * a];
+            for (int px = -1; px <= 1; ++px)
+                for (int py = -1; py <= 1; ++py)
+                    for (int pz = -1; pz <= 1; ++pz)
+                        for (int c = 0; c < 8; ++c) {
+                            int ib[3] = {((ia[0] >> 1) + px) * 2 + ((c >> 2) & 1),
+                                         ((ia[1] >> 1) + py) * 2 + ((c >> 1) & 1),
+                                         ((ia[2] >> 1) + pz) * 2 + (c & 1)};
+                            bool ok = true;
+                            int dmax = 0;
+                            for (int k = 0; k < 3; ++k) {
+                                if (ib[k] < 0 || ib[k] >= n1) ok = false;
+                                dmax = std::max(dmax, std::abs(ib[k] - ia[k]));
+                            }
+                            if (!ok || dmax <= 1) continue;
+                            int64_t b = find_key(L.key, morton(ib[0], ib[1], ib[2], l));
+                            if (b < 0) continue;
+                            int v = (ib[0] - ia[0] + 3) * 49 + (ib[1] - ia[1] + 3) * 7 + (ib[2] - ia[2] + 3);
+                            found[a].push_back({(int64_t)L.key[b], b, v});
+                        }
+            std::sort(found[a].begin(), found[a].end());
+        }
+        for (int64_t a = 0; a < L.nbox(); ++a) L.ioff[a + 1] = L.ioff[a] + (int32_t)found[a].size();
+        L.iidx.resize(L.ioff.back());
+        L.iv.resize(L.ioff.back());
+        for (int64_t a = 0; a < L.nbox(); ++a)
+            for (size_t t = 0; t < found[a].size(); ++t) {
+                L.iidx[L.ioff[a] + t] = (int32_t)found[a][t][1];
+                L.iv[L.ioff[a] + t] = (int32_t)found[a][t][2];
+            }
+    }
+    // neighbour lists at the leaf level
+    hp.noff.assign(nb + 1, 0);
+    std::vector<std::vector<std::pair<uint64_t, int64_t>>> nf(nb);
+    const int n1 = 1 << D;
+    for (int64_t a = 0; a < nb; ++a) {
+        const int32_t* ia = &leaf.idx[3 * a];
+        for (int dx = -1; dx <= 1; ++dx)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dz = -1; dz <= 1; ++dz) {
+                    int ib[3] = {ia[0] + dx, ia[1] + dy, ia[2] + dz};
+                    if (ib[0] < 0 || ib[1] < 0 || ib[2] < 0 || ib[0] >= n1 || ib[1] >= n1 || ib[2] >= n1)
+                        continue;
+                    int64_t b = find_key(leaf.key, morton(ib[0], ib[1], ib[2], D));
+                    if (b >= 0) nf[a].push_back({leaf.key[b], b});
+                }
+        std::sort(nf[a].begin(), nf[a].end());
+        hp.noff[a + 1] = hp.noff[a] + (int32_t)nf[a].size();
+    }
+    hp.nidx.resize(hp.noff.back());
+    hp.p2p_pairs = 0;
+    for (int64_t a = 0; a < nb; ++a)
+        for (size_t t = 0; t < nf[a].size(); ++t) {
+            hp.nidx[hp.noff[a] + t] = (int32_t)nf[a][t].second;
+            hp.p2p_pairs += (int64_t)hp.tgt_count[a] * hp.src_count[nf[a][t].second];
+        }
+}
+
+// ---------------------------------------------------------------------------
+std::string build_host_plan(HostPlan& hp) {
+    // root cube
+    std::vector<double> lo(3), hi(3);
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = hp.src[k];
+        hi[k] = hp.src[k];
+    }
+    for (int64_t i = 0; i < hp.ns; ++i)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], hp.src[3 * i + k]);
+            hi[k] = std::max(hi[k], hp.src[3 * i + k]);
+        }
+    for (int64_t i = 0; i < hp.nt; ++i)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], hp.tgt[3 * i + k]);
+            hi[k] = std::max(hi[k], hp.tgt[3 * i + k]);
+        }
+    if (hp.has_root) {
+        for (int k = 0; k < 3; ++k) hp.corner[k] = hp.root[k];
+        hp.side = hp.root[3];
+    } else {
+        double side = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+        if (side == 0.0) side = 1.0;
+        hp.side = side;
+        for (int k = 0; k < 3; ++k) hp.corner[k] = (lo[k] + hi[k]) / 2.0 - side / 2.0;
+    }
+    // depth bound
+    if (hp.depth_req > 0) {
+        hp.occ_depth = hp.depth_req;
+    } else {
+        std::vector<uint64_t> ks, kt;
+        leaf_keys(hp.src, hp.ns, hp.corner, hp.side, ks);
+        leaf_keys(hp.tgt, hp.nt, hp.corner, hp.side, kt);
+        std::sort(ks.begin(), ks.end());
+        std::sort(kt.begin(), kt.end());
+        hp.occ_depth = kTreeBits;
+        for (int d = 0; d <= kTreeBits; ++d) {
+            int sh = 3 * (kTreeBits - d);
+            if (max_run(ks, sh) <= hp.max_leaf && max_run(kt, sh) <= hp.max_leaf) {
+                hp.occ_depth = d;
+                break;
+            }
+        }
+    }
+    // active levels: alpha ladder outer, precision inner, precision never decreasing with depth
+    hp.eps_l = hp.eps_scale * hp.eps;
+    hp.lp.assign(kMaxLevels, LevelPlan());
+    std::vector<int> allowed = (hp.precision == 1) ? std::vector<int>{kFP32, kFP64}
+                                                   : std::vector<int>{kFP64};
+    int lf = 1;
+    for (int l = 2; l <= hp.occ_depth && l < kMaxLevels; ++l) {
+        bool ok = false;
+        for (double alpha : hp.alphas) {
+            LevelPlan cand;
+            plan_level(hp.kappa, hp.side / (double)(1u << l), hp.eps_l, alpha, cand);
+            for (int p : allowed) {
+                double u = (p == kFP64) ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+                double f = (p == kFP64) ? 1.0 / 16.0 : 1.0;
+                double est = round_off_estimate(cand.quad.ell, hp.kappa, cand.r0, cand.quad.K, u);
+                if (est <= hp.eps_l * f) {
+                    cand.prec = p;
+                    cand.est = est;
+                    hp.lp[l] = cand;
+                    ok = true;
+                    allowed.erase(allowed.begin(), std::find(allowed.begin(), allowed.end(), p));
+                    break;
+                }
+            }
+            if (ok) break;
+        }
+        if (!ok) break;
+        lf = l;
+    }
+    if (hp.occ_depth < 2) lf = hp.occ_depth;
+    hp.lf = lf;
+    build_tree(hp);
+    for (int l = 2; l <= hp.lf; ++l) build_tables(hp.lp[l], hp.kappa);
+    return "";
+}
+
+}  // namespace hfmm

@@ -1,0 +1,119 @@
+"""Python face of the C ABI: FmmPlan(sources, targets, kappa, eps, ...).apply(q).
+
+Argument marshalling only.  Device buffers are torch tensors (PyTorch supplies memory and
+streams); every step of the apply runs inside libhfmm.so.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _native as nat
+
+
+class FmmPlan:
+    """Plan of the FMM apply for fixed sources, targets, kappa and eps.
+
+    precision: "fp64" (every stage float64) or "mixed" (float32 where the planner's
+    round-off estimate allows, float64 elsewhere).  device=-1 builds a host-only plan
+    (queries only).
+    """
+
+    def __init__(self, sources, targets, kappa, eps, precision="fp64", alphas=(0.8, 0.7, 0.6),
+                 eps_scale=0.25, max_leaf=64, depth=0, root=None, max_rhs=1, device=0):
+        L = nat.lib()
+        src = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 3)
+        tgt = np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 3)
+        self.same = sources is targets
+        opt = nat.Options()
+        L.hfmm_default_options(ctypes.byref(opt))
+        for i in range(4):
+            opt.alpha_ladder[i] = alphas[i] if i < len(alphas) else 0.0
+        opt.eps_scale = eps_scale
+        opt.max_leaf = max_leaf
+        opt.depth = depth
+        if root is not None:
+            opt.has_root = 1
+            for i in range(4):
+                opt.root[i] = float(root[i])
+        opt.precision = {"fp64": nat.PREC_FP64, "mixed": nat.PREC_MIXED}[precision]
+        opt.max_rhs = max_rhs
+        opt.device = device
+        h = ctypes.c_void_p()
+        nat.check(L.hfmm_plan(src.ctypes.data, src.shape[0], tgt.ctypes.data, tgt.shape[0],
+                              float(kappa), float(eps), ctypes.byref(opt), ctypes.byref(h)))
+        self._h = h
+        self.ns, self.nt = src.shape[0], tgt.shape[0]
+        self.max_rhs = max_rhs
+        self.precision = precision
+        self.device = device
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            nat.lib().hfmm_destroy(h)
+            self._h = None
+
+    def close(self):
+        self.__del__()
+
+    # -- apply ---------------------------------------------------------------
+    def apply_ptr(self, q_ptr, phi_ptr, nrhs, dtype, stream_ptr=0):
+        """Raw C-ABI call: device pointers (ints), nrhs, dtype (0 = c64, 1 = c128), stream."""
+        nat.check(nat.lib().hfmm_apply(self._h, q_ptr, phi_ptr, int(nrhs), int(dtype), stream_ptr))
+
+    def apply(self, q, out=None, stream=None):
+        """phi = A q for a CUDA complex64/complex128 tensor q of shape (ns,) or (ns, R)."""
+        import torch
+        if not q.is_cuda:
+            raise ValueError("q must be a CUDA tensor")
+        if q.dtype not in (torch.complex64, torch.complex128):
+            raise ValueError("q must be complex64 or complex128")
+        single = q.dim() == 1
+        q2 = q.reshape(q.shape[0], -1).contiguous()
+        if q2.shape[0] != self.ns:
+            raise ValueError(f"q has {q2.shape[0]} rows, plan has {self.ns} sources")
+        r = q2.shape[1]
+        if out is None:
+            out = torch.empty((self.nt, r), dtype=q.dtype, device=q.device)
+        elif out.shape != (self.nt, r) or out.dtype != q.dtype or not out.is_contiguous():
+            raise ValueError("out must be a contiguous (nt, R) tensor of q's dtype")
+        st = stream if stream is not None else torch.cuda.current_stream(q.device)
+        dtype = nat.C64 if q.dtype == torch.complex64 else nat.C128
+        self.apply_ptr(q2.data_ptr(), out.data_ptr(), r, dtype, st.cuda_stream)
+        return out[:, 0] if single else out
+
+    # -- queries -------------------------------------------------------------
+    def set_timing(self, on=True):
+        nat.check(nat.lib().hfmm_set_timing(self._h, 1 if on else 0))
+
+    def info(self):
+        inf = nat.Info()
+        nat.check(nat.lib().hfmm_query(self._h, ctypes.byref(inf)))
+        lf = inf.lf
+        levels = {}
+        for l in range(2, lf + 1):
+            levels[l] = dict(nbox=inf.level_nbox[l], ell=inf.level_ell[l], ntheta=inf.level_ntheta[l],
+                             K=inf.level_K[l], alpha=inf.level_alpha[l],
+                             precision="fp64" if inf.level_precision[l] == 0 else "fp32",
+                             round_est=inf.level_round_est[l], ilist_total=inf.level_ilist_total[l])
+        return dict(ns=inf.ns, nt=inf.nt, kappa=inf.kappa, eps=inf.eps, occupancy_depth=inf.occupancy_depth,
+                    lf=lf, p2p_pairs=inf.p2p_pairs, nbox=[inf.level_nbox[l] for l in range(lf + 1)],
+                    levels=levels, stage_ms={nat.STAGES[i]: inf.stage_ms[i] for i in range(nat.N_STAGES)},
+                    workspace_bytes=inf.workspace_bytes)
+
+    def debug_get(self, what, level=0, arg=0):
+        L = nat.lib()
+        code = nat.GET[what]
+        n = L.hfmm_debug_get(self._h, code, level, arg, None, 0)
+        if n < 0:
+            raise KeyError((what, level, arg))
+        dt = {"SRC_PERM": np.int64, "TGT_PERM": np.int64, "TABLE": np.float64}.get(what, np.int32)
+        out = np.zeros(n, dtype=dt)
+        L.hfmm_debug_get(self._h, code, level, arg, out.ctypes.data, n)
+        if what == "TABLE":
+            return out[0::2] + 1j * out[1::2]
+        if what == "BOX_IDX":
+            return out.reshape(-1, 3)
+        if what in ("LEAF_SRC", "LEAF_TGT"):
+            return out.reshape(-1, 2)
+        return out

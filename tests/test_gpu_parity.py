@@ -1,0 +1,104 @@
+"""GPU parity: the CUDA apply (through the C ABI) against the CPU oracle.
+
+FP64 path: element-wise against the oracle FMM on the same plan integers (bound from the
+arithmetic, floor 1e-12) and within eps of the direct sum.  Mixed path: within eps of
+the direct sum.  Full-size sphere: 1,000 sampled targets against the direct sum.
+"""
+import numpy as np
+import pytest
+
+from oracle import direct, fmm as ofmm
+from paper_0911_4114_gb300 import FmmPlan, workloads as wl
+from gpu_util import fp64_parity_tol, rel, run_apply
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _case(name):
+    g = wl.rng(90 + hash(name) % 97)
+    if name == "cube4k":                       # the 4,096-point uniform-cube workload
+        x, _ = wl.points("cube4k_fp64")
+        return x, x, 8 * np.pi, 1e-6, dict(depth=3, root=(0, 0, 0, 1.0))
+    if name == "cube_hf":                      # two active levels, high frequency
+        x = wl.cube(3000, g)
+        return x, x, 60.0, 1e-6, dict(depth=3, root=(0, 0, 0, 1.0))
+    if name == "sphere_small":
+        x = wl.sphere(6000, g)
+        return x, x, 24.0, 1e-6, dict(max_leaf=32)
+    if name == "two_spheres":
+        s = wl.sphere(2000, g)
+        t = wl.sphere(1500, g, radius=1.5)
+        return s, t, 12.0, 1e-6, dict(max_leaf=16)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["cube4k", "cube_hf", "sphere_small", "two_spheres"])
+def test_fp64_matches_oracle_fmm_and_direct(name):
+    s, t, kappa, eps, kw = _case(name)
+    q = wl.charges(len(s), 0, wl.rng(7))
+    lib = FmmPlan(s, t, kappa, eps, precision="fp64", **kw)
+    orc = ofmm.Plan(s, t, kappa, eps, precision="fp64", **kw)
+    assert lib.info()["lf"] == orc.lf
+    got = run_apply(lib, q)
+    want = ofmm.apply(orc, q)
+    tol = fp64_parity_tol(orc)
+    assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want)), (name, tol)
+    assert rel(got, direct.direct(s, t, q, kappa)) <= eps
+
+
+@pytest.mark.parametrize("name", ["cube4k", "cube_hf", "sphere_small", "two_spheres"])
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_mixed_within_eps_of_direct(name, dtype):
+    s, t, kappa, eps, kw = _case(name)
+    q = wl.charges(len(s), 0, wl.rng(8))
+    lib = FmmPlan(s, t, kappa, eps, precision="mixed", **kw)
+    got = run_apply(lib, q, dtype)
+    assert rel(got, direct.direct(s, t, q, kappa)) <= eps
+
+
+def test_multi_rhs_columns_agree():
+    s, t, kappa, eps, kw = _case("cube_hf")
+    q = wl.charges(len(s), 3, wl.rng(9))
+    lib = FmmPlan(s, t, kappa, eps, precision="fp64", max_rhs=4, **kw)
+    orc = ofmm.Plan(s, t, kappa, eps, precision="fp64", **kw)
+    got = run_apply(lib, q)
+    tol = fp64_parity_tol(orc)
+    for r in range(3):
+        one = run_apply(lib, q[:, r])
+        assert np.max(np.abs(one - got[:, r])) <= tol * np.max(np.abs(got))
+    assert rel(got, direct.direct(s, t, q, kappa)) <= eps
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 65, 300])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ragged_and_tiny_inputs(n, precision):
+    g = wl.rng(11, salt=n)
+    x = wl.cube(n, g)
+    x[n // 2] = x[0]                      # a coincident pair where n > 1
+    q = wl.charges(n, 0, g)
+    lib = FmmPlan(x, x, 5.0, 1e-6, precision=precision, max_leaf=8)
+    got = run_apply(lib, q)
+    want = direct.direct(x, x, q, 5.0)
+    if not np.any(want):                  # one point, or only a coincident pair: nothing to sum
+        assert np.all(got == 0)
+    else:
+        assert rel(got, want) <= (1e-13 if precision == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sphere262k_sampled_targets(precision):
+    """The 262,144-point sphere workload at kappa = 64, eps = 1e-6: 1,000 sampled targets."""
+    s, t = wl.points("sphere262k")
+    q = wl.charges(len(s), 0, wl.rng(1, salt=1)).astype(np.complex64)
+    lib = FmmPlan(s, t, 64.0, 1e-6, precision=precision)
+    got = run_apply(lib, q, "c64")
+    idx = np.sort(wl.rng(1, salt=2).choice(len(t), 1000, replace=False))
+    want = direct.direct(s, t[idx], q.astype(np.complex128), 64.0)
+    assert rel(got[idx], want) <= 1e-6

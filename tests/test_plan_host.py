@@ -1,0 +1,126 @@
+"""The library's host planner against the oracle's (CPU only; host-only plans, no GPU).
+
+Integer work (tree, lists, permutations, l, N_theta, N_phi, active levels, alpha and
+precision choices) must agree bit for bit; the T^{s,LL} tables (the library computes
+34 vectors and reflects them, the oracle computes every vector directly) must agree to
+round-off.
+"""
+import numpy as np
+import pytest
+
+from oracle import fmm as ofmm
+from oracle import quadrature as oq
+from paper_0911_4114_gb300 import FmmPlan
+
+CASES = {
+    "cube_low_freq": dict(n=1500, kind="cube", kappa=8 * np.pi, eps=1e-6, depth=3, root=(0, 0, 0, 1.0)),
+    "cube_two_levels": dict(n=1200, kind="cube", kappa=60.0, eps=1e-6, depth=3, root=(0, 0, 0, 1.0)),
+    "sphere_auto_depth": dict(n=3000, kind="sphere", kappa=24.0, eps=1e-5, depth=0, root=None, max_leaf=32),
+    "two_spheres": dict(n=800, kind="two", kappa=12.0, eps=1e-6, depth=0, root=None, max_leaf=16),
+}
+
+
+def _points(c, rng):
+    n = c["n"]
+    if c["kind"] == "cube":
+        x = rng.random((n, 3))
+        return x, x
+    s = rng.standard_normal((n, 3))
+    s /= np.linalg.norm(s, axis=1)[:, None]
+    if c["kind"] == "sphere":
+        return s, s
+    t = rng.standard_normal((n // 2, 3))
+    t *= 1.5 / np.linalg.norm(t, axis=1)[:, None]
+    return s, t
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def pair(request):
+    c = CASES[request.param]
+    rng = np.random.default_rng(hash(request.param) % 2 ** 32)
+    s, t = _points(c, rng)
+    kw = dict(depth=c["depth"], root=c["root"], max_leaf=c.get("max_leaf", 64))
+    out = {}
+    for prec in ("fp64", "mixed"):
+        lib = FmmPlan(s, t, c["kappa"], c["eps"], precision=prec, device=-1, **kw)
+        orc = ofmm.Plan(s, t, c["kappa"], c["eps"], precision=prec, **kw)
+        out[prec] = (lib, orc)
+    return request.param, out
+
+
+def test_levels_and_quadrature_integers(pair):
+    name, out = pair
+    for prec, (lib, orc) in out.items():
+        info = lib.info()
+        assert info["lf"] == orc.lf, (name, prec)
+        assert info["occupancy_depth"] == orc.occupancy_depth
+        for l, lp in orc.levels.items():
+            li = info["levels"][l]
+            assert (li["ell"], li["ntheta"], li["K"]) == (lp.ell, lp.ntheta, lp.K), (name, prec, l)
+            assert li["alpha"] == lp.alpha
+            assert li["precision"] == orc.level_precision[l]
+            assert np.array_equal(lib.debug_get("NPHI", l), lp.nphi)
+            assert li["round_est"] == pytest.approx(lp.rounding_estimate(
+                ofmm.PRECISION_UNIT[orc.level_precision[l]]), rel=1e-9)
+
+
+def test_tree_and_lists_bit_exact(pair):
+    name, out = pair
+    lib, orc = out["fp64"]
+    t = orc.tree
+    assert np.array_equal(lib.debug_get("SRC_PERM"), t.src_perm)
+    assert np.array_equal(lib.debug_get("TGT_PERM"), t.tgt_perm)
+    for l in range(t.depth + 1):
+        assert np.array_equal(lib.debug_get("BOX_IDX", l), t.levels[l]["idx"])
+        if l > 0:
+            assert np.array_equal(lib.debug_get("BOX_PARENT", l), t.levels[l]["parent"])
+    for l in range(2, t.depth + 1):
+        off = lib.debug_get("ILIST_OFF", l)
+        idx = lib.debug_get("ILIST_IDX", l)
+        v = lib.debug_get("ILIST_V", l)
+        for a in range(len(t.ilist[l])):
+            assert np.array_equal(idx[off[a]:off[a + 1]], t.ilist[l][a])
+            assert np.array_equal(v[off[a]:off[a + 1]], t.vlist[l][a])
+    off = lib.debug_get("NLIST_OFF")
+    idx = lib.debug_get("NLIST_IDX")
+    for a in range(len(t.nlist)):
+        assert np.array_equal(idx[off[a]:off[a + 1]], t.nlist[a])
+    ls = lib.debug_get("LEAF_SRC")
+    lt = lib.debug_get("LEAF_TGT")
+    assert np.array_equal(ls[:, 1], t.src_count) and np.array_equal(lt[:, 1], t.tgt_count)
+    nz = t.src_count > 0
+    assert np.array_equal(ls[nz, 0], t.src_start[nz])
+
+
+def test_transfer_tables(pair):
+    name, out = pair
+    lib, orc = out["fp64"]
+    t = orc.tree
+    for l in range(2, t.depth + 1):
+        vs = sorted(set(np.concatenate(t.vlist[l]).tolist()))
+        for v in vs[:: max(1, len(vs) // 12)]:
+            a = lib.debug_get("TABLE", l, v)
+            b = orc.table(l, v)
+            scale = np.max(np.abs(b))
+            est = orc.levels[l].rounding_estimate(oq.U_FP64)
+            assert np.max(np.abs(a - b)) <= max(1e-11, 1e3 * est) * scale, (name, l, v)
+
+
+def test_all_316_reflections_match_direct():
+    rng = np.random.default_rng(0)
+    x = rng.random((600, 3))
+    lib = FmmPlan(x, x, 60.0, 1e-4, depth=2, root=(0, 0, 0, 1.0), device=-1)
+    orc = ofmm.Plan(x, x, 60.0, 1e-4, depth=2, root=(0, 0, 0, 1.0))
+    assert lib.info()["lf"] == 2
+    lp = orc.levels[2]
+    worst = 0.0
+    for v in range(343):
+        d = np.array([v // 49 - 3, (v // 7) % 7 - 3, v % 7 - 3])
+        if np.max(np.abs(d)) < 2:
+            with pytest.raises(KeyError):
+                lib.debug_get("TABLE", 2, v)
+            continue
+        a = lib.debug_get("TABLE", 2, v)
+        b = oq.tsll(lp.ell, 60.0, d * 0.25, lp.ntheta, lp.nphi)
+        worst = max(worst, np.max(np.abs(a - b)) / np.max(np.abs(b)))
+    assert worst < 1e-12
