@@ -162,6 +162,32 @@ typedef enum {
 
 int64_t hfmm_debug_get(hfmm_plan_t plan, int what, int level, int64_t arg, void* out, int64_t cap);
 
+/* Largest ns + nt that hfmm_direct_noalloc accepts. */
+#define HFMM_NOALLOC_MAX_POINTS (1 << 19)
+
+/* Direct near-field sum for callers that cannot allocate device memory.  The paper has
+ * no counterpart: this is a library service.  Some callers cannot call cudaMalloc --
+ * code running while a stream is captured into a CUDA graph (allocation cannot be
+ * captured), or code inside a host framework's operator callback that may only use the
+ * framework's own memory pool.  They have no plan (creating one allocates), so this
+ * entry point takes everything as device pointers and allocates nothing:
+ *   sources (ns, 3), targets (nt, 3): device float64, row-major;
+ *   q (ns, nrhs), phi (nt, nrhs): device complex of dtype; phi is overwritten with
+ *   sum_{j : R_ij > 0} q_j exp(i kappa R_ij) / R_ij over ALL sources (O(ns * nt) work),
+ *   computed with the mixed-precision near-field arithmetic of the planned apply (exact
+ *   float32 grid coordinates, float64 accumulation of float32 tile sums).
+ * Its only extra device memory is a fixed file-scope __device__ array of 256 bytes plus
+ * 32 bytes per point for HFMM_NOALLOC_MAX_POINTS points (16 MiB), which every GPU that
+ * loads the library holds until the process exits.  ns + nt above the limit returns
+ * HFMM_ERR_ARG with a message.  The first call on a device resolves the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call shares the array, so calls that overlap on the GPU
+ * (other streams, other threads) race and must be serialised by the caller.  Enqueued on
+ * `stream`; no synchronisation.  Errors: HFMM_ERR_ARG, HFMM_ERR_CUDA. */
+hfmm_status hfmm_direct_noalloc(const double* sources, int64_t ns, const double* targets, int64_t nt,
+                                const void* q, void* phi, int nrhs, hfmm_dtype dtype, double kappa,
+                                void* stream);
+
 #ifdef __cplusplus
 }
 #endif

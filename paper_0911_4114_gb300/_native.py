@@ -21,7 +21,8 @@ GET = dict(BOX_IDX=0, BOX_PARENT=1, ILIST_OFF=2, ILIST_IDX=3, ILIST_V=4, NLIST_O
            SRC_PERM=7, TGT_PERM=8, NPHI=9, TABLE=10, LEAF_SRC=11, LEAF_TGT=12)
 
 EXPORTS = ("hfmm_default_options", "hfmm_plan", "hfmm_apply", "hfmm_query", "hfmm_set_timing",
-           "hfmm_destroy", "hfmm_last_error", "hfmm_debug_get")
+           "hfmm_destroy", "hfmm_last_error", "hfmm_debug_get", "hfmm_direct_noalloc")
+NOALLOC_MAX_POINTS = 1 << 19
 
 
 class Options(ctypes.Structure):
@@ -71,6 +72,8 @@ def lib():
     L.hfmm_last_error.restype = ctypes.c_char_p
     L.hfmm_debug_get.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64, vp, i64]
     L.hfmm_debug_get.restype = i64
+    L.hfmm_direct_noalloc.argtypes = [vp, i64, vp, i64, vp, vp, ctypes.c_int, ctypes.c_int, dbl, vp]
+    L.hfmm_direct_noalloc.restype = ctypes.c_int
     _lib = L
     return L
 

@@ -33,10 +33,11 @@ def build(verbose=False, extra_nvcc=()):
         obj = os.path.join(BUILD, src + ".o")
         objs.append(obj)
         jobs.append(["g++", *host, "-c", os.path.join(CSRC, src), "-o", obj])
-    obj = os.path.join(BUILD, "api.cu.o")
-    objs.append(obj)
-    jobs.append([nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
-                 *extra_nvcc, "-c", os.path.join(CSRC, "api.cu"), "-o", obj])
+    for src in ("api.cu", "noalloc.cu"):
+        obj = os.path.join(BUILD, src + ".o")
+        objs.append(obj)
+        jobs.append([nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
+                     *extra_nvcc, "-c", os.path.join(CSRC, src), "-o", obj])
     procs = [subprocess.Popen(j, stdout=subprocess.PIPE, stderr=subprocess.STDOUT) for j in jobs]
     failed = []
     for j, p in zip(jobs, procs):

@@ -25,6 +25,12 @@ hfmm_status fail(hfmm_status s, const std::string& msg) {
     return s;
 }
 
+}  // namespace
+
+void hfmm::set_last_error(const std::string& msg) { g_err = msg; }
+
+namespace {
+
 #define CK(call)                                                                              \
     do {                                                                                      \
         cudaError_t e_ = (call);                                                              \

@@ -77,6 +77,9 @@ void sph_jn_all(int nmax, double x, double* out);     // j_0..j_nmax
 void sph_yn_all(int nmax, double x, double* out);     // y_0..y_nmax
 void bessel_jn_all(int nmax, double x, double* out);  // J_0..J_nmax (integer order)
 
+// thread-local message returned by hfmm_last_error (api.cu)
+void set_last_error(const std::string& msg);
+
 // --- helpers shared by the planner and the device-side setup -----------------
 bool is_235(int64_t k);
 int64_t round_fft(int64_t n, int64_t mult);

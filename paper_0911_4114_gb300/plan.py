@@ -117,3 +117,28 @@ class FmmPlan:
         if what in ("LEAF_SRC", "LEAF_TGT"):
             return out.reshape(-1, 2)
         return out
+
+
+def direct_noalloc(sources, targets, q, kappa, out=None, stream=None):
+    """Direct near-field sum through hfmm_direct_noalloc (no device allocation inside).
+
+    sources (ns, 3), targets (nt, 3): CUDA float64 tensors; q: CUDA complex64/128 (ns,) or
+    (ns, R).  For callers that cannot allocate, pass `out` (nt, R) preallocated.
+    """
+    import torch
+    for name, t in (("sources", sources), ("targets", targets)):
+        if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() or t.dim() != 2 or t.shape[1] != 3:
+            raise ValueError(f"{name} must be a contiguous CUDA float64 (n, 3) tensor")
+    if not q.is_cuda or q.dtype not in (torch.complex64, torch.complex128):
+        raise ValueError("q must be a CUDA complex64/complex128 tensor")
+    single = q.dim() == 1
+    q2 = q.reshape(q.shape[0], -1).contiguous()
+    r = q2.shape[1]
+    if out is None:
+        out = torch.empty((targets.shape[0], r), dtype=q.dtype, device=q.device)
+    st = stream if stream is not None else torch.cuda.current_stream(q.device)
+    dtype = nat.C64 if q.dtype == torch.complex64 else nat.C128
+    nat.check(nat.lib().hfmm_direct_noalloc(sources.data_ptr(), sources.shape[0], targets.data_ptr(),
+                                             targets.shape[0], q2.data_ptr(), out.data_ptr(), r, dtype,
+                                             float(kappa), st.cuda_stream))
+    return out[:, 0] if single else out
