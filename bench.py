@@ -35,6 +35,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the float64-path measurement")
+    ap.add_argument("--points", type=int, default=262144, help="smaller sphere for profiling runs")
+    ap.add_argument("--skip-oracle", action="store_true", help="skip the CPU oracle timing")
     return ap.parse_args()
 
 
@@ -164,7 +166,7 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    s, t = wl.points("sphere262k")
+    s, t = wl.points("sphere262k", n=args.points)
     kappa, eps = 64.0, 1e-6
     q_host = wl.charges(len(s), 0, wl.rng(1, salt=1)).astype(np.complex64)
     q = torch.as_tensor(q_host).to(dev)
@@ -245,7 +247,7 @@ def main():
 
     # CPU oracle on this host (rank 0 only), bounded sample
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.skip_oracle:
         secs = time_oracle(s, t, q_host.astype(np.complex128), kappa, ORACLE_TARGETS, 300)
         cpu = {"value": ORACLE_TARGETS / secs / 1e6, "unit": "Mpoints*RHS/s", "cores": oracle_threads(),
                "kind": "oracle", "sample": f"float64 direct sum over all 262,144 sources for {ORACLE_TARGETS} "
@@ -276,7 +278,7 @@ def main():
             "value": value, "unit": "Mpoints*RHS/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": results["mixed"]["ms"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": dict(WORKLOAD, parallelism="replicas" if world > 1 else "single",
+            "config": dict(WORKLOAD, points=len(t), parallelism="replicas" if world > 1 else "single",
                            l2="flushed before every timed apply (512 MiB write)",
                            lf=info["lf"], levels={str(l): v for l, v in info["levels"].items()},
                            p2p_pairs=info["p2p_pairs"]),
