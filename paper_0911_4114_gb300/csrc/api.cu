@@ -79,6 +79,7 @@ struct hfmm_plan_s {
     void *ga = nullptr, *gb = nullptr;
     void *tw64 = nullptr, *tw32 = nullptr;
     int* twoff = nullptr;
+    cdf* cis_tab = nullptr;     // exp(2 pi i j / 256) as double-float pairs
     int64_t workspace = 0;
     bool timing = false;
     cudaEvent_t ev[HFMM_N_STAGES + 1] = {};
@@ -356,6 +357,14 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
         P->up[l].args.tw.pool = (P->lev[l - 1].prec == kFP64) ? P->tw64 : P->tw32;
         P->down[l - 1].args.tw.pool = (P->lev[l].prec == kFP64) ? P->tw64 : P->tw32;
     }
+    {
+        std::vector<cdf> tab(kCisTable);
+        for (int j = 0; j < kCisTable; ++j) {
+            const double a = 2.0 * 3.14159265358979323846 * (double)j / (double)kCisTable;
+            tab[j] = cdf{df_from_double(std::cos(a)), df_from_double(std::sin(a))};
+        }
+        TRY(upload(P, &P->cis_tab, tab));
+    }
     for (int i = 0; i <= HFMM_N_STAGES; ++i) CK(cudaEventCreate(&P->ev[i]));
     return HFMM_OK;
 }
@@ -422,10 +431,20 @@ void launch_m2l(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
                                    (const cx<T>*)d.M, R, (cx<T>*)d.IL);
 }
 
+// float64 levels of the mixed policy evaluate their plane waves in double-float
+bool use_df(hfmm_plan_s* P, int l) { return P->hp.precision == HFMM_PREC_MIXED && P->lev[l].prec == kFP64; }
+
 template <typename T>
 void launch_s2m(hfmm_plan_s* P, int R, cudaStream_t st) {
     const int lf = P->hp.lf;
     DevLevel& d = P->lev[lf];
+    if (std::is_same<T, double>::value && use_df(P, lf)) {
+        dim3 grid(d.nbox, nblk(d.K, kS2MThreads));
+        k_s2m_df<<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, P->sstart, P->scount, P->sx, P->sy, P->sz, P->qs, R,
+                                               P->hp.kappa / (2.0 * 3.14159265358979323846), P->cis_tab,
+                                               (cxd*)d.M);
+        return;
+    }
     dim3 grid(d.nbox, nblk(d.K, kS2MThreads));
     k_s2m<T><<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, P->sstart, P->scount, P->sx, P->sy, P->sz, P->qs, R,
                                            P->hp.kappa / (2.0 * 3.14159265358979323846), (cx<T>*)d.M);
@@ -435,6 +454,12 @@ template <typename T>
 void launch_l2t(hfmm_plan_s* P, int R, cudaStream_t st) {
     const int lf = P->hp.lf;
     DevLevel& d = P->lev[lf];
+    if (std::is_same<T, double>::value && use_df(P, lf)) {
+        k_l2t_df<<<d.nbox, kL2TThreads, 0, st>>>(d.bv, d.qv, P->tstart, P->tcount, P->tx, P->ty, P->tz,
+                                                 (const cxd*)d.IL, R,
+                                                 P->hp.kappa / (2.0 * 3.14159265358979323846), P->cis_tab, P->phis);
+        return;
+    }
     k_l2t<T><<<d.nbox, kL2TThreads, 0, st>>>(d.bv, d.qv, P->tstart, P->tcount, P->tx, P->ty, P->tz,
                                              (const cx<T>*)d.IL, R,
                                              P->hp.kappa / (2.0 * 3.14159265358979323846), P->phis);

@@ -3,6 +3,7 @@
 // (rows n = 0..ntheta/2, N_phi(theta_n) samples each).
 #pragma once
 #include "cx.cuh"
+#include "df.cuh"
 #include "fft.cuh"
 
 namespace hfmm {
@@ -329,6 +330,116 @@ __global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstar
                 cxd& o = phis[(int64_t)(t0 + ti) * R_ + r];
                 o.x += (double)acc.x;
                 o.y += (double)acc.y;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// S2M and L2T of float64 levels in double-float arithmetic on the float32 pipe (about 48
+// significant bits; float64 in memory).  s' = s_k * kappa / (2 pi) and the offsets are
+// split into df pairs; the phase in turns is reduced by its nearest integer and cis_turns
+// evaluates exp(2 pi i r).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ df df_reduce(df t) {
+    const float n = rintf(t.hi);
+    return df_fast_sum(__fsub_rn(t.hi, n), t.lo);
+}
+
+__device__ __forceinline__ void load_cis_table(cdf* sh, const cdf* tab) {
+    for (int i = threadIdx.x; i < kCisTable; i += blockDim.x) sh[i] = tab[i];
+}
+
+__global__ void k_s2m_df(BoxView bx, QuadView qv, const int32_t* __restrict__ sstart,
+                         const int32_t* __restrict__ scount, const double* __restrict__ sx,
+                         const double* __restrict__ sy, const double* __restrict__ sz,
+                         const cxd* __restrict__ qs, int R_, double kappa_turns, const cdf* __restrict__ cis_tab,
+                         cxd* __restrict__ M) {
+    __shared__ df shd[kS2MThreads * 3];
+    __shared__ cdf shq[kS2MThreads];
+    __shared__ cdf tab[kCisTable];
+    load_cis_table(tab, cis_tab);
+    const int b = blockIdx.x;
+    const int64_t k = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
+    const bool active = k < qv.K;
+    df s[3] = {{0, 0}, {0, 0}, {0, 0}};
+    if (active)
+        for (int c = 0; c < 3; ++c) s[c] = df_from_double(qv.shat[3 * k + c] * kappa_turns);
+    const int s0 = sstart[b], sc = scount[b];
+    const double cxx = bx.center[3 * b], cyy = bx.center[3 * b + 1], czz = bx.center[3 * b + 2];
+    for (int r = 0; r < R_; ++r) {
+        cdf acc = {{0, 0}, {0, 0}};
+        for (int jb = 0; jb < sc; jb += kS2MThreads) {
+            const int jn = min(kS2MThreads, sc - jb);
+            __syncthreads();
+            if (threadIdx.x < jn) {
+                const int j = s0 + jb + threadIdx.x;
+                shd[3 * threadIdx.x] = df_from_double(sx[j] - cxx);
+                shd[3 * threadIdx.x + 1] = df_from_double(sy[j] - cyy);
+                shd[3 * threadIdx.x + 2] = df_from_double(sz[j] - czz);
+                const cxd qq = qs[(int64_t)j * R_ + r];
+                shq[threadIdx.x] = cdf{df_from_double(qq.x), df_from_double(qq.y)};
+            }
+            __syncthreads();
+            if (active)
+                for (int jj = 0; jj < jn; ++jj) {
+                    df t = df_mul(s[0], shd[3 * jj]);
+                    t = df_add(t, df_mul(s[1], shd[3 * jj + 1]));
+                    t = df_add(t, df_mul(s[2], shd[3 * jj + 2]));
+                    acc = cdf_add(acc, cdf_mul(cis_turns(df_reduce(t), tab), shq[jj]));
+                }
+        }
+        if (active) M[((int64_t)b * R_ + r) * qv.K + k] = mk<double>(df_to_double(acc.x), df_to_double(acc.y));
+    }
+}
+
+__global__ void k_l2t_df(BoxView bx, QuadView qv, const int32_t* __restrict__ tstart,
+                         const int32_t* __restrict__ tcount, const double* __restrict__ tx,
+                         const double* __restrict__ ty, const double* __restrict__ tz,
+                         const cxd* __restrict__ L, int R_, double kappa_turns, const cdf* __restrict__ cis_tab,
+                         cxd* __restrict__ phis) {
+    __shared__ df shs[kL2TThreads * 3];
+    __shared__ cdf shl[kL2TThreads];
+    __shared__ cdf tab[kCisTable];
+    load_cis_table(tab, cis_tab);
+    const int b = blockIdx.x;
+    const int t0 = tstart[b], tc = tcount[b];
+    if (tc == 0) return;
+    const double cxx = bx.center[3 * b], cyy = bx.center[3 * b + 1], czz = bx.center[3 * b + 2];
+    for (int r = 0; r < R_; ++r) {
+        const cxd* Lb = L + ((int64_t)b * R_ + r) * qv.K;
+        for (int tb = 0; tb < tc; tb += kL2TThreads) {
+            const int ti = tb + threadIdx.x;
+            const bool active = ti < tc;
+            df d[3] = {{0, 0}, {0, 0}, {0, 0}};
+            if (active) {
+                d[0] = df_from_double(cxx - tx[t0 + ti]);
+                d[1] = df_from_double(cyy - ty[t0 + ti]);
+                d[2] = df_from_double(czz - tz[t0 + ti]);
+            }
+            cdf acc = {{0, 0}, {0, 0}};
+            for (int64_t kb = 0; kb < qv.K; kb += kL2TThreads) {
+                const int kn = (int)min((int64_t)kL2TThreads, qv.K - kb);
+                __syncthreads();
+                if (threadIdx.x < kn) {
+                    const int64_t k = kb + threadIdx.x;
+                    for (int c = 0; c < 3; ++c) shs[3 * threadIdx.x + c] = df_from_double(qv.shat[3 * k + c] * kappa_turns);
+                    const cxd wl = qv.w[k] * Lb[k];
+                    shl[threadIdx.x] = cdf{df_from_double(wl.x), df_from_double(wl.y)};
+                }
+                __syncthreads();
+                if (active)
+                    for (int kk = 0; kk < kn; ++kk) {
+                        df t = df_mul(shs[3 * kk], d[0]);
+                        t = df_add(t, df_mul(shs[3 * kk + 1], d[1]));
+                        t = df_add(t, df_mul(shs[3 * kk + 2], d[2]));
+                        acc = cdf_add(acc, cdf_mul(cis_turns(df_reduce(t), tab), shl[kk]));
+                    }
+            }
+            if (active) {
+                cxd& o = phis[(int64_t)(t0 + ti) * R_ + r];
+                o.x += df_to_double(acc.x);
+                o.y += df_to_double(acc.y);
             }
         }
     }
