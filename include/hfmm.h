@@ -126,6 +126,20 @@ hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, 
 hfmm_status hfmm_apply(hfmm_plan_t plan, const void* q, void* phi, int nrhs, hfmm_dtype dtype,
                        void* stream);
 
+/* Adjoint apply: out = A^H w = conj(A^T conj(w)), A the FMM operator of hfmm_apply, by the
+ * transposed FMM (each stage of Section 2 transposed: near field with the roles of sources
+ * and targets exchanged, transposed L2T, transposed L2L (interpolation in place of
+ * anterpolation, Section 3.4 steps reversed), M2L with the opposite transfer vector,
+ * transposed M2M, transposed S2M).  It is the exact transpose of the apply's arithmetic,
+ * so <A x, y> = <x, A^H y> to round-off.
+ * w: device (nt, nrhs) complex of dtype; out: device (ns, nrhs) complex of dtype,
+ * overwritten.  Same rules as hfmm_apply (shares its workspace; do not overlap them).
+ * Stage times (hfmm_query) are stored in the same slots: near field, transposed L2T,
+ * transposed L2L, transposed M2L, transposed M2M, transposed S2M.
+ * Errors: HFMM_ERR_ARG, HFMM_ERR_STATE, HFMM_ERR_CUDA. */
+hfmm_status hfmm_apply_adjoint(hfmm_plan_t plan, const void* w, void* out, int nrhs, hfmm_dtype dtype,
+                               void* stream);
+
 /* Plan summary and the per-stage times of the last timed apply.  Errors: HFMM_ERR_ARG. */
 hfmm_status hfmm_query(hfmm_plan_t plan, hfmm_info* info);
 

@@ -351,3 +351,39 @@ def rounding_estimate(ell, kappa, r0, K, u):
     n = np.arange(ell + 1)
     s = np.sum((2 * n + 1) * np.abs(sph_h1(n, kappa * r0)) ** 2)
     return u * kappa * r0 * math.sqrt(s) / math.sqrt(K)
+
+
+def requadrature_transpose(flat, qa, qb):
+    """Transpose of requadrature(., qa, qb): data on quadrature qb -> quadrature qa.
+
+    Each step of Section 3.4 transposed in reverse order.  A one-dimensional re-sampling
+    from K to K' points transposes to (K'/K) times the re-sampling from K' to K (the
+    band is symmetric in K and K'); step 4's duplication of the pole rows transposes to a
+    sum of the two halves, step 2's selection to a scatter with zeros.
+    """
+    flat = np.asarray(flat, dtype=np.complex128)
+    lead = flat.shape[:-1]
+    big = int(max(qa.nphi.max(), qb.nphi.max()))
+    half_a, half_b = qa.ntheta // 2, qb.ntheta // 2
+    # step 5^T: rows of qb, N'_phi(n) -> big, scaled by N'_phi(n) / big
+    h = np.zeros(lead + (half_b + 1, big), dtype=np.complex128)
+    for n, row in enumerate(qb.rows(flat)):
+        h[..., n, :] = resample(row, big) * (row.shape[-1] / big)
+    # step 4^T: columns of length ntheta_b, pole rows collect both halves
+    cols = np.zeros(lead + (big // 2, qb.ntheta), dtype=np.complex128)
+    for t in range(qb.ntheta):
+        if t <= half_b:
+            cols[..., :, t] += h[..., t, :big // 2]
+        if t == 0 or t >= half_b:
+            cols[..., :, t] += h[..., (qb.ntheta - t) % qb.ntheta, big // 2:]
+    # step 3^T: theta re-sampling ntheta_b -> ntheta_a, scaled by ntheta_b / ntheta_a
+    cols = resample(cols, qa.ntheta) * (qb.ntheta / qa.ntheta)
+    # step 2^T: back to the half grid of qa, zeros in the second half of the pole rows
+    g = np.zeros(lead + (half_a + 1, big), dtype=np.complex128)
+    for t in range(half_a + 1):
+        g[..., t, :big // 2] = cols[..., :, t]
+        if 0 < t < half_a:
+            g[..., t, big // 2:] = cols[..., :, qa.ntheta - t]
+    # step 1^T: big -> N_phi(theta_n), scaled by big / N_phi(theta_n)
+    out = [resample(g[..., n, :], int(qa.nphi[n])) * (big / qa.nphi[n]) for n in range(half_a + 1)]
+    return np.concatenate(out, axis=-1)

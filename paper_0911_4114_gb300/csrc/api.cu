@@ -7,6 +7,7 @@
 #include <cstring>
 #include <map>
 #include <type_traits>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -47,6 +48,7 @@ struct DevLevel {
     int32_t* octant = nullptr;
     int32_t *ioff = nullptr, *iidx = nullptr, *iv = nullptr;
     int32_t* tslot = nullptr;
+    int32_t* tslot_t = nullptr;  // slot of the opposite vector (342 - v): transposed M2L
     void* table = nullptr;      // compact T^{s,LL} tables in the level precision
     cxd* shift64 = nullptr;     // [8][K] exp(i k s.d_o), d_o = child-centre offsets of level l+1
     cxf* shift32 = nullptr;
@@ -174,6 +176,9 @@ hfmm_status upload_level(hfmm_plan_s* P, int l) {
     int ns = 0;
     for (int v = 0; v < kNumTransfer; ++v) slot[v] = lp.table[v].empty() ? 0 : ns++;
     TRY(upload(P, &d.tslot, slot));
+    std::vector<int32_t> slot_t(kNumTransfer, 0);
+    for (int v = 0; v < kNumTransfer; ++v) slot_t[v] = slot[kNumTransfer - 1 - v];
+    TRY(upload(P, &d.tslot_t, slot_t));
     if (d.prec == kFP64) {
         std::vector<cxd> t((size_t)ns * q.K);
         for (int v = 0; v < kNumTransfer; ++v)
@@ -388,18 +393,41 @@ void launch_up(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
     const size_t sm = (size_t)kWarps * 2 * rq.args.maxlen * sizeof(cx<Tc>);
     cx<Tc>* GA = (cx<Tc>*)P->ga;
     cx<Tc>* GB = (cx<Tc>*)P->gb;
-    smem_opt_in(k_requad_rows_a<Tin, Tc, false>, sm);
-    smem_opt_in(k_requad_cols<Tc>, sm);
-    smem_opt_in(k_requad_rows_c_m2m<Tc, Tc>, sm);
+    smem_opt_in(k_requad_rows_a<Tin, Tc, kNoShift, false>, sm);
+    smem_opt_in(k_requad_cols<Tc, false>, sm);
+    smem_opt_in(k_requad_rows_c_m2m<Tc, Tc, kShiftPlain, false>, sm);
     int64_t nA = (int64_t)c.nbox * R * rq.args.qa.nrows;
-    k_requad_rows_a<Tin, Tc, false><<<nblk(nA, kWarps), 32 * kWarps, sm, st>>>(
+    k_requad_rows_a<Tin, Tc, kNoShift, false><<<nblk(nA, kWarps), 32 * kWarps, sm, st>>>(
         rq.args, c.nbox, R, (const cx<Tin>*)c.M, nullptr, nullptr, nullptr, GA);
     int64_t nB = (int64_t)c.nbox * R * (rq.args.big / 2);
-    k_requad_cols<Tc><<<nblk(nB, kWarps), 32 * kWarps, sm, st>>>(rq.args, c.nbox, R, GA, GB);
+    k_requad_cols<Tc, false><<<nblk(nB, kWarps), 32 * kWarps, sm, st>>>(rq.args, c.nbox, R, GA, GB);
     int64_t nC = (int64_t)p.nbox * R * rq.args.qb.nrows;
     const cx<Tc>* shift = (const cx<Tc>*)(std::is_same<Tc, double>::value ? (void*)p.shift64 : (void*)p.shift32);
-    k_requad_rows_c_m2m<Tc, Tc><<<nblk(nC, kWarps), 32 * kWarps, sm, st>>>(
+    k_requad_rows_c_m2m<Tc, Tc, kShiftPlain, false><<<nblk(nC, kWarps), 32 * kWarps, sm, st>>>(
         rq.args, p.nbox, R, p.bv.child_start, p.bv.child_count, c.octant, shift, GB, (cx<Tc>*)p.M);
+}
+
+// transposed L2L: level l+1 (Lambda_L of the children) -> level l (Lambda_L of the parents)
+template <typename Tin, typename Tc>
+void launch_l2l_t(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
+    Requad& rq = P->up[l + 1];
+    DevLevel& c = P->lev[l + 1];
+    DevLevel& p = P->lev[l];
+    const size_t sm = (size_t)kWarps * 2 * rq.args.maxlen * sizeof(cx<Tc>);
+    cx<Tc>* GA = (cx<Tc>*)P->ga;
+    cx<Tc>* GB = (cx<Tc>*)P->gb;
+    smem_opt_in(k_requad_rows_a<Tin, Tc, kNoShift, true>, sm);
+    smem_opt_in(k_requad_cols<Tc, true>, sm);
+    smem_opt_in(k_requad_rows_c_m2m<Tc, Tc, kShiftConj, true>, sm);
+    int64_t nA = (int64_t)c.nbox * R * rq.args.qa.nrows;
+    k_requad_rows_a<Tin, Tc, kNoShift, true><<<nblk(nA, kWarps), 32 * kWarps, sm, st>>>(
+        rq.args, c.nbox, R, (const cx<Tin>*)c.IL, nullptr, nullptr, nullptr, GA);
+    int64_t nB = (int64_t)c.nbox * R * (rq.args.big / 2);
+    k_requad_cols<Tc, true><<<nblk(nB, kWarps), 32 * kWarps, sm, st>>>(rq.args, c.nbox, R, GA, GB);
+    int64_t nC = (int64_t)p.nbox * R * rq.args.qb.nrows;
+    const cx<Tc>* shift = (const cx<Tc>*)(std::is_same<Tc, double>::value ? (void*)p.shift64 : (void*)p.shift32);
+    k_requad_rows_c_m2m<Tc, Tc, kShiftConj, true><<<nblk(nC, kWarps), 32 * kWarps, sm, st>>>(
+        rq.args, p.nbox, R, p.bv.child_start, p.bv.child_count, c.octant, shift, GB, (cx<Tc>*)p.IL);
 }
 
 template <typename Tin, typename Tc>
@@ -411,58 +439,104 @@ void launch_down(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
     cx<Tc>* GA = (cx<Tc>*)P->ga;
     cx<Tc>* GB = (cx<Tc>*)P->gb;
     const cx<Tc>* shift = (const cx<Tc>*)(std::is_same<Tc, double>::value ? (void*)p.shift64 : (void*)p.shift32);
-    smem_opt_in(k_requad_rows_a<Tin, Tc, true>, sm);
-    smem_opt_in(k_requad_cols<Tc>, sm);
-    smem_opt_in(k_requad_rows_c_l2l<Tc>, sm);
+    smem_opt_in(k_requad_rows_a<Tin, Tc, kShiftConj, false>, sm);
+    smem_opt_in(k_requad_cols<Tc, false>, sm);
+    smem_opt_in(k_requad_rows_c_l2l<Tc, false>, sm);
     int64_t nA = (int64_t)c.nbox * R * rq.args.qa.nrows;
-    k_requad_rows_a<Tin, Tc, true><<<nblk(nA, kWarps), 32 * kWarps, sm, st>>>(
+    k_requad_rows_a<Tin, Tc, kShiftConj, false><<<nblk(nA, kWarps), 32 * kWarps, sm, st>>>(
         rq.args, c.nbox, R, (const cx<Tin>*)p.IL, c.bv.parent, c.octant, shift, GA);
     int64_t nB = (int64_t)c.nbox * R * (rq.args.big / 2);
-    k_requad_cols<Tc><<<nblk(nB, kWarps), 32 * kWarps, sm, st>>>(rq.args, c.nbox, R, GA, GB);
+    k_requad_cols<Tc, false><<<nblk(nB, kWarps), 32 * kWarps, sm, st>>>(rq.args, c.nbox, R, GA, GB);
     int64_t nC = (int64_t)c.nbox * R * rq.args.qb.nrows;
-    k_requad_rows_c_l2l<Tc><<<nblk(nC, kWarps), 32 * kWarps, sm, st>>>(rq.args, c.nbox, R, GB, (cx<Tc>*)c.IL);
+    k_requad_rows_c_l2l<Tc, false><<<nblk(nC, kWarps), 32 * kWarps, sm, st>>>(rq.args, c.nbox, R, GB, (cx<Tc>*)c.IL);
+}
+
+// transposed M2M: level l-1 (Lambda_M of the parents) -> level l (Lambda_M of the children, added)
+template <typename Tin, typename Tc>
+void launch_m2m_t(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
+    Requad& rq = P->down[l - 1];
+    DevLevel& p = P->lev[l - 1];
+    DevLevel& c = P->lev[l];
+    const size_t sm = (size_t)kWarps * 2 * rq.args.maxlen * sizeof(cx<Tc>);
+    cx<Tc>* GA = (cx<Tc>*)P->ga;
+    cx<Tc>* GB = (cx<Tc>*)P->gb;
+    const cx<Tc>* shift = (const cx<Tc>*)(std::is_same<Tc, double>::value ? (void*)p.shift64 : (void*)p.shift32);
+    smem_opt_in(k_requad_rows_a<Tin, Tc, kShiftPlain, true>, sm);
+    smem_opt_in(k_requad_cols<Tc, true>, sm);
+    smem_opt_in(k_requad_rows_c_l2l<Tc, true>, sm);
+    int64_t nA = (int64_t)c.nbox * R * rq.args.qa.nrows;
+    k_requad_rows_a<Tin, Tc, kShiftPlain, true><<<nblk(nA, kWarps), 32 * kWarps, sm, st>>>(
+        rq.args, c.nbox, R, (const cx<Tin>*)p.M, c.bv.parent, c.octant, shift, GA);
+    int64_t nB = (int64_t)c.nbox * R * (rq.args.big / 2);
+    k_requad_cols<Tc, true><<<nblk(nB, kWarps), 32 * kWarps, sm, st>>>(rq.args, c.nbox, R, GA, GB);
+    int64_t nC = (int64_t)c.nbox * R * rq.args.qb.nrows;
+    k_requad_rows_c_l2l<Tc, true><<<nblk(nC, kWarps), 32 * kWarps, sm, st>>>(rq.args, c.nbox, R, GB, (cx<Tc>*)c.M);
 }
 
 template <typename T>
-void launch_m2l(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
+void launch_m2l(hfmm_plan_s* P, int l, int R, cudaStream_t st, bool transposed = false) {
     DevLevel& d = P->lev[l];
     dim3 grid(d.nbox, nblk(d.K, 256));
-    k_m2l<T><<<grid, 256, 0, st>>>(d.nbox, d.K, d.ioff, d.iidx, d.iv, d.tslot, (const cx<T>*)d.table,
-                                   (const cx<T>*)d.M, R, (cx<T>*)d.IL);
+    if (!transposed)
+        k_m2l<T><<<grid, 256, 0, st>>>(d.nbox, d.K, d.ioff, d.iidx, d.iv, d.tslot, (const cx<T>*)d.table,
+                                       (const cx<T>*)d.M, R, (cx<T>*)d.IL);
+    else
+        k_m2l<T><<<grid, 256, 0, st>>>(d.nbox, d.K, d.ioff, d.iidx, d.iv, d.tslot_t, (const cx<T>*)d.table,
+                                       (const cx<T>*)d.IL, R, (cx<T>*)d.M);
 }
 
 // float64 levels of the mixed policy evaluate their plane waves in double-float
 bool use_df(hfmm_plan_s* P, int l) { return P->hp.precision == HFMM_PREC_MIXED && P->lev[l].prec == kFP64; }
 
+// points -> signature at the leaf level: S2M (sources, sign +1) or transposed L2T
+// (targets, sign -1, weighted)
 template <typename T>
-void launch_s2m(hfmm_plan_s* P, int R, cudaStream_t st) {
+void launch_s2m(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false) {
     const int lf = P->hp.lf;
     DevLevel& d = P->lev[lf];
+    const int32_t* start = transposed ? P->tstart : P->sstart;
+    const int32_t* count = transposed ? P->tcount : P->scount;
+    const double* px = transposed ? P->tx : P->sx;
+    const double* py = transposed ? P->ty : P->sy;
+    const double* pz = transposed ? P->tz : P->sz;
+    const cxd* charges = transposed ? P->phis : P->qs;
+    void* out = transposed ? d.IL : d.M;
+    const double sign = transposed ? -1.0 : 1.0;
+    const double* wk = transposed ? d.qv.w : nullptr;
+    const double kt = P->hp.kappa / (2.0 * 3.14159265358979323846);
+    dim3 grid(d.nbox, nblk(d.K, kS2MThreads));
     if (std::is_same<T, double>::value && use_df(P, lf)) {
-        dim3 grid(d.nbox, nblk(d.K, kS2MThreads));
-        k_s2m_df<<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, P->sstart, P->scount, P->sx, P->sy, P->sz, P->qs, R,
-                                               P->hp.kappa / (2.0 * 3.14159265358979323846), P->cis_tab,
-                                               (cxd*)d.M);
+        k_s2m_df<<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt, P->cis_tab,
+                                               (cxd*)out, sign, wk);
         return;
     }
-    dim3 grid(d.nbox, nblk(d.K, kS2MThreads));
-    k_s2m<T><<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, P->sstart, P->scount, P->sx, P->sy, P->sz, P->qs, R,
-                                           P->hp.kappa / (2.0 * 3.14159265358979323846), (cx<T>*)d.M);
+    k_s2m<T><<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt, (cx<T>*)out,
+                                           sign, wk);
 }
 
+// signature -> points at the leaf level: L2T (targets, sign +1, weighted) or transposed
+// S2M (sources, sign -1)
 template <typename T>
-void launch_l2t(hfmm_plan_s* P, int R, cudaStream_t st) {
+void launch_l2t(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false) {
     const int lf = P->hp.lf;
     DevLevel& d = P->lev[lf];
+    const int32_t* start = transposed ? P->sstart : P->tstart;
+    const int32_t* count = transposed ? P->scount : P->tcount;
+    const double* px = transposed ? P->sx : P->tx;
+    const double* py = transposed ? P->sy : P->ty;
+    const double* pz = transposed ? P->sz : P->tz;
+    const void* in = transposed ? d.M : d.IL;
+    cxd* out = transposed ? P->qs : P->phis;
+    const double sign = transposed ? -1.0 : 1.0;
+    const double* wk = transposed ? nullptr : d.qv.w;
+    const double kt = P->hp.kappa / (2.0 * 3.14159265358979323846);
     if (std::is_same<T, double>::value && use_df(P, lf)) {
-        k_l2t_df<<<d.nbox, kL2TThreads, 0, st>>>(d.bv, d.qv, P->tstart, P->tcount, P->tx, P->ty, P->tz,
-                                                 (const cxd*)d.IL, R,
-                                                 P->hp.kappa / (2.0 * 3.14159265358979323846), P->cis_tab, P->phis);
+        k_l2t_df<<<d.nbox, kL2TThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, (const cxd*)in, R, kt,
+                                                 P->cis_tab, out, sign, wk);
         return;
     }
-    k_l2t<T><<<d.nbox, kL2TThreads, 0, st>>>(d.bv, d.qv, P->tstart, P->tcount, P->tx, P->ty, P->tz,
-                                             (const cx<T>*)d.IL, R,
-                                             P->hp.kappa / (2.0 * 3.14159265358979323846), P->phis);
+    k_l2t<T><<<d.nbox, kL2TThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, (const cx<T>*)in, R, kt, out,
+                                             sign, wk);
 }
 
 hfmm_status check_launch(const char* what) {
@@ -622,9 +696,9 @@ hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_d
     };
     mark(0);
     if (dtype == HFMM_C64)
-        k_permute_in<float><<<nblk(hp.ns * R, 256), 256, 0, st>>>((const cxf*)q, hp.ns, R, P->src_perm, P->qs);
+        k_permute_in<float, false><<<nblk(hp.ns * R, 256), 256, 0, st>>>((const cxf*)q, hp.ns, R, P->src_perm, P->qs);
     else
-        k_permute_in<double><<<nblk(hp.ns * R, 256), 256, 0, st>>>((const cxd*)q, hp.ns, R, P->src_perm, P->qs);
+        k_permute_in<double, false><<<nblk(hp.ns * R, 256), 256, 0, st>>>((const cxd*)q, hp.ns, R, P->src_perm, P->qs);
     mark(1);
     const int nleaf = (int)hp.levels[lf].nbox();
     if (hp.precision == HFMM_PREC_MIXED)
@@ -665,12 +739,91 @@ hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_d
         for (int i = 3; i <= 7; ++i) mark(i);
     }
     if (dtype == HFMM_C64)
-        k_permute_out<float><<<nblk(hp.nt * R, 256), 256, 0, st>>>(P->phis, hp.nt, R, P->tgt_perm, (cxf*)phi);
+        k_permute_out<float, false><<<nblk(hp.nt * R, 256), 256, 0, st>>>(P->phis, hp.nt, R, P->tgt_perm, (cxf*)phi);
     else
-        k_permute_out<double><<<nblk(hp.nt * R, 256), 256, 0, st>>>(P->phis, hp.nt, R, P->tgt_perm, (cxd*)phi);
+        k_permute_out<double, false><<<nblk(hp.nt * R, 256), 256, 0, st>>>(P->phis, hp.nt, R, P->tgt_perm, (cxd*)phi);
     mark(8);
     P->ev_recorded = P->timing;
     return check_launch("hfmm_apply");
+}
+
+hfmm_status hfmm_apply_adjoint(hfmm_plan_t P, const void* w, void* out, int nrhs, hfmm_dtype dtype,
+                               void* stream) {
+    if (!P) return fail(HFMM_ERR_ARG, "plan is NULL");
+    if (P->device < 0) return fail(HFMM_ERR_STATE, "host-only plan has no device data");
+    if (!w || !out) return fail(HFMM_ERR_ARG, "w and out must be device pointers");
+    if (nrhs < 1 || nrhs > P->rmax) return fail(HFMM_ERR_ARG, "nrhs must be in [1, max_rhs]");
+    if (dtype != HFMM_C64 && dtype != HFMM_C128) return fail(HFMM_ERR_ARG, "unknown dtype");
+    CK(cudaSetDevice(P->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    HostPlan& hp = P->hp;
+    const int R = nrhs;
+    const int lf = hp.lf;
+    auto mark = [&](int i) {
+        if (P->timing) cudaEventRecord(P->ev[i], st);
+    };
+    mark(0);
+    // conj(w) on the targets, sorted, into the target-side buffer
+    if (dtype == HFMM_C64)
+        k_permute_in<float, true><<<nblk(hp.nt * R, 256), 256, 0, st>>>((const cxf*)w, hp.nt, R, P->tgt_perm, P->phis);
+    else
+        k_permute_in<double, true><<<nblk(hp.nt * R, 256), 256, 0, st>>>((const cxd*)w, hp.nt, R, P->tgt_perm, P->phis);
+    mark(1);
+    // transposed near field: source boxes gather the targets of their neighbours
+    const int nleaf = (int)hp.levels[lf].nbox();
+    if (hp.precision == HFMM_PREC_MIXED) {
+        P2PMixedArgs a = P->mixed;
+        std::swap(a.tpt, a.spt);
+        std::swap(a.tof, a.sof);
+        k_p2p_mixed<<<nleaf, kP2PThreads, 0, st>>>(nleaf, P->sstart, P->scount, P->tstart, P->tcount, P->noff,
+                                                   P->nidx, a, P->phis, P->qs, R);
+    } else {
+        k_p2p_fp64<<<nleaf, kP2PThreads, 0, st>>>(nleaf, P->sstart, P->scount, P->tstart, P->tcount, P->noff,
+                                                  P->nidx, P->sx, P->sy, P->sz, P->tx, P->ty, P->tz, P->phis,
+                                                  P->qs, R, hp.kappa);
+    }
+    mark(2);
+    if (lf >= 2) {
+        // transposed L2T: weighted plane-wave sums of the targets into Lambda_L at the leaf level
+        if (P->lev[lf].prec == kFP64) launch_s2m<double>(P, R, st, true);
+        else launch_s2m<float>(P, R, st, true);
+        mark(3);
+        // transposed L2L, leaf level up to level 2
+        for (int l = lf - 1; l >= 2; --l) {
+            const int pi = P->lev[l + 1].prec, po = P->lev[l].prec;
+            if (pi == kFP64 && po == kFP64) launch_l2l_t<double, double>(P, l, R, st);
+            else if (pi == kFP64) launch_l2l_t<double, float>(P, l, R, st);
+            else launch_l2l_t<float, float>(P, l, R, st);
+        }
+        mark(4);
+        // transposed M2L: the opposite transfer vectors
+        for (int l = 2; l <= lf; ++l) {
+            if (P->lev[l].prec == kFP64) launch_m2l<double>(P, l, R, st, true);
+            else launch_m2l<float>(P, l, R, st, true);
+        }
+        mark(5);
+        // transposed M2M, level 2 down to the leaf level, added to the M2L part
+        for (int l = 3; l <= lf; ++l) {
+            const int pi = P->lev[l - 1].prec, po = P->lev[l].prec;
+            if (pi == kFP64 && po == kFP64) launch_m2m_t<double, double>(P, l, R, st);
+            else if (po == kFP64) launch_m2m_t<float, double>(P, l, R, st);
+            else launch_m2m_t<float, float>(P, l, R, st);
+        }
+        mark(6);
+        // transposed S2M: plane-wave sums back onto the sources
+        if (P->lev[lf].prec == kFP64) launch_l2t<double>(P, R, st, true);
+        else launch_l2t<float>(P, R, st, true);
+        mark(7);
+    } else {
+        for (int i = 3; i <= 7; ++i) mark(i);
+    }
+    if (dtype == HFMM_C64)
+        k_permute_out<float, true><<<nblk(hp.ns * R, 256), 256, 0, st>>>(P->qs, hp.ns, R, P->src_perm, (cxf*)out);
+    else
+        k_permute_out<double, true><<<nblk(hp.ns * R, 256), 256, 0, st>>>(P->qs, hp.ns, R, P->src_perm, (cxd*)out);
+    mark(8);
+    P->ev_recorded = P->timing;
+    return check_launch("hfmm_apply_adjoint");
 }
 
 hfmm_status hfmm_query(hfmm_plan_t P, hfmm_info* info) {

@@ -32,24 +32,26 @@ struct BoxView {
 // ---------------------------------------------------------------------------
 // permutations
 // ---------------------------------------------------------------------------
-template <typename Tin>
+template <typename Tin, bool kConj>
 __global__ void k_permute_in(const cx<Tin>* __restrict__ q, int64_t n, int R,
                              const int64_t* __restrict__ perm, cxd* __restrict__ qs) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n * R) return;
     int64_t p = t / R;
     int r = (int)(t - p * R);
-    qs[t] = cvt<double>(q[perm[p] * R + r]);
+    cxd v = cvt<double>(q[perm[p] * R + r]);
+    qs[t] = kConj ? conj(v) : v;
 }
 
-template <typename Tout>
+template <typename Tout, bool kConj>
 __global__ void k_permute_out(const cxd* __restrict__ phis, int64_t n, int R,
                               const int64_t* __restrict__ perm, cx<Tout>* __restrict__ phi) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n * R) return;
     int64_t p = t / R;
     int r = (int)(t - p * R);
-    phi[perm[p] * R + r] = cvt<Tout>(phis[t]);
+    cxd v = kConj ? conj(phis[t]) : phis[t];
+    phi[perm[p] * R + r] = cvt<Tout>(v);
 }
 
 // ---------------------------------------------------------------------------
@@ -240,11 +242,14 @@ __device__ __forceinline__ double turns(double kappa_turns, const double* s, dou
     return p - rint(p);
 }
 
+// Points to signature: M_b(s_k) = w_k sum_{j in b} exp(i k s_k . sign (p_j - c_b)) q_j.
+// S2M: sources, sign +1, no weights.  Transposed L2T: targets, sign -1, quadrature weights.
 template <typename R>
 __global__ void k_s2m(BoxView bx, QuadView qv, const int32_t* __restrict__ sstart,
                       const int32_t* __restrict__ scount, const double* __restrict__ sx,
                       const double* __restrict__ sy, const double* __restrict__ sz,
-                      const cxd* __restrict__ qs, int R_, double kappa_turns, cx<R>* __restrict__ M) {
+                      const cxd* __restrict__ qs, int R_, double kappa_turns, cx<R>* __restrict__ M,
+                      double sign, const double* __restrict__ wk) {
     __shared__ double shd[kS2MThreads * 3];
     __shared__ cxd shq[kS2MThreads];
     const int b = blockIdx.x;
@@ -265,9 +270,9 @@ __global__ void k_s2m(BoxView bx, QuadView qv, const int32_t* __restrict__ sstar
             __syncthreads();
             if (threadIdx.x < jn) {
                 const int j = s0 + jb + threadIdx.x;
-                shd[3 * threadIdx.x] = sx[j] - cxx;
-                shd[3 * threadIdx.x + 1] = sy[j] - cyy;
-                shd[3 * threadIdx.x + 2] = sz[j] - czz;
+                shd[3 * threadIdx.x] = sign * (sx[j] - cxx);
+                shd[3 * threadIdx.x + 1] = sign * (sy[j] - cyy);
+                shd[3 * threadIdx.x + 2] = sign * (sz[j] - czz);
                 shq[threadIdx.x] = qs[(int64_t)j * R_ + r];
             }
             __syncthreads();
@@ -277,7 +282,10 @@ __global__ void k_s2m(BoxView bx, QuadView qv, const int32_t* __restrict__ sstar
                     mac(acc, plane_wave<R>(t), cvt<R>(shq[jj]));
                 }
         }
-        if (active) M[((int64_t)b * R_ + r) * qv.K + k] = acc;
+        if (active) {
+            if (wk) acc = (R)wk[k] * acc;
+            M[((int64_t)b * R_ + r) * qv.K + k] = acc;
+        }
     }
 }
 
@@ -286,11 +294,14 @@ __global__ void k_s2m(BoxView bx, QuadView qv, const int32_t* __restrict__ sstar
 // ---------------------------------------------------------------------------
 constexpr int kL2TThreads = 128;
 
+// Signature to points: phi_i += sum_k w_k L_b(s_k) exp(i k s_k . sign (c_b - p_i)).
+// L2T: targets, sign +1, quadrature weights.  Transposed S2M: sources, sign -1, no weights.
 template <typename R>
 __global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstart,
                       const int32_t* __restrict__ tcount, const double* __restrict__ tx,
                       const double* __restrict__ ty, const double* __restrict__ tz,
-                      const cx<R>* __restrict__ L, int R_, double kappa_turns, cxd* __restrict__ phis) {
+                      const cx<R>* __restrict__ L, int R_, double kappa_turns, cxd* __restrict__ phis,
+                      double sign, const double* __restrict__ wk) {
     __shared__ double shs[kL2TThreads * 3];
     __shared__ cx<R> shl[kL2TThreads];
     const int b = blockIdx.x;
@@ -304,9 +315,9 @@ __global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstar
             const bool active = ti < tc;
             double dx = 0, dy = 0, dz = 0;
             if (active) {
-                dx = cxx - tx[t0 + ti];
-                dy = cyy - ty[t0 + ti];
-                dz = czz - tz[t0 + ti];
+                dx = sign * (cxx - tx[t0 + ti]);
+                dy = sign * (cyy - ty[t0 + ti]);
+                dz = sign * (czz - tz[t0 + ti]);
             }
             cx<R> acc = mk<R>(0, 0);
             for (int64_t kb = 0; kb < qv.K; kb += kL2TThreads) {
@@ -317,7 +328,7 @@ __global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstar
                     shs[3 * threadIdx.x] = qv.shat[3 * k];
                     shs[3 * threadIdx.x + 1] = qv.shat[3 * k + 1];
                     shs[3 * threadIdx.x + 2] = qv.shat[3 * k + 2];
-                    shl[threadIdx.x] = (R)qv.w[k] * Lb[k];
+                    shl[threadIdx.x] = wk ? (R)wk[k] * Lb[k] : Lb[k];
                 }
                 __syncthreads();
                 if (active)
@@ -354,7 +365,7 @@ __global__ void k_s2m_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ss
                          const int32_t* __restrict__ scount, const double* __restrict__ sx,
                          const double* __restrict__ sy, const double* __restrict__ sz,
                          const cxd* __restrict__ qs, int R_, double kappa_turns, const cdf* __restrict__ cis_tab,
-                         cxd* __restrict__ M) {
+                         cxd* __restrict__ M, double sign, const double* __restrict__ wk) {
     __shared__ df shd[kS2MThreads * 3];
     __shared__ cdf shq[kS2MThreads];
     __shared__ cdf tab[kCisTable];
@@ -374,9 +385,9 @@ __global__ void k_s2m_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ss
             __syncthreads();
             if (threadIdx.x < jn) {
                 const int j = s0 + jb + threadIdx.x;
-                shd[3 * threadIdx.x] = df_from_double(sx[j] - cxx);
-                shd[3 * threadIdx.x + 1] = df_from_double(sy[j] - cyy);
-                shd[3 * threadIdx.x + 2] = df_from_double(sz[j] - czz);
+                shd[3 * threadIdx.x] = df_from_double(sign * (sx[j] - cxx));
+                shd[3 * threadIdx.x + 1] = df_from_double(sign * (sy[j] - cyy));
+                shd[3 * threadIdx.x + 2] = df_from_double(sign * (sz[j] - czz));
                 const cxd qq = qs[(int64_t)j * R_ + r];
                 shq[threadIdx.x] = cdf{df_from_double(qq.x), df_from_double(qq.y)};
             }
@@ -389,7 +400,11 @@ __global__ void k_s2m_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ss
                     acc = cdf_add(acc, cdf_mul(cis_turns(df_reduce(t), tab), shq[jj]));
                 }
         }
-        if (active) M[((int64_t)b * R_ + r) * qv.K + k] = mk<double>(df_to_double(acc.x), df_to_double(acc.y));
+        if (active) {
+            cxd v = mk<double>(df_to_double(acc.x), df_to_double(acc.y));
+            if (wk) v = wk[k] * v;
+            M[((int64_t)b * R_ + r) * qv.K + k] = v;
+        }
     }
 }
 
@@ -397,7 +412,7 @@ __global__ void k_l2t_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ts
                          const int32_t* __restrict__ tcount, const double* __restrict__ tx,
                          const double* __restrict__ ty, const double* __restrict__ tz,
                          const cxd* __restrict__ L, int R_, double kappa_turns, const cdf* __restrict__ cis_tab,
-                         cxd* __restrict__ phis) {
+                         cxd* __restrict__ phis, double sign, const double* __restrict__ wk) {
     __shared__ df shs[kL2TThreads * 3];
     __shared__ cdf shl[kL2TThreads];
     __shared__ cdf tab[kCisTable];
@@ -413,9 +428,9 @@ __global__ void k_l2t_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ts
             const bool active = ti < tc;
             df d[3] = {{0, 0}, {0, 0}, {0, 0}};
             if (active) {
-                d[0] = df_from_double(cxx - tx[t0 + ti]);
-                d[1] = df_from_double(cyy - ty[t0 + ti]);
-                d[2] = df_from_double(czz - tz[t0 + ti]);
+                d[0] = df_from_double(sign * (cxx - tx[t0 + ti]));
+                d[1] = df_from_double(sign * (cyy - ty[t0 + ti]));
+                d[2] = df_from_double(sign * (czz - tz[t0 + ti]));
             }
             cdf acc = {{0, 0}, {0, 0}};
             for (int64_t kb = 0; kb < qv.K; kb += kL2TThreads) {
@@ -424,7 +439,7 @@ __global__ void k_l2t_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ts
                 if (threadIdx.x < kn) {
                     const int64_t k = kb + threadIdx.x;
                     for (int c = 0; c < 3; ++c) shs[3 * threadIdx.x + c] = df_from_double(qv.shat[3 * k + c] * kappa_turns);
-                    const cxd wl = qv.w[k] * Lb[k];
+                    const cxd wl = wk ? wk[k] * Lb[k] : Lb[k];
                     shl[threadIdx.x] = cdf{df_from_double(wl.x), df_from_double(wl.y)};
                 }
                 __syncthreads();
@@ -483,10 +498,19 @@ struct RequadArgs {
     TwiddleView tw;
 };
 
+// Shift modes of the passes that touch the parent grid.
+enum ShiftMode { kNoShift = 0, kShiftConj = 1, kShiftPlain = 2 };
+
+// Transposition (kT): the transposed re-quadrature runs the same passes from the output
+// grid back to the input grid; a transposed 1-D re-sampling from K to K' points is
+// (K/K') times the plain one, the duplicated pole halves of step 4 are summed, and the
+// dropped pole halves of step 2 are set to zero.
+
 // Pass A.  Sequence = (box, r, n) over nbox_seq boxes.  Input signature of box `src_box(b)`:
-//   M2M: the child itself (src = box b of level a, no shift)
-//   L2L: the parent of child b (level a = parent level), times conj(shift[octant(b)])
-template <typename Tin, typename Tc, bool kShift>
+//   M2M / transposed L2L: box b itself on grid a, no shift
+//   L2L: the parent of child b on grid a, times conj(shift[octant(b)])
+//   transposed M2M: the parent of child b on grid a, times shift[octant(b)]
+template <typename Tin, typename Tc, int kShift, bool kT>
 __global__ void k_requad_rows_a(RequadArgs ra, int nbox_seq, int R_, const cx<Tin>* __restrict__ in,
                                 const int32_t* __restrict__ src_box, const int32_t* __restrict__ octant,
                                 const cx<Tc>* __restrict__ shift, cx<Tc>* __restrict__ GA) {
@@ -509,17 +533,19 @@ __global__ void k_requad_rows_a(RequadArgs ra, int nbox_seq, int R_, const cx<Ti
     const cx<Tc>* sh = kShift ? shift + (int64_t)octant[b] * ra.qa.K + o : nullptr;
     for (int j = lane; j < len; j += 32) {
         cx<Tc> v = cvt<Tc>(src[j]);
-        if (kShift) v = v * conj(sh[j]);
+        if (kShift == kShiftConj) v = v * conj(sh[j]);
+        if (kShift == kShiftPlain) v = v * sh[j];
         buf0[j] = v;
     }
     __syncwarp();
     cx<Tc>* res = warp_resample(buf0, buf1, len, ra.big, ra.tw, lane);
+    const Tc sc = kT ? (Tc)len / (Tc)ra.big : (Tc)1;   // transposed: (length in) / (length out)
     cx<Tc>* dst = GA + seq * ra.big;
-    for (int j = lane; j < ra.big; j += 32) dst[j] = res[j];
+    for (int j = lane; j < ra.big; j += 32) dst[j] = kT ? sc * res[j] : res[j];
 }
 
 // Pass B.  Sequence = (box, r, m), m < big/2.
-template <typename Tc>
+template <typename Tc, bool kT>
 __global__ void k_requad_cols(RequadArgs ra, int nbox_seq, int R_, const cx<Tc>* __restrict__ GA,
                               cx<Tc>* __restrict__ GB) {
     extern __shared__ unsigned char smem_raw[];
@@ -537,19 +563,33 @@ __global__ void k_requad_cols(RequadArgs ra, int nbox_seq, int R_, const cx<Tc>*
     const int ha = nta / 2, hbr = ntb / 2;
     const cx<Tc>* ga = GA + br * (int64_t)ra.qa.nrows * ra.big;
     for (int t = lane; t < nta; t += 32) {
-        buf0[t] = (t <= ha) ? ga[(int64_t)t * ra.big + m] : ga[(int64_t)(nta - t) * ra.big + m + hb];
+        if (!kT) {
+            buf0[t] = (t <= ha) ? ga[(int64_t)t * ra.big + m] : ga[(int64_t)(nta - t) * ra.big + m + hb];
+        } else {
+            cx<Tc> v = mk<Tc>(0, 0);
+            if (t <= ha) v = ga[(int64_t)t * ra.big + m];
+            if (t == 0 || t >= ha) v = v + ga[(int64_t)((nta - t) % nta) * ra.big + m + hb];
+            buf0[t] = v;
+        }
     }
     __syncwarp();
     cx<Tc>* res = warp_resample(buf0, buf1, nta, ntb, ra.tw, lane);
+    const Tc sc = (Tc)nta / (Tc)ntb;
     cx<Tc>* gb = GB + br * (int64_t)ra.qb.nrows * ra.big;
     for (int n = lane; n <= hbr; n += 32) {
-        gb[(int64_t)n * ra.big + m] = res[n];
-        gb[(int64_t)n * ra.big + m + hb] = res[(ntb - n) % ntb];
+        if (!kT) {
+            gb[(int64_t)n * ra.big + m] = res[n];
+            gb[(int64_t)n * ra.big + m + hb] = res[(ntb - n) % ntb];
+        } else {
+            gb[(int64_t)n * ra.big + m] = sc * res[n];
+            gb[(int64_t)n * ra.big + m + hb] = (n > 0 && n < hbr) ? sc * res[ntb - n] : mk<Tc>(0, 0);
+        }
     }
 }
 
-// Pass C for L2L.  Sequence = (child, r, n'); L_child = anterp(...) + I_child, in place.
-template <typename Tc>
+// Pass C, adding into the output in place.  Sequence = (box, r, n').
+//   L2L: L_child = anterp(...) + I_child;  transposed M2M: Lambda_M(child) += ...
+template <typename Tc, bool kT>
 __global__ void k_requad_rows_c_l2l(RequadArgs ra, int nbox_seq, int R_, const cx<Tc>* __restrict__ GB,
                                     cx<Tc>* __restrict__ IL) {
     extern __shared__ unsigned char smem_raw[];
@@ -568,12 +608,15 @@ __global__ void k_requad_rows_c_l2l(RequadArgs ra, int nbox_seq, int R_, const c
     __syncwarp();
     const int len = ra.qb.nphi[n];
     cx<Tc>* res = warp_resample(buf0, buf1, ra.big, len, ra.tw, lane);
+    const Tc sc = kT ? (Tc)ra.big / (Tc)len : (Tc)1;
     cx<Tc>* dst = IL + br * ra.qb.K + ra.qb.off[n];
-    for (int j = lane; j < len; j += 32) dst[j] = dst[j] + res[j];
+    for (int j = lane; j < len; j += 32) dst[j] = dst[j] + (kT ? sc * res[j] : res[j]);
 }
 
-// Pass C for M2M.  Sequence = (parent, r, n'); M_parent = sum_children shift * anterp(child).
-template <typename Tc, typename Tout>
+// Pass C summing children, overwriting the parent.  Sequence = (parent, r, n').
+//   M2M: M_parent = sum_children shift * requad(child)
+//   transposed L2L: Lambda_L(parent) = sum_children conj(shift) * requad^T(child)
+template <typename Tc, typename Tout, int kShift, bool kT>
 __global__ void k_requad_rows_c_m2m(RequadArgs ra, int nparent, int R_, const int32_t* __restrict__ child_start,
                                     const int32_t* __restrict__ child_count, const int32_t* __restrict__ octant,
                                     const cx<Tc>* __restrict__ shift, const cx<Tc>* __restrict__ GB,
@@ -603,7 +646,11 @@ __global__ void k_requad_rows_c_m2m(RequadArgs ra, int nparent, int R_, const in
         __syncwarp();
         cx<Tc>* res = warp_resample(buf0, buf1, ra.big, len, ra.tw, lane);
         const cx<Tc>* sh = shift + (int64_t)octant[c] * ra.qb.K + o;
-        for (int i = 0, j = lane; j < len; ++i, j += 32) acc[i] = acc[i] + res[j] * sh[j];
+        const Tc sc = kT ? (Tc)ra.big / (Tc)len : (Tc)1;
+        for (int i = 0, j = lane; j < len; ++i, j += 32) {
+            cx<Tc> v = kT ? sc * res[j] : res[j];
+            acc[i] = acc[i] + v * (kShift == kShiftConj ? conj(sh[j]) : sh[j]);
+        }
         __syncwarp();
     }
     cx<Tout>* dst = Mp + ((int64_t)p * R_ + r) * ra.qb.K + o;

@@ -82,6 +82,28 @@ class FmmPlan:
         self.apply_ptr(q2.data_ptr(), out.data_ptr(), r, dtype, st.cuda_stream)
         return out[:, 0] if single else out
 
+    def apply_adjoint_ptr(self, w_ptr, out_ptr, nrhs, dtype, stream_ptr=0):
+        nat.check(nat.lib().hfmm_apply_adjoint(self._h, w_ptr, out_ptr, int(nrhs), int(dtype), stream_ptr))
+
+    def apply_adjoint(self, w, out=None, stream=None):
+        """A^H w for a CUDA complex64/complex128 tensor w of shape (nt,) or (nt, R)."""
+        import torch
+        if not w.is_cuda or w.dtype not in (torch.complex64, torch.complex128):
+            raise ValueError("w must be a CUDA complex64/complex128 tensor")
+        single = w.dim() == 1
+        w2 = w.reshape(w.shape[0], -1).contiguous()
+        if w2.shape[0] != self.nt:
+            raise ValueError(f"w has {w2.shape[0]} rows, plan has {self.nt} targets")
+        r = w2.shape[1]
+        if out is None:
+            out = torch.empty((self.ns, r), dtype=w.dtype, device=w.device)
+        elif out.shape != (self.ns, r) or out.dtype != w.dtype or not out.is_contiguous():
+            raise ValueError("out must be a contiguous (ns, R) tensor of w's dtype")
+        st = stream if stream is not None else torch.cuda.current_stream(w.device)
+        dtype = nat.C64 if w.dtype == torch.complex64 else nat.C128
+        self.apply_adjoint_ptr(w2.data_ptr(), out.data_ptr(), r, dtype, st.cuda_stream)
+        return out[:, 0] if single else out
+
     # -- queries -------------------------------------------------------------
     def set_timing(self, on=True):
         nat.check(nat.lib().hfmm_set_timing(self._h, 1 if on else 0))

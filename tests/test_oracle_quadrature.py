@@ -177,3 +177,13 @@ def test_requadrature_exact_on_band_limited_data():
     assert np.max(np.abs(back - da)) < 1e-12 * np.max(np.abs(da))
     # quadrature sums agree
     assert abs(np.sum(qa.w * da) - np.sum(qb.w * db)) < 1e-12 * np.sum(np.abs(qa.w * da))
+
+
+def test_requadrature_transpose_is_the_matrix_transpose():
+    """Section 3.4 re-quadrature: the transposed pipeline equals the explicit matrix transpose."""
+    qa = qd.Quadrature(6, 12, np.array([4, 8, 12, 12, 12, 8, 4]))
+    qb = qd.Quadrature(8, 16, np.array([4, 8, 12, 16, 16, 16, 12, 8, 4]))
+    for x, y in ((qa, qb), (qb, qa)):
+        A = np.stack([qd.requadrature(e, x, y) for e in np.eye(x.K)], axis=1)          # K_y x K_x
+        At = np.stack([qd.requadrature_transpose(e, x, y) for e in np.eye(y.K)], axis=1)  # K_x x K_y
+        assert np.max(np.abs(At - A.T)) < 1e-13
