@@ -140,6 +140,20 @@ hfmm_status hfmm_apply(hfmm_plan_t plan, const void* q, void* phi, int nrhs, hfm
 hfmm_status hfmm_apply_adjoint(hfmm_plan_t plan, const void* w, void* out, int nrhs, hfmm_dtype dtype,
                                void* stream);
 
+/* Position gradient of the apply (vector-Jacobian product for a real loss L, complex
+ * autograd convention g = dL/d conj(phi), e.g. g = 2 (phi - phi*) for L = sum |phi - phi*|^2):
+ *   grad[j, c] = Re sum_r q_jr ( sum_k i kappa s_k,c exp(i kappa s_k.(y_j - c_b)) Lambda_b,r(k)
+ *                               + sum_{i in N(b)} conj(g_ir) dG(x_i, y_j)/dy_j,c )
+ * where Lambda is the transposed far-field chain of hfmm_apply_adjoint applied to conj(g)
+ * (s-weighted transposed S2M: the derivative of S2M's plane waves) and dG/dy =
+ * G (i kappa - 1/R) (y - x)/R is the near-field kernel derivative.  It is the exact
+ * derivative of the FMM approximation with the plan's tree held fixed.
+ * q: device (ns, nrhs); g: device (nt, nrhs), complex of dtype; grad: device (ns, 3)
+ * float64, overwritten.  Same rules as hfmm_apply.  Errors: HFMM_ERR_ARG, HFMM_ERR_STATE,
+ * HFMM_ERR_CUDA. */
+hfmm_status hfmm_grad_sources(hfmm_plan_t plan, const void* q, const void* g, double* grad, int nrhs,
+                              hfmm_dtype dtype, void* stream);
+
 /* Plan summary and the per-stage times of the last timed apply.  Errors: HFMM_ERR_ARG. */
 hfmm_status hfmm_query(hfmm_plan_t plan, hfmm_info* info);
 

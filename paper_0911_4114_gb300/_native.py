@@ -21,7 +21,7 @@ GET = dict(BOX_IDX=0, BOX_PARENT=1, ILIST_OFF=2, ILIST_IDX=3, ILIST_V=4, NLIST_O
            SRC_PERM=7, TGT_PERM=8, NPHI=9, TABLE=10, LEAF_SRC=11, LEAF_TGT=12)
 
 EXPORTS = ("hfmm_default_options", "hfmm_plan", "hfmm_apply", "hfmm_query", "hfmm_set_timing",
-           "hfmm_destroy", "hfmm_last_error", "hfmm_debug_get", "hfmm_direct_noalloc", "hfmm_apply_adjoint")
+           "hfmm_destroy", "hfmm_last_error", "hfmm_debug_get", "hfmm_direct_noalloc", "hfmm_apply_adjoint", "hfmm_grad_sources")
 NOALLOC_MAX_POINTS = 1 << 19
 
 
@@ -64,6 +64,8 @@ def lib():
     L.hfmm_apply.restype = ctypes.c_int
     L.hfmm_apply_adjoint.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
     L.hfmm_apply_adjoint.restype = ctypes.c_int
+    L.hfmm_grad_sources.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
+    L.hfmm_grad_sources.restype = ctypes.c_int
     L.hfmm_query.argtypes = [vp, ctypes.POINTER(Info)]
     L.hfmm_query.restype = ctypes.c_int
     L.hfmm_set_timing.argtypes = [vp, ctypes.c_int]

@@ -75,6 +75,7 @@ struct hfmm_plan_s {
     int32_t *noff = nullptr, *nidx = nullptr;
     P2PMixedArgs mixed{};
     cxd *qs = nullptr, *phis = nullptr;
+    double* gsort = nullptr;    // sorted position gradient (ns, 3)
     DevLevel lev[kMaxLevels];
     Requad up[kMaxLevels];    // up[l]: level l -> l-1
     Requad down[kMaxLevels];  // down[l]: level l -> l+1
@@ -302,6 +303,7 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
     }
     TRY(dalloc(P, &P->qs, (size_t)hp.ns * P->rmax));
     TRY(dalloc(P, &P->phis, (size_t)hp.nt * P->rmax));
+    TRY(dalloc(P, &P->gsort, (size_t)hp.ns * 3));
     // levels
     for (int l = 2; l <= hp.lf; ++l) TRY(upload_level(P, l));
     // re-quadrature passes and scratch
@@ -537,6 +539,39 @@ void launch_l2t(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false)
     }
     k_l2t<T><<<d.nbox, kL2TThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, (const cx<T>*)in, R, kt, out,
                                              sign, wk);
+}
+
+// transposed far field up to (not including) the transposed S2M: conj(w) on the targets
+// (P->phis) -> Lambda_M at the leaf level (M buffers); marks stages 3..6
+template <typename Mark>
+void transposed_far_chain(hfmm_plan_s* P, int R, cudaStream_t st, Mark mark) {
+    const int lf = P->hp.lf;
+    // transposed L2T: weighted plane-wave sums of the targets into Lambda_L at the leaf level
+    if (P->lev[lf].prec == kFP64) launch_s2m<double>(P, R, st, true);
+    else launch_s2m<float>(P, R, st, true);
+    mark(3);
+    // transposed L2L, leaf level up to level 2
+    for (int l = lf - 1; l >= 2; --l) {
+        const int pi = P->lev[l + 1].prec, po = P->lev[l].prec;
+        if (pi == kFP64 && po == kFP64) launch_l2l_t<double, double>(P, l, R, st);
+        else if (pi == kFP64) launch_l2l_t<double, float>(P, l, R, st);
+        else launch_l2l_t<float, float>(P, l, R, st);
+    }
+    mark(4);
+    // transposed M2L: the opposite transfer vectors
+    for (int l = 2; l <= lf; ++l) {
+        if (P->lev[l].prec == kFP64) launch_m2l<double>(P, l, R, st, true);
+        else launch_m2l<float>(P, l, R, st, true);
+    }
+    mark(5);
+    // transposed M2M, level 2 down to the leaf level, added to the M2L part
+    for (int l = 3; l <= lf; ++l) {
+        const int pi = P->lev[l - 1].prec, po = P->lev[l].prec;
+        if (pi == kFP64 && po == kFP64) launch_m2m_t<double, double>(P, l, R, st);
+        else if (po == kFP64) launch_m2m_t<float, double>(P, l, R, st);
+        else launch_m2m_t<float, float>(P, l, R, st);
+    }
+    mark(6);
 }
 
 hfmm_status check_launch(const char* what) {
@@ -784,32 +819,7 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t P, const void* w, void* out, int nrhs
     }
     mark(2);
     if (lf >= 2) {
-        // transposed L2T: weighted plane-wave sums of the targets into Lambda_L at the leaf level
-        if (P->lev[lf].prec == kFP64) launch_s2m<double>(P, R, st, true);
-        else launch_s2m<float>(P, R, st, true);
-        mark(3);
-        // transposed L2L, leaf level up to level 2
-        for (int l = lf - 1; l >= 2; --l) {
-            const int pi = P->lev[l + 1].prec, po = P->lev[l].prec;
-            if (pi == kFP64 && po == kFP64) launch_l2l_t<double, double>(P, l, R, st);
-            else if (pi == kFP64) launch_l2l_t<double, float>(P, l, R, st);
-            else launch_l2l_t<float, float>(P, l, R, st);
-        }
-        mark(4);
-        // transposed M2L: the opposite transfer vectors
-        for (int l = 2; l <= lf; ++l) {
-            if (P->lev[l].prec == kFP64) launch_m2l<double>(P, l, R, st, true);
-            else launch_m2l<float>(P, l, R, st, true);
-        }
-        mark(5);
-        // transposed M2M, level 2 down to the leaf level, added to the M2L part
-        for (int l = 3; l <= lf; ++l) {
-            const int pi = P->lev[l - 1].prec, po = P->lev[l].prec;
-            if (pi == kFP64 && po == kFP64) launch_m2m_t<double, double>(P, l, R, st);
-            else if (po == kFP64) launch_m2m_t<float, double>(P, l, R, st);
-            else launch_m2m_t<float, float>(P, l, R, st);
-        }
-        mark(6);
+        transposed_far_chain(P, R, st, mark);
         // transposed S2M: plane-wave sums back onto the sources
         if (P->lev[lf].prec == kFP64) launch_l2t<double>(P, R, st, true);
         else launch_l2t<float>(P, R, st, true);
@@ -824,6 +834,54 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t P, const void* w, void* out, int nrhs
     mark(8);
     P->ev_recorded = P->timing;
     return check_launch("hfmm_apply_adjoint");
+}
+
+hfmm_status hfmm_grad_sources(hfmm_plan_t P, const void* q, const void* g, double* grad, int nrhs,
+                              hfmm_dtype dtype, void* stream) {
+    if (!P) return fail(HFMM_ERR_ARG, "plan is NULL");
+    if (P->device < 0) return fail(HFMM_ERR_STATE, "host-only plan has no device data");
+    if (!q || !g || !grad) return fail(HFMM_ERR_ARG, "q, g and grad must be device pointers");
+    if (nrhs < 1 || nrhs > P->rmax) return fail(HFMM_ERR_ARG, "nrhs must be in [1, max_rhs]");
+    if (dtype != HFMM_C64 && dtype != HFMM_C128) return fail(HFMM_ERR_ARG, "unknown dtype");
+    CK(cudaSetDevice(P->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    HostPlan& hp = P->hp;
+    const int R = nrhs;
+    const int lf = hp.lf;
+    auto mark = [&](int i) {
+        if (P->timing) cudaEventRecord(P->ev[i], st);
+    };
+    mark(0);
+    if (dtype == HFMM_C64) {
+        k_permute_in<float, false><<<nblk(hp.ns * R, 256), 256, 0, st>>>((const cxf*)q, hp.ns, R, P->src_perm, P->qs);
+        k_permute_in<float, true><<<nblk(hp.nt * R, 256), 256, 0, st>>>((const cxf*)g, hp.nt, R, P->tgt_perm, P->phis);
+    } else {
+        k_permute_in<double, false><<<nblk(hp.ns * R, 256), 256, 0, st>>>((const cxd*)q, hp.ns, R, P->src_perm, P->qs);
+        k_permute_in<double, true><<<nblk(hp.nt * R, 256), 256, 0, st>>>((const cxd*)g, hp.nt, R, P->tgt_perm, P->phis);
+    }
+    mark(1);
+    const int nleaf = (int)hp.levels[lf].nbox();
+    k_grad_near<<<nleaf, kP2PThreads, 0, st>>>(nleaf, P->sstart, P->scount, P->tstart, P->tcount, P->noff, P->nidx,
+                                               P->sx, P->sy, P->sz, P->tx, P->ty, P->tz, P->qs, P->phis, R,
+                                               hp.kappa, P->gsort);
+    mark(2);
+    if (lf >= 2) {
+        transposed_far_chain(P, R, st, mark);
+        DevLevel& d = P->lev[lf];
+        if (d.prec == kFP64)
+            k_grad_far<double><<<d.nbox, kL2TThreads, 0, st>>>(d.bv, d.qv, P->sstart, P->scount, P->sx, P->sy, P->sz,
+                                                               (const cxd*)d.M, P->qs, R, hp.kappa, P->gsort);
+        else
+            k_grad_far<float><<<d.nbox, kL2TThreads, 0, st>>>(d.bv, d.qv, P->sstart, P->scount, P->sx, P->sy, P->sz,
+                                                              (const cxf*)d.M, P->qs, R, hp.kappa, P->gsort);
+        mark(7);
+    } else {
+        for (int i = 3; i <= 7; ++i) mark(i);
+    }
+    k_scatter_grad<<<nblk(hp.ns * 3, 256), 256, 0, st>>>(P->gsort, hp.ns, P->src_perm, grad);
+    mark(8);
+    P->ev_recorded = P->timing;
+    return check_launch("hfmm_grad_sources");
 }
 
 hfmm_status hfmm_query(hfmm_plan_t P, hfmm_info* info) {

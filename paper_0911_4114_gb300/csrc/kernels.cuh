@@ -461,6 +461,147 @@ __global__ void k_l2t_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ts
 }
 
 // ---------------------------------------------------------------------------
+// Position gradient (vector-Jacobian product of phi = A(y) q for a real loss, with
+// g = dL/d conj(phi) in the convention of complex autograd):
+//   grad_j = Re[ sum_r q_jr ( i k sum_k s_k exp(i k s_k.(y_j - c_b)) Lambda_b,r(k)
+//                             + sum_{i in N(b)} conj(g_ir) dG(x_i, y_j)/dy_j ) ]
+// with Lambda = the transposed far-field chain applied to conj(g) and
+// dG/dy = G (i k - 1/R) (y - x) / R.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_grad_far(BoxView bx, QuadView qv, const int32_t* __restrict__ sstart,
+                           const int32_t* __restrict__ scount, const double* __restrict__ sx,
+                           const double* __restrict__ sy, const double* __restrict__ sz,
+                           const cx<R>* __restrict__ Lam, const cxd* __restrict__ qs, int R_, double kappa,
+                           double* __restrict__ grad) {
+    __shared__ double shs[kL2TThreads * 3];
+    __shared__ cx<R> shl[kL2TThreads];
+    const int b = blockIdx.x;
+    const int s0 = sstart[b], sc = scount[b];
+    if (sc == 0) return;
+    const double kt = kappa / (2.0 * 3.14159265358979323846);
+    const double cxx = bx.center[3 * b], cyy = bx.center[3 * b + 1], czz = bx.center[3 * b + 2];
+    for (int jb = 0; jb < sc; jb += kL2TThreads) {
+        const int jj = jb + threadIdx.x;
+        const bool active = jj < sc;
+        double d[3] = {0, 0, 0};
+        if (active) {
+            d[0] = sx[s0 + jj] - cxx;
+            d[1] = sy[s0 + jj] - cyy;
+            d[2] = sz[s0 + jj] - czz;
+        }
+        double g[3] = {0, 0, 0};
+        for (int r = 0; r < R_; ++r) {
+            const cx<R>* Lb = Lam + ((int64_t)b * R_ + r) * qv.K;
+            cxd acc[3] = {mk<double>(0, 0), mk<double>(0, 0), mk<double>(0, 0)};
+            for (int64_t kb = 0; kb < qv.K; kb += kL2TThreads) {
+                const int kn = (int)min((int64_t)kL2TThreads, qv.K - kb);
+                __syncthreads();
+                if (threadIdx.x < kn) {
+                    const int64_t k = kb + threadIdx.x;
+                    for (int c = 0; c < 3; ++c) shs[3 * threadIdx.x + c] = qv.shat[3 * k + c];
+                    shl[threadIdx.x] = Lb[k];
+                }
+                __syncthreads();
+                if (active)
+                    for (int kk = 0; kk < kn; ++kk) {
+                        double t = turns(kt, &shs[3 * kk], d[0], d[1], d[2]);
+                        cx<R> e = plane_wave<R>(t) * shl[kk];
+                        for (int c = 0; c < 3; ++c) {
+                            acc[c].x += shs[3 * kk + c] * (double)e.x;
+                            acc[c].y += shs[3 * kk + c] * (double)e.y;
+                        }
+                    }
+            }
+            if (active) {
+                const cxd q = qs[(int64_t)(s0 + jj) * R_ + r];
+                for (int c = 0; c < 3; ++c) {
+                    // Re[q * i k acc] = -k (q.x acc.y + q.y acc.x)
+                    g[c] += -kappa * (q.x * acc[c].y + q.y * acc[c].x);
+                }
+            }
+        }
+        if (active)
+            for (int c = 0; c < 3; ++c) grad[(int64_t)(s0 + jj) * 3 + c] += g[c];
+    }
+}
+
+// near-field part; one CTA per source leaf box, targets of the neighbour boxes staged
+__global__ void k_grad_near(int nbox, const int32_t* __restrict__ sstart, const int32_t* __restrict__ scount,
+                            const int32_t* __restrict__ tstart, const int32_t* __restrict__ tcount,
+                            const int32_t* __restrict__ noff, const int32_t* __restrict__ nidx,
+                            const double* __restrict__ sx, const double* __restrict__ sy,
+                            const double* __restrict__ sz, const double* __restrict__ tx,
+                            const double* __restrict__ ty, const double* __restrict__ tz,
+                            const cxd* __restrict__ qs, const cxd* __restrict__ gconj, int R_, double kappa,
+                            double* __restrict__ grad) {
+    __shared__ double shx[kP2PThreads], shy[kP2PThreads], shz[kP2PThreads];
+    __shared__ cxd shg[kP2PThreads];
+    const int b = blockIdx.x;
+    if (b >= nbox) return;
+    const int s0 = sstart[b], sc = scount[b];
+    for (int jb = 0; jb < sc; jb += kP2PThreads) {
+        const int jj = jb + threadIdx.x;
+        const bool active = jj < sc;
+        double y0 = 0, y1 = 0, y2 = 0;
+        if (active) {
+            y0 = sx[s0 + jj];
+            y1 = sy[s0 + jj];
+            y2 = sz[s0 + jj];
+        }
+        double gsum[3] = {0, 0, 0};
+        for (int r = 0; r < R_; ++r) {
+            cxd acc[3] = {mk<double>(0, 0), mk<double>(0, 0), mk<double>(0, 0)};
+            for (int nb = noff[b]; nb < noff[b + 1]; ++nb) {
+                const int t = nidx[nb];
+                const int t0 = tstart[t], tc = tcount[t];
+                for (int ib = 0; ib < tc; ib += kP2PThreads) {
+                    const int in = min(kP2PThreads, tc - ib);
+                    __syncthreads();
+                    if (threadIdx.x < in) {
+                        const int i = t0 + ib + threadIdx.x;
+                        shx[threadIdx.x] = tx[i];
+                        shy[threadIdx.x] = ty[i];
+                        shz[threadIdx.x] = tz[i];
+                        shg[threadIdx.x] = gconj[(int64_t)i * R_ + r];
+                    }
+                    __syncthreads();
+                    if (active)
+                        for (int ii = 0; ii < in; ++ii) {
+                            const double dx = y0 - shx[ii], dy = y1 - shy[ii], dz = y2 - shz[ii];
+                            const double r2 = dx * dx + dy * dy + dz * dz;
+                            if (r2 == 0.0) continue;
+                            const double rr = sqrt(r2), inv = 1.0 / rr;
+                            double sn_, cs_;
+                            sincos(kappa * rr, &sn_, &cs_);
+                            // G (i k - 1/R) / R
+                            const cxd gk = mk<double>(cs_ * inv, sn_ * inv) * mk<double>(-inv * inv, kappa * inv);
+                            const cxd v = gk * shg[ii];
+                            acc[0].x += v.x * dx; acc[0].y += v.y * dx;
+                            acc[1].x += v.x * dy; acc[1].y += v.y * dy;
+                            acc[2].x += v.x * dz; acc[2].y += v.y * dz;
+                        }
+                }
+            }
+            if (active) {
+                const cxd q = qs[(int64_t)(s0 + jj) * R_ + r];
+                for (int c = 0; c < 3; ++c) gsum[c] += q.x * acc[c].x - q.y * acc[c].y;
+            }
+        }
+        if (active)
+            for (int c = 0; c < 3; ++c) grad[(int64_t)(s0 + jj) * 3 + c] = gsum[c];
+    }
+}
+
+__global__ void k_scatter_grad(const double* __restrict__ gs, int64_t n, const int64_t* __restrict__ perm,
+                               double* __restrict__ grad) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n * 3) return;
+    int64_t p = t / 3;
+    grad[perm[p] * 3 + (t - p * 3)] = gs[t];
+}
+
+// ---------------------------------------------------------------------------
 // M2L: I_a(s_k) = sum_{b in I(a)} T^{s,LL}_{v(a,b)}(s_k) M_b(s_k); thread per (box, k)
 // ---------------------------------------------------------------------------
 template <typename R>

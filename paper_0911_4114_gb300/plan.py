@@ -104,6 +104,24 @@ class FmmPlan:
         self.apply_adjoint_ptr(w2.data_ptr(), out.data_ptr(), r, dtype, st.cuda_stream)
         return out[:, 0] if single else out
 
+    def grad_sources(self, q, g, out=None, stream=None):
+        """Source-position gradient: Re sum_r q_r * (d phi / d y)^T conj(g_r), shape (ns, 3) float64.
+
+        g = dL/d conj(phi) in complex autograd's convention (2 (phi - phi*) for a squared error).
+        """
+        import torch
+        q2 = q.reshape(q.shape[0], -1).contiguous()
+        g2 = g.reshape(g.shape[0], -1).to(q.dtype).contiguous()
+        if q2.shape != (self.ns, g2.shape[1]) or g2.shape[0] != self.nt:
+            raise ValueError("q must be (ns, R) and g (nt, R)")
+        if out is None:
+            out = torch.empty((self.ns, 3), dtype=torch.float64, device=q.device)
+        st = stream if stream is not None else torch.cuda.current_stream(q.device)
+        dtype = nat.C64 if q.dtype == torch.complex64 else nat.C128
+        nat.check(nat.lib().hfmm_grad_sources(self._h, q2.data_ptr(), g2.data_ptr(), out.data_ptr(),
+                                               q2.shape[1], dtype, st.cuda_stream))
+        return out
+
     # -- queries -------------------------------------------------------------
     def set_timing(self, on=True):
         nat.check(nat.lib().hfmm_set_timing(self._h, 1 if on else 0))
