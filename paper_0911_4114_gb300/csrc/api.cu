@@ -52,6 +52,7 @@ struct DevLevel {
     void* table = nullptr;      // compact T^{s,LL} tables in the level precision
     cxd* shift64 = nullptr;     // [8][K] exp(i k s.d_o), d_o = child-centre offsets of level l+1
     cxf* shift32 = nullptr;
+    cx<df>* shiftdf = nullptr;
     void* M = nullptr;          // nbox * Rmax * K
     void* IL = nullptr;         // incoming, then local expansions (in place)
 };
@@ -75,12 +76,13 @@ struct hfmm_plan_s {
     int32_t *noff = nullptr, *nidx = nullptr;
     P2PMixedArgs mixed{};
     cxd *qs = nullptr, *phis = nullptr;
+    int max_src_leaf = 1, max_tgt_leaf = 1;   // largest leaf-box point counts (grid heights)
     double* gsort = nullptr;    // sorted position gradient (ns, 3)
     DevLevel lev[kMaxLevels];
     Requad up[kMaxLevels];    // up[l]: level l -> l-1
     Requad down[kMaxLevels];  // down[l]: level l -> l+1
     void *ga = nullptr, *gb = nullptr;
-    void *tw64 = nullptr, *tw32 = nullptr;
+    void *tw64 = nullptr, *tw32 = nullptr, *twdf = nullptr;
     int* twoff = nullptr;
     cdf* cis_tab = nullptr;     // exp(2 pi i j / 256) as double-float pairs
     int64_t workspace = 0;
@@ -180,7 +182,17 @@ hfmm_status upload_level(hfmm_plan_s* P, int l) {
     std::vector<int32_t> slot_t(kNumTransfer, 0);
     for (int v = 0; v < kNumTransfer; ++v) slot_t[v] = slot[kNumTransfer - 1 - v];
     TRY(upload(P, &d.tslot_t, slot_t));
-    if (d.prec == kFP64) {
+    const bool store_df = d.prec == kFP64 && hp.precision == HFMM_PREC_MIXED;
+    if (store_df) {
+        std::vector<cx<df>> t((size_t)ns * q.K);
+        for (int v = 0; v < kNumTransfer; ++v)
+            if (!lp.table[v].empty())
+                for (int64_t k = 0; k < q.K; ++k)
+                    t[(size_t)slot[v] * q.K + k] = mk<df>(df(lp.table[v][k].real()), df(lp.table[v][k].imag()));
+        cx<df>* dt;
+        TRY(upload(P, &dt, t));
+        d.table = dt;
+    } else if (d.prec == kFP64) {
         std::vector<cxd> t((size_t)ns * q.K);
         for (int v = 0; v < kNumTransfer; ++v)
             if (!lp.table[v].empty())
@@ -205,6 +217,7 @@ hfmm_status upload_level(hfmm_plan_s* P, int l) {
         const double ac = hp.side / (double)(1u << (l + 1));
         std::vector<cxd> s64((size_t)8 * q.K);
         std::vector<cxf> s32((size_t)8 * q.K);
+        std::vector<cx<df>> sdf((size_t)8 * q.K);
         for (int o = 0; o < 8; ++o) {
             const double dvec[3] = {(((o >> 2) & 1) - 0.5) * ac, (((o >> 1) & 1) - 0.5) * ac,
                                     ((o & 1) - 0.5) * ac};
@@ -213,10 +226,12 @@ hfmm_status upload_level(hfmm_plan_s* P, int l) {
                                               shat[3 * k + 2] * dvec[2]);
                 s64[(size_t)o * q.K + k] = mk<double>(std::cos(ph), std::sin(ph));
                 s32[(size_t)o * q.K + k] = mk<float>((float)std::cos(ph), (float)std::sin(ph));
+                sdf[(size_t)o * q.K + k] = mk<df>(df(std::cos(ph)), df(std::sin(ph)));
             }
         }
         TRY(upload(P, &d.shift64, s64));
         TRY(upload(P, &d.shift32, s32));
+        TRY(upload(P, &d.shiftdf, sdf));
     }
     // signature buffers
     const size_t bytes = (size_t)d.nbox * P->rmax * q.K * cx_bytes(d.prec);
@@ -261,6 +276,8 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
     TRY(soa(hp.tgt, hp.tgt_perm, &P->tx, &P->ty, &P->tz));
     TRY(upload(P, &P->src_perm, hp.src_perm));
     TRY(upload(P, &P->tgt_perm, hp.tgt_perm));
+    for (int32_t c : hp.src_count) P->max_src_leaf = std::max(P->max_src_leaf, (int)c);
+    for (int32_t c : hp.tgt_count) P->max_tgt_leaf = std::max(P->max_tgt_leaf, (int)c);
     TRY(upload(P, &P->sstart, hp.src_start));
     TRY(upload(P, &P->scount, hp.src_count));
     TRY(upload(P, &P->tstart, hp.tgt_start));
@@ -332,6 +349,7 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
     std::vector<int> off(maxlen + 1, -1);
     std::vector<cxd> t64;
     std::vector<cxf> t32;
+    std::vector<cx<df>> tdf;
     std::sort(lengths.begin(), lengths.end());
     lengths.erase(std::unique(lengths.begin(), lengths.end()), lengths.end());
     for (int n : lengths) {
@@ -341,15 +359,19 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
             const double ang = 2.0 * 3.14159265358979323846 * (double)t / (double)n;
             t64.push_back(mk<double>(std::cos(ang), -std::sin(ang)));
             t32.push_back(mk<float>((float)std::cos(ang), (float)-std::sin(ang)));
+            tdf.push_back(mk<df>(df(std::cos(ang)), df(-std::sin(ang))));
         }
     }
     cxd* d64;
     cxf* d32;
+    cx<df>* ddf;
     TRY(upload(P, &d64, t64));
     TRY(upload(P, &d32, t32));
+    TRY(upload(P, &ddf, tdf));
     TRY(upload(P, &P->twoff, off));
     P->tw64 = d64;
     P->tw32 = d32;
+    P->twdf = ddf;
     for (int l = 2; l <= hp.lf; ++l) {
         for (Requad* r : {&P->up[l], &P->down[l]}) {
             r->args.tw.off = P->twoff;
@@ -360,9 +382,6 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
         P->up[l].args.qb = P->lev[l - 1].qv;
         P->down[l - 1].args.qa = P->lev[l - 1].qv;
         P->down[l - 1].args.qb = P->lev[l].qv;
-        // M2M computes in the parent's precision, L2L in the child's
-        P->up[l].args.tw.pool = (P->lev[l - 1].prec == kFP64) ? P->tw64 : P->tw32;
-        P->down[l - 1].args.tw.pool = (P->lev[l].prec == kFP64) ? P->tw64 : P->tw32;
     }
     {
         std::vector<cdf> tab(kCisTable);
@@ -387,104 +406,155 @@ void smem_opt_in(K kernel, size_t bytes) {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <typename Tin, typename Tc>
+template <typename T> const void* pool_of(hfmm_plan_s* P);
+template <> const void* pool_of<float>(hfmm_plan_s* P) { return P->tw32; }
+template <> const void* pool_of<double>(hfmm_plan_s* P) { return P->tw64; }
+template <> const void* pool_of<df>(hfmm_plan_s* P) { return P->twdf; }
+template <typename T> const cx<T>* shift_of(const DevLevel& d);
+template <> const cx<float>* shift_of<float>(const DevLevel& d) { return d.shift32; }
+template <> const cx<double>* shift_of<double>(const DevLevel& d) { return d.shift64; }
+template <> const cx<df>* shift_of<df>(const DevLevel& d) { return d.shiftdf; }
+
+// Re-quadrature launches.  Tin / Tout: storage types of the input and output levels;
+// Tc: compute type (the precision of the level whose accuracy the result needs).
+//   M2M l -> l-1: compute in level l-1's type     L2L l -> l+1: compute in level l+1's type
+//   transposed L2L l+1 -> l: level l's type        transposed M2M l-1 -> l: level l's type
+template <typename Tin, typename Tc, typename Tout>
 void launch_up(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
-    Requad& rq = P->up[l];
+    RequadArgs ra = P->up[l].args;
+    ra.tw.pool = pool_of<Tc>(P);
     DevLevel& c = P->lev[l];
     DevLevel& p = P->lev[l - 1];
-    const size_t sm = (size_t)kWarps * 2 * rq.args.maxlen * sizeof(cx<Tc>);
+    const size_t sm = (size_t)kWarps * 2 * ra.maxlen * sizeof(cx<Tc>);
     cx<Tc>* GA = (cx<Tc>*)P->ga;
     cx<Tc>* GB = (cx<Tc>*)P->gb;
     smem_opt_in(k_requad_rows_a<Tin, Tc, kNoShift, false>, sm);
     smem_opt_in(k_requad_cols<Tc, false>, sm);
-    smem_opt_in(k_requad_rows_c_m2m<Tc, Tc, kShiftPlain, false>, sm);
-    int64_t nA = (int64_t)c.nbox * R * rq.args.qa.nrows;
-    k_requad_rows_a<Tin, Tc, kNoShift, false><<<nblk(nA, kWarps), 32 * kWarps, sm, st>>>(
-        rq.args, c.nbox, R, (const cx<Tin>*)c.M, nullptr, nullptr, nullptr, GA);
-    int64_t nB = (int64_t)c.nbox * R * (rq.args.big / 2);
-    k_requad_cols<Tc, false><<<nblk(nB, kWarps), 32 * kWarps, sm, st>>>(rq.args, c.nbox, R, GA, GB);
-    int64_t nC = (int64_t)p.nbox * R * rq.args.qb.nrows;
-    const cx<Tc>* shift = (const cx<Tc>*)(std::is_same<Tc, double>::value ? (void*)p.shift64 : (void*)p.shift32);
-    k_requad_rows_c_m2m<Tc, Tc, kShiftPlain, false><<<nblk(nC, kWarps), 32 * kWarps, sm, st>>>(
-        rq.args, p.nbox, R, p.bv.child_start, p.bv.child_count, c.octant, shift, GB, (cx<Tc>*)p.M);
+    smem_opt_in(k_requad_rows_c_m2m<Tc, Tout, kShiftPlain, false>, sm);
+    k_requad_rows_a<Tin, Tc, kNoShift, false><<<nblk((int64_t)c.nbox * R * ra.qa.nrows, kWarps), 32 * kWarps, sm, st>>>(
+        ra, c.nbox, R, (const cx<Tin>*)c.M, nullptr, nullptr, nullptr, GA);
+    k_requad_cols<Tc, false><<<nblk((int64_t)c.nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(
+        ra, c.nbox, R, GA, GB);
+    k_requad_rows_c_m2m<Tc, Tout, kShiftPlain, false><<<nblk((int64_t)p.nbox * R * ra.qb.nrows, kWarps), 32 * kWarps, sm, st>>>(
+        ra, p.nbox, R, p.bv.child_start, p.bv.child_count, c.octant, shift_of<Tc>(p), GB, (cx<Tout>*)p.M);
 }
 
-// transposed L2L: level l+1 (Lambda_L of the children) -> level l (Lambda_L of the parents)
-template <typename Tin, typename Tc>
+template <typename Tin, typename Tc, typename Tout>
 void launch_l2l_t(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
-    Requad& rq = P->up[l + 1];
+    RequadArgs ra = P->up[l + 1].args;
+    ra.tw.pool = pool_of<Tc>(P);
     DevLevel& c = P->lev[l + 1];
     DevLevel& p = P->lev[l];
-    const size_t sm = (size_t)kWarps * 2 * rq.args.maxlen * sizeof(cx<Tc>);
+    const size_t sm = (size_t)kWarps * 2 * ra.maxlen * sizeof(cx<Tc>);
     cx<Tc>* GA = (cx<Tc>*)P->ga;
     cx<Tc>* GB = (cx<Tc>*)P->gb;
     smem_opt_in(k_requad_rows_a<Tin, Tc, kNoShift, true>, sm);
     smem_opt_in(k_requad_cols<Tc, true>, sm);
-    smem_opt_in(k_requad_rows_c_m2m<Tc, Tc, kShiftConj, true>, sm);
-    int64_t nA = (int64_t)c.nbox * R * rq.args.qa.nrows;
-    k_requad_rows_a<Tin, Tc, kNoShift, true><<<nblk(nA, kWarps), 32 * kWarps, sm, st>>>(
-        rq.args, c.nbox, R, (const cx<Tin>*)c.IL, nullptr, nullptr, nullptr, GA);
-    int64_t nB = (int64_t)c.nbox * R * (rq.args.big / 2);
-    k_requad_cols<Tc, true><<<nblk(nB, kWarps), 32 * kWarps, sm, st>>>(rq.args, c.nbox, R, GA, GB);
-    int64_t nC = (int64_t)p.nbox * R * rq.args.qb.nrows;
-    const cx<Tc>* shift = (const cx<Tc>*)(std::is_same<Tc, double>::value ? (void*)p.shift64 : (void*)p.shift32);
-    k_requad_rows_c_m2m<Tc, Tc, kShiftConj, true><<<nblk(nC, kWarps), 32 * kWarps, sm, st>>>(
-        rq.args, p.nbox, R, p.bv.child_start, p.bv.child_count, c.octant, shift, GB, (cx<Tc>*)p.IL);
+    smem_opt_in(k_requad_rows_c_m2m<Tc, Tout, kShiftConj, true>, sm);
+    k_requad_rows_a<Tin, Tc, kNoShift, true><<<nblk((int64_t)c.nbox * R * ra.qa.nrows, kWarps), 32 * kWarps, sm, st>>>(
+        ra, c.nbox, R, (const cx<Tin>*)c.IL, nullptr, nullptr, nullptr, GA);
+    k_requad_cols<Tc, true><<<nblk((int64_t)c.nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(
+        ra, c.nbox, R, GA, GB);
+    k_requad_rows_c_m2m<Tc, Tout, kShiftConj, true><<<nblk((int64_t)p.nbox * R * ra.qb.nrows, kWarps), 32 * kWarps, sm, st>>>(
+        ra, p.nbox, R, p.bv.child_start, p.bv.child_count, c.octant, shift_of<Tc>(p), GB, (cx<Tout>*)p.IL);
 }
 
-template <typename Tin, typename Tc>
+template <typename Tin, typename Tc, typename Tout>
 void launch_down(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
-    Requad& rq = P->down[l];
+    RequadArgs ra = P->down[l].args;
+    ra.tw.pool = pool_of<Tc>(P);
     DevLevel& p = P->lev[l];
     DevLevel& c = P->lev[l + 1];
-    const size_t sm = (size_t)kWarps * 2 * rq.args.maxlen * sizeof(cx<Tc>);
+    const size_t sm = (size_t)kWarps * 2 * ra.maxlen * sizeof(cx<Tc>);
     cx<Tc>* GA = (cx<Tc>*)P->ga;
     cx<Tc>* GB = (cx<Tc>*)P->gb;
-    const cx<Tc>* shift = (const cx<Tc>*)(std::is_same<Tc, double>::value ? (void*)p.shift64 : (void*)p.shift32);
     smem_opt_in(k_requad_rows_a<Tin, Tc, kShiftConj, false>, sm);
     smem_opt_in(k_requad_cols<Tc, false>, sm);
-    smem_opt_in(k_requad_rows_c_l2l<Tc, false>, sm);
-    int64_t nA = (int64_t)c.nbox * R * rq.args.qa.nrows;
-    k_requad_rows_a<Tin, Tc, kShiftConj, false><<<nblk(nA, kWarps), 32 * kWarps, sm, st>>>(
-        rq.args, c.nbox, R, (const cx<Tin>*)p.IL, c.bv.parent, c.octant, shift, GA);
-    int64_t nB = (int64_t)c.nbox * R * (rq.args.big / 2);
-    k_requad_cols<Tc, false><<<nblk(nB, kWarps), 32 * kWarps, sm, st>>>(rq.args, c.nbox, R, GA, GB);
-    int64_t nC = (int64_t)c.nbox * R * rq.args.qb.nrows;
-    k_requad_rows_c_l2l<Tc, false><<<nblk(nC, kWarps), 32 * kWarps, sm, st>>>(rq.args, c.nbox, R, GB, (cx<Tc>*)c.IL);
+    smem_opt_in(k_requad_rows_c_l2l<Tc, Tout, false>, sm);
+    k_requad_rows_a<Tin, Tc, kShiftConj, false><<<nblk((int64_t)c.nbox * R * ra.qa.nrows, kWarps), 32 * kWarps, sm, st>>>(
+        ra, c.nbox, R, (const cx<Tin>*)p.IL, c.bv.parent, c.octant, shift_of<Tc>(p), GA);
+    k_requad_cols<Tc, false><<<nblk((int64_t)c.nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(
+        ra, c.nbox, R, GA, GB);
+    k_requad_rows_c_l2l<Tc, Tout, false><<<nblk((int64_t)c.nbox * R * ra.qb.nrows, kWarps), 32 * kWarps, sm, st>>>(
+        ra, c.nbox, R, GB, (cx<Tout>*)c.IL);
 }
 
-// transposed M2M: level l-1 (Lambda_M of the parents) -> level l (Lambda_M of the children, added)
-template <typename Tin, typename Tc>
+template <typename Tin, typename Tc, typename Tout>
 void launch_m2m_t(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
-    Requad& rq = P->down[l - 1];
+    RequadArgs ra = P->down[l - 1].args;
+    ra.tw.pool = pool_of<Tc>(P);
     DevLevel& p = P->lev[l - 1];
     DevLevel& c = P->lev[l];
-    const size_t sm = (size_t)kWarps * 2 * rq.args.maxlen * sizeof(cx<Tc>);
+    const size_t sm = (size_t)kWarps * 2 * ra.maxlen * sizeof(cx<Tc>);
     cx<Tc>* GA = (cx<Tc>*)P->ga;
     cx<Tc>* GB = (cx<Tc>*)P->gb;
-    const cx<Tc>* shift = (const cx<Tc>*)(std::is_same<Tc, double>::value ? (void*)p.shift64 : (void*)p.shift32);
     smem_opt_in(k_requad_rows_a<Tin, Tc, kShiftPlain, true>, sm);
     smem_opt_in(k_requad_cols<Tc, true>, sm);
-    smem_opt_in(k_requad_rows_c_l2l<Tc, true>, sm);
-    int64_t nA = (int64_t)c.nbox * R * rq.args.qa.nrows;
-    k_requad_rows_a<Tin, Tc, kShiftPlain, true><<<nblk(nA, kWarps), 32 * kWarps, sm, st>>>(
-        rq.args, c.nbox, R, (const cx<Tin>*)p.M, c.bv.parent, c.octant, shift, GA);
-    int64_t nB = (int64_t)c.nbox * R * (rq.args.big / 2);
-    k_requad_cols<Tc, true><<<nblk(nB, kWarps), 32 * kWarps, sm, st>>>(rq.args, c.nbox, R, GA, GB);
-    int64_t nC = (int64_t)c.nbox * R * rq.args.qb.nrows;
-    k_requad_rows_c_l2l<Tc, true><<<nblk(nC, kWarps), 32 * kWarps, sm, st>>>(rq.args, c.nbox, R, GB, (cx<Tc>*)c.M);
+    smem_opt_in(k_requad_rows_c_l2l<Tc, Tout, true>, sm);
+    k_requad_rows_a<Tin, Tc, kShiftPlain, true><<<nblk((int64_t)c.nbox * R * ra.qa.nrows, kWarps), 32 * kWarps, sm, st>>>(
+        ra, c.nbox, R, (const cx<Tin>*)p.M, c.bv.parent, c.octant, shift_of<Tc>(p), GA);
+    k_requad_cols<Tc, true><<<nblk((int64_t)c.nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(
+        ra, c.nbox, R, GA, GB);
+    k_requad_rows_c_l2l<Tc, Tout, true><<<nblk((int64_t)c.nbox * R * ra.qb.nrows, kWarps), 32 * kWarps, sm, st>>>(
+        ra, c.nbox, R, GB, (cx<Tout>*)c.M);
 }
 
-template <typename T>
-void launch_m2l(hfmm_plan_s* P, int l, int R, cudaStream_t st, bool transposed = false) {
+template <typename S, typename C>
+void launch_m2l(hfmm_plan_s* P, int l, int R, cudaStream_t st, bool transposed) {
     DevLevel& d = P->lev[l];
     dim3 grid(d.nbox, nblk(d.K, 256));
     if (!transposed)
-        k_m2l<T><<<grid, 256, 0, st>>>(d.nbox, d.K, d.ioff, d.iidx, d.iv, d.tslot, (const cx<T>*)d.table,
-                                       (const cx<T>*)d.M, R, (cx<T>*)d.IL);
+        k_m2l<S, C><<<grid, 256, 0, st>>>(d.nbox, d.K, d.ioff, d.iidx, d.iv, d.tslot, (const cx<S>*)d.table,
+                                          (const cx<S>*)d.M, R, (cx<S>*)d.IL);
     else
-        k_m2l<T><<<grid, 256, 0, st>>>(d.nbox, d.K, d.ioff, d.iidx, d.iv, d.tslot_t, (const cx<T>*)d.table,
-                                       (const cx<T>*)d.IL, R, (cx<T>*)d.M);
+        k_m2l<S, C><<<grid, 256, 0, st>>>(d.nbox, d.K, d.ioff, d.iidx, d.iv, d.tslot_t, (const cx<S>*)d.table,
+                                          (const cx<S>*)d.IL, R, (cx<S>*)d.M);
+}
+
+// type codes of a level's signatures and arithmetic: 0 float, 1 double, 2 double-float
+// (float64 levels of the mixed policy store and compute in double-float pairs)
+int store_code(hfmm_plan_s* P, int l) {
+    if (P->lev[l].prec != kFP64) return 0;
+    return P->hp.precision == HFMM_PREC_MIXED ? 2 : 1;
+}
+int compute_code(hfmm_plan_s* P, int l) { return store_code(P, l); }
+
+template <typename Fn>
+bool dispatch3(int sin, int cc, int sout, Fn fn) {
+    if (sin == 1 && cc == 1 && sout == 1) fn(double{}, double{}, double{});
+    else if (sin == 2 && cc == 2 && sout == 2) fn(df{}, df{}, df{});
+    else if (sin == 2 && cc == 0 && sout == 0) fn(df{}, float{}, float{});
+    else if (sin == 0 && cc == 0 && sout == 0) fn(float{}, float{}, float{});
+    else if (sin == 0 && cc == 2 && sout == 2) fn(float{}, df{}, df{});
+    else return false;
+    return true;
+}
+
+void run_up(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
+    dispatch3(store_code(P, l), compute_code(P, l - 1), store_code(P, l - 1), [&](auto a, auto b, auto c) {
+        launch_up<decltype(a), decltype(b), decltype(c)>(P, l, R, st);
+    });
+}
+void run_down(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
+    dispatch3(store_code(P, l), compute_code(P, l + 1), store_code(P, l + 1), [&](auto a, auto b, auto c) {
+        launch_down<decltype(a), decltype(b), decltype(c)>(P, l, R, st);
+    });
+}
+void run_l2l_t(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
+    dispatch3(store_code(P, l + 1), compute_code(P, l), store_code(P, l), [&](auto a, auto b, auto c) {
+        launch_l2l_t<decltype(a), decltype(b), decltype(c)>(P, l, R, st);
+    });
+}
+void run_m2m_t(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
+    dispatch3(store_code(P, l - 1), compute_code(P, l), store_code(P, l), [&](auto a, auto b, auto c) {
+        launch_m2m_t<decltype(a), decltype(b), decltype(c)>(P, l, R, st);
+    });
+}
+void run_m2l(hfmm_plan_s* P, int l, int R, cudaStream_t st, bool transposed) {
+    const int cc = compute_code(P, l);
+    if (cc == 0) launch_m2l<float, float>(P, l, R, st, transposed);
+    else if (cc == 1) launch_m2l<double, double>(P, l, R, st, transposed);
+    else launch_m2l<df, df>(P, l, R, st, transposed);
 }
 
 // float64 levels of the mixed policy evaluate their plane waves in double-float
@@ -509,7 +579,7 @@ void launch_s2m(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false)
     dim3 grid(d.nbox, nblk(d.K, kS2MThreads));
     if (std::is_same<T, double>::value && use_df(P, lf)) {
         k_s2m_df<<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt, P->cis_tab,
-                                               (cxd*)out, sign, wk);
+                                               (cx<df>*)out, sign, wk);
         return;
     }
     k_s2m<T><<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt, (cx<T>*)out,
@@ -532,12 +602,13 @@ void launch_l2t(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false)
     const double sign = transposed ? -1.0 : 1.0;
     const double* wk = transposed ? nullptr : d.qv.w;
     const double kt = P->hp.kappa / (2.0 * 3.14159265358979323846);
+    const dim3 grid(d.nbox, nblk(transposed ? P->max_src_leaf : P->max_tgt_leaf, kL2TThreads));
     if (std::is_same<T, double>::value && use_df(P, lf)) {
-        k_l2t_df<<<d.nbox, kL2TThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, (const cxd*)in, R, kt,
+        k_l2t_df<<<grid, kL2TThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, (const cx<df>*)in, R, kt,
                                                  P->cis_tab, out, sign, wk);
         return;
     }
-    k_l2t<T><<<d.nbox, kL2TThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, (const cx<T>*)in, R, kt, out,
+    k_l2t<T><<<grid, kL2TThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, (const cx<T>*)in, R, kt, out,
                                              sign, wk);
 }
 
@@ -551,26 +622,13 @@ void transposed_far_chain(hfmm_plan_s* P, int R, cudaStream_t st, Mark mark) {
     else launch_s2m<float>(P, R, st, true);
     mark(3);
     // transposed L2L, leaf level up to level 2
-    for (int l = lf - 1; l >= 2; --l) {
-        const int pi = P->lev[l + 1].prec, po = P->lev[l].prec;
-        if (pi == kFP64 && po == kFP64) launch_l2l_t<double, double>(P, l, R, st);
-        else if (pi == kFP64) launch_l2l_t<double, float>(P, l, R, st);
-        else launch_l2l_t<float, float>(P, l, R, st);
-    }
+    for (int l = lf - 1; l >= 2; --l) run_l2l_t(P, l, R, st);
     mark(4);
     // transposed M2L: the opposite transfer vectors
-    for (int l = 2; l <= lf; ++l) {
-        if (P->lev[l].prec == kFP64) launch_m2l<double>(P, l, R, st, true);
-        else launch_m2l<float>(P, l, R, st, true);
-    }
+    for (int l = 2; l <= lf; ++l) run_m2l(P, l, R, st, true);
     mark(5);
     // transposed M2M, level 2 down to the leaf level, added to the M2L part
-    for (int l = 3; l <= lf; ++l) {
-        const int pi = P->lev[l - 1].prec, po = P->lev[l].prec;
-        if (pi == kFP64 && po == kFP64) launch_m2m_t<double, double>(P, l, R, st);
-        else if (po == kFP64) launch_m2m_t<float, double>(P, l, R, st);
-        else launch_m2m_t<float, float>(P, l, R, st);
-    }
+    for (int l = 3; l <= lf; ++l) run_m2m_t(P, l, R, st);
     mark(6);
 }
 
@@ -736,11 +794,12 @@ hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_d
         k_permute_in<double, false><<<nblk(hp.ns * R, 256), 256, 0, st>>>((const cxd*)q, hp.ns, R, P->src_perm, P->qs);
     mark(1);
     const int nleaf = (int)hp.levels[lf].nbox();
+    const dim3 g_fwd(nleaf, nblk(P->max_tgt_leaf, kP2PThreads));
     if (hp.precision == HFMM_PREC_MIXED)
-        k_p2p_mixed<<<nleaf, kP2PThreads, 0, st>>>(nleaf, P->tstart, P->tcount, P->sstart, P->scount, P->noff,
+        k_p2p_mixed<<<g_fwd, kP2PThreads, 0, st>>>(nleaf, P->tstart, P->tcount, P->sstart, P->scount, P->noff,
                                                    P->nidx, P->mixed, P->qs, P->phis, R);
     else
-        k_p2p_fp64<<<nleaf, kP2PThreads, 0, st>>>(nleaf, P->tstart, P->tcount, P->sstart, P->scount, P->noff,
+        k_p2p_fp64<<<g_fwd, kP2PThreads, 0, st>>>(nleaf, P->tstart, P->tcount, P->sstart, P->scount, P->noff,
                                                   P->nidx, P->tx, P->ty, P->tz, P->sx, P->sy, P->sz, P->qs,
                                                   P->phis, R, hp.kappa);
     mark(2);
@@ -748,24 +807,11 @@ hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_d
         if (P->lev[lf].prec == kFP64) launch_s2m<double>(P, R, st);
         else launch_s2m<float>(P, R, st);
         mark(3);
-        for (int l = lf; l >= 3; --l) {
-            const int pi = P->lev[l].prec, po = P->lev[l - 1].prec;
-            if (pi == kFP64 && po == kFP64) launch_up<double, double>(P, l, R, st);
-            else if (pi == kFP64) launch_up<double, float>(P, l, R, st);
-            else launch_up<float, float>(P, l, R, st);
-        }
+        for (int l = lf; l >= 3; --l) run_up(P, l, R, st);
         mark(4);
-        for (int l = 2; l <= lf; ++l) {
-            if (P->lev[l].prec == kFP64) launch_m2l<double>(P, l, R, st);
-            else launch_m2l<float>(P, l, R, st);
-        }
+        for (int l = 2; l <= lf; ++l) run_m2l(P, l, R, st, false);
         mark(5);
-        for (int l = 2; l < lf; ++l) {
-            const int pi = P->lev[l].prec, po = P->lev[l + 1].prec;
-            if (pi == kFP64 && po == kFP64) launch_down<double, double>(P, l, R, st);
-            else if (po == kFP64) launch_down<float, double>(P, l, R, st);
-            else launch_down<float, float>(P, l, R, st);
-        }
+        for (int l = 2; l < lf; ++l) run_down(P, l, R, st);
         mark(6);
         if (P->lev[lf].prec == kFP64) launch_l2t<double>(P, R, st);
         else launch_l2t<float>(P, R, st);
@@ -806,14 +852,15 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t P, const void* w, void* out, int nrhs
     mark(1);
     // transposed near field: source boxes gather the targets of their neighbours
     const int nleaf = (int)hp.levels[lf].nbox();
+    const dim3 g_adj(nleaf, nblk(P->max_src_leaf, kP2PThreads));
     if (hp.precision == HFMM_PREC_MIXED) {
         P2PMixedArgs a = P->mixed;
         std::swap(a.tpt, a.spt);
         std::swap(a.tof, a.sof);
-        k_p2p_mixed<<<nleaf, kP2PThreads, 0, st>>>(nleaf, P->sstart, P->scount, P->tstart, P->tcount, P->noff,
+        k_p2p_mixed<<<g_adj, kP2PThreads, 0, st>>>(nleaf, P->sstart, P->scount, P->tstart, P->tcount, P->noff,
                                                    P->nidx, a, P->phis, P->qs, R);
     } else {
-        k_p2p_fp64<<<nleaf, kP2PThreads, 0, st>>>(nleaf, P->sstart, P->scount, P->tstart, P->tcount, P->noff,
+        k_p2p_fp64<<<g_adj, kP2PThreads, 0, st>>>(nleaf, P->sstart, P->scount, P->tstart, P->tcount, P->noff,
                                                   P->nidx, P->sx, P->sy, P->sz, P->tx, P->ty, P->tz, P->phis,
                                                   P->qs, R, hp.kappa);
     }
@@ -861,19 +908,24 @@ hfmm_status hfmm_grad_sources(hfmm_plan_t P, const void* q, const void* g, doubl
     }
     mark(1);
     const int nleaf = (int)hp.levels[lf].nbox();
-    k_grad_near<<<nleaf, kP2PThreads, 0, st>>>(nleaf, P->sstart, P->scount, P->tstart, P->tcount, P->noff, P->nidx,
+    k_grad_near<<<dim3(nleaf, nblk(P->max_src_leaf, kP2PThreads)), kP2PThreads, 0, st>>>(nleaf, P->sstart, P->scount, P->tstart, P->tcount, P->noff, P->nidx,
                                                P->sx, P->sy, P->sz, P->tx, P->ty, P->tz, P->qs, P->phis, R,
                                                hp.kappa, P->gsort);
     mark(2);
     if (lf >= 2) {
         transposed_far_chain(P, R, st, mark);
         DevLevel& d = P->lev[lf];
-        if (d.prec == kFP64)
-            k_grad_far<double><<<d.nbox, kL2TThreads, 0, st>>>(d.bv, d.qv, P->sstart, P->scount, P->sx, P->sy, P->sz,
-                                                               (const cxd*)d.M, P->qs, R, hp.kappa, P->gsort);
+        const dim3 gg(d.nbox, nblk(P->max_src_leaf, kL2TThreads));
+        const int sc = store_code(P, lf);
+        if (sc == 1)
+            k_grad_far<double, double><<<gg, kL2TThreads, 0, st>>>(d.bv, d.qv, P->sstart, P->scount, P->sx, P->sy,
+                                                                   P->sz, (const cxd*)d.M, P->qs, R, hp.kappa, P->gsort);
+        else if (sc == 2)
+            k_grad_far<df, double><<<gg, kL2TThreads, 0, st>>>(d.bv, d.qv, P->sstart, P->scount, P->sx, P->sy,
+                                                               P->sz, (const cx<df>*)d.M, P->qs, R, hp.kappa, P->gsort);
         else
-            k_grad_far<float><<<d.nbox, kL2TThreads, 0, st>>>(d.bv, d.qv, P->sstart, P->scount, P->sx, P->sy, P->sz,
-                                                              (const cxf*)d.M, P->qs, R, hp.kappa, P->gsort);
+            k_grad_far<float, float><<<gg, kL2TThreads, 0, st>>>(d.bv, d.qv, P->sstart, P->scount, P->sx, P->sy,
+                                                                 P->sz, (const cxf*)d.M, P->qs, R, hp.kappa, P->gsort);
         mark(7);
     } else {
         for (int i = 3; i <= 7; ++i) mark(i);

@@ -42,6 +42,9 @@ __host__ __device__ __forceinline__ void mac(cx<R>& a, cx<R> b, cx<R> c) {
 }
 template <typename To, typename Ti>
 __host__ __device__ __forceinline__ cx<To> cvt(cx<Ti> a) { return mk<To>((To)a.x, (To)a.y); }
+// real scalar of type R from a double (works for float, double and double-float)
+template <typename R>
+__host__ __device__ __forceinline__ R rval(double v) { return (R)v; }
 
 using cxd = cx<double>;
 using cxf = cx<float>;

@@ -13,6 +13,11 @@ namespace hfmm {
 
 struct df {
     float hi, lo;
+    df() = default;
+    __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ explicit df(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+    __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+    __host__ __device__ explicit operator float() const { return hi + lo; }
 };
 
 __device__ __forceinline__ df df_two_sum(float a, float b) {
@@ -55,6 +60,14 @@ __host__ __device__ __forceinline__ double df_to_double(df a) { return (double)a
 struct cdf {
     df x, y;
 };
+
+// arithmetic operators so that complex and FFT templates instantiate for df
+__device__ __forceinline__ df operator+(df a, df b) { return df_add(a, b); }
+__device__ __forceinline__ df operator-(df a, df b) { return df_sub(a, b); }
+__device__ __forceinline__ df operator-(df a) { return df_neg(a); }
+__device__ __forceinline__ df operator*(df a, df b) { return df_mul(a, b); }
+__device__ __forceinline__ df& operator+=(df& a, df b) { a = df_add(a, b); return a; }
+__device__ __forceinline__ df& operator-=(df& a, df b) { a = df_sub(a, b); return a; }
 __device__ __forceinline__ cdf cdf_mul(cdf a, cdf b) {
     return {df_sub(df_mul(a.x, b.x), df_mul(a.y, b.y)), df_add(df_mul(a.x, b.y), df_mul(a.y, b.x))};
 }

@@ -8,6 +8,7 @@
 // from a per-length table.
 #pragma once
 #include "cx.cuh"
+#include "df.cuh"
 
 namespace hfmm {
 
@@ -30,18 +31,18 @@ __device__ __forceinline__ void dft_small(cx<R>* v, int radix, bool inv) {
         v[1] = t1 + t3;
         v[3] = t1 - t3;
     } else if (radix == 3) {
-        const R h = (R)0.86602540378443864676;  // sqrt(3)/2
+        const R h = rval<R>(0.86602540378443864676);  // sqrt(3)/2
         cx<R> s = v[1] + v[2], d = v[1] - v[2];
-        cx<R> m = v[0] - (R)0.5 * s;
+        cx<R> m = v[0] - rval<R>(0.5) * s;
         cx<R> rot = inv ? mul_pi(h * d) : mul_mi(h * d);
         v[0] = v[0] + s;
         v[1] = m + rot;
         v[2] = m - rot;
     } else {  // radix 5
-        const R c1 = (R)0.30901699437494742410;   // cos(2 pi / 5)
-        const R c2 = (R)-0.80901699437494742410;  // cos(4 pi / 5)
-        const R s1 = (R)0.95105651629515357212;   // sin(2 pi / 5)
-        const R s2 = (R)0.58778525229247312917;   // sin(4 pi / 5)
+        const R c1 = rval<R>(0.30901699437494742410);   // cos(2 pi / 5)
+        const R c2 = rval<R>(-0.80901699437494742410);  // cos(4 pi / 5)
+        const R s1 = rval<R>(0.95105651629515357212);   // sin(2 pi / 5)
+        const R s2 = rval<R>(0.58778525229247312917);   // sin(4 pi / 5)
         cx<R> a1 = v[1] + v[4], b1 = v[1] - v[4], a2 = v[2] + v[3], b2 = v[2] - v[3];
         cx<R> p1 = v[0] + c1 * a1 + c2 * a2;
         cx<R> p2 = v[0] + c2 * a1 + c1 * a2;
@@ -106,10 +107,10 @@ __device__ cx<R>* warp_resample(cx<R>* a, cx<R>* b, int n, int np, const Twiddle
     cx<R>* s = warp_fft(a, b, n, false, pool + tv.off[n], lane);
     cx<R>* o = (s == a) ? b : a;
     const int band = min((n + 1) / 2, (np + 1) / 2) - 1;
-    const R scale = (R)1 / (R)n;
+    const R scale = rval<R>(1.0 / (double)n);
     for (int j = lane; j < np; j += 32) {
         int f = (2 * j <= np) ? j : j - np;
-        cx<R> v = mk<R>(0, 0);
+        cx<R> v = mk<R>(rval<R>(0.0), rval<R>(0.0));
         if (f <= band && f >= -band) v = scale * s[(f + n) % n];
         o[j] = v;
     }

@@ -72,9 +72,11 @@ __global__ void k_p2p_fp64(int nbox, const int32_t* __restrict__ tstart, const i
     const int b = blockIdx.x;
     if (b >= nbox) return;
     const int t0 = tstart[b], tc = tcount[b];
+    if ((int)blockIdx.y * kP2PThreads >= tc) return;
     for (int r0 = 0; r0 < R; r0 += 4) {
         const int rn = min(4, R - r0);
-        for (int tb = 0; tb < tc; tb += kP2PThreads) {
+        {
+            const int tb = blockIdx.y * kP2PThreads;
             const int ti = tb + threadIdx.x;
             const bool active = ti < tc;
             double x = 0, y = 0, z = 0;
@@ -145,10 +147,12 @@ __global__ void k_p2p_mixed(int nbox, const int32_t* __restrict__ tstart, const 
     const int b = blockIdx.x;
     if (b >= nbox) return;
     const int t0 = tstart[b], tc = tcount[b];
+    if ((int)blockIdx.y * kP2PThreads >= tc) return;
     const float two_pi = 6.28318530717958647692f;
     for (int r0 = 0; r0 < R; r0 += 4) {
         const int rn = min(4, R - r0);
-        for (int tb = 0; tb < tc; tb += kP2PThreads) {
+        {
+            const int tb = blockIdx.y * kP2PThreads;
             const int ti = tb + threadIdx.x;
             const bool active = ti < tc;
             float4 gp = make_float4(0, 0, 0, 0), op = gp;
@@ -306,11 +310,12 @@ __global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstar
     __shared__ cx<R> shl[kL2TThreads];
     const int b = blockIdx.x;
     const int t0 = tstart[b], tc = tcount[b];
-    if (tc == 0) return;
+    if ((int)blockIdx.y * kL2TThreads >= tc) return;
     const double cxx = bx.center[3 * b], cyy = bx.center[3 * b + 1], czz = bx.center[3 * b + 2];
     for (int r = 0; r < R_; ++r) {
         const cx<R>* Lb = L + ((int64_t)b * R_ + r) * qv.K;
-        for (int tb = 0; tb < tc; tb += kL2TThreads) {
+        {
+            const int tb = blockIdx.y * kL2TThreads;
             const int ti = tb + threadIdx.x;
             const bool active = ti < tc;
             double dx = 0, dy = 0, dz = 0;
@@ -365,7 +370,7 @@ __global__ void k_s2m_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ss
                          const int32_t* __restrict__ scount, const double* __restrict__ sx,
                          const double* __restrict__ sy, const double* __restrict__ sz,
                          const cxd* __restrict__ qs, int R_, double kappa_turns, const cdf* __restrict__ cis_tab,
-                         cxd* __restrict__ M, double sign, const double* __restrict__ wk) {
+                         cx<df>* __restrict__ M, double sign, const double* __restrict__ wk) {
     __shared__ df shd[kS2MThreads * 3];
     __shared__ cdf shq[kS2MThreads];
     __shared__ cdf tab[kCisTable];
@@ -401,9 +406,11 @@ __global__ void k_s2m_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ss
                 }
         }
         if (active) {
-            cxd v = mk<double>(df_to_double(acc.x), df_to_double(acc.y));
-            if (wk) v = wk[k] * v;
-            M[((int64_t)b * R_ + r) * qv.K + k] = v;
+            if (wk) {
+                const df w = df_from_double(wk[k]);
+                acc = cdf{df_mul(acc.x, w), df_mul(acc.y, w)};
+            }
+            M[((int64_t)b * R_ + r) * qv.K + k] = mk<df>(acc.x, acc.y);
         }
     }
 }
@@ -411,7 +418,7 @@ __global__ void k_s2m_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ss
 __global__ void k_l2t_df(BoxView bx, QuadView qv, const int32_t* __restrict__ tstart,
                          const int32_t* __restrict__ tcount, const double* __restrict__ tx,
                          const double* __restrict__ ty, const double* __restrict__ tz,
-                         const cxd* __restrict__ L, int R_, double kappa_turns, const cdf* __restrict__ cis_tab,
+                         const cx<df>* __restrict__ L, int R_, double kappa_turns, const cdf* __restrict__ cis_tab,
                          cxd* __restrict__ phis, double sign, const double* __restrict__ wk) {
     __shared__ df shs[kL2TThreads * 3];
     __shared__ cdf shl[kL2TThreads];
@@ -419,11 +426,12 @@ __global__ void k_l2t_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ts
     load_cis_table(tab, cis_tab);
     const int b = blockIdx.x;
     const int t0 = tstart[b], tc = tcount[b];
-    if (tc == 0) return;
+    if ((int)blockIdx.y * kL2TThreads >= tc) return;
     const double cxx = bx.center[3 * b], cyy = bx.center[3 * b + 1], czz = bx.center[3 * b + 2];
     for (int r = 0; r < R_; ++r) {
-        const cxd* Lb = L + ((int64_t)b * R_ + r) * qv.K;
-        for (int tb = 0; tb < tc; tb += kL2TThreads) {
+        const cx<df>* Lb = L + ((int64_t)b * R_ + r) * qv.K;
+        {
+            const int tb = blockIdx.y * kL2TThreads;
             const int ti = tb + threadIdx.x;
             const bool active = ti < tc;
             df d[3] = {{0, 0}, {0, 0}, {0, 0}};
@@ -439,8 +447,12 @@ __global__ void k_l2t_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ts
                 if (threadIdx.x < kn) {
                     const int64_t k = kb + threadIdx.x;
                     for (int c = 0; c < 3; ++c) shs[3 * threadIdx.x + c] = df_from_double(qv.shat[3 * k + c] * kappa_turns);
-                    const cxd wl = wk ? wk[k] * Lb[k] : Lb[k];
-                    shl[threadIdx.x] = cdf{df_from_double(wl.x), df_from_double(wl.y)};
+                    cdf wl = cdf{Lb[k].x, Lb[k].y};
+                    if (wk) {
+                        const df w = df_from_double(wk[k]);
+                        wl = cdf{df_mul(wl.x, w), df_mul(wl.y, w)};
+                    }
+                    shl[threadIdx.x] = wl;
                 }
                 __syncthreads();
                 if (active)
@@ -468,20 +480,21 @@ __global__ void k_l2t_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ts
 // with Lambda = the transposed far-field chain applied to conj(g) and
 // dG/dy = G (i k - 1/R) (y - x) / R.
 // ---------------------------------------------------------------------------
-template <typename R>
+template <typename S, typename R>
 __global__ void k_grad_far(BoxView bx, QuadView qv, const int32_t* __restrict__ sstart,
                            const int32_t* __restrict__ scount, const double* __restrict__ sx,
                            const double* __restrict__ sy, const double* __restrict__ sz,
-                           const cx<R>* __restrict__ Lam, const cxd* __restrict__ qs, int R_, double kappa,
+                           const cx<S>* __restrict__ Lam, const cxd* __restrict__ qs, int R_, double kappa,
                            double* __restrict__ grad) {
     __shared__ double shs[kL2TThreads * 3];
     __shared__ cx<R> shl[kL2TThreads];
     const int b = blockIdx.x;
     const int s0 = sstart[b], sc = scount[b];
-    if (sc == 0) return;
+    if ((int)blockIdx.y * kL2TThreads >= sc) return;
     const double kt = kappa / (2.0 * 3.14159265358979323846);
     const double cxx = bx.center[3 * b], cyy = bx.center[3 * b + 1], czz = bx.center[3 * b + 2];
-    for (int jb = 0; jb < sc; jb += kL2TThreads) {
+    {
+        const int jb = blockIdx.y * kL2TThreads;
         const int jj = jb + threadIdx.x;
         const bool active = jj < sc;
         double d[3] = {0, 0, 0};
@@ -492,7 +505,7 @@ __global__ void k_grad_far(BoxView bx, QuadView qv, const int32_t* __restrict__ 
         }
         double g[3] = {0, 0, 0};
         for (int r = 0; r < R_; ++r) {
-            const cx<R>* Lb = Lam + ((int64_t)b * R_ + r) * qv.K;
+            const cx<S>* Lb = Lam + ((int64_t)b * R_ + r) * qv.K;
             cxd acc[3] = {mk<double>(0, 0), mk<double>(0, 0), mk<double>(0, 0)};
             for (int64_t kb = 0; kb < qv.K; kb += kL2TThreads) {
                 const int kn = (int)min((int64_t)kL2TThreads, qv.K - kb);
@@ -500,7 +513,7 @@ __global__ void k_grad_far(BoxView bx, QuadView qv, const int32_t* __restrict__ 
                 if (threadIdx.x < kn) {
                     const int64_t k = kb + threadIdx.x;
                     for (int c = 0; c < 3; ++c) shs[3 * threadIdx.x + c] = qv.shat[3 * k + c];
-                    shl[threadIdx.x] = Lb[k];
+                    shl[threadIdx.x] = cvt<R>(Lb[k]);
                 }
                 __syncthreads();
                 if (active)
@@ -540,7 +553,9 @@ __global__ void k_grad_near(int nbox, const int32_t* __restrict__ sstart, const 
     const int b = blockIdx.x;
     if (b >= nbox) return;
     const int s0 = sstart[b], sc = scount[b];
-    for (int jb = 0; jb < sc; jb += kP2PThreads) {
+    if ((int)blockIdx.y * kP2PThreads >= sc) return;
+    {
+        const int jb = blockIdx.y * kP2PThreads;
         const int jj = jb + threadIdx.x;
         const bool active = jj < sc;
         double y0 = 0, y1 = 0, y2 = 0;
@@ -604,23 +619,25 @@ __global__ void k_scatter_grad(const double* __restrict__ gs, int64_t n, const i
 // ---------------------------------------------------------------------------
 // M2L: I_a(s_k) = sum_{b in I(a)} T^{s,LL}_{v(a,b)}(s_k) M_b(s_k); thread per (box, k)
 // ---------------------------------------------------------------------------
-template <typename R>
+// S: storage type of tables and signatures, C: compute type (double-float for float64
+// levels of the mixed policy)
+template <typename S, typename C>
 __global__ void k_m2l(int nbox, int64_t K, const int32_t* __restrict__ ioff, const int32_t* __restrict__ iidx,
                       const int32_t* __restrict__ iv, const int32_t* __restrict__ tslot,
-                      const cx<R>* __restrict__ T, const cx<R>* __restrict__ M, int R_,
-                      cx<R>* __restrict__ I) {
+                      const cx<S>* __restrict__ T, const cx<S>* __restrict__ M, int R_,
+                      cx<S>* __restrict__ I) {
     const int a = blockIdx.x;
     const int64_t k = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
     if (k >= K) return;
     const int l0 = ioff[a], l1 = ioff[a + 1];
     for (int r = 0; r < R_; ++r) {
-        cx<R> acc = mk<R>(0, 0);
+        cx<C> acc = mk<C>(rval<C>(0.0), rval<C>(0.0));
         for (int t = l0; t < l1; ++t) {
             const int b = iidx[t];
-            const cx<R> tv = T[(int64_t)tslot[iv[t]] * K + k];
-            mac(acc, tv, M[((int64_t)b * R_ + r) * K + k]);
+            const cx<C> tv = cvt<C>(T[(int64_t)tslot[iv[t]] * K + k]);
+            acc = acc + tv * cvt<C>(M[((int64_t)b * R_ + r) * K + k]);
         }
-        I[((int64_t)a * R_ + r) * K + k] = acc;
+        I[((int64_t)a * R_ + r) * K + k] = cvt<S>(acc);
     }
 }
 
@@ -680,7 +697,7 @@ __global__ void k_requad_rows_a(RequadArgs ra, int nbox_seq, int R_, const cx<Ti
     }
     __syncwarp();
     cx<Tc>* res = warp_resample(buf0, buf1, len, ra.big, ra.tw, lane);
-    const Tc sc = kT ? (Tc)len / (Tc)ra.big : (Tc)1;   // transposed: (length in) / (length out)
+    const Tc sc = rval<Tc>(kT ? (double)len / (double)ra.big : 1.0);   // transposed: (length in) / (length out)
     cx<Tc>* dst = GA + seq * ra.big;
     for (int j = lane; j < ra.big; j += 32) dst[j] = kT ? sc * res[j] : res[j];
 }
@@ -707,7 +724,7 @@ __global__ void k_requad_cols(RequadArgs ra, int nbox_seq, int R_, const cx<Tc>*
         if (!kT) {
             buf0[t] = (t <= ha) ? ga[(int64_t)t * ra.big + m] : ga[(int64_t)(nta - t) * ra.big + m + hb];
         } else {
-            cx<Tc> v = mk<Tc>(0, 0);
+            cx<Tc> v = mk<Tc>(rval<Tc>(0.0), rval<Tc>(0.0));
             if (t <= ha) v = ga[(int64_t)t * ra.big + m];
             if (t == 0 || t >= ha) v = v + ga[(int64_t)((nta - t) % nta) * ra.big + m + hb];
             buf0[t] = v;
@@ -715,7 +732,7 @@ __global__ void k_requad_cols(RequadArgs ra, int nbox_seq, int R_, const cx<Tc>*
     }
     __syncwarp();
     cx<Tc>* res = warp_resample(buf0, buf1, nta, ntb, ra.tw, lane);
-    const Tc sc = (Tc)nta / (Tc)ntb;
+    const Tc sc = rval<Tc>((double)nta / (double)ntb);
     cx<Tc>* gb = GB + br * (int64_t)ra.qb.nrows * ra.big;
     for (int n = lane; n <= hbr; n += 32) {
         if (!kT) {
@@ -723,16 +740,16 @@ __global__ void k_requad_cols(RequadArgs ra, int nbox_seq, int R_, const cx<Tc>*
             gb[(int64_t)n * ra.big + m + hb] = res[(ntb - n) % ntb];
         } else {
             gb[(int64_t)n * ra.big + m] = sc * res[n];
-            gb[(int64_t)n * ra.big + m + hb] = (n > 0 && n < hbr) ? sc * res[ntb - n] : mk<Tc>(0, 0);
+            gb[(int64_t)n * ra.big + m + hb] = (n > 0 && n < hbr) ? sc * res[ntb - n] : mk<Tc>(rval<Tc>(0.0), rval<Tc>(0.0));
         }
     }
 }
 
 // Pass C, adding into the output in place.  Sequence = (box, r, n').
 //   L2L: L_child = anterp(...) + I_child;  transposed M2M: Lambda_M(child) += ...
-template <typename Tc, bool kT>
+template <typename Tc, typename Tout, bool kT>
 __global__ void k_requad_rows_c_l2l(RequadArgs ra, int nbox_seq, int R_, const cx<Tc>* __restrict__ GB,
-                                    cx<Tc>* __restrict__ IL) {
+                                    cx<Tout>* __restrict__ IL) {
     extern __shared__ unsigned char smem_raw[];
     cx<Tc>* sm = reinterpret_cast<cx<Tc>*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -749,9 +766,9 @@ __global__ void k_requad_rows_c_l2l(RequadArgs ra, int nbox_seq, int R_, const c
     __syncwarp();
     const int len = ra.qb.nphi[n];
     cx<Tc>* res = warp_resample(buf0, buf1, ra.big, len, ra.tw, lane);
-    const Tc sc = kT ? (Tc)ra.big / (Tc)len : (Tc)1;
-    cx<Tc>* dst = IL + br * ra.qb.K + ra.qb.off[n];
-    for (int j = lane; j < len; j += 32) dst[j] = dst[j] + (kT ? sc * res[j] : res[j]);
+    const Tc sc = rval<Tc>(kT ? (double)ra.big / (double)len : 1.0);
+    cx<Tout>* dst = IL + br * ra.qb.K + ra.qb.off[n];
+    for (int j = lane; j < len; j += 32) dst[j] = cvt<Tout>(cvt<Tc>(dst[j]) + (kT ? sc * res[j] : res[j]));
 }
 
 // Pass C summing children, overwriting the parent.  Sequence = (parent, r, n').
@@ -779,7 +796,7 @@ __global__ void k_requad_rows_c_m2m(RequadArgs ra, int nparent, int R_, const in
     // each lane owns outputs j = lane, lane + 32, ...: accumulate across children in registers
     constexpr int kMaxPerLane = 32;   // len <= 1024
     cx<Tc> acc[kMaxPerLane];
-    for (int i = 0; i < kMaxPerLane; ++i) acc[i] = mk<Tc>(0, 0);
+    for (int i = 0; i < kMaxPerLane; ++i) acc[i] = mk<Tc>(rval<Tc>(0.0), rval<Tc>(0.0));
     const int c0 = child_start[p], cn = child_count[p];
     for (int c = c0; c < c0 + cn; ++c) {
         const cx<Tc>* row = GB + (((int64_t)c * R_ + r) * rows + n) * ra.big;
@@ -787,7 +804,7 @@ __global__ void k_requad_rows_c_m2m(RequadArgs ra, int nparent, int R_, const in
         __syncwarp();
         cx<Tc>* res = warp_resample(buf0, buf1, ra.big, len, ra.tw, lane);
         const cx<Tc>* sh = shift + (int64_t)octant[c] * ra.qb.K + o;
-        const Tc sc = kT ? (Tc)ra.big / (Tc)len : (Tc)1;
+        const Tc sc = rval<Tc>(kT ? (double)ra.big / (double)len : 1.0);
         for (int i = 0, j = lane; j < len; ++i, j += 32) {
             cx<Tc> v = kT ? sc * res[j] : res[j];
             acc[i] = acc[i] + v * (kShift == kShiftConj ? conj(sh[j]) : sh[j]);
