@@ -36,6 +36,12 @@ __device__ __forceinline__ df df_add(df a, df b) {
     float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
     return df_fast_sum(s.hi, e);
 }
+// a + b when |a| >= |b| (Dekker's Fast2Sum on the leading parts)
+__device__ __forceinline__ df df_add_big(df a, df b) {
+    float s = __fadd_rn(a.hi, b.hi);
+    float e = __fadd_rn(__fsub_rn(b.hi, __fsub_rn(s, a.hi)), __fadd_rn(a.lo, b.lo));
+    return df_fast_sum(s, e);
+}
 __device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
 __device__ __forceinline__ df df_mul(df a, df b) {
@@ -88,17 +94,18 @@ __device__ __forceinline__ cdf cis_turns(df r, const cdf* tab) {
     const df c24 = {0.0416666679084301f, -1.2417634698280722e-09f};     // 1/24
     const df c6 = {0.1666666716337204f, -4.967053879312289e-09f};       // 1/6
     const df c120 = {0.008333333767950535f, -4.34617203337595e-10f};   // 1/120
-    df cc = df_add(c24, {__fmul_rn(yh, -1.0f / 720.0f), 0.0f});
+    // every addition below has a dominant left operand (|y| <= 1.6e-4): Fast2Sum suffices
+    df cc = df_add_big(c24, {__fmul_rn(yh, -1.0f / 720.0f), 0.0f});
     cc = df_mul(y, cc);
-    cc = df_add({-0.5f, 0.0f}, cc);
+    cc = df_add_big({-0.5f, 0.0f}, cc);
     cc = df_mul(y, cc);
-    cc = df_add({1.0f, 0.0f}, cc);
-    df ss = df_add(c120, {__fmul_rn(yh, -1.0f / 5040.0f), 0.0f});
+    cc = df_add_big({1.0f, 0.0f}, cc);
+    df ss = df_add_big(c120, {__fmul_rn(yh, -1.0f / 5040.0f), 0.0f});
     ss = df_mul(y, ss);
-    ss = df_sub(ss, c6);
+    ss = df_add_big(df_neg(c6), ss);
     ss = df_mul(y, ss);
     ss = df_mul(x, ss);
-    ss = df_add(x, ss);
+    ss = df_add_big(x, ss);
     const int j = ((int)jf) & (kCisTable - 1);
     return cdf_mul(tab[j], cdf{cc, ss});
 }

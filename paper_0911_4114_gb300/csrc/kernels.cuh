@@ -59,6 +59,7 @@ __global__ void k_permute_out(const cxd* __restrict__ phis, int64_t n, int R,
 // one CTA per target leaf box, sources staged through shared memory
 // ---------------------------------------------------------------------------
 constexpr int kP2PThreads = 128;
+constexpr int kP2PTile = 128;      // sources staged per barrier (mixed near field): one float32 tile sum
 
 __global__ void k_p2p_fp64(int nbox, const int32_t* __restrict__ tstart, const int32_t* __restrict__ tcount,
                            const int32_t* __restrict__ sstart, const int32_t* __restrict__ scount,
@@ -142,8 +143,8 @@ __global__ void k_p2p_mixed(int nbox, const int32_t* __restrict__ tstart, const 
                             const int32_t* __restrict__ sstart, const int32_t* __restrict__ scount,
                             const int32_t* __restrict__ noff, const int32_t* __restrict__ nidx,
                             P2PMixedArgs a, const cxd* __restrict__ qs, cxd* __restrict__ phis, int R) {
-    __shared__ float4 shp[kP2PThreads], sho[kP2PThreads];
-    __shared__ cxf shq[kP2PThreads * 4];
+    __shared__ float4 shp[kP2PTile], sho[kP2PTile];
+    __shared__ cxf shq[kP2PTile * 4];
     const int b = blockIdx.x;
     if (b >= nbox) return;
     const int t0 = tstart[b], tc = tcount[b];
@@ -165,15 +166,14 @@ __global__ void k_p2p_mixed(int nbox, const int32_t* __restrict__ tstart, const 
             for (int nb = noff[b]; nb < noff[b + 1]; ++nb) {
                 const int s = nidx[nb];
                 const int s0 = sstart[s], sc = scount[s];
-                for (int sb = 0; sb < sc; sb += kP2PThreads) {
-                    const int sn = min(kP2PThreads, sc - sb);
+                for (int sb = 0; sb < sc; sb += kP2PTile) {
+                    const int sn = min(kP2PTile, sc - sb);
                     __syncthreads();
-                    if (threadIdx.x < sn) {
-                        const int j = s0 + sb + threadIdx.x;
-                        shp[threadIdx.x] = a.spt[j];
-                        sho[threadIdx.x] = a.sof[j];
-                        for (int r = 0; r < rn; ++r)
-                            shq[threadIdx.x * 4 + r] = cvt<float>(qs[(int64_t)j * R + r0 + r]);
+                    for (int u = threadIdx.x; u < sn; u += kP2PThreads) {
+                        const int j = s0 + sb + u;
+                        shp[u] = a.spt[j];
+                        sho[u] = a.sof[j];
+                        for (int r = 0; r < rn; ++r) shq[u * 4 + r] = cvt<float>(qs[(int64_t)j * R + r0 + r]);
                     }
                     __syncthreads();
                     if (active) {
@@ -223,6 +223,7 @@ __global__ void k_p2p_mixed(int nbox, const int32_t* __restrict__ tstart, const 
 // thread per (box, k); sources of the box staged through shared memory
 // ---------------------------------------------------------------------------
 constexpr int kS2MThreads = 128;
+constexpr int kS2MTile = 256;      // sources staged per barrier (double-float S2M)
 
 template <typename R>
 __device__ __forceinline__ cx<R> plane_wave(double phase_turns_reduced);
@@ -297,6 +298,7 @@ __global__ void k_s2m(BoxView bx, QuadView qv, const int32_t* __restrict__ sstar
 // L2T: phi_i += sum_k w_k L_b(s_k) exp(i k s_k . (c_b - x_i)); thread per target
 // ---------------------------------------------------------------------------
 constexpr int kL2TThreads = 128;
+constexpr int kL2TTile = 512;      // quadrature samples staged per barrier
 
 // Signature to points: phi_i += sum_k w_k L_b(s_k) exp(i k s_k . sign (c_b - p_i)).
 // L2T: targets, sign +1, quadrature weights.  Transposed S2M: sources, sign -1, no weights.
@@ -371,8 +373,8 @@ __global__ void k_s2m_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ss
                          const double* __restrict__ sy, const double* __restrict__ sz,
                          const cxd* __restrict__ qs, int R_, double kappa_turns, const cdf* __restrict__ cis_tab,
                          cx<df>* __restrict__ M, double sign, const double* __restrict__ wk) {
-    __shared__ df shd[kS2MThreads * 3];
-    __shared__ cdf shq[kS2MThreads];
+    __shared__ df shd[kS2MTile * 3];
+    __shared__ cdf shq[kS2MTile];
     __shared__ cdf tab[kCisTable];
     load_cis_table(tab, cis_tab);
     const int b = blockIdx.x;
@@ -385,16 +387,16 @@ __global__ void k_s2m_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ss
     const double cxx = bx.center[3 * b], cyy = bx.center[3 * b + 1], czz = bx.center[3 * b + 2];
     for (int r = 0; r < R_; ++r) {
         cdf acc = {{0, 0}, {0, 0}};
-        for (int jb = 0; jb < sc; jb += kS2MThreads) {
-            const int jn = min(kS2MThreads, sc - jb);
+        for (int jb = 0; jb < sc; jb += kS2MTile) {
+            const int jn = min(kS2MTile, sc - jb);
             __syncthreads();
-            if (threadIdx.x < jn) {
-                const int j = s0 + jb + threadIdx.x;
-                shd[3 * threadIdx.x] = df_from_double(sign * (sx[j] - cxx));
-                shd[3 * threadIdx.x + 1] = df_from_double(sign * (sy[j] - cyy));
-                shd[3 * threadIdx.x + 2] = df_from_double(sign * (sz[j] - czz));
+            for (int u = threadIdx.x; u < jn; u += kS2MThreads) {
+                const int j = s0 + jb + u;
+                shd[3 * u] = df_from_double(sign * (sx[j] - cxx));
+                shd[3 * u + 1] = df_from_double(sign * (sy[j] - cyy));
+                shd[3 * u + 2] = df_from_double(sign * (sz[j] - czz));
                 const cxd qq = qs[(int64_t)j * R_ + r];
-                shq[threadIdx.x] = cdf{df_from_double(qq.x), df_from_double(qq.y)};
+                shq[u] = cdf{df_from_double(qq.x), df_from_double(qq.y)};
             }
             __syncthreads();
             if (active)
@@ -420,8 +422,8 @@ __global__ void k_l2t_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ts
                          const double* __restrict__ ty, const double* __restrict__ tz,
                          const cx<df>* __restrict__ L, int R_, double kappa_turns, const cdf* __restrict__ cis_tab,
                          cxd* __restrict__ phis, double sign, const double* __restrict__ wk) {
-    __shared__ df shs[kL2TThreads * 3];
-    __shared__ cdf shl[kL2TThreads];
+    __shared__ df shs[kL2TTile * 3];
+    __shared__ cdf shl[kL2TTile];
     __shared__ cdf tab[kCisTable];
     load_cis_table(tab, cis_tab);
     const int b = blockIdx.x;
@@ -441,18 +443,18 @@ __global__ void k_l2t_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ts
                 d[2] = df_from_double(sign * (czz - tz[t0 + ti]));
             }
             cdf acc = {{0, 0}, {0, 0}};
-            for (int64_t kb = 0; kb < qv.K; kb += kL2TThreads) {
-                const int kn = (int)min((int64_t)kL2TThreads, qv.K - kb);
+            for (int64_t kb = 0; kb < qv.K; kb += kL2TTile) {
+                const int kn = (int)min((int64_t)kL2TTile, qv.K - kb);
                 __syncthreads();
-                if (threadIdx.x < kn) {
-                    const int64_t k = kb + threadIdx.x;
-                    for (int c = 0; c < 3; ++c) shs[3 * threadIdx.x + c] = df_from_double(qv.shat[3 * k + c] * kappa_turns);
+                for (int u = threadIdx.x; u < kn; u += kL2TThreads) {
+                    const int64_t k = kb + u;
+                    for (int c = 0; c < 3; ++c) shs[3 * u + c] = df_from_double(qv.shat[3 * k + c] * kappa_turns);
                     cdf wl = cdf{Lb[k].x, Lb[k].y};
                     if (wk) {
                         const df w = df_from_double(wk[k]);
                         wl = cdf{df_mul(wl.x, w), df_mul(wl.y, w)};
                     }
-                    shl[threadIdx.x] = wl;
+                    shl[u] = wl;
                 }
                 __syncthreads();
                 if (active)
