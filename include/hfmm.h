@@ -154,6 +154,39 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t plan, const void* w, void* out, int n
 hfmm_status hfmm_grad_sources(hfmm_plan_t plan, const void* q, const void* g, double* grad, int nrhs,
                               hfmm_dtype dtype, void* stream);
 
+/* Many independent problems applied by one graph launch (batching of uneven problems).
+ * Each problem has its own sources, targets, kappa and eps; all share the options. */
+typedef struct hfmm_batch_s* hfmm_batch_t;
+typedef struct {
+    const double* sources;  /* host (ns, 3) float64 */
+    int64_t ns;
+    const double* targets;  /* host (nt, 3) float64, may alias sources */
+    int64_t nt;
+    double kappa;
+    double eps;
+} hfmm_problem;
+
+/* Plans every problem as hfmm_plan does (the options apply to all of them).  Errors as
+ * hfmm_plan; on error nothing is left allocated. */
+hfmm_status hfmm_plan_batch(int nprob, const hfmm_problem* problems, const hfmm_options* opt,
+                            hfmm_batch_t* out);
+
+/* Applies problem p to q[p] -> phi[p] for every p with ONE cudaGraphLaunch on `stream`.
+ * q, phi: host arrays of nprob device pointers ((ns_p, nrhs) and (nt_p, nrhs) complex of
+ * dtype).  The graph (every problem's stage kernels, problems spread over concurrent
+ * branches) is captured on the first call for a given set of pointers, nrhs and dtype and
+ * replayed afterwards; a call with different pointers re-captures.  The first call also
+ * runs each problem once outside the graph, on `stream`.  Concurrent calls on one batch
+ * are not allowed.  Errors: HFMM_ERR_ARG, HFMM_ERR_STATE, HFMM_ERR_CUDA. */
+hfmm_status hfmm_apply_batch(hfmm_batch_t batch, const void* const* q, void* const* phi, int nrhs,
+                             hfmm_dtype dtype, void* stream);
+
+/* Number of problems and the plan of problem p (owned by the batch; do not destroy it). */
+hfmm_status hfmm_batch_plan(hfmm_batch_t batch, int p, hfmm_plan_t* plan);
+
+/* Releases every plan and the cached graph.  NULL is accepted. */
+hfmm_status hfmm_batch_destroy(hfmm_batch_t batch);
+
 /* Plan summary and the per-stage times of the last timed apply.  Errors: HFMM_ERR_ARG. */
 hfmm_status hfmm_query(hfmm_plan_t plan, hfmm_info* info);
 

@@ -21,7 +21,8 @@ GET = dict(BOX_IDX=0, BOX_PARENT=1, ILIST_OFF=2, ILIST_IDX=3, ILIST_V=4, NLIST_O
            SRC_PERM=7, TGT_PERM=8, NPHI=9, TABLE=10, LEAF_SRC=11, LEAF_TGT=12)
 
 EXPORTS = ("hfmm_default_options", "hfmm_plan", "hfmm_apply", "hfmm_query", "hfmm_set_timing",
-           "hfmm_destroy", "hfmm_last_error", "hfmm_debug_get", "hfmm_direct_noalloc", "hfmm_apply_adjoint", "hfmm_grad_sources")
+           "hfmm_destroy", "hfmm_last_error", "hfmm_debug_get", "hfmm_direct_noalloc", "hfmm_apply_adjoint", "hfmm_grad_sources", "hfmm_plan_batch",
+           "hfmm_apply_batch", "hfmm_batch_plan", "hfmm_batch_destroy")
 NOALLOC_MAX_POINTS = 1 << 19
 
 
@@ -30,6 +31,11 @@ class Options(ctypes.Structure):
                 ("max_leaf", ctypes.c_int), ("depth", ctypes.c_int), ("has_root", ctypes.c_int),
                 ("root", ctypes.c_double * 4), ("precision", ctypes.c_int), ("max_rhs", ctypes.c_int),
                 ("device", ctypes.c_int)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("sources", ctypes.c_void_p), ("ns", ctypes.c_int64), ("targets", ctypes.c_void_p),
+                ("nt", ctypes.c_int64), ("kappa", ctypes.c_double), ("eps", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -66,6 +72,14 @@ def lib():
     L.hfmm_apply_adjoint.restype = ctypes.c_int
     L.hfmm_grad_sources.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
     L.hfmm_grad_sources.restype = ctypes.c_int
+    L.hfmm_plan_batch.argtypes = [ctypes.c_int, ctypes.POINTER(Problem), ctypes.POINTER(Options), ctypes.POINTER(vp)]
+    L.hfmm_plan_batch.restype = ctypes.c_int
+    L.hfmm_apply_batch.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, vp]
+    L.hfmm_apply_batch.restype = ctypes.c_int
+    L.hfmm_batch_plan.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp)]
+    L.hfmm_batch_plan.restype = ctypes.c_int
+    L.hfmm_batch_destroy.argtypes = [vp]
+    L.hfmm_batch_destroy.restype = ctypes.c_int
     L.hfmm_query.argtypes = [vp, ctypes.POINTER(Info)]
     L.hfmm_query.restype = ctypes.c_int
     L.hfmm_set_timing.argtypes = [vp, ctypes.c_int]

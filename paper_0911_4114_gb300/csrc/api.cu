@@ -973,6 +973,138 @@ hfmm_status hfmm_query(hfmm_plan_t P, hfmm_info* info) {
     return HFMM_OK;
 }
 
+}  // extern "C"
+
+struct hfmm_batch_s {
+    std::vector<hfmm_plan_t> plans;
+    int device = 0;
+    static constexpr int kBranches = 8;
+    cudaStream_t cap = nullptr;                 // capture origin
+    cudaStream_t br[kBranches] = {};            // concurrent branches inside the graph
+    cudaEvent_t fork = nullptr, join[kBranches] = {};
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void*> key_q;
+    std::vector<void*> key_phi;
+    int key_r = -1, key_dtype = -1;
+    bool warmed = false;
+};
+
+extern "C" {
+
+hfmm_status hfmm_batch_destroy(hfmm_batch_t B) {
+    if (!B) return HFMM_OK;
+    cudaSetDevice(B->device);
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    for (int i = 0; i < hfmm_batch_s::kBranches; ++i) {
+        if (B->br[i]) cudaStreamDestroy(B->br[i]);
+        if (B->join[i]) cudaEventDestroy(B->join[i]);
+    }
+    if (B->fork) cudaEventDestroy(B->fork);
+    if (B->cap) cudaStreamDestroy(B->cap);
+    for (hfmm_plan_t p : B->plans) hfmm_destroy(p);
+    delete B;
+    return HFMM_OK;
+}
+
+hfmm_status hfmm_plan_batch(int nprob, const hfmm_problem* probs, const hfmm_options* opt, hfmm_batch_t* out) {
+    g_err.clear();
+    if (!out) return fail(HFMM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nprob < 1 || !probs) return fail(HFMM_ERR_ARG, "need nprob >= 1 and a problem array");
+    hfmm_options o;
+    hfmm_default_options(&o);
+    if (opt) o = *opt;
+    if (o.device < 0) return fail(HFMM_ERR_ARG, "a batch needs a device");
+    hfmm_batch_s* B = new (std::nothrow) hfmm_batch_s();
+    if (!B) return fail(HFMM_ERR_NOMEM, "host allocation failed");
+    B->device = o.device;
+    for (int p = 0; p < nprob; ++p) {
+        hfmm_plan_t h = nullptr;
+        hfmm_status s = hfmm_plan(probs[p].sources, probs[p].ns, probs[p].targets, probs[p].nt, probs[p].kappa,
+                                  probs[p].eps, &o, &h);
+        if (s != HFMM_OK) {
+            std::string msg = "problem " + std::to_string(p) + ": " + g_err;
+            hfmm_batch_destroy(B);
+            return fail(s, msg);
+        }
+        B->plans.push_back(h);
+    }
+    cudaSetDevice(B->device);
+    bool ok = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < hfmm_batch_s::kBranches; ++i)
+        ok = cudaStreamCreateWithFlags(&B->br[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&B->join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        hfmm_batch_destroy(B);
+        return fail(HFMM_ERR_CUDA, "stream/event creation failed");
+    }
+    *out = B;
+    return HFMM_OK;
+}
+
+hfmm_status hfmm_batch_plan(hfmm_batch_t B, int p, hfmm_plan_t* plan) {
+    if (!B || !plan || p < 0 || p >= (int)B->plans.size()) return fail(HFMM_ERR_ARG, "bad batch index");
+    *plan = B->plans[p];
+    return HFMM_OK;
+}
+
+hfmm_status hfmm_apply_batch(hfmm_batch_t B, const void* const* q, void* const* phi, int nrhs, hfmm_dtype dtype,
+                             void* stream) {
+    if (!B || !q || !phi) return fail(HFMM_ERR_ARG, "NULL argument");
+    const int n = (int)B->plans.size();
+    for (int p = 0; p < n; ++p) {
+        if (!q[p] || !phi[p]) return fail(HFMM_ERR_ARG, "NULL buffer for problem " + std::to_string(p));
+        if (nrhs < 1 || nrhs > B->plans[p]->rmax) return fail(HFMM_ERR_ARG, "nrhs must be in [1, max_rhs]");
+    }
+    if (dtype != HFMM_C64 && dtype != HFMM_C128) return fail(HFMM_ERR_ARG, "unknown dtype");
+    CK(cudaSetDevice(B->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<const void*> kq(q, q + n);
+    std::vector<void*> kp(phi, phi + n);
+    if (!B->exec || kq != B->key_q || kp != B->key_phi || nrhs != B->key_r || (int)dtype != B->key_dtype) {
+        if (!B->warmed) {  // load every kernel once outside the capture
+            for (int p = 0; p < n; ++p) TRY(hfmm_apply(B->plans[p], q[p], phi[p], nrhs, dtype, stream));
+            CK(cudaStreamSynchronize(st));
+            B->warmed = true;
+        }
+        if (B->exec) {
+            cudaGraphExecDestroy(B->exec);
+            B->exec = nullptr;
+        }
+        for (int p = 0; p < n; ++p) B->plans[p]->timing = false;
+        CK(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeRelaxed));
+        CK(cudaEventRecord(B->fork, B->cap));
+        for (int i = 0; i < hfmm_batch_s::kBranches; ++i) CK(cudaStreamWaitEvent(B->br[i], B->fork, 0));
+        hfmm_status s = HFMM_OK;
+        for (int p = 0; p < n && s == HFMM_OK; ++p)
+            s = hfmm_apply(B->plans[p], q[p], phi[p], nrhs, dtype, B->br[p % hfmm_batch_s::kBranches]);
+        for (int i = 0; i < hfmm_batch_s::kBranches; ++i) {
+            cudaEventRecord(B->join[i], B->br[i]);
+            cudaStreamWaitEvent(B->cap, B->join[i], 0);
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(B->cap, &graph);
+        if (s != HFMM_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        if (e != cudaSuccess) return fail(HFMM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&B->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            B->exec = nullptr;
+            return fail(HFMM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        }
+        B->key_q = kq;
+        B->key_phi = kp;
+        B->key_r = nrhs;
+        B->key_dtype = (int)dtype;
+    }
+    CK(cudaGraphLaunch(B->exec, st));
+    return HFMM_OK;
+}
+
 int64_t hfmm_debug_get(hfmm_plan_t P, int what, int level, int64_t arg, void* out, int64_t cap) {
     if (!P) return -1;
     const HostPlan& hp = P->hp;

@@ -10,6 +10,25 @@ import numpy as np
 from . import _native as nat
 
 
+def make_options(precision="fp64", alphas=(0.8, 0.7, 0.6), eps_scale=0.25, max_leaf=64, depth=0, root=None,
+                 max_rhs=1, device=0):
+    opt = nat.Options()
+    nat.lib().hfmm_default_options(ctypes.byref(opt))
+    for i in range(4):
+        opt.alpha_ladder[i] = alphas[i] if i < len(alphas) else 0.0
+    opt.eps_scale = eps_scale
+    opt.max_leaf = max_leaf
+    opt.depth = depth
+    if root is not None:
+        opt.has_root = 1
+        for i in range(4):
+            opt.root[i] = float(root[i])
+    opt.precision = {"fp64": nat.PREC_FP64, "mixed": nat.PREC_MIXED}[precision]
+    opt.max_rhs = max_rhs
+    opt.device = device
+    return opt
+
+
 class FmmPlan:
     """Plan of the FMM apply for fixed sources, targets, kappa and eps.
 
@@ -24,20 +43,7 @@ class FmmPlan:
         src = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 3)
         tgt = np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 3)
         self.same = sources is targets
-        opt = nat.Options()
-        L.hfmm_default_options(ctypes.byref(opt))
-        for i in range(4):
-            opt.alpha_ladder[i] = alphas[i] if i < len(alphas) else 0.0
-        opt.eps_scale = eps_scale
-        opt.max_leaf = max_leaf
-        opt.depth = depth
-        if root is not None:
-            opt.has_root = 1
-            for i in range(4):
-                opt.root[i] = float(root[i])
-        opt.precision = {"fp64": nat.PREC_FP64, "mixed": nat.PREC_MIXED}[precision]
-        opt.max_rhs = max_rhs
-        opt.device = device
+        opt = make_options(precision, alphas, eps_scale, max_leaf, depth, root, max_rhs, device)
         h = ctypes.c_void_p()
         nat.check(L.hfmm_plan(src.ctypes.data, src.shape[0], tgt.ctypes.data, tgt.shape[0],
                               float(kappa), float(eps), ctypes.byref(opt), ctypes.byref(h)))
@@ -182,3 +188,73 @@ def direct_noalloc(sources, targets, q, kappa, out=None, stream=None):
                                              targets.shape[0], q2.data_ptr(), out.data_ptr(), r, dtype,
                                              float(kappa), st.cuda_stream))
     return out[:, 0] if single else out
+
+
+class _BorrowedPlan(FmmPlan):
+    """A plan owned by a batch (not destroyed by Python)."""
+
+    def __init__(self, handle, ns, nt, max_rhs):
+        self._borrowed = handle
+        self.ns, self.nt, self.max_rhs = ns, nt, max_rhs
+
+    def __del__(self):
+        pass
+
+    @property
+    def _h(self):
+        return self._borrowed
+
+
+class FmmBatch:
+    """Independent problems applied by one CUDA graph launch (hfmm_plan_batch / hfmm_apply_batch).
+
+    problems: list of (sources, targets, kappa, eps); options as for FmmPlan.
+    """
+
+    def __init__(self, problems, **opts):
+        L = nat.lib()
+        self._keep = []
+        arr = (nat.Problem * len(problems))()
+        self.sizes = []
+        for i, (s, t, kappa, eps) in enumerate(problems):
+            s = np.ascontiguousarray(s, dtype=np.float64).reshape(-1, 3)
+            t = np.ascontiguousarray(t, dtype=np.float64).reshape(-1, 3)
+            self._keep += [s, t]
+            arr[i] = nat.Problem(s.ctypes.data, s.shape[0], t.ctypes.data, t.shape[0], float(kappa), float(eps))
+            self.sizes.append((s.shape[0], t.shape[0]))
+        opt = make_options(**opts)
+        self.max_rhs = opt.max_rhs
+        h = ctypes.c_void_p()
+        nat.check(L.hfmm_plan_batch(len(problems), arr, ctypes.byref(opt), ctypes.byref(h)))
+        self._h = h
+        self._keep = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            nat.lib().hfmm_batch_destroy(h)
+            self._h = None
+
+    def plan(self, p):
+        ph = ctypes.c_void_p()
+        nat.check(nat.lib().hfmm_batch_plan(self._h, p, ctypes.byref(ph)))
+        ns, nt = self.sizes[p]
+        return _BorrowedPlan(ph, ns, nt, self.max_rhs)
+
+    def apply(self, qs, outs=None, stream=None):
+        """qs: list of CUDA (ns_p, R) complex tensors; returns the list of (nt_p, R) results."""
+        import torch
+        n = len(self.sizes)
+        if len(qs) != n:
+            raise ValueError(f"need {n} charge tensors")
+        q2 = [q.reshape(q.shape[0], -1).contiguous() for q in qs]
+        r = q2[0].shape[1]
+        dt = q2[0].dtype
+        if outs is None:
+            outs = [torch.empty((self.sizes[p][1], r), dtype=dt, device=q2[p].device) for p in range(n)]
+        qp = (ctypes.c_void_p * n)(*[q.data_ptr() for q in q2])
+        op = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+        st = stream if stream is not None else torch.cuda.current_stream(q2[0].device)
+        dtype = nat.C64 if dt == torch.complex64 else nat.C128
+        nat.check(nat.lib().hfmm_apply_batch(self._h, qp, op, r, dtype, st.cuda_stream))
+        return outs
