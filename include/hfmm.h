@@ -61,7 +61,7 @@ typedef enum { HFMM_LEVEL_FP64 = 0, HFMM_LEVEL_FP32 = 1 } hfmm_level_precision;
 
 typedef struct {
     /* alpha values tried for each level, in order (Section 3.3.3: |r| = alpha sqrt(3) a_l);
-     * a 0 ends the list.  Default {0.8, 0.7, 0.6, 0}. */
+     * a 0 ends the list.  Default {0.8, 0.6, 0, 0}. */
     double alpha_ladder[4];
     /* per-level target eps_l = eps_scale * eps (default 0.25) */
     double eps_scale;

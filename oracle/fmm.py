@@ -19,7 +19,7 @@ apply is the near field over the level-L_f neighbour lists, i.e. the direct sum.
 
 The stability rule (a reading; the paper only names the low-frequency breakdown
 and notes that a lower alpha gives a smaller quadrature):  for each level, top
-down, the first alpha of the ladder (0.8, 0.7, 0.6) whose plan passes
+down, the first alpha of the ladder (0.8, 0.6) whose plan passes
     est(u) = u * k|r0| * sqrt(sum_{n<=l} (2n+1)|h_n(k|r0|)|^2) / sqrt(K) <= f_p * eps_l
 in one of the precisions the policy allows is taken (u = 2^-53, f = 1/16 for
 fp64; u = 2^-24, f = 1 for fp32; the policy 'fp64' allows fp64 only, 'mixed'
@@ -42,7 +42,7 @@ from .tree import Tree, root_cube, occupancy_depth
 PRECISION_UNIT = {'fp64': qd.U_FP64, 'fp32': qd.U_FP32}
 # acceptance factor of the stability rule per precision (see module docstring)
 PRECISION_FACTOR = {'fp64': 1.0 / 16.0, 'fp32': 1.0}
-ALPHA_LADDER = (0.8, 0.7, 0.6)
+ALPHA_LADDER = (0.8, 0.6)
 
 
 def level_precisions(policy):

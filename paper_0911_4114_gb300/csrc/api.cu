@@ -50,6 +50,7 @@ struct DevLevel {
     int32_t* tslot = nullptr;
     int32_t* tslot_t = nullptr;  // slot of the opposite vector (342 - v): transposed M2L
     void* table = nullptr;      // compact T^{s,LL} tables in the level precision
+    df* sdf = nullptr;          // (K, 3) s_k * kappa / 2 pi as double-float pairs
     cxd* shift64 = nullptr;     // [8][K] exp(i k s.d_o), d_o = child-centre offsets of level l+1
     cxf* shift32 = nullptr;
     cx<df>* shiftdf = nullptr;
@@ -77,6 +78,8 @@ struct hfmm_plan_s {
     P2PMixedArgs mixed{};
     cxd *qs = nullptr, *phis = nullptr;
     int max_src_leaf = 1, max_tgt_leaf = 1;   // largest leaf-box point counts (grid heights)
+    int2 *tunits = nullptr, *sunits = nullptr;  // (leaf box, first point) of every 32-point chunk
+    int ntunits = 0, nsunits = 0;
     double* gsort = nullptr;    // sorted position gradient (ns, 3)
     DevLevel lev[kMaxLevels];
     Requad up[kMaxLevels];    // up[l]: level l -> l-1
@@ -156,6 +159,12 @@ hfmm_status upload_level(hfmm_plan_s* P, int l) {
     TRY(upload(P, &dshat, shat));
     TRY(upload(P, &dw, w));
     d.qv = QuadView{q.ntheta, half + 1, q.K, nphi, off, dshat, dw};
+    {
+        std::vector<df> sd(3 * q.K);
+        const double kt = hp.kappa / (2.0 * 3.14159265358979323846);
+        for (int64_t i = 0; i < 3 * q.K; ++i) sd[i] = df_from_double(shat[i] * kt);
+        TRY(upload(P, &d.sdf, sd));
+    }
     // boxes
     double* center;
     int32_t *idx, *parent, *cs = nullptr, *cc = nullptr;
@@ -276,6 +285,17 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
     TRY(soa(hp.tgt, hp.tgt_perm, &P->tx, &P->ty, &P->tz));
     TRY(upload(P, &P->src_perm, hp.src_perm));
     TRY(upload(P, &P->tgt_perm, hp.tgt_perm));
+    {
+        auto chunks = [&](const std::vector<int32_t>& count, int2** dst, int* n) -> hfmm_status {
+            std::vector<int2> u;
+            for (size_t b = 0; b < count.size(); ++b)
+                for (int c = 0; c < count[b]; c += 32) u.push_back(make_int2((int)b, c));
+            *n = (int)u.size();
+            return upload(P, dst, u);
+        };
+        TRY(chunks(hp.tgt_count, &P->tunits, &P->ntunits));
+        TRY(chunks(hp.src_count, &P->sunits, &P->nsunits));
+    }
     for (int32_t c : hp.src_count) P->max_src_leaf = std::max(P->max_src_leaf, (int)c);
     for (int32_t c : hp.tgt_count) P->max_tgt_leaf = std::max(P->max_tgt_leaf, (int)c);
     TRY(upload(P, &P->sstart, hp.src_start));
@@ -604,8 +624,11 @@ void launch_l2t(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false)
     const double kt = P->hp.kappa / (2.0 * 3.14159265358979323846);
     const dim3 grid(d.nbox, nblk(transposed ? P->max_src_leaf : P->max_tgt_leaf, kL2TThreads));
     if (std::is_same<T, double>::value && use_df(P, lf)) {
-        k_l2t_df<<<grid, kL2TThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, (const cx<df>*)in, R, kt,
-                                                 P->cis_tab, out, sign, wk);
+        const int2* units = transposed ? P->sunits : P->tunits;
+        const int nu = transposed ? P->nsunits : P->ntunits;
+        if (nu > 0)
+            k_l2t_df_warp<<<nblk(nu, 4), 128, 0, st>>>(units, nu, d.bv, d.qv, d.sdf, start, count, px, py, pz,
+                                                      (const cx<df>*)in, R, P->cis_tab, out, sign, wk);
         return;
     }
     k_l2t<T><<<grid, kL2TThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, (const cx<T>*)in, R, kt, out,
@@ -649,8 +672,8 @@ void hfmm_default_options(hfmm_options* opt) {
     if (!opt) return;
     std::memset(opt, 0, sizeof(*opt));
     opt->alpha_ladder[0] = 0.8;
-    opt->alpha_ladder[1] = 0.7;
-    opt->alpha_ladder[2] = 0.6;
+    opt->alpha_ladder[1] = 0.6;
+    opt->alpha_ladder[2] = 0.0;
     opt->alpha_ladder[3] = 0.0;
     opt->eps_scale = 0.25;
     opt->max_leaf = 64;
@@ -795,9 +818,12 @@ hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_d
     mark(1);
     const int nleaf = (int)hp.levels[lf].nbox();
     const dim3 g_fwd(nleaf, nblk(P->max_tgt_leaf, kP2PThreads));
-    if (hp.precision == HFMM_PREC_MIXED)
-        k_p2p_mixed<<<g_fwd, kP2PThreads, 0, st>>>(nleaf, P->tstart, P->tcount, P->sstart, P->scount, P->noff,
-                                                   P->nidx, P->mixed, P->qs, P->phis, R);
+    if (hp.precision == HFMM_PREC_MIXED) {
+        if (P->ntunits > 0)
+            k_p2p_mixed_warp<<<nblk(P->ntunits, 4), 128, 0, st>>>(P->tunits, P->ntunits, P->tstart, P->tcount,
+                                                                  P->sstart, P->scount, P->noff, P->nidx, P->mixed,
+                                                                  P->qs, P->phis, R);
+    }
     else
         k_p2p_fp64<<<g_fwd, kP2PThreads, 0, st>>>(nleaf, P->tstart, P->tcount, P->sstart, P->scount, P->noff,
                                                   P->nidx, P->tx, P->ty, P->tz, P->sx, P->sy, P->sz, P->qs,
@@ -857,8 +883,10 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t P, const void* w, void* out, int nrhs
         P2PMixedArgs a = P->mixed;
         std::swap(a.tpt, a.spt);
         std::swap(a.tof, a.sof);
-        k_p2p_mixed<<<g_adj, kP2PThreads, 0, st>>>(nleaf, P->sstart, P->scount, P->tstart, P->tcount, P->noff,
-                                                   P->nidx, a, P->phis, P->qs, R);
+        if (P->nsunits > 0)
+            k_p2p_mixed_warp<<<nblk(P->nsunits, 4), 128, 0, st>>>(P->sunits, P->nsunits, P->sstart, P->scount,
+                                                                  P->tstart, P->tcount, P->noff, P->nidx, a, P->phis,
+                                                                  P->qs, R);
     } else {
         k_p2p_fp64<<<g_adj, kP2PThreads, 0, st>>>(nleaf, P->sstart, P->scount, P->tstart, P->tcount, P->noff,
                                                   P->nidx, P->sx, P->sy, P->sz, P->tx, P->ty, P->tz, P->phis,

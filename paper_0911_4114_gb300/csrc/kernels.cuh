@@ -475,6 +475,155 @@ __global__ void k_l2t_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ts
 }
 
 // ---------------------------------------------------------------------------
+// Warp-granular versions: one warp per (leaf box, 32-point chunk) work unit, warp-private
+// shared staging and __syncwarp only, so a box's last partial chunk idles at most one warp
+// and no warp waits at a block barrier for another box's work.
+// ---------------------------------------------------------------------------
+constexpr int kWarpTile = 64;    // quadrature samples (or sources) staged per warp step
+
+// signature -> points, double-float (L2T: targets, sign +1, weights; transposed S2M: sources,
+// sign -1, no weights); sdf = s_k * kappa / 2 pi as df triples, precomputed per level
+__global__ void __launch_bounds__(128) k_l2t_df_warp(
+    const int2* __restrict__ units, int nunits, BoxView bx, QuadView qv, const df* __restrict__ sdf,
+    const int32_t* __restrict__ pstart, const int32_t* __restrict__ pcount, const double* __restrict__ px,
+    const double* __restrict__ py, const double* __restrict__ pz, const cx<df>* __restrict__ L, int R_,
+    const cdf* __restrict__ cis_tab, cxd* __restrict__ out, double sign, const double* __restrict__ wk) {
+    __shared__ cdf tab[kCisTable];
+    __shared__ df shs[4][kWarpTile * 3];
+    __shared__ cdf shl[4][kWarpTile];
+    load_cis_table(tab, cis_tab);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int u = blockIdx.x * 4 + warp;
+    if (u >= nunits) return;
+    const int b = units[u].x, c0 = units[u].y;
+    const int t0 = pstart[b], tc = pcount[b];
+    const int ti = c0 + lane;
+    const bool active = ti < tc;
+    const double cxx = bx.center[3 * b], cyy = bx.center[3 * b + 1], czz = bx.center[3 * b + 2];
+    df d[3] = {{0, 0}, {0, 0}, {0, 0}};
+    if (active) {
+        d[0] = df_from_double(sign * (cxx - px[t0 + ti]));
+        d[1] = df_from_double(sign * (cyy - py[t0 + ti]));
+        d[2] = df_from_double(sign * (czz - pz[t0 + ti]));
+    }
+    df* ss = shs[warp];
+    cdf* sl = shl[warp];
+    for (int r = 0; r < R_; ++r) {
+        const cx<df>* Lb = L + ((int64_t)b * R_ + r) * qv.K;
+        cdf acc = {{0, 0}, {0, 0}};
+        for (int64_t kb = 0; kb < qv.K; kb += kWarpTile) {
+            const int kn = (int)min((int64_t)kWarpTile, qv.K - kb);
+            __syncwarp();
+            for (int v = lane; v < kn; v += 32) {
+                const int64_t k = kb + v;
+                ss[3 * v] = sdf[3 * k];
+                ss[3 * v + 1] = sdf[3 * k + 1];
+                ss[3 * v + 2] = sdf[3 * k + 2];
+                cdf wl = cdf{Lb[k].x, Lb[k].y};
+                if (wk) {
+                    const df w = df_from_double(wk[k]);
+                    wl = cdf{df_mul(wl.x, w), df_mul(wl.y, w)};
+                }
+                sl[v] = wl;
+            }
+            __syncwarp();
+            if (active)
+                for (int kk = 0; kk < kn; ++kk) {
+                    df t = df_mul(ss[3 * kk], d[0]);
+                    t = df_add(t, df_mul(ss[3 * kk + 1], d[1]));
+                    t = df_add(t, df_mul(ss[3 * kk + 2], d[2]));
+                    acc = cdf_add(acc, cdf_mul(cis_turns(df_reduce(t), tab), sl[kk]));
+                }
+        }
+        if (active) {
+            cxd& o = out[(int64_t)(t0 + ti) * R_ + r];
+            o.x += df_to_double(acc.x);
+            o.y += df_to_double(acc.y);
+        }
+    }
+}
+
+// mixed near field, one warp per (target box, 32-target chunk); float32 sums over tiles of
+// kWarpTile sources, flushed into float64
+__global__ void __launch_bounds__(128) k_p2p_mixed_warp(
+    const int2* __restrict__ units, int nunits, const int32_t* __restrict__ tstart,
+    const int32_t* __restrict__ tcount, const int32_t* __restrict__ sstart, const int32_t* __restrict__ scount,
+    const int32_t* __restrict__ noff, const int32_t* __restrict__ nidx, P2PMixedArgs a,
+    const cxd* __restrict__ qs, cxd* __restrict__ phis, int R) {
+    __shared__ float4 shp[4][kWarpTile], sho[4][kWarpTile];
+    __shared__ cxf shq[4][kWarpTile * 4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int u = blockIdx.x * 4 + warp;
+    if (u >= nunits) return;
+    const int b = units[u].x, c0 = units[u].y;
+    const int t0 = tstart[b], tc = tcount[b];
+    const int ti = c0 + lane;
+    const bool active = ti < tc;
+    const float two_pi = 6.28318530717958647692f;
+    float4 gp = make_float4(0, 0, 0, 0), op = gp;
+    if (active) {
+        gp = a.tpt[t0 + ti];
+        op = a.tof[t0 + ti];
+    }
+    float4* wp = shp[warp];
+    float4* wo = sho[warp];
+    cxf* wq = shq[warp];
+    for (int r0 = 0; r0 < R; r0 += 4) {
+        const int rn = min(4, R - r0);
+        cxd acc[4];
+        for (int r = 0; r < 4; ++r) acc[r] = mk<double>(0, 0);
+        for (int nb = noff[b]; nb < noff[b + 1]; ++nb) {
+            const int s = nidx[nb];
+            const int s0 = sstart[s], sc = scount[s];
+            for (int sb = 0; sb < sc; sb += kWarpTile) {
+                const int sn = min(kWarpTile, sc - sb);
+                __syncwarp();
+                for (int v = lane; v < sn; v += 32) {
+                    const int j = s0 + sb + v;
+                    wp[v] = a.spt[j];
+                    wo[v] = a.sof[j];
+                    for (int r = 0; r < rn; ++r) wq[v * 4 + r] = cvt<float>(qs[(int64_t)j * R + r0 + r]);
+                }
+                __syncwarp();
+                if (!active) continue;
+                cxf tile[4];
+                for (int r = 0; r < 4; ++r) tile[r] = mk<float>(0, 0);
+                for (int jj = 0; jj < sn; ++jj) {
+                    const float4 sp = wp[jj], so = wo[jj];
+                    const float Dx = gp.x - sp.x, Dy = gp.y - sp.y, Dz = gp.z - sp.z;  // exact
+                    const float ex = op.x - so.x, ey = op.y - so.y, ez = op.z - so.z;
+                    const float A = fmaf(Dx, Dx, fmaf(Dy, Dy, Dz * Dz));           // exact
+                    const float B = fmaf(ex, fmaf(2.0f, Dx, ex),
+                                         fmaf(ey, fmaf(2.0f, Dy, ey), ez * fmaf(2.0f, Dz, ez)));
+                    const float s2 = A + B;
+                    if (s2 <= 0.0f) continue;
+                    const float rho = rsqrtf(s2);
+                    const float r0f = s2 * rho;
+                    const float e = fmaf(-r0f, r0f, A);
+                    const float c = (e + B) * (0.5f * rho);
+                    const float th = a.tau_hi * r0f;
+                    float te = fmaf(a.tau_hi, r0f, -th);
+                    te = fmaf(a.tau_hi, c, te);
+                    te = fmaf(a.tau_lo, r0f, te);
+                    const float f = (th - rintf(th)) + te;
+                    float sn_, cs_;
+                    __sincosf(two_pi * f, &sn_, &cs_);
+                    const cxf g = mk<float>(cs_ * rho, sn_ * rho);
+                    for (int r = 0; r < rn; ++r) mac(tile[r], g, wq[jj * 4 + r]);
+                }
+                for (int r = 0; r < rn; ++r) {
+                    acc[r].x += (double)tile[r].x;
+                    acc[r].y += (double)tile[r].y;
+                }
+            }
+        }
+        if (active)
+            for (int r = 0; r < rn; ++r) phis[(int64_t)(t0 + ti) * R + r0 + r] = a.inv_unit * acc[r];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Position gradient (vector-Jacobian product of phi = A(y) q for a real loss, with
 // g = dL/d conj(phi) in the convention of complex autograd):
 //   grad_j = Re[ sum_r q_jr ( i k sum_k s_k exp(i k s_k.(y_j - c_b)) Lambda_b,r(k)

@@ -10,7 +10,7 @@ import numpy as np
 from . import _native as nat
 
 
-def make_options(precision="fp64", alphas=(0.8, 0.7, 0.6), eps_scale=0.25, max_leaf=64, depth=0, root=None,
+def make_options(precision="fp64", alphas=(0.8, 0.6), eps_scale=0.25, max_leaf=64, depth=0, root=None,
                  max_rhs=1, device=0):
     opt = nat.Options()
     nat.lib().hfmm_default_options(ctypes.byref(opt))
@@ -37,7 +37,7 @@ class FmmPlan:
     (queries only).
     """
 
-    def __init__(self, sources, targets, kappa, eps, precision="fp64", alphas=(0.8, 0.7, 0.6),
+    def __init__(self, sources, targets, kappa, eps, precision="fp64", alphas=(0.8, 0.6),
                  eps_scale=0.25, max_leaf=64, depth=0, root=None, max_rhs=1, device=0):
         L = nat.lib()
         src = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 3)
