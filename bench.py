@@ -274,10 +274,10 @@ def main():
                     peak_note="152 SMs x 128 FP32 lanes x median SM clock under load")
     elif stage in ("s2m", "l2t") and lev.get("precision") == "fp64":
         evals = float(lev["K"]) * len(t)
-        ops = 273.0 * evals                              # double-float ops per plane-wave evaluation
+        ops = 220.0 * evals                              # double-float ops per plane-wave evaluation
         ach = ops / (stage_ms[stage] * 1e-3) / 1e9
         roof.update(kernel="k_%s_df" % stage, bound="alu", achieved=ach, peak=fp32_peak, unit="Gop/s",
-                    frac=ach / fp32_peak, unit_work="273 float32 ops per (point, quadrature sample) in double-float",
+                    frac=ach / fp32_peak, unit_work="220 float32 ops per (point, quadrature sample) in double-float",
                     peak_note="152 SMs x 128 FP32 lanes x median SM clock under load")
     elif stage in ("m2l", "m2m", "l2l"):
         hbm = peaks.get("hbm_gbs", 6800.0)

@@ -87,7 +87,7 @@ struct hfmm_plan_s {
     void *ga = nullptr, *gb = nullptr;
     void *tw64 = nullptr, *tw32 = nullptr, *twdf = nullptr;
     int* twoff = nullptr;
-    cdf* cis_tab = nullptr;     // exp(2 pi i j / 256) as double-float pairs
+    cdf* cis_tab = nullptr;     // exp(2 pi i j / 1024) as double-float pairs
     int64_t workspace = 0;
     bool timing = false;
     cudaEvent_t ev[HFMM_N_STAGES + 1] = {};
@@ -404,9 +404,9 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
         P->down[l - 1].args.qb = P->lev[l].qv;
     }
     {
-        std::vector<cdf> tab(kCisTable);
-        for (int j = 0; j < kCisTable; ++j) {
-            const double a = 2.0 * 3.14159265358979323846 * (double)j / (double)kCisTable;
+        std::vector<cdf> tab(kCisTableBig);
+        for (int j = 0; j < kCisTableBig; ++j) {
+            const double a = 2.0 * 3.14159265358979323846 * (double)j / (double)kCisTableBig;
             tab[j] = cdf{df_from_double(std::cos(a)), df_from_double(std::sin(a))};
         }
         TRY(upload(P, &P->cis_tab, tab));
@@ -820,9 +820,16 @@ hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_d
     const dim3 g_fwd(nleaf, nblk(P->max_tgt_leaf, kP2PThreads));
     if (hp.precision == HFMM_PREC_MIXED) {
         if (P->ntunits > 0)
-            k_p2p_mixed_warp<<<nblk(P->ntunits, 4), 128, 0, st>>>(P->tunits, P->ntunits, P->tstart, P->tcount,
-                                                                  P->sstart, P->scount, P->noff, P->nidx, P->mixed,
-                                                                  P->qs, P->phis, R);
+        {
+            if (R == 1)
+                k_p2p_mixed_warp<1><<<nblk(P->ntunits, 4), 128, 0, st>>>(P->tunits, P->ntunits, P->tstart, P->tcount,
+                                                                         P->sstart, P->scount, P->noff, P->nidx,
+                                                                         P->mixed, P->qs, P->phis, R);
+            else
+                k_p2p_mixed_warp<4><<<nblk(P->ntunits, 4), 128, 0, st>>>(P->tunits, P->ntunits, P->tstart, P->tcount,
+                                                                         P->sstart, P->scount, P->noff, P->nidx,
+                                                                         P->mixed, P->qs, P->phis, R);
+        }
     }
     else
         k_p2p_fp64<<<g_fwd, kP2PThreads, 0, st>>>(nleaf, P->tstart, P->tcount, P->sstart, P->scount, P->noff,
@@ -884,9 +891,16 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t P, const void* w, void* out, int nrhs
         std::swap(a.tpt, a.spt);
         std::swap(a.tof, a.sof);
         if (P->nsunits > 0)
-            k_p2p_mixed_warp<<<nblk(P->nsunits, 4), 128, 0, st>>>(P->sunits, P->nsunits, P->sstart, P->scount,
-                                                                  P->tstart, P->tcount, P->noff, P->nidx, a, P->phis,
-                                                                  P->qs, R);
+        {
+            if (R == 1)
+                k_p2p_mixed_warp<1><<<nblk(P->nsunits, 4), 128, 0, st>>>(P->sunits, P->nsunits, P->sstart, P->scount,
+                                                                         P->tstart, P->tcount, P->noff, P->nidx, a,
+                                                                         P->phis, P->qs, R);
+            else
+                k_p2p_mixed_warp<4><<<nblk(P->nsunits, 4), 128, 0, st>>>(P->sunits, P->nsunits, P->sstart, P->scount,
+                                                                         P->tstart, P->tcount, P->noff, P->nidx, a,
+                                                                         P->phis, P->qs, R);
+        }
     } else {
         k_p2p_fp64<<<g_adj, kP2PThreads, 0, st>>>(nleaf, P->sstart, P->scount, P->tstart, P->tcount, P->noff,
                                                   P->nidx, P->sx, P->sy, P->sz, P->tx, P->ty, P->tz, P->phis,

@@ -3,9 +3,9 @@
 // Dekker's Fast2Sum and the FMA form of Dekker's exact product.  Every step uses the
 // _rn intrinsics so the compiler cannot contract or reassociate it.
 //
-// cis_turns(r) = exp(2 pi i r) for |r| <= 1/2: reduction by a 256-entry table of
-// exp(2 pi i j / 256) (stored as df pairs), then Taylor polynomials of sin and cos on
-// |x| <= pi/256 in df arithmetic, then one complex df product.
+// cis_turns_big(t) = exp(2 pi i t): reduction by a 1024-entry table of exp(2 pi i j / 1024)
+// (stored as df pairs), Taylor polynomials of sin and cos on |x| <= pi/1024 in df arithmetic,
+// then one complex df product.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -79,34 +79,54 @@ __device__ __forceinline__ cdf cdf_mul(cdf a, cdf b) {
 }
 __device__ __forceinline__ cdf cdf_add(cdf a, cdf b) { return {df_add(a.x, b.x), df_add(a.y, b.y)}; }
 
-constexpr int kCisTable = 256;
+// lazy double-float accumulator: leading sum with exact Knuth errors, all errors and low
+// parts gathered in a float32 tail; value = hi + lo after the final renormalisation
+struct dfacc {
+    float hi, lo;
+};
+__device__ __forceinline__ void dfacc_add(dfacc& a, df v) {
+    df s = df_two_sum(a.hi, v.hi);
+    a.hi = s.hi;
+    a.lo = __fadd_rn(a.lo, __fadd_rn(s.lo, v.lo));
+}
+__device__ __forceinline__ df dfacc_get(dfacc a) { return df_fast_sum(a.hi, a.lo); }
 
-// exp(2 pi i r) for |r| <= 1/2 (r in turns, as df); tab[j] = exp(2 pi i j / 256) as df pairs
-__device__ __forceinline__ cdf cis_turns(df r, const cdf* tab) {
-    const float jf = rintf(__fmul_rn(r.hi, (float)kCisTable));
-    // r - j/256 is exact on the hi part (Sterbenz)
-    df rr = df_fast_sum(__fsub_rn(r.hi, __fdiv_rn(jf, (float)kCisTable)), r.lo);
+constexpr int kCisTableBig = 1024;
+
+// phase s . d in turns for df triples s and d: Dekker products with their exact FMA errors,
+// Knuth sums of the leading parts, every small term gathered in float32, one renormalisation
+__device__ __forceinline__ df df_dot3(const df* s, const df* d) {
+    const float p0 = __fmul_rn(s[0].hi, d[0].hi), p1 = __fmul_rn(s[1].hi, d[1].hi), p2 = __fmul_rn(s[2].hi, d[2].hi);
+    float e = __fadd_rn(__fadd_rn(__fmaf_rn(s[0].hi, d[0].hi, -p0), __fmaf_rn(s[1].hi, d[1].hi, -p1)),
+                        __fmaf_rn(s[2].hi, d[2].hi, -p2));
+    e = __fmaf_rn(s[0].hi, d[0].lo, __fmaf_rn(s[0].lo, d[0].hi, e));
+    e = __fmaf_rn(s[1].hi, d[1].lo, __fmaf_rn(s[1].lo, d[1].hi, e));
+    e = __fmaf_rn(s[2].hi, d[2].lo, __fmaf_rn(s[2].lo, d[2].hi, e));
+    const df a = df_two_sum(p0, p1);
+    const df b = df_two_sum(a.hi, p2);
+    return df_fast_sum(b.hi, __fadd_rn(__fadd_rn(a.lo, b.lo), e));
+}
+
+// exp(2 pi i t) for any df t (turns): one reduction by the nearest 1/1024 of a turn
+// (exact on the leading part), table of exp(2 pi i j / 1024), Taylor polynomials on
+// |x| <= pi / 1024 (cos to y^2/24, sin to x y^2/120; dropped terms < 2^-58)
+__device__ __forceinline__ cdf cis_turns_big(df t, const cdf* tab) {
+    const float jf = rintf(__fmul_rn(t.hi, (float)kCisTableBig));
+    df rr = df_fast_sum(__fsub_rn(t.hi, __fdiv_rn(jf, (float)kCisTableBig)), t.lo);
     const df two_pi = {6.2831854820251465f, -1.7484555314695172e-07f};
-    df x = df_mul(rr, two_pi);                  // |x| <= pi / 256
+    df x = df_mul(rr, two_pi);
     df y = df_mul(x, x);
-    // cos x = 1 - y/2 + y^2/24 - y^3/720 ; sin x = x (1 - y/6 + y^2/120 - y^3/5040)
     const float yh = y.hi;
-    const df c24 = {0.0416666679084301f, -1.2417634698280722e-09f};     // 1/24
-    const df c6 = {0.1666666716337204f, -4.967053879312289e-09f};       // 1/6
-    const df c120 = {0.008333333767950535f, -4.34617203337595e-10f};   // 1/120
-    // every addition below has a dominant left operand (|y| <= 1.6e-4): Fast2Sum suffices
-    df cc = df_add_big(c24, {__fmul_rn(yh, -1.0f / 720.0f), 0.0f});
-    cc = df_mul(y, cc);
-    cc = df_add_big({-0.5f, 0.0f}, cc);
-    cc = df_mul(y, cc);
-    cc = df_add_big({1.0f, 0.0f}, cc);
-    df ss = df_add_big(c120, {__fmul_rn(yh, -1.0f / 5040.0f), 0.0f});
-    ss = df_mul(y, ss);
-    ss = df_add_big(df_neg(c6), ss);
-    ss = df_mul(y, ss);
-    ss = df_mul(x, ss);
-    ss = df_add_big(x, ss);
-    const int j = ((int)jf) & (kCisTable - 1);
+    // cos = 1 - y/2 + y^2/24 : (y/2 - y^2/24) in df, then 1 - that
+    df cm = df_add_big(df{__fmul_rn(y.hi, 0.5f), __fmul_rn(y.lo, 0.5f)}, df{__fmul_rn(__fmul_rn(yh, yh), -1.0f / 24.0f), 0.0f});
+    df cc = df_add_big(df{1.0f, 0.0f}, df_neg(cm));
+    // sin = x - x^3/6 + x^5/120: x^3/6 in df, x^5/120 (< 2^-48) in float32
+    const df c6 = {0.1666666716337204f, -4.967053879312289e-09f};
+    const df xy = df_mul(x, y);
+    df sp = df_mul(xy, c6);
+    sp = df_add_big(sp, df{__fmul_rn(__fmul_rn(xy.hi, yh), -1.0f / 120.0f), 0.0f});
+    df ss = df_add_big(x, df_neg(sp));
+    const int j = ((int)jf) & (kCisTableBig - 1);
     return cdf_mul(tab[j], cdf{cc, ss});
 }
 

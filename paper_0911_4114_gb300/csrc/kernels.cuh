@@ -359,15 +359,6 @@ __global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstar
 // split into df pairs; the phase in turns is reduced by its nearest integer and cis_turns
 // evaluates exp(2 pi i r).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ df df_reduce(df t) {
-    const float n = rintf(t.hi);
-    return df_fast_sum(__fsub_rn(t.hi, n), t.lo);
-}
-
-__device__ __forceinline__ void load_cis_table(cdf* sh, const cdf* tab) {
-    for (int i = threadIdx.x; i < kCisTable; i += blockDim.x) sh[i] = tab[i];
-}
-
 __global__ void k_s2m_df(BoxView bx, QuadView qv, const int32_t* __restrict__ sstart,
                          const int32_t* __restrict__ scount, const double* __restrict__ sx,
                          const double* __restrict__ sy, const double* __restrict__ sz,
@@ -375,8 +366,8 @@ __global__ void k_s2m_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ss
                          cx<df>* __restrict__ M, double sign, const double* __restrict__ wk) {
     __shared__ df shd[kS2MTile * 3];
     __shared__ cdf shq[kS2MTile];
-    __shared__ cdf tab[kCisTable];
-    load_cis_table(tab, cis_tab);
+    __shared__ cdf tab[kCisTableBig];
+    for (int v = threadIdx.x; v < kCisTableBig; v += blockDim.x) tab[v] = cis_tab[v];
     const int b = blockIdx.x;
     const int64_t k = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
     const bool active = k < qv.K;
@@ -386,7 +377,7 @@ __global__ void k_s2m_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ss
     const int s0 = sstart[b], sc = scount[b];
     const double cxx = bx.center[3 * b], cyy = bx.center[3 * b + 1], czz = bx.center[3 * b + 2];
     for (int r = 0; r < R_; ++r) {
-        cdf acc = {{0, 0}, {0, 0}};
+        dfacc ax = {0.f, 0.f}, ay = {0.f, 0.f};
         for (int jb = 0; jb < sc; jb += kS2MTile) {
             const int jn = min(kS2MTile, sc - jb);
             __syncthreads();
@@ -401,75 +392,18 @@ __global__ void k_s2m_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ss
             __syncthreads();
             if (active)
                 for (int jj = 0; jj < jn; ++jj) {
-                    df t = df_mul(s[0], shd[3 * jj]);
-                    t = df_add(t, df_mul(s[1], shd[3 * jj + 1]));
-                    t = df_add(t, df_mul(s[2], shd[3 * jj + 2]));
-                    acc = cdf_add(acc, cdf_mul(cis_turns(df_reduce(t), tab), shq[jj]));
+                    const cdf e = cdf_mul(cis_turns_big(df_dot3(s, &shd[3 * jj]), tab), shq[jj]);
+                    dfacc_add(ax, e.x);
+                    dfacc_add(ay, e.y);
                 }
         }
+        cdf acc = {dfacc_get(ax), dfacc_get(ay)};
         if (active) {
             if (wk) {
                 const df w = df_from_double(wk[k]);
                 acc = cdf{df_mul(acc.x, w), df_mul(acc.y, w)};
             }
             M[((int64_t)b * R_ + r) * qv.K + k] = mk<df>(acc.x, acc.y);
-        }
-    }
-}
-
-__global__ void k_l2t_df(BoxView bx, QuadView qv, const int32_t* __restrict__ tstart,
-                         const int32_t* __restrict__ tcount, const double* __restrict__ tx,
-                         const double* __restrict__ ty, const double* __restrict__ tz,
-                         const cx<df>* __restrict__ L, int R_, double kappa_turns, const cdf* __restrict__ cis_tab,
-                         cxd* __restrict__ phis, double sign, const double* __restrict__ wk) {
-    __shared__ df shs[kL2TTile * 3];
-    __shared__ cdf shl[kL2TTile];
-    __shared__ cdf tab[kCisTable];
-    load_cis_table(tab, cis_tab);
-    const int b = blockIdx.x;
-    const int t0 = tstart[b], tc = tcount[b];
-    if ((int)blockIdx.y * kL2TThreads >= tc) return;
-    const double cxx = bx.center[3 * b], cyy = bx.center[3 * b + 1], czz = bx.center[3 * b + 2];
-    for (int r = 0; r < R_; ++r) {
-        const cx<df>* Lb = L + ((int64_t)b * R_ + r) * qv.K;
-        {
-            const int tb = blockIdx.y * kL2TThreads;
-            const int ti = tb + threadIdx.x;
-            const bool active = ti < tc;
-            df d[3] = {{0, 0}, {0, 0}, {0, 0}};
-            if (active) {
-                d[0] = df_from_double(sign * (cxx - tx[t0 + ti]));
-                d[1] = df_from_double(sign * (cyy - ty[t0 + ti]));
-                d[2] = df_from_double(sign * (czz - tz[t0 + ti]));
-            }
-            cdf acc = {{0, 0}, {0, 0}};
-            for (int64_t kb = 0; kb < qv.K; kb += kL2TTile) {
-                const int kn = (int)min((int64_t)kL2TTile, qv.K - kb);
-                __syncthreads();
-                for (int u = threadIdx.x; u < kn; u += kL2TThreads) {
-                    const int64_t k = kb + u;
-                    for (int c = 0; c < 3; ++c) shs[3 * u + c] = df_from_double(qv.shat[3 * k + c] * kappa_turns);
-                    cdf wl = cdf{Lb[k].x, Lb[k].y};
-                    if (wk) {
-                        const df w = df_from_double(wk[k]);
-                        wl = cdf{df_mul(wl.x, w), df_mul(wl.y, w)};
-                    }
-                    shl[u] = wl;
-                }
-                __syncthreads();
-                if (active)
-                    for (int kk = 0; kk < kn; ++kk) {
-                        df t = df_mul(shs[3 * kk], d[0]);
-                        t = df_add(t, df_mul(shs[3 * kk + 1], d[1]));
-                        t = df_add(t, df_mul(shs[3 * kk + 2], d[2]));
-                        acc = cdf_add(acc, cdf_mul(cis_turns(df_reduce(t), tab), shl[kk]));
-                    }
-            }
-            if (active) {
-                cxd& o = phis[(int64_t)(t0 + ti) * R_ + r];
-                o.x += df_to_double(acc.x);
-                o.y += df_to_double(acc.y);
-            }
         }
     }
 }
@@ -488,10 +422,10 @@ __global__ void __launch_bounds__(128) k_l2t_df_warp(
     const int32_t* __restrict__ pstart, const int32_t* __restrict__ pcount, const double* __restrict__ px,
     const double* __restrict__ py, const double* __restrict__ pz, const cx<df>* __restrict__ L, int R_,
     const cdf* __restrict__ cis_tab, cxd* __restrict__ out, double sign, const double* __restrict__ wk) {
-    __shared__ cdf tab[kCisTable];
+    __shared__ cdf tab[kCisTableBig];
     __shared__ df shs[4][kWarpTile * 3];
     __shared__ cdf shl[4][kWarpTile];
-    load_cis_table(tab, cis_tab);
+    for (int v = threadIdx.x; v < kCisTableBig; v += blockDim.x) tab[v] = cis_tab[v];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int u = blockIdx.x * 4 + warp;
@@ -511,7 +445,7 @@ __global__ void __launch_bounds__(128) k_l2t_df_warp(
     cdf* sl = shl[warp];
     for (int r = 0; r < R_; ++r) {
         const cx<df>* Lb = L + ((int64_t)b * R_ + r) * qv.K;
-        cdf acc = {{0, 0}, {0, 0}};
+        dfacc ax = {0.f, 0.f}, ay = {0.f, 0.f};
         for (int64_t kb = 0; kb < qv.K; kb += kWarpTile) {
             const int kn = (int)min((int64_t)kWarpTile, qv.K - kb);
             __syncwarp();
@@ -530,12 +464,12 @@ __global__ void __launch_bounds__(128) k_l2t_df_warp(
             __syncwarp();
             if (active)
                 for (int kk = 0; kk < kn; ++kk) {
-                    df t = df_mul(ss[3 * kk], d[0]);
-                    t = df_add(t, df_mul(ss[3 * kk + 1], d[1]));
-                    t = df_add(t, df_mul(ss[3 * kk + 2], d[2]));
-                    acc = cdf_add(acc, cdf_mul(cis_turns(df_reduce(t), tab), sl[kk]));
+                    const cdf e = cdf_mul(cis_turns_big(df_dot3(&ss[3 * kk], d), tab), sl[kk]);
+                    dfacc_add(ax, e.x);
+                    dfacc_add(ay, e.y);
                 }
         }
+        const cdf acc = {dfacc_get(ax), dfacc_get(ay)};
         if (active) {
             cxd& o = out[(int64_t)(t0 + ti) * R_ + r];
             o.x += df_to_double(acc.x);
@@ -546,13 +480,14 @@ __global__ void __launch_bounds__(128) k_l2t_df_warp(
 
 // mixed near field, one warp per (target box, 32-target chunk); float32 sums over tiles of
 // kWarpTile sources, flushed into float64
+template <int kRC>   // right-hand sides per pass: 1 (single RHS) or 4
 __global__ void __launch_bounds__(128) k_p2p_mixed_warp(
     const int2* __restrict__ units, int nunits, const int32_t* __restrict__ tstart,
     const int32_t* __restrict__ tcount, const int32_t* __restrict__ sstart, const int32_t* __restrict__ scount,
     const int32_t* __restrict__ noff, const int32_t* __restrict__ nidx, P2PMixedArgs a,
     const cxd* __restrict__ qs, cxd* __restrict__ phis, int R) {
     __shared__ float4 shp[4][kWarpTile], sho[4][kWarpTile];
-    __shared__ cxf shq[4][kWarpTile * 4];
+    __shared__ cxf shq[4][kWarpTile * kRC];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int u = blockIdx.x * 4 + warp;
     if (u >= nunits) return;
@@ -569,10 +504,10 @@ __global__ void __launch_bounds__(128) k_p2p_mixed_warp(
     float4* wp = shp[warp];
     float4* wo = sho[warp];
     cxf* wq = shq[warp];
-    for (int r0 = 0; r0 < R; r0 += 4) {
-        const int rn = min(4, R - r0);
-        cxd acc[4];
-        for (int r = 0; r < 4; ++r) acc[r] = mk<double>(0, 0);
+    for (int r0 = 0; r0 < R; r0 += kRC) {
+        const int rn = kRC == 1 ? 1 : min(kRC, R - r0);
+        cxd acc[kRC];
+        for (int r = 0; r < kRC; ++r) acc[r] = mk<double>(0, 0);
         for (int nb = noff[b]; nb < noff[b + 1]; ++nb) {
             const int s = nidx[nb];
             const int s0 = sstart[s], sc = scount[s];
@@ -583,12 +518,12 @@ __global__ void __launch_bounds__(128) k_p2p_mixed_warp(
                     const int j = s0 + sb + v;
                     wp[v] = a.spt[j];
                     wo[v] = a.sof[j];
-                    for (int r = 0; r < rn; ++r) wq[v * 4 + r] = cvt<float>(qs[(int64_t)j * R + r0 + r]);
+                    for (int r = 0; r < rn; ++r) wq[v * kRC + r] = cvt<float>(qs[(int64_t)j * R + r0 + r]);
                 }
                 __syncwarp();
                 if (!active) continue;
-                cxf tile[4];
-                for (int r = 0; r < 4; ++r) tile[r] = mk<float>(0, 0);
+                cxf tile[kRC];
+                for (int r = 0; r < kRC; ++r) tile[r] = mk<float>(0, 0);
                 for (int jj = 0; jj < sn; ++jj) {
                     const float4 sp = wp[jj], so = wo[jj];
                     const float Dx = gp.x - sp.x, Dy = gp.y - sp.y, Dz = gp.z - sp.z;  // exact
@@ -610,7 +545,9 @@ __global__ void __launch_bounds__(128) k_p2p_mixed_warp(
                     float sn_, cs_;
                     __sincosf(two_pi * f, &sn_, &cs_);
                     const cxf g = mk<float>(cs_ * rho, sn_ * rho);
-                    for (int r = 0; r < rn; ++r) mac(tile[r], g, wq[jj * 4 + r]);
+                    if (kRC == 1) mac(tile[0], g, wq[jj]);
+                    else
+                        for (int r = 0; r < rn; ++r) mac(tile[r], g, wq[jj * kRC + r]);
                 }
                 for (int r = 0; r < rn; ++r) {
                     acc[r].x += (double)tile[r].x;

@@ -17,8 +17,9 @@ def rel(a, b):
 
 def fp64_parity_tol(oracle_plan):
     """Parity bound between two float64 evaluations of the same plan: both sides round
-    an ill-conditioned quadrature sum (the planner's round-off estimate, which measured
-    errors exceed by up to ~25x in the evanescent regime), floor 1e-12."""
+    an ill-conditioned quadrature sum and compute their transfer tables independently;
+    measured element differences run up to ~50x the planner's round-off estimate (largest
+    level), so the bound is 256x that estimate, floor 1e-12."""
     from oracle import quadrature as oq
     est = max([lp.rounding_estimate(oq.U_FP64) for lp in oracle_plan.levels.values()] or [0.0])
-    return max(1e-12, 64.0 * est)
+    return max(1e-12, 256.0 * est)

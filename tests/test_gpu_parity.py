@@ -4,6 +4,8 @@ FP64 path: element-wise against the oracle FMM on the same plan integers (bound 
 arithmetic, floor 1e-12) and within eps of the direct sum.  Mixed path: within eps of
 the direct sum.  Full-size sphere: 1,000 sampled targets against the direct sum.
 """
+import zlib
+
 import numpy as np
 import pytest
 
@@ -22,7 +24,7 @@ def _cuda():
 
 
 def _case(name):
-    g = wl.rng(90 + hash(name) % 97)
+    g = wl.rng(90 + zlib.crc32(name.encode()) % 97)
     if name == "cube4k":                       # the 4,096-point uniform-cube workload
         x, _ = wl.points("cube4k_fp64")
         return x, x, 8 * np.pi, 1e-6, dict(depth=3, root=(0, 0, 0, 1.0))
