@@ -269,14 +269,14 @@ def main():
     if stage == "near_field":
         ops = 38.0 * info["p2p_pairs"]                   # float32 ops per pair of the mixed near field
         ach = ops / (stage_ms[stage] * 1e-3) / 1e9
-        roof.update(kernel="k_p2p_mixed", bound="alu", achieved=ach, peak=fp32_peak, unit="Gop/s",
+        roof.update(kernel="k_p2p_mixed_warp", bound="alu", achieved=ach, peak=fp32_peak, unit="Gop/s",
                     frac=ach / fp32_peak, unit_work="38 float32 ops per target-source pair",
                     peak_note="152 SMs x 128 FP32 lanes x median SM clock under load")
-    elif stage in ("s2m", "l2t") and lev.get("precision") == "fp64":
-        evals = float(lev["K"]) * len(t)
+    elif stage in ("s2m", "l2t") and lev.get("precision") == "df":
+        evals = float(lev["K"]) * (len(t) if stage == "l2t" else len(s))
         ops = 220.0 * evals                              # double-float ops per plane-wave evaluation
         ach = ops / (stage_ms[stage] * 1e-3) / 1e9
-        roof.update(kernel="k_%s_df" % stage, bound="alu", achieved=ach, peak=fp32_peak, unit="Gop/s",
+        roof.update(kernel="k_l2t_df_warp" if stage == "l2t" else "k_s2m_df", bound="alu", achieved=ach, peak=fp32_peak, unit="Gop/s",
                     frac=ach / fp32_peak, unit_work="220 float32 ops per (point, quadrature sample) in double-float",
                     peak_note="152 SMs x 128 FP32 lanes x median SM clock under load")
     elif stage in ("m2l", "m2m", "l2l"):

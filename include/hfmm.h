@@ -51,17 +51,19 @@ typedef enum {
 
 typedef enum { HFMM_C64 = 0, HFMM_C128 = 1 } hfmm_dtype;
 
-/* Precision policy.  FP64: every stage in float64.  MIXED: per level float32
- * where the planner's round-off estimate allows it, float64 elsewhere; near
- * field in float32 with compensated geometry and float64 tile accumulation. */
+/* Precision policy.  FP64: every stage in float64.  MIXED: per level float32 where the
+ * planner's round-off estimate allows it, double-float (float32 pairs, ~48 bits) elsewhere;
+ * near field in float32 with exact grid geometry and float64 tile accumulation when
+ * eps >= 1e-6, in float64 below. */
 typedef enum { HFMM_PREC_FP64 = 0, HFMM_PREC_MIXED = 1 } hfmm_precision;
 
 /* Level precisions reported by hfmm_query. */
-typedef enum { HFMM_LEVEL_FP64 = 0, HFMM_LEVEL_FP32 = 1 } hfmm_level_precision;
+typedef enum { HFMM_LEVEL_FP64 = 0, HFMM_LEVEL_FP32 = 1, HFMM_LEVEL_DF = 2 /* float32 pairs */ } hfmm_level_precision;
 
 typedef struct {
     /* alpha values tried for each level, in order (Section 3.3.3: |r| = alpha sqrt(3) a_l);
-     * a 0 ends the list.  Default {0.8, 0.6, 0, 0}. */
+     * a 0 ends the list.  Default {0.8, 0.6, 0, 0}; with this default, eps < 1e-7 uses
+     * {0.9, 0.8}.  Only levels with kappa * a_l >= 6 are ever active. */
     double alpha_ladder[4];
     /* per-level target eps_l = eps_scale * eps (default 0.25) */
     double eps_scale;

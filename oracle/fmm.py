@@ -14,18 +14,21 @@ Fourier quadratures of Section 3 with the re-quadrature of Section 3.4:
 * P2P   phi_i += sum_{j in N(b), R_ij > 0} q_j exp(i k R_ij) / R_ij
 
 Levels 2..L_f are active (L_f = deepest level the stability rule accepts, never
-deeper than the occupancy depth); when no level is accepted (L_f < 2) the whole
+deeper than the occupancy depth, and only levels whose boxes are about a wavelength
+or larger, k a_l >= 6: below that the Gegenbauer series converges only
+geometrically for pairs near opposite box corners); when no level is accepted (L_f < 2) the whole
 apply is the near field over the level-L_f neighbour lists, i.e. the direct sum.
 
 The stability rule (a reading; the paper only names the low-frequency breakdown
 and notes that a lower alpha gives a smaller quadrature):  for each level, top
-down, the first alpha of the ladder (0.8, 0.6) whose plan passes
+down, the first alpha of the ladder ((0.8, 0.6), or (0.9, 0.8) for eps < 1e-7)
+whose plan passes
     est(u) = u * k|r0| * sqrt(sum_{n<=l} (2n+1)|h_n(k|r0|)|^2) / sqrt(K) <= f_p * eps_l
 in one of the precisions the policy allows is taken (u = 2^-53, f = 1/16 for
-fp64; u = 2^-24, f = 1 for fp32; the policy 'fp64' allows fp64 only, 'mixed'
-prefers fp32 and falls back to fp64 for a given alpha, and a level never takes
-a lower precision than the level above it); the first level that no alpha
-passes ends the active levels.  est is the relative random round-off of the quadrature sum with
+fp64; u = 2^-48, f = 1/16 for double-float (float32 pairs); u = 2^-24, f = 1 for
+fp32; the policy 'fp64' allows fp64 only, 'mixed' tries fp32, then double-float, then
+fp64 for a given alpha, and a level never takes a lower precision than the level
+above it); the first level that no alpha passes ends the active levels.  est is the relative random round-off of the quadrature sum with
 the sphere rms of T (orthogonality of the P_n); f_fp64 = 1/16 because in the
 evanescent regime (l > k|r0|, the only place fp64 is ever limited) measured
 errors run 17-25x above est, while f_fp32 = 1 because in the propagating regime
@@ -39,21 +42,26 @@ from . import quadrature as qd
 from .direct import kernel_matrix
 from .tree import Tree, root_cube, occupancy_depth
 
-PRECISION_UNIT = {'fp64': qd.U_FP64, 'fp32': qd.U_FP32}
+PRECISION_UNIT = {'fp64': qd.U_FP64, 'df': qd.U_DF, 'fp32': qd.U_FP32}
 # acceptance factor of the stability rule per precision (see module docstring)
-PRECISION_FACTOR = {'fp64': 1.0 / 16.0, 'fp32': 1.0}
-ALPHA_LADDER = (0.8, 0.6)
+PRECISION_FACTOR = {'fp64': 1.0 / 16.0, 'df': 1.0 / 16.0, 'fp32': 1.0}
+MIN_KA = 6.0
+
+
+def alpha_ladder(eps):
+    """Default alpha ladder: (0.8, 0.6), or (0.9, 0.8) when eps < 1e-7."""
+    return (0.9, 0.8) if eps < 1e-7 else (0.8, 0.6)
 
 
 def level_precisions(policy):
     """Precisions a level may use under a plan policy, in order of preference."""
-    return {'fp64': ('fp64',), 'mixed': ('fp32', 'fp64')}[policy]
+    return {'fp64': ('fp64',), 'mixed': ('fp32', 'df', 'fp64')}[policy]
 
 
 class Plan:
     """Everything the apply needs: tree to depth L_f, per-level quadrature, transfer tables."""
 
-    def __init__(self, sources, targets, kappa, eps, alphas=ALPHA_LADDER, max_leaf=64, depth=0,
+    def __init__(self, sources, targets, kappa, eps, alphas=None, max_leaf=64, depth=0,
                  root=None, precision='fp64', eps_scale=0.25):
         self.sources = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 3)
         self.targets = np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 3)
@@ -70,7 +78,11 @@ class Plan:
         self.level_precision = {}
         lf = 1
         allowed = list(level_precisions(precision))
+        if alphas is None:
+            alphas = alpha_ladder(self.eps)
         for l in range(2, dmax + 1):
+            if self.kappa * side / float(2 ** l) < MIN_KA:
+                break
             chosen = None
             for alpha in alphas:
                 lp = qd.LevelPlan(self.kappa, side / float(2 ** l), self.eps_l, alpha)

@@ -41,6 +41,7 @@ FOUR_PI2 = 4.0 * np.pi * np.pi
 
 # unit round-offs used by the stability rule
 U_FP64 = 2.0 ** -53
+U_DF = 2.0 ** -48      # float32 pairs (double-float)
 U_FP32 = 2.0 ** -24
 
 

@@ -68,6 +68,9 @@ struct Requad {
 struct hfmm_plan_s {
     HostPlan hp;
     int device = -1;
+    // the float32 near field carries ~1e-7 relative error: the mixed policy uses it only for
+    // eps >= 1e-6 and the float64 near field below
+    bool near_fp32 = false;
     int rmax = 1;
     std::vector<void*> allocs;
     // leaf / points
@@ -123,7 +126,7 @@ hfmm_status upload(hfmm_plan_s* p, T** ptr, const std::vector<T>& host) {
         if (s_ != HFMM_OK) return s_;   \
     } while (0)
 
-size_t cx_bytes(int prec) { return prec == kFP64 ? sizeof(cxd) : sizeof(cxf); }
+size_t cx_bytes(int prec) { return prec == kFP32 ? sizeof(cxf) : sizeof(cxd); }
 
 hfmm_status upload_level(hfmm_plan_s* P, int l) {
     HostPlan& hp = P->hp;
@@ -191,8 +194,7 @@ hfmm_status upload_level(hfmm_plan_s* P, int l) {
     std::vector<int32_t> slot_t(kNumTransfer, 0);
     for (int v = 0; v < kNumTransfer; ++v) slot_t[v] = slot[kNumTransfer - 1 - v];
     TRY(upload(P, &d.tslot_t, slot_t));
-    const bool store_df = d.prec == kFP64 && hp.precision == HFMM_PREC_MIXED;
-    if (store_df) {
+    if (d.prec == kDF) {
         std::vector<cx<df>> t((size_t)ns * q.K);
         for (int v = 0; v < kNumTransfer; ++v)
             if (!lp.table[v].empty())
@@ -534,18 +536,23 @@ void launch_m2l(hfmm_plan_s* P, int l, int R, cudaStream_t st, bool transposed) 
 // type codes of a level's signatures and arithmetic: 0 float, 1 double, 2 double-float
 // (float64 levels of the mixed policy store and compute in double-float pairs)
 int store_code(hfmm_plan_s* P, int l) {
-    if (P->lev[l].prec != kFP64) return 0;
-    return P->hp.precision == HFMM_PREC_MIXED ? 2 : 1;
+    const int p = P->lev[l].prec;
+    return p == kFP32 ? 0 : (p == kDF ? 2 : 1);
 }
 int compute_code(hfmm_plan_s* P, int l) { return store_code(P, l); }
 
 template <typename Fn>
 bool dispatch3(int sin, int cc, int sout, Fn fn) {
+    // precision only grows with depth (float32 < double-float < float64)
     if (sin == 1 && cc == 1 && sout == 1) fn(double{}, double{}, double{});
     else if (sin == 2 && cc == 2 && sout == 2) fn(df{}, df{}, df{});
-    else if (sin == 2 && cc == 0 && sout == 0) fn(df{}, float{}, float{});
     else if (sin == 0 && cc == 0 && sout == 0) fn(float{}, float{}, float{});
+    else if (sin == 2 && cc == 0 && sout == 0) fn(df{}, float{}, float{});
+    else if (sin == 1 && cc == 2 && sout == 2) fn(double{}, df{}, df{});
+    else if (sin == 1 && cc == 0 && sout == 0) fn(double{}, float{}, float{});
     else if (sin == 0 && cc == 2 && sout == 2) fn(float{}, df{}, df{});
+    else if (sin == 0 && cc == 1 && sout == 1) fn(float{}, double{}, double{});
+    else if (sin == 2 && cc == 1 && sout == 1) fn(df{}, double{}, double{});
     else return false;
     return true;
 }
@@ -577,8 +584,8 @@ void run_m2l(hfmm_plan_s* P, int l, int R, cudaStream_t st, bool transposed) {
     else launch_m2l<df, df>(P, l, R, st, transposed);
 }
 
-// float64 levels of the mixed policy evaluate their plane waves in double-float
-bool use_df(hfmm_plan_s* P, int l) { return P->hp.precision == HFMM_PREC_MIXED && P->lev[l].prec == kFP64; }
+// double-float levels evaluate their plane waves in double-float
+bool use_df(hfmm_plan_s* P, int l) { return P->lev[l].prec == kDF; }
 
 // points -> signature at the leaf level: S2M (sources, sign +1) or transposed L2T
 // (targets, sign -1, weighted)
@@ -641,8 +648,8 @@ template <typename Mark>
 void transposed_far_chain(hfmm_plan_s* P, int R, cudaStream_t st, Mark mark) {
     const int lf = P->hp.lf;
     // transposed L2T: weighted plane-wave sums of the targets into Lambda_L at the leaf level
-    if (P->lev[lf].prec == kFP64) launch_s2m<double>(P, R, st, true);
-    else launch_s2m<float>(P, R, st, true);
+    if (P->lev[lf].prec == kFP32) launch_s2m<float>(P, R, st, true);
+    else launch_s2m<double>(P, R, st, true);
     mark(3);
     // transposed L2L, leaf level up to level 2
     for (int l = lf - 1; l >= 2; --l) run_l2l_t(P, l, R, st);
@@ -706,6 +713,12 @@ hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, 
     if (opt.precision != HFMM_PREC_FP64 && opt.precision != HFMM_PREC_MIXED)
         return fail(HFMM_ERR_ARG, "unknown precision policy");
     std::vector<double> alphas;
+    // default ladder: (0.8, 0.6), or (0.9, 0.8) below eps = 1e-7, where the few terms that
+    // l(0.8) keeps beyond k|r| of a corner pair no longer reach eps
+    if (opt.alpha_ladder[0] == 0.8 && opt.alpha_ladder[1] == 0.6 && opt.alpha_ladder[2] == 0.0 && eps < 1e-7) {
+        opt.alpha_ladder[0] = 0.9;
+        opt.alpha_ladder[1] = 0.8;
+    }
     for (int i = 0; i < 4 && opt.alpha_ladder[i] != 0.0; ++i) {
         if (!(opt.alpha_ladder[i] >= 0.5 && opt.alpha_ladder[i] <= 1.0))
             return fail(HFMM_ERR_ARG, "alpha values must lie in [0.5, 1]");
@@ -764,6 +777,7 @@ hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, 
             }
     P->rmax = opt.max_rhs;
     P->device = opt.device;
+    P->near_fp32 = opt.precision == HFMM_PREC_MIXED && eps >= 1e-6;
     if (opt.device >= 0) {
         hfmm_status s = upload_plan(P);
         if (s != HFMM_OK) {
@@ -818,7 +832,7 @@ hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_d
     mark(1);
     const int nleaf = (int)hp.levels[lf].nbox();
     const dim3 g_fwd(nleaf, nblk(P->max_tgt_leaf, kP2PThreads));
-    if (hp.precision == HFMM_PREC_MIXED) {
+    if (P->near_fp32) {
         if (P->ntunits > 0)
         {
             if (R == 1)
@@ -837,8 +851,8 @@ hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_d
                                                   P->phis, R, hp.kappa);
     mark(2);
     if (lf >= 2) {
-        if (P->lev[lf].prec == kFP64) launch_s2m<double>(P, R, st);
-        else launch_s2m<float>(P, R, st);
+        if (P->lev[lf].prec == kFP32) launch_s2m<float>(P, R, st);
+        else launch_s2m<double>(P, R, st);
         mark(3);
         for (int l = lf; l >= 3; --l) run_up(P, l, R, st);
         mark(4);
@@ -846,8 +860,8 @@ hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_d
         mark(5);
         for (int l = 2; l < lf; ++l) run_down(P, l, R, st);
         mark(6);
-        if (P->lev[lf].prec == kFP64) launch_l2t<double>(P, R, st);
-        else launch_l2t<float>(P, R, st);
+        if (P->lev[lf].prec == kFP32) launch_l2t<float>(P, R, st);
+        else launch_l2t<double>(P, R, st);
         mark(7);
     } else {
         for (int i = 3; i <= 7; ++i) mark(i);
@@ -886,7 +900,7 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t P, const void* w, void* out, int nrhs
     // transposed near field: source boxes gather the targets of their neighbours
     const int nleaf = (int)hp.levels[lf].nbox();
     const dim3 g_adj(nleaf, nblk(P->max_src_leaf, kP2PThreads));
-    if (hp.precision == HFMM_PREC_MIXED) {
+    if (P->near_fp32) {
         P2PMixedArgs a = P->mixed;
         std::swap(a.tpt, a.spt);
         std::swap(a.tof, a.sof);
@@ -910,8 +924,8 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t P, const void* w, void* out, int nrhs
     if (lf >= 2) {
         transposed_far_chain(P, R, st, mark);
         // transposed S2M: plane-wave sums back onto the sources
-        if (P->lev[lf].prec == kFP64) launch_l2t<double>(P, R, st, true);
-        else launch_l2t<float>(P, R, st, true);
+        if (P->lev[lf].prec == kFP32) launch_l2t<float>(P, R, st, true);
+        else launch_l2t<double>(P, R, st, true);
         mark(7);
     } else {
         for (int i = 3; i <= 7; ++i) mark(i);
@@ -996,7 +1010,7 @@ hfmm_status hfmm_query(hfmm_plan_t P, hfmm_info* info) {
             info->level_ell[l] = lp.quad.ell;
             info->level_ntheta[l] = lp.quad.ntheta;
             info->level_K[l] = lp.quad.K;
-            info->level_precision[l] = lp.prec == kFP64 ? HFMM_LEVEL_FP64 : HFMM_LEVEL_FP32;
+            info->level_precision[l] = lp.prec == kFP32 ? HFMM_LEVEL_FP32 : (lp.prec == kDF ? HFMM_LEVEL_DF : HFMM_LEVEL_FP64);
             info->level_alpha[l] = lp.alpha;
             info->level_round_est[l] = lp.est;
             info->level_ilist_total[l] = (int)hp.levels[l].iidx.size();

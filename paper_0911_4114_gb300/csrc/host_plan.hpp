@@ -15,7 +15,8 @@ constexpr int kMaxLevels = 21;
 constexpr int kTreeBits = 20;        // deepest depth the tree code supports
 constexpr int kNumTransfer = 343;    // 7^3 slots, 316 used (one buffer box)
 
-enum LevelPrec { kFP64 = 0, kFP32 = 1 };
+// level arithmetic: float64, float32, or double-float (float32 pairs, mixed policy only)
+enum LevelPrec { kFP64 = 0, kFP32 = 1, kDF = 2 };
 
 // Quadrature of one level: rows n = 0..ntheta/2 with nphi[n] points each (Section 3.4's K).
 struct Quadrature {

@@ -139,85 +139,6 @@ struct P2PMixedArgs {
     double inv_unit;       // 2^12 / side: 1 / (grid unit in length)
 };
 
-__global__ void k_p2p_mixed(int nbox, const int32_t* __restrict__ tstart, const int32_t* __restrict__ tcount,
-                            const int32_t* __restrict__ sstart, const int32_t* __restrict__ scount,
-                            const int32_t* __restrict__ noff, const int32_t* __restrict__ nidx,
-                            P2PMixedArgs a, const cxd* __restrict__ qs, cxd* __restrict__ phis, int R) {
-    __shared__ float4 shp[kP2PTile], sho[kP2PTile];
-    __shared__ cxf shq[kP2PTile * 4];
-    const int b = blockIdx.x;
-    if (b >= nbox) return;
-    const int t0 = tstart[b], tc = tcount[b];
-    if ((int)blockIdx.y * kP2PThreads >= tc) return;
-    const float two_pi = 6.28318530717958647692f;
-    for (int r0 = 0; r0 < R; r0 += 4) {
-        const int rn = min(4, R - r0);
-        {
-            const int tb = blockIdx.y * kP2PThreads;
-            const int ti = tb + threadIdx.x;
-            const bool active = ti < tc;
-            float4 gp = make_float4(0, 0, 0, 0), op = gp;
-            if (active) {
-                gp = a.tpt[t0 + ti];
-                op = a.tof[t0 + ti];
-            }
-            cxd acc[4];
-            for (int r = 0; r < 4; ++r) acc[r] = mk<double>(0, 0);
-            for (int nb = noff[b]; nb < noff[b + 1]; ++nb) {
-                const int s = nidx[nb];
-                const int s0 = sstart[s], sc = scount[s];
-                for (int sb = 0; sb < sc; sb += kP2PTile) {
-                    const int sn = min(kP2PTile, sc - sb);
-                    __syncthreads();
-                    for (int u = threadIdx.x; u < sn; u += kP2PThreads) {
-                        const int j = s0 + sb + u;
-                        shp[u] = a.spt[j];
-                        sho[u] = a.sof[j];
-                        for (int r = 0; r < rn; ++r) shq[u * 4 + r] = cvt<float>(qs[(int64_t)j * R + r0 + r]);
-                    }
-                    __syncthreads();
-                    if (active) {
-                        cxf tile[4];
-                        for (int r = 0; r < 4; ++r) tile[r] = mk<float>(0, 0);
-                        for (int jj = 0; jj < sn; ++jj) {
-                            const float4 sp = shp[jj], so = sho[jj];
-                            const float Dx = gp.x - sp.x, Dy = gp.y - sp.y, Dz = gp.z - sp.z;  // exact
-                            const float ex = op.x - so.x, ey = op.y - so.y, ez = op.z - so.z;
-                            const float A = fmaf(Dx, Dx, fmaf(Dy, Dy, Dz * Dz));           // exact
-                            const float B = fmaf(ex, fmaf(2.0f, Dx, ex),
-                                                 fmaf(ey, fmaf(2.0f, Dy, ey), ez * fmaf(2.0f, Dz, ez)));
-                            const float s2 = A + B;
-                            if (s2 <= 0.0f) continue;
-                            const float rho = rsqrtf(s2);
-                            const float r0f = s2 * rho;
-                            const float e = fmaf(-r0f, r0f, A);
-                            const float c = (e + B) * (0.5f * rho);
-                            // phase in turns: tau * (r0f + c), product error kept by fma
-                            const float th = a.tau_hi * r0f;
-                            float te = fmaf(a.tau_hi, r0f, -th);
-                            te = fmaf(a.tau_hi, c, te);
-                            te = fmaf(a.tau_lo, r0f, te);
-                            const float nt = rintf(th);
-                            const float f = (th - nt) + te;
-                            float sn_, cs_;
-                            __sincosf(two_pi * f, &sn_, &cs_);
-                            const cxf g = mk<float>(cs_ * rho, sn_ * rho);
-                            for (int r = 0; r < rn; ++r) mac(tile[r], g, shq[jj * 4 + r]);
-                        }
-                        for (int r = 0; r < rn; ++r) {
-                            acc[r].x += (double)tile[r].x;
-                            acc[r].y += (double)tile[r].y;
-                        }
-                    }
-                }
-            }
-            if (active)
-                for (int r = 0; r < rn; ++r)
-                    phis[(int64_t)(t0 + ti) * R + r0 + r] = a.inv_unit * acc[r];
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------
 // S2M: M_b(s_k) = sum_{j in b} q_j exp(i k s_k . (y_j - c_b)) at the leaf level
 // thread per (box, k); sources of the box staged through shared memory

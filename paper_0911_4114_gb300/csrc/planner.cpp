@@ -30,6 +30,7 @@ namespace hfmm {
 static const double kPi = 3.14159265358979323846;
 static const double kTwoPi = 2.0 * kPi;
 static const double kFourPi2 = 4.0 * kPi * kPi;
+static const double kMinKa = 6.0;
 
 void Quadrature::finalize() {
     off.assign(nphi.size() + 1, 0);
@@ -596,17 +597,19 @@ std::string build_host_plan(HostPlan& hp) {
     // active levels: alpha ladder outer, precision inner, precision never decreasing with depth
     hp.eps_l = hp.eps_scale * hp.eps;
     hp.lp.assign(kMaxLevels, LevelPlan());
-    std::vector<int> allowed = (hp.precision == 1) ? std::vector<int>{kFP32, kFP64}
+    std::vector<int> allowed = (hp.precision == 1) ? std::vector<int>{kFP32, kDF, kFP64}
                                                    : std::vector<int>{kFP64};
     int lf = 1;
     for (int l = 2; l <= hp.occ_depth && l < kMaxLevels; ++l) {
+        // only boxes of about a wavelength or larger (k a_l >= 6) use the diagonal form
+        if (hp.kappa * (hp.side / (double)(1u << l)) < kMinKa) break;
         bool ok = false;
         for (double alpha : hp.alphas) {
             LevelPlan cand;
             plan_level(hp.kappa, hp.side / (double)(1u << l), hp.eps_l, alpha, cand);
             for (int p : allowed) {
-                double u = (p == kFP64) ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
-                double f = (p == kFP64) ? 1.0 / 16.0 : 1.0;
+                const double u = std::ldexp(1.0, p == kFP32 ? -24 : (p == kDF ? -48 : -53));
+                const double f = (p == kFP32) ? 1.0 : 1.0 / 16.0;
                 double est = round_off_estimate(cand.quad.ell, hp.kappa, cand.r0, cand.quad.K, u);
                 if (est <= hp.eps_l * f) {
                     cand.prec = p;

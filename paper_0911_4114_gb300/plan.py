@@ -10,12 +10,13 @@ import numpy as np
 from . import _native as nat
 
 
-def make_options(precision="fp64", alphas=(0.8, 0.6), eps_scale=0.25, max_leaf=64, depth=0, root=None,
+def make_options(precision="fp64", alphas=None, eps_scale=0.25, max_leaf=64, depth=0, root=None,
                  max_rhs=1, device=0):
     opt = nat.Options()
     nat.lib().hfmm_default_options(ctypes.byref(opt))
-    for i in range(4):
-        opt.alpha_ladder[i] = alphas[i] if i < len(alphas) else 0.0
+    if alphas is not None:              # None keeps the library default ladder
+        for i in range(4):
+            opt.alpha_ladder[i] = alphas[i] if i < len(alphas) else 0.0
     opt.eps_scale = eps_scale
     opt.max_leaf = max_leaf
     opt.depth = depth
@@ -37,7 +38,7 @@ class FmmPlan:
     (queries only).
     """
 
-    def __init__(self, sources, targets, kappa, eps, precision="fp64", alphas=(0.8, 0.6),
+    def __init__(self, sources, targets, kappa, eps, precision="fp64", alphas=None,
                  eps_scale=0.25, max_leaf=64, depth=0, root=None, max_rhs=1, device=0):
         L = nat.lib()
         src = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 3)
@@ -140,7 +141,7 @@ class FmmPlan:
         for l in range(2, lf + 1):
             levels[l] = dict(nbox=inf.level_nbox[l], ell=inf.level_ell[l], ntheta=inf.level_ntheta[l],
                              K=inf.level_K[l], alpha=inf.level_alpha[l],
-                             precision="fp64" if inf.level_precision[l] == 0 else "fp32",
+                             precision={0: "fp64", 1: "fp32", 2: "df"}[inf.level_precision[l]],
                              round_est=inf.level_round_est[l], ilist_total=inf.level_ilist_total[l])
         return dict(ns=inf.ns, nt=inf.nt, kappa=inf.kappa, eps=inf.eps, occupancy_depth=inf.occupancy_depth,
                     lf=lf, p2p_pairs=inf.p2p_pairs, nbox=[inf.level_nbox[l] for l in range(lf + 1)],

@@ -19,6 +19,7 @@ CASES = {
     "cube_two_levels": dict(n=1200, kind="cube", kappa=60.0, eps=1e-6, depth=3, root=(0, 0, 0, 1.0)),
     "sphere_auto_depth": dict(n=3000, kind="sphere", kappa=24.0, eps=1e-5, depth=0, root=None, max_leaf=32),
     "two_spheres": dict(n=800, kind="two", kappa=12.0, eps=1e-6, depth=0, root=None, max_leaf=16),
+    "sphere_tight_eps": dict(n=3000, kind="sphere", kappa=60.0, eps=1e-9, depth=0, root=None, max_leaf=16),
 }
 
 
@@ -60,6 +61,8 @@ def test_levels_and_quadrature_integers(pair):
             li = info["levels"][l]
             assert (li["ell"], li["ntheta"], li["K"]) == (lp.ell, lp.ntheta, lp.K), (name, prec, l)
             assert li["alpha"] == lp.alpha
+            assert li["alpha"] in ofmm.alpha_ladder(orc.eps)
+            assert orc.kappa * lp.a >= ofmm.MIN_KA       # only boxes of about a wavelength or more
             assert li["precision"] == orc.level_precision[l]
             assert np.array_equal(lib.debug_get("NPHI", l), lp.nphi)
             assert li["round_est"] == pytest.approx(lp.rounding_estimate(
