@@ -253,8 +253,7 @@ def main():
                "kind": "oracle", "sample": f"float64 direct sum over all 262,144 sources for {ORACLE_TARGETS} "
                                            f"seeded targets ({secs:.1f} s)"}
 
-    # roofline of the dominant kernel (work per unit: the design doc section 6)
-    stage = max(stage_ms, key=stage_ms.get)
+    # rooflines per stage; the top-level entry is the dominant stage's
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -262,36 +261,53 @@ def main():
         pass
     sm_clock = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * sm_clock * 1e6 / 1e9          # FP32-pipe ops/s (Gop/s)
-    lf = info["lf"]
-    lev = info["levels"].get(lf, {})
-    roof = {"kernel": stage, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
-            "traffic": None, "stage_ms": stage_ms[stage]}
-    if stage == "near_field":
-        ops = 38.0 * info["p2p_pairs"]                   # float32 ops per pair of the mixed near field
-        ach = ops / (stage_ms[stage] * 1e-3) / 1e9
-        roof.update(kernel="k_p2p_mixed_warp", bound="alu", achieved=ach, peak=fp32_peak, unit="Gop/s",
-                    frac=ach / fp32_peak, unit_work="38 float32 ops per target-source pair",
-                    peak_note="152 SMs x 128 FP32 lanes x median SM clock under load")
-    elif stage in ("s2m", "l2t") and lev.get("precision") == "df":
-        evals = float(lev["K"]) * (len(t) if stage == "l2t" else len(s))
-        ops = 220.0 * evals                              # double-float ops per plane-wave evaluation
-        ach = ops / (stage_ms[stage] * 1e-3) / 1e9
-        roof.update(kernel="k_l2t_df_warp" if stage == "l2t" else "k_s2m_df", bound="alu", achieved=ach, peak=fp32_peak, unit="Gop/s",
-                    frac=ach / fp32_peak, unit_work="220 float32 ops per (point, quadrature sample) in double-float",
-                    peak_note="152 SMs x 128 FP32 lanes x median SM clock under load")
-    elif stage in ("m2l", "m2m", "l2l"):
-        hbm = peaks.get("hbm_gbs", 6800.0)
-        b = 16.0
-        tot = 0.0
-        for l, v in info["levels"].items():
-            if stage == "m2l":
-                tot += (2.0 * v["nbox"] * v["K"] + 316.0 * v["K"]) * b
-            elif int(l) > 2:
-                up = info["levels"][int(l) - 1]
-                tot += (v["nbox"] * v["K"] + up["nbox"] * up["K"]) * b
-        ach = tot / (stage_ms[stage] * 1e-3) / 1e9
-        roof.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
-                    unit_work="algorithmic signature bytes (each read and written once)")
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    levels = {int(l): v for l, v in info["levels"].items()}
+    lev = levels.get(info["lf"], {})
+    sample_bytes = {"fp32": 8.0, "df": 16.0, "fp64": 16.0}
+    alu_note = "152 SMs x 128 FP32 lanes x median SM clock under load"
+
+    def stage_roof(stage):
+        ms = stage_ms[stage]
+        if ms <= 0.0:
+            return None
+        if stage == "near_field" and info["near_precision"] == "fp32":
+            ops = 38.0 * info["p2p_pairs"]               # float32 ops per pair of the mixed near field
+            return dict(kernel="k_p2p_mixed_warp", bound="alu", achieved=ops / (ms * 1e-3) / 1e9,
+                        peak=fp32_peak, unit="Gop/s", unit_work="38 float32 ops per target-source pair",
+                        peak_note=alu_note)
+        if stage in ("s2m", "l2t") and lev.get("precision") == "df":
+            units = float(lev["K"]) / 2 * (len(t) if stage == "l2t" else len(s))
+            ops = 205.0 * units                          # double-float ops per (point, antipodal pair)
+            return dict(kernel="k_l2t_df_warp" if stage == "l2t" else "k_s2m_df", bound="alu",
+                        achieved=ops / (ms * 1e-3) / 1e9, peak=fp32_peak, unit="Gop/s",
+                        unit_work="205 float32 ops per (point, antipodal sample pair) in double-float",
+                        peak_note=alu_note)
+        if stage in ("m2l", "m2m", "l2l"):
+            tot = 0.0
+            for l, v in levels.items():
+                b = sample_bytes[v["precision"]]
+                if stage == "m2l":
+                    tot += (2.0 * v["nbox"] * v["K"] + 316.0 * v["K"]) * b
+                elif l > 2:
+                    up = levels[l - 1]
+                    tot += v["nbox"] * v["K"] * b + up["nbox"] * up["K"] * sample_bytes[up["precision"]]
+            return dict(kernel={"m2l": "k_m2l", "m2m": "k_requad_* (M2M)", "l2l": "k_requad_* (L2L)"}[stage],
+                        bound="hbm", achieved=tot / (ms * 1e-3) / 1e9, peak=hbm, unit="GB/s",
+                        unit_work="algorithmic signature bytes (each read and written once)")
+        return None
+
+    roof_stages = {}
+    for st_name in stage_ms:
+        r_ = stage_roof(st_name)
+        if r_ is not None:
+            r_["frac"] = r_["achieved"] / r_["peak"]
+            r_["stage_ms"] = stage_ms[st_name]
+            roof_stages[st_name] = r_
+    stage = max(stage_ms, key=stage_ms.get)
+    roof = dict(roof_stages.get(stage) or {"kernel": stage, "bound": None, "achieved": None, "peak": None,
+                                          "unit": None, "frac": None, "stage_ms": stage_ms[stage]})
+    roof["traffic"] = None
     roof["peak_source"] = "of measured" if peaks else "of fallback"
 
     nt = len(t)
@@ -311,7 +327,9 @@ def main():
             "stage_ms": stage_ms, "plan_seconds": plans["mixed"].plan_seconds,
             "e2e": {"value": world * nt / (e2e * 1e-3) / 1e6, "unit": "Mpoints*RHS/s",
                     "h2d_bytes_per_step": int(qh.numel() * 8), "d2h_bytes_per_step": int(ph.numel() * 8)},
-            "roofline": roof, "cpu_baseline": cpu, "gpu_launches": count_launches(info) * args.steps,
+            "roofline": roof, "roofline_stages": {k: {kk: v[kk] for kk in ("kernel", "bound", "achieved", "unit", "frac")}
+                                                  for k, v in roof_stages.items()},
+            "cpu_baseline": cpu, "gpu_launches": count_launches(info) * args.steps,
             "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -102,6 +102,9 @@ typedef struct {
      * 0 permute-in, 1 near field, 2 S2M, 3 M2M, 4 M2L, 5 L2L, 6 L2T, 7 permute-out */
     double stage_ms[HFMM_N_STAGES];
     int64_t workspace_bytes;
+    /* arithmetic of the near field: HFMM_LEVEL_FP32 (float32 exact-grid form, mixed policy
+     * with eps >= 1e-6) or HFMM_LEVEL_FP64 */
+    int near_precision;
 } hfmm_info;
 
 /* Fill *opt with the defaults listed above. */

@@ -47,7 +47,8 @@ class Info(ctypes.Structure):
                 ("level_precision", ctypes.c_int * MAX_LEVELS), ("level_alpha", ctypes.c_double * MAX_LEVELS),
                 ("level_round_est", ctypes.c_double * MAX_LEVELS),
                 ("level_ilist_total", ctypes.c_int * MAX_LEVELS),
-                ("stage_ms", ctypes.c_double * N_STAGES), ("workspace_bytes", ctypes.c_int64)]
+                ("stage_ms", ctypes.c_double * N_STAGES), ("workspace_bytes", ctypes.c_int64),
+                ("near_precision", ctypes.c_int)]
 
 
 _lib = None

@@ -161,7 +161,21 @@ hfmm_status upload_level(hfmm_plan_s* P, int l) {
     TRY(upload(P, &off, q.off));
     TRY(upload(P, &dshat, shat));
     TRY(upload(P, &dw, w));
-    d.qv = QuadView{q.ntheta, half + 1, q.K, nphi, off, dshat, dw};
+    // antipodal pairs: (n, m) with n < N_theta/2 - n, or the middle row's first half
+    std::vector<int2> pairs;
+    pairs.reserve(q.K / 2);
+    for (int n = 0; 2 * n <= half; ++n) {
+        const int np = q.nphi[n];
+        if (np % 2 != 0 || q.nphi[half - n] != np)
+            return fail(HFMM_ERR_STATE, "quadrature grid is not antipodally symmetric");
+        const int mend = (2 * n == half) ? np / 2 : np;
+        for (int m = 0; m < mend; ++m)
+            pairs.push_back(make_int2((int)(q.off[n] + m), (int)(q.off[half - n] + (m + np / 2) % np)));
+    }
+    if ((int64_t)pairs.size() * 2 != q.K) return fail(HFMM_ERR_STATE, "antipodal pairs do not cover the grid");
+    int2* dpair;
+    TRY(upload(P, &dpair, pairs));
+    d.qv = QuadView{q.ntheta, half + 1, q.K, nphi, off, dshat, dw, dpair, (int64_t)pairs.size()};
     {
         std::vector<df> sd(3 * q.K);
         const double kt = hp.kappa / (2.0 * 3.14159265358979323846);
@@ -603,7 +617,7 @@ void launch_s2m(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false)
     const double sign = transposed ? -1.0 : 1.0;
     const double* wk = transposed ? d.qv.w : nullptr;
     const double kt = P->hp.kappa / (2.0 * 3.14159265358979323846);
-    dim3 grid(d.nbox, nblk(d.K, kS2MThreads));
+    dim3 grid(d.nbox, nblk(d.qv.npair, kS2MThreads));
     if (std::is_same<T, double>::value && use_df(P, lf)) {
         k_s2m_df<<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt, P->cis_tab,
                                                (cx<df>*)out, sign, wk);
@@ -1017,6 +1031,7 @@ hfmm_status hfmm_query(hfmm_plan_t P, hfmm_info* info) {
         }
     }
     info->workspace_bytes = P->workspace;
+    info->near_precision = P->near_fp32 ? HFMM_LEVEL_FP32 : HFMM_LEVEL_FP64;
     if (P->ev_recorded) {
         if (cudaEventSynchronize(P->ev[HFMM_N_STAGES]) != cudaSuccess)
             return fail(HFMM_ERR_CUDA, "event synchronize failed");

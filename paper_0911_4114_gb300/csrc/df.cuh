@@ -90,6 +90,17 @@ __device__ __forceinline__ void dfacc_add(dfacc& a, df v) {
     a.lo = __fadd_rn(a.lo, __fadd_rn(s.lo, v.lo));
 }
 __device__ __forceinline__ df dfacc_get(dfacc a) { return df_fast_sum(a.hi, a.lo); }
+// a += x * y: Dekker's product (leading part exact by FMA) summed into the accumulator
+// without renormalising the product first
+__device__ __forceinline__ void dfacc_add_prod(dfacc& a, df x, df y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    const df s = df_two_sum(a.hi, p);
+    a.hi = s.hi;
+    a.lo = __fadd_rn(a.lo, __fadd_rn(s.lo, e));
+}
 
 constexpr int kCisTableBig = 1024;
 
@@ -112,7 +123,7 @@ __device__ __forceinline__ df df_dot3(const df* s, const df* d) {
 // |x| <= pi / 1024 (cos to y^2/24, sin to x y^2/120; dropped terms < 2^-58)
 __device__ __forceinline__ cdf cis_turns_big(df t, const cdf* tab) {
     const float jf = rintf(__fmul_rn(t.hi, (float)kCisTableBig));
-    df rr = df_fast_sum(__fsub_rn(t.hi, __fdiv_rn(jf, (float)kCisTableBig)), t.lo);
+    df rr = df_fast_sum(__fsub_rn(t.hi, __fmul_rn(jf, 1.0f / (float)kCisTableBig)), t.lo);  // exact
     const df two_pi = {6.2831854820251465f, -1.7484555314695172e-07f};
     df x = df_mul(rr, two_pi);
     df y = df_mul(x, x);

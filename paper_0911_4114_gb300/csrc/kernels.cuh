@@ -18,6 +18,11 @@ struct QuadView {
     const int64_t* off;  // nrows + 1
     const double* shat;  // (K, 3)
     const double* w;     // (K) folded quadrature weights
+    // antipodal pairs (k, k'): s_k' = -s_k, so exp(i k s_k' . d) = conj(exp(i k s_k . d)).
+    // Row n mirrors row N_theta/2 - n with the same N_phi (a multiple of 4), so sample
+    // (n, m) pairs with (N_theta/2 - n, m + N_phi/2); npair = K / 2.
+    const int2* pair;
+    int64_t npair;
 };
 
 struct BoxView {
@@ -170,6 +175,8 @@ __device__ __forceinline__ double turns(double kappa_turns, const double* s, dou
 
 // Points to signature: M_b(s_k) = w_k sum_{j in b} exp(i k s_k . sign (p_j - c_b)) q_j.
 // S2M: sources, sign +1, no weights.  Transposed L2T: targets, sign -1, quadrature weights.
+// One thread per antipodal pair (k, k'): with E = C + iS the plane wave of s_k, it sums
+// U = sum q C and V = sum q S; then M(k) = U + iV and M(k') = U - iV.
 template <typename R>
 __global__ void k_s2m(BoxView bx, QuadView qv, const int32_t* __restrict__ sstart,
                       const int32_t* __restrict__ scount, const double* __restrict__ sx,
@@ -179,18 +186,20 @@ __global__ void k_s2m(BoxView bx, QuadView qv, const int32_t* __restrict__ sstar
     __shared__ double shd[kS2MThreads * 3];
     __shared__ cxd shq[kS2MThreads];
     const int b = blockIdx.x;
-    const int64_t k = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
-    const bool active = k < qv.K;
+    const int64_t p = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
+    const bool active = p < qv.npair;
+    int2 kk2 = make_int2(0, 0);
     double s[3] = {0, 0, 0};
     if (active) {
-        s[0] = qv.shat[3 * k];
-        s[1] = qv.shat[3 * k + 1];
-        s[2] = qv.shat[3 * k + 2];
+        kk2 = qv.pair[p];
+        s[0] = qv.shat[3 * kk2.x];
+        s[1] = qv.shat[3 * kk2.x + 1];
+        s[2] = qv.shat[3 * kk2.x + 2];
     }
     const int s0 = sstart[b], sc = scount[b];
     const double cxx = bx.center[3 * b], cyy = bx.center[3 * b + 1], czz = bx.center[3 * b + 2];
     for (int r = 0; r < R_; ++r) {
-        cx<R> acc = mk<R>(0, 0);
+        cx<R> U = mk<R>(0, 0), V = mk<R>(0, 0);
         for (int jb = 0; jb < sc; jb += kS2MThreads) {
             const int jn = min(kS2MThreads, sc - jb);
             __syncthreads();
@@ -204,13 +213,21 @@ __global__ void k_s2m(BoxView bx, QuadView qv, const int32_t* __restrict__ sstar
             __syncthreads();
             if (active)
                 for (int jj = 0; jj < jn; ++jj) {
-                    double t = turns(kappa_turns, s, shd[3 * jj], shd[3 * jj + 1], shd[3 * jj + 2]);
-                    mac(acc, plane_wave<R>(t), cvt<R>(shq[jj]));
+                    const double t = turns(kappa_turns, s, shd[3 * jj], shd[3 * jj + 1], shd[3 * jj + 2]);
+                    const cx<R> e = plane_wave<R>(t);
+                    const cx<R> q = cvt<R>(shq[jj]);
+                    U = U + e.x * q;
+                    V = V + e.y * q;
                 }
         }
         if (active) {
-            if (wk) acc = (R)wk[k] * acc;
-            M[((int64_t)b * R_ + r) * qv.K + k] = acc;
+            cx<R> a = mk<R>(U.x - V.y, U.y + V.x), c = mk<R>(U.x + V.y, U.y - V.x);
+            if (wk) {
+                a = (R)wk[kk2.x] * a;
+                c = (R)wk[kk2.y] * c;
+            }
+            M[((int64_t)b * R_ + r) * qv.K + kk2.x] = a;
+            M[((int64_t)b * R_ + r) * qv.K + kk2.y] = c;
         }
     }
 }
@@ -219,10 +236,11 @@ __global__ void k_s2m(BoxView bx, QuadView qv, const int32_t* __restrict__ sstar
 // L2T: phi_i += sum_k w_k L_b(s_k) exp(i k s_k . (c_b - x_i)); thread per target
 // ---------------------------------------------------------------------------
 constexpr int kL2TThreads = 128;
-constexpr int kL2TTile = 512;      // quadrature samples staged per barrier
 
 // Signature to points: phi_i += sum_k w_k L_b(s_k) exp(i k s_k . sign (c_b - p_i)).
 // L2T: targets, sign +1, quadrature weights.  Transposed S2M: sources, sign -1, no weights.
+// Over antipodal pairs (k, k') with A = w_k L(k), B = w_k' L(k'), E = C + iS the plane wave
+// of s_k: A E + B conj(E) = (P.x C - Q.y S) + i (P.y C + Q.x S), P = A + B, Q = A - B.
 template <typename R>
 __global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstart,
                       const int32_t* __restrict__ tcount, const double* __restrict__ tx,
@@ -230,46 +248,49 @@ __global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstar
                       const cx<R>* __restrict__ L, int R_, double kappa_turns, cxd* __restrict__ phis,
                       double sign, const double* __restrict__ wk) {
     __shared__ double shs[kL2TThreads * 3];
-    __shared__ cx<R> shl[kL2TThreads];
+    __shared__ cx<R> shp[kL2TThreads], shq[kL2TThreads];
     const int b = blockIdx.x;
     const int t0 = tstart[b], tc = tcount[b];
     if ((int)blockIdx.y * kL2TThreads >= tc) return;
     const double cxx = bx.center[3 * b], cyy = bx.center[3 * b + 1], czz = bx.center[3 * b + 2];
+    const int ti = blockIdx.y * kL2TThreads + threadIdx.x;
+    const bool active = ti < tc;
+    double dx = 0, dy = 0, dz = 0;
+    if (active) {
+        dx = sign * (cxx - tx[t0 + ti]);
+        dy = sign * (cyy - ty[t0 + ti]);
+        dz = sign * (czz - tz[t0 + ti]);
+    }
     for (int r = 0; r < R_; ++r) {
         const cx<R>* Lb = L + ((int64_t)b * R_ + r) * qv.K;
-        {
-            const int tb = blockIdx.y * kL2TThreads;
-            const int ti = tb + threadIdx.x;
-            const bool active = ti < tc;
-            double dx = 0, dy = 0, dz = 0;
-            if (active) {
-                dx = sign * (cxx - tx[t0 + ti]);
-                dy = sign * (cyy - ty[t0 + ti]);
-                dz = sign * (czz - tz[t0 + ti]);
+        cx<R> acc = mk<R>(0, 0);
+        for (int64_t pb = 0; pb < qv.npair; pb += kL2TThreads) {
+            const int pn = (int)min((int64_t)kL2TThreads, qv.npair - pb);
+            __syncthreads();
+            if (threadIdx.x < pn) {
+                const int2 kk2 = qv.pair[pb + threadIdx.x];
+                shs[3 * threadIdx.x] = qv.shat[3 * kk2.x];
+                shs[3 * threadIdx.x + 1] = qv.shat[3 * kk2.x + 1];
+                shs[3 * threadIdx.x + 2] = qv.shat[3 * kk2.x + 2];
+                const cx<R> A = wk ? (R)wk[kk2.x] * Lb[kk2.x] : Lb[kk2.x];
+                const cx<R> B = wk ? (R)wk[kk2.y] * Lb[kk2.y] : Lb[kk2.y];
+                shp[threadIdx.x] = A + B;
+                shq[threadIdx.x] = A - B;
             }
-            cx<R> acc = mk<R>(0, 0);
-            for (int64_t kb = 0; kb < qv.K; kb += kL2TThreads) {
-                const int kn = (int)min((int64_t)kL2TThreads, qv.K - kb);
-                __syncthreads();
-                if (threadIdx.x < kn) {
-                    const int64_t k = kb + threadIdx.x;
-                    shs[3 * threadIdx.x] = qv.shat[3 * k];
-                    shs[3 * threadIdx.x + 1] = qv.shat[3 * k + 1];
-                    shs[3 * threadIdx.x + 2] = qv.shat[3 * k + 2];
-                    shl[threadIdx.x] = wk ? (R)wk[k] * Lb[k] : Lb[k];
+            __syncthreads();
+            if (active)
+                for (int kk = 0; kk < pn; ++kk) {
+                    const double t = turns(kappa_turns, &shs[3 * kk], dx, dy, dz);
+                    const cx<R> e = plane_wave<R>(t);
+                    const cx<R> P = shp[kk], Q = shq[kk];
+                    acc.x += P.x * e.x - Q.y * e.y;
+                    acc.y += P.y * e.x + Q.x * e.y;
                 }
-                __syncthreads();
-                if (active)
-                    for (int kk = 0; kk < kn; ++kk) {
-                        double t = turns(kappa_turns, &shs[3 * kk], dx, dy, dz);
-                        mac(acc, plane_wave<R>(t), shl[kk]);
-                    }
-            }
-            if (active) {
-                cxd& o = phis[(int64_t)(t0 + ti) * R_ + r];
-                o.x += (double)acc.x;
-                o.y += (double)acc.y;
-            }
+        }
+        if (active) {
+            cxd& o = phis[(int64_t)(t0 + ti) * R_ + r];
+            o.x += (double)acc.x;
+            o.y += (double)acc.y;
         }
     }
 }
@@ -290,15 +311,19 @@ __global__ void k_s2m_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ss
     __shared__ cdf tab[kCisTableBig];
     for (int v = threadIdx.x; v < kCisTableBig; v += blockDim.x) tab[v] = cis_tab[v];
     const int b = blockIdx.x;
-    const int64_t k = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
-    const bool active = k < qv.K;
+    const int64_t p = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;   // antipodal pair
+    const bool active = p < qv.npair;
+    int2 kk2 = make_int2(0, 0);
     df s[3] = {{0, 0}, {0, 0}, {0, 0}};
-    if (active)
-        for (int c = 0; c < 3; ++c) s[c] = df_from_double(qv.shat[3 * k + c] * kappa_turns);
+    if (active) {
+        kk2 = qv.pair[p];
+        for (int c = 0; c < 3; ++c) s[c] = df_from_double(qv.shat[3 * kk2.x + c] * kappa_turns);
+    }
     const int s0 = sstart[b], sc = scount[b];
     const double cxx = bx.center[3 * b], cyy = bx.center[3 * b + 1], czz = bx.center[3 * b + 2];
     for (int r = 0; r < R_; ++r) {
-        dfacc ax = {0.f, 0.f}, ay = {0.f, 0.f};
+        // U = sum q C, V = sum q S with C + iS = exp(i k s_k . d)
+        dfacc ux = {0.f, 0.f}, uy = {0.f, 0.f}, vx = {0.f, 0.f}, vy = {0.f, 0.f};
         for (int jb = 0; jb < sc; jb += kS2MTile) {
             const int jn = min(kS2MTile, sc - jb);
             __syncthreads();
@@ -313,18 +338,25 @@ __global__ void k_s2m_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ss
             __syncthreads();
             if (active)
                 for (int jj = 0; jj < jn; ++jj) {
-                    const cdf e = cdf_mul(cis_turns_big(df_dot3(s, &shd[3 * jj]), tab), shq[jj]);
-                    dfacc_add(ax, e.x);
-                    dfacc_add(ay, e.y);
+                    const cdf e = cis_turns_big(df_dot3(s, &shd[3 * jj]), tab);
+                    const cdf q = shq[jj];
+                    dfacc_add_prod(ux, q.x, e.x);
+                    dfacc_add_prod(uy, q.y, e.x);
+                    dfacc_add_prod(vx, q.x, e.y);
+                    dfacc_add_prod(vy, q.y, e.y);
                 }
         }
-        cdf acc = {dfacc_get(ax), dfacc_get(ay)};
         if (active) {
+            const df Ux = dfacc_get(ux), Uy = dfacc_get(uy), Vx = dfacc_get(vx), Vy = dfacc_get(vy);
+            cdf a = {df_sub(Ux, Vy), df_add(Uy, Vx)};   // M(k)  = U + iV
+            cdf c = {df_add(Ux, Vy), df_sub(Uy, Vx)};   // M(k') = U - iV
             if (wk) {
-                const df w = df_from_double(wk[k]);
-                acc = cdf{df_mul(acc.x, w), df_mul(acc.y, w)};
+                const df wa = df_from_double(wk[kk2.x]), wc = df_from_double(wk[kk2.y]);
+                a = cdf{df_mul(a.x, wa), df_mul(a.y, wa)};
+                c = cdf{df_mul(c.x, wc), df_mul(c.y, wc)};
             }
-            M[((int64_t)b * R_ + r) * qv.K + k] = mk<df>(acc.x, acc.y);
+            M[((int64_t)b * R_ + r) * qv.K + kk2.x] = mk<df>(a.x, a.y);
+            M[((int64_t)b * R_ + r) * qv.K + kk2.y] = mk<df>(c.x, c.y);
         }
     }
 }
@@ -345,7 +377,7 @@ __global__ void __launch_bounds__(128) k_l2t_df_warp(
     const cdf* __restrict__ cis_tab, cxd* __restrict__ out, double sign, const double* __restrict__ wk) {
     __shared__ cdf tab[kCisTableBig];
     __shared__ df shs[4][kWarpTile * 3];
-    __shared__ cdf shl[4][kWarpTile];
+    __shared__ cdf shp[4][kWarpTile], shiq[4][kWarpTile];
     for (int v = threadIdx.x; v < kCisTableBig; v += blockDim.x) tab[v] = cis_tab[v];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -363,31 +395,37 @@ __global__ void __launch_bounds__(128) k_l2t_df_warp(
         d[2] = df_from_double(sign * (czz - pz[t0 + ti]));
     }
     df* ss = shs[warp];
-    cdf* sl = shl[warp];
+    cdf* sp = shp[warp];
+    cdf* siq = shiq[warp];
     for (int r = 0; r < R_; ++r) {
         const cx<df>* Lb = L + ((int64_t)b * R_ + r) * qv.K;
         dfacc ax = {0.f, 0.f}, ay = {0.f, 0.f};
-        for (int64_t kb = 0; kb < qv.K; kb += kWarpTile) {
-            const int kn = (int)min((int64_t)kWarpTile, qv.K - kb);
+        for (int64_t pb = 0; pb < qv.npair; pb += kWarpTile) {
+            const int pn = (int)min((int64_t)kWarpTile, qv.npair - pb);
             __syncwarp();
-            for (int v = lane; v < kn; v += 32) {
-                const int64_t k = kb + v;
-                ss[3 * v] = sdf[3 * k];
-                ss[3 * v + 1] = sdf[3 * k + 1];
-                ss[3 * v + 2] = sdf[3 * k + 2];
-                cdf wl = cdf{Lb[k].x, Lb[k].y};
+            for (int v = lane; v < pn; v += 32) {
+                const int2 kk2 = qv.pair[pb + v];
+                ss[3 * v] = sdf[3 * kk2.x];
+                ss[3 * v + 1] = sdf[3 * kk2.x + 1];
+                ss[3 * v + 2] = sdf[3 * kk2.x + 2];
+                cdf A = cdf{Lb[kk2.x].x, Lb[kk2.x].y}, B = cdf{Lb[kk2.y].x, Lb[kk2.y].y};
                 if (wk) {
-                    const df w = df_from_double(wk[k]);
-                    wl = cdf{df_mul(wl.x, w), df_mul(wl.y, w)};
+                    const df wa = df_from_double(wk[kk2.x]), wb = df_from_double(wk[kk2.y]);
+                    A = cdf{df_mul(A.x, wa), df_mul(A.y, wa)};
+                    B = cdf{df_mul(B.x, wb), df_mul(B.y, wb)};
                 }
-                sl[v] = wl;
+                sp[v] = cdf{df_add(A.x, B.x), df_add(A.y, B.y)};    // P = A + B
+                siq[v] = cdf{df_sub(B.y, A.y), df_sub(A.x, B.x)};   // i Q, Q = A - B
             }
             __syncwarp();
             if (active)
-                for (int kk = 0; kk < kn; ++kk) {
-                    const cdf e = cdf_mul(cis_turns_big(df_dot3(&ss[3 * kk], d), tab), sl[kk]);
-                    dfacc_add(ax, e.x);
-                    dfacc_add(ay, e.y);
+                for (int kk = 0; kk < pn; ++kk) {
+                    const cdf e = cis_turns_big(df_dot3(&ss[3 * kk], d), tab);
+                    const cdf P = sp[kk], iQ = siq[kk];
+                    dfacc_add_prod(ax, P.x, e.x);
+                    dfacc_add_prod(ax, iQ.x, e.y);
+                    dfacc_add_prod(ay, P.y, e.x);
+                    dfacc_add_prod(ay, iQ.y, e.y);
                 }
         }
         const cdf acc = {dfacc_get(ax), dfacc_get(ay)};

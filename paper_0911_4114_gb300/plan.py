@@ -10,6 +10,8 @@ import numpy as np
 from . import _native as nat
 
 
+_PREC_NAMES = {0: "fp64", 1: "fp32", 2: "df"}   # hfmm_level_precision codes
+
 def make_options(precision="fp64", alphas=None, eps_scale=0.25, max_leaf=64, depth=0, root=None,
                  max_rhs=1, device=0):
     opt = nat.Options()
@@ -141,12 +143,13 @@ class FmmPlan:
         for l in range(2, lf + 1):
             levels[l] = dict(nbox=inf.level_nbox[l], ell=inf.level_ell[l], ntheta=inf.level_ntheta[l],
                              K=inf.level_K[l], alpha=inf.level_alpha[l],
-                             precision={0: "fp64", 1: "fp32", 2: "df"}[inf.level_precision[l]],
+                             precision=_PREC_NAMES[inf.level_precision[l]],
                              round_est=inf.level_round_est[l], ilist_total=inf.level_ilist_total[l])
         return dict(ns=inf.ns, nt=inf.nt, kappa=inf.kappa, eps=inf.eps, occupancy_depth=inf.occupancy_depth,
                     lf=lf, p2p_pairs=inf.p2p_pairs, nbox=[inf.level_nbox[l] for l in range(lf + 1)],
                     levels=levels, stage_ms={nat.STAGES[i]: inf.stage_ms[i] for i in range(nat.N_STAGES)},
-                    workspace_bytes=inf.workspace_bytes)
+                    workspace_bytes=inf.workspace_bytes,
+                    near_precision=_PREC_NAMES[inf.near_precision])
 
     def debug_get(self, what, level=0, arg=0):
         L = nat.lib()
