@@ -359,6 +359,12 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
     TRY(dalloc(P, &P->gsort, (size_t)hp.ns * 3));
     // levels
     for (int l = 2; l <= hp.lf; ++l) TRY(upload_level(P, l));
+    // the re-quadrature dispatch covers precision pairs that never decrease with depth
+    for (int l = 3; l <= hp.lf; ++l) {
+        auto rank = [](int prec) { return prec == kFP32 ? 0 : (prec == kDF ? 1 : 2); };
+        if (rank(P->lev[l].prec) < rank(P->lev[l - 1].prec))
+            return fail(HFMM_ERR_STATE, "internal: level precision decreases with depth");
+    }
     // re-quadrature passes and scratch
     int64_t ga = 0, gb = 0;
     std::vector<int> lengths;
@@ -452,9 +458,12 @@ template <> const cx<double>* shift_of<double>(const DevLevel& d) { return d.shi
 template <> const cx<df>* shift_of<df>(const DevLevel& d) { return d.shiftdf; }
 
 // Re-quadrature launches.  Tin / Tout: storage types of the input and output levels;
-// Tc: compute type (the precision of the level whose accuracy the result needs).
-//   M2M l -> l-1: compute in level l-1's type     L2L l -> l+1: compute in level l+1's type
-//   transposed L2L l+1 -> l: level l's type        transposed M2M l-1 -> l: level l's type
+// Tc: compute type, always the parent's (the coarser of the two; precision never decreases
+// with depth).  Going up, the parent's signature needs no more.  Going down, the parent's
+// data carries only its own precision, so interpolating it in that type adds round-off of
+// the size it already has; the child's own part is added in the child's type.
+//   M2M l -> l-1, transposed L2L l+1 -> l: level l-1 (resp. l)
+//   L2L l -> l+1, transposed M2M l-1 -> l: level l (resp. l-1)
 template <typename Tin, typename Tc, typename Tout>
 void launch_up(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
     RequadArgs ra = P->up[l].args;
@@ -466,12 +475,13 @@ void launch_up(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
     cx<Tc>* GB = (cx<Tc>*)P->gb;
     smem_opt_in(k_requad_rows_a<Tin, Tc, kNoShift, false>, sm);
     smem_opt_in(k_requad_cols<Tc, false>, sm);
-    smem_opt_in(k_requad_rows_c_m2m<Tc, Tout, kShiftPlain, false>, sm);
+    const size_t sm3 = (size_t)kWarps * 3 * ra.maxlen * sizeof(cx<Tc>);   // + per-warp child sum
+    smem_opt_in(k_requad_rows_c_m2m<Tc, Tout, kShiftPlain, false>, sm3);
     k_requad_rows_a<Tin, Tc, kNoShift, false><<<nblk((int64_t)c.nbox * R * ra.qa.nrows, kWarps), 32 * kWarps, sm, st>>>(
         ra, c.nbox, R, (const cx<Tin>*)c.M, nullptr, nullptr, nullptr, GA);
     k_requad_cols<Tc, false><<<nblk((int64_t)c.nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(
         ra, c.nbox, R, GA, GB);
-    k_requad_rows_c_m2m<Tc, Tout, kShiftPlain, false><<<nblk((int64_t)p.nbox * R * ra.qb.nrows, kWarps), 32 * kWarps, sm, st>>>(
+    k_requad_rows_c_m2m<Tc, Tout, kShiftPlain, false><<<nblk((int64_t)p.nbox * R * ra.qb.nrows, kWarps), 32 * kWarps, sm3, st>>>(
         ra, p.nbox, R, p.bv.child_start, p.bv.child_count, c.octant, shift_of<Tc>(p), GB, (cx<Tout>*)p.M);
 }
 
@@ -486,12 +496,13 @@ void launch_l2l_t(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
     cx<Tc>* GB = (cx<Tc>*)P->gb;
     smem_opt_in(k_requad_rows_a<Tin, Tc, kNoShift, true>, sm);
     smem_opt_in(k_requad_cols<Tc, true>, sm);
-    smem_opt_in(k_requad_rows_c_m2m<Tc, Tout, kShiftConj, true>, sm);
+    const size_t sm3 = (size_t)kWarps * 3 * ra.maxlen * sizeof(cx<Tc>);   // + per-warp child sum
+    smem_opt_in(k_requad_rows_c_m2m<Tc, Tout, kShiftConj, true>, sm3);
     k_requad_rows_a<Tin, Tc, kNoShift, true><<<nblk((int64_t)c.nbox * R * ra.qa.nrows, kWarps), 32 * kWarps, sm, st>>>(
         ra, c.nbox, R, (const cx<Tin>*)c.IL, nullptr, nullptr, nullptr, GA);
     k_requad_cols<Tc, true><<<nblk((int64_t)c.nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(
         ra, c.nbox, R, GA, GB);
-    k_requad_rows_c_m2m<Tc, Tout, kShiftConj, true><<<nblk((int64_t)p.nbox * R * ra.qb.nrows, kWarps), 32 * kWarps, sm, st>>>(
+    k_requad_rows_c_m2m<Tc, Tout, kShiftConj, true><<<nblk((int64_t)p.nbox * R * ra.qb.nrows, kWarps), 32 * kWarps, sm3, st>>>(
         ra, p.nbox, R, p.bv.child_start, p.bv.child_count, c.octant, shift_of<Tc>(p), GB, (cx<Tout>*)p.IL);
 }
 
@@ -557,16 +568,18 @@ int compute_code(hfmm_plan_s* P, int l) { return store_code(P, l); }
 
 template <typename Fn>
 bool dispatch3(int sin, int cc, int sout, Fn fn) {
-    // precision only grows with depth (float32 < double-float < float64)
+    // precision only grows with depth (float32 < double-float < float64); cc is the parent's
     if (sin == 1 && cc == 1 && sout == 1) fn(double{}, double{}, double{});
     else if (sin == 2 && cc == 2 && sout == 2) fn(df{}, df{}, df{});
     else if (sin == 0 && cc == 0 && sout == 0) fn(float{}, float{}, float{});
+    // up: child (finer type) -> parent
     else if (sin == 2 && cc == 0 && sout == 0) fn(df{}, float{}, float{});
     else if (sin == 1 && cc == 2 && sout == 2) fn(double{}, df{}, df{});
     else if (sin == 1 && cc == 0 && sout == 0) fn(double{}, float{}, float{});
-    else if (sin == 0 && cc == 2 && sout == 2) fn(float{}, df{}, df{});
-    else if (sin == 0 && cc == 1 && sout == 1) fn(float{}, double{}, double{});
-    else if (sin == 2 && cc == 1 && sout == 1) fn(df{}, double{}, double{});
+    // down: parent -> child (finer type)
+    else if (sin == 0 && cc == 0 && sout == 2) fn(float{}, float{}, df{});
+    else if (sin == 0 && cc == 0 && sout == 1) fn(float{}, float{}, double{});
+    else if (sin == 2 && cc == 2 && sout == 1) fn(df{}, df{}, double{});
     else return false;
     return true;
 }
@@ -577,7 +590,7 @@ void run_up(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
     });
 }
 void run_down(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
-    dispatch3(store_code(P, l), compute_code(P, l + 1), store_code(P, l + 1), [&](auto a, auto b, auto c) {
+    dispatch3(store_code(P, l), compute_code(P, l), store_code(P, l + 1), [&](auto a, auto b, auto c) {
         launch_down<decltype(a), decltype(b), decltype(c)>(P, l, R, st);
     });
 }
@@ -587,7 +600,7 @@ void run_l2l_t(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
     });
 }
 void run_m2m_t(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
-    dispatch3(store_code(P, l - 1), compute_code(P, l), store_code(P, l), [&](auto a, auto b, auto c) {
+    dispatch3(store_code(P, l - 1), compute_code(P, l - 1), store_code(P, l), [&](auto a, auto b, auto c) {
         launch_m2m_t<decltype(a), decltype(b), decltype(c)>(P, l, R, st);
     });
 }

@@ -67,6 +67,9 @@ __device__ __forceinline__ int next_radix(int m) {
 
 // In-place-by-ping-pong FFT of a[0..n) (sign -1 forward, +1 inverse, unnormalised).
 // Returns the buffer (a or b) that holds the result.  All 32 lanes must call it.
+// Stage with ns accumulated outputs: element j = k + ns * g (k < ns) of each of the radix
+// input strides is multiplied by exp(-+2 pi i k r / (ns radix)) = tw[k r n / (ns radix)],
+// an index below n; r = 0 and the whole first stage (k = 0) have unit twiddles and skip it.
 template <typename R>
 __device__ cx<R>* warp_fft(cx<R>* a, cx<R>* b, int n, bool inv, const cx<R>* tw, int lane) {
     cx<R>* src = a;
@@ -75,19 +78,22 @@ __device__ cx<R>* warp_fft(cx<R>* a, cx<R>* b, int n, bool inv, const cx<R>* tw,
     while (rest > 1) {
         const int radix = next_radix(rest);
         const int nr = n / radix;
-        const int stride = n / (ns * radix);
+        const int stride = rest / radix;     // n / (ns * radix)
         for (int j = lane; j < nr; j += 32) {
-            const int k = j % ns;
+            const int k = (ns == 1) ? 0 : j % ns;
             cx<R> v[5];
-            for (int r = 0; r < radix; ++r) {
-                cx<R> x = src[j + r * nr];
-                int t = (k * r * stride) % n;
-                cx<R> w = tw[t];
-                if (inv) w = conj(w);
-                v[r] = x * w;
+            v[0] = src[j];
+            if (ns == 1) {
+                for (int r = 1; r < radix; ++r) v[r] = src[j + r * nr];
+            } else {
+                for (int r = 1; r < radix; ++r) {
+                    cx<R> w = tw[k * r * stride];
+                    if (inv) w = conj(w);
+                    v[r] = src[j + r * nr] * w;
+                }
             }
             dft_small(v, radix, inv);
-            const int d = (j / ns) * ns * radix + k;
+            const int d = (j - k) * radix + k;
             for (int r = 0; r < radix; ++r) dst[d + r * ns] = v[r];
         }
         __syncwarp();

@@ -815,7 +815,8 @@ __global__ void k_requad_rows_c_l2l(RequadArgs ra, int nbox_seq, int R_, const c
     cx<Tc>* res = warp_resample(buf0, buf1, ra.big, len, ra.tw, lane);
     const Tc sc = rval<Tc>(kT ? (double)ra.big / (double)len : 1.0);
     cx<Tout>* dst = IL + br * ra.qb.K + ra.qb.off[n];
-    for (int j = lane; j < len; j += 32) dst[j] = cvt<Tout>(cvt<Tc>(dst[j]) + (kT ? sc * res[j] : res[j]));
+    // the sum is formed in the output level's type (Tc may be the coarser parent type)
+    for (int j = lane; j < len; j += 32) dst[j] = dst[j] + cvt<Tout>(kT ? sc * res[j] : res[j]);
 }
 
 // Pass C summing children, overwriting the parent.  Sequence = (parent, r, n').
@@ -829,8 +830,9 @@ __global__ void k_requad_rows_c_m2m(RequadArgs ra, int nparent, int R_, const in
     extern __shared__ unsigned char smem_raw[];
     cx<Tc>* sm = reinterpret_cast<cx<Tc>*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    cx<Tc>* buf0 = sm + (size_t)warp * 2 * ra.maxlen;
+    cx<Tc>* buf0 = sm + (size_t)warp * 3 * ra.maxlen;
     cx<Tc>* buf1 = buf0 + ra.maxlen;
+    cx<Tc>* acc = buf1 + ra.maxlen;   // sum over children; entry j belongs to lane j % 32
     const int rows = ra.qb.nrows;
     const int64_t seq = (int64_t)blockIdx.x * kWarps + warp;
     const int64_t nseq = (int64_t)nparent * R_ * rows;
@@ -840,10 +842,7 @@ __global__ void k_requad_rows_c_m2m(RequadArgs ra, int nparent, int R_, const in
     const int p = (int)(pr / R_), r = (int)(pr % R_);
     const int len = ra.qb.nphi[n];
     const int64_t o = ra.qb.off[n];
-    // each lane owns outputs j = lane, lane + 32, ...: accumulate across children in registers
-    constexpr int kMaxPerLane = 32;   // len <= 1024
-    cx<Tc> acc[kMaxPerLane];
-    for (int i = 0; i < kMaxPerLane; ++i) acc[i] = mk<Tc>(rval<Tc>(0.0), rval<Tc>(0.0));
+    for (int j = lane; j < len; j += 32) acc[j] = mk<Tc>(rval<Tc>(0.0), rval<Tc>(0.0));
     const int c0 = child_start[p], cn = child_count[p];
     for (int c = c0; c < c0 + cn; ++c) {
         const cx<Tc>* row = GB + (((int64_t)c * R_ + r) * rows + n) * ra.big;
@@ -852,14 +851,14 @@ __global__ void k_requad_rows_c_m2m(RequadArgs ra, int nparent, int R_, const in
         cx<Tc>* res = warp_resample(buf0, buf1, ra.big, len, ra.tw, lane);
         const cx<Tc>* sh = shift + (int64_t)octant[c] * ra.qb.K + o;
         const Tc sc = rval<Tc>(kT ? (double)ra.big / (double)len : 1.0);
-        for (int i = 0, j = lane; j < len; ++i, j += 32) {
+        for (int j = lane; j < len; j += 32) {
             cx<Tc> v = kT ? sc * res[j] : res[j];
-            acc[i] = acc[i] + v * (kShift == kShiftConj ? conj(sh[j]) : sh[j]);
+            acc[j] = acc[j] + v * (kShift == kShiftConj ? conj(sh[j]) : sh[j]);
         }
         __syncwarp();
     }
     cx<Tout>* dst = Mp + ((int64_t)p * R_ + r) * ra.qb.K + o;
-    for (int i = 0, j = lane; j < len; ++i, j += 32) dst[j] = cvt<Tout>(acc[i]);
+    for (int j = lane; j < len; j += 32) dst[j] = cvt<Tout>(acc[j]);
 }
 
 }  // namespace hfmm
