@@ -51,10 +51,11 @@ typedef enum {
 
 typedef enum { HFMM_C64 = 0, HFMM_C128 = 1 } hfmm_dtype;
 
-/* Precision policy.  FP64: every stage in float64.  MIXED: per level float32 where the
- * planner's round-off estimate allows it, double-float (float32 pairs, ~48 bits) elsewhere;
- * near field in float32 with exact grid geometry and float64 tile accumulation when
- * eps >= 1e-6, in float64 below. */
+/* Precision policy.  FP64: every stage in float64.  MIXED: per level the first of float32,
+ * double-float (float32 pairs, ~48 bits) and float64 that the planner's round-off estimate
+ * allows, never coarser than the level above; near field in float32 with exact grid
+ * geometry and float64 tile accumulation when eps >= 1e-6, in double-float for
+ * 1e-11 <= eps < 1e-6, in float64 below. */
 typedef enum { HFMM_PREC_FP64 = 0, HFMM_PREC_MIXED = 1 } hfmm_precision;
 
 /* Level precisions reported by hfmm_query. */
@@ -103,7 +104,8 @@ typedef struct {
     double stage_ms[HFMM_N_STAGES];
     int64_t workspace_bytes;
     /* arithmetic of the near field: HFMM_LEVEL_FP32 (float32 exact-grid form, mixed policy
-     * with eps >= 1e-6) or HFMM_LEVEL_FP64 */
+     * with eps >= 1e-6), HFMM_LEVEL_DF (double-float, mixed policy with 1e-11 <= eps < 1e-6)
+     * or HFMM_LEVEL_FP64 (float64 policy, or eps < 1e-11) */
     int near_precision;
 } hfmm_info;
 

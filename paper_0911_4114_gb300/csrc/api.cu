@@ -68,9 +68,13 @@ struct Requad {
 struct hfmm_plan_s {
     HostPlan hp;
     int device = -1;
-    // the float32 near field carries ~1e-7 relative error: the mixed policy uses it only for
-    // eps >= 1e-6 and the float64 near field below
-    bool near_fp32 = false;
+    // near-field arithmetic (kFP32 / kDF / kFP64).  The float32 exact-grid form carries ~1e-7
+    // relative error per pair, double-float ~1e-13: the mixed policy takes float32 for
+    // eps >= 1e-6, double-float for 1e-11 <= eps < 1e-6, float64 below; the float64 policy
+    // always float64
+    int near_prec = kFP64;
+    df* tpos_df = nullptr;      // (nt, 3) sorted targets minus the root corner, double-float
+    df* spos_df = nullptr;      // (ns, 3) sorted sources
     int rmax = 1;
     std::vector<void*> allocs;
     // leaf / points
@@ -353,6 +357,16 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
         P->mixed.tau_hi = (float)tau;
         P->mixed.tau_lo = (float)(tau - (double)P->mixed.tau_hi);
         P->mixed.inv_unit = scale;
+    }
+    if (P->near_prec == kDF) {
+        auto pos = [&](const std::vector<double>& pts, const std::vector<int64_t>& perm, df** out) -> hfmm_status {
+            std::vector<df> v(3 * perm.size());
+            for (size_t i = 0; i < perm.size(); ++i)
+                for (int k = 0; k < 3; ++k) v[3 * i + k] = df_from_double(pts[3 * perm[i] + k] - hp.corner[k]);
+            return upload(P, out, v);
+        };
+        TRY(pos(hp.tgt, hp.tgt_perm, &P->tpos_df));
+        TRY(pos(hp.src, hp.src_perm, &P->spos_df));
     }
     TRY(dalloc(P, &P->qs, (size_t)hp.ns * P->rmax));
     TRY(dalloc(P, &P->phis, (size_t)hp.nt * P->rmax));
@@ -804,7 +818,7 @@ hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, 
             }
     P->rmax = opt.max_rhs;
     P->device = opt.device;
-    P->near_fp32 = opt.precision == HFMM_PREC_MIXED && eps >= 1e-6;
+    if (opt.precision == HFMM_PREC_MIXED) P->near_prec = eps >= 1e-6 ? kFP32 : (eps >= 1e-11 ? kDF : kFP64);
     if (opt.device >= 0) {
         hfmm_status s = upload_plan(P);
         if (s != HFMM_OK) {
@@ -859,9 +873,9 @@ hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_d
     mark(1);
     const int nleaf = (int)hp.levels[lf].nbox();
     const dim3 g_fwd(nleaf, nblk(P->max_tgt_leaf, kP2PThreads));
-    if (P->near_fp32) {
-        if (P->ntunits > 0)
-        {
+    const df kt_df = df_from_double(hp.kappa / (2.0 * 3.14159265358979323846));
+    if (P->near_prec == kFP32) {
+        if (P->ntunits > 0) {
             if (R == 1)
                 k_p2p_mixed_warp<1><<<nblk(P->ntunits, 4), 128, 0, st>>>(P->tunits, P->ntunits, P->tstart, P->tcount,
                                                                          P->sstart, P->scount, P->noff, P->nidx,
@@ -871,11 +885,24 @@ hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_d
                                                                          P->sstart, P->scount, P->noff, P->nidx,
                                                                          P->mixed, P->qs, P->phis, R);
         }
-    }
-    else
+    } else if (P->near_prec == kDF) {
+        if (P->ntunits > 0) {
+            if (R == 1)
+                k_p2p_df_warp<1><<<nblk(P->ntunits, 4), 128, 0, st>>>(P->tunits, P->ntunits, P->tstart, P->tcount,
+                                                                      P->sstart, P->scount, P->noff, P->nidx,
+                                                                      P->tpos_df, P->spos_df, kt_df, P->cis_tab,
+                                                                      P->qs, P->phis, R);
+            else
+                k_p2p_df_warp<4><<<nblk(P->ntunits, 4), 128, 0, st>>>(P->tunits, P->ntunits, P->tstart, P->tcount,
+                                                                      P->sstart, P->scount, P->noff, P->nidx,
+                                                                      P->tpos_df, P->spos_df, kt_df, P->cis_tab,
+                                                                      P->qs, P->phis, R);
+        }
+    } else {
         k_p2p_fp64<<<g_fwd, kP2PThreads, 0, st>>>(nleaf, P->tstart, P->tcount, P->sstart, P->scount, P->noff,
                                                   P->nidx, P->tx, P->ty, P->tz, P->sx, P->sy, P->sz, P->qs,
                                                   P->phis, R, hp.kappa);
+    }
     mark(2);
     if (lf >= 2) {
         if (P->lev[lf].prec == kFP32) launch_s2m<float>(P, R, st);
@@ -927,12 +954,12 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t P, const void* w, void* out, int nrhs
     // transposed near field: source boxes gather the targets of their neighbours
     const int nleaf = (int)hp.levels[lf].nbox();
     const dim3 g_adj(nleaf, nblk(P->max_src_leaf, kP2PThreads));
-    if (P->near_fp32) {
+    const df kt_df = df_from_double(hp.kappa / (2.0 * 3.14159265358979323846));
+    if (P->near_prec == kFP32) {
         P2PMixedArgs a = P->mixed;
         std::swap(a.tpt, a.spt);
         std::swap(a.tof, a.sof);
-        if (P->nsunits > 0)
-        {
+        if (P->nsunits > 0) {
             if (R == 1)
                 k_p2p_mixed_warp<1><<<nblk(P->nsunits, 4), 128, 0, st>>>(P->sunits, P->nsunits, P->sstart, P->scount,
                                                                          P->tstart, P->tcount, P->noff, P->nidx, a,
@@ -941,6 +968,19 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t P, const void* w, void* out, int nrhs
                 k_p2p_mixed_warp<4><<<nblk(P->nsunits, 4), 128, 0, st>>>(P->sunits, P->nsunits, P->sstart, P->scount,
                                                                          P->tstart, P->tcount, P->noff, P->nidx, a,
                                                                          P->phis, P->qs, R);
+        }
+    } else if (P->near_prec == kDF) {
+        if (P->nsunits > 0) {
+            if (R == 1)
+                k_p2p_df_warp<1><<<nblk(P->nsunits, 4), 128, 0, st>>>(P->sunits, P->nsunits, P->sstart, P->scount,
+                                                                      P->tstart, P->tcount, P->noff, P->nidx,
+                                                                      P->spos_df, P->tpos_df, kt_df, P->cis_tab,
+                                                                      P->phis, P->qs, R);
+            else
+                k_p2p_df_warp<4><<<nblk(P->nsunits, 4), 128, 0, st>>>(P->sunits, P->nsunits, P->sstart, P->scount,
+                                                                      P->tstart, P->tcount, P->noff, P->nidx,
+                                                                      P->spos_df, P->tpos_df, kt_df, P->cis_tab,
+                                                                      P->phis, P->qs, R);
         }
     } else {
         k_p2p_fp64<<<g_adj, kP2PThreads, 0, st>>>(nleaf, P->sstart, P->scount, P->tstart, P->tcount, P->noff,
@@ -1044,7 +1084,7 @@ hfmm_status hfmm_query(hfmm_plan_t P, hfmm_info* info) {
         }
     }
     info->workspace_bytes = P->workspace;
-    info->near_precision = P->near_fp32 ? HFMM_LEVEL_FP32 : HFMM_LEVEL_FP64;
+    info->near_precision = P->near_prec == kFP32 ? HFMM_LEVEL_FP32 : (P->near_prec == kDF ? HFMM_LEVEL_DF : HFMM_LEVEL_FP64);
     if (P->ev_recorded) {
         if (cudaEventSynchronize(P->ev[HFMM_N_STAGES]) != cudaSuccess)
             return fail(HFMM_ERR_CUDA, "event synchronize failed");

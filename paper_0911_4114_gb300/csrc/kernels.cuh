@@ -520,6 +520,100 @@ __global__ void __launch_bounds__(128) k_p2p_mixed_warp(
 }
 
 // ---------------------------------------------------------------------------
+// near field in double-float (mixed policy, 1e-11 <= eps < 1e-6): positions as df pairs
+// relative to the root corner; one warp per (target box, 32-target chunk).
+// ---------------------------------------------------------------------------
+// G = exp(i k R) / R for the df difference d; false when R = 0.  R and 1/R: the float
+// rsqrt seed y refined by one Newton step each (relative error ~ 2^-45).
+__device__ __forceinline__ bool green_df(const df* d, df kt, const cdf* tab, cdf& g) {
+    const df r2 = df_dot3(d, d);
+    if (!(r2.hi > 0.0f)) return false;
+    const float y = rsqrtf(r2.hi);
+    const float r0 = __fmul_rn(r2.hi, y);
+    const float p = __fmul_rn(r0, r0);
+    const float pe = __fmaf_rn(r0, r0, -p);
+    const float res = __fadd_rn(__fsub_rn(__fsub_rn(r2.hi, p), pe), r2.lo);     // r2 - r0^2
+    const df R = df_fast_sum(r0, __fmul_rn(res, __fmul_rn(0.5f, y)));
+    const float q = __fmul_rn(R.hi, y);
+    const float qe = __fmaf_rn(R.hi, y, -q);
+    const float e = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, q), qe), __fmul_rn(R.lo, y));  // 1 - R y
+    const df inv = df_fast_sum(y, __fmul_rn(y, e));
+    const cdf c = cis_turns_big(df_mul(R, kt), tab);
+    g = cdf{df_mul(c.x, inv), df_mul(c.y, inv)};
+    return true;
+}
+
+template <int kRC>   // right-hand sides per pass: 1 (single RHS) or 4
+__global__ void __launch_bounds__(128) k_p2p_df_warp(
+    const int2* __restrict__ units, int nunits, const int32_t* __restrict__ tstart,
+    const int32_t* __restrict__ tcount, const int32_t* __restrict__ sstart, const int32_t* __restrict__ scount,
+    const int32_t* __restrict__ noff, const int32_t* __restrict__ nidx, const df* __restrict__ tpos,
+    const df* __restrict__ spos, df kt, const cdf* __restrict__ cis_tab, const cxd* __restrict__ qs,
+    cxd* __restrict__ phis, int R) {
+    __shared__ cdf tab[kCisTableBig];
+    __shared__ df shp[4][kWarpTile * 3];
+    __shared__ cdf shq[4][kWarpTile * kRC];
+    for (int v = threadIdx.x; v < kCisTableBig; v += blockDim.x) tab[v] = cis_tab[v];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int u = blockIdx.x * 4 + warp;
+    if (u >= nunits) return;
+    const int b = units[u].x, c0 = units[u].y;
+    const int t0 = tstart[b], tc = tcount[b];
+    const int ti = c0 + lane;
+    const bool active = ti < tc;
+    df x[3] = {{0, 0}, {0, 0}, {0, 0}};
+    if (active)
+        for (int c = 0; c < 3; ++c) x[c] = tpos[3 * (int64_t)(t0 + ti) + c];
+    df* wp = shp[warp];
+    cdf* wq = shq[warp];
+    for (int r0 = 0; r0 < R; r0 += kRC) {
+        const int rn = kRC == 1 ? 1 : min(kRC, R - r0);
+        cxd acc[kRC];
+        for (int r = 0; r < kRC; ++r) acc[r] = mk<double>(0, 0);
+        for (int nb = noff[b]; nb < noff[b + 1]; ++nb) {
+            const int s = nidx[nb];
+            const int s0 = sstart[s], sc = scount[s];
+            for (int sb = 0; sb < sc; sb += kWarpTile) {
+                const int sn = min(kWarpTile, sc - sb);
+                __syncwarp();
+                for (int v = lane; v < sn; v += 32) {
+                    const int64_t j = s0 + sb + v;
+                    for (int c = 0; c < 3; ++c) wp[3 * v + c] = spos[3 * j + c];
+                    for (int r = 0; r < rn; ++r) {
+                        const cxd qq = qs[j * R + r0 + r];
+                        wq[v * kRC + r] = cdf{df_from_double(qq.x), df_from_double(qq.y)};
+                    }
+                }
+                __syncwarp();
+                if (!active) continue;
+                dfacc ax[kRC], ay[kRC];
+                for (int r = 0; r < kRC; ++r) ax[r] = ay[r] = dfacc{0.f, 0.f};
+                for (int jj = 0; jj < sn; ++jj) {
+                    const df d[3] = {df_sub(x[0], wp[3 * jj]), df_sub(x[1], wp[3 * jj + 1]),
+                                     df_sub(x[2], wp[3 * jj + 2])};
+                    cdf g;
+                    if (!green_df(d, kt, tab, g)) continue;
+                    for (int r = 0; r < rn; ++r) {
+                        const cdf q = wq[jj * kRC + r];
+                        dfacc_add_prod(ax[r], g.x, q.x);
+                        dfacc_add_prod(ax[r], df_neg(g.y), q.y);
+                        dfacc_add_prod(ay[r], g.x, q.y);
+                        dfacc_add_prod(ay[r], g.y, q.x);
+                    }
+                }
+                for (int r = 0; r < rn; ++r) {
+                    acc[r].x += df_to_double(dfacc_get(ax[r]));
+                    acc[r].y += df_to_double(dfacc_get(ay[r]));
+                }
+            }
+        }
+        if (active)
+            for (int r = 0; r < rn; ++r) phis[(int64_t)(t0 + ti) * R + r0 + r] = acc[r];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Position gradient (vector-Jacobian product of phi = A(y) q for a real loss, with
 // g = dL/d conj(phi) in the convention of complex autograd):
 //   grad_j = Re[ sum_r q_jr ( i k sum_k s_k exp(i k s_k.(y_j - c_b)) Lambda_b,r(k)

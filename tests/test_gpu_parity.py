@@ -104,3 +104,37 @@ def test_sphere262k_sampled_targets(precision):
     idx = np.sort(wl.rng(1, salt=2).choice(len(t), 1000, replace=False))
     want = direct.direct(s, t[idx], q.astype(np.complex128), 64.0)
     assert rel(got[idx], want) <= 1e-6
+
+
+@pytest.mark.parametrize("nrhs", [1, 5])
+def test_double_float_near_field_against_direct(nrhs):
+    """Mixed policy below eps = 1e-6: the near field runs in double-float.  With one box
+    (no far field) the apply is the near field alone, so it must match the float64 direct
+    sum to double-float round-off; the transposed near field must match the direct
+    adjoint the same way.  R = 5 covers the four-RHS pass and a ragged remainder."""
+    g = wl.rng(12, salt=nrhs)
+    x = wl.cube(2500, g)
+    x[100] = x[7]                                   # a coincident pair: skipped (R = 0)
+    q = wl.charges(len(x), nrhs if nrhs > 1 else 0, g)
+    lib = FmmPlan(x, x, 30.0, 1e-9, precision="mixed", max_leaf=4096, max_rhs=nrhs)
+    info = lib.info()
+    assert info["near_precision"] == "df" and info["lf"] < 2
+    got = run_apply(lib, q)
+    want = direct.direct(x, x, q, 30.0)
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+    import torch
+    w = wl.charges(len(x), nrhs if nrhs > 1 else 0, g)
+    adj = lib.apply_adjoint(torch.as_tensor(w, device="cuda")).cpu().numpy()
+    want_adj = direct.direct_adjoint(x, x, w, 30.0)
+    assert np.max(np.abs(adj - want_adj)) <= 1e-12 * np.max(np.abs(want_adj))
+
+
+@pytest.mark.parametrize("name", ["cube_hf", "sphere_small", "two_spheres"])
+def test_mixed_tight_eps_within_eps_of_direct(name):
+    """eps = 1e-9 under the mixed policy: double-float near field and levels."""
+    s, t, kappa, _, kw = _case(name)
+    q = wl.charges(len(s), 0, wl.rng(13))
+    lib = FmmPlan(s, t, kappa, 1e-9, precision="mixed", **kw)
+    assert lib.info()["near_precision"] == "df"
+    got = run_apply(lib, q)
+    assert rel(got, direct.direct(s, t, q, kappa)) <= 1e-9
