@@ -73,6 +73,9 @@ struct hfmm_plan_s {
     // eps >= 1e-6, double-float for 1e-11 <= eps < 1e-6, float64 below; the float64 policy
     // always float64
     int near_prec = kFP64;
+    // sources and targets are the same point set: the float32 near field evaluates each
+    // pair of distinct neighbouring boxes once for both directions (one RHS)
+    bool sym = false;
     df* tpos_df = nullptr;      // (nt, 3) sorted targets minus the root corner, double-float
     df* spos_df = nullptr;      // (ns, 3) sorted sources
     int rmax = 1;
@@ -306,15 +309,16 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
     TRY(upload(P, &P->src_perm, hp.src_perm));
     TRY(upload(P, &P->tgt_perm, hp.tgt_perm));
     {
-        auto chunks = [&](const std::vector<int32_t>& count, int2** dst, int* n) -> hfmm_status {
+        auto chunks = [&](const std::vector<int32_t>& count, int2** dst, int* n, int width) -> hfmm_status {
             std::vector<int2> u;
             for (size_t b = 0; b < count.size(); ++b)
-                for (int c = 0; c < count[b]; c += 32) u.push_back(make_int2((int)b, c));
+                for (int c = 0; c < count[b]; c += width) u.push_back(make_int2((int)b, c));
             *n = (int)u.size();
             return upload(P, dst, u);
         };
-        TRY(chunks(hp.tgt_count, &P->tunits, &P->ntunits));
-        TRY(chunks(hp.src_count, &P->sunits, &P->nsunits));
+        TRY(chunks(hp.tgt_count, &P->tunits, &P->ntunits, 32));
+        TRY(chunks(hp.src_count, &P->sunits, &P->nsunits, 32));
+
     }
     for (int32_t c : hp.src_count) P->max_src_leaf = std::max(P->max_src_leaf, (int)c);
     for (int32_t c : hp.tgt_count) P->max_tgt_leaf = std::max(P->max_tgt_leaf, (int)c);
@@ -357,6 +361,7 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
         P->mixed.tau_hi = (float)tau;
         P->mixed.tau_lo = (float)(tau - (double)P->mixed.tau_hi);
         P->mixed.inv_unit = scale;
+        P->mixed.inv_unit_f = (float)scale;
     }
     if (P->near_prec == kDF) {
         auto pos = [&](const std::vector<double>& pts, const std::vector<int64_t>& perm, df** out) -> hfmm_status {
@@ -810,15 +815,23 @@ hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, 
         delete P;
         return fail(HFMM_ERR_ARG, ex.what());
     }
-    for (int l = 2; l <= hp.lf; ++l)
+    // FFT lengths are bounded by the warp transforms' shared buffers and index arithmetic
+    for (int l = 2; l <= hp.lf; ++l) {
+        if (hp.lp[l].quad.ntheta > 1024) {
+            delete P;
+            return fail(HFMM_ERR_ARG, "N_theta above 1024 is not supported");
+        }
         for (int v : hp.lp[l].quad.nphi)
             if (v > 1024) {
                 delete P;
                 return fail(HFMM_ERR_ARG, "N_phi above 1024 is not supported");
             }
+    }
     P->rmax = opt.max_rhs;
     P->device = opt.device;
     if (opt.precision == HFMM_PREC_MIXED) P->near_prec = eps >= 1e-6 ? kFP32 : (eps >= 1e-11 ? kDF : kFP64);
+    P->sym = ns == nt && (sources == targets || std::memcmp(sources, targets, sizeof(double) * 3 * ns) == 0) &&
+             P->hp.src_perm == P->hp.tgt_perm && P->hp.src_count == P->hp.tgt_count;
     if (opt.device >= 0) {
         hfmm_status s = upload_plan(P);
         if (s != HFMM_OK) {
@@ -874,7 +887,12 @@ hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_d
     const int nleaf = (int)hp.levels[lf].nbox();
     const dim3 g_fwd(nleaf, nblk(P->max_tgt_leaf, kP2PThreads));
     const df kt_df = df_from_double(hp.kappa / (2.0 * 3.14159265358979323846));
-    if (P->near_prec == kFP32) {
+    if (P->near_prec == kFP32 && P->sym && R == 1) {
+        CK(cudaMemsetAsync(P->phis, 0, sizeof(cxd) * (size_t)hp.nt, st));
+        if (P->ntunits > 0)
+            k_p2p_mixed_sym_warp<<<nblk(P->ntunits, 4), 128, 0, st>>>(P->tunits, P->ntunits, P->tstart, P->tcount,
+                                                                     P->noff, P->nidx, P->mixed, P->qs, P->phis);
+    } else if (P->near_prec == kFP32) {
         if (P->ntunits > 0) {
             if (R == 1)
                 k_p2p_mixed_warp<1><<<nblk(P->ntunits, 4), 128, 0, st>>>(P->tunits, P->ntunits, P->tstart, P->tcount,
@@ -955,7 +973,12 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t P, const void* w, void* out, int nrhs
     const int nleaf = (int)hp.levels[lf].nbox();
     const dim3 g_adj(nleaf, nblk(P->max_src_leaf, kP2PThreads));
     const df kt_df = df_from_double(hp.kappa / (2.0 * 3.14159265358979323846));
-    if (P->near_prec == kFP32) {
+    if (P->near_prec == kFP32 && P->sym && R == 1) {
+        CK(cudaMemsetAsync(P->qs, 0, sizeof(cxd) * (size_t)hp.ns, st));
+        if (P->nsunits > 0)
+            k_p2p_mixed_sym_warp<<<nblk(P->nsunits, 4), 128, 0, st>>>(P->sunits, P->nsunits, P->sstart, P->scount,
+                                                                     P->noff, P->nidx, P->mixed, P->phis, P->qs);
+    } else if (P->near_prec == kFP32) {
         P2PMixedArgs a = P->mixed;
         std::swap(a.tpt, a.spt);
         std::swap(a.tof, a.sof);

@@ -9,6 +9,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "cx.cuh"
+
 namespace hfmm {
 
 struct df {
@@ -74,10 +76,25 @@ __device__ __forceinline__ df operator-(df a) { return df_neg(a); }
 __device__ __forceinline__ df operator*(df a, df b) { return df_mul(a, b); }
 __device__ __forceinline__ df& operator+=(df& a, df b) { a = df_add(a, b); return a; }
 __device__ __forceinline__ df& operator-=(df& a, df b) { a = df_sub(a, b); return a; }
+// a b + c d: both Dekker products and their exact FMA errors, one Knuth sum of the leading
+// parts, every small term gathered in float32, one renormalisation
+__device__ __forceinline__ df df_dot2(df a, df b, df c, df d) {
+    const float p = __fmul_rn(a.hi, b.hi), q = __fmul_rn(c.hi, d.hi);
+    float e = __fadd_rn(__fmaf_rn(a.hi, b.hi, -p), __fmaf_rn(c.hi, d.hi, -q));
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    e = __fmaf_rn(c.hi, d.lo, __fmaf_rn(c.lo, d.hi, e));
+    const df s = df_two_sum(p, q);
+    return df_fast_sum(s.hi, __fadd_rn(s.lo, e));
+}
 __device__ __forceinline__ cdf cdf_mul(cdf a, cdf b) {
-    return {df_sub(df_mul(a.x, b.x), df_mul(a.y, b.y)), df_add(df_mul(a.x, b.y), df_mul(a.y, b.x))};
+    return {df_dot2(a.x, b.x, df_neg(a.y), b.y), df_dot2(a.x, b.y, a.y, b.x)};
 }
 __device__ __forceinline__ cdf cdf_add(cdf a, cdf b) { return {df_add(a.x, b.x), df_add(a.y, b.y)}; }
+
+// complex double-float product (non-template: preferred over the generic cx<R> operator)
+__device__ __forceinline__ cx<df> operator*(cx<df> a, cx<df> b) {
+    return mk<df>(df_dot2(a.x, b.x, df_neg(a.y), b.y), df_dot2(a.x, b.y, a.y, b.x));
+}
 
 // lazy double-float accumulator: leading sum with exact Knuth errors, all errors and low
 // parts gathered in a float32 tail; value = hi + lo after the final renormalisation

@@ -79,8 +79,12 @@ __device__ cx<R>* warp_fft(cx<R>* a, cx<R>* b, int n, bool inv, const cx<R>* tw,
         const int radix = next_radix(rest);
         const int nr = n / radix;
         const int stride = rest / radix;     // n / (ns * radix)
+        // k = j mod ns through a float quotient: j, ns <= 1024, so j / ns is within 2^-14
+        // of its value and the fractional parts are multiples of 1/ns >= 2^-10; adding
+        // 2^-12 before truncation gives the exact floor
+        const float inv_ns = 1.0f / (float)ns;
         for (int j = lane; j < nr; j += 32) {
-            const int k = (ns == 1) ? 0 : j % ns;
+            const int k = (ns == 1) ? 0 : j - ns * (int)fmaf((float)j, inv_ns, 0.000244140625f);
             cx<R> v[5];
             v[0] = src[j];
             if (ns == 1) {

@@ -142,7 +142,17 @@ struct P2PMixedArgs {
     const float4* sof;
     float tau_hi, tau_lo;  // turns per grid unit (kappa * side / 2^12 / 2 pi), split
     double inv_unit;       // 2^12 / side: 1 / (grid unit in length)
+    float inv_unit_f;
 };
+
+// float -> double by assembling the bits (exact for normal numbers and zero; subnormal
+// floats become zero), keeping the conversion off the slow float64 pipe
+__device__ __forceinline__ double f2d_bits(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t sign = u & 0x80000000u, ex = (u >> 23) & 0xffu, man = u & 0x7fffffu;
+    if (ex == 0) return __hiloint2double((int)sign, 0);
+    return __hiloint2double((int)(sign | ((ex + 896u) << 20) | (man >> 3)), (int)(man << 29));
+}
 
 // ---------------------------------------------------------------------------
 // S2M: M_b(s_k) = sum_{j in b} q_j exp(i k s_k . (y_j - c_b)) at the leaf level
@@ -465,8 +475,8 @@ __global__ void __launch_bounds__(128) k_p2p_mixed_warp(
     cxf* wq = shq[warp];
     for (int r0 = 0; r0 < R; r0 += kRC) {
         const int rn = kRC == 1 ? 1 : min(kRC, R - r0);
-        cxd acc[kRC];
-        for (int r = 0; r < kRC; ++r) acc[r] = mk<double>(0, 0);
+        dfacc ax[kRC], ay[kRC];   // float32 tile sums gathered in double-float
+        for (int r = 0; r < kRC; ++r) ax[r] = ay[r] = dfacc{0.f, 0.f};
         for (int nb = noff[b]; nb < noff[b + 1]; ++nb) {
             const int s = nidx[nb];
             const int s0 = sstart[s], sc = scount[s];
@@ -509,13 +519,146 @@ __global__ void __launch_bounds__(128) k_p2p_mixed_warp(
                         for (int r = 0; r < rn; ++r) mac(tile[r], g, wq[jj * kRC + r]);
                 }
                 for (int r = 0; r < rn; ++r) {
-                    acc[r].x += (double)tile[r].x;
-                    acc[r].y += (double)tile[r].y;
+                    dfacc_add(ax[r], df{tile[r].x, 0.f});
+                    dfacc_add(ay[r], df{tile[r].y, 0.f});
                 }
             }
         }
         if (active)
-            for (int r = 0; r < rn; ++r) phis[(int64_t)(t0 + ti) * R + r0 + r] = a.inv_unit * acc[r];
+            for (int r = 0; r < rn; ++r)
+                phis[(int64_t)(t0 + ti) * R + r0 + r] =
+                    mk<double>(a.inv_unit * df_to_double(dfacc_get(ax[r])), a.inv_unit * df_to_double(dfacc_get(ay[r])));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Symmetric mixed near field (sources = targets, one right-hand side).  G is symmetric,
+// so the units of box b evaluate each pair with a neighbour s > b once and use it both
+// ways: phi_i += G_ij q_j in registers, phi_j += G_ij q_i summed over the warp's 32
+// targets for groups of 8 sources (recursive halving with shuffles, then a butterfly)
+// and added atomically; pairs inside box b run one way.  phi must be zero on entry.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ cxf sel(bool c, cxf a, cxf b) { return c ? a : b; }
+
+// sum of v[k] over the warp for k = 0..7; lane l returns the total of k = (l >> 2) & 7
+__device__ __forceinline__ cxf warp_reduce8(cxf v[8], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const cxf send = sel(b4, v[i], v[i + 4]), keep = sel(b4, v[i + 4], v[i]);
+        v[i] = mk<float>(keep.x + __shfl_xor_sync(0xffffffffu, send.x, 16),
+                         keep.y + __shfl_xor_sync(0xffffffffu, send.y, 16));
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const cxf send = sel(b3, v[i], v[i + 2]), keep = sel(b3, v[i + 2], v[i]);
+        v[i] = mk<float>(keep.x + __shfl_xor_sync(0xffffffffu, send.x, 8),
+                         keep.y + __shfl_xor_sync(0xffffffffu, send.y, 8));
+    }
+    const cxf send = sel(b2, v[0], v[1]), keep = sel(b2, v[1], v[0]);
+    cxf r = mk<float>(keep.x + __shfl_xor_sync(0xffffffffu, send.x, 4),
+                      keep.y + __shfl_xor_sync(0xffffffffu, send.y, 4));
+    r.x += __shfl_xor_sync(0xffffffffu, r.x, 2);
+    r.y += __shfl_xor_sync(0xffffffffu, r.y, 2);
+    r.x += __shfl_xor_sync(0xffffffffu, r.x, 1);
+    r.y += __shfl_xor_sync(0xffffffffu, r.y, 1);
+    return r;
+}
+
+// float32 kernel value of the exact-grid form (target grid/offset gp, op; source sp, so);
+// zero for coincident points
+__device__ __forceinline__ cxf green_grid(float4 gp, float4 op, float4 sp, float4 so, float tau_hi,
+                                          float tau_lo) {
+    const float Dx = gp.x - sp.x, Dy = gp.y - sp.y, Dz = gp.z - sp.z;  // exact
+    const float ex = op.x - so.x, ey = op.y - so.y, ez = op.z - so.z;
+    const float A = fmaf(Dx, Dx, fmaf(Dy, Dy, Dz * Dz));           // exact
+    const float B = fmaf(ex, fmaf(2.0f, Dx, ex), fmaf(ey, fmaf(2.0f, Dy, ey), ez * fmaf(2.0f, Dz, ez)));
+    const float s2 = A + B;
+    const float rho = s2 > 0.0f ? rsqrtf(s2) : 0.0f;
+    const float r0f = s2 * rho;
+    const float e = fmaf(-r0f, r0f, A);
+    const float c = (e + B) * (0.5f * rho);
+    const float th = tau_hi * r0f;
+    float te = fmaf(tau_hi, r0f, -th);
+    te = fmaf(tau_hi, c, te);
+    te = fmaf(tau_lo, r0f, te);
+    const float f = (th - rintf(th)) + te;
+    float sn, cs;
+    __sincosf(6.28318530717958647692f * f, &sn, &cs);
+    return mk<float>(cs * rho, sn * rho);
+}
+
+// one warp per (box, 32-target chunk)
+__global__ void __launch_bounds__(128, 7) k_p2p_mixed_sym_warp(
+    const int2* __restrict__ units, int nunits, const int32_t* __restrict__ start,
+    const int32_t* __restrict__ count, const int32_t* __restrict__ noff, const int32_t* __restrict__ nidx,
+    P2PMixedArgs a, const cxd* __restrict__ qs, cxd* __restrict__ phis) {
+    __shared__ float4 shp[4][kWarpTile], sho[4][kWarpTile];
+    __shared__ cxf shq[4][kWarpTile];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int u = blockIdx.x * 4 + warp;
+    if (u >= nunits) return;                       // warp-uniform
+    const int b = units[u].x, c0 = units[u].y;
+    const int t0 = start[b], tc = count[b];
+    const int ti = c0 + lane;
+    const bool active = ti < tc;
+    float4 gp = make_float4(0, 0, 0, 0), op = gp;
+    cxf qi = mk<float>(0, 0);
+    if (active) {
+        gp = a.tpt[t0 + ti];
+        op = a.tof[t0 + ti];
+        qi = cvt<float>(qs[t0 + ti]);
+    }
+    float4* wp = shp[warp];
+    float4* wo = sho[warp];
+    cxf* wq = shq[warp];
+    dfacc ax = {0.f, 0.f}, ay = {0.f, 0.f};      // float32 tile sums gathered in double-float
+    for (int nb = noff[b]; nb < noff[b + 1]; ++nb) {
+        const int s = nidx[nb];
+        if (s < b) continue;                       // that pair belongs to box s's units
+        const bool both = s > b;
+        const int s0 = start[s], sc = count[s];
+        for (int sb = 0; sb < sc; sb += kWarpTile) {
+            const int sn = min(kWarpTile, sc - sb);
+            __syncwarp();
+            for (int v = lane; v < sn; v += 32) {
+                const int j = s0 + sb + v;
+                wp[v] = a.spt[j];
+                wo[v] = a.sof[j];
+                wq[v] = cvt<float>(qs[j]);
+            }
+            __syncwarp();
+            cxf tile = mk<float>(0, 0);
+            for (int jg = 0; jg < sn; jg += 8) {
+                cxf rv[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    rv[k] = mk<float>(0, 0);
+                    const int jj = jg + k;
+                    if (jj < sn) {                 // warp-uniform
+                        cxf g = green_grid(gp, op, wp[jj], wo[jj], a.tau_hi, a.tau_lo);
+                        if (!active) g = mk<float>(0, 0);
+                        mac(tile, g, wq[jj]);
+                        rv[k] = g * qi;
+                    }
+                }
+                if (both) {                        // warp-uniform
+                    const cxf r = warp_reduce8(rv, lane);
+                    const int k = (lane >> 2) & 7;
+                    if ((lane & 3) == 0 && jg + k < sn) {
+                        cxd* o = phis + (s0 + sb + jg + k);
+                        atomicAdd(&o->x, f2d_bits(a.inv_unit_f * r.x));
+                        atomicAdd(&o->y, f2d_bits(a.inv_unit_f * r.y));
+                    }
+                }
+            }
+            dfacc_add(ax, df{tile.x, 0.f});
+            dfacc_add(ay, df{tile.y, 0.f});
+        }
+    }
+    if (active) {
+        atomicAdd(&phis[t0 + ti].x, a.inv_unit * df_to_double(dfacc_get(ax)));
+        atomicAdd(&phis[t0 + ti].y, a.inv_unit * df_to_double(dfacc_get(ay)));
     }
 }
 
@@ -762,6 +905,28 @@ __global__ void k_scatter_grad(const double* __restrict__ gs, int64_t n, const i
 // ---------------------------------------------------------------------------
 // S: storage type of tables and signatures, C: compute type (double-float for float64
 // levels of the mixed policy)
+// complex multiply-accumulate of the list sum: plain for float / double; for double-float
+// the four Dekker products go straight into lazy accumulators (no per-term renormalisation)
+template <typename C>
+struct M2LAcc {
+    cx<C> v;
+    __device__ __forceinline__ void zero() { v = mk<C>(rval<C>(0.0), rval<C>(0.0)); }
+    __device__ __forceinline__ void mac(cx<C> t, cx<C> m) { v = v + t * m; }
+    __device__ __forceinline__ cx<C> get() const { return v; }
+};
+template <>
+struct M2LAcc<df> {
+    dfacc x, y;
+    __device__ __forceinline__ void zero() { x = y = dfacc{0.f, 0.f}; }
+    __device__ __forceinline__ void mac(cx<df> t, cx<df> m) {
+        dfacc_add_prod(x, t.x, m.x);
+        dfacc_add_prod(x, df_neg(t.y), m.y);
+        dfacc_add_prod(y, t.x, m.y);
+        dfacc_add_prod(y, t.y, m.x);
+    }
+    __device__ __forceinline__ cx<df> get() const { return mk<df>(dfacc_get(x), dfacc_get(y)); }
+};
+
 template <typename S, typename C>
 __global__ void k_m2l(int nbox, int64_t K, const int32_t* __restrict__ ioff, const int32_t* __restrict__ iidx,
                       const int32_t* __restrict__ iv, const int32_t* __restrict__ tslot,
@@ -772,13 +937,13 @@ __global__ void k_m2l(int nbox, int64_t K, const int32_t* __restrict__ ioff, con
     if (k >= K) return;
     const int l0 = ioff[a], l1 = ioff[a + 1];
     for (int r = 0; r < R_; ++r) {
-        cx<C> acc = mk<C>(rval<C>(0.0), rval<C>(0.0));
+        M2LAcc<C> acc;
+        acc.zero();
         for (int t = l0; t < l1; ++t) {
             const int b = iidx[t];
-            const cx<C> tv = cvt<C>(T[(int64_t)tslot[iv[t]] * K + k]);
-            acc = acc + tv * cvt<C>(M[((int64_t)b * R_ + r) * K + k]);
+            acc.mac(cvt<C>(T[(int64_t)tslot[iv[t]] * K + k]), cvt<C>(M[((int64_t)b * R_ + r) * K + k]));
         }
-        I[((int64_t)a * R_ + r) * K + k] = cvt<S>(acc);
+        I[((int64_t)a * R_ + r) * K + k] = cvt<S>(acc.get());
     }
 }
 
