@@ -107,6 +107,11 @@ typedef struct {
      * with eps >= 1e-6), HFMM_LEVEL_DF (double-float, mixed policy with 1e-11 <= eps < 1e-6)
      * or HFMM_LEVEL_FP64 (float64 policy, or eps < 1e-11) */
     int near_precision;
+    /* target-source pairs inside one leaf box (part of p2p_pairs) */
+    int64_t p2p_self_pairs;
+    /* 1 when sources = targets and the near field evaluates each pair of distinct
+     * neighbouring boxes once for both directions (float32 near field, one RHS) */
+    int near_symmetric;
 } hfmm_info;
 
 /* Fill *opt with the defaults listed above. */

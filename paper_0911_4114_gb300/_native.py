@@ -48,7 +48,8 @@ class Info(ctypes.Structure):
                 ("level_round_est", ctypes.c_double * MAX_LEVELS),
                 ("level_ilist_total", ctypes.c_int * MAX_LEVELS),
                 ("stage_ms", ctypes.c_double * N_STAGES), ("workspace_bytes", ctypes.c_int64),
-                ("near_precision", ctypes.c_int)]
+                ("near_precision", ctypes.c_int), ("p2p_self_pairs", ctypes.c_int64),
+                ("near_symmetric", ctypes.c_int)]
 
 
 _lib = None

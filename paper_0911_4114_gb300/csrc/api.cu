@@ -651,8 +651,12 @@ void launch_s2m(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false)
     const double kt = P->hp.kappa / (2.0 * 3.14159265358979323846);
     dim3 grid(d.nbox, nblk(d.qv.npair, kS2MThreads));
     if (std::is_same<T, double>::value && use_df(P, lf)) {
-        k_s2m_df<<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt, P->cis_tab,
-                                               (cx<df>*)out, sign, wk);
+        if (R == 1)
+            k_s2m_df<1><<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt,
+                                                      P->cis_tab, (cx<df>*)out, sign, wk);
+        else
+            k_s2m_df<4><<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt,
+                                                      P->cis_tab, (cx<df>*)out, sign, wk);
         return;
     }
     k_s2m<T><<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt, (cx<T>*)out,
@@ -679,9 +683,14 @@ void launch_l2t(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false)
     if (std::is_same<T, double>::value && use_df(P, lf)) {
         const int2* units = transposed ? P->sunits : P->tunits;
         const int nu = transposed ? P->nsunits : P->ntunits;
-        if (nu > 0)
-            k_l2t_df_warp<<<nblk(nu, 4), 128, 0, st>>>(units, nu, d.bv, d.qv, d.sdf, start, count, px, py, pz,
-                                                      (const cx<df>*)in, R, P->cis_tab, out, sign, wk);
+        if (nu > 0) {
+            if (R == 1)
+                k_l2t_df_warp<1><<<nblk(nu, 4), 128, 0, st>>>(units, nu, d.bv, d.qv, d.sdf, start, count, px, py, pz,
+                                                             (const cx<df>*)in, R, P->cis_tab, out, sign, wk);
+            else
+                k_l2t_df_warp<4><<<nblk(nu, 4), 128, 0, st>>>(units, nu, d.bv, d.qv, d.sdf, start, count, px, py, pz,
+                                                             (const cx<df>*)in, R, P->cis_tab, out, sign, wk);
+        }
         return;
     }
     k_l2t<T><<<grid, kL2TThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, (const cx<T>*)in, R, kt, out,
@@ -1107,6 +1116,8 @@ hfmm_status hfmm_query(hfmm_plan_t P, hfmm_info* info) {
         }
     }
     info->workspace_bytes = P->workspace;
+    info->p2p_self_pairs = hp.p2p_self_pairs;
+    info->near_symmetric = (P->sym && P->near_prec == kFP32) ? 1 : 0;
     info->near_precision = P->near_prec == kFP32 ? HFMM_LEVEL_FP32 : (P->near_prec == kDF ? HFMM_LEVEL_DF : HFMM_LEVEL_FP64);
     if (P->ev_recorded) {
         if (cudaEventSynchronize(P->ev[HFMM_N_STAGES]) != cudaSuccess)

@@ -66,6 +66,7 @@ struct HostPlan {
     std::vector<int32_t> src_start, src_count, tgt_start, tgt_count;  // per leaf box
     std::vector<int32_t> noff, nidx;                // leaf neighbour lists (CSR)
     int64_t p2p_pairs = 0;
+    int64_t p2p_self_pairs = 0;   // pairs inside one leaf box (target count x source count)
     // per level l = 2..lf
     std::vector<LevelPlan> lp;                      // indexed by level (0, 1 unused)
 };

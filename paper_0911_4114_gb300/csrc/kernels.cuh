@@ -311,13 +311,15 @@ __global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstar
 // split into df pairs; the phase in turns is reduced by its nearest integer and cis_turns
 // evaluates exp(2 pi i r).
 // ---------------------------------------------------------------------------
+// kRC right-hand sides per plane-wave evaluation (1, or 4 when R > 1).
+template <int kRC>
 __global__ void k_s2m_df(BoxView bx, QuadView qv, const int32_t* __restrict__ sstart,
                          const int32_t* __restrict__ scount, const double* __restrict__ sx,
                          const double* __restrict__ sy, const double* __restrict__ sz,
                          const cxd* __restrict__ qs, int R_, double kappa_turns, const cdf* __restrict__ cis_tab,
                          cx<df>* __restrict__ M, double sign, const double* __restrict__ wk) {
     __shared__ df shd[kS2MTile * 3];
-    __shared__ cdf shq[kS2MTile];
+    __shared__ cdf shq[kS2MTile * kRC];
     __shared__ cdf tab[kCisTableBig];
     for (int v = threadIdx.x; v < kCisTableBig; v += blockDim.x) tab[v] = cis_tab[v];
     const int b = blockIdx.x;
@@ -331,9 +333,11 @@ __global__ void k_s2m_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ss
     }
     const int s0 = sstart[b], sc = scount[b];
     const double cxx = bx.center[3 * b], cyy = bx.center[3 * b + 1], czz = bx.center[3 * b + 2];
-    for (int r = 0; r < R_; ++r) {
+    for (int r0 = 0; r0 < R_; r0 += kRC) {
+        const int rn = kRC == 1 ? 1 : min(kRC, R_ - r0);
         // U = sum q C, V = sum q S with C + iS = exp(i k s_k . d)
-        dfacc ux = {0.f, 0.f}, uy = {0.f, 0.f}, vx = {0.f, 0.f}, vy = {0.f, 0.f};
+        dfacc ux[kRC], uy[kRC], vx[kRC], vy[kRC];
+        for (int r = 0; r < kRC; ++r) ux[r] = uy[r] = vx[r] = vy[r] = dfacc{0.f, 0.f};
         for (int jb = 0; jb < sc; jb += kS2MTile) {
             const int jn = min(kS2MTile, sc - jb);
             __syncthreads();
@@ -342,32 +346,37 @@ __global__ void k_s2m_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ss
                 shd[3 * u] = df_from_double(sign * (sx[j] - cxx));
                 shd[3 * u + 1] = df_from_double(sign * (sy[j] - cyy));
                 shd[3 * u + 2] = df_from_double(sign * (sz[j] - czz));
-                const cxd qq = qs[(int64_t)j * R_ + r];
-                shq[u] = cdf{df_from_double(qq.x), df_from_double(qq.y)};
+                for (int r = 0; r < rn; ++r) {
+                    const cxd qq = qs[(int64_t)j * R_ + r0 + r];
+                    shq[u * kRC + r] = cdf{df_from_double(qq.x), df_from_double(qq.y)};
+                }
             }
             __syncthreads();
             if (active)
                 for (int jj = 0; jj < jn; ++jj) {
                     const cdf e = cis_turns_big(df_dot3(s, &shd[3 * jj]), tab);
-                    const cdf q = shq[jj];
-                    dfacc_add_prod(ux, q.x, e.x);
-                    dfacc_add_prod(uy, q.y, e.x);
-                    dfacc_add_prod(vx, q.x, e.y);
-                    dfacc_add_prod(vy, q.y, e.y);
+                    for (int r = 0; r < rn; ++r) {
+                        const cdf q = shq[jj * kRC + r];
+                        dfacc_add_prod(ux[r], q.x, e.x);
+                        dfacc_add_prod(uy[r], q.y, e.x);
+                        dfacc_add_prod(vx[r], q.x, e.y);
+                        dfacc_add_prod(vy[r], q.y, e.y);
+                    }
                 }
         }
-        if (active) {
-            const df Ux = dfacc_get(ux), Uy = dfacc_get(uy), Vx = dfacc_get(vx), Vy = dfacc_get(vy);
-            cdf a = {df_sub(Ux, Vy), df_add(Uy, Vx)};   // M(k)  = U + iV
-            cdf c = {df_add(Ux, Vy), df_sub(Uy, Vx)};   // M(k') = U - iV
-            if (wk) {
-                const df wa = df_from_double(wk[kk2.x]), wc = df_from_double(wk[kk2.y]);
-                a = cdf{df_mul(a.x, wa), df_mul(a.y, wa)};
-                c = cdf{df_mul(c.x, wc), df_mul(c.y, wc)};
+        if (active)
+            for (int r = 0; r < rn; ++r) {
+                const df Ux = dfacc_get(ux[r]), Uy = dfacc_get(uy[r]), Vx = dfacc_get(vx[r]), Vy = dfacc_get(vy[r]);
+                cdf a = {df_sub(Ux, Vy), df_add(Uy, Vx)};   // M(k)  = U + iV
+                cdf c = {df_add(Ux, Vy), df_sub(Uy, Vx)};   // M(k') = U - iV
+                if (wk) {
+                    const df wa = df_from_double(wk[kk2.x]), wc = df_from_double(wk[kk2.y]);
+                    a = cdf{df_mul(a.x, wa), df_mul(a.y, wa)};
+                    c = cdf{df_mul(c.x, wc), df_mul(c.y, wc)};
+                }
+                M[((int64_t)b * R_ + r0 + r) * qv.K + kk2.x] = mk<df>(a.x, a.y);
+                M[((int64_t)b * R_ + r0 + r) * qv.K + kk2.y] = mk<df>(c.x, c.y);
             }
-            M[((int64_t)b * R_ + r) * qv.K + kk2.x] = mk<df>(a.x, a.y);
-            M[((int64_t)b * R_ + r) * qv.K + kk2.y] = mk<df>(c.x, c.y);
-        }
     }
 }
 
@@ -379,15 +388,18 @@ __global__ void k_s2m_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ss
 constexpr int kWarpTile = 64;    // quadrature samples (or sources) staged per warp step
 
 // signature -> points, double-float (L2T: targets, sign +1, weights; transposed S2M: sources,
-// sign -1, no weights); sdf = s_k * kappa / 2 pi as df triples, precomputed per level
+// sign -1, no weights); sdf = s_k * kappa / 2 pi as df triples, precomputed per level.
+// kRC right-hand sides per plane-wave evaluation.
+template <int kRC>
 __global__ void __launch_bounds__(128) k_l2t_df_warp(
     const int2* __restrict__ units, int nunits, BoxView bx, QuadView qv, const df* __restrict__ sdf,
     const int32_t* __restrict__ pstart, const int32_t* __restrict__ pcount, const double* __restrict__ px,
     const double* __restrict__ py, const double* __restrict__ pz, const cx<df>* __restrict__ L, int R_,
     const cdf* __restrict__ cis_tab, cxd* __restrict__ out, double sign, const double* __restrict__ wk) {
+    constexpr int kTile = kRC == 1 ? kWarpTile : 16;   // pairs staged per warp step
     __shared__ cdf tab[kCisTableBig];
-    __shared__ df shs[4][kWarpTile * 3];
-    __shared__ cdf shp[4][kWarpTile], shiq[4][kWarpTile];
+    __shared__ df shs[4][kTile * 3];
+    __shared__ cdf shp[4][kTile * kRC], shiq[4][kTile * kRC];
     for (int v = threadIdx.x; v < kCisTableBig; v += blockDim.x) tab[v] = cis_tab[v];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -407,43 +419,53 @@ __global__ void __launch_bounds__(128) k_l2t_df_warp(
     df* ss = shs[warp];
     cdf* sp = shp[warp];
     cdf* siq = shiq[warp];
-    for (int r = 0; r < R_; ++r) {
-        const cx<df>* Lb = L + ((int64_t)b * R_ + r) * qv.K;
-        dfacc ax = {0.f, 0.f}, ay = {0.f, 0.f};
-        for (int64_t pb = 0; pb < qv.npair; pb += kWarpTile) {
-            const int pn = (int)min((int64_t)kWarpTile, qv.npair - pb);
+    for (int r0 = 0; r0 < R_; r0 += kRC) {
+        const int rn = kRC == 1 ? 1 : min(kRC, R_ - r0);
+        dfacc ax[kRC], ay[kRC];
+        for (int r = 0; r < kRC; ++r) ax[r] = ay[r] = dfacc{0.f, 0.f};
+        for (int64_t pb = 0; pb < qv.npair; pb += kTile) {
+            const int pn = (int)min((int64_t)kTile, qv.npair - pb);
             __syncwarp();
             for (int v = lane; v < pn; v += 32) {
                 const int2 kk2 = qv.pair[pb + v];
                 ss[3 * v] = sdf[3 * kk2.x];
                 ss[3 * v + 1] = sdf[3 * kk2.x + 1];
                 ss[3 * v + 2] = sdf[3 * kk2.x + 2];
-                cdf A = cdf{Lb[kk2.x].x, Lb[kk2.x].y}, B = cdf{Lb[kk2.y].x, Lb[kk2.y].y};
+                df wa = {1.f, 0.f}, wb = {1.f, 0.f};
                 if (wk) {
-                    const df wa = df_from_double(wk[kk2.x]), wb = df_from_double(wk[kk2.y]);
-                    A = cdf{df_mul(A.x, wa), df_mul(A.y, wa)};
-                    B = cdf{df_mul(B.x, wb), df_mul(B.y, wb)};
+                    wa = df_from_double(wk[kk2.x]);
+                    wb = df_from_double(wk[kk2.y]);
                 }
-                sp[v] = cdf{df_add(A.x, B.x), df_add(A.y, B.y)};    // P = A + B
-                siq[v] = cdf{df_sub(B.y, A.y), df_sub(A.x, B.x)};   // i Q, Q = A - B
+                for (int r = 0; r < rn; ++r) {
+                    const cx<df>* Lb = L + ((int64_t)b * R_ + r0 + r) * qv.K;
+                    cdf A = cdf{Lb[kk2.x].x, Lb[kk2.x].y}, B = cdf{Lb[kk2.y].x, Lb[kk2.y].y};
+                    if (wk) {
+                        A = cdf{df_mul(A.x, wa), df_mul(A.y, wa)};
+                        B = cdf{df_mul(B.x, wb), df_mul(B.y, wb)};
+                    }
+                    sp[v * kRC + r] = cdf{df_add(A.x, B.x), df_add(A.y, B.y)};    // P = A + B
+                    siq[v * kRC + r] = cdf{df_sub(B.y, A.y), df_sub(A.x, B.x)};   // i Q, Q = A - B
+                }
             }
             __syncwarp();
             if (active)
                 for (int kk = 0; kk < pn; ++kk) {
                     const cdf e = cis_turns_big(df_dot3(&ss[3 * kk], d), tab);
-                    const cdf P = sp[kk], iQ = siq[kk];
-                    dfacc_add_prod(ax, P.x, e.x);
-                    dfacc_add_prod(ax, iQ.x, e.y);
-                    dfacc_add_prod(ay, P.y, e.x);
-                    dfacc_add_prod(ay, iQ.y, e.y);
+                    for (int r = 0; r < rn; ++r) {
+                        const cdf P = sp[kk * kRC + r], iQ = siq[kk * kRC + r];
+                        dfacc_add_prod(ax[r], P.x, e.x);
+                        dfacc_add_prod(ax[r], iQ.x, e.y);
+                        dfacc_add_prod(ay[r], P.y, e.x);
+                        dfacc_add_prod(ay[r], iQ.y, e.y);
+                    }
                 }
         }
-        const cdf acc = {dfacc_get(ax), dfacc_get(ay)};
-        if (active) {
-            cxd& o = out[(int64_t)(t0 + ti) * R_ + r];
-            o.x += df_to_double(acc.x);
-            o.y += df_to_double(acc.y);
-        }
+        if (active)
+            for (int r = 0; r < rn; ++r) {
+                cxd& o = out[(int64_t)(t0 + ti) * R_ + r0 + r];
+                o.x += df_to_double(dfacc_get(ax[r]));
+                o.y += df_to_double(dfacc_get(ay[r]));
+            }
     }
 }
 

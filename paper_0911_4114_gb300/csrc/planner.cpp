@@ -547,6 +547,8 @@ static void build_tree(HostPlan& hp) {
             hp.nidx[hp.noff[a] + t] = (int32_t)nf[a][t].second;
             hp.p2p_pairs += (int64_t)hp.tgt_count[a] * hp.src_count[nf[a][t].second];
         }
+    hp.p2p_self_pairs = 0;
+    for (int64_t a = 0; a < nb; ++a) hp.p2p_self_pairs += (int64_t)hp.tgt_count[a] * hp.src_count[a];
 }
 
 // ---------------------------------------------------------------------------

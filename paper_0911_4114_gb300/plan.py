@@ -149,7 +149,8 @@ class FmmPlan:
                     lf=lf, p2p_pairs=inf.p2p_pairs, nbox=[inf.level_nbox[l] for l in range(lf + 1)],
                     levels=levels, stage_ms={nat.STAGES[i]: inf.stage_ms[i] for i in range(nat.N_STAGES)},
                     workspace_bytes=inf.workspace_bytes,
-                    near_precision=_PREC_NAMES[inf.near_precision])
+                    near_precision=_PREC_NAMES[inf.near_precision],
+                    p2p_self_pairs=inf.p2p_self_pairs, near_symmetric=bool(inf.near_symmetric))
 
     def debug_get(self, what, level=0, arg=0):
         L = nat.lib()

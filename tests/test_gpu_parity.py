@@ -159,3 +159,28 @@ def test_symmetric_near_field_matches_one_way(name):
     adj1 = lib.apply_adjoint(w[:, 0].contiguous()).cpu().numpy()
     assert rel(adj1, adj2[:, 0]) <= 1e-6
     assert rel(one, direct.direct(s, s, q[:, 0], kappa)) <= eps
+
+
+def test_double_float_leaf_multi_rhs():
+    """Double-float leaf level (S2M / L2T on the float32 pipe) with several right-hand
+    sides: the kernels evaluate each plane wave once for a group of four RHS.  Column 1
+    of a three-RHS apply must match a one-RHS apply (which also takes the symmetric
+    near field) to float32 near-field round-off, the three-RHS apply must match the
+    float64 policy to eps, and the adjoint must satisfy the dot-product identity."""
+    import torch
+    x = wl.sphere(20000, wl.rng(15))
+    g = wl.rng(15, salt=1)
+    q = wl.charges(len(x), 3, g)
+    lib = FmmPlan(x, x, 64.0, 1e-6, precision="mixed", max_rhs=3)
+    info = lib.info()
+    assert info["levels"][info["lf"]]["precision"] == "df"
+    three = run_apply(lib, q)
+    one = run_apply(lib, q[:, 1])
+    assert rel(one, three[:, 1]) <= 1e-6
+    ref = run_apply(FmmPlan(x, x, 64.0, 1e-6, precision="fp64", max_rhs=3), q)
+    assert rel(three, ref) <= 1e-6
+    w = wl.charges(len(x), 3, g)
+    aw = lib.apply_adjoint(torch.as_tensor(w, device="cuda")).cpu().numpy()
+    lhs = np.vdot(w, three)                          # <w, A q>
+    rhs = np.vdot(aw, q)                             # <A^H w, q>
+    assert abs(lhs - rhs) <= 1e-6 * abs(lhs)
