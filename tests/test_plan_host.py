@@ -129,3 +129,28 @@ def test_all_316_reflections_match_direct():
         b = oq.tsll(lp.ell, 60.0, d * 0.25, lp.ntheta, lp.nphi)
         worst = max(worst, np.max(np.abs(a - b)) / np.max(np.abs(b)))
     assert worst < 1e-12
+
+
+def test_near_field_policy_and_symmetry_flags():
+    """Host plan properties that select kernels: the near-field arithmetic follows the
+    precision policy and eps (mixed: float32 for eps >= 1e-6, double-float down to 1e-11,
+    float64 below; float64 policy: float64); the symmetric near field is chosen exactly
+    when the two point sets are equal (same values, not just the same multiset) and the
+    near field is float32; self pairs are sum_b n_b^2 over leaf boxes."""
+    rng = np.random.default_rng(zlib.crc32(b"near-policy"))
+    x = rng.random((3000, 3))
+    kw = dict(depth=3, root=(0, 0, 0, 1.0), device=-1)
+    cases = [("mixed", 1e-5, "fp32"), ("mixed", 1e-6, "fp32"), ("mixed", 9.9e-7, "df"),
+             ("mixed", 1e-11, "df"), ("mixed", 9e-12, "fp64"), ("fp64", 1e-5, "fp64")]
+    for prec, eps, want in cases:
+        info = FmmPlan(x, x, 20.0, eps, precision=prec, **kw).info()
+        assert info["near_precision"] == want, (prec, eps)
+        assert info["near_symmetric"] == (want == "fp32")
+    perm = rng.permutation(len(x))
+    assert not FmmPlan(x, x[perm], 20.0, 1e-5, precision="mixed", **kw).info()["near_symmetric"]
+    assert FmmPlan(x, x.copy(), 20.0, 1e-5, precision="mixed", **kw).info()["near_symmetric"]
+    lib = FmmPlan(x, x, 20.0, 1e-5, precision="mixed", **kw)
+    t = ofmm.Plan(x, x, 20.0, 1e-5, precision="mixed", depth=3, root=(0, 0, 0, 1.0)).tree
+    info = lib.info()
+    assert info["p2p_self_pairs"] == int(np.sum(t.src_count.astype(np.int64) * t.tgt_count))
+    assert 0 < info["p2p_self_pairs"] < info["p2p_pairs"]
