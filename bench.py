@@ -287,10 +287,10 @@ def main():
                         peak_note=alu_note)
         if stage in ("s2m", "l2t") and lev.get("precision") == "df":
             units = float(lev["K"]) / 2 * (len(t) if stage == "l2t" else len(s))
-            ops = 193.0 * units                          # double-float ops per (point, antipodal pair)
+            ops = 156.0 * units                          # double-float ops per (point, antipodal pair)
             return dict(kernel="k_l2t_df_warp" if stage == "l2t" else "k_s2m_df", bound="alu",
                         achieved=ops / (ms * 1e-3) / 1e9, peak=fp32_peak, unit="Gop/s",
-                        unit_work="193 float32 ops per (point, antipodal sample pair) in double-float",
+                        unit_work="156 float32 ops per (point, antipodal sample pair) in double-float",
                         peak_note=alu_note)
         if stage in ("m2l", "m2m", "l2l"):
             tot = 0.0

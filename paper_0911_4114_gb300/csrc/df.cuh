@@ -4,8 +4,8 @@
 // _rn intrinsics so the compiler cannot contract or reassociate it.
 //
 // cis_turns_big(t) = exp(2 pi i t): reduction by a 1024-entry table of exp(2 pi i j / 1024)
-// (stored as df pairs), Taylor polynomials of sin and cos on |x| <= pi/1024 in df arithmetic,
-// then one complex df product.
+// (stored as df pairs), Taylor polynomials of sin and cos on |x| <= pi/1024, then one complex
+// df product.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -135,25 +135,30 @@ __device__ __forceinline__ df df_dot3(const df* s, const df* d) {
     return df_fast_sum(b.hi, __fadd_rn(__fadd_rn(a.lo, b.lo), e));
 }
 
-// exp(2 pi i t) for any df t (turns): one reduction by the nearest 1/1024 of a turn
-// (exact on the leading part), table of exp(2 pi i j / 1024), Taylor polynomials on
-// |x| <= pi / 1024 (cos to y^2/24, sin to x y^2/120; dropped terms < 2^-58)
+// exp(2 pi i t) for any df t (turns): one reduction by the nearest 1/1024 of a turn (exact
+// on the leading part), x = 2 pi r with |x| <= pi / 1024, then Taylor terms.  The result has
+// modulus 1, so each term needs an absolute error below ~2^-49 only: x, x^2 and 1 - x^2/2
+// are kept as double-float pairs (exact products by FMA, an exact Fast2Sum for 1 - x^2/2);
+// x^4/24 (< 4e-12), x^3/6 (< 5e-9) and x^5/120 (< 3e-15) enter as float32 corrections of
+// the low parts (rounding below 3e-16).  One fused complex product with the table entry.
 __device__ __forceinline__ cdf cis_turns_big(df t, const cdf* tab) {
     const float jf = rintf(__fmul_rn(t.hi, (float)kCisTableBig));
-    df rr = df_fast_sum(__fsub_rn(t.hi, __fmul_rn(jf, 1.0f / (float)kCisTableBig)), t.lo);  // exact
+    const df rr = df_fast_sum(__fsub_rn(t.hi, __fmul_rn(jf, 1.0f / (float)kCisTableBig)), t.lo);  // exact
     const df two_pi = {6.2831854820251465f, -1.7484555314695172e-07f};
-    df x = df_mul(rr, two_pi);
-    df y = df_mul(x, x);
-    const float yh = y.hi;
-    // cos = 1 - y/2 + y^2/24 : (y/2 - y^2/24) in df, then 1 - that
-    df cm = df_add_big(df{__fmul_rn(y.hi, 0.5f), __fmul_rn(y.lo, 0.5f)}, df{__fmul_rn(__fmul_rn(yh, yh), -1.0f / 24.0f), 0.0f});
-    df cc = df_add_big(df{1.0f, 0.0f}, df_neg(cm));
-    // sin = x - x^3/6 + x^5/120: x^3/6 in df, x^5/120 (< 2^-48) in float32
-    const df c6 = {0.1666666716337204f, -4.967053879312289e-09f};
-    const df xy = df_mul(x, y);
-    df sp = df_mul(xy, c6);
-    sp = df_add_big(sp, df{__fmul_rn(__fmul_rn(xy.hi, yh), -1.0f / 120.0f), 0.0f});
-    df ss = df_add_big(x, df_neg(sp));
+    const df x = df_mul(rr, two_pi);
+    // y = x^2 = yh + ye (|ye| small, not renormalised)
+    const float yh = __fmul_rn(x.hi, x.hi);
+    const float ye = __fmaf_rn(__fadd_rn(x.hi, x.hi), x.lo, __fmaf_rn(x.hi, x.hi, -yh));
+    // cos x = 1 - y/2 + y^2/24: 1 - yh/2 exactly as (c, ce), the rest into the low part
+    const float h = __fmul_rn(-0.5f, yh);
+    const float c = __fadd_rn(1.0f, h);
+    const float ce = __fsub_rn(h, __fsub_rn(c, 1.0f));
+    const float clo = __fmaf_rn(__fmul_rn(yh, yh), 1.0f / 24.0f, __fmaf_rn(-0.5f, ye, ce));
+    const df cc = df_fast_sum(c, clo);
+    // sin x = x - x^3/6 + x^5/120: the two odd terms as one float32 correction
+    const float x3 = __fmul_rn(x.hi, yh);
+    const float corr = __fmul_rn(x3, __fmaf_rn(yh, 1.0f / 120.0f, -1.0f / 6.0f));
+    const df ss = df_fast_sum(x.hi, __fadd_rn(x.lo, corr));
     const int j = ((int)jf) & (kCisTableBig - 1);
     return cdf_mul(tab[j], cdf{cc, ss});
 }
