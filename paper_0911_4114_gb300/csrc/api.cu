@@ -90,6 +90,8 @@ struct hfmm_plan_s {
     int max_src_leaf = 1, max_tgt_leaf = 1;   // largest leaf-box point counts (grid heights)
     int2 *tunits = nullptr, *sunits = nullptr;  // (leaf box, first point) of every 32-point chunk
     int ntunits = 0, nsunits = 0;
+    int2* symunits = nullptr;                   // the same chunks, heaviest first (symmetric near field)
+    int nsymunits = 0;
     double* gsort = nullptr;    // sorted position gradient (ns, 3)
     DevLevel lev[kMaxLevels];
     Requad up[kMaxLevels];    // up[l]: level l -> l-1
@@ -318,6 +320,25 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
         };
         TRY(chunks(hp.tgt_count, &P->tunits, &P->ntunits, 32));
         TRY(chunks(hp.src_count, &P->sunits, &P->nsunits, 32));
+        if (P->sym) {
+            // symmetric near field: a unit of box b sums over neighbours s >= b, so the work of
+            // units varies widely; launch them heaviest first (longest-processing-time order)
+            std::vector<std::pair<int64_t, int2>> w;
+            for (size_t b = 0; b < hp.tgt_count.size(); ++b) {
+                int64_t work = 0;
+                for (int32_t t = hp.noff[b]; t < hp.noff[b + 1]; ++t)
+                    if (hp.nidx[t] >= (int32_t)b) work += hp.src_count[hp.nidx[t]];
+                for (int c = 0; c < hp.tgt_count[b]; c += 32)
+                    w.push_back({work * std::min(32, hp.tgt_count[b] - c), make_int2((int)b, c)});
+            }
+            std::stable_sort(w.begin(), w.end(), [](const std::pair<int64_t, int2>& a, const std::pair<int64_t, int2>& b) {
+                return a.first > b.first;
+            });
+            std::vector<int2> u(w.size());
+            for (size_t i = 0; i < w.size(); ++i) u[i] = w[i].second;
+            P->nsymunits = (int)u.size();
+            TRY(upload(P, &P->symunits, u));
+        }
 
     }
     for (int32_t c : hp.src_count) P->max_src_leaf = std::max(P->max_src_leaf, (int)c);
@@ -490,17 +511,17 @@ void launch_up(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
     DevLevel& c = P->lev[l];
     DevLevel& p = P->lev[l - 1];
     const size_t sm = (size_t)kWarps * 2 * ra.maxlen * sizeof(cx<Tc>);
+    const size_t sm3 = (size_t)kWarps * 3 * ra.maxlen * sizeof(cx<Tc>);   // + per-warp child sum
     cx<Tc>* GA = (cx<Tc>*)P->ga;
     cx<Tc>* GB = (cx<Tc>*)P->gb;
-    smem_opt_in(k_requad_rows_a<Tin, Tc, kNoShift, false>, sm);
-    smem_opt_in(k_requad_cols<Tc, false>, sm);
-    const size_t sm3 = (size_t)kWarps * 3 * ra.maxlen * sizeof(cx<Tc>);   // + per-warp child sum
-    smem_opt_in(k_requad_rows_c_m2m<Tc, Tout, kShiftPlain, false>, sm3);
-    k_requad_rows_a<Tin, Tc, kNoShift, false><<<nblk((int64_t)c.nbox * R * ra.qa.nrows, kWarps), 32 * kWarps, sm, st>>>(
+    smem_opt_in(k_requad_spec_a<Tin, Tc, kNoShift>, sm);
+    smem_opt_in(k_requad_spec_cols<Tc>, sm);
+    smem_opt_in(k_requad_spec_c_m2m<Tc, Tout>, sm3);
+    k_requad_spec_a<Tin, Tc, kNoShift><<<nblk((int64_t)c.nbox * R * ra.qa.nrows, kWarps), 32 * kWarps, sm, st>>>(
         ra, c.nbox, R, (const cx<Tin>*)c.M, nullptr, nullptr, nullptr, GA);
-    k_requad_cols<Tc, false><<<nblk((int64_t)c.nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(
+    k_requad_spec_cols<Tc><<<nblk((int64_t)c.nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(
         ra, c.nbox, R, GA, GB);
-    k_requad_rows_c_m2m<Tc, Tout, kShiftPlain, false><<<nblk((int64_t)p.nbox * R * ra.qb.nrows, kWarps), 32 * kWarps, sm3, st>>>(
+    k_requad_spec_c_m2m<Tc, Tout><<<nblk((int64_t)p.nbox * R * ra.qb.nrows, kWarps), 32 * kWarps, sm3, st>>>(
         ra, p.nbox, R, p.bv.child_start, p.bv.child_count, c.octant, shift_of<Tc>(p), GB, (cx<Tout>*)p.M);
 }
 
@@ -534,14 +555,14 @@ void launch_down(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
     const size_t sm = (size_t)kWarps * 2 * ra.maxlen * sizeof(cx<Tc>);
     cx<Tc>* GA = (cx<Tc>*)P->ga;
     cx<Tc>* GB = (cx<Tc>*)P->gb;
-    smem_opt_in(k_requad_rows_a<Tin, Tc, kShiftConj, false>, sm);
-    smem_opt_in(k_requad_cols<Tc, false>, sm);
-    smem_opt_in(k_requad_rows_c_l2l<Tc, Tout, false>, sm);
-    k_requad_rows_a<Tin, Tc, kShiftConj, false><<<nblk((int64_t)c.nbox * R * ra.qa.nrows, kWarps), 32 * kWarps, sm, st>>>(
+    smem_opt_in(k_requad_spec_a<Tin, Tc, kShiftConj>, sm);
+    smem_opt_in(k_requad_spec_cols<Tc>, sm);
+    smem_opt_in(k_requad_spec_c_l2l<Tc, Tout>, sm);
+    k_requad_spec_a<Tin, Tc, kShiftConj><<<nblk((int64_t)c.nbox * R * ra.qa.nrows, kWarps), 32 * kWarps, sm, st>>>(
         ra, c.nbox, R, (const cx<Tin>*)p.IL, c.bv.parent, c.octant, shift_of<Tc>(p), GA);
-    k_requad_cols<Tc, false><<<nblk((int64_t)c.nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(
+    k_requad_spec_cols<Tc><<<nblk((int64_t)c.nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(
         ra, c.nbox, R, GA, GB);
-    k_requad_rows_c_l2l<Tc, Tout, false><<<nblk((int64_t)c.nbox * R * ra.qb.nrows, kWarps), 32 * kWarps, sm, st>>>(
+    k_requad_spec_c_l2l<Tc, Tout><<<nblk((int64_t)c.nbox * R * ra.qb.nrows, kWarps), 32 * kWarps, sm, st>>>(
         ra, c.nbox, R, GB, (cx<Tout>*)c.IL);
 }
 
@@ -898,9 +919,10 @@ hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_d
     const df kt_df = df_from_double(hp.kappa / (2.0 * 3.14159265358979323846));
     if (P->near_prec == kFP32 && P->sym && R == 1) {
         CK(cudaMemsetAsync(P->phis, 0, sizeof(cxd) * (size_t)hp.nt, st));
-        if (P->ntunits > 0)
-            k_p2p_mixed_sym_warp<<<nblk(P->ntunits, 4), 128, 0, st>>>(P->tunits, P->ntunits, P->tstart, P->tcount,
-                                                                     P->noff, P->nidx, P->mixed, P->qs, P->phis);
+        if (P->nsymunits > 0)
+            k_p2p_mixed_sym_warp<<<nblk(P->nsymunits, 4), 128, 0, st>>>(P->symunits, P->nsymunits, P->tstart,
+                                                                       P->tcount, P->noff, P->nidx, P->mixed, P->qs,
+                                                                       P->phis);
     } else if (P->near_prec == kFP32) {
         if (P->ntunits > 0) {
             if (R == 1)
@@ -984,9 +1006,10 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t P, const void* w, void* out, int nrhs
     const df kt_df = df_from_double(hp.kappa / (2.0 * 3.14159265358979323846));
     if (P->near_prec == kFP32 && P->sym && R == 1) {
         CK(cudaMemsetAsync(P->qs, 0, sizeof(cxd) * (size_t)hp.ns, st));
-        if (P->nsunits > 0)
-            k_p2p_mixed_sym_warp<<<nblk(P->nsunits, 4), 128, 0, st>>>(P->sunits, P->nsunits, P->sstart, P->scount,
-                                                                     P->noff, P->nidx, P->mixed, P->phis, P->qs);
+        if (P->nsymunits > 0)
+            k_p2p_mixed_sym_warp<<<nblk(P->nsymunits, 4), 128, 0, st>>>(P->symunits, P->nsymunits, P->sstart,
+                                                                       P->scount, P->noff, P->nidx, P->mixed, P->phis,
+                                                                       P->qs);
     } else if (P->near_prec == kFP32) {
         P2PMixedArgs a = P->mixed;
         std::swap(a.tpt, a.spt);

@@ -1142,4 +1142,161 @@ __global__ void k_requad_rows_c_m2m(RequadArgs ra, int nparent, int R_, const in
     for (int j = lane; j < len; j += 32) dst[j] = cvt<Tout>(acc[j]);
 }
 
+// ---------------------------------------------------------------------------
+// Forward re-quadrature on phi-Fourier coefficients.  The phi re-sampling of a row and the
+// theta re-sampling of a column act on different axes, so the theta passes may run on the
+// band-limited phi coefficients: the big-grid interpolation of step 1 and the big-length
+// transform of step 5 drop out.  Coefficient f sits in slot (f + big) % big; a shift of phi
+// by pi multiplies it by (-1)^f, so the theta circle of coefficient f is even (f even) or
+// odd (f odd) in theta.  Slots c and big - 1 - c (f = c and f = -(c + 1), opposite parity)
+// share one complex circle; the even and odd parts separate after the re-sampling.  Same
+// bands as the sample passes: min(ceil(n/2), ceil(n'/2)) - 1 for each 1-D step.
+// ---------------------------------------------------------------------------
+// Pass A': rows of grid a -> band-limited coefficients (scaled by 1/N_phi) in GA
+template <typename Tin, typename Tc, int kShift>
+__global__ void k_requad_spec_a(RequadArgs ra, int nbox_seq, int R_, const cx<Tin>* __restrict__ in,
+                                const int32_t* __restrict__ src_box, const int32_t* __restrict__ octant,
+                                const cx<Tc>* __restrict__ shift, cx<Tc>* __restrict__ GA) {
+    extern __shared__ unsigned char smem_raw[];
+    cx<Tc>* sm = reinterpret_cast<cx<Tc>*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cx<Tc>* buf0 = sm + (size_t)warp * 2 * ra.maxlen;
+    cx<Tc>* buf1 = buf0 + ra.maxlen;
+    const int64_t seq = (int64_t)blockIdx.x * kWarps + warp;
+    const int rows = ra.qa.nrows;
+    if (seq >= (int64_t)nbox_seq * R_ * rows) return;
+    const int n = (int)(seq % rows);
+    const int64_t br = seq / rows;
+    const int b = (int)(br / R_), r = (int)(br % R_);
+    const int len = ra.qa.nphi[n];
+    const int64_t o = ra.qa.off[n];
+    const int sb = kShift ? src_box[b] : b;
+    const cx<Tin>* src = in + ((int64_t)sb * R_ + r) * ra.qa.K + o;
+    const cx<Tc>* sh = kShift ? shift + (int64_t)octant[b] * ra.qa.K + o : nullptr;
+    for (int j = lane; j < len; j += 32) {
+        cx<Tc> v = cvt<Tc>(src[j]);
+        if (kShift == kShiftConj) v = v * conj(sh[j]);
+        if (kShift == kShiftPlain) v = v * sh[j];
+        buf0[j] = v;
+    }
+    __syncwarp();
+    const cx<Tc>* pool = reinterpret_cast<const cx<Tc>*>(ra.tw.pool);
+    const cx<Tc>* sp = warp_fft(buf0, buf1, len, false, pool + ra.tw.off[len], lane);
+    const int band = min((len + 1) / 2, (ra.big + 1) / 2) - 1;
+    const Tc scale = rval<Tc>(1.0 / (double)len);
+    cx<Tc>* dst = GA + seq * ra.big;
+    for (int j = lane; j < ra.big; j += 32) {
+        const int f = (2 * j <= ra.big) ? j : j - ra.big;
+        cx<Tc> v = mk<Tc>(rval<Tc>(0.0), rval<Tc>(0.0));
+        if (f <= band && f >= -band) v = scale * sp[(f + len) % len];
+        dst[j] = v;
+    }
+}
+
+// Pass B': one circle per slot pair (c, big - 1 - c), c < big / 2
+template <typename Tc>
+__global__ void k_requad_spec_cols(RequadArgs ra, int nbox_seq, int R_, const cx<Tc>* __restrict__ GA,
+                                   cx<Tc>* __restrict__ GB) {
+    extern __shared__ unsigned char smem_raw[];
+    cx<Tc>* sm = reinterpret_cast<cx<Tc>*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cx<Tc>* buf0 = sm + (size_t)warp * 2 * ra.maxlen;
+    cx<Tc>* buf1 = buf0 + ra.maxlen;
+    const int hb = ra.big / 2;
+    const int64_t seq = (int64_t)blockIdx.x * kWarps + warp;
+    if (seq >= (int64_t)nbox_seq * R_ * hb) return;
+    const int c = (int)(seq % hb);
+    const int64_t br = seq / hb;
+    // slot c holds f = c, slot big - 1 - c holds f = -(c + 1): opposite parity
+    const int s_even = (c % 2 == 0) ? c : ra.big - 1 - c;
+    const int s_odd = (c % 2 == 0) ? ra.big - 1 - c : c;
+    const int nta = ra.qa.ntheta, ntb = ra.qb.ntheta;
+    const int ha = nta / 2, hbr = ntb / 2;
+    const cx<Tc>* ga = GA + br * (int64_t)ra.qa.nrows * ra.big;
+    for (int t = lane; t < nta; t += 32) {
+        const int u = (t <= ha) ? t : nta - t;
+        const cx<Tc> e = ga[(int64_t)u * ra.big + s_even], d = ga[(int64_t)u * ra.big + s_odd];
+        buf0[t] = (t <= ha) ? e + d : e - d;    // the odd circle changes sign past theta = pi
+    }
+    __syncwarp();
+    cx<Tc>* res = warp_resample(buf0, buf1, nta, ntb, ra.tw, lane);
+    const Tc half = rval<Tc>(0.5);
+    cx<Tc>* gb = GB + br * (int64_t)ra.qb.nrows * ra.big;
+    for (int n = lane; n <= hbr; n += 32) {
+        const cx<Tc> y = res[n], ym = res[(ntb - n) % ntb];
+        gb[(int64_t)n * ra.big + s_even] = half * (y + ym);
+        gb[(int64_t)n * ra.big + s_odd] = half * (y - ym);
+    }
+}
+
+// coefficients of a GB' row, limited to the band of a length-len output row, into buf (length len)
+template <typename Tc>
+__device__ __forceinline__ void spec_row_to_buf(const cx<Tc>* row, int big, int len, cx<Tc>* buf, int lane) {
+    const int band = min((big + 1) / 2, (len + 1) / 2) - 1;
+    for (int j = lane; j < len; j += 32) {
+        const int f = (2 * j <= len) ? j : j - len;
+        cx<Tc> v = mk<Tc>(rval<Tc>(0.0), rval<Tc>(0.0));
+        if (f <= band && f >= -band) v = row[(f + big) % big];
+        buf[j] = v;
+    }
+}
+
+// Pass C' (L2L): L_child = rows of grid b from the coefficients + I_child, in place
+template <typename Tc, typename Tout>
+__global__ void k_requad_spec_c_l2l(RequadArgs ra, int nbox_seq, int R_, const cx<Tc>* __restrict__ GB,
+                                    cx<Tout>* __restrict__ IL) {
+    extern __shared__ unsigned char smem_raw[];
+    cx<Tc>* sm = reinterpret_cast<cx<Tc>*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cx<Tc>* buf0 = sm + (size_t)warp * 2 * ra.maxlen;
+    cx<Tc>* buf1 = buf0 + ra.maxlen;
+    const int rows = ra.qb.nrows;
+    const int64_t seq = (int64_t)blockIdx.x * kWarps + warp;
+    if (seq >= (int64_t)nbox_seq * R_ * rows) return;
+    const int n = (int)(seq % rows);
+    const int64_t br = seq / rows;
+    const int len = ra.qb.nphi[n];
+    spec_row_to_buf(GB + seq * ra.big, ra.big, len, buf0, lane);
+    __syncwarp();
+    const cx<Tc>* pool = reinterpret_cast<const cx<Tc>*>(ra.tw.pool);
+    const cx<Tc>* res = warp_fft(buf0, buf1, len, true, pool + ra.tw.off[len], lane);
+    cx<Tout>* dst = IL + br * ra.qb.K + ra.qb.off[n];
+    for (int j = lane; j < len; j += 32) dst[j] = dst[j] + cvt<Tout>(res[j]);
+}
+
+// Pass C' (M2M): M_parent = sum over children of shift * (rows of grid b from the coefficients)
+template <typename Tc, typename Tout>
+__global__ void k_requad_spec_c_m2m(RequadArgs ra, int nparent, int R_, const int32_t* __restrict__ child_start,
+                                    const int32_t* __restrict__ child_count, const int32_t* __restrict__ octant,
+                                    const cx<Tc>* __restrict__ shift, const cx<Tc>* __restrict__ GB,
+                                    cx<Tout>* __restrict__ Mp) {
+    extern __shared__ unsigned char smem_raw[];
+    cx<Tc>* sm = reinterpret_cast<cx<Tc>*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cx<Tc>* buf0 = sm + (size_t)warp * 3 * ra.maxlen;
+    cx<Tc>* buf1 = buf0 + ra.maxlen;
+    cx<Tc>* acc = buf1 + ra.maxlen;   // sum over children; entry j belongs to lane j % 32
+    const int rows = ra.qb.nrows;
+    const int64_t seq = (int64_t)blockIdx.x * kWarps + warp;
+    if (seq >= (int64_t)nparent * R_ * rows) return;
+    const int n = (int)(seq % rows);
+    const int64_t pr = seq / rows;
+    const int p = (int)(pr / R_), r = (int)(pr % R_);
+    const int len = ra.qb.nphi[n];
+    const int64_t o = ra.qb.off[n];
+    for (int j = lane; j < len; j += 32) acc[j] = mk<Tc>(rval<Tc>(0.0), rval<Tc>(0.0));
+    const cx<Tc>* pool = reinterpret_cast<const cx<Tc>*>(ra.tw.pool);
+    const int c0 = child_start[p], cn = child_count[p];
+    for (int c = c0; c < c0 + cn; ++c) {
+        spec_row_to_buf(GB + (((int64_t)c * R_ + r) * rows + n) * ra.big, ra.big, len, buf0, lane);
+        __syncwarp();
+        const cx<Tc>* res = warp_fft(buf0, buf1, len, true, pool + ra.tw.off[len], lane);
+        const cx<Tc>* sh = shift + (int64_t)octant[c] * ra.qb.K + o;
+        for (int j = lane; j < len; j += 32) acc[j] = acc[j] + res[j] * sh[j];
+        __syncwarp();
+    }
+    cx<Tout>* dst = Mp + ((int64_t)p * R_ + r) * ra.qb.K + o;
+    for (int j = lane; j < len; j += 32) dst[j] = cvt<Tout>(acc[j]);
+}
+
 }  // namespace hfmm
