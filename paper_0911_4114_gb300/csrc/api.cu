@@ -76,6 +76,8 @@ struct hfmm_plan_s {
     // sources and targets are the same point set: the float32 near field evaluates each
     // pair of distinct neighbouring boxes once for both directions (one RHS)
     bool sym = false;
+    // right-hand sides from which the float32 near field runs as a tensor-core GEMM form
+    static constexpr int kTcMinRhs = 8;
     df* tpos_df = nullptr;      // (nt, 3) sorted targets minus the root corner, double-float
     df* spos_df = nullptr;      // (ns, 3) sorted sources
     int rmax = 1;
@@ -92,6 +94,8 @@ struct hfmm_plan_s {
     int ntunits = 0, nsunits = 0;
     int2* symunits = nullptr;                   // the same chunks, heaviest first (symmetric near field)
     int nsymunits = 0;
+    int2 *tunits64 = nullptr, *sunits64 = nullptr;  // 64-point chunks (tensor-core near field)
+    int ntunits64 = 0, nsunits64 = 0;
     double* gsort = nullptr;    // sorted position gradient (ns, 3)
     DevLevel lev[kMaxLevels];
     Requad up[kMaxLevels];    // up[l]: level l -> l-1
@@ -320,6 +324,10 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
         };
         TRY(chunks(hp.tgt_count, &P->tunits, &P->ntunits, 32));
         TRY(chunks(hp.src_count, &P->sunits, &P->nsunits, 32));
+        if (P->rmax >= hfmm_plan_s::kTcMinRhs) {
+            TRY(chunks(hp.tgt_count, &P->tunits64, &P->ntunits64, 64));
+            TRY(chunks(hp.src_count, &P->sunits64, &P->nsunits64, 64));
+        }
         if (P->sym) {
             // symmetric near field: a unit of box b sums over neighbours s >= b, so the work of
             // units varies widely; launch them heaviest first (longest-processing-time order)
@@ -923,6 +931,13 @@ hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_d
             k_p2p_mixed_sym_warp<<<nblk(P->nsymunits, 4), 128, 0, st>>>(P->symunits, P->nsymunits, P->tstart,
                                                                        P->tcount, P->noff, P->nidx, P->mixed, P->qs,
                                                                        P->phis);
+    } else if (P->near_prec == kFP32 && R >= hfmm_plan_s::kTcMinRhs) {
+        // static + dynamic shared memory exceeds 48 KiB: opt in explicitly
+        cudaFuncSetAttribute(k_p2p_mixed_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcDynSmem);
+        if (P->ntunits64 > 0)
+            k_p2p_mixed_tc<<<P->ntunits64, 128, kTcDynSmem, st>>>(P->tunits64, P->ntunits64, P->tstart, P->tcount,
+                                                                P->sstart, P->scount, P->noff, P->nidx, P->mixed,
+                                                                P->qs, P->phis, R);
     } else if (P->near_prec == kFP32) {
         if (P->ntunits > 0) {
             if (R == 1)
@@ -1010,6 +1025,16 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t P, const void* w, void* out, int nrhs
             k_p2p_mixed_sym_warp<<<nblk(P->nsymunits, 4), 128, 0, st>>>(P->symunits, P->nsymunits, P->sstart,
                                                                        P->scount, P->noff, P->nidx, P->mixed, P->phis,
                                                                        P->qs);
+    } else if (P->near_prec == kFP32 && R >= hfmm_plan_s::kTcMinRhs) {
+        P2PMixedArgs a = P->mixed;
+        std::swap(a.tpt, a.spt);
+        std::swap(a.tof, a.sof);
+        // static + dynamic shared memory exceeds 48 KiB: opt in explicitly
+        cudaFuncSetAttribute(k_p2p_mixed_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcDynSmem);
+        if (P->nsunits64 > 0)
+            k_p2p_mixed_tc<<<P->nsunits64, 128, kTcDynSmem, st>>>(P->sunits64, P->nsunits64, P->sstart, P->scount,
+                                                                P->tstart, P->tcount, P->noff, P->nidx, a, P->phis,
+                                                                P->qs, R);
     } else if (P->near_prec == kFP32) {
         P2PMixedArgs a = P->mixed;
         std::swap(a.tpt, a.spt);

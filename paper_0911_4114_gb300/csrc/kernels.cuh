@@ -685,6 +685,173 @@ __global__ void __launch_bounds__(128, 7) k_p2p_mixed_sym_warp(
 }
 
 // ---------------------------------------------------------------------------
+// Mixed near field as a tensor-core GEMM form (many right-hand sides): for a tile of 16
+// targets and 8 sources the float32 kernel values G (exact-grid form, as above) are the A
+// operand of mma.sync m16n8k8 (TF32), the charges Q of 8 right-hand sides the B operand.
+// Each real product is split 3xTF32 (hi*hi + hi*lo + lo*hi, float32 accumulation), so the
+// GEMM keeps float32 accuracy; the complex product takes four real ones (Gr Qr - Gi Qi,
+// Gr Qi + Gi Qr).  One block per (target box, 64 targets): 4 warps x 16 targets, sources
+// staged by the block 32 at a time; float32 sums of each 32-source tile are gathered in
+// double-float accumulators in shared memory (per lane, [element][lane] layout).
+// Fragment layouts (PTX ISA, mma.m16n8k8 .tf32): g = lane / 4, c = lane % 4;
+// A: a0 (g, c), a1 (g+8, c), a2 (g, c+4), a3 (g+8, c+4); B: b0 (c, g), b1 (c+4, g);
+// C: c0 (g, 2c), c1 (g, 2c+1), c2 (g+8, 2c), c3 (g+8, 2c+1).
+// ---------------------------------------------------------------------------
+constexpr int kTcRhs = 32;              // right-hand sides per pass (4 n-tiles of 8)
+constexpr int kTcSrc = 32;              // sources staged per block step
+constexpr int kTcQStride = kTcRhs + 8;  // padded row: B-fragment loads hit 32 distinct banks
+constexpr int kTcAccPerWarp = 2 * 2 * 4 * (kTcRhs / 8) * 32;   // floats of df accumulators per warp
+constexpr size_t kTcDynSmem = 4 * kTcAccPerWarp * sizeof(float);
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+    hi = tf32_rna(x);
+    lo = tf32_rna(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(128) k_p2p_mixed_tc(
+    const int2* __restrict__ units, int nunits, const int32_t* __restrict__ tstart,
+    const int32_t* __restrict__ tcount, const int32_t* __restrict__ sstart, const int32_t* __restrict__ scount,
+    const int32_t* __restrict__ noff, const int32_t* __restrict__ nidx, P2PMixedArgs a,
+    const cxd* __restrict__ qs, cxd* __restrict__ phis, int R) {
+    __shared__ float4 shp[kTcSrc], sho[kTcSrc];
+    __shared__ float shq[4][kTcSrc * kTcQStride];   // Qr hi, Qr lo, Qi hi, Qi lo (tf32 bits)
+    extern __shared__ float acc_dyn[];              // [warp][element][lane]: df (hi, lo) of C
+    const int u = blockIdx.x;
+    if (u >= nunits) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, c = lane & 3;
+    const int b = units[u].x, c0 = units[u].y + 16 * warp;
+    const int t0 = tstart[b], tc = tcount[b];
+    // this lane's two target rows g and g + 8
+    float4 gp[2], op[2];
+    bool act[2];
+    for (int h = 0; h < 2; ++h) {
+        const int ti = c0 + g + 8 * h;
+        act[h] = ti < tc;
+        gp[h] = op[h] = make_float4(0, 0, 0, 0);
+        if (act[h]) {
+            gp[h] = a.tpt[t0 + ti];
+            op[h] = a.tof[t0 + ti];
+        }
+    }
+    constexpr int kNT = kTcRhs / 8;
+    float* ac = acc_dyn + (size_t)warp * kTcAccPerWarp;
+    for (int r0 = 0; r0 < R; r0 += kTcRhs) {
+        for (int e = 0; e < 2 * 2 * 4 * kNT; ++e) ac[e * 32 + lane] = 0.f;
+        for (int nb = noff[b]; nb < noff[b + 1]; ++nb) {
+            const int s = nidx[nb];
+            const int s0 = sstart[s], sc = scount[s];
+            for (int sb = 0; sb < sc; sb += kTcSrc) {
+                const int sn = min(kTcSrc, sc - sb);
+                __syncthreads();
+                for (int v = threadIdx.x; v < kTcSrc; v += blockDim.x) {
+                    shp[v] = v < sn ? a.spt[s0 + sb + v] : make_float4(0, 0, 0, 0);
+                    sho[v] = v < sn ? a.sof[s0 + sb + v] : make_float4(0, 0, 0, 0);
+                }
+                for (int v = threadIdx.x; v < kTcSrc * kTcRhs; v += blockDim.x) {
+                    const int j = v / kTcRhs, r = v % kTcRhs;
+                    float qx = 0.f, qy = 0.f;
+                    if (j < sn && r0 + r < R) {
+                        const cxd qq = qs[(int64_t)(s0 + sb + j) * R + r0 + r];
+                        qx = (float)qq.x;
+                        qy = (float)qq.y;
+                    }
+                    uint32_t h0, l0, h1, l1;
+                    tf32_split(qx, h0, l0);
+                    tf32_split(qy, h1, l1);
+                    shq[0][j * kTcQStride + r] = __uint_as_float(h0);
+                    shq[1][j * kTcQStride + r] = __uint_as_float(l0);
+                    shq[2][j * kTcQStride + r] = __uint_as_float(h1);
+                    shq[3][j * kTcQStride + r] = __uint_as_float(l1);
+                }
+                __syncthreads();
+                float cr[kNT][4], ci[kNT][4];
+                for (int nt = 0; nt < kNT; ++nt)
+                    for (int i = 0; i < 4; ++i) cr[nt][i] = ci[nt][i] = 0.f;
+                for (int kb = 0; kb < kTcSrc; kb += 8) {
+                    if (kb >= sn) break;                       // block-uniform
+                    // A fragments: G(row g + 8 (i & 1), source kb + c + 4 (i >> 1))
+                    uint32_t grh[4], grl[4], gih[4], gil[4], ngih[4], ngil[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int h = i & 1, jj = kb + c + 4 * (i >> 1);
+                        cxf gv = green_grid(gp[h], op[h], shp[jj], sho[jj], a.tau_hi, a.tau_lo);
+                        if (!act[h] || jj >= sn) gv = mk<float>(0, 0);
+                        tf32_split(gv.x, grh[i], grl[i]);
+                        tf32_split(gv.y, gih[i], gil[i]);
+                        ngih[i] = gih[i] ^ 0x80000000u;           // -Gi (sign flip is exact)
+                        ngil[i] = gil[i] ^ 0x80000000u;
+                    }
+#pragma unroll
+                    for (int nt = 0; nt < kNT; ++nt) {
+                        const int col = nt * 8 + g;
+                        const int rA = (kb + c) * kTcQStride + col, rB = (kb + c + 4) * kTcQStride + col;
+                        const uint32_t qrh0 = __float_as_uint(shq[0][rA]), qrh1 = __float_as_uint(shq[0][rB]);
+                        const uint32_t qrl0 = __float_as_uint(shq[1][rA]), qrl1 = __float_as_uint(shq[1][rB]);
+                        const uint32_t qih0 = __float_as_uint(shq[2][rA]), qih1 = __float_as_uint(shq[2][rB]);
+                        const uint32_t qil0 = __float_as_uint(shq[3][rA]), qil1 = __float_as_uint(shq[3][rB]);
+                        // real part: Gr Qr - Gi Qi
+                        mma_tf32(cr[nt], grh, qrh0, qrh1);
+                        mma_tf32(cr[nt], grh, qrl0, qrl1);
+                        mma_tf32(cr[nt], grl, qrh0, qrh1);
+                        mma_tf32(cr[nt], ngih, qih0, qih1);
+                        mma_tf32(cr[nt], ngih, qil0, qil1);
+                        mma_tf32(cr[nt], ngil, qih0, qih1);
+                        // imaginary part: Gr Qi + Gi Qr
+                        mma_tf32(ci[nt], grh, qih0, qih1);
+                        mma_tf32(ci[nt], grh, qil0, qil1);
+                        mma_tf32(ci[nt], grl, qih0, qih1);
+                        mma_tf32(ci[nt], gih, qrh0, qrh1);
+                        mma_tf32(ci[nt], gih, qrl0, qrl1);
+                        mma_tf32(ci[nt], gil, qrh0, qrh1);
+                    }
+                }
+                // float32 tile sums into the double-float accumulators (lane-private entries)
+#pragma unroll
+                for (int nt = 0; nt < kNT; ++nt)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int e = (nt * 4 + i) * 4;
+                        dfacc x = {ac[(e + 0) * 32 + lane], ac[(e + 1) * 32 + lane]};
+                        dfacc y = {ac[(e + 2) * 32 + lane], ac[(e + 3) * 32 + lane]};
+                        dfacc_add(x, df{cr[nt][i], 0.f});
+                        dfacc_add(y, df{ci[nt][i], 0.f});
+                        ac[(e + 0) * 32 + lane] = x.hi;
+                        ac[(e + 1) * 32 + lane] = x.lo;
+                        ac[(e + 2) * 32 + lane] = y.hi;
+                        ac[(e + 3) * 32 + lane] = y.lo;
+                    }
+            }
+        }
+        // C element (nt, i): row g + 8 (i >> 1), column nt * 8 + 2c + (i & 1)
+#pragma unroll
+        for (int nt = 0; nt < kNT; ++nt)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int h = i >> 1, r = r0 + nt * 8 + 2 * c + (i & 1);
+                if (act[h] && r < R) {
+                    const int e = (nt * 4 + i) * 4;
+                    const double xr = (double)ac[(e + 0) * 32 + lane] + (double)ac[(e + 1) * 32 + lane];
+                    const double yi = (double)ac[(e + 2) * 32 + lane] + (double)ac[(e + 3) * 32 + lane];
+                    phis[(int64_t)(t0 + c0 + g + 8 * h) * R + r] = mk<double>(a.inv_unit * xr, a.inv_unit * yi);
+                }
+            }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // near field in double-float (mixed policy, 1e-11 <= eps < 1e-6): positions as df pairs
 // relative to the root corner; one warp per (target box, 32-target chunk).
 // ---------------------------------------------------------------------------

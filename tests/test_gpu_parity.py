@@ -184,3 +184,27 @@ def test_double_float_leaf_multi_rhs():
     lhs = np.vdot(w, three)                          # <w, A q>
     rhs = np.vdot(aw, q)                             # <A^H w, q>
     assert abs(lhs - rhs) <= 1e-6 * abs(lhs)
+
+
+@pytest.mark.parametrize("nrhs", [9, 40])
+def test_tensor_core_near_field(nrhs):
+    """From 8 right-hand sides the float32 near field runs as a tensor-core GEMM form
+    (mma.sync TF32, 3xTF32 split products).  With one box (no far field) the apply is the
+    near field alone: it must match the float64 direct sum to float32 accuracy, apply and
+    adjoint; R = 9 and 40 cover ragged passes of 32 RHS, ragged source tiles of 32 and a
+    coincident pair.  Each column must also match the one-RHS scalar kernel."""
+    import torch
+    g = wl.rng(17, salt=nrhs)
+    x = wl.cube(1500, g)
+    x[10] = x[3]
+    q = wl.charges(len(x), nrhs, g)
+    lib = FmmPlan(x, x, 25.0, 1e-5, precision="mixed", max_leaf=4096, max_rhs=nrhs)
+    assert lib.info()["near_precision"] == "fp32" and lib.info()["lf"] < 2
+    got = run_apply(lib, q)
+    want = direct.direct(x, x, q, 25.0)
+    assert rel(got, want) <= 1e-6
+    for r in (0, nrhs - 1):
+        assert rel(run_apply(lib, q[:, r]), got[:, r]) <= 1e-6
+    w = wl.charges(len(x), nrhs, g)
+    adj = lib.apply_adjoint(torch.as_tensor(w, device="cuda")).cpu().numpy()
+    assert rel(adj, direct.direct_adjoint(x, x, w, 25.0)) <= 1e-6
