@@ -37,6 +37,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the float64-path measurement")
     ap.add_argument("--points", type=int, default=262144, help="smaller sphere for profiling runs")
     ap.add_argument("--skip-oracle", action="store_true", help="skip the CPU oracle timing")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the adjoint and 64-RHS cube measurements")
     return ap.parse_args()
 
 
@@ -245,6 +247,40 @@ def main():
         e2e_ms.append(a.elapsed_time(b))
     e2e = allmax(float(np.mean(e2e_ms)), world)
 
+    # adjoint of the same plan, and the 64-RHS cube (tensor-core near field), device-timed
+    extras = None
+    if not args.no_extras and args.points == 262144:
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+        wadj = torch.empty((len(s), 1), dtype=torch.complex64, device=dev)
+        mp.apply_adjoint(q.reshape(-1, 1), out=wadj)
+        for a, b in ev:
+            flush.fill_(1.0)
+            a.record(stream)
+            mp.apply_adjoint(q.reshape(-1, 1), out=wadj)
+            b.record(stream)
+        torch.cuda.synchronize()
+        adj_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        cs, ct = wl.points("cube512k_rhs64")
+        cplan = FmmPlan(cs, ct, 40.0, 1e-5, precision="mixed", max_rhs=64)
+        cq = torch.as_tensor(wl.charges(len(cs), 64, wl.rng(3, salt=1)).astype(np.complex64)).to(dev)
+        cout = torch.empty((len(ct), 64), dtype=torch.complex64, device=dev)
+        cplan.apply(cq, out=cout)
+        for a, b in ev[:2]:
+            a.record(stream)
+            cplan.apply(cq, out=cout)
+            b.record(stream)
+        torch.cuda.synchronize()
+        cms = float(np.mean([a.elapsed_time(b) for a, b in ev[:2]]))
+        ci = cplan.info()
+        extras = {"adjoint": {"ms_per_step": adj_ms, "value": len(s) / (adj_ms * 1e-3) / 1e6,
+                              "unit": "Mpoints*RHS/s"},
+                  "cube512k_rhs64": {"ms_per_step": cms, "value": len(ct) * 64 / (cms * 1e-3) / 1e6,
+                                     "unit": "Mpoints*RHS/s", "nrhs": 64, "kappa": 40.0, "eps": 1e-5,
+                                     "lf": ci["lf"], "p2p_pairs": ci["p2p_pairs"],
+                                     "near_field": "tensor-core GEMM form (mma.sync 3xTF32)",
+                                     "pair_rhs_per_s": ci["p2p_pairs"] * 64 / (cms * 1e-3)}}
+        del cplan, cq, cout
+
     # CPU oracle on this host (rank 0 only), bounded sample
     cpu = None
     if rank == 0 and world == 1 and not args.skip_oracle:
@@ -343,7 +379,7 @@ def main():
             "roofline": roof, "roofline_stages": {k: {kk: v[kk] for kk in ("kernel", "bound", "achieved", "unit", "frac")}
                                                   for k, v in roof_stages.items()},
             "cpu_baseline": cpu, "gpu_launches": count_launches(info) * args.steps,
-            "clocks": clocks}
+            "clocks": clocks, "extras": extras}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
