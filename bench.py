@@ -271,14 +271,20 @@ def main():
             b.record(stream)
         torch.cuda.synchronize()
         cms = float(np.mean([a.elapsed_time(b) for a, b in ev[:2]]))
+        cplan.set_timing(True)
+        cplan.apply(cq, out=cout)
+        torch.cuda.synchronize()
         ci = cplan.info()
+        cplan.set_timing(False)
         extras = {"adjoint": {"ms_per_step": adj_ms, "value": len(s) / (adj_ms * 1e-3) / 1e6,
                               "unit": "Mpoints*RHS/s"},
                   "cube512k_rhs64": {"ms_per_step": cms, "value": len(ct) * 64 / (cms * 1e-3) / 1e6,
                                      "unit": "Mpoints*RHS/s", "nrhs": 64, "kappa": 40.0, "eps": 1e-5,
                                      "lf": ci["lf"], "p2p_pairs": ci["p2p_pairs"],
                                      "near_field": "tensor-core GEMM form (mma.sync 3xTF32)",
-                                     "pair_rhs_per_s": ci["p2p_pairs"] * 64 / (cms * 1e-3)}}
+                                     "pair_rhs_per_s": ci["p2p_pairs"] * 64 / (cms * 1e-3),
+                                     "stage_ms": ci["stage_ms"],
+                                     "levels": {str(l): v["precision"] for l, v in ci["levels"].items()}}}
         del cplan, cq, cout
 
     # CPU oracle on this host (rank 0 only), bounded sample

@@ -688,8 +688,12 @@ void launch_s2m(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false)
                                                       P->cis_tab, (cx<df>*)out, sign, wk);
         return;
     }
-    k_s2m<T><<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt, (cx<T>*)out,
-                                           sign, wk);
+    if (R == 1)
+        k_s2m<T, 1><<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt,
+                                                  (cx<T>*)out, sign, wk);
+    else
+        k_s2m<T, 4><<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt,
+                                                  (cx<T>*)out, sign, wk);
 }
 
 // signature -> points at the leaf level: L2T (targets, sign +1, weighted) or transposed
@@ -722,8 +726,12 @@ void launch_l2t(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false)
         }
         return;
     }
-    k_l2t<T><<<grid, kL2TThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, (const cx<T>*)in, R, kt, out,
-                                             sign, wk);
+    if (R == 1)
+        k_l2t<T, 1><<<grid, kL2TThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, (const cx<T>*)in, R, kt,
+                                                  out, sign, wk);
+    else
+        k_l2t<T, 4><<<grid, kL2TThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, (const cx<T>*)in, R, kt,
+                                                  out, sign, wk);
 }
 
 // transposed far field up to (not including) the transposed S2M: conj(w) on the targets

@@ -186,15 +186,16 @@ __device__ __forceinline__ double turns(double kappa_turns, const double* s, dou
 // Points to signature: M_b(s_k) = w_k sum_{j in b} exp(i k s_k . sign (p_j - c_b)) q_j.
 // S2M: sources, sign +1, no weights.  Transposed L2T: targets, sign -1, quadrature weights.
 // One thread per antipodal pair (k, k'): with E = C + iS the plane wave of s_k, it sums
-// U = sum q C and V = sum q S; then M(k) = U + iV and M(k') = U - iV.
-template <typename R>
+// U = sum q C and V = sum q S; then M(k) = U + iV and M(k') = U - iV.  kRC right-hand
+// sides per plane-wave evaluation (1, or 4 when R > 1).
+template <typename R, int kRC>
 __global__ void k_s2m(BoxView bx, QuadView qv, const int32_t* __restrict__ sstart,
                       const int32_t* __restrict__ scount, const double* __restrict__ sx,
                       const double* __restrict__ sy, const double* __restrict__ sz,
                       const cxd* __restrict__ qs, int R_, double kappa_turns, cx<R>* __restrict__ M,
                       double sign, const double* __restrict__ wk) {
     __shared__ double shd[kS2MThreads * 3];
-    __shared__ cxd shq[kS2MThreads];
+    __shared__ cxd shq[kS2MThreads * kRC];
     const int b = blockIdx.x;
     const int64_t p = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
     const bool active = p < qv.npair;
@@ -208,8 +209,10 @@ __global__ void k_s2m(BoxView bx, QuadView qv, const int32_t* __restrict__ sstar
     }
     const int s0 = sstart[b], sc = scount[b];
     const double cxx = bx.center[3 * b], cyy = bx.center[3 * b + 1], czz = bx.center[3 * b + 2];
-    for (int r = 0; r < R_; ++r) {
-        cx<R> U = mk<R>(0, 0), V = mk<R>(0, 0);
+    for (int r0 = 0; r0 < R_; r0 += kRC) {
+        const int rn = kRC == 1 ? 1 : min(kRC, R_ - r0);
+        cx<R> U[kRC], V[kRC];
+        for (int r = 0; r < kRC; ++r) U[r] = V[r] = mk<R>(0, 0);
         for (int jb = 0; jb < sc; jb += kS2MThreads) {
             const int jn = min(kS2MThreads, sc - jb);
             __syncthreads();
@@ -218,27 +221,30 @@ __global__ void k_s2m(BoxView bx, QuadView qv, const int32_t* __restrict__ sstar
                 shd[3 * threadIdx.x] = sign * (sx[j] - cxx);
                 shd[3 * threadIdx.x + 1] = sign * (sy[j] - cyy);
                 shd[3 * threadIdx.x + 2] = sign * (sz[j] - czz);
-                shq[threadIdx.x] = qs[(int64_t)j * R_ + r];
+                for (int r = 0; r < rn; ++r) shq[threadIdx.x * kRC + r] = qs[(int64_t)j * R_ + r0 + r];
             }
             __syncthreads();
             if (active)
                 for (int jj = 0; jj < jn; ++jj) {
                     const double t = turns(kappa_turns, s, shd[3 * jj], shd[3 * jj + 1], shd[3 * jj + 2]);
                     const cx<R> e = plane_wave<R>(t);
-                    const cx<R> q = cvt<R>(shq[jj]);
-                    U = U + e.x * q;
-                    V = V + e.y * q;
+                    for (int r = 0; r < rn; ++r) {
+                        const cx<R> q = cvt<R>(shq[jj * kRC + r]);
+                        U[r] = U[r] + e.x * q;
+                        V[r] = V[r] + e.y * q;
+                    }
                 }
         }
-        if (active) {
-            cx<R> a = mk<R>(U.x - V.y, U.y + V.x), c = mk<R>(U.x + V.y, U.y - V.x);
-            if (wk) {
-                a = (R)wk[kk2.x] * a;
-                c = (R)wk[kk2.y] * c;
+        if (active)
+            for (int r = 0; r < rn; ++r) {
+                cx<R> a = mk<R>(U[r].x - V[r].y, U[r].y + V[r].x), c = mk<R>(U[r].x + V[r].y, U[r].y - V[r].x);
+                if (wk) {
+                    a = (R)wk[kk2.x] * a;
+                    c = (R)wk[kk2.y] * c;
+                }
+                M[((int64_t)b * R_ + r0 + r) * qv.K + kk2.x] = a;
+                M[((int64_t)b * R_ + r0 + r) * qv.K + kk2.y] = c;
             }
-            M[((int64_t)b * R_ + r) * qv.K + kk2.x] = a;
-            M[((int64_t)b * R_ + r) * qv.K + kk2.y] = c;
-        }
     }
 }
 
@@ -251,14 +257,15 @@ constexpr int kL2TThreads = 128;
 // L2T: targets, sign +1, quadrature weights.  Transposed S2M: sources, sign -1, no weights.
 // Over antipodal pairs (k, k') with A = w_k L(k), B = w_k' L(k'), E = C + iS the plane wave
 // of s_k: A E + B conj(E) = (P.x C - Q.y S) + i (P.y C + Q.x S), P = A + B, Q = A - B.
-template <typename R>
+// kRC right-hand sides per plane-wave evaluation.
+template <typename R, int kRC>
 __global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstart,
                       const int32_t* __restrict__ tcount, const double* __restrict__ tx,
                       const double* __restrict__ ty, const double* __restrict__ tz,
                       const cx<R>* __restrict__ L, int R_, double kappa_turns, cxd* __restrict__ phis,
                       double sign, const double* __restrict__ wk) {
     __shared__ double shs[kL2TThreads * 3];
-    __shared__ cx<R> shp[kL2TThreads], shq[kL2TThreads];
+    __shared__ cx<R> shp[kL2TThreads * kRC], shq[kL2TThreads * kRC];
     const int b = blockIdx.x;
     const int t0 = tstart[b], tc = tcount[b];
     if ((int)blockIdx.y * kL2TThreads >= tc) return;
@@ -271,9 +278,10 @@ __global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstar
         dy = sign * (cyy - ty[t0 + ti]);
         dz = sign * (czz - tz[t0 + ti]);
     }
-    for (int r = 0; r < R_; ++r) {
-        const cx<R>* Lb = L + ((int64_t)b * R_ + r) * qv.K;
-        cx<R> acc = mk<R>(0, 0);
+    for (int r0 = 0; r0 < R_; r0 += kRC) {
+        const int rn = kRC == 1 ? 1 : min(kRC, R_ - r0);
+        cx<R> acc[kRC];
+        for (int r = 0; r < kRC; ++r) acc[r] = mk<R>(0, 0);
         for (int64_t pb = 0; pb < qv.npair; pb += kL2TThreads) {
             const int pn = (int)min((int64_t)kL2TThreads, qv.npair - pb);
             __syncthreads();
@@ -282,26 +290,32 @@ __global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstar
                 shs[3 * threadIdx.x] = qv.shat[3 * kk2.x];
                 shs[3 * threadIdx.x + 1] = qv.shat[3 * kk2.x + 1];
                 shs[3 * threadIdx.x + 2] = qv.shat[3 * kk2.x + 2];
-                const cx<R> A = wk ? (R)wk[kk2.x] * Lb[kk2.x] : Lb[kk2.x];
-                const cx<R> B = wk ? (R)wk[kk2.y] * Lb[kk2.y] : Lb[kk2.y];
-                shp[threadIdx.x] = A + B;
-                shq[threadIdx.x] = A - B;
+                for (int r = 0; r < rn; ++r) {
+                    const cx<R>* Lb = L + ((int64_t)b * R_ + r0 + r) * qv.K;
+                    const cx<R> A = wk ? (R)wk[kk2.x] * Lb[kk2.x] : Lb[kk2.x];
+                    const cx<R> B = wk ? (R)wk[kk2.y] * Lb[kk2.y] : Lb[kk2.y];
+                    shp[threadIdx.x * kRC + r] = A + B;
+                    shq[threadIdx.x * kRC + r] = A - B;
+                }
             }
             __syncthreads();
             if (active)
                 for (int kk = 0; kk < pn; ++kk) {
                     const double t = turns(kappa_turns, &shs[3 * kk], dx, dy, dz);
                     const cx<R> e = plane_wave<R>(t);
-                    const cx<R> P = shp[kk], Q = shq[kk];
-                    acc.x += P.x * e.x - Q.y * e.y;
-                    acc.y += P.y * e.x + Q.x * e.y;
+                    for (int r = 0; r < rn; ++r) {
+                        const cx<R> P = shp[kk * kRC + r], Q = shq[kk * kRC + r];
+                        acc[r].x += P.x * e.x - Q.y * e.y;
+                        acc[r].y += P.y * e.x + Q.x * e.y;
+                    }
                 }
         }
-        if (active) {
-            cxd& o = phis[(int64_t)(t0 + ti) * R_ + r];
-            o.x += (double)acc.x;
-            o.y += (double)acc.y;
-        }
+        if (active)
+            for (int r = 0; r < rn; ++r) {
+                cxd& o = phis[(int64_t)(t0 + ti) * R_ + r0 + r];
+                o.x += (double)acc[r].x;
+                o.y += (double)acc[r].y;
+            }
     }
 }
 
