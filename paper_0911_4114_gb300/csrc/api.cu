@@ -533,25 +533,26 @@ void launch_up(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
         ra, p.nbox, R, p.bv.child_start, p.bv.child_count, c.octant, shift_of<Tc>(p), GB, (cx<Tout>*)p.M);
 }
 
+// transposed L2L, child l+1 -> parent l: transpose of the forward L2L (down[l] passes)
 template <typename Tin, typename Tc, typename Tout>
 void launch_l2l_t(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
-    RequadArgs ra = P->up[l + 1].args;
+    RequadArgs ra = P->down[l].args;
     ra.tw.pool = pool_of<Tc>(P);
     DevLevel& c = P->lev[l + 1];
     DevLevel& p = P->lev[l];
     const size_t sm = (size_t)kWarps * 2 * ra.maxlen * sizeof(cx<Tc>);
+    const size_t sm3 = (size_t)kWarps * 3 * ra.maxlen * sizeof(cx<Tc>);
     cx<Tc>* GA = (cx<Tc>*)P->ga;
     cx<Tc>* GB = (cx<Tc>*)P->gb;
-    smem_opt_in(k_requad_rows_a<Tin, Tc, kNoShift, true>, sm);
-    smem_opt_in(k_requad_cols<Tc, true>, sm);
-    const size_t sm3 = (size_t)kWarps * 3 * ra.maxlen * sizeof(cx<Tc>);   // + per-warp child sum
-    smem_opt_in(k_requad_rows_c_m2m<Tc, Tout, kShiftConj, true>, sm3);
-    k_requad_rows_a<Tin, Tc, kNoShift, true><<<nblk((int64_t)c.nbox * R * ra.qa.nrows, kWarps), 32 * kWarps, sm, st>>>(
-        ra, c.nbox, R, (const cx<Tin>*)c.IL, nullptr, nullptr, nullptr, GA);
-    k_requad_cols<Tc, true><<<nblk((int64_t)c.nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(
-        ra, c.nbox, R, GA, GB);
-    k_requad_rows_c_m2m<Tc, Tout, kShiftConj, true><<<nblk((int64_t)p.nbox * R * ra.qb.nrows, kWarps), 32 * kWarps, sm3, st>>>(
-        ra, p.nbox, R, p.bv.child_start, p.bv.child_count, c.octant, shift_of<Tc>(p), GB, (cx<Tout>*)p.IL);
+    smem_opt_in(k_requad_spec_ct<Tin, Tc, kNoShift>, sm);
+    smem_opt_in(k_requad_spec_cols_t<Tc>, sm);
+    smem_opt_in(k_requad_spec_at_sum<Tc, Tout>, sm3);
+    k_requad_spec_ct<Tin, Tc, kNoShift><<<nblk((int64_t)c.nbox * R * ra.qb.nrows, kWarps), 32 * kWarps, sm, st>>>(
+        ra, c.nbox, R, (const cx<Tin>*)c.IL, nullptr, nullptr, nullptr, GB);
+    k_requad_spec_cols_t<Tc><<<nblk((int64_t)c.nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(
+        ra, c.nbox, R, GB, GA);
+    k_requad_spec_at_sum<Tc, Tout><<<nblk((int64_t)p.nbox * R * ra.qa.nrows, kWarps), 32 * kWarps, sm3, st>>>(
+        ra, p.nbox, R, p.bv.child_start, p.bv.child_count, c.octant, shift_of<Tc>(p), GA, (cx<Tout>*)p.IL);
 }
 
 template <typename Tin, typename Tc, typename Tout>
@@ -574,24 +575,25 @@ void launch_down(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
         ra, c.nbox, R, GB, (cx<Tout>*)c.IL);
 }
 
+// transposed M2M, parent l-1 -> child l: transpose of the forward M2M (up[l] passes)
 template <typename Tin, typename Tc, typename Tout>
 void launch_m2m_t(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
-    RequadArgs ra = P->down[l - 1].args;
+    RequadArgs ra = P->up[l].args;
     ra.tw.pool = pool_of<Tc>(P);
     DevLevel& p = P->lev[l - 1];
     DevLevel& c = P->lev[l];
     const size_t sm = (size_t)kWarps * 2 * ra.maxlen * sizeof(cx<Tc>);
     cx<Tc>* GA = (cx<Tc>*)P->ga;
     cx<Tc>* GB = (cx<Tc>*)P->gb;
-    smem_opt_in(k_requad_rows_a<Tin, Tc, kShiftPlain, true>, sm);
-    smem_opt_in(k_requad_cols<Tc, true>, sm);
-    smem_opt_in(k_requad_rows_c_l2l<Tc, Tout, true>, sm);
-    k_requad_rows_a<Tin, Tc, kShiftPlain, true><<<nblk((int64_t)c.nbox * R * ra.qa.nrows, kWarps), 32 * kWarps, sm, st>>>(
-        ra, c.nbox, R, (const cx<Tin>*)p.M, c.bv.parent, c.octant, shift_of<Tc>(p), GA);
-    k_requad_cols<Tc, true><<<nblk((int64_t)c.nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(
-        ra, c.nbox, R, GA, GB);
-    k_requad_rows_c_l2l<Tc, Tout, true><<<nblk((int64_t)c.nbox * R * ra.qb.nrows, kWarps), 32 * kWarps, sm, st>>>(
-        ra, c.nbox, R, GB, (cx<Tout>*)c.M);
+    smem_opt_in(k_requad_spec_ct<Tin, Tc, kShiftPlain>, sm);
+    smem_opt_in(k_requad_spec_cols_t<Tc>, sm);
+    smem_opt_in(k_requad_spec_at_add<Tc, Tout>, sm);
+    k_requad_spec_ct<Tin, Tc, kShiftPlain><<<nblk((int64_t)c.nbox * R * ra.qb.nrows, kWarps), 32 * kWarps, sm, st>>>(
+        ra, c.nbox, R, (const cx<Tin>*)p.M, c.bv.parent, c.octant, shift_of<Tc>(p), GB);
+    k_requad_spec_cols_t<Tc><<<nblk((int64_t)c.nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(
+        ra, c.nbox, R, GB, GA);
+    k_requad_spec_at_add<Tc, Tout><<<nblk((int64_t)c.nbox * R * ra.qa.nrows, kWarps), 32 * kWarps, sm, st>>>(
+        ra, c.nbox, R, GA, (cx<Tout>*)c.M);
 }
 
 template <typename S, typename C>

@@ -1151,11 +1151,12 @@ __global__ void k_m2l(int nbox, int64_t K, const int32_t* __restrict__ ioff, con
 }
 
 // ---------------------------------------------------------------------------
-// Re-quadrature (Section 3.4) in three passes through global scratch:
-//   A: rows n of quadrature a, N_phi^a(n) -> big          (step 1; optional shift pre-multiply)
-//   B: theta columns m < big/2, ntheta^a -> ntheta^b      (steps 2-4)
-//   C: rows n' of quadrature b, big -> N_phi^b(n')        (step 5; M2M: shift + child sum,
-//                                                          L2L: add the incoming I)
+// Re-quadrature (Section 3.4) in three passes through global scratch (kernels below):
+//   A': rows n of quadrature a, N_phi^a(n) -> band-limited phi coefficients (step 1;
+//       optional shift pre-multiply)
+//   B': theta circles of coefficient pairs, ntheta^a -> ntheta^b        (steps 2-4)
+//   C': rows n' of quadrature b from their coefficients                 (step 5; M2M: shift +
+//       child sum, L2L: add the incoming I)
 // GA layout: [(seq_box * R + r) * rows_a + n] * big ; GB: [(seq_box * R + r) * rows_b + n] * big
 // ---------------------------------------------------------------------------
 struct RequadArgs {
@@ -1167,161 +1168,6 @@ struct RequadArgs {
 
 // Shift modes of the passes that touch the parent grid.
 enum ShiftMode { kNoShift = 0, kShiftConj = 1, kShiftPlain = 2 };
-
-// Transposition (kT): the transposed re-quadrature runs the same passes from the output
-// grid back to the input grid; a transposed 1-D re-sampling from K to K' points is
-// (K/K') times the plain one, the duplicated pole halves of step 4 are summed, and the
-// dropped pole halves of step 2 are set to zero.
-
-// Pass A.  Sequence = (box, r, n) over nbox_seq boxes.  Input signature of box `src_box(b)`:
-//   M2M / transposed L2L: box b itself on grid a, no shift
-//   L2L: the parent of child b on grid a, times conj(shift[octant(b)])
-//   transposed M2M: the parent of child b on grid a, times shift[octant(b)]
-template <typename Tin, typename Tc, int kShift, bool kT>
-__global__ void k_requad_rows_a(RequadArgs ra, int nbox_seq, int R_, const cx<Tin>* __restrict__ in,
-                                const int32_t* __restrict__ src_box, const int32_t* __restrict__ octant,
-                                const cx<Tc>* __restrict__ shift, cx<Tc>* __restrict__ GA) {
-    extern __shared__ unsigned char smem_raw[];
-    cx<Tc>* sm = reinterpret_cast<cx<Tc>*>(smem_raw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    cx<Tc>* buf0 = sm + (size_t)warp * 2 * ra.maxlen;
-    cx<Tc>* buf1 = buf0 + ra.maxlen;
-    const int64_t seq = (int64_t)blockIdx.x * kWarps + warp;
-    const int rows = ra.qa.nrows;
-    const int64_t nseq = (int64_t)nbox_seq * R_ * rows;
-    if (seq >= nseq) return;
-    const int n = (int)(seq % rows);
-    const int64_t br = seq / rows;          // box * R + r
-    const int b = (int)(br / R_), r = (int)(br % R_);
-    const int len = ra.qa.nphi[n];
-    const int64_t o = ra.qa.off[n];
-    const int sb = kShift ? src_box[b] : b;
-    const cx<Tin>* src = in + ((int64_t)sb * R_ + r) * ra.qa.K + o;
-    const cx<Tc>* sh = kShift ? shift + (int64_t)octant[b] * ra.qa.K + o : nullptr;
-    for (int j = lane; j < len; j += 32) {
-        cx<Tc> v = cvt<Tc>(src[j]);
-        if (kShift == kShiftConj) v = v * conj(sh[j]);
-        if (kShift == kShiftPlain) v = v * sh[j];
-        buf0[j] = v;
-    }
-    __syncwarp();
-    cx<Tc>* res = warp_resample(buf0, buf1, len, ra.big, ra.tw, lane);
-    const Tc sc = rval<Tc>(kT ? (double)len / (double)ra.big : 1.0);   // transposed: (length in) / (length out)
-    cx<Tc>* dst = GA + seq * ra.big;
-    for (int j = lane; j < ra.big; j += 32) dst[j] = kT ? sc * res[j] : res[j];
-}
-
-// Pass B.  Sequence = (box, r, m), m < big/2.
-template <typename Tc, bool kT>
-__global__ void k_requad_cols(RequadArgs ra, int nbox_seq, int R_, const cx<Tc>* __restrict__ GA,
-                              cx<Tc>* __restrict__ GB) {
-    extern __shared__ unsigned char smem_raw[];
-    cx<Tc>* sm = reinterpret_cast<cx<Tc>*>(smem_raw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    cx<Tc>* buf0 = sm + (size_t)warp * 2 * ra.maxlen;
-    cx<Tc>* buf1 = buf0 + ra.maxlen;
-    const int hb = ra.big / 2;
-    const int64_t seq = (int64_t)blockIdx.x * kWarps + warp;
-    const int64_t nseq = (int64_t)nbox_seq * R_ * hb;
-    if (seq >= nseq) return;
-    const int m = (int)(seq % hb);
-    const int64_t br = seq / hb;
-    const int nta = ra.qa.ntheta, ntb = ra.qb.ntheta;
-    const int ha = nta / 2, hbr = ntb / 2;
-    const cx<Tc>* ga = GA + br * (int64_t)ra.qa.nrows * ra.big;
-    for (int t = lane; t < nta; t += 32) {
-        if (!kT) {
-            buf0[t] = (t <= ha) ? ga[(int64_t)t * ra.big + m] : ga[(int64_t)(nta - t) * ra.big + m + hb];
-        } else {
-            cx<Tc> v = mk<Tc>(rval<Tc>(0.0), rval<Tc>(0.0));
-            if (t <= ha) v = ga[(int64_t)t * ra.big + m];
-            if (t == 0 || t >= ha) v = v + ga[(int64_t)((nta - t) % nta) * ra.big + m + hb];
-            buf0[t] = v;
-        }
-    }
-    __syncwarp();
-    cx<Tc>* res = warp_resample(buf0, buf1, nta, ntb, ra.tw, lane);
-    const Tc sc = rval<Tc>((double)nta / (double)ntb);
-    cx<Tc>* gb = GB + br * (int64_t)ra.qb.nrows * ra.big;
-    for (int n = lane; n <= hbr; n += 32) {
-        if (!kT) {
-            gb[(int64_t)n * ra.big + m] = res[n];
-            gb[(int64_t)n * ra.big + m + hb] = res[(ntb - n) % ntb];
-        } else {
-            gb[(int64_t)n * ra.big + m] = sc * res[n];
-            gb[(int64_t)n * ra.big + m + hb] = (n > 0 && n < hbr) ? sc * res[ntb - n] : mk<Tc>(rval<Tc>(0.0), rval<Tc>(0.0));
-        }
-    }
-}
-
-// Pass C, adding into the output in place.  Sequence = (box, r, n').
-//   L2L: L_child = anterp(...) + I_child;  transposed M2M: Lambda_M(child) += ...
-template <typename Tc, typename Tout, bool kT>
-__global__ void k_requad_rows_c_l2l(RequadArgs ra, int nbox_seq, int R_, const cx<Tc>* __restrict__ GB,
-                                    cx<Tout>* __restrict__ IL) {
-    extern __shared__ unsigned char smem_raw[];
-    cx<Tc>* sm = reinterpret_cast<cx<Tc>*>(smem_raw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    cx<Tc>* buf0 = sm + (size_t)warp * 2 * ra.maxlen;
-    cx<Tc>* buf1 = buf0 + ra.maxlen;
-    const int rows = ra.qb.nrows;
-    const int64_t seq = (int64_t)blockIdx.x * kWarps + warp;
-    const int64_t nseq = (int64_t)nbox_seq * R_ * rows;
-    if (seq >= nseq) return;
-    const int n = (int)(seq % rows);
-    const int64_t br = seq / rows;
-    const cx<Tc>* row = GB + seq * ra.big;
-    for (int j = lane; j < ra.big; j += 32) buf0[j] = row[j];
-    __syncwarp();
-    const int len = ra.qb.nphi[n];
-    cx<Tc>* res = warp_resample(buf0, buf1, ra.big, len, ra.tw, lane);
-    const Tc sc = rval<Tc>(kT ? (double)ra.big / (double)len : 1.0);
-    cx<Tout>* dst = IL + br * ra.qb.K + ra.qb.off[n];
-    // the sum is formed in the output level's type (Tc may be the coarser parent type)
-    for (int j = lane; j < len; j += 32) dst[j] = dst[j] + cvt<Tout>(kT ? sc * res[j] : res[j]);
-}
-
-// Pass C summing children, overwriting the parent.  Sequence = (parent, r, n').
-//   M2M: M_parent = sum_children shift * requad(child)
-//   transposed L2L: Lambda_L(parent) = sum_children conj(shift) * requad^T(child)
-template <typename Tc, typename Tout, int kShift, bool kT>
-__global__ void k_requad_rows_c_m2m(RequadArgs ra, int nparent, int R_, const int32_t* __restrict__ child_start,
-                                    const int32_t* __restrict__ child_count, const int32_t* __restrict__ octant,
-                                    const cx<Tc>* __restrict__ shift, const cx<Tc>* __restrict__ GB,
-                                    cx<Tout>* __restrict__ Mp) {
-    extern __shared__ unsigned char smem_raw[];
-    cx<Tc>* sm = reinterpret_cast<cx<Tc>*>(smem_raw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    cx<Tc>* buf0 = sm + (size_t)warp * 3 * ra.maxlen;
-    cx<Tc>* buf1 = buf0 + ra.maxlen;
-    cx<Tc>* acc = buf1 + ra.maxlen;   // sum over children; entry j belongs to lane j % 32
-    const int rows = ra.qb.nrows;
-    const int64_t seq = (int64_t)blockIdx.x * kWarps + warp;
-    const int64_t nseq = (int64_t)nparent * R_ * rows;
-    if (seq >= nseq) return;
-    const int n = (int)(seq % rows);
-    const int64_t pr = seq / rows;
-    const int p = (int)(pr / R_), r = (int)(pr % R_);
-    const int len = ra.qb.nphi[n];
-    const int64_t o = ra.qb.off[n];
-    for (int j = lane; j < len; j += 32) acc[j] = mk<Tc>(rval<Tc>(0.0), rval<Tc>(0.0));
-    const int c0 = child_start[p], cn = child_count[p];
-    for (int c = c0; c < c0 + cn; ++c) {
-        const cx<Tc>* row = GB + (((int64_t)c * R_ + r) * rows + n) * ra.big;
-        for (int j = lane; j < ra.big; j += 32) buf0[j] = row[j];
-        __syncwarp();
-        cx<Tc>* res = warp_resample(buf0, buf1, ra.big, len, ra.tw, lane);
-        const cx<Tc>* sh = shift + (int64_t)octant[c] * ra.qb.K + o;
-        const Tc sc = rval<Tc>(kT ? (double)ra.big / (double)len : 1.0);
-        for (int j = lane; j < len; j += 32) {
-            cx<Tc> v = kT ? sc * res[j] : res[j];
-            acc[j] = acc[j] + v * (kShift == kShiftConj ? conj(sh[j]) : sh[j]);
-        }
-        __syncwarp();
-    }
-    cx<Tout>* dst = Mp + ((int64_t)p * R_ + r) * ra.qb.K + o;
-    for (int j = lane; j < len; j += 32) dst[j] = cvt<Tout>(acc[j]);
-}
 
 // ---------------------------------------------------------------------------
 // Forward re-quadrature on phi-Fourier coefficients.  The phi re-sampling of a row and the
@@ -1477,6 +1323,167 @@ __global__ void k_requad_spec_c_m2m(RequadArgs ra, int nparent, int R_, const in
         __syncwarp();
     }
     cx<Tout>* dst = Mp + ((int64_t)p * R_ + r) * ra.qb.K + o;
+    for (int j = lane; j < len; j += 32) dst[j] = cvt<Tout>(acc[j]);
+}
+
+// ---------------------------------------------------------------------------
+// Transposed coefficient-space re-quadrature (adjoint and gradient): the exact transposes of
+// the passes above, in reverse order.  C'^T: a grid-b row through the unnormalised inverse
+// FFT of its length into band slots; B'^T: the transposed even/odd split, the transposed
+// theta re-sampling ((ntheta_b / ntheta_a) times the re-sampling back) and the transposed
+// gather (a row collects the circle values at t and -t); A'^T: band slots into a row of its
+// own length, forward FFT, 1/N_phi.
+// ---------------------------------------------------------------------------
+template <typename Tin, typename Tc, int kShift>
+__global__ void k_requad_spec_ct(RequadArgs ra, int nbox_seq, int R_, const cx<Tin>* __restrict__ in,
+                                 const int32_t* __restrict__ src_box, const int32_t* __restrict__ octant,
+                                 const cx<Tc>* __restrict__ shift, cx<Tc>* __restrict__ GB) {
+    extern __shared__ unsigned char smem_raw[];
+    cx<Tc>* sm = reinterpret_cast<cx<Tc>*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cx<Tc>* buf0 = sm + (size_t)warp * 2 * ra.maxlen;
+    cx<Tc>* buf1 = buf0 + ra.maxlen;
+    const int64_t seq = (int64_t)blockIdx.x * kWarps + warp;
+    const int rows = ra.qb.nrows;
+    if (seq >= (int64_t)nbox_seq * R_ * rows) return;
+    const int n = (int)(seq % rows);
+    const int64_t br = seq / rows;
+    const int b = (int)(br / R_), r = (int)(br % R_);
+    const int len = ra.qb.nphi[n];
+    const int64_t o = ra.qb.off[n];
+    const int sb = kShift ? src_box[b] : b;
+    const cx<Tin>* src = in + ((int64_t)sb * R_ + r) * ra.qb.K + o;
+    const cx<Tc>* sh = kShift ? shift + (int64_t)octant[b] * ra.qb.K + o : nullptr;
+    for (int j = lane; j < len; j += 32) {
+        cx<Tc> v = cvt<Tc>(src[j]);
+        if (kShift == kShiftPlain) v = v * sh[j];
+        buf0[j] = v;
+    }
+    __syncwarp();
+    const cx<Tc>* pool = reinterpret_cast<const cx<Tc>*>(ra.tw.pool);
+    const cx<Tc>* res = warp_fft(buf0, buf1, len, true, pool + ra.tw.off[len], lane);
+    const int band = min((ra.big + 1) / 2, (len + 1) / 2) - 1;
+    cx<Tc>* dst = GB + seq * ra.big;
+    for (int j = lane; j < ra.big; j += 32) {
+        const int f = (2 * j <= ra.big) ? j : j - ra.big;
+        cx<Tc> v = mk<Tc>(rval<Tc>(0.0), rval<Tc>(0.0));
+        if (f <= band && f >= -band) v = res[(f + len) % len];
+        dst[j] = v;
+    }
+}
+
+template <typename Tc>
+__global__ void k_requad_spec_cols_t(RequadArgs ra, int nbox_seq, int R_, const cx<Tc>* __restrict__ GB,
+                                     cx<Tc>* __restrict__ GA) {
+    extern __shared__ unsigned char smem_raw[];
+    cx<Tc>* sm = reinterpret_cast<cx<Tc>*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cx<Tc>* buf0 = sm + (size_t)warp * 2 * ra.maxlen;
+    cx<Tc>* buf1 = buf0 + ra.maxlen;
+    const int hb = ra.big / 2;
+    const int64_t seq = (int64_t)blockIdx.x * kWarps + warp;
+    if (seq >= (int64_t)nbox_seq * R_ * hb) return;
+    const int c = (int)(seq % hb);
+    const int64_t br = seq / hb;
+    const int s_even = (c % 2 == 0) ? c : ra.big - 1 - c;
+    const int s_odd = (c % 2 == 0) ? ra.big - 1 - c : c;
+    const int nta = ra.qa.ntheta, ntb = ra.qb.ntheta;
+    const int ha = nta / 2, hbr = ntb / 2;
+    const Tc half = rval<Tc>(0.5);
+    const cx<Tc>* gb = GB + br * (int64_t)ra.qb.nrows * ra.big;
+    // transposed even/odd split: rows n <= ntheta_b / 2 of the two slots -> one circle
+    for (int m = lane; m < ntb; m += 32) {
+        cx<Tc> y;
+        if (m == 0 || m == hbr) {
+            y = gb[(int64_t)m * ra.big + s_even];
+        } else {
+            const int n = m < hbr ? m : ntb - m;
+            const cx<Tc> e = gb[(int64_t)n * ra.big + s_even], d = gb[(int64_t)n * ra.big + s_odd];
+            y = half * (m < hbr ? e + d : e - d);
+        }
+        buf0[m] = y;
+    }
+    __syncwarp();
+    cx<Tc>* res = warp_resample(buf0, buf1, ntb, nta, ra.tw, lane);
+    const Tc sc = rval<Tc>((double)ntb / (double)nta);
+    cx<Tc>* ga = GA + br * (int64_t)ra.qa.nrows * ra.big;
+    // transposed gather: row u collects t = u and t = ntheta_a - u (odd slot with a sign flip)
+    for (int u = lane; u <= ha; u += 32) {
+        const cx<Tc> h0 = res[u];
+        const cx<Tc> hm = (u != 0 && u != ha) ? res[nta - u] : mk<Tc>(rval<Tc>(0.0), rval<Tc>(0.0));
+        ga[(int64_t)u * ra.big + s_even] = sc * (h0 + hm);
+        ga[(int64_t)u * ra.big + s_odd] = sc * (h0 - hm);
+    }
+}
+
+// band slots of a GA row into a grid-a row of length len, forward FFT, 1/len
+template <typename Tc>
+__device__ __forceinline__ const cx<Tc>* spec_at_row(const cx<Tc>* row, int big, int len, cx<Tc>* buf0,
+                                                     cx<Tc>* buf1, const RequadArgs& ra, int lane) {
+    const int band = min((len + 1) / 2, (big + 1) / 2) - 1;
+    for (int j = lane; j < len; j += 32) {
+        const int f = (2 * j <= len) ? j : j - len;
+        cx<Tc> v = mk<Tc>(rval<Tc>(0.0), rval<Tc>(0.0));
+        if (f <= band && f >= -band) v = row[(f + big) % big];
+        buf0[j] = v;
+    }
+    __syncwarp();
+    const cx<Tc>* pool = reinterpret_cast<const cx<Tc>*>(ra.tw.pool);
+    return warp_fft(buf0, buf1, len, false, pool + ra.tw.off[len], lane);
+}
+
+// A'^T of the transposed M2M: add into the child's rows
+template <typename Tc, typename Tout>
+__global__ void k_requad_spec_at_add(RequadArgs ra, int nbox_seq, int R_, const cx<Tc>* __restrict__ GA,
+                                     cx<Tout>* __restrict__ out) {
+    extern __shared__ unsigned char smem_raw[];
+    cx<Tc>* sm = reinterpret_cast<cx<Tc>*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cx<Tc>* buf0 = sm + (size_t)warp * 2 * ra.maxlen;
+    cx<Tc>* buf1 = buf0 + ra.maxlen;
+    const int rows = ra.qa.nrows;
+    const int64_t seq = (int64_t)blockIdx.x * kWarps + warp;
+    if (seq >= (int64_t)nbox_seq * R_ * rows) return;
+    const int t = (int)(seq % rows);
+    const int64_t br = seq / rows;
+    const int len = ra.qa.nphi[t];
+    const cx<Tc>* res = spec_at_row(GA + seq * ra.big, ra.big, len, buf0, buf1, ra, lane);
+    const Tc sc = rval<Tc>(1.0 / (double)len);
+    cx<Tout>* dst = out + br * ra.qa.K + ra.qa.off[t];
+    for (int j = lane; j < len; j += 32) dst[j] = dst[j] + cvt<Tout>(sc * res[j]);
+}
+
+// A'^T of the transposed L2L: parent row = sum over children of conj(shift) * (A'^T of the child)
+template <typename Tc, typename Tout>
+__global__ void k_requad_spec_at_sum(RequadArgs ra, int nparent, int R_, const int32_t* __restrict__ child_start,
+                                     const int32_t* __restrict__ child_count, const int32_t* __restrict__ octant,
+                                     const cx<Tc>* __restrict__ shift, const cx<Tc>* __restrict__ GA,
+                                     cx<Tout>* __restrict__ Mp) {
+    extern __shared__ unsigned char smem_raw[];
+    cx<Tc>* sm = reinterpret_cast<cx<Tc>*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cx<Tc>* buf0 = sm + (size_t)warp * 3 * ra.maxlen;
+    cx<Tc>* buf1 = buf0 + ra.maxlen;
+    cx<Tc>* acc = buf1 + ra.maxlen;
+    const int rows = ra.qa.nrows;
+    const int64_t seq = (int64_t)blockIdx.x * kWarps + warp;
+    if (seq >= (int64_t)nparent * R_ * rows) return;
+    const int t = (int)(seq % rows);
+    const int64_t pr = seq / rows;
+    const int p = (int)(pr / R_), r = (int)(pr % R_);
+    const int len = ra.qa.nphi[t];
+    const int64_t o = ra.qa.off[t];
+    const Tc sc = rval<Tc>(1.0 / (double)len);
+    for (int j = lane; j < len; j += 32) acc[j] = mk<Tc>(rval<Tc>(0.0), rval<Tc>(0.0));
+    const int c0 = child_start[p], cn = child_count[p];
+    for (int c = c0; c < c0 + cn; ++c) {
+        const cx<Tc>* res = spec_at_row(GA + (((int64_t)c * R_ + r) * rows + t) * ra.big, ra.big, len, buf0, buf1,
+                                        ra, lane);
+        const cx<Tc>* sh = shift + (int64_t)octant[c] * ra.qa.K + o;
+        for (int j = lane; j < len; j += 32) acc[j] = acc[j] + (sc * res[j]) * conj(sh[j]);
+        __syncwarp();
+    }
+    cx<Tout>* dst = Mp + ((int64_t)p * R_ + r) * ra.qa.K + o;
     for (int j = lane; j < len; j += 32) dst[j] = cvt<Tout>(acc[j]);
 }
 
