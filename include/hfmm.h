@@ -54,7 +54,9 @@ typedef enum { HFMM_C64 = 0, HFMM_C128 = 1 } hfmm_dtype;
 /* Precision policy.  FP64: every stage in float64.  MIXED: per level the first of float32,
  * double-float (float32 pairs, ~48 bits) and float64 that the planner's round-off estimate
  * allows, never coarser than the level above; near field in float32 with exact grid
- * geometry and float64 tile accumulation when eps >= 1e-6, in double-float for
+ * geometry and double-float tile accumulation when eps >= 1e-6 (from 8 right-hand sides
+ * as a tensor-core GEMM form with 3xTF32 split products; with sources = targets and one
+ * right-hand side each pair of distinct boxes evaluated once), in double-float for
  * 1e-11 <= eps < 1e-6, in float64 below. */
 typedef enum { HFMM_PREC_FP64 = 0, HFMM_PREC_MIXED = 1 } hfmm_precision;
 
@@ -132,7 +134,8 @@ hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, 
 /* Apply (device; Section 2 steps on the Section 3 quadratures).
  * q: device (ns, nrhs) complex of dtype; phi: device (nt, nrhs) complex of dtype,
  * overwritten with the FMM approximation of the sum above.  1 <= nrhs <= max_rhs.
- * Enqueued on `stream`; no allocation, no synchronisation.
+ * Enqueued on `stream` (kernels and, for the symmetric near field, a zero fill of the
+ * plan's workspace); no allocation, no synchronisation.
  * Errors: HFMM_ERR_ARG (bad pointer/size/dtype), HFMM_ERR_STATE (host-only plan),
  * HFMM_ERR_CUDA (launch failure). */
 hfmm_status hfmm_apply(hfmm_plan_t plan, const void* q, void* phi, int nrhs, hfmm_dtype dtype,
