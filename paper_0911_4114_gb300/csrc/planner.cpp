@@ -153,25 +153,38 @@ static void bmtf_coeffs(const Transfer& T, const Twiddle& tw, int ntheta, double
     for (int j = 0; j < m; ++j) samp[j] = 0.5 * T.eval(kTwoPi * j / m, phi);
     for (int f = -ell; f <= ell; ++f) {
         cd acc = 0.0;
-        for (int j = 0; j < m; ++j) acc += samp[j] * tw.fwd(j, f);
+        const int step = mod(f, m);          // (j * f) mod m, stepped with j
+        int t = 0;
+        for (int j = 0; j < m; ++j) {
+            acc += samp[j] * tw.w[t];
+            t += step;
+            if (t >= m) t -= m;
+        }
         tf[f + ell] = acc / (double)m;
     }
     const int b = ntheta / 2 - 1;
+    // F[|sin|] at n - f for |n - f| <= b + ell; zero at odd arguments, so those terms are skipped
+    std::vector<double> st(2 * (b + ell) + 1);
+    for (int k = -(b + ell); k <= b + ell; ++k) st[k + b + ell] = s_tilde(k);
     out.assign(2 * b + 1, cd(0.0));
     for (int n = -b; n <= b; ++n) {
         cd acc = 0.0;
-        for (int f = -ell; f <= ell; ++f) acc += s_tilde(n - f) * tf[f + ell];
+        const int f0 = ((n - (-ell)) % 2 == 0) ? -ell : -ell + 1;
+        for (int f = f0; f <= ell; f += 2) acc += st[n - f + b + ell] * tf[f + ell];
         out[n + b] = acc;
     }
 }
 
-static cd eval_theta(const std::vector<cd>& coef, int ntheta, int n_row) {
-    const int b = ntheta / 2 - 1;
+// sum_f coef_f exp(2 pi i f n_row / ntheta); twt = Twiddle(ntheta) (its inv() holds the same
+// cos / sin values a direct evaluation of each angle gives)
+static cd eval_theta(const std::vector<cd>& coef, const Twiddle& twt, int n_row) {
+    const int b = twt.n / 2 - 1, n = twt.n;
     cd acc = 0.0;
+    int t = mod(-(int64_t)b * n_row, n);   // (f * n_row) mod n, stepped with f
     for (int f = -b; f <= b; ++f) {
-        int64_t t = mod((int64_t)f * n_row, ntheta);
-        double ang = kTwoPi * (double)t / (double)ntheta;
-        acc += coef[f + b] * cd(std::cos(ang), std::sin(ang));
+        acc += coef[f + b] * std::conj(twt.w[t]);
+        t += n_row;
+        if (t >= n) t -= n;
     }
     return acc;
 }
@@ -213,10 +226,11 @@ static std::vector<int> choose_nphi(int ell, double kappa, double r, double r0, 
     const int half = ntheta / 2;
     // T^{s,L}(theta_n, 2 pi p / m) for rows n <= half/2
     std::vector<std::vector<cd>> rows(half / 2 + 1, std::vector<cd>(m));
+    const Twiddle twt(ntheta);
     for (int p = 0; p < m; ++p) {
         std::vector<cd> coef;
         bmtf_coeffs(T, tw, ntheta, kTwoPi * p / m, coef);
-        for (int n = 0; n <= half / 2; ++n) rows[n][p] = eval_theta(coef, ntheta, n);
+        for (int n = 0; n <= half / 2; ++n) rows[n][p] = eval_theta(coef, twt, n);
     }
     std::vector<int> nphi(half + 1, 0);
     for (int n = 0; n <= half / 2; ++n) {
@@ -283,11 +297,12 @@ static std::vector<cd> tsll_canonical(const LevelPlan& lp, double kappa, const i
     const int nfull = 4 * ((2 * ell + 1 + 3) / 4);  // even, >= 2l+2: holds the phi band |m| <= l
     // T^{s,L}(theta_n, phi_p), p < nfull/2 directly, the rest by Eq. NumSphereSym
     std::vector<cd> grid((size_t)(half + 1) * nfull);
+    const Twiddle twt(ntheta);
     for (int p = 0; p < nfull / 2; ++p) {
         std::vector<cd> coef;
         bmtf_coeffs(T, tw, ntheta, kTwoPi * p / nfull, coef);
         for (int n = 0; n < ntheta; ++n) {
-            cd v = eval_theta(coef, ntheta, n);
+            cd v = eval_theta(coef, twt, n);
             if (n <= half) grid[(size_t)n * nfull + p] = v;
             int nn = (ntheta - n) % ntheta;  // f(theta_nn, phi_{p + nfull/2}) = f(theta_n, phi_p)
             if (nn <= half) grid[(size_t)nn * nfull + p + nfull / 2] = v;
@@ -302,13 +317,24 @@ static std::vector<cd> tsll_canonical(const LevelPlan& lp, double kappa, const i
         std::vector<cd> spec(2 * b + 1);
         for (int f = -b; f <= b; ++f) {
             cd acc = 0.0;
-            for (int p = 0; p < nfull; ++p) acc += grid[(size_t)n * nfull + p] * twf.fwd(p, f);
+            const int step = mod(f, nfull);   // (p * f) mod nfull, stepped with p
+            int t = 0;
+            for (int p = 0; p < nfull; ++p) {
+                acc += grid[(size_t)n * nfull + p] * twf.w[t];
+                t += step;
+                if (t >= nfull) t -= nfull;
+            }
             spec[f + b] = acc / (double)nfull;
         }
         Twiddle twn(np);
         for (int j = 0; j < np; ++j) {
             cd acc = 0.0;
-            for (int f = -b; f <= b; ++f) acc += spec[f + b] * twn.inv(j, f);
+            int t = mod(-(int64_t)b * j, np);  // (j * f) mod np, stepped with f
+            for (int f = -b; f <= b; ++f) {
+                acc += spec[f + b] * std::conj(twn.w[t]);
+                t += j;
+                if (t >= np) t -= np;
+            }
             out[(size_t)q.off[n] + j] = acc;
         }
     }
