@@ -425,7 +425,7 @@ static void leaf_keys(const std::vector<double>& p, int64_t n, const double corn
     }
 }
 
-static int max_run(std::vector<uint64_t> sorted_keys, int shift) {
+static int max_run(const std::vector<uint64_t>& sorted_keys, int shift) {
     int best = 0, run = 0;
     for (size_t i = 0; i < sorted_keys.size(); ++i) {
         uint64_t k = sorted_keys[i] >> shift;
@@ -447,12 +447,24 @@ static void build_tree(HostPlan& hp) {
     leaf_keys(hp.tgt, hp.nt, hp.corner, hp.side, kt);
     const int D = hp.lf;
     const int shift = 3 * (kTreeBits - D);
-    // stable sort by depth-D key, ties by original index
+    // sort by depth-D key, ties by original index: one sort of packed (key, index) words when
+    // both fit in 64 bits (3 D key bits + index bits), else a stable index sort
     auto sort_perm = [&](const std::vector<uint64_t>& k, std::vector<int64_t>& perm) {
-        perm.resize(k.size());
-        std::iota(perm.begin(), perm.end(), 0);
-        std::stable_sort(perm.begin(), perm.end(),
-                         [&](int64_t a, int64_t b) { return (k[a] >> shift) < (k[b] >> shift); });
+        const int64_t n = (int64_t)k.size();
+        perm.resize(n);
+        int ibits = 1;
+        while (ibits < 63 && (int64_t(1) << ibits) < n) ++ibits;
+        if (3 * D + ibits <= 64) {
+            std::vector<uint64_t> w(n);
+            for (int64_t i = 0; i < n; ++i) w[i] = ((k[i] >> shift) << ibits) | (uint64_t)i;
+            std::sort(w.begin(), w.end());
+            const uint64_t mask = (ibits == 64) ? ~uint64_t(0) : ((uint64_t(1) << ibits) - 1);
+            for (int64_t i = 0; i < n; ++i) perm[i] = (int64_t)(w[i] & mask);
+        } else {
+            std::iota(perm.begin(), perm.end(), 0);
+            std::stable_sort(perm.begin(), perm.end(),
+                             [&](int64_t a, int64_t b) { return (k[a] >> shift) < (k[b] >> shift); });
+        }
     };
     sort_perm(ks, hp.src_perm);
     sort_perm(kt, hp.tgt_perm);
