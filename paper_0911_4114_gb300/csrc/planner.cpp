@@ -279,6 +279,8 @@ static void plan_level(double kappa, double a, double eps_l, double alpha, Level
     Quadrature& q = lp.quad;
     q.ell = choose_ell(kappa, lp.r, lp.r0, lp.eps_abs, d0);
     q.ntheta = (int)round_fft(choose_ntheta(q.ell, kappa, lp.r, lp.r0, lp.eps_abs), 2);
+    // the device transforms work on lengths up to 1024; refuse before the O(l^3) N_phi search
+    if (q.ntheta > 1024) throw std::runtime_error("N_theta above 1024 is not supported");
     std::vector<int> raw = choose_nphi(q.ell, kappa, lp.r, lp.r0, q.ntheta, lp.eps_abs);
     q.nphi.resize(raw.size());
     for (size_t n = 0; n < raw.size(); ++n) q.nphi[n] = (int)round_fft(raw[n], 4);
@@ -667,6 +669,12 @@ std::string build_host_plan(HostPlan& hp) {
     }
     if (hp.occ_depth < 2) lf = hp.occ_depth;
     hp.lf = lf;
+    // the device transforms work on lengths up to 1024: refuse before the costly tables
+    for (int l = 2; l <= hp.lf; ++l) {
+        if (hp.lp[l].quad.ntheta > 1024) return "N_theta above 1024 is not supported";
+        for (int v : hp.lp[l].quad.nphi)
+            if (v > 1024) return "N_phi above 1024 is not supported";
+    }
     build_tree(hp);
     for (int l = 2; l <= hp.lf; ++l) build_tables(hp.lp[l], hp.kappa);
     return "";

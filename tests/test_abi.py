@@ -61,3 +61,49 @@ def test_degenerate_inputs_plan():
     y = np.repeat(x, 10, axis=0)           # coincident points
     p = FmmPlan(y, y, 1.0, 1e-6, max_leaf=4, device=-1)
     assert p.info()["lf"] <= 1
+
+
+def test_option_and_state_errors():
+    """Options outside their ranges and calls a host-only plan cannot serve are refused
+    with status codes; quadratures beyond the device transform lengths are refused before
+    the transfer tables are built."""
+    import time
+    L = nat.lib()
+    rng = np.random.default_rng(1)
+    x = rng.random((40, 3))
+    h = ctypes.c_void_p()
+
+    def plan_status(**kw):
+        opt = nat.Options()
+        L.hfmm_default_options(ctypes.byref(opt))
+        opt.device = -1
+        for k, v in kw.items():
+            if k == "alphas":
+                for i in range(4):
+                    opt.alpha_ladder[i] = v[i] if i < len(v) else 0.0
+            else:
+                setattr(opt, k, v)
+        return L.hfmm_plan(x.ctypes.data, 40, x.ctypes.data, 40, 5.0, 1e-6, ctypes.byref(opt), ctypes.byref(h))
+
+    assert plan_status() == nat.OK
+    L.hfmm_destroy(h)
+    for bad in (dict(max_rhs=0), dict(max_rhs=5000), dict(depth=21), dict(depth=-1), dict(eps_scale=0.0),
+                dict(eps_scale=1.5), dict(precision=7), dict(max_leaf=0), dict(alphas=(0.3,)),
+                dict(alphas=(1.2,)), dict(alphas=())):
+        assert plan_status(**bad) == nat.ERR_ARG, bad
+    nan_t = x.copy()
+    nan_t[3, 0] = np.inf
+    assert L.hfmm_plan(x.ctypes.data, 40, nan_t.ctypes.data, 40, 5.0, 1e-6, None, ctypes.byref(h)) == nat.ERR_ARG
+    assert L.hfmm_query(None, None) == nat.ERR_ARG
+    assert L.hfmm_destroy(None) == nat.OK
+    p = FmmPlan(x, x, 5.0, 1e-6, device=-1)
+    for call in (lambda: p.apply_adjoint_ptr(1, 1, 1, nat.C128), lambda: p.set_timing(True)):
+        with pytest.raises(nat.HfmmError) as e:
+            call()
+        assert e.value.status == nat.ERR_STATE
+    # a very high-frequency coarse level needs N_theta > 1024: refused quickly
+    t0 = time.perf_counter()
+    with pytest.raises(nat.HfmmError) as e:
+        FmmPlan(x, x, 4000.0, 1e-6, depth=2, root=(0, 0, 0, 1.0), device=-1)
+    assert e.value.status == nat.ERR_ARG and b"above 1024" in L.hfmm_last_error()
+    assert time.perf_counter() - t0 < 30.0
