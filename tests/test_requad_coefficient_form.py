@@ -103,3 +103,58 @@ def test_differs_when_pole_rows_vary():
     # not a signature elsewhere, but the only difference left is in how the pole rows are read
     a2, b2 = oq.requadrature(x2, qa, qb), coefficient_requad(x2, qa, qb)
     assert np.max(np.abs(a2 - b2)) <= 1e-12 * np.max(np.abs(a2))
+
+
+def coefficient_requad_transpose(yflat, qa, qb):
+    """Transpose of coefficient_requad(., qa, qb) as the transposed kernels compute it
+    (k_requad_spec_ct, k_requad_spec_cols_t, k_requad_spec_at_*): grid b -> grid a."""
+    big = int(max(qa.nphi.max(), qb.nphi.max()))
+    nta, ntb = qa.ntheta, qb.ntheta
+    ha, hbr = nta // 2, ntb // 2
+    GB = np.zeros((hbr + 1, big), complex)                  # C'^T: unnormalised inverse FFT
+    for n, row in enumerate(qb.rows(yflat)):
+        ln = len(row)
+        b = _band(big, ln)
+        z = np.fft.ifft(row) * ln
+        for j in range(ln):
+            f = _freq(j, ln)
+            if -b <= f <= b:
+                GB[n, (f + big) % big] = z[j]
+    GA = np.zeros((ha + 1, big), complex)                   # B'^T
+    for c in range(big // 2):
+        se, so = (c, big - 1 - c) if c % 2 == 0 else (big - 1 - c, c)
+        y = np.zeros(ntb, complex)
+        for m in range(ntb):
+            if m in (0, hbr):
+                y[m] = GB[m, se]
+            elif m < hbr:
+                y[m] = 0.5 * (GB[m, se] + GB[m, so])
+            else:
+                y[m] = 0.5 * (GB[ntb - m, se] - GB[ntb - m, so])
+        h = _resample(y, nta) * (ntb / nta)
+        for u in range(ha + 1):
+            hm = h[nta - u] if 0 < u < ha else 0.0
+            GA[u, se], GA[u, so] = h[u] + hm, h[u] - hm
+    out = []                                                # A'^T: forward FFT / N_phi
+    for t in range(ha + 1):
+        ln = int(qa.nphi[t])
+        b = _band(ln, big)
+        buf = np.zeros(ln, complex)
+        for j in range(ln):
+            f = _freq(j, ln)
+            if -b <= f <= b:
+                buf[j] = GA[t, (f + big) % big]
+        out.append(np.fft.fft(buf) / ln)
+    return np.concatenate(out)
+
+
+@pytest.mark.parametrize("kappa,sizes", [(40.0, (2.0 / 8, 2.0 / 4)), (30.0, (2.0 / 16, 2.0 / 8))])
+def test_transposed_passes_are_the_transpose(kappa, sizes):
+    qa, qb = (oq.LevelPlan(kappa, a, 1e-4, 0.8).quad for a in sizes)
+    assert qa.ntheta != qb.ntheta
+    F = np.array([coefficient_requad(e, qa, qb) for e in np.eye(qa.K)]).T    # K_b x K_a
+    rng = np.random.default_rng(11)
+    y = rng.standard_normal(qb.K) + 1j * rng.standard_normal(qb.K)
+    want = F.T @ y
+    got = coefficient_requad_transpose(y, qa, qb)
+    assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
