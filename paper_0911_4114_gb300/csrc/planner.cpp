@@ -227,12 +227,16 @@ static std::vector<int> choose_nphi(int ell, double kappa, double r, double r0, 
     // T^{s,L}(theta_n, 2 pi p / m) for rows n <= half/2
     std::vector<std::vector<cd>> rows(half / 2 + 1, std::vector<cd>(m));
     const Twiddle twt(ntheta);
+    // independent phi samples (each writes its own column)
+#pragma omp parallel for schedule(dynamic, 4)
     for (int p = 0; p < m; ++p) {
         std::vector<cd> coef;
         bmtf_coeffs(T, tw, ntheta, kTwoPi * p / m, coef);
         for (int n = 0; n <= half / 2; ++n) rows[n][p] = eval_theta(coef, twt, n);
     }
     std::vector<int> nphi(half + 1, 0);
+    // independent rows (each writes its own N_phi)
+#pragma omp parallel for schedule(dynamic, 1)
     for (int n = 0; n <= half / 2; ++n) {
         std::vector<double> tt(m);
         for (int f = -ell; f <= ell; ++f) {
