@@ -166,6 +166,69 @@ def count_launches(info):
     return n
 
 
+ALU_NOTE = "152 SMs x 128 FP32 lanes x median SM clock under load"
+
+
+def stage_rooflines(info, stage_ms, n_src, n_tgt, fp32_peak, hbm):
+    """Roofline entry of every stage with a defined unit of work (plan summary `info`, live
+    stage times in ms); FP32-pipe operations against fp32_peak (Gop/s) for arithmetic-bound
+    stages, algorithmic bytes against hbm (GB/s) for the re-quadratures."""
+    levels = {int(l): v for l, v in info["levels"].items()}
+    lev = levels.get(info["lf"], {})
+    sample_bytes = {"fp32": 8.0, "df": 16.0, "fp64": 16.0}
+    # FP32-pipe operations per (list entry, sample) of M2L: complex multiply-add in float32
+    # (4 FMA) or four Dekker products into lazy double-float accumulators (48)
+    m2l_ops = {"fp32": 4.0, "df": 48.0}
+
+    def alu(kernel, ops, ms, unit_work):
+        return dict(kernel=kernel, bound="alu", achieved=ops / (ms * 1e-3) / 1e9, peak=fp32_peak,
+                    unit="Gop/s", unit_work=unit_work, peak_note=ALU_NOTE)
+
+    def one(stage):
+        ms = stage_ms[stage]
+        if ms <= 0.0:
+            return None
+        if stage == "near_field" and info["near_precision"] == "fp32":
+            if info["near_symmetric"]:
+                # pairs of distinct boxes evaluated once (38 ops) plus the reverse product and
+                # its share of the warp reduction (13 ops); pairs inside a box one way (38 ops)
+                off = info["p2p_pairs"] - info["p2p_self_pairs"]
+                ops = 38.0 * info["p2p_self_pairs"] + (38.0 + 13.0) * off / 2
+                return alu("k_p2p_mixed_sym_warp", ops, ms,
+                           "38 float32 ops per evaluated pair + 13 for the reverse direction")
+            return alu("k_p2p_mixed_warp", 38.0 * info["p2p_pairs"], ms, "38 float32 ops per target-source pair")
+        if stage in ("s2m", "l2t") and lev.get("precision") == "df":
+            units = float(lev["K"]) / 2 * (n_tgt if stage == "l2t" else n_src)
+            return alu("k_l2t_df_warp" if stage == "l2t" else "k_s2m_df", 156.0 * units, ms,
+                       "156 float32 ops per (point, antipodal sample pair) in double-float")
+        if stage == "m2l" and levels and all(v["precision"] in m2l_ops for v in levels.values()):
+            ops = sum(m2l_ops[v["precision"]] * v["ilist_total"] * v["K"] for v in levels.values())
+            return alu("k_m2l", ops, ms, "4 (float32) or 48 (double-float) float32 ops per list entry and sample")
+        if stage in ("m2l", "m2m", "l2l"):
+            tot = 0.0
+            for l, v in levels.items():
+                b = sample_bytes[v["precision"]]
+                if stage == "m2l":
+                    tot += (2.0 * v["nbox"] * v["K"] + 316.0 * v["K"]) * b
+                elif l > 2:
+                    up = levels[l - 1]
+                    tot += v["nbox"] * v["K"] * b + up["nbox"] * up["K"] * sample_bytes[up["precision"]]
+            return dict(kernel={"m2l": "k_m2l", "m2m": "k_requad_spec_* (M2M)",
+                                "l2l": "k_requad_spec_* (L2L)"}[stage],
+                        bound="hbm", achieved=tot / (ms * 1e-3) / 1e9, peak=hbm, unit="GB/s",
+                        unit_work="algorithmic signature bytes (each read and written once)")
+        return None
+
+    out = {}
+    for name in stage_ms:
+        r = one(name)
+        if r is not None:
+            r["frac"] = r["achieved"] / r["peak"]
+            r["stage_ms"] = stage_ms[name]
+            out[name] = r
+    return out
+
+
 def main():
     args = parse()
     rank, world = dist_setup(args.gpus)
@@ -314,57 +377,7 @@ def main():
     sm_clock = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * sm_clock * 1e6 / 1e9          # FP32-pipe ops/s (Gop/s)
     hbm = peaks.get("hbm_gbs", 6800.0)
-    levels = {int(l): v for l, v in info["levels"].items()}
-    lev = levels.get(info["lf"], {})
-    sample_bytes = {"fp32": 8.0, "df": 16.0, "fp64": 16.0}
-    alu_note = "152 SMs x 128 FP32 lanes x median SM clock under load"
-
-    def stage_roof(stage):
-        ms = stage_ms[stage]
-        if ms <= 0.0:
-            return None
-        if stage == "near_field" and info["near_precision"] == "fp32":
-            if info["near_symmetric"]:
-                # pairs of distinct boxes evaluated once (38 ops) plus the reverse product and
-                # its share of the warp reduction (13 ops); pairs inside a box one way (38 ops)
-                off = info["p2p_pairs"] - info["p2p_self_pairs"]
-                ops = 38.0 * info["p2p_self_pairs"] + (38.0 + 13.0) * off / 2
-                return dict(kernel="k_p2p_mixed_sym_warp", bound="alu", achieved=ops / (ms * 1e-3) / 1e9,
-                            peak=fp32_peak, unit="Gop/s",
-                            unit_work="38 float32 ops per evaluated pair + 13 for the reverse direction",
-                            peak_note=alu_note)
-            ops = 38.0 * info["p2p_pairs"]               # float32 ops per pair of the mixed near field
-            return dict(kernel="k_p2p_mixed_warp", bound="alu", achieved=ops / (ms * 1e-3) / 1e9,
-                        peak=fp32_peak, unit="Gop/s", unit_work="38 float32 ops per target-source pair",
-                        peak_note=alu_note)
-        if stage in ("s2m", "l2t") and lev.get("precision") == "df":
-            units = float(lev["K"]) / 2 * (len(t) if stage == "l2t" else len(s))
-            ops = 156.0 * units                          # double-float ops per (point, antipodal pair)
-            return dict(kernel="k_l2t_df_warp" if stage == "l2t" else "k_s2m_df", bound="alu",
-                        achieved=ops / (ms * 1e-3) / 1e9, peak=fp32_peak, unit="Gop/s",
-                        unit_work="156 float32 ops per (point, antipodal sample pair) in double-float",
-                        peak_note=alu_note)
-        if stage in ("m2l", "m2m", "l2l"):
-            tot = 0.0
-            for l, v in levels.items():
-                b = sample_bytes[v["precision"]]
-                if stage == "m2l":
-                    tot += (2.0 * v["nbox"] * v["K"] + 316.0 * v["K"]) * b
-                elif l > 2:
-                    up = levels[l - 1]
-                    tot += v["nbox"] * v["K"] * b + up["nbox"] * up["K"] * sample_bytes[up["precision"]]
-            return dict(kernel={"m2l": "k_m2l", "m2m": "k_requad_* (M2M)", "l2l": "k_requad_* (L2L)"}[stage],
-                        bound="hbm", achieved=tot / (ms * 1e-3) / 1e9, peak=hbm, unit="GB/s",
-                        unit_work="algorithmic signature bytes (each read and written once)")
-        return None
-
-    roof_stages = {}
-    for st_name in stage_ms:
-        r_ = stage_roof(st_name)
-        if r_ is not None:
-            r_["frac"] = r_["achieved"] / r_["peak"]
-            r_["stage_ms"] = stage_ms[st_name]
-            roof_stages[st_name] = r_
+    roof_stages = stage_rooflines(info, stage_ms, len(s), len(t), fp32_peak, hbm)
     stage = max(stage_ms, key=stage_ms.get)
     roof = dict(roof_stages.get(stage) or {"kernel": stage, "bound": None, "achieved": None, "peak": None,
                                           "unit": None, "frac": None, "stage_ms": stage_ms[stage]})
