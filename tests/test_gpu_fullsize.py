@@ -1,8 +1,10 @@
 """Full-size workloads on the GPU, checked on sampled outputs against the CPU oracle.
 
 * 2,097,152 points on the (1, 0.5, 0.25) ellipsoid, kappa = 200: eps = 1e-4 (mixed, complex64)
-  and eps = 1e-8 (mixed policy: double-float far field, float64 near field, complex128);
-* 524,288 points in the unit cube, kappa = 40, 64 right-hand sides, eps = 1e-5;
+  and eps = 1e-8 (mixed policy: double-float and float64 far-field levels, double-float near
+  field, complex128);
+* 524,288 points in the unit cube, kappa = 40, 64 right-hand sides, eps = 1e-5 (tensor-core
+  near field);
 * 32 uneven problems (N log-uniform in [8192, 131072], kappa uniform in [10, 60], 4 RHS,
   eps = 1e-5) in one graph launch;
 * 131,072 sources on the unit sphere, 131,072 targets on the radius-1.5 sphere, kappa = 32,
