@@ -294,57 +294,59 @@ static void plan_level(double kappa, double a, double eps_l, double alpha, Level
 // ---------------------------------------------------------------------------
 // T^{s,LL}: 34 canonical vectors by Algorithm BMTF + per-row anterpolation, 316 by reflection
 // ---------------------------------------------------------------------------
-static std::vector<cd> tsll_canonical(const LevelPlan& lp, double kappa, const int d[3]) {
+// Per canonical vector: T^{s,L}(theta_n, phi_p) on the full phi grid (nfull samples, p <
+// nfull/2 directly, the rest by Eq. NumSphereSym), then each row anterpolated nfull ->
+// N_phi(theta_n).  The work is split into independent items (vector, phi sample) and
+// (vector, row) so that all cores share one level's tables.
+struct CanonWork {
+    int d[3];
+    Transfer T;
+    std::vector<cd> grid;   // (half + 1) x nfull
+    std::vector<cd> out;    // K
+    CanonWork(const int dd[3], const LevelPlan& lp, double kappa)
+        : d{dd[0], dd[1], dd[2]},
+          T(lp.quad.ell, kappa, std::array<double, 3>{dd[0] * lp.a, dd[1] * lp.a, dd[2] * lp.a}.data()) {}
+};
+
+static void tsll_column(CanonWork& w, const LevelPlan& lp, const Twiddle& tw, const Twiddle& twt, int nfull, int p) {
+    const int ntheta = lp.quad.ntheta, half = ntheta / 2;
+    std::vector<cd> coef;
+    bmtf_coeffs(w.T, tw, ntheta, kTwoPi * p / nfull, coef);
+    for (int n = 0; n < ntheta; ++n) {
+        cd v = eval_theta(coef, twt, n);
+        if (n <= half) w.grid[(size_t)n * nfull + p] = v;
+        int nn = (ntheta - n) % ntheta;  // f(theta_nn, phi_{p + nfull/2}) = f(theta_n, phi_p)
+        if (nn <= half) w.grid[(size_t)nn * nfull + p + nfull / 2] = v;
+    }
+}
+
+static void tsll_row(CanonWork& w, const LevelPlan& lp, const Twiddle& twf, int nfull, int n) {
     const Quadrature& q = lp.quad;
-    const int ell = q.ell, ntheta = q.ntheta, half = ntheta / 2;
-    double r0v[3] = {d[0] * lp.a, d[1] * lp.a, d[2] * lp.a};
-    Transfer T(ell, kappa, r0v);
-    Twiddle tw(2 * ell + 1);
-    const int nfull = 4 * ((2 * ell + 1 + 3) / 4);  // even, >= 2l+2: holds the phi band |m| <= l
-    // T^{s,L}(theta_n, phi_p), p < nfull/2 directly, the rest by Eq. NumSphereSym
-    std::vector<cd> grid((size_t)(half + 1) * nfull);
-    const Twiddle twt(ntheta);
-    for (int p = 0; p < nfull / 2; ++p) {
-        std::vector<cd> coef;
-        bmtf_coeffs(T, tw, ntheta, kTwoPi * p / nfull, coef);
-        for (int n = 0; n < ntheta; ++n) {
-            cd v = eval_theta(coef, twt, n);
-            if (n <= half) grid[(size_t)n * nfull + p] = v;
-            int nn = (ntheta - n) % ntheta;  // f(theta_nn, phi_{p + nfull/2}) = f(theta_n, phi_p)
-            if (nn <= half) grid[(size_t)nn * nfull + p + nfull / 2] = v;
+    const int np = q.nphi[n];
+    const int b = std::min((nfull + 1) / 2, (np + 1) / 2) - 1;
+    std::vector<cd> spec(2 * b + 1);
+    for (int f = -b; f <= b; ++f) {
+        cd acc = 0.0;
+        const int step = mod(f, nfull);   // (p * f) mod nfull, stepped with p
+        int t = 0;
+        for (int p = 0; p < nfull; ++p) {
+            acc += w.grid[(size_t)n * nfull + p] * twf.w[t];
+            t += step;
+            if (t >= nfull) t -= nfull;
         }
+        spec[f + b] = acc / (double)nfull;
     }
-    // anterpolate each row nfull -> N_phi(theta_n)
-    Twiddle twf(nfull);
-    std::vector<cd> out((size_t)q.K);
-    for (int n = 0; n <= half; ++n) {
-        const int np = q.nphi[n];
-        const int b = std::min((nfull + 1) / 2, (np + 1) / 2) - 1;
-        std::vector<cd> spec(2 * b + 1);
+    Twiddle twn(np);
+    for (int j = 0; j < np; ++j) {
+        cd acc = 0.0;
+        int t = mod(-(int64_t)b * j, np);  // (j * f) mod np, stepped with f
         for (int f = -b; f <= b; ++f) {
-            cd acc = 0.0;
-            const int step = mod(f, nfull);   // (p * f) mod nfull, stepped with p
-            int t = 0;
-            for (int p = 0; p < nfull; ++p) {
-                acc += grid[(size_t)n * nfull + p] * twf.w[t];
-                t += step;
-                if (t >= nfull) t -= nfull;
-            }
-            spec[f + b] = acc / (double)nfull;
+            acc += spec[f + b] * std::conj(twn.w[t]);
+            t += j;
+            if (t >= np) t -= np;
         }
-        Twiddle twn(np);
-        for (int j = 0; j < np; ++j) {
-            cd acc = 0.0;
-            int t = mod(-(int64_t)b * j, np);  // (j * f) mod np, stepped with f
-            for (int f = -b; f <= b; ++f) {
-                acc += spec[f + b] * std::conj(twn.w[t]);
-                t += j;
-                if (t >= np) t -= np;
-            }
-            out[(size_t)q.off[n] + j] = acc;
-        }
+        w.out[(size_t)q.off[n] + j] = acc;
     }
-    return out;
 }
 
 // reflect the canonical table into vector d: T_d(s) = T_canon(P F s)
@@ -375,9 +377,24 @@ static void build_tables(LevelPlan& lp, double kappa) {
         for (int y = 0; y <= x; ++y)
             for (int z = 0; z <= 3; ++z)
                 if (std::max(x, std::max(y, z)) >= 2) canon.push_back({x, y, z});
+    const Quadrature& q = lp.quad;
+    const int ell = q.ell, half = q.ntheta / 2;
+    const int nfull = 4 * ((2 * ell + 1 + 3) / 4);  // even, >= 2l+2: holds the phi band |m| <= l
+    const Twiddle tw(2 * ell + 1), twt(q.ntheta), twf(nfull);
+    std::vector<CanonWork> work;
+    work.reserve(canon.size());
+    for (auto& cv : canon) {
+        work.emplace_back(cv.data(), lp, kappa);
+        work.back().grid.assign((size_t)(half + 1) * nfull, cd(0.0));
+        work.back().out.assign((size_t)q.K, cd(0.0));
+    }
+    const int nc = (int)canon.size(), ncol = nfull / 2, nrow = half + 1;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int it = 0; it < nc * ncol; ++it) tsll_column(work[it / ncol], lp, tw, twt, nfull, it % ncol);
+#pragma omp parallel for schedule(dynamic, 2)
+    for (int it = 0; it < nc * nrow; ++it) tsll_row(work[it / nrow], lp, twf, nfull, it % nrow);
     std::vector<std::vector<cd>> ct(canon.size());
-#pragma omp parallel for schedule(dynamic, 1)
-    for (int c = 0; c < (int)canon.size(); ++c) ct[c] = tsll_canonical(lp, kappa, canon[c].data());
+    for (int c = 0; c < nc; ++c) ct[c] = std::move(work[c].out);
     for (int di = -3; di <= 3; ++di)
         for (int dj = -3; dj <= 3; ++dj)
             for (int dk = -3; dk <= 3; ++dk) {
