@@ -154,3 +154,37 @@ def test_near_field_policy_and_symmetry_flags():
     info = lib.info()
     assert info["p2p_self_pairs"] == int(np.sum(t.src_count.astype(np.int64) * t.tgt_count))
     assert 0 < info["p2p_self_pairs"] < info["p2p_pairs"]
+
+
+def test_plan_independent_of_thread_count(tmp_path):
+    """The planner's parallel loops (quadrature search, transfer tables, interaction lists)
+    compute independent items: a plan built with one OpenMP thread must equal the default
+    one bit for bit."""
+    import os
+    import pickle
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "dump.py"
+    script.write_text(
+        "import sys, pickle, numpy as np\n"
+        f"sys.path.insert(0, {root!r})\n"
+        "from paper_0911_4114_gb300 import FmmPlan\n"
+        "x = np.random.default_rng(5).random((2000, 3))\n"
+        "p = FmmPlan(x, x, 50.0, 1e-7, precision='mixed', depth=3, root=(0, 0, 0, 1.0), device=-1)\n"
+        "out = {'lf': p.info()['lf'], 'perm': p.debug_get('SRC_PERM')}\n"
+        "for l in range(2, out['lf'] + 1):\n"
+        "    out[('nphi', l)] = p.debug_get('NPHI', l)\n"
+        "    for v in (0 * 49 + 1 * 7 + 5, 5 * 49 + 3 * 7 + 0, 6 * 49 + 6 * 7 + 6, 1 * 49 + 6 * 7 + 3):\n"
+        "        out[('T', l, v)] = p.debug_get('TABLE', l, v)\n"
+        "pickle.dump(out, open(sys.argv[1], 'wb'))\n")
+    res = {}
+    for threads in ("1", "4"):
+        f = tmp_path / f"plan{threads}.pkl"
+        env = dict(os.environ, OMP_NUM_THREADS=threads)
+        subprocess.run([sys.executable, str(script), str(f)], check=True, env=env)
+        res[threads] = pickle.load(open(f, "rb"))
+    a, b = res["1"], res["4"]
+    assert a.keys() == b.keys() and a["lf"] >= 2
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
