@@ -35,9 +35,9 @@ def make_options(precision="fp64", alphas=None, eps_scale=0.25, max_leaf=64, dep
 class FmmPlan:
     """Plan of the FMM apply for fixed sources, targets, kappa and eps.
 
-    precision: "fp64" (every stage float64) or "mixed" (float32 where the planner's
-    round-off estimate allows, float64 elsewhere).  device=-1 builds a host-only plan
-    (queries only).
+    precision: "fp64" (every stage float64) or "mixed" (per level float32, double-float or
+    float64, the first the planner's round-off estimate allows; the near field in float32,
+    double-float or float64 by eps).  device=-1 builds a host-only plan (queries only).
     """
 
     def __init__(self, sources, targets, kappa, eps, precision="fp64", alphas=None,
