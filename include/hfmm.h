@@ -242,11 +242,13 @@ int64_t hfmm_debug_get(hfmm_plan_t plan, int what, int level, int64_t arg, void*
 #define HFMM_NOALLOC_MAX_POINTS (1 << 19)
 
 /* Direct near-field sum for callers that cannot allocate device memory.  The paper has
- * no counterpart: this is a library service.  Some callers cannot call cudaMalloc --
- * code running while a stream is captured into a CUDA graph (allocation cannot be
- * captured), or code inside a host framework's operator callback that may only use the
- * framework's own memory pool.  They have no plan (creating one allocates), so this
- * entry point takes everything as device pointers and allocates nothing:
+ * no counterpart: this is a library service.  Some callers cannot call cudaMalloc -- code
+ * inside a host framework's operator whose device memory may only come from the
+ * framework's own pool (an allocation behind the pool's back escapes its accounting and
+ * memory limit), or code on a latency-critical path, where a device allocation is an
+ * implicit synchronisation point between streams.  They have no plan (creating one
+ * allocates), so this entry point takes everything as device pointers and allocates
+ * nothing:
  *   sources (ns, 3), targets (nt, 3): device float64, row-major;
  *   q (ns, nrhs), phi (nt, nrhs): device complex of dtype; phi is overwritten with
  *   sum_{j : R_ij > 0} q_j exp(i kappa R_ij) / R_ij over ALL sources (O(ns * nt) work),
@@ -259,7 +261,9 @@ int64_t hfmm_debug_get(hfmm_plan_t plan, int what, int level, int64_t arg, void*
  * address (cudaGetSymbolAddress) with that device current; make that first call before
  * any stream capture.  Every call shares the array, so calls that overlap on the GPU
  * (other streams, other threads) race and must be serialised by the caller.  Enqueued on
- * `stream`; no synchronisation.  Errors: HFMM_ERR_ARG, HFMM_ERR_CUDA. */
+ * `stream`; no synchronisation.  A CUDA error already pending when the call starts is
+ * reported (HFMM_ERR_CUDA) and left in place; nothing is launched then.
+ * Errors: HFMM_ERR_ARG, HFMM_ERR_CUDA. */
 hfmm_status hfmm_direct_noalloc(const double* sources, int64_t ns, const double* targets, int64_t nt,
                                 const void* q, void* phi, int nrhs, hfmm_dtype dtype, double kappa,
                                 void* stream);

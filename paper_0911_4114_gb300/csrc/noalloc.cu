@@ -1,13 +1,14 @@
 // hfmm_direct_noalloc: the mixed-precision near-field sum without any device allocation.
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is being captured
-// into a CUDA graph (allocation is not a capturable operation), or code inside a host
-// framework's operator callback whose device memory must come only from the framework's
-// own pool.  This entry point serves them: the caller passes device inputs and outputs,
-// and the only extra device memory it uses -- the point coordinates converted to the
-// exact grid + fraction form of the mixed near-field arithmetic and the bounding box --
-// lives in one file-scope __device__ array of fixed size that every GPU loading this
-// library holds until the process exits.
+// Some callers cannot call cudaMalloc: code inside a host framework's operator whose device
+// memory may only come from the framework's own pool (an allocation behind the pool's back
+// escapes its accounting and its memory limit), and code on a latency-critical path, where
+// a device allocation is an implicit synchronisation point between streams.  Such callers
+// cannot build a plan, because planning allocates.  This entry point serves them: the
+// caller passes device inputs and outputs, and the only extra device memory it uses -- the
+// point coordinates converted to the exact grid + fraction form of the mixed near-field
+// arithmetic and the bounding box -- lives in one file-scope __device__ array of fixed size
+// that every GPU loading this library holds until the process exits.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -196,8 +197,14 @@ hfmm_status hfmm_direct_noalloc(const double* sources, int64_t ns, const double*
     if (nrhs < 1 || nrhs > 4096) return fail(HFMM_ERR_ARG, "nrhs must be in [1, 4096]");
     if (dtype != HFMM_C64 && dtype != HFMM_C128) return fail(HFMM_ERR_ARG, "unknown dtype");
     if (!(kappa > 0.0)) return fail(HFMM_ERR_ARG, "kappa must be > 0");
+    // an error left by earlier, unrelated work is reported as such and not cleared, so that
+    // the caller's own error state survives and the launch check below sees only our launches
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess)
+        return fail(HFMM_ERR_CUDA, std::string("a CUDA error was pending before hfmm_direct_noalloc was called "
+                                               "(left in place): ") + cudaGetErrorString(e));
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(HFMM_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     unsigned char* base = nullptr;
     hfmm_status s = scratch_for(dev, &base);

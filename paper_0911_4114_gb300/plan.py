@@ -174,7 +174,9 @@ def direct_noalloc(sources, targets, q, kappa, out=None, stream=None):
     """Direct near-field sum through hfmm_direct_noalloc (no device allocation inside).
 
     sources (ns, 3), targets (nt, 3): CUDA float64 tensors; q: CUDA complex64/128 (ns,) or
-    (ns, R).  For callers that cannot allocate, pass `out` (nt, R) preallocated.
+    (ns, R), all on one device.  Callers that may not allocate pass `out`, a contiguous
+    (nt, R) tensor of q's dtype on that device; without it this wrapper allocates `out`.
+    Every shape, dtype and device is checked here, before the native call.
     """
     import torch
     for name, t in (("sources", sources), ("targets", targets)):
@@ -182,15 +184,25 @@ def direct_noalloc(sources, targets, q, kappa, out=None, stream=None):
             raise ValueError(f"{name} must be a contiguous CUDA float64 (n, 3) tensor")
     if not q.is_cuda or q.dtype not in (torch.complex64, torch.complex128):
         raise ValueError("q must be a CUDA complex64/complex128 tensor")
+    if q.dim() not in (1, 2):
+        raise ValueError("q must have shape (ns,) or (ns, R)")
+    if sources.device != q.device or targets.device != q.device:
+        raise ValueError("sources, targets and q must be on one device")
     single = q.dim() == 1
     q2 = q.reshape(q.shape[0], -1).contiguous()
+    if q2.shape[0] != sources.shape[0]:
+        raise ValueError(f"q has {q2.shape[0]} rows, there are {sources.shape[0]} sources")
     r = q2.shape[1]
+    nt = targets.shape[0]
     if out is None:
-        out = torch.empty((targets.shape[0], r), dtype=q.dtype, device=q.device)
+        out = torch.empty((nt, r), dtype=q.dtype, device=q.device)
+    elif (out.device != q.device or out.dtype != q.dtype or tuple(out.shape) != (nt, r)
+          or not out.is_contiguous()):
+        raise ValueError("out must be a contiguous (nt, R) tensor of q's dtype on q's device")
     st = stream if stream is not None else torch.cuda.current_stream(q.device)
     dtype = nat.C64 if q.dtype == torch.complex64 else nat.C128
     nat.check(nat.lib().hfmm_direct_noalloc(sources.data_ptr(), sources.shape[0], targets.data_ptr(),
-                                             targets.shape[0], q2.data_ptr(), out.data_ptr(), r, dtype,
+                                             nt, q2.data_ptr(), out.data_ptr(), r, dtype,
                                              float(kappa), st.cuda_stream))
     return out[:, 0] if single else out
 

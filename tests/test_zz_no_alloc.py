@@ -1,12 +1,13 @@
 """hfmm_direct_noalloc: the near-field sum for callers that cannot allocate device memory.
 
-Such callers (code running under CUDA graph stream capture, or inside a host framework's
-operator callback that may only use the framework's memory pool) cannot create a plan,
-because planning allocates.  The entry point takes device inputs and outputs and keeps its
-scratch in a fixed static device array.  It must agree with the planned apply, which for a
-plan whose whole tree is one box is the same mixed-precision direct sum, on two calls in a
-row (the second reuses the array the first one filled).  This file is collected last so a
-stop-at-first-failure run has already run every other test.
+Such callers (code inside a host framework's operator that may only use the framework's
+memory pool, or code on a latency-critical path where an allocation would synchronise
+streams) cannot create a plan, because planning allocates.  The entry point takes device
+inputs and outputs and keeps its scratch in a fixed static device array.  It must agree
+with the planned apply, which for a plan whose whole tree is one box is the same
+mixed-precision direct sum, on two calls in a row (the second reuses the array the first
+one filled).  This file is collected last so a stop-at-first-failure run has already run
+every other test.
 """
 import ctypes
 
