@@ -9,7 +9,7 @@ import pytest
 
 from oracle import direct, fmm as ofmm
 from paper_0911_4114_gb300 import FmmPlan, workloads as wl
-from gpu_util import fp64_parity_tol, rel
+from gpu_util import fp64_parity_tol, fp64_round_est, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -60,6 +60,8 @@ def test_dot_product_identity_and_direct_adjoint(name, precision):
     if precision == "fp64":
         orc = ofmm.Plan(s, t, kappa, eps, precision="fp64", **kw)
         tol = fp64_parity_tol(orc)
+        print(f"fp64-dot {name}: |<Ax,y> - <x,A^H y>|/(|Ax||y|) = {abs(lhs - rhs) / scale:.3e}  "
+              f"est = {fp64_round_est(orc):.3e}")
     else:
         tol = 1e-6
     assert abs(lhs - rhs) <= tol * scale, (name, abs(lhs - rhs) / scale)

@@ -11,7 +11,7 @@ import pytest
 
 from oracle import direct, fmm as ofmm
 from paper_0911_4114_gb300 import FmmPlan, workloads as wl
-from gpu_util import fp64_parity_tol, rel, run_apply
+from gpu_util import check_fp64_parity, fp64_parity_tol, rel, run_apply
 
 pytestmark = pytest.mark.gpu
 
@@ -50,9 +50,26 @@ def test_fp64_matches_oracle_fmm_and_direct(name):
     assert lib.info()["lf"] == orc.lf
     got = run_apply(lib, q)
     want = ofmm.apply(orc, q)
-    tol = fp64_parity_tol(orc)
-    assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want)), (name, tol)
+    check_fp64_parity(got, want, orc, name)
     assert rel(got, direct.direct(s, t, q, kappa)) <= eps
+
+
+def test_fp64_well_conditioned_cube_matches_oracle_to_1e12():
+    """The 4,096-point uniform-cube workload on one propagating level (depth 2, root [0,1]^3,
+    kappa = 120 so kappa a_2 = 30: the quadrature sum has little cancellation and the
+    round-off estimate is ~4e-16).  Here the float64 GPU apply must match the oracle FMM
+    element-wise to 1e-12 relative to max|phi| with no round-off allowance."""
+    x, _ = wl.points("cube4k_fp64")
+    kappa, eps, kw = 120.0, 1e-6, dict(depth=2, root=(0, 0, 0, 1.0))
+    q = wl.charges(len(x), 0, wl.rng(7))
+    lib = FmmPlan(x, x, kappa, eps, precision="fp64", **kw)
+    orc = ofmm.Plan(x, x, kappa, eps, precision="fp64", **kw)
+    assert lib.info()["lf"] == orc.lf == 2
+    got = run_apply(lib, q)
+    want = ofmm.apply(orc, q)
+    diff, est = check_fp64_parity(got, want, orc, "cube4k_kappa120_depth2", mult=0.0)
+    assert est < 1e-15 and diff <= 1e-12
+    assert rel(got, direct.direct(x, x, q, kappa)) <= eps
 
 
 @pytest.mark.parametrize("name", ["cube4k", "cube_hf", "sphere_small", "two_spheres"])
