@@ -1,0 +1,80 @@
+"""Full-size plans: the library's host planner against the oracle's, bit for bit (CPU only).
+
+The configurations that the benchmark and the full-size GPU tests run -- 262,144 points on
+the sphere, 2,097,152 on the ellipsoid at eps 1e-4 and 1e-8, the 524,288-point cube with 64
+right-hand sides, the two-sphere gradient problem -- are planned by both sides with host-only
+plans.  Point permutations, every level's box coordinates and parents, every interaction
+list with its transfer vectors, every leaf neighbour list, the leaf point ranges, and the
+plan integers (active levels, l, N_theta, N_phi(theta_n), K, alpha, level precision) must be
+identical.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+from oracle import fmm as ofmm
+from paper_0911_4114_gb300 import FmmPlan, workloads as wl
+
+CONFIGS = [
+    ("sphere262k", 64.0, 1e-6, "mixed"),
+    ("sphere262k", 64.0, 1e-6, "fp64"),
+    ("ellipsoid2m", 200.0, 1e-4, "mixed"),
+    ("ellipsoid2m", 200.0, 1e-8, "mixed"),
+    ("cube512k_rhs64", 40.0, 1e-5, "mixed"),
+    ("spheres131k_grad", 32.0, 1e-6, "fp64"),
+    ("spheres131k_grad", 32.0, 1e-6, "mixed"),
+]
+
+
+@functools.lru_cache(maxsize=2)
+def _points(name):
+    return wl.points(name)
+
+
+def _csr(lists):
+    off = np.zeros(len(lists) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([len(x) for x in lists])
+    flat = np.concatenate(lists) if len(lists) else np.zeros(0, dtype=np.int64)
+    return off, flat
+
+
+@pytest.mark.parametrize("cfg", CONFIGS, ids=[f"{c[0]}-{c[2]:g}-{c[3]}" for c in CONFIGS])
+def test_fullsize_plan_bit_exact(cfg):
+    name, kappa, eps, prec = cfg
+    s, t = _points(name)
+    lib = FmmPlan(s, t, kappa, eps, precision=prec, device=-1)
+    orc = ofmm.Plan(s, t, kappa, eps, precision=prec)
+    info = lib.info()
+    # plan integers
+    assert info["lf"] == orc.lf >= 2
+    assert info["occupancy_depth"] == orc.occupancy_depth
+    for l, lp in orc.levels.items():
+        li = info["levels"][l]
+        assert (li["ell"], li["ntheta"], li["K"]) == (lp.ell, lp.ntheta, lp.K), (name, l)
+        assert li["alpha"] == lp.alpha and li["precision"] == orc.level_precision[l], (name, l)
+        assert np.array_equal(lib.debug_get("NPHI", l), lp.nphi), (name, l)
+    # tree
+    tr = orc.tree
+    assert np.array_equal(lib.debug_get("SRC_PERM"), tr.src_perm)
+    assert np.array_equal(lib.debug_get("TGT_PERM"), tr.tgt_perm)
+    for l in range(tr.depth + 1):
+        assert np.array_equal(lib.debug_get("BOX_IDX", l), tr.levels[l]["idx"]), (name, l)
+        if l > 0:
+            assert np.array_equal(lib.debug_get("BOX_PARENT", l), tr.levels[l]["parent"]), (name, l)
+    # lists
+    for l in range(2, tr.depth + 1):
+        off, idx = _csr(tr.ilist[l])
+        _, v = _csr(tr.vlist[l])
+        assert np.array_equal(lib.debug_get("ILIST_OFF", l), off), (name, l)
+        assert np.array_equal(lib.debug_get("ILIST_IDX", l), idx), (name, l)
+        assert np.array_equal(lib.debug_get("ILIST_V", l), v), (name, l)
+    off, idx = _csr(tr.nlist)
+    assert np.array_equal(lib.debug_get("NLIST_OFF"), off)
+    assert np.array_equal(lib.debug_get("NLIST_IDX"), idx)
+    ls, lt = lib.debug_get("LEAF_SRC"), lib.debug_get("LEAF_TGT")
+    assert np.array_equal(ls[:, 1], tr.src_count) and np.array_equal(lt[:, 1], tr.tgt_count)
+    nz = tr.src_count > 0
+    assert np.array_equal(ls[nz, 0], tr.src_start[nz])
+    nz = tr.tgt_count > 0
+    assert np.array_equal(lt[nz, 0], tr.tgt_start[nz])
