@@ -1,14 +1,24 @@
 """Benchmark of the FMM apply on one GB300 (or N independent replicas under torchrun).
 
-Workload: 262,144 points uniform on the unit sphere (sources = targets), kappa = 64,
-eps = 1e-6, complex64 charges N(0,1), one right-hand side.  The headline `value` is the
-mixed-precision apply in Mpoints*RHS/s (N_t * R / t_apply / 1e6) with inputs resident in
-HBM; `fp64_path` is the all-float64 apply on the same workload; `e2e` is the same metric
-through the public API with pinned host buffers and both copies inside the timed region.
-Every timed apply is preceded by an L2 flush (a 512 MiB write) outside its event pair.
+Headline workload: 2,097,152 points uniform by area on the (1, 0.5, 0.25) ellipsoid
+(sources = targets), kappa = 200, eps = 1e-4, complex64 charges N(0,1), one right-hand side,
+mixed precision.  `value` is that apply in Mpoints*RHS/s (N_t * R / t_apply / 1e6) with
+inputs resident in HBM; every timed apply is preceded by an L2 flush (a 512 MiB write)
+outside its event pair.  Beside it, on the same points:
+  fp64_path   the all-float64 apply at eps 1e-4;
+  tight       the mixed apply at eps 1e-8 with complex128 charges, and the float64 apply there;
+  rel_err     relative L2 error against the float64 direct sum on 1,000 seeded targets
+              (the library's float64 direct sum, which the tests pin to the oracle), and
+              against the oracle's direct sum on a 64-target subset;
+  e2e         the headline metric through the public API, pinned host buffers, both copies
+              inside the timed region.
+`extras`: the 262,144-point sphere (kappa 64, eps 1e-6, mixed and float64), the adjoint of
+the headline plan, the 524,288-point cube with 64 right-hand sides and 32 uneven problems in
+one graph launch.
 
---impl reference times the CPU oracle (direct sum over all sources for a seeded subset of
-targets) on the host cores; it is the baseline arm, not the target.
+cpu_baseline / --impl reference: the oracle's float64 Fourier FMM at the same plan, timed
+stage by stage on seeded samples of boxes and extrapolated by each stage's work (plan and
+transfer tables excluded, as for the GPU); the baseline arm, not the target.
 """
 import argparse
 import json
@@ -23,9 +33,13 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(workload="sphere262k", points=262144, surface="unit sphere", kappa=64.0, eps=1e-6,
-                nrhs=1, charges="complex64 N(0,1)")
-ORACLE_TARGETS = 2000
+METRIC = "FMM apply Mpoints*RHS/s at stated rel. err; mixed vs FP64 on one GB300"
+HEADLINE = dict(workload="ellipsoid2m", points=2097152, surface="(1, 0.5, 0.25) ellipsoid, uniform by area",
+                kappa=200.0, eps=1e-4, nrhs=1, charges="complex64 N(0,1)", precision="mixed")
+TIGHT_EPS = 1e-8
+REL_ERR_TARGETS = 1000
+ORACLE_DIRECT_TARGETS = 64
+STAGES = ("permute_in", "near_field", "s2m", "m2m", "m2l", "l2l", "l2t", "permute_out")
 
 
 def parse():
@@ -34,11 +48,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-fp64", action="store_true", help="skip the float64-path measurement")
-    ap.add_argument("--points", type=int, default=262144, help="smaller sphere for profiling runs")
+    ap.add_argument("--points", type=int, default=2097152, help="smaller ellipsoid for profiling runs")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the float64-path measurements")
+    ap.add_argument("--no-tight", action="store_true", help="skip the eps = 1e-8 measurements")
     ap.add_argument("--skip-oracle", action="store_true", help="skip the CPU oracle timing")
-    ap.add_argument("--no-extras", action="store_true",
-                    help="skip the adjoint and 64-RHS cube measurements")
+    ap.add_argument("--no-extras", action="store_true", help="skip the extra workloads")
     return ap.parse_args()
 
 
@@ -120,14 +134,9 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(sm)}
 
 
-def time_oracle(s, t, q, kappa, ntargets, seed):
-    from oracle import direct
-    idx = np.sort(np.random.default_rng(seed).choice(len(t), ntargets, replace=False))
-    t0 = time.perf_counter()
-    direct.direct(s, t[idx], q, kappa)
-    return time.perf_counter() - t0
-
-
+# ----------------------------------------------------------------------------------------
+# CPU oracle legs (cpu_baseline and --impl reference)
+# ----------------------------------------------------------------------------------------
 def oracle_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -136,29 +145,134 @@ def oracle_threads():
         return os.cpu_count() or 1
 
 
+def oracle_direct_sample(s, t, q, kappa, ntargets, seed):
+    """The oracle's float64 direct sum over all sources for `ntargets` seeded targets."""
+    from oracle import direct
+    idx = np.sort(np.random.default_rng(seed).choice(len(t), ntargets, replace=False))
+    t0 = time.perf_counter()
+    vals = direct.direct(s, t[idx], q, kappa, block=8)
+    return idx, vals, time.perf_counter() - t0
+
+
+class OracleFmmSampler:
+    """The oracle's Fourier FMM at the GPU run's plan, timed stage by stage on seeded samples
+    of boxes and extrapolated to one whole apply by each stage's work.
+
+    Work measures: near field, target-source pairs; S2M, sources; L2T, targets; M2M and L2L,
+    child boxes; M2L, interaction-list entries.  The plan (tree, quadratures) and the transfer
+    tables of the sampled boxes are built before timing, as the GPU apply excludes its plan.
+    Signatures fed to the sampled stages are zeros of the right shapes (the arithmetic does not
+    depend on their values)."""
+
+    def __init__(self, s, t, q, kappa, eps, precision="mixed", leaf_boxes=12, level_boxes=3, seed=0):
+        from oracle import fmm as ofmm
+        self.ofmm = ofmm
+        self.plan = ofmm.Plan(s, t, kappa, eps, precision=precision)
+        self.q = np.asarray(q, dtype=np.complex128).reshape(len(s), -1)
+        self.nt = len(t)
+        tr = self.plan.tree
+        lf = tr.depth
+        g = np.random.default_rng(seed)
+        nleaf = len(tr.levels[lf]["key"])
+        busy = np.flatnonzero((tr.tgt_count > 0) | (tr.src_count > 0))
+        self.leaf = np.sort(g.choice(busy, min(leaf_boxes, len(busy)), replace=False))
+        self.level = {}
+        for l in range(2, lf + 1):
+            nb = len(tr.levels[l]["key"])
+            self.level[l] = np.sort(g.choice(nb, min(level_boxes, nb), replace=False))
+        # work of the samples and of the whole apply
+        pairs = np.array([tr.tgt_count[b] * sum(int(tr.src_count[n]) for n in tr.nlist[b]) for b in range(nleaf)],
+                         dtype=np.float64)
+        self.work = {"near": (pairs[self.leaf].sum(), pairs.sum()),
+                     "s2m": (tr.src_count[self.leaf].sum(), tr.src_count.sum()),
+                     "l2t": (tr.tgt_count[self.leaf].sum(), tr.tgt_count.sum())}
+        for l in range(2, lf + 1):
+            ilen = np.array([len(x) for x in tr.ilist[l]], dtype=np.float64)
+            self.work[("m2l", l)] = (ilen[self.level[l]].sum(), ilen.sum())
+            nb = len(tr.levels[l]["key"])
+            if l > 2:
+                self.work[("m2m", l)] = (len(self.level[l]), nb)
+                self.work[("l2l", l)] = (len(self.level[l]), nb)
+        # transfer tables of the sampled M2L boxes (plan time)
+        for l in range(2, lf + 1):
+            for a in self.level[l]:
+                for v in tr.vlist[l][a]:
+                    self.plan.table(l, v)
+
+    def time_once(self):
+        """Seconds of one extrapolated apply, and the per-stage estimates."""
+        p, tr, of = self.plan, self.plan.tree, self.ofmm
+        lf = tr.depth
+        R = self.q.shape[1]
+        qs = self.q[tr.src_perm]
+        zeros = {l: np.zeros((len(tr.levels[l]["key"]), R, p.levels[l].K), dtype=np.complex128)
+                 for l in range(2, lf + 1)}
+        est = {}
+
+        def clock(key, fn):
+            t0 = time.perf_counter()
+            fn()
+            dt = time.perf_counter() - t0
+            done, total = self.work[key]
+            est[key] = dt * (total / done) if done > 0 else 0.0
+
+        clock("near", lambda: of.p2p(p, qs, boxes=self.leaf))
+        if lf >= 2:
+            clock("s2m", lambda: of.s2m(p, qs, boxes=self.leaf))
+            for l in range(lf, 2, -1):
+                clock(("m2m", l), lambda l=l: of.m2m(p, zeros[l], l, boxes=self.level[l]))
+            for l in range(2, lf + 1):
+                clock(("m2l", l), lambda l=l: of.m2l(p, zeros[l], l, boxes=self.level[l]))
+            for l in range(2, lf):
+                clock(("l2l", l + 1), lambda l=l: of.l2l(p, zeros[l], zeros[l + 1], l, boxes=self.level[l + 1]))
+            clock("l2t", lambda: of.l2t(p, zeros[lf], R, boxes=self.leaf))
+        return float(sum(est.values())), est
+
+    def sample_text(self):
+        lf = self.plan.tree.depth
+        return (f"oracle float64 Fourier FMM at the same plan (L_f = {lf}), timed on {len(self.leaf)} seeded leaf "
+                f"boxes (near field, S2M, L2T) and {max(len(v) for v in self.level.values()) if self.level else 0} "
+                f"boxes per level (M2M, M2L, L2L), extrapolated per stage by pairs / points / boxes / list "
+                f"entries; plan and transfer tables excluded")
+
+
+def headline_points(n=None):
+    from paper_0911_4114_gb300 import workloads as wl
+    s, t = wl.points("ellipsoid2m", n=n)
+    q = wl.charges(len(s), 0, wl.rng(2, salt=1)).astype(np.complex64)
+    return s, t, q
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    from paper_0911_4114_gb300 import workloads as wl
-    s, t = wl.points("sphere262k")
-    q = wl.charges(len(s), 0, wl.rng(1, salt=1)).astype(np.complex64).astype(np.complex128)
-    for i in range(args.warmup):
-        time_oracle(s, t, q, 64.0, 200, 100 + i)
-    secs = [time_oracle(s, t, q, 64.0, ORACLE_TARGETS, 200 + i) for i in range(args.steps)]
-    value = ORACLE_TARGETS / float(np.mean(secs)) / 1e6
-    line = {"impl": "reference", "metric": "FMM apply Mpoints*RHS/s at stated rel. err; mixed vs FP64 on one GB300",
-            "value": value, "unit": "Mpoints*RHS/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(WORKLOAD, l2="n/a (host)"),
+    s, t, q = headline_points(args.points if args.points != 2097152 else None)
+    smp = OracleFmmSampler(s, t, q.astype(np.complex128), HEADLINE["kappa"], HEADLINE["eps"],
+                           leaf_boxes=4, level_boxes=1)
+    for _ in range(args.warmup):
+        smp.time_once()
+    secs = [smp.time_once()[0] for _ in range(args.steps)]
+    value = len(t) / float(np.mean(secs)) / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpoints*RHS/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(HEADLINE, points=len(t), l2="n/a (host)"),
             "cpu_baseline": {"value": value, "unit": "Mpoints*RHS/s", "cores": oracle_threads(), "kind": "oracle",
-                             "sample": f"float64 direct sum over all 262,144 sources for {ORACLE_TARGETS} seeded "
-                                       f"targets per step (exact; the FMM approximates it)"},
+                             "sample": smp.sample_text()},
             "e2e": {"value": value, "unit": "Mpoints*RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------------------
+# roofline arithmetic
+# ----------------------------------------------------------------------------------------
+ALU_NOTE = "152 SMs x 128 FP32 lanes x median SM clock under load"
+FP64_NOTE = "152 SMs x 2 FP64 FMA per clock (4 flops) x median SM clock under load"
+
+
 def count_launches(info):
+    """Kernel launches of one apply (permutes, near field, the far-field stages)."""
     lf = info["lf"]
     n = 3  # permute in, near field, permute out
     if lf >= 2:
@@ -166,13 +280,11 @@ def count_launches(info):
     return n
 
 
-ALU_NOTE = "152 SMs x 128 FP32 lanes x median SM clock under load"
-
-
-def stage_rooflines(info, stage_ms, n_src, n_tgt, fp32_peak, hbm):
+def stage_rooflines(info, stage_ms, n_src, n_tgt, fp32_peak, hbm, fp64_peak=None):
     """Roofline entry of every stage with a defined unit of work (plan summary `info`, live
     stage times in ms); FP32-pipe operations against fp32_peak (Gop/s) for arithmetic-bound
-    stages, algorithmic bytes against hbm (GB/s) for the re-quadratures."""
+    stages, float64 flops against fp64_peak (Gflop/s) for the float64 plane-wave tables,
+    algorithmic bytes against hbm (GB/s) for the re-quadratures."""
     levels = {int(l): v for l, v in info["levels"].items()}
     lev = levels.get(info["lf"], {})
     sample_bytes = {"fp32": 8.0, "df": 16.0, "fp64": 16.0}
@@ -201,6 +313,13 @@ def stage_rooflines(info, stage_ms, n_src, n_tgt, fp32_peak, hbm):
             units = float(lev["K"]) / 2 * (n_tgt if stage == "l2t" else n_src)
             return alu("k_l2t_df_warp" if stage == "l2t" else "k_s2m_df", 156.0 * units, ms,
                        "156 float32 ops per (point, antipodal sample pair) in double-float")
+        if stage in ("s2m", "l2t") and lev.get("precision") == "fp64" and info.get("leaf_tables") and fp64_peak:
+            # table-driven float64 plane waves: 4 FMA (8 flops) per (point, antipodal pair, RHS)
+            units = float(lev["K"]) / 2 * (n_tgt if stage == "l2t" else n_src) * info.get("nrhs", 1)
+            return dict(kernel="k_l2t_tab" if stage == "l2t" else "k_s2m_tab", bound="alu",
+                        achieved=8.0 * units / (ms * 1e-3) / 1e9, peak=fp64_peak, unit="Gflop/s",
+                        unit_work="8 float64 flops (4 FMA) per (point, antipodal sample pair, RHS)",
+                        peak_note=FP64_NOTE)
         if stage == "m2l" and levels and all(v["precision"] in m2l_ops for v in levels.values()):
             ops = sum(m2l_ops[v["precision"]] * v["ilist_total"] * v["K"] for v in levels.values())
             return alu("k_m2l", ops, ms, "4 (float32) or 48 (double-float) float32 ops per list entry and sample")
@@ -229,6 +348,114 @@ def stage_rooflines(info, stage_ms, n_src, n_tgt, fp32_peak, hbm):
     return out
 
 
+# ----------------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------------
+class Timer:
+    """Device-timed applies on one stream with an L2 flush before each."""
+
+    def __init__(self, dev, world):
+        import torch
+        self.torch = torch
+        self.dev = dev
+        self.world = world
+        self.flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        self.stream = torch.cuda.current_stream(dev)
+
+    def run(self, fn, steps, warmup):
+        torch = self.torch
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier(self.world)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            self.flush.fill_(1.0)
+            a.record(self.stream)
+            fn()
+            b.record(self.stream)
+        torch.cuda.synchronize()
+        barrier(self.world)
+        return allmax(float(np.mean([a.elapsed_time(b) for a, b in ev])), self.world)
+
+    def stages(self, plan, fn, reps):
+        plan.set_timing(True)
+        acc = {k: 0.0 for k in STAGES}
+        for _ in range(reps):
+            self.flush.fill_(1.0)
+            fn()
+            self.torch.cuda.synchronize()
+            for k, v in plan.info()["stage_ms"].items():
+                acc[k] += v / reps
+        plan.set_timing(False)
+        return acc
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def gpu_direct_reference(s, t_sub, q, kappa, dev):
+    """Float64 direct sum at a subset of targets by the library's float64 near-field kernel:
+    a one-box float64 plan (occupancy bound = all sources) has no far field."""
+    import torch
+    from paper_0911_4114_gb300 import FmmPlan
+    plan = FmmPlan(s, t_sub, kappa, 1e-6, precision="fp64", max_leaf=max(len(s), len(t_sub)))
+    assert plan.info()["lf"] < 2
+    out = plan.apply(torch.as_tensor(q.astype(np.complex128)).reshape(-1, 1).to(dev))
+    torch.cuda.synchronize()
+    return out[:, 0].cpu().numpy()
+
+
+def extras_run(timer, dev, steps):
+    """Device-timed extra workloads: the sphere, the 64-RHS cube and the 32-problem batch."""
+    import torch
+    from paper_0911_4114_gb300 import FmmBatch, FmmPlan, workloads as wl
+    out = {}
+    # 262,144 points on the unit sphere, kappa 64, eps 1e-6, mixed and float64
+    s, t = wl.points("sphere262k")
+    q = torch.as_tensor(wl.charges(len(s), 0, wl.rng(1, salt=1)).astype(np.complex64)).reshape(-1, 1).to(dev)
+    o = torch.empty((len(t), 1), dtype=torch.complex64, device=dev)
+    sph = {}
+    for prec in ("mixed", "fp64"):
+        p = FmmPlan(s, t, 64.0, 1e-6, precision=prec)
+        ms = timer.run(lambda: p.apply(q, out=o), max(3, steps // 2), 2)
+        sph[prec] = {"ms_per_step": ms, "value": len(t) / (ms * 1e-3) / 1e6}
+        if prec == "mixed":
+            sph["stage_ms"] = timer.stages(p, lambda: p.apply(q, out=o), 3)
+            sph["lf"] = p.info()["lf"]
+        del p
+    out["sphere262k"] = dict(sph, unit="Mpoints*RHS/s", kappa=64.0, eps=1e-6, charges="complex64")
+    # 524,288 points in the unit cube, 64 right-hand sides, kappa 40, eps 1e-5
+    cs, ct = wl.points("cube512k_rhs64")
+    cplan = FmmPlan(cs, ct, 40.0, 1e-5, precision="mixed", max_rhs=64)
+    cq = torch.as_tensor(wl.charges(len(cs), 64, wl.rng(3, salt=1)).astype(np.complex64)).to(dev)
+    cout = torch.empty((len(ct), 64), dtype=torch.complex64, device=dev)
+    cms = timer.run(lambda: cplan.apply(cq, out=cout), 2, 1)
+    ci = cplan.info()
+    out["cube512k_rhs64"] = {"ms_per_step": cms, "value": len(ct) * 64 / (cms * 1e-3) / 1e6,
+                             "unit": "Mpoints*RHS/s", "nrhs": 64, "kappa": 40.0, "eps": 1e-5, "lf": ci["lf"],
+                             "p2p_pairs": ci["p2p_pairs"],
+                             "stage_ms": timer.stages(cplan, lambda: cplan.apply(cq, out=cout), 1),
+                             "levels": {str(l): v["precision"] for l, v in ci["levels"].items()}}
+    del cplan, cq, cout
+    # 32 uneven cube problems, 4 RHS each, one graph launch per apply
+    g = wl.rng(5)
+    sizes = np.exp(g.uniform(np.log(8192), np.log(131072), 32)).astype(int)
+    kappas = g.uniform(10.0, 60.0, 32)
+    probs = [(wl.cube(int(n), g), float(k)) for n, k in zip(sizes, kappas)]
+    batch = FmmBatch([(x, x, k, 1e-5) for x, k in probs], precision="mixed", max_rhs=4)
+    qs = [torch.as_tensor(wl.charges(len(x), 4, g).astype(np.complex64)).to(dev) for x, _ in probs]
+    outs = [torch.empty((len(x), 4), dtype=torch.complex64, device=dev) for x, _ in probs]
+    bms = timer.run(lambda: batch.apply(qs, outs), max(3, steps // 2), 2)
+    npts = int(sum(len(x) for x, _ in probs))
+    out["batch32_rhs4"] = {"ms_per_step": bms, "value": npts * 4 / (bms * 1e-3) / 1e6, "unit": "Mpoints*RHS/s",
+                           "problems": 32, "points_total": npts, "nrhs": 4, "eps": 1e-5,
+                           "launch": "one cudaGraphLaunch per apply (hfmm_apply_batch replay)"}
+    del batch
+    return out
+
+
 def main():
     args = parse()
     rank, world = dist_setup(args.gpus)
@@ -236,137 +463,92 @@ def main():
         run_reference(args, rank, world)
         return
     import torch
-    from oracle import direct
-    from paper_0911_4114_gb300 import FmmPlan, workloads as wl
+    from paper_0911_4114_gb300 import FmmPlan
     local = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    s, t = wl.points("sphere262k", n=args.points)
-    kappa, eps = 64.0, 1e-6
-    q_host = wl.charges(len(s), 0, wl.rng(1, salt=1)).astype(np.complex64)
-    q = torch.as_tensor(q_host).to(dev)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    s, t, q_host = headline_points(args.points if args.points != 2097152 else None)
+    kappa, eps = HEADLINE["kappa"], HEADLINE["eps"]
+    nt = len(t)
+    timer = Timer(dev, world)
+    q64 = torch.as_tensor(q_host).reshape(-1, 1).to(dev)
+    q128 = q64.to(torch.complex128)
+    o64 = torch.empty((nt, 1), dtype=torch.complex64, device=dev)
+    o128 = torch.empty((nt, 1), dtype=torch.complex128, device=dev)
 
-    def timed(plan, steps, warmup):
-        out = torch.empty((len(t), 1), dtype=torch.complex64, device=dev)
-        q2 = q.reshape(-1, 1)
-        for _ in range(warmup):
-            plan.apply(q2, out=out)
-        torch.cuda.synchronize()
-        barrier(world)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        for a, b in ev:
-            flush.fill_(1.0)
-            a.record(stream)
-            plan.apply(q2, out=out)
-            b.record(stream)
-        torch.cuda.synchronize()
-        barrier(world)
-        ms = [a.elapsed_time(b) for a, b in ev]
-        return allmax(float(np.mean(ms)), world), out
+    t0 = time.perf_counter()
+    mp = FmmPlan(s, t, kappa, eps, precision="mixed")
+    plan_seconds = time.perf_counter() - t0
+    info = mp.info()
 
-    plans = {}
-    for precision in (("mixed",) if args.no_fp64 else ("mixed", "fp64")):
-        t0 = time.perf_counter()
-        plans[precision] = FmmPlan(s, t, kappa, eps, precision=precision)
-        plans[precision].plan_seconds = time.perf_counter() - t0
-
-    idx = np.sort(wl.rng(1, salt=2).choice(len(t), 1000, replace=False))
-    ref = direct.direct(s, t[idx], q_host.astype(np.complex128), kappa)
     results = {}
     with ClockSampler(local) as clk:
-        for precision, plan in plans.items():
-            ms, out = timed(plan, args.steps, args.warmup)
-            got = out[:, 0].cpu().numpy().astype(np.complex128)[idx]
-            results[precision] = dict(ms=ms, rel_err=float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+        results["mixed"] = timer.run(lambda: mp.apply(q64, out=o64), args.steps, args.warmup)
+        head_out = o64[:, 0].cpu().numpy().astype(np.complex128)
     clocks = clk.summary()
-
-    # per-stage device times of the mixed apply (library events on the apply stream)
-    mp = plans["mixed"]
-    mp.set_timing(True)
-    stage_ms = {k: 0.0 for k in ("permute_in", "near_field", "s2m", "m2m", "m2l", "l2l", "l2t", "permute_out")}
-    nst = max(3, args.steps // 2)
-    out = torch.empty((len(t), 1), dtype=torch.complex64, device=dev)
-    for _ in range(nst):
-        flush.fill_(1.0)
-        mp.apply(q.reshape(-1, 1), out=out)
-        for k, v in mp.info()["stage_ms"].items():
-            stage_ms[k] += v / nst
-    mp.set_timing(False)
-    info = mp.info()
+    stage_ms = timer.stages(mp, lambda: mp.apply(q64, out=o64), max(3, args.steps // 4))
 
     # end to end through the public API: pinned host in, host out
     qh = torch.as_tensor(q_host).reshape(-1, 1).pin_memory()
-    ph = torch.empty((len(t), 1), dtype=torch.complex64).pin_memory()
+    ph = torch.empty((nt, 1), dtype=torch.complex64).pin_memory()
     qd = torch.empty_like(qh, device=dev)
-    od = torch.empty((len(t), 1), dtype=torch.complex64, device=dev)
-    for _ in range(args.warmup):
-        qd.copy_(qh, non_blocking=True)
-        mp.apply(qd, out=od)
-        ph.copy_(od, non_blocking=True)
-    torch.cuda.synchronize()
-    barrier(world)
-    e2e_ms = []
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        qd.copy_(qh, non_blocking=True)
-        mp.apply(qd, out=od)
-        ph.copy_(od, non_blocking=True)
-        b.record(stream)
-        b.synchronize()
-        e2e_ms.append(a.elapsed_time(b))
-    e2e = allmax(float(np.mean(e2e_ms)), world)
 
-    # adjoint of the same plan, and the 64-RHS cube (tensor-core near field), device-timed
-    extras = None
-    if not args.no_extras and args.points == 262144:
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
-        wadj = torch.empty((len(s), 1), dtype=torch.complex64, device=dev)
-        mp.apply_adjoint(q.reshape(-1, 1), out=wadj)
-        for a, b in ev:
-            flush.fill_(1.0)
-            a.record(stream)
-            mp.apply_adjoint(q.reshape(-1, 1), out=wadj)
-            b.record(stream)
-        torch.cuda.synchronize()
-        adj_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
-        cs, ct = wl.points("cube512k_rhs64")
-        cplan = FmmPlan(cs, ct, 40.0, 1e-5, precision="mixed", max_rhs=64)
-        cq = torch.as_tensor(wl.charges(len(cs), 64, wl.rng(3, salt=1)).astype(np.complex64)).to(dev)
-        cout = torch.empty((len(ct), 64), dtype=torch.complex64, device=dev)
-        cplan.apply(cq, out=cout)
-        for a, b in ev[:2]:
-            a.record(stream)
-            cplan.apply(cq, out=cout)
-            b.record(stream)
-        torch.cuda.synchronize()
-        cms = float(np.mean([a.elapsed_time(b) for a, b in ev[:2]]))
-        cplan.set_timing(True)
-        cplan.apply(cq, out=cout)
-        torch.cuda.synchronize()
-        ci = cplan.info()
-        cplan.set_timing(False)
-        extras = {"adjoint": {"ms_per_step": adj_ms, "value": len(s) / (adj_ms * 1e-3) / 1e6,
-                              "unit": "Mpoints*RHS/s"},
-                  "cube512k_rhs64": {"ms_per_step": cms, "value": len(ct) * 64 / (cms * 1e-3) / 1e6,
-                                     "unit": "Mpoints*RHS/s", "nrhs": 64, "kappa": 40.0, "eps": 1e-5,
-                                     "lf": ci["lf"], "p2p_pairs": ci["p2p_pairs"],
-                                     "near_field": "tensor-core GEMM form (mma.sync 3xTF32)",
-                                     "pair_rhs_per_s": ci["p2p_pairs"] * 64 / (cms * 1e-3),
-                                     "stage_ms": ci["stage_ms"],
-                                     "levels": {str(l): v["precision"] for l, v in ci["levels"].items()}}}
-        del cplan, cq, cout
+    def e2e_step():
+        qd.copy_(qh, non_blocking=True)
+        mp.apply(qd, out=o64)
+        ph.copy_(o64, non_blocking=True)
+    e2e_ms = timer.run(e2e_step, args.steps, args.warmup)
 
-    # CPU oracle on this host (rank 0 only), bounded sample
+    # adjoint of the headline plan
+    adj_out = torch.empty((len(s), 1), dtype=torch.complex64, device=dev)
+    adj_ms = timer.run(lambda: mp.apply_adjoint(q64, out=adj_out), max(3, args.steps // 4), 1)
+    del mp
+
+    # accuracy: float64 direct sum on seeded targets
+    idx = np.sort(np.random.default_rng(20260102).choice(nt, min(REL_ERR_TARGETS, nt), replace=False))
+    ref = gpu_direct_reference(s, t[idx], q_host, kappa, dev)
+    errs = {"mixed": rel(head_out[idx], ref)}
+
+    fp64 = None
+    if not args.no_fp64:
+        p = FmmPlan(s, t, kappa, eps, precision="fp64")
+        ms = timer.run(lambda: p.apply(q64, out=o64), 2, 1)
+        errs["fp64"] = rel(o64[:, 0].cpu().numpy().astype(np.complex128)[idx], ref)
+        fp64 = {"value": nt / (ms * 1e-3) / 1e6, "ms_per_step": ms, "rel_err": errs["fp64"], "lf": p.info()["lf"],
+                "stage_ms": timer.stages(p, lambda: p.apply(q64, out=o64), 1)}
+        del p
+
+    tight = None
+    if not args.no_tight:
+        tight = {"eps": TIGHT_EPS, "charges": "complex128 (the complex64 values)"}
+        for prec in (("mixed",) if args.no_fp64 else ("mixed", "fp64")):
+            p = FmmPlan(s, t, kappa, TIGHT_EPS, precision=prec)
+            ms = timer.run(lambda: p.apply(q128, out=o128), 1 if prec == "fp64" else 2, 1)
+            got = o128[:, 0].cpu().numpy()[idx]
+            tight[prec] = {"value": nt / (ms * 1e-3) / 1e6, "ms_per_step": ms, "rel_err": rel(got, ref),
+                           "lf": p.info()["lf"]}
+            if prec == "mixed":
+                tight[prec]["stage_ms"] = timer.stages(p, lambda: p.apply(q128, out=o128), 1)
+            del p
+
+    extras = {"adjoint": {"ms_per_step": adj_ms, "value": len(s) / (adj_ms * 1e-3) / 1e6,
+                          "unit": "Mpoints*RHS/s", "workload": "ellipsoid2m, eps 1e-4, mixed"}}
+    if not args.no_extras and args.points == 2097152:
+        extras.update(extras_run(timer, dev, args.steps))
+
+    # CPU oracle on this host (rank 0 only): FMM at the same plan on a sample, direct-sum sample
     cpu = None
     if rank == 0 and world == 1 and not args.skip_oracle:
-        secs = time_oracle(s, t, q_host.astype(np.complex128), kappa, ORACLE_TARGETS, 300)
-        cpu = {"value": ORACLE_TARGETS / secs / 1e6, "unit": "Mpoints*RHS/s", "cores": oracle_threads(),
-               "kind": "oracle", "sample": f"float64 direct sum over all 262,144 sources for {ORACLE_TARGETS} "
-                                           f"seeded targets ({secs:.1f} s)"}
+        oidx, ovals, osecs = oracle_direct_sample(s, t, q_host.astype(np.complex128), kappa,
+                                                  ORACLE_DIRECT_TARGETS, 20260103)
+        errs["mixed_vs_oracle_direct"] = rel(head_out[oidx], ovals)
+        smp = OracleFmmSampler(s, t, q_host.astype(np.complex128), kappa, eps)
+        fmm_secs, parts = smp.time_once()
+        cpu = {"value": nt / fmm_secs / 1e6, "unit": "Mpoints*RHS/s", "cores": oracle_threads(), "kind": "oracle",
+               "sample": smp.sample_text(), "seconds_per_apply_extrapolated": fmm_secs,
+               "direct_sum": {"value": ORACLE_DIRECT_TARGETS / osecs / 1e6, "unit": "Mpoints*RHS/s",
+                              "sample": f"oracle float64 direct sum over all {len(s):,} sources for "
+                                        f"{ORACLE_DIRECT_TARGETS} seeded targets ({osecs:.1f} s)"}}
 
     # rooflines per stage; the top-level entry is the dominant stage's
     peaks = {}
@@ -376,39 +558,36 @@ def main():
         pass
     sm_clock = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * sm_clock * 1e6 / 1e9          # FP32-pipe ops/s (Gop/s)
+    fp64_peak = 152 * 4 * sm_clock * 1e6 / 1e9            # float64 flops/s (Gflop/s)
     hbm = peaks.get("hbm_gbs", 6800.0)
-    roof_stages = stage_rooflines(info, stage_ms, len(s), len(t), fp32_peak, hbm)
+    info_r = dict(info, nrhs=1)
+    roof_stages = stage_rooflines(info_r, stage_ms, len(s), nt, fp32_peak, hbm, fp64_peak)
     stage = max(stage_ms, key=stage_ms.get)
     roof = dict(roof_stages.get(stage) or {"kernel": stage, "bound": None, "achieved": None, "peak": None,
                                           "unit": None, "frac": None, "stage_ms": stage_ms[stage]})
-    # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
-    # this workload at full size (profiles/sphere262k_launch_list.md); a kernel changed since its
-    # capture has no entry
-    traffic = {"k_p2p_mixed_sym_warp": 25.35e6}
-    roof["traffic"] = traffic.get(roof.get("kernel")) if len(t) == 262144 else None
+    # DRAM bytes per launch come from an ncu capture of the current build; none is read here
+    roof["traffic"] = None
     roof["peak_source"] = "of measured" if peaks else "of fallback"
 
-    nt = len(t)
-    _, value = replica_rate(results["mixed"]["ms"], nt, world)
-    fp64_value = replica_rate(results["fp64"]["ms"], nt, world)[1] if "fp64" in results else None
-    _, e2e_value = replica_rate(e2e, nt, world)
-    line = {"metric": "FMM apply Mpoints*RHS/s at stated rel. err; mixed vs FP64 on one GB300",
-            "value": value, "unit": "Mpoints*RHS/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": results["mixed"]["ms"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": dict(WORKLOAD, points=len(t), parallelism="replicas" if world > 1 else "single",
+    _, value = replica_rate(results["mixed"], nt, world)
+    _, e2e_value = replica_rate(e2e_ms, nt, world)
+    line = {"metric": METRIC, "value": value, "unit": "Mpoints*RHS/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": results["mixed"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+df+f64", "data": "synthetic",
+            "config": dict(HEADLINE, points=nt, parallelism="replicas" if world > 1 else "single",
                            l2="flushed before every timed apply (512 MiB write)",
                            lf=info["lf"], levels={str(l): v for l, v in info["levels"].items()},
                            p2p_pairs=info["p2p_pairs"]),
-            "rel_err": results["mixed"]["rel_err"],
-            "fp64_path": ({"value": fp64_value,
-                           "ms_per_step": results["fp64"]["ms"], "rel_err": results["fp64"]["rel_err"],
-                           "lf": plans["fp64"].info()["lf"]} if "fp64" in results else None),
-            "stage_ms": stage_ms, "plan_seconds": plans["mixed"].plan_seconds,
+            "rel_err": errs["mixed"],
+            "rel_err_ref": f"float64 direct sum at {len(idx)} seeded targets (library float64 kernel); "
+                           f"mixed_vs_oracle_direct: oracle direct sum at {ORACLE_DIRECT_TARGETS} targets",
+            "rel_errs": errs, "fp64_path": fp64, "tight": tight,
+            "stage_ms": stage_ms, "plan_seconds": plan_seconds,
             "e2e": {"value": e2e_value, "unit": "Mpoints*RHS/s",
                     "h2d_bytes_per_step": int(qh.numel() * 8), "d2h_bytes_per_step": int(ph.numel() * 8)},
-            "roofline": roof, "roofline_stages": {k: {kk: v[kk] for kk in ("kernel", "bound", "achieved", "unit", "frac")}
-                                                  for k, v in roof_stages.items()},
+            "roofline": roof,
+            "roofline_stages": {k: {kk: v[kk] for kk in ("kernel", "bound", "achieved", "unit", "frac")}
+                                for k, v in roof_stages.items()},
             "cpu_baseline": cpu, "gpu_launches": count_launches(info) * args.steps,
             "clocks": clocks, "extras": extras}
     if rank == 0:

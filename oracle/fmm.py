@@ -116,15 +116,20 @@ class Plan:
         return self._tables[key]
 
 
-def s2m(plan, qs):
-    """Leaf signatures M[b, r, k]."""
+def _boxes(boxes, n):
+    """All n boxes, or the given subset (used to time the oracle on a sample of boxes)."""
+    return range(n) if boxes is None else [int(b) for b in boxes]
+
+
+def s2m(plan, qs, boxes=None):
+    """Leaf signatures M[b, r, k] (boxes: optional subset; the others stay zero)."""
     t = plan.tree
     lf = t.depth
     quad = plan.levels[lf].quad
     lev = t.levels[lf]
     ys = plan.sources[t.src_perm]
     out = np.zeros((len(lev['key']), qs.shape[1], quad.K), dtype=np.complex128)
-    for b in range(len(lev['key'])):
+    for b in _boxes(boxes, len(lev['key'])):
         s0, sc = t.src_start[b], t.src_count[b]
         if sc == 0:
             continue
@@ -134,50 +139,53 @@ def s2m(plan, qs):
     return out
 
 
-def m2m(plan, mchild, l):
-    """Level l signatures -> level l-1 signatures."""
+def m2m(plan, mchild, l, boxes=None):
+    """Level l signatures -> level l-1 signatures (boxes: optional subset of children)."""
     t = plan.tree
     qa, qb = plan.levels[l].quad, plan.levels[l - 1].quad
     child, par = t.levels[l], t.levels[l - 1]
-    up = qd.requadrature(mchild, qa, qb)                   # [nb, R, K_{l-1}]
+    kids = list(_boxes(boxes, len(child['key'])))
+    up = qd.requadrature(mchild[kids], qa, qb)             # [nb, R, K_{l-1}]
     out = np.zeros((len(par['key']),) + up.shape[1:], dtype=np.complex128)
-    for b in range(len(child['key'])):
+    for i, b in enumerate(kids):
         p = child['parent'][b]
         d = child['center'][b] - par['center'][p]
-        out[p] += up[b] * np.exp(1j * plan.kappa * (qb.shat @ d))
+        out[p] += up[i] * np.exp(1j * plan.kappa * (qb.shat @ d))
     return out
 
 
-def m2l(plan, mlev, l):
+def m2l(plan, mlev, l, boxes=None):
     t = plan.tree
     out = np.zeros_like(mlev)
-    for a in range(len(t.levels[l]['key'])):
+    for a in _boxes(boxes, len(t.levels[l]['key'])):
         for b, v in zip(t.ilist[l][a], t.vlist[l][a]):
             out[a] += plan.table(l, v) * mlev[b]
     return out
 
 
-def l2l(plan, lpar, ichild, l):
-    """Level l locals -> level l+1 locals (plus that level's incoming I)."""
+def l2l(plan, lpar, ichild, l, boxes=None):
+    """Level l locals -> level l+1 locals (plus that level's incoming I); boxes: optional
+    subset of children (the result then holds those children only, in that order)."""
     t = plan.tree
     qa, qb = plan.levels[l].quad, plan.levels[l + 1].quad
     child, par = t.levels[l + 1], t.levels[l]
-    shifted = np.zeros((len(child['key']),) + lpar.shape[1:], dtype=np.complex128)
-    for c in range(len(child['key'])):
+    kids = list(_boxes(boxes, len(child['key'])))
+    shifted = np.zeros((len(kids),) + lpar.shape[1:], dtype=np.complex128)
+    for i, c in enumerate(kids):
         p = child['parent'][c]
         d = par['center'][p] - child['center'][c]
-        shifted[c] = lpar[p] * np.exp(1j * plan.kappa * (qa.shat @ d))
-    return qd.requadrature(shifted, qa, qb) + ichild
+        shifted[i] = lpar[p] * np.exp(1j * plan.kappa * (qa.shat @ d))
+    return qd.requadrature(shifted, qa, qb) + ichild[kids]
 
 
-def l2t(plan, lleaf, nrhs):
+def l2t(plan, lleaf, nrhs, boxes=None):
     t = plan.tree
     lf = t.depth
     quad = plan.levels[lf].quad
     lev = t.levels[lf]
     xs = plan.targets[t.tgt_perm]
     out = np.zeros((xs.shape[0], nrhs), dtype=np.complex128)
-    for b in range(len(lev['key'])):
+    for b in _boxes(boxes, len(lev['key'])):
         t0, tc = t.tgt_start[b], t.tgt_count[b]
         if tc == 0:
             continue
@@ -187,13 +195,13 @@ def l2t(plan, lleaf, nrhs):
     return out
 
 
-def p2p(plan, qs):
+def p2p(plan, qs, boxes=None):
     t = plan.tree
     lf = t.depth
     ys = plan.sources[t.src_perm]
     xs = plan.targets[t.tgt_perm]
     out = np.zeros((xs.shape[0], qs.shape[1]), dtype=np.complex128)
-    for b in range(len(t.levels[lf]['key'])):
+    for b in _boxes(boxes, len(t.levels[lf]['key'])):
         t0, tc = t.tgt_start[b], t.tgt_count[b]
         if tc == 0:
             continue
