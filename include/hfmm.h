@@ -44,7 +44,7 @@ typedef enum {
     HFMM_ERR_ARG = 1,      /* invalid argument (sizes, NaN, kappa <= 0, eps outside (0, 0.1], ...) */
     HFMM_ERR_CUDA = 2,     /* a CUDA call failed (message in hfmm_last_error) */
     HFMM_ERR_NOMEM = 3,    /* host or device allocation failed at plan time */
-    HFMM_ERR_UNSTABLE = 4, /* reserved: eps unreachable in the requested precision */
+    HFMM_ERR_UNSTABLE = 4, /* no far-field level at this eps and precision (HFMM_FLAG_REQUIRE_FAR) */
     HFMM_ERR_TIMEOUT = 5,  /* reserved: device watchdog */
     HFMM_ERR_STATE = 6     /* call not valid for this plan (e.g. apply on a host-only plan) */
 } hfmm_status;
@@ -84,7 +84,22 @@ typedef struct {
     int max_rhs;
     /* CUDA device ordinal (default 0); -1 builds a host-only plan (queries only, no apply) */
     int device;
+    /* bit flags, HFMM_FLAG_* below (default 0) */
+    int flags;
+    /* device bytes the plan may spend on the plane-wave tables of a float64 leaf level
+     * (E[j][p] = exp(i kappa s_p . (x_j - c_b)) for every point and antipodal sample pair,
+     * 16 bytes each, evaluated once at plan time; S2M and L2T then read them instead of
+     * evaluating float64 sincos): -1 = up to half of the device memory free at plan time
+     * (default), 0 = never, > 0 = at most this many bytes.  Levels in float32 or
+     * double-float never use tables. */
+    int64_t leaf_table_bytes;
 } hfmm_options;
+
+/* hfmm_options.flags: fail with HFMM_ERR_UNSTABLE instead of planning a pure near field
+ * (an O(N M) direct sum) when no level can carry a far field -- kappa a_2 < 6, the
+ * round-off rule rejects level 2 in every allowed precision and alpha, or the occupancy
+ * depth is below 2. */
+#define HFMM_FLAG_REQUIRE_FAR 1
 
 typedef struct {
     int64_t ns, nt;
@@ -114,6 +129,9 @@ typedef struct {
     /* 1 when sources = targets and the near field evaluates each pair of distinct
      * neighbouring boxes once for both directions (float32 near field, one RHS) */
     int near_symmetric;
+    /* 1 when S2M / L2T of the (float64) leaf level read plane-wave tables built at plan time */
+    int leaf_tables;
+    int64_t leaf_table_bytes;   /* device bytes of those tables (0 without) */
 } hfmm_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -127,7 +145,8 @@ void hfmm_default_options(hfmm_options* opt);
  * (Algorithm Nphi) and the T^{s,LL} tables (Algorithm BMTF, 34 computed, reflected to
  * 316), copies the points, and (device >= 0) uploads everything and allocates the apply
  * workspace on the device.  On success *out owns all of it; release with hfmm_destroy.
- * Errors: HFMM_ERR_ARG, HFMM_ERR_NOMEM, HFMM_ERR_CUDA. */
+ * Errors: HFMM_ERR_ARG, HFMM_ERR_NOMEM, HFMM_ERR_CUDA, HFMM_ERR_UNSTABLE (only with
+ * HFMM_FLAG_REQUIRE_FAR: no level carries a far field). */
 hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, int64_t nt,
                       double kappa, double eps, const hfmm_options* opt, hfmm_plan_t* out);
 

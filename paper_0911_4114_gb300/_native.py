@@ -15,6 +15,7 @@ STAGES = ("permute_in", "near_field", "s2m", "m2m", "m2l", "l2l", "l2t", "permut
 
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_UNSTABLE, ERR_TIMEOUT, ERR_STATE = range(7)
 C64, C128 = 0, 1
+FLAG_REQUIRE_FAR = 1
 PREC_FP64, PREC_MIXED = 0, 1
 
 GET = dict(BOX_IDX=0, BOX_PARENT=1, ILIST_OFF=2, ILIST_IDX=3, ILIST_V=4, NLIST_OFF=5, NLIST_IDX=6,
@@ -30,7 +31,7 @@ class Options(ctypes.Structure):
     _fields_ = [("alpha_ladder", ctypes.c_double * 4), ("eps_scale", ctypes.c_double),
                 ("max_leaf", ctypes.c_int), ("depth", ctypes.c_int), ("has_root", ctypes.c_int),
                 ("root", ctypes.c_double * 4), ("precision", ctypes.c_int), ("max_rhs", ctypes.c_int),
-                ("device", ctypes.c_int)]
+                ("device", ctypes.c_int), ("flags", ctypes.c_int), ("leaf_table_bytes", ctypes.c_int64)]
 
 
 class Problem(ctypes.Structure):
@@ -49,7 +50,8 @@ class Info(ctypes.Structure):
                 ("level_ilist_total", ctypes.c_int * MAX_LEVELS),
                 ("stage_ms", ctypes.c_double * N_STAGES), ("workspace_bytes", ctypes.c_int64),
                 ("near_precision", ctypes.c_int), ("p2p_self_pairs", ctypes.c_int64),
-                ("near_symmetric", ctypes.c_int)]
+                ("near_symmetric", ctypes.c_int), ("leaf_tables", ctypes.c_int),
+                ("leaf_table_bytes", ctypes.c_int64)]
 
 
 _lib = None

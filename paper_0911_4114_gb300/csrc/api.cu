@@ -104,6 +104,11 @@ struct hfmm_plan_s {
     void *tw64 = nullptr, *tw32 = nullptr, *twdf = nullptr;
     int* twoff = nullptr;
     cdf* cis_tab = nullptr;     // exp(2 pi i j / 1024) as double-float pairs
+    // plane-wave tables of a float64 leaf level: [sorted point][antipodal pair] (sources, and
+    // targets unless the two point sets are the same); null when not built
+    int64_t tab_budget = -1;
+    cxd *tab_s = nullptr, *tab_t = nullptr;
+    int64_t tab_bytes = 0;
     int64_t workspace = 0;
     bool timing = false;
     cudaEvent_t ev[HFMM_N_STAGES + 1] = {};
@@ -291,6 +296,44 @@ Requad make_requad(const Quadrature& a, const Quadrature& b, int nbox_seq, int r
     r.ga_elems = (int64_t)nbox_seq * rmax * (a.ntheta / 2 + 1) * big;
     r.gb_elems = (int64_t)nbox_seq * rmax * (b.ntheta / 2 + 1) * big;
     return r;
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// Plane-wave tables of a float64 leaf level (see k_pw_table), when they fit the budget.
+hfmm_status build_leaf_tables(hfmm_plan_s* P) {
+    const HostPlan& hp = P->hp;
+    const int lf = hp.lf;
+    if (lf < 2 || P->lev[lf].prec != kFP64 || P->tab_budget == 0) return HFMM_OK;
+    const DevLevel& d = P->lev[lf];
+    const int64_t npair = d.qv.npair;
+    const int64_t rows = hp.ns + (P->sym ? 0 : hp.nt);
+    const int64_t bytes = rows * npair * (int64_t)sizeof(cxd);
+    int64_t budget = P->tab_budget;
+    if (budget < 0) {
+        size_t fr = 0, tot = 0;
+        CK(cudaMemGetInfo(&fr, &tot));
+        budget = (int64_t)(fr / 2);
+    }
+    if (bytes > budget) return HFMM_OK;
+    const double kt = hp.kappa / (2.0 * 3.14159265358979323846);
+    TRY(dalloc(P, &P->tab_s, (size_t)hp.ns * npair));
+    if (P->nsunits > 0)
+        k_pw_table<<<dim3(P->nsunits, nblk(npair, kTabThreads)), kTabThreads>>>(P->sunits, d.bv, d.qv, P->sstart,
+                                                                               P->scount, P->sx, P->sy, P->sz, kt,
+                                                                               P->tab_s);
+    if (P->sym) {
+        P->tab_t = P->tab_s;
+    } else {
+        TRY(dalloc(P, &P->tab_t, (size_t)hp.nt * npair));
+        if (P->ntunits > 0)
+            k_pw_table<<<dim3(P->ntunits, nblk(npair, kTabThreads)), kTabThreads>>>(
+                P->tunits, d.bv, d.qv, P->tstart, P->tcount, P->tx, P->ty, P->tz, kt, P->tab_t);
+    }
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    P->tab_bytes = bytes;
+    return HFMM_OK;
 }
 
 hfmm_status upload_plan(hfmm_plan_s* P) {
@@ -481,6 +524,7 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
         }
         TRY(upload(P, &P->cis_tab, tab));
     }
+    TRY(build_leaf_tables(P));
     for (int i = 0; i <= HFMM_N_STAGES; ++i) CK(cudaEventCreate(&P->ev[i]));
     return HFMM_OK;
 }
@@ -488,7 +532,6 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
 // ---------------------------------------------------------------------------
 // apply helpers
 // ---------------------------------------------------------------------------
-inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // opt a kernel into more than 48 KiB of dynamic shared memory when a launch needs it
 template <typename K>
@@ -681,6 +724,20 @@ void launch_s2m(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false)
     const double* wk = transposed ? d.qv.w : nullptr;
     const double kt = P->hp.kappa / (2.0 * 3.14159265358979323846);
     dim3 grid(d.nbox, nblk(d.qv.npair, kS2MThreads));
+    if (std::is_same<T, double>::value && P->tab_s) {
+        // float64 leaf with plane-wave tables: S2M reads the sources' table as stored, the
+        // transposed L2T the targets' table conjugated
+        const cxd* E = transposed ? P->tab_t : P->tab_s;
+        const dim3 g(d.nbox, nblk(d.qv.npair, kTabThreads));
+        if (transposed) {
+            if (R == 1) k_s2m_tab<1, true><<<g, kTabThreads, 0, st>>>(d.qv, start, count, E, charges, R, (cxd*)out, wk);
+            else k_s2m_tab<4, true><<<g, kTabThreads, 0, st>>>(d.qv, start, count, E, charges, R, (cxd*)out, wk);
+        } else {
+            if (R == 1) k_s2m_tab<1, false><<<g, kTabThreads, 0, st>>>(d.qv, start, count, E, charges, R, (cxd*)out, wk);
+            else k_s2m_tab<4, false><<<g, kTabThreads, 0, st>>>(d.qv, start, count, E, charges, R, (cxd*)out, wk);
+        }
+        return;
+    }
     if (std::is_same<T, double>::value && use_df(P, lf)) {
         if (R == 1)
             k_s2m_df<1><<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt,
@@ -715,6 +772,25 @@ void launch_l2t(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false)
     const double* wk = transposed ? nullptr : d.qv.w;
     const double kt = P->hp.kappa / (2.0 * 3.14159265358979323846);
     const dim3 grid(d.nbox, nblk(transposed ? P->max_src_leaf : P->max_tgt_leaf, kL2TThreads));
+    if (std::is_same<T, double>::value && P->tab_s) {
+        // float64 leaf with plane-wave tables: L2T reads the targets' table conjugated, the
+        // transposed S2M the sources' table as stored
+        const cxd* E = transposed ? P->tab_s : P->tab_t;
+        const int2* units = transposed ? P->sunits : P->tunits;
+        const int nu = transposed ? P->nsunits : P->ntunits;
+        if (nu > 0) {
+            const unsigned th = 32 * kL2TabWarps;
+            const cxd* Lin = (const cxd*)in;
+            if (transposed) {
+                if (R == 1) k_l2t_tab<1, false><<<nu, th, 0, st>>>(units, d.qv, start, count, E, Lin, R, out, wk);
+                else k_l2t_tab<4, false><<<nu, th, 0, st>>>(units, d.qv, start, count, E, Lin, R, out, wk);
+            } else {
+                if (R == 1) k_l2t_tab<1, true><<<nu, th, 0, st>>>(units, d.qv, start, count, E, Lin, R, out, wk);
+                else k_l2t_tab<4, true><<<nu, th, 0, st>>>(units, d.qv, start, count, E, Lin, R, out, wk);
+            }
+        }
+        return;
+    }
     if (std::is_same<T, double>::value && use_df(P, lf)) {
         const int2* units = transposed ? P->sunits : P->tunits;
         const int nu = transposed ? P->nsunits : P->ntunits;
@@ -784,6 +860,8 @@ void hfmm_default_options(hfmm_options* opt) {
     opt->precision = HFMM_PREC_FP64;
     opt->max_rhs = 1;
     opt->device = 0;
+    opt->flags = 0;
+    opt->leaf_table_bytes = -1;
 }
 
 const char* hfmm_last_error(void) { return g_err.c_str(); }
@@ -806,6 +884,8 @@ hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, 
     if (!(opt.eps_scale > 0.0 && opt.eps_scale <= 1.0)) return fail(HFMM_ERR_ARG, "eps_scale must be in (0, 1]");
     if (opt.precision != HFMM_PREC_FP64 && opt.precision != HFMM_PREC_MIXED)
         return fail(HFMM_ERR_ARG, "unknown precision policy");
+    if (opt.flags & ~HFMM_FLAG_REQUIRE_FAR) return fail(HFMM_ERR_ARG, "unknown flag bits");
+    if (opt.leaf_table_bytes < -1) return fail(HFMM_ERR_ARG, "leaf_table_bytes must be -1, 0 or positive");
     std::vector<double> alphas;
     // default ladder: (0.8, 0.6), or (0.9, 0.8) below eps = 1e-7, where the few terms that
     // l(0.8) keeps beyond k|r| of a corner pair no longer reach eps
@@ -875,8 +955,20 @@ hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, 
                 return fail(HFMM_ERR_ARG, "N_phi above 1024 is not supported");
             }
     }
+    if ((opt.flags & HFMM_FLAG_REQUIRE_FAR) && hp.lf < 2) {
+        std::string why;
+        if (hp.occ_depth < 2)
+            why = "the occupancy depth is " + std::to_string(hp.occ_depth) + " (fewer than 2 levels)";
+        else if (kappa * hp.side / 4.0 < 6.0)
+            why = "level 2 boxes are below a wavelength (kappa a_2 = " + std::to_string(kappa * hp.side / 4.0) + " < 6)";
+        else
+            why = "the round-off rule rejects level 2 for every alpha in every allowed precision";
+        delete P;
+        return fail(HFMM_ERR_UNSTABLE, "no far-field level: " + why);
+    }
     P->rmax = opt.max_rhs;
     P->device = opt.device;
+    P->tab_budget = opt.leaf_table_bytes;
     if (opt.precision == HFMM_PREC_MIXED) P->near_prec = eps >= 1e-6 ? kFP32 : (eps >= 1e-11 ? kDF : kFP64);
     P->sym = ns == nt && (sources == targets || std::memcmp(sources, targets, sizeof(double) * 3 * ns) == 0) &&
              P->hp.src_perm == P->hp.tgt_perm && P->hp.src_count == P->hp.tgt_count;
@@ -1177,6 +1269,8 @@ hfmm_status hfmm_query(hfmm_plan_t P, hfmm_info* info) {
     info->p2p_self_pairs = hp.p2p_self_pairs;
     info->near_symmetric = (P->sym && P->near_prec == kFP32) ? 1 : 0;
     info->near_precision = P->near_prec == kFP32 ? HFMM_LEVEL_FP32 : (P->near_prec == kDF ? HFMM_LEVEL_DF : HFMM_LEVEL_FP64);
+    info->leaf_tables = P->tab_s != nullptr;
+    info->leaf_table_bytes = P->tab_bytes;
     if (P->ev_recorded) {
         if (cudaEventSynchronize(P->ev[HFMM_N_STAGES]) != cudaSuccess)
             return fail(HFMM_ERR_CUDA, "event synchronize failed");

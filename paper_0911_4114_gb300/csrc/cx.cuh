@@ -49,4 +49,12 @@ __host__ __device__ __forceinline__ R rval(double v) { return (R)v; }
 using cxd = cx<double>;
 using cxf = cx<float>;
 
+#ifdef __CUDACC__
+// read-only (non-coherent cache) load of a float64 complex value
+__device__ __forceinline__ cxd ldg_cx(const cxd* p) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    return mk<double>(v.x, v.y);
+}
+#endif
+
 }  // namespace hfmm

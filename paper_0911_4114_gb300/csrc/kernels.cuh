@@ -320,6 +320,153 @@ __global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstar
 }
 
 // ---------------------------------------------------------------------------
+// Plane-wave tables of a float64 leaf level.  GB300 executes float64 at 1/64 of the float32
+// rate: a float64 plane wave exp(i kappa s_k . (p - c_b)) (phase, reduction, sincospi) costs
+// tens of float64 operations, the sums that use it 4 FMA per right-hand side.  The plan
+// therefore evaluates every plane wave of the leaf level once into HBM,
+//     E[j][p] = exp(i kappa s_k . (p_j - c_b)),  k = pair[p].x,
+// for every sorted point j (leaf box b) and antipodal pair p, with the same arithmetic as
+// k_s2m (phase in turns, reduced, sincospi), and S2M / L2T and their transposes read it:
+// one 16-byte load and 4 FMA per (point, pair, RHS).  The plane wave of s_k' = -s_k is the
+// conjugate, and the opposite offset (c_b - p_j) conjugates too.
+// ---------------------------------------------------------------------------
+constexpr int kTabThreads = 128;
+
+// one block per (leaf box, 32-point chunk) x 128 pairs; E row-major [point][pair]
+__global__ void __launch_bounds__(kTabThreads) k_pw_table(
+    const int2* __restrict__ units, BoxView bx, QuadView qv, const int32_t* __restrict__ pstart,
+    const int32_t* __restrict__ pcount, const double* __restrict__ px, const double* __restrict__ py,
+    const double* __restrict__ pz, double kappa_turns, cxd* __restrict__ E) {
+    const int b = units[blockIdx.x].x, c0 = units[blockIdx.x].y;
+    const int64_t p = blockIdx.y * (int64_t)kTabThreads + threadIdx.x;
+    if (p >= qv.npair) return;
+    const int k = qv.pair[p].x;
+    const double s[3] = {qv.shat[3 * k], qv.shat[3 * k + 1], qv.shat[3 * k + 2]};
+    const double cxx = bx.center[3 * b], cyy = bx.center[3 * b + 1], czz = bx.center[3 * b + 2];
+    const int n = min(32, pcount[b] - c0);
+    for (int jj = 0; jj < n; ++jj) {
+        const int64_t j = pstart[b] + c0 + jj;
+        const double t = turns(kappa_turns, s, px[j] - cxx, py[j] - cyy, pz[j] - czz);
+        E[j * qv.npair + p] = plane_wave<double>(t);
+    }
+}
+
+// points -> signature from the table (S2M: sources, E as stored; transposed L2T: targets,
+// conjugated, weighted).  Thread per (box, antipodal pair); U = sum q C, V = sum q S over the
+// box's points, M(k) = U + iV, M(k') = U - iV (as k_s2m).  kRC right-hand sides per pass.
+template <int kRC, bool kConj>
+__global__ void __launch_bounds__(kTabThreads) k_s2m_tab(
+    QuadView qv, const int32_t* __restrict__ sstart, const int32_t* __restrict__ scount,
+    const cxd* __restrict__ E, const cxd* __restrict__ qs, int R_, cxd* __restrict__ M,
+    const double* __restrict__ wk) {
+    const int b = blockIdx.x;
+    const int64_t p = blockIdx.y * (int64_t)kTabThreads + threadIdx.x;
+    if (p >= qv.npair) return;
+    const int2 kk2 = qv.pair[p];
+    const int s0 = sstart[b], sc = scount[b];
+    const cxd* Ep = E + (int64_t)s0 * qv.npair + p;
+    for (int r0 = 0; r0 < R_; r0 += kRC) {
+        const int rn = kRC == 1 ? 1 : min(kRC, R_ - r0);
+        cxd U[kRC], V[kRC];
+        for (int r = 0; r < kRC; ++r) U[r] = V[r] = mk<double>(0, 0);
+        for (int jj = 0; jj < sc; ++jj) {
+            cxd e = ldg_cx(Ep + (int64_t)jj * qv.npair);
+            if (kConj) e.y = -e.y;
+            const cxd* qj = qs + (int64_t)(s0 + jj) * R_ + r0;
+            for (int r = 0; r < rn; ++r) {
+                const cxd q = ldg_cx(qj + r);
+                U[r] = U[r] + e.x * q;
+                V[r] = V[r] + e.y * q;
+            }
+        }
+        for (int r = 0; r < rn; ++r) {
+            cxd a = mk<double>(U[r].x - V[r].y, U[r].y + V[r].x), c = mk<double>(U[r].x + V[r].y, U[r].y - V[r].x);
+            if (wk) {
+                a = wk[kk2.x] * a;
+                c = wk[kk2.y] * c;
+            }
+            M[((int64_t)b * R_ + r0 + r) * qv.K + kk2.x] = a;
+            M[((int64_t)b * R_ + r0 + r) * qv.K + kk2.y] = c;
+        }
+    }
+}
+
+// signature -> points from the table (L2T: targets, conjugated, weighted; transposed S2M:
+// sources, E as stored).  One block per (leaf box, 32-point chunk); warp w takes points
+// w, w + 8, w + 16, w + 24 of the chunk, its lanes stride the antipodal pairs (coalesced
+// table rows); P = A + B, Q = A - B (A = w_k L(k), B = w_k' L(k')) are staged in shared
+// memory 128 pairs at a time; A E + B conj(E) = (P.x C - Q.y S) + i (P.y C + Q.x S).
+constexpr int kL2TabWarps = 8;
+constexpr int kL2TabChunk = 128;
+
+template <int kRC, bool kConj>
+__global__ void __launch_bounds__(32 * kL2TabWarps) k_l2t_tab(
+    const int2* __restrict__ units, QuadView qv, const int32_t* __restrict__ pstart,
+    const int32_t* __restrict__ pcount, const cxd* __restrict__ E, const cxd* __restrict__ L, int R_,
+    cxd* __restrict__ out, const double* __restrict__ wk) {
+    constexpr int kPts = 32 / kL2TabWarps;
+    __shared__ cxd shp[kL2TabChunk * kRC], shq[kL2TabChunk * kRC];
+    const int b = units[blockIdx.x].x, c0 = units[blockIdx.x].y;
+    const int t0 = pstart[b], n = min(32, pcount[b] - c0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r0 = 0; r0 < R_; r0 += kRC) {
+        const int rn = kRC == 1 ? 1 : min(kRC, R_ - r0);
+        cxd acc[kPts][kRC];
+        for (int i = 0; i < kPts; ++i)
+            for (int r = 0; r < kRC; ++r) acc[i][r] = mk<double>(0, 0);
+        for (int64_t pb = 0; pb < qv.npair; pb += kL2TabChunk) {
+            const int pn = (int)min((int64_t)kL2TabChunk, qv.npair - pb);
+            __syncthreads();
+            for (int v = threadIdx.x; v < pn * kRC; v += blockDim.x) {
+                const int pp = v / kRC, r = v % kRC;
+                cxd P = mk<double>(0, 0), Q = P;
+                if (r < rn) {
+                    const int2 kk2 = qv.pair[pb + pp];
+                    const cxd* Lb = L + ((int64_t)b * R_ + r0 + r) * qv.K;
+                    const cxd A = wk ? wk[kk2.x] * Lb[kk2.x] : Lb[kk2.x];
+                    const cxd B = wk ? wk[kk2.y] * Lb[kk2.y] : Lb[kk2.y];
+                    P = A + B;
+                    Q = A - B;
+                }
+                shp[pp * kRC + r] = P;
+                shq[pp * kRC + r] = Q;
+            }
+            __syncthreads();
+            for (int i = 0; i < kPts; ++i) {
+                const int ti = warp + kL2TabWarps * i;
+                if (ti >= n) break;
+                const cxd* Er = E + (int64_t)(t0 + c0 + ti) * qv.npair + pb;
+                for (int pp = lane; pp < pn; pp += 32) {
+                    cxd e = ldg_cx(Er + pp);
+                    if (kConj) e.y = -e.y;
+                    for (int r = 0; r < rn; ++r) {
+                        const cxd P = shp[pp * kRC + r], Q = shq[pp * kRC + r];
+                        acc[i][r].x += P.x * e.x - Q.y * e.y;
+                        acc[i][r].y += P.y * e.x + Q.x * e.y;
+                    }
+                }
+            }
+        }
+        for (int i = 0; i < kPts; ++i) {
+            const int ti = warp + kL2TabWarps * i;
+            if (ti >= n) break;
+            for (int r = 0; r < rn; ++r) {
+                double x = acc[i][r].x, y = acc[i][r].y;
+                for (int o = 16; o > 0; o >>= 1) {
+                    x += __shfl_xor_sync(0xffffffffu, x, o);
+                    y += __shfl_xor_sync(0xffffffffu, y, o);
+                }
+                if (lane == 0) {
+                    cxd& o = out[(int64_t)(t0 + c0 + ti) * R_ + r0 + r];
+                    o.x += x;
+                    o.y += y;
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // S2M and L2T of float64 levels in double-float arithmetic on the float32 pipe (about 48
 // significant bits; float64 in memory).  s' = s_k * kappa / (2 pi) and the offsets are
 // split into df pairs; the phase in turns is reduced by its nearest integer and cis_turns

@@ -107,3 +107,38 @@ def test_option_and_state_errors():
         FmmPlan(x, x, 4000.0, 1e-6, depth=2, root=(0, 0, 0, 1.0), device=-1)
     assert e.value.status == nat.ERR_ARG and b"above 1024" in L.hfmm_last_error()
     assert time.perf_counter() - t0 < 30.0
+
+
+def test_require_far_flag_returns_unstable():
+    """HFMM_FLAG_REQUIRE_FAR: a plan with no far-field level (boxes below a wavelength, or
+    too few points for two levels) fails with HFMM_ERR_UNSTABLE and a reason; a plan with a
+    far field is unaffected; without the flag the same inputs plan a pure near field."""
+    L = nat.lib()
+    rng = np.random.default_rng(2)
+    x = rng.random((3000, 3))
+    h = ctypes.c_void_p()
+
+    def status(kappa, flags, **kw):
+        opt = nat.Options()
+        L.hfmm_default_options(ctypes.byref(opt))
+        opt.device = -1
+        opt.flags = flags
+        for k, v in kw.items():
+            setattr(opt, k, v)
+        st = L.hfmm_plan(x.ctypes.data, len(x), x.ctypes.data, len(x), kappa, 1e-6, ctypes.byref(opt),
+                         ctypes.byref(h))
+        if st == nat.OK:
+            L.hfmm_destroy(h)
+        return st
+
+    assert status(5.0, 0, max_leaf=16) == nat.OK                       # near field only, allowed
+    assert status(5.0, nat.FLAG_REQUIRE_FAR, max_leaf=16) == nat.ERR_UNSTABLE
+    assert b"wavelength" in L.hfmm_last_error()
+    assert status(60.0, nat.FLAG_REQUIRE_FAR, max_leaf=16) == nat.OK    # kappa a_2 = 15
+    assert status(60.0, nat.FLAG_REQUIRE_FAR, max_leaf=4000) == nat.ERR_UNSTABLE   # depth 0
+    assert b"occupancy depth" in L.hfmm_last_error()
+    assert status(60.0, 4, max_leaf=16) == nat.ERR_ARG                  # unknown flag bit
+    assert status(60.0, 0, max_leaf=16, leaf_table_bytes=-2) == nat.ERR_ARG
+    with pytest.raises(nat.HfmmError) as e:
+        FmmPlan(x, x, 5.0, 1e-6, max_leaf=16, device=-1, require_far=True)
+    assert e.value.status == nat.ERR_UNSTABLE
