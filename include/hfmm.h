@@ -93,6 +93,11 @@ typedef struct {
      * (default), 0 = never, > 0 = at most this many bytes.  Levels in float32 or
      * double-float never use tables. */
     int64_t leaf_table_bytes;
+    /* buffer boxes between a box and its interaction list (Section 3.3.3): 1 (default, the
+     * common case: |r0| >= 2 a_l, neighbour lists of 3^3 boxes, 316 transfer vectors) or 2
+     * (|r0| >= 3 a_l: a smaller truncation l and more stable levels for the same eps,
+     * neighbour lists of 5^3 boxes, 1206 transfer vectors) */
+    int buffer;
 } hfmm_options;
 
 /* hfmm_options.flags: fail with HFMM_ERR_UNSTABLE instead of planning a pure near field
@@ -132,6 +137,7 @@ typedef struct {
     /* 1 when S2M / L2T of the (float64) leaf level read plane-wave tables built at plan time */
     int leaf_tables;
     int64_t leaf_table_bytes;   /* device bytes of those tables (0 without) */
+    int buffer;                 /* buffer boxes of the plan (1 or 2) */
 } hfmm_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -142,8 +148,8 @@ void hfmm_default_options(hfmm_options* opt);
  * may be the same pointer as sources.  kappa > 0; 0 < eps <= 0.1.  opt may be NULL.
  * Builds the octree, the interaction and neighbour lists, the per-level truncation
  * (Eq. EBF refined by Eq. CollinoError), N_theta (Algorithm Ntheta), N_phi(theta_n)
- * (Algorithm Nphi) and the T^{s,LL} tables (Algorithm BMTF, 34 computed, reflected to
- * 316), copies the points, and (device >= 0) uploads everything and allocates the apply
+ * (Algorithm Nphi) and the T^{s,LL} tables of the vectors the lists use (Algorithm BMTF;
+ * canonical vectors computed, reflected into the others), copies the points, and (device >= 0) uploads everything and allocates the apply
  * workspace on the device.  On success *out owns all of it; release with hfmm_destroy.
  * Errors: HFMM_ERR_ARG, HFMM_ERR_NOMEM, HFMM_ERR_CUDA, HFMM_ERR_UNSTABLE (only with
  * HFMM_FLAG_REQUIRE_FAR: no level carries a far field). */
@@ -244,8 +250,10 @@ typedef enum {
     HFMM_GET_BOX_PARENT = 1,   /* int32 (nbox) parent position in level-1 */
     HFMM_GET_ILIST_OFF = 2,    /* int32 (nbox+1) CSR offsets of the interaction lists */
     HFMM_GET_ILIST_IDX = 3,    /* int32 interaction-list box positions */
-    HFMM_GET_ILIST_V = 4,      /* int32 transfer-vector indices (di+3)*49+(dj+3)*7+(dk+3) */
-    HFMM_GET_NLIST_OFF = 5,    /* int32 (nbox+1) CSR offsets of the leaf neighbour lists */
+    HFMM_GET_ILIST_V = 4,      /* int32 transfer-vector indices (di+D)*W*W+(dj+D)*W+(dk+D), D = 2b+1,
+                                  W = 2D+1 for b buffer boxes (b = 1: (di+3)*49+(dj+3)*7+(dk+3)) */
+    HFMM_GET_NLIST_OFF = 5,    /* int32 (nbox+1) CSR offsets of the leaf neighbour lists (Chebyshev
+                                  distance <= b) */
     HFMM_GET_NLIST_IDX = 6,    /* int32 neighbour-list box positions */
     HFMM_GET_SRC_PERM = 7,     /* int64 (ns) original index of each sorted source */
     HFMM_GET_TGT_PERM = 8,     /* int64 (nt) original index of each sorted target */

@@ -40,7 +40,7 @@ import numpy as np
 
 from . import quadrature as qd
 from .direct import kernel_matrix
-from .tree import Tree, root_cube, occupancy_depth
+from .tree import Tree, root_cube, occupancy_depth, transfer_offset
 
 PRECISION_UNIT = {'fp64': qd.U_FP64, 'df': qd.U_DF, 'fp32': qd.U_FP32}
 # acceptance factor of the stability rule per precision (see module docstring)
@@ -62,12 +62,13 @@ class Plan:
     """Everything the apply needs: tree to depth L_f, per-level quadrature, transfer tables."""
 
     def __init__(self, sources, targets, kappa, eps, alphas=None, max_leaf=64, depth=0,
-                 root=None, precision='fp64', eps_scale=0.25):
+                 root=None, precision='fp64', eps_scale=0.25, buffer=1):
         self.sources = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 3)
         self.targets = np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 3)
         self.kappa = float(kappa)
         self.eps = float(eps)
         self.eps_l = eps_scale * self.eps
+        self.buffer = int(buffer)
         allp = np.concatenate([self.sources, self.targets], axis=0)
         corner, side = root_cube(allp, root)
         if depth > 0:
@@ -85,7 +86,7 @@ class Plan:
                 break
             chosen = None
             for alpha in alphas:
-                lp = qd.LevelPlan(self.kappa, side / float(2 ** l), self.eps_l, alpha)
+                lp = qd.LevelPlan(self.kappa, side / float(2 ** l), self.eps_l, alpha, self.buffer)
                 for p in allowed:
                     if lp.rounding_estimate(PRECISION_UNIT[p]) <= self.eps_l * PRECISION_FACTOR[p]:
                         chosen = (lp, p)
@@ -102,14 +103,14 @@ class Plan:
             lf = dmax
         self.occupancy_depth = dmax
         self.lf = lf
-        self.tree = Tree(self.sources, self.targets, lf, root)
+        self.tree = Tree(self.sources, self.targets, lf, root, self.buffer)
         self._tables = {}
 
     def table(self, l, v):
         """T^{s,LL} of level l for transfer-vector index v (computed directly, no symmetry)."""
         key = (l, int(v))
         if key not in self._tables:
-            d = np.array([v // 49 - 3, (v // 7) % 7 - 3, v % 7 - 3], dtype=np.float64)
+            d = transfer_offset(v, self.buffer).astype(np.float64)
             a = self.tree.levels[l]['a']
             lp = self.levels[l]
             self._tables[key] = qd.tsll(lp.ell, self.kappa, d * a, lp.ntheta, lp.nphi)

@@ -17,7 +17,8 @@ independently there):
 
 * per-level relative target eps_l = eps / 4; absolute threshold eps_l / |r0|
   (|G| ~ 1 / |r0| for the closest far-field pair); d0 = -log10(eps_l);
-* |r| = alpha sqrt(3) a_l, |r0| = 2 a_l (one buffer box, Section 3.3.3);
+* |r| = alpha sqrt(3) a_l, |r0| = (b + 1) a_l for b buffer boxes (Section 3.3.3:
+  b = 1, the common case, |r0| = 2 a_l; b = 2, |r0| = 3 a_l);
 * l: start at the EBF value; if it passes the Collino bound step down while the
   next smaller l still passes, else step up until one passes;
 * N_theta^max = N_phi^max = 2l + 64, doubled when nothing below it passes;
@@ -324,10 +325,10 @@ def requadrature(flat, qa, qb):
 class LevelPlan:
     """l, quadrature and error-model numbers of one level with box size a."""
 
-    def __init__(self, kappa, a, eps_l, alpha):
+    def __init__(self, kappa, a, eps_l, alpha, buffer=1):
         self.kappa, self.a, self.eps_l, self.alpha = kappa, a, eps_l, alpha
         self.r = alpha * math.sqrt(3.0) * a
-        self.r0 = 2.0 * a
+        self.r0 = (buffer + 1.0) * a
         self.eps_abs = eps_l / self.r0
         d0 = -math.log10(eps_l)
         self.ell = choose_ell(kappa, self.r, self.r0, self.eps_abs, d0)

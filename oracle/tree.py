@@ -19,9 +19,13 @@ for bit:
 * only boxes holding at least one source or target exist (sparse, level uniform);
 * boxes and points are ordered by Morton key (x bit above y bit above z bit),
   points by key and then by original index;
-* "neighbour" = Chebyshev distance of box indices <= 1 (a box is its own
-  neighbour); transfer-vector index v = (di+3)*49 + (dj+3)*7 + (dk+3) with
-  (di, dj, dk) = idx(source box) - idx(target box).
+* "neighbour" = Chebyshev distance of box indices <= b, b the number of buffer
+  boxes (Section 3.3.3: b = 1, the common case, or 2, so that |r0| >= (b + 1) a_l);
+  a box is its own neighbour.  The interaction list of a box then holds the
+  children of its parent's neighbours that are not its own neighbours, at offsets
+  (di, dj, dk) = idx(source box) - idx(target box) in [-D, D]^3, D = 2b + 1;
+  transfer-vector index v = (di+D) W^2 + (dj+D) W + (dk+D), W = 2D + 1 (b = 1:
+  v = (di+3)*49 + (dj+3)*7 + (dk+3), 316 vectors; b = 2: W = 11, 1206 vectors).
 
 Everything is plain Python / numpy on float64 and int64.
 """
@@ -81,9 +85,22 @@ def occupancy_depth(sources, targets, corner, side, max_leaf):
     return MAX_DEPTH
 
 
-def transfer_index(d):
-    """Index 0..342 of a box offset (di, dj, dk), each in [-3, 3]."""
-    return (d[0] + 3) * 49 + (d[1] + 3) * 7 + (d[2] + 3)
+def transfer_span(buffer=1):
+    """(D, W): offsets lie in [-D, D]^3, D = 2 buffer + 1; W = 2 D + 1 index values per axis."""
+    D = 2 * buffer + 1
+    return D, 2 * D + 1
+
+
+def transfer_index(d, buffer=1):
+    """Index 0..W^3-1 of a box offset (di, dj, dk), each in [-D, D] (b = 1: 0..342)."""
+    D, W = transfer_span(buffer)
+    return (d[0] + D) * W * W + (d[1] + D) * W + (d[2] + D)
+
+
+def transfer_offset(v, buffer=1):
+    """Inverse of transfer_index."""
+    D, W = transfer_span(buffer)
+    return np.array([v // (W * W) - D, (v // W) % W - D, v % W - D], dtype=np.int64)
 
 
 class Tree:
@@ -100,9 +117,11 @@ class Tree:
     ilist[l], vlist[l] : for l >= 2, per box, the interaction-list box positions
                 (ascending) and their transfer-vector indices
     nlist : per depth-level box, the neighbour-list box positions (ascending)
+    buffer : number of buffer boxes (1 or 2)
     """
 
-    def __init__(self, sources, targets, depth, root=None):
+    def __init__(self, sources, targets, depth, root=None, buffer=1):
+        self.buffer = int(buffer)
         sources = np.asarray(sources, dtype=np.float64).reshape(-1, 3)
         targets = np.asarray(targets, dtype=np.float64).reshape(-1, 3)
         allp = np.concatenate([sources, targets], axis=0)
@@ -160,24 +179,26 @@ class Tree:
         lev = self.levels[l]
         where = self._lookup(l)
         nb = 2 ** l
+        bw = self.buffer
+        span = 2 * bw + 1
         il, vl = [], []
         for a in range(len(lev['key'])):
             ia = lev['idx'][a]
             pa = ia >> 1
             found = []
-            # children of the parent's neighbours
-            for dp in np.ndindex(3, 3, 3):
-                pn = pa + np.array(dp) - 1
+            # children of the parent's neighbours (Chebyshev distance <= buffer)
+            for dp in np.ndindex(span, span, span):
+                pn = pa + np.array(dp) - bw
                 for dc in np.ndindex(2, 2, 2):
                     ib = pn * 2 + np.array(dc)
                     if np.any(ib < 0) or np.any(ib >= nb):
                         continue
                     d = ib - ia
-                    if np.max(np.abs(d)) <= 1:
+                    if np.max(np.abs(d)) <= bw:
                         continue
                     b = where.get(tuple(int(c) for c in ib))
                     if b is not None:
-                        found.append((lev['key'][b], b, transfer_index(d)))
+                        found.append((lev['key'][b], b, transfer_index(d, bw)))
             found.sort()
             il.append(np.array([f[1] for f in found], dtype=np.int64))
             vl.append(np.array([f[2] for f in found], dtype=np.int64))
@@ -186,12 +207,14 @@ class Tree:
     def _neighbour_lists(self, l):
         lev = self.levels[l]
         where = self._lookup(l)
+        bw = self.buffer
+        span = 2 * bw + 1
         out = []
         for a in range(len(lev['key'])):
             ia = lev['idx'][a]
             found = []
-            for d in np.ndindex(3, 3, 3):
-                ib = ia + np.array(d) - 1
+            for d in np.ndindex(span, span, span):
+                ib = ia + np.array(d) - bw
                 b = where.get(tuple(int(c) for c in ib))
                 if b is not None:
                     found.append((lev['key'][b], b))

@@ -31,7 +31,8 @@ class Options(ctypes.Structure):
     _fields_ = [("alpha_ladder", ctypes.c_double * 4), ("eps_scale", ctypes.c_double),
                 ("max_leaf", ctypes.c_int), ("depth", ctypes.c_int), ("has_root", ctypes.c_int),
                 ("root", ctypes.c_double * 4), ("precision", ctypes.c_int), ("max_rhs", ctypes.c_int),
-                ("device", ctypes.c_int), ("flags", ctypes.c_int), ("leaf_table_bytes", ctypes.c_int64)]
+                ("device", ctypes.c_int), ("flags", ctypes.c_int), ("leaf_table_bytes", ctypes.c_int64),
+                ("buffer", ctypes.c_int)]
 
 
 class Problem(ctypes.Structure):
@@ -51,7 +52,7 @@ class Info(ctypes.Structure):
                 ("stage_ms", ctypes.c_double * N_STAGES), ("workspace_bytes", ctypes.c_int64),
                 ("near_precision", ctypes.c_int), ("p2p_self_pairs", ctypes.c_int64),
                 ("near_symmetric", ctypes.c_int), ("leaf_tables", ctypes.c_int),
-                ("leaf_table_bytes", ctypes.c_int64)]
+                ("leaf_table_bytes", ctypes.c_int64), ("buffer", ctypes.c_int)]
 
 
 _lib = None

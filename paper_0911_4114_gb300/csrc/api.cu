@@ -218,17 +218,19 @@ hfmm_status upload_level(hfmm_plan_s* P, int l) {
     TRY(upload(P, &d.ioff, T.ioff));
     TRY(upload(P, &d.iidx, T.iidx));
     TRY(upload(P, &d.iv, T.iv));
-    // transfer tables, compact
-    std::vector<int32_t> slot(kNumTransfer, 0);
+    // transfer tables, compact: slot of every used vector (the lists are symmetric, so the
+    // opposite vector W^3 - 1 - v of a used v is used too)
+    const int nslots = transfer_slots(hp.buffer);
+    std::vector<int32_t> slot(nslots, 0);
     int ns = 0;
-    for (int v = 0; v < kNumTransfer; ++v) slot[v] = lp.table[v].empty() ? 0 : ns++;
+    for (int v = 0; v < nslots; ++v) slot[v] = lp.table[v].empty() ? 0 : ns++;
     TRY(upload(P, &d.tslot, slot));
-    std::vector<int32_t> slot_t(kNumTransfer, 0);
-    for (int v = 0; v < kNumTransfer; ++v) slot_t[v] = slot[kNumTransfer - 1 - v];
+    std::vector<int32_t> slot_t(nslots, 0);
+    for (int v = 0; v < nslots; ++v) slot_t[v] = slot[nslots - 1 - v];
     TRY(upload(P, &d.tslot_t, slot_t));
     if (d.prec == kDF) {
         std::vector<cx<df>> t((size_t)ns * q.K);
-        for (int v = 0; v < kNumTransfer; ++v)
+        for (int v = 0; v < transfer_slots(hp.buffer); ++v)
             if (!lp.table[v].empty())
                 for (int64_t k = 0; k < q.K; ++k)
                     t[(size_t)slot[v] * q.K + k] = mk<df>(df(lp.table[v][k].real()), df(lp.table[v][k].imag()));
@@ -237,7 +239,7 @@ hfmm_status upload_level(hfmm_plan_s* P, int l) {
         d.table = dt;
     } else if (d.prec == kFP64) {
         std::vector<cxd> t((size_t)ns * q.K);
-        for (int v = 0; v < kNumTransfer; ++v)
+        for (int v = 0; v < transfer_slots(hp.buffer); ++v)
             if (!lp.table[v].empty())
                 for (int64_t k = 0; k < q.K; ++k)
                     t[(size_t)slot[v] * q.K + k] = mk<double>(lp.table[v][k].real(), lp.table[v][k].imag());
@@ -246,7 +248,7 @@ hfmm_status upload_level(hfmm_plan_s* P, int l) {
         d.table = dt;
     } else {
         std::vector<cxf> t((size_t)ns * q.K);
-        for (int v = 0; v < kNumTransfer; ++v)
+        for (int v = 0; v < transfer_slots(hp.buffer); ++v)
             if (!lp.table[v].empty())
                 for (int64_t k = 0; k < q.K; ++k)
                     t[(size_t)slot[v] * q.K + k] =
@@ -862,6 +864,7 @@ void hfmm_default_options(hfmm_options* opt) {
     opt->device = 0;
     opt->flags = 0;
     opt->leaf_table_bytes = -1;
+    opt->buffer = 1;
 }
 
 const char* hfmm_last_error(void) { return g_err.c_str(); }
@@ -886,6 +889,7 @@ hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, 
         return fail(HFMM_ERR_ARG, "unknown precision policy");
     if (opt.flags & ~HFMM_FLAG_REQUIRE_FAR) return fail(HFMM_ERR_ARG, "unknown flag bits");
     if (opt.leaf_table_bytes < -1) return fail(HFMM_ERR_ARG, "leaf_table_bytes must be -1, 0 or positive");
+    if (opt.buffer != 1 && opt.buffer != 2) return fail(HFMM_ERR_ARG, "buffer must be 1 or 2");
     std::vector<double> alphas;
     // default ladder: (0.8, 0.6), or (0.9, 0.8) below eps = 1e-7, where the few terms that
     // l(0.8) keeps beyond k|r| of a corner pair no longer reach eps
@@ -929,6 +933,7 @@ hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, 
         hp.max_leaf = opt.max_leaf;
         hp.depth_req = opt.depth;
         hp.precision = opt.precision;
+        hp.buffer = opt.buffer;
         hp.has_root = opt.has_root;
         for (int k = 0; k < 4; ++k) hp.root[k] = opt.root[k];
         std::string e = build_host_plan(hp);
@@ -1270,6 +1275,7 @@ hfmm_status hfmm_query(hfmm_plan_t P, hfmm_info* info) {
     info->near_symmetric = (P->sym && P->near_prec == kFP32) ? 1 : 0;
     info->near_precision = P->near_prec == kFP32 ? HFMM_LEVEL_FP32 : (P->near_prec == kDF ? HFMM_LEVEL_DF : HFMM_LEVEL_FP64);
     info->leaf_tables = P->tab_s != nullptr;
+    info->buffer = hp.buffer;
     info->leaf_table_bytes = P->tab_bytes;
     if (P->ev_recorded) {
         if (cudaEventSynchronize(P->ev[HFMM_N_STAGES]) != cudaSuccess)
@@ -1451,7 +1457,7 @@ int64_t hfmm_debug_get(hfmm_plan_t P, int what, int level, int64_t arg, void* ou
             if (!lev_ok || level < 2) return -1;
             return give(hp.lp[level].quad.nphi.data(), (int64_t)hp.lp[level].quad.nphi.size(), 4);
         case HFMM_GET_TABLE: {
-            if (!lev_ok || level < 2 || arg < 0 || arg >= kNumTransfer) return -1;
+            if (!lev_ok || level < 2 || arg < 0 || arg >= transfer_slots(hp.buffer)) return -1;
             const auto& t = hp.lp[level].table[arg];
             if (t.empty()) return -1;
             const int64_t n = (int64_t)t.size();

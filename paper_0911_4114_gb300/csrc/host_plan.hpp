@@ -13,7 +13,12 @@ using cd = std::complex<double>;
 
 constexpr int kMaxLevels = 21;
 constexpr int kTreeBits = 20;        // deepest depth the tree code supports
-constexpr int kNumTransfer = 343;    // 7^3 slots, 316 used (one buffer box)
+// transfer-vector offsets of b buffer boxes lie in [-D, D]^3, D = 2b + 1; index
+// v = (di + D) W^2 + (dj + D) W + (dk + D), W = 2D + 1 (b = 1: 343 slots, 316 vectors;
+// b = 2: 1331 slots, 1206 vectors)
+inline int transfer_span(int buffer) { return 2 * buffer + 1; }
+inline int transfer_width(int buffer) { return 2 * transfer_span(buffer) + 1; }
+inline int transfer_slots(int buffer) { int w = transfer_width(buffer); return w * w * w; }
 
 // level arithmetic: float64, float32, or double-float (float32 pairs, mixed policy only)
 enum LevelPrec { kFP64 = 0, kFP32 = 1, kDF = 2 };
@@ -32,7 +37,7 @@ struct LevelPlan {
     double a = 0, alpha = 0, r = 0, r0 = 0, eps_abs = 0, est = 0;
     int prec = kFP64;
     Quadrature quad;
-    // T^{s,LL} for each of the 343 transfer-vector slots (empty where unused), K each
+    // T^{s,LL} for each transfer-vector slot (empty where the level's lists never use it), K each
     std::vector<std::vector<cd>> table;
 };
 
@@ -55,6 +60,7 @@ struct HostPlan {
     std::vector<double> alphas;
     double eps_scale = 0.25;
     int max_leaf = 64, depth_req = 0, precision = 0;
+    int buffer = 1;      // buffer boxes between a box and its interaction list (Section 3.3.3)
     int has_root = 0;
     double root[4] = {0, 0, 0, 1};
     // tree

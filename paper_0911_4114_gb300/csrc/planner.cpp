@@ -3,9 +3,11 @@
 //   * per level: truncation l (Eq. EBF start, Eq. CollinoError refinement, Section 2.1),
 //     N_theta (Algorithm Ntheta), N_phi(theta_n) (Algorithm Nphi), the choice of alpha and
 //     precision by the round-off estimate of the quadrature sum;
-//   * T^{s,LL} for the 34 transfer vectors with x >= y >= 0, z >= 0 (Figure SemiOctant) by
-//     Algorithm BMTF followed by the per-row phi anterpolation of Section 3.3.2, then
-//     reflected into the other 282 of the 316 one-buffer-box vectors by index permutations.
+//   * T^{s,LL} for the canonical transfer vectors with x >= y >= 0, z >= 0 (Figure
+//     SemiOctant) by Algorithm BMTF followed by the per-row phi anterpolation of Section
+//     3.3.2, then reflected into the other vectors by index permutations (one buffer box:
+//     34 canonical of 316; two buffer boxes, Section 3.3.3: 108 of 1206); only vectors that
+//     the level's interaction lists use are computed.
 //
 // Conventions that the paper leaves open (identical rules are applied by the test oracle,
 // which is an independent implementation):
@@ -13,7 +15,8 @@
 //   box index at depth D = clamp(floor((x - corner) * (2^D / side)), 0, 2^D - 1);
 //   Morton order with the x bit above y above z; points by key then original index;
 //   eps_l = eps_scale * eps, absolute threshold eps_l / |r0|, d0 = -log10(eps_l);
-//   |r| = alpha sqrt(3) a_l, |r0| = 2 a_l; N^max = 2l + 64 doubled on failure;
+//   |r| = alpha sqrt(3) a_l, |r0| = (b + 1) a_l for b buffer boxes; N^max = 2l + 64 doubled
+//   on failure;
 //   N_theta rounded up to 2 * 2^a 3^b 5^c, N_phi to 4 * 2^a 3^b 5^c; rows mirrored about
 //   theta = pi/2; re-sampling keeps |k| <= min(ceil(K/2), ceil(K'/2)) - 1.
 // Built with -ffp-contract=off so the tree arithmetic rounds exactly as written.
@@ -273,11 +276,11 @@ static double round_off_estimate(int ell, double kappa, double r0, int64_t K, do
     return u * kappa * r0 * std::sqrt(s) / std::sqrt((double)K);
 }
 
-static void plan_level(double kappa, double a, double eps_l, double alpha, LevelPlan& lp) {
+static void plan_level(double kappa, double a, double eps_l, double alpha, int buffer, LevelPlan& lp) {
     lp.a = a;
     lp.alpha = alpha;
     lp.r = alpha * std::sqrt(3.0) * a;
-    lp.r0 = 2.0 * a;
+    lp.r0 = (buffer + 1.0) * a;
     lp.eps_abs = eps_l / lp.r0;
     double d0 = -std::log10(eps_l);
     Quadrature& q = lp.quad;
@@ -369,14 +372,25 @@ static std::vector<cd> reflect(const std::vector<cd>& canon, const Quadrature& q
     return out;
 }
 
-static void build_tables(LevelPlan& lp, double kappa) {
-    lp.table.assign(kNumTransfer, {});
-    // canonical set: x >= y >= 0, z >= 0, max >= 2
+// canonical representative (x >= y >= 0, z >= 0) of an offset under the reflections
+static std::array<int, 3> canonical(int di, int dj, int dk) {
+    return {std::max(std::abs(di), std::abs(dj)), std::min(std::abs(di), std::abs(dj)), std::abs(dk)};
+}
+
+static void build_tables(LevelPlan& lp, double kappa, int buffer, const std::vector<char>& used) {
+    const int D = transfer_span(buffer), W = transfer_width(buffer);
+    lp.table.assign(transfer_slots(buffer), {});
+    // canonical set: x >= y >= 0, z >= 0, max > buffer, restricted to what the lists use
     std::vector<std::array<int, 3>> canon;
-    for (int x = 0; x <= 3; ++x)
-        for (int y = 0; y <= x; ++y)
-            for (int z = 0; z <= 3; ++z)
-                if (std::max(x, std::max(y, z)) >= 2) canon.push_back({x, y, z});
+    for (int di = -D; di <= D; ++di)
+        for (int dj = -D; dj <= D; ++dj)
+            for (int dk = -D; dk <= D; ++dk) {
+                const int v = (di + D) * W * W + (dj + D) * W + (dk + D);
+                if (!used[v]) continue;
+                const std::array<int, 3> cv = canonical(di, dj, dk);
+                if (std::find(canon.begin(), canon.end(), cv) == canon.end()) canon.push_back(cv);
+            }
+    std::sort(canon.begin(), canon.end());
     const Quadrature& q = lp.quad;
     const int ell = q.ell, half = q.ntheta / 2;
     const int nfull = 4 * ((2 * ell + 1 + 3) / 4);  // even, >= 2l+2: holds the phi band |m| <= l
@@ -395,15 +409,13 @@ static void build_tables(LevelPlan& lp, double kappa) {
     for (int it = 0; it < nc * nrow; ++it) tsll_row(work[it / nrow], lp, twf, nfull, it % nrow);
     std::vector<std::vector<cd>> ct(canon.size());
     for (int c = 0; c < nc; ++c) ct[c] = std::move(work[c].out);
-    for (int di = -3; di <= 3; ++di)
-        for (int dj = -3; dj <= 3; ++dj)
-            for (int dk = -3; dk <= 3; ++dk) {
-                if (std::max(std::abs(di), std::max(std::abs(dj), std::abs(dk))) < 2) continue;
+    for (int di = -D; di <= D; ++di)
+        for (int dj = -D; dj <= D; ++dj)
+            for (int dk = -D; dk <= D; ++dk) {
+                const int v = (di + D) * W * W + (dj + D) * W + (dk + D);
+                if (!used[v]) continue;
                 int d[3] = {di, dj, dk};
-                std::array<int, 3> cv = {std::max(std::abs(di), std::abs(dj)),
-                                         std::min(std::abs(di), std::abs(dj)), std::abs(dk)};
-                size_t c = std::find(canon.begin(), canon.end(), cv) - canon.begin();
-                int v = (di + 3) * 49 + (dj + 3) * 7 + (dk + 3);
+                size_t c = std::find(canon.begin(), canon.end(), canonical(di, dj, dk)) - canon.begin();
                 lp.table[v] = reflect(ct[c], lp.quad, d);
             }
 }
@@ -544,7 +556,9 @@ static void build_tree(HostPlan& hp) {
     };
     ranges(ks, hp.src_perm, hp.src_start, hp.src_count);
     ranges(kt, hp.tgt_perm, hp.tgt_start, hp.tgt_count);
-    // interaction lists
+    // interaction lists: children of the parent's neighbours (Chebyshev distance <= buffer)
+    // that are not neighbours of the box itself
+    const int bw = hp.buffer, TD = transfer_span(bw), TW = transfer_width(bw);
     for (int l = 2; l <= D; ++l) {
         TreeLevel& L = hp.levels[l];
         const int n1 = 1 << l;
@@ -553,9 +567,9 @@ static void build_tree(HostPlan& hp) {
 #pragma omp parallel for schedule(static)
         for (int64_t a = 0; a < L.nbox(); ++a) {
             const int32_t* ia = &L.idx[3 * a];
-            for (int px = -1; px <= 1; ++px)
-                for (int py = -1; py <= 1; ++py)
-                    for (int pz = -1; pz <= 1; ++pz)
+            for (int px = -bw; px <= bw; ++px)
+                for (int py = -bw; py <= bw; ++py)
+                    for (int pz = -bw; pz <= bw; ++pz)
                         for (int c = 0; c < 8; ++c) {
                             int ib[3] = {((ia[0] >> 1) + px) * 2 + ((c >> 2) & 1),
                                          ((ia[1] >> 1) + py) * 2 + ((c >> 1) & 1),
@@ -566,10 +580,10 @@ static void build_tree(HostPlan& hp) {
                                 if (ib[k] < 0 || ib[k] >= n1) ok = false;
                                 dmax = std::max(dmax, std::abs(ib[k] - ia[k]));
                             }
-                            if (!ok || dmax <= 1) continue;
+                            if (!ok || dmax <= bw) continue;
                             int64_t b = find_key(L.key, morton(ib[0], ib[1], ib[2], l));
                             if (b < 0) continue;
-                            int v = (ib[0] - ia[0] + 3) * 49 + (ib[1] - ia[1] + 3) * 7 + (ib[2] - ia[2] + 3);
+                            int v = (ib[0] - ia[0] + TD) * TW * TW + (ib[1] - ia[1] + TD) * TW + (ib[2] - ia[2] + TD);
                             found[a].push_back({(int64_t)L.key[b], b, v});
                         }
             std::sort(found[a].begin(), found[a].end());
@@ -589,9 +603,9 @@ static void build_tree(HostPlan& hp) {
     const int n1 = 1 << D;
     for (int64_t a = 0; a < nb; ++a) {
         const int32_t* ia = &leaf.idx[3 * a];
-        for (int dx = -1; dx <= 1; ++dx)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dz = -1; dz <= 1; ++dz) {
+        for (int dx = -bw; dx <= bw; ++dx)
+            for (int dy = -bw; dy <= bw; ++dy)
+                for (int dz = -bw; dz <= bw; ++dz) {
                     int ib[3] = {ia[0] + dx, ia[1] + dy, ia[2] + dz};
                     if (ib[0] < 0 || ib[1] < 0 || ib[2] < 0 || ib[0] >= n1 || ib[1] >= n1 || ib[2] >= n1)
                         continue;
@@ -669,7 +683,7 @@ std::string build_host_plan(HostPlan& hp) {
         bool ok = false;
         for (double alpha : hp.alphas) {
             LevelPlan cand;
-            plan_level(hp.kappa, hp.side / (double)(1u << l), hp.eps_l, alpha, cand);
+            plan_level(hp.kappa, hp.side / (double)(1u << l), hp.eps_l, alpha, hp.buffer, cand);
             for (int p : allowed) {
                 const double u = std::ldexp(1.0, p == kFP32 ? -24 : (p == kDF ? -48 : -53));
                 const double f = (p == kFP32) ? 1.0 : 1.0 / 16.0;
@@ -697,7 +711,11 @@ std::string build_host_plan(HostPlan& hp) {
             if (v > 1024) return "N_phi above 1024 is not supported";
     }
     build_tree(hp);
-    for (int l = 2; l <= hp.lf; ++l) build_tables(hp.lp[l], hp.kappa);
+    for (int l = 2; l <= hp.lf; ++l) {
+        std::vector<char> used(transfer_slots(hp.buffer), 0);
+        for (int32_t v : hp.levels[l].iv) used[v] = 1;
+        build_tables(hp.lp[l], hp.kappa, hp.buffer, used);
+    }
     return "";
 }
 

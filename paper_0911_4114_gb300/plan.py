@@ -13,7 +13,7 @@ from . import _native as nat
 _PREC_NAMES = {0: "fp64", 1: "fp32", 2: "df"}   # hfmm_level_precision codes
 
 def make_options(precision="fp64", alphas=None, eps_scale=0.25, max_leaf=64, depth=0, root=None,
-                 max_rhs=1, device=0, require_far=False, leaf_table_bytes=-1):
+                 max_rhs=1, device=0, require_far=False, leaf_table_bytes=-1, buffer=1):
     opt = nat.Options()
     nat.lib().hfmm_default_options(ctypes.byref(opt))
     if alphas is not None:              # None keeps the library default ladder
@@ -31,6 +31,7 @@ def make_options(precision="fp64", alphas=None, eps_scale=0.25, max_leaf=64, dep
     opt.device = device
     opt.flags = nat.FLAG_REQUIRE_FAR if require_far else 0
     opt.leaf_table_bytes = int(leaf_table_bytes)
+    opt.buffer = int(buffer)
     return opt
 
 
@@ -43,17 +44,18 @@ class FmmPlan:
     require_far: raise (HFMM_ERR_UNSTABLE) instead of planning a pure near field.
     leaf_table_bytes: device bytes allowed for the plane-wave tables of a float64 leaf level
     (-1: up to half the free device memory, 0: none).
+    buffer: buffer boxes between a box and its interaction list, 1 or 2 (Section 3.3.3).
     """
 
     def __init__(self, sources, targets, kappa, eps, precision="fp64", alphas=None,
                  eps_scale=0.25, max_leaf=64, depth=0, root=None, max_rhs=1, device=0,
-                 require_far=False, leaf_table_bytes=-1):
+                 require_far=False, leaf_table_bytes=-1, buffer=1):
         L = nat.lib()
         src = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 3)
         tgt = np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 3)
         self.same = sources is targets
         opt = make_options(precision, alphas, eps_scale, max_leaf, depth, root, max_rhs, device,
-                           require_far, leaf_table_bytes)
+                           require_far, leaf_table_bytes, buffer)
         h = ctypes.c_void_p()
         nat.check(L.hfmm_plan(src.ctypes.data, src.shape[0], tgt.ctypes.data, tgt.shape[0],
                               float(kappa), float(eps), ctypes.byref(opt), ctypes.byref(h)))
@@ -158,7 +160,8 @@ class FmmPlan:
                     workspace_bytes=inf.workspace_bytes,
                     near_precision=_PREC_NAMES[inf.near_precision],
                     p2p_self_pairs=inf.p2p_self_pairs, near_symmetric=bool(inf.near_symmetric),
-                    leaf_tables=bool(inf.leaf_tables), leaf_table_bytes=inf.leaf_table_bytes)
+                    leaf_tables=bool(inf.leaf_tables), leaf_table_bytes=inf.leaf_table_bytes,
+                    buffer=inf.buffer)
 
     def debug_get(self, what, level=0, arg=0):
         L = nat.lib()

@@ -225,3 +225,32 @@ def test_tensor_core_near_field(nrhs):
     w = wl.charges(len(x), nrhs, g)
     adj = lib.apply_adjoint(torch.as_tensor(w, device="cuda")).cpu().numpy()
     assert rel(adj, direct.direct_adjoint(x, x, w, 25.0)) <= 1e-6
+
+
+@pytest.mark.parametrize("kind", ["cube", "two_spheres"])
+def test_two_buffer_boxes(kind):
+    """Two buffer boxes (Section 3.3.3, |r0| >= 3 a_l; 5^3 neighbour lists, transfer vectors
+    over [-5, 5]^3): float64 apply element-wise against the oracle FMM with the same option,
+    mixed apply and adjoint within eps of the direct sums."""
+    import torch
+    g = wl.rng(130)
+    if kind == "cube":
+        s = t = wl.cube(2500, g)
+        kappa, eps, kw = 70.0, 1e-6, dict(depth=3, root=(0, 0, 0, 1.0), buffer=2)
+    else:
+        s = wl.sphere(3000, g)
+        t = wl.sphere(2000, g, radius=1.5)
+        kappa, eps, kw = 16.0, 1e-6, dict(max_leaf=16, buffer=2)
+    q = wl.charges(len(s), 0, wl.rng(131))
+    lib = FmmPlan(s, t, kappa, eps, precision="fp64", **kw)
+    orc = ofmm.Plan(s, t, kappa, eps, precision="fp64", **kw)
+    assert lib.info()["lf"] == orc.lf >= 2 and lib.info()["buffer"] == 2
+    got = run_apply(lib, q)
+    check_fp64_parity(got, ofmm.apply(orc, q), orc, f"{kind}_buffer2")
+    want = direct.direct(s, t, q, kappa)
+    assert rel(got, want) <= eps
+    mixed = FmmPlan(s, t, kappa, eps, precision="mixed", **kw)
+    assert rel(run_apply(mixed, q, "c64"), want) <= eps
+    w = wl.charges(len(t), 0, wl.rng(132))
+    adj = mixed.apply_adjoint(torch.as_tensor(w, device="cuda")).cpu().numpy()
+    assert rel(adj, direct.direct_adjoint(s, t, w, kappa)) <= eps

@@ -126,3 +126,30 @@ def test_adjoint_and_gradient_direct():
         sm[j, c] -= h
         fd = (loss(sp) - loss(sm)) / (2 * h)
         assert fd == pytest.approx(g[j, c], rel=1e-6, abs=1e-6)
+
+
+@pytest.mark.parametrize("kind", ["cube", "two_spheres"])
+def test_two_buffer_boxes(kind):
+    """Section 3.3.3 with two buffer boxes (|r0| >= 3 a_l): a smaller truncation l per level
+    for the same eps, interaction lists over [-5, 5]^3 offsets, neighbour lists over 5^3
+    boxes; the apply stays within eps of the direct sum."""
+    rng = np.random.default_rng(31)
+    if kind == "cube":
+        s = t = rng.random((2500, 3))
+        kappa, kw = 70.0, dict(depth=3, root=(0, 0, 0, 1.0))
+    else:
+        s = rng.standard_normal((1500, 3))
+        s /= np.linalg.norm(s, axis=1)[:, None]
+        t = rng.standard_normal((900, 3))
+        t *= 1.5 / np.linalg.norm(t, axis=1)[:, None]
+        kappa, kw = 16.0, dict(max_leaf=16)
+    q = _charges(rng, len(s))
+    p1 = fmm.Plan(s, t, kappa, 1e-6, **kw)
+    p2 = fmm.Plan(s, t, kappa, 1e-6, buffer=2, **kw)
+    assert p2.lf >= 2
+    for l in p2.levels:
+        assert p2.levels[l].r0 == 3 * p2.tree.levels[l]['a']
+        if l in p1.levels and p1.levels[l].alpha == p2.levels[l].alpha:
+            assert p2.levels[l].ell < p1.levels[l].ell
+    assert max(len(x) for x in p2.tree.nlist) <= 125
+    assert _rel(fmm.apply(p2, q), direct.direct(s, t, q, kappa)) < 1e-6

@@ -97,17 +97,18 @@ def _full_grid_sum(lp, rv, r0v):
     return np.sum(q.w * np.exp(1j * lp.kappa * (q.shat @ rv)) * t)
 
 
-@pytest.mark.parametrize("kappa", [20.0, 40.0])   # outside the low-frequency breakdown
-def test_total_error_within_target(kappa):
-    """Section 3.5.1: eps_T of the worst-case directions stays within ~2x of the target."""
+@pytest.mark.parametrize("kappa,buffer", [(20.0, 1), (40.0, 1), (20.0, 2), (40.0, 2)])   # outside the breakdown
+def test_total_error_within_target(kappa, buffer):
+    """Section 3.5.1: eps_T of the worst-case directions stays within ~2x of the target, with
+    one buffer box (|r0| = 2a) and with two (|r0| = 3a, Section 3.3.3)."""
     a = 1.0
     eps_l = 1e-6
-    lp = qd.LevelPlan(kappa, a, eps_l, 0.8)
+    lp = qd.LevelPlan(kappa, a, eps_l, 0.8, buffer)
     r = lp.r
     worst = 0.0
     for r0dir, rdirs in (((0, 0, 1), [(0, 0, 1), (0, 0, -1), (1, 0, 0)]),
                          ((1, 0, 0), [(1, 0, 0), (-1, 0, 0), (0, 1, 1)])):
-        r0v = 2 * a * np.array(r0dir, dtype=float)
+        r0v = (buffer + 1) * a * np.array(r0dir, dtype=float)
         for rd in rdirs:
             rv = r * np.array(rd, dtype=float) / np.linalg.norm(rd)
             d = np.linalg.norm(rv + r0v)

@@ -23,13 +23,18 @@ def _cheb(a, b):
     return max(abs(x - y) for x, y in zip(a, b))
 
 
-@pytest.mark.parametrize("seed,n,depth", [(0, 300, 3), (1, 500, 4), (2, 60, 2)])
-def test_lists_match_definitions(seed, n, depth):
+@pytest.mark.parametrize("seed,n,depth,buffer", [(0, 300, 3, 1), (1, 500, 4, 1), (2, 60, 2, 1),
+                                                 (3, 400, 3, 2), (4, 700, 4, 2)])
+def test_lists_match_definitions(seed, n, depth, buffer):
+    """Interaction list = boxes farther than `buffer` (Chebyshev) whose parents are within
+    `buffer` of the parent (Section 2, with b buffer boxes, Section 3.3.3); neighbour list =
+    boxes within `buffer`.  |I| <= (2b+1)^3 * 8 - (2b+1)^3 (189 for b = 1, 875 for b = 2)."""
     rng = np.random.default_rng(seed)
     src = rng.random((n, 3)) ** 2          # clustered towards a corner
     tgt = rng.random((n // 2, 3))
-    t = tr.Tree(src, tgt, depth)
+    t = tr.Tree(src, tgt, depth, buffer=buffer)
     brute = _brute(src, tgt, t.corner, t.side, depth)
+    span = 2 * buffer + 1
     for l in range(depth + 1):
         got = {tuple(int(c) for c in i) for i in t.levels[l]['idx']}
         assert got == brute[l]
@@ -37,13 +42,15 @@ def test_lists_match_definitions(seed, n, depth):
         idx = [tuple(int(c) for c in i) for i in t.levels[l]['idx']]
         for a, ia in enumerate(idx):
             want = sorted(b for b, ib in enumerate(idx)
-                          if _cheb(ia, ib) > 1 and _cheb([x >> 1 for x in ia], [x >> 1 for x in ib]) <= 1)
+                          if _cheb(ia, ib) > buffer
+                          and _cheb([x >> 1 for x in ia], [x >> 1 for x in ib]) <= buffer)
             assert sorted(t.ilist[l][a].tolist()) == want
-            assert len(want) <= 189
+            assert len(want) <= span ** 3 * 8 - span ** 3
             for b, v in zip(t.ilist[l][a], t.vlist[l][a]):
                 d = np.array(idx[b]) - np.array(ia)
-                assert 2 <= np.max(np.abs(d)) <= 3
-                assert v == tr.transfer_index(d)
+                assert buffer + 1 <= np.max(np.abs(d)) <= span
+                assert v == tr.transfer_index(d, buffer)
+                assert np.array_equal(tr.transfer_offset(v, buffer), d)
             keys = t.levels[l]['key'][t.ilist[l][a]]
             assert np.all(np.diff(keys) > 0)
         # symmetry: b in I(a) <=> a in I(b)
@@ -52,7 +59,7 @@ def test_lists_match_definitions(seed, n, depth):
                 assert a in t.ilist[l][b]
     idx = [tuple(int(c) for c in i) for i in t.levels[depth]['idx']]
     for a, ia in enumerate(idx):
-        assert sorted(t.nlist[a].tolist()) == sorted(b for b, ib in enumerate(idx) if _cheb(ia, ib) <= 1)
+        assert sorted(t.nlist[a].tolist()) == sorted(b for b, ib in enumerate(idx) if _cheb(ia, ib) <= buffer)
 
 
 def test_points_in_their_boxes_and_parents():
@@ -78,11 +85,18 @@ def test_points_in_their_boxes_and_parents():
     assert np.all(np.diff(t.src_perm)[same] > 0)
 
 
-def test_all_316_transfer_vectors_and_34_canonical():
-    vecs = [d for d in itertools.product(range(-3, 4), repeat=3) if max(map(abs, d)) >= 2]
-    assert len(vecs) == 316
+@pytest.mark.parametrize("buffer,nvec,ncanon", [(1, 316, 34), (2, 1206, 108)])
+def test_transfer_vectors_and_canonical(buffer, nvec, ncanon):
+    """Offsets of interaction-list boxes: [-(2b+1), 2b+1]^3 without [-b, b]^3 (316 for one
+    buffer box, Section 3.3.2); up to the reflections x -> -x, y -> -y, z -> -z and x <-> y,
+    34 (Figure SemiOctant) or 108 canonical ones with x >= y >= 0, z >= 0."""
+    D = 2 * buffer + 1
+    vecs = [d for d in itertools.product(range(-D, D + 1), repeat=3) if max(map(abs, d)) > buffer]
+    assert len(vecs) == nvec
     canon = {(max(abs(d[0]), abs(d[1])), min(abs(d[0]), abs(d[1])), abs(d[2])) for d in vecs}
-    assert len(canon) == 34
+    assert len(canon) == ncanon
+    idx = {tr.transfer_index(d, buffer) for d in vecs}
+    assert len(idx) == nvec and max(idx) < (2 * D + 1) ** 3
 
 
 def test_root_cube_and_depth():

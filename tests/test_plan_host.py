@@ -20,6 +20,10 @@ CASES = {
     "sphere_auto_depth": dict(n=3000, kind="sphere", kappa=24.0, eps=1e-5, depth=0, root=None, max_leaf=32),
     "two_spheres": dict(n=800, kind="two", kappa=12.0, eps=1e-6, depth=0, root=None, max_leaf=16),
     "sphere_tight_eps": dict(n=3000, kind="sphere", kappa=60.0, eps=1e-9, depth=0, root=None, max_leaf=16),
+    # two buffer boxes (Section 3.3.3): 5^3 neighbour lists, offsets in [-5, 5]^3
+    "cube_two_buffer": dict(n=2500, kind="cube", kappa=70.0, eps=1e-6, depth=3, root=(0, 0, 0, 1.0), buffer=2),
+    "spheres_two_buffer": dict(n=1500, kind="two", kappa=16.0, eps=1e-6, depth=0, root=None, max_leaf=16,
+                               buffer=2),
 }
 
 
@@ -42,7 +46,7 @@ def pair(request):
     c = CASES[request.param]
     rng = np.random.default_rng(zlib.crc32(request.param.encode()))
     s, t = _points(c, rng)
-    kw = dict(depth=c["depth"], root=c["root"], max_leaf=c.get("max_leaf", 64))
+    kw = dict(depth=c["depth"], root=c["root"], max_leaf=c.get("max_leaf", 64), buffer=c.get("buffer", 1))
     out = {}
     for prec in ("fp64", "mixed"):
         lib = FmmPlan(s, t, c["kappa"], c["eps"], precision=prec, device=-1, **kw)
@@ -57,6 +61,7 @@ def test_levels_and_quadrature_integers(pair):
         info = lib.info()
         assert info["lf"] == orc.lf, (name, prec)
         assert info["occupancy_depth"] == orc.occupancy_depth
+        assert info["buffer"] == orc.buffer
         for l, lp in orc.levels.items():
             li = info["levels"][l]
             assert (li["ell"], li["ntheta"], li["K"]) == (lp.ell, lp.ntheta, lp.K), (name, prec, l)
