@@ -45,7 +45,16 @@ from .tree import Tree, root_cube, occupancy_depth, transfer_offset
 PRECISION_UNIT = {'fp64': qd.U_FP64, 'df': qd.U_DF, 'fp32': qd.U_FP32}
 # acceptance factor of the stability rule per precision (see module docstring)
 PRECISION_FACTOR = {'fp64': 1.0 / 16.0, 'df': 1.0 / 16.0, 'fp32': 1.0}
-MIN_KA = 6.0
+MIN_KA = 6.0          # one buffer box
+MIN_KA_TWO_BUFFER = 0.0
+
+
+def min_ka(buffer):
+    """Smallest k a_l of an active level: 6 with one buffer box (boxes of about a wavelength:
+    the Gegenbauer series converges only geometrically, ratio up to alpha sqrt(3)/2, for pairs
+    near opposite corners of small boxes); none with two (ratio at most alpha sqrt(3)/3; the
+    round-off rule alone decides)."""
+    return MIN_KA if buffer == 1 else MIN_KA_TWO_BUFFER
 
 
 def alpha_ladder(eps):
@@ -82,7 +91,7 @@ class Plan:
         if alphas is None:
             alphas = alpha_ladder(self.eps)
         for l in range(2, dmax + 1):
-            if self.kappa * side / float(2 ** l) < MIN_KA:
+            if self.kappa * side / float(2 ** l) < min_ka(self.buffer):
                 break
             chosen = None
             for alpha in alphas:

@@ -432,17 +432,24 @@ __global__ void __launch_bounds__(32 * kL2TabWarps) k_l2t_tab(
                 shq[pp * kRC + r] = Q;
             }
             __syncthreads();
-            for (int i = 0; i < kPts; ++i) {
-                const int ti = warp + kL2TabWarps * i;
-                if (ti >= n) break;
-                const cxd* Er = E + (int64_t)(t0 + c0 + ti) * qv.npair + pb;
-                for (int pp = lane; pp < pn; pp += 32) {
-                    cxd e = ldg_cx(Er + pp);
-                    if (kConj) e.y = -e.y;
-                    for (int r = 0; r < rn; ++r) {
-                        const cxd P = shp[pp * kRC + r], Q = shq[pp * kRC + r];
-                        acc[i][r].x += P.x * e.x - Q.y * e.y;
-                        acc[i][r].y += P.y * e.x + Q.x * e.y;
+            // the warp's points side by side: kPts independent table loads in flight per lane,
+            // and each staged P, Q serves all of them (points past the chunk read nothing and
+            // add zeros)
+#pragma unroll 2
+            for (int pp = lane; pp < pn; pp += 32) {
+                cxd e[kPts];
+#pragma unroll
+                for (int i = 0; i < kPts; ++i) {
+                    const int ti = warp + kL2TabWarps * i;
+                    e[i] = ti < n ? ldg_cx(E + (int64_t)(t0 + c0 + ti) * qv.npair + pb + pp) : mk<double>(0, 0);
+                    if (kConj) e[i].y = -e[i].y;
+                }
+                for (int r = 0; r < rn; ++r) {
+                    const cxd P = shp[pp * kRC + r], Q = shq[pp * kRC + r];
+#pragma unroll
+                    for (int i = 0; i < kPts; ++i) {
+                        acc[i][r].x += P.x * e[i].x - Q.y * e[i].y;
+                        acc[i][r].y += P.y * e[i].x + Q.x * e[i].y;
                     }
                 }
             }

@@ -33,7 +33,11 @@ namespace hfmm {
 static const double kPi = 3.14159265358979323846;
 static const double kTwoPi = 2.0 * kPi;
 static const double kFourPi2 = 4.0 * kPi * kPi;
-static const double kMinKa = 6.0;
+// smallest kappa a_l of an active level: one buffer box needs boxes of about a wavelength
+// (the Gegenbauer series converges only geometrically, ratio up to alpha sqrt(3)/2, for
+// pairs near opposite corners of small boxes); with two buffer boxes the ratio is at most
+// alpha sqrt(3)/3 and the round-off rule alone decides
+static double min_ka(int buffer) { return buffer >= 2 ? 0.0 : 6.0; }
 
 void Quadrature::finalize() {
     off.assign(nphi.size() + 1, 0);
@@ -679,7 +683,7 @@ std::string build_host_plan(HostPlan& hp) {
     int lf = 1;
     for (int l = 2; l <= hp.occ_depth && l < kMaxLevels; ++l) {
         // only boxes of about a wavelength or larger (k a_l >= 6) use the diagonal form
-        if (hp.kappa * (hp.side / (double)(1u << l)) < kMinKa) break;
+        if (hp.kappa * (hp.side / (double)(1u << l)) < min_ka(hp.buffer)) break;
         bool ok = false;
         for (double alpha : hp.alphas) {
             LevelPlan cand;

@@ -67,7 +67,7 @@ def test_levels_and_quadrature_integers(pair):
             assert (li["ell"], li["ntheta"], li["K"]) == (lp.ell, lp.ntheta, lp.K), (name, prec, l)
             assert li["alpha"] == lp.alpha
             assert li["alpha"] in ofmm.alpha_ladder(orc.eps)
-            assert orc.kappa * lp.a >= ofmm.MIN_KA       # only boxes of about a wavelength or more
+            assert orc.kappa * lp.a >= ofmm.min_ka(orc.buffer)   # one buffer box: about a wavelength or more
             assert li["precision"] == orc.level_precision[l]
             assert np.array_equal(lib.debug_get("NPHI", l), lp.nphi)
             assert li["round_est"] == pytest.approx(lp.rounding_estimate(
