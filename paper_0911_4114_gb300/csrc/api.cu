@@ -193,7 +193,19 @@ hfmm_status upload_level(hfmm_plan_s* P, int l) {
     if ((int64_t)pairs.size() * 2 != q.K) return fail(HFMM_ERR_STATE, "antipodal pairs do not cover the grid");
     int2* dpair;
     TRY(upload(P, &dpair, pairs));
-    d.qv = QuadView{q.ntheta, half + 1, q.K, nphi, off, dshat, dw, dpair, (int64_t)pairs.size()};
+    std::vector<float> asp(6 * q.K);
+    {
+        const double kt = hp.kappa / (2.0 * 3.14159265358979323846);
+        for (int64_t k = 0; k < q.K; ++k)
+            for (int c = 0; c < 3; ++c) {
+                const double a = kt * shat[3 * k + c];
+                asp[6 * k + c] = (float)a;
+                asp[6 * k + 3 + c] = (float)(a - (double)(float)a);
+            }
+    }
+    float* dasp;
+    TRY(upload(P, &dasp, asp));
+    d.qv = QuadView{q.ntheta, half + 1, q.K, nphi, off, dshat, dw, dpair, (int64_t)pairs.size(), dasp};
     {
         std::vector<df> sd(3 * q.K);
         const double kt = hp.kappa / (2.0 * 3.14159265358979323846);

@@ -2,6 +2,8 @@
 // Signatures are stored box-major: sig[(box * R + r) * K + k], k over the half grid
 // (rows n = 0..ntheta/2, N_phi(theta_n) samples each).
 #pragma once
+#include <type_traits>
+
 #include "cx.cuh"
 #include "df.cuh"
 #include "fft.cuh"
@@ -23,6 +25,10 @@ struct QuadView {
     // (n, m) pairs with (N_theta/2 - n, m + N_phi/2); npair = K / 2.
     const int2* pair;
     int64_t npair;
+    // (K, 6) floats per sample: kappa s_k / (2 pi) split into a leading float and the float
+    // rounding of the rest (hi x, y, z, lo x, y, z): float32 levels form plane-wave phases
+    // from these without float64 arithmetic
+    const float* asplit;
 };
 
 struct BoxView {
@@ -183,6 +189,31 @@ __device__ __forceinline__ double turns(double kappa_turns, const double* s, dou
     return p - rint(p);
 }
 
+// The same reduced phase in float32 arithmetic only, for float32 levels (float64 runs at 1/64
+// of the float32 rate on this GPU).  a = kappa s / (2 pi) and d are given as float pairs
+// (hi, lo), each exact to about 2^-48.  The leading products a_hi d_hi are formed exactly (FMA
+// error terms) and summed with Knuth's TwoSum, so the integer part drops out exactly
+// (s - rint(s) is exact in float); the error terms and the cross products a_hi d_lo, a_lo d_hi
+// are added to the reduced fraction.  Absolute error about 2^-25 turns, the size of the
+// rounding of a float64 phase reduced into [-1/2, 1/2] and converted to float.
+__device__ __forceinline__ float two_sum_err(float a, float b, float s) {
+    const float bb = s - a;
+    return (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ float turns_f(const float* a, const float* d) {
+    const float p0 = a[0] * d[0], p1 = a[1] * d[1], p2 = a[2] * d[2];
+    const float e0 = fmaf(a[0], d[0], -p0), e1 = fmaf(a[1], d[1], -p1), e2 = fmaf(a[2], d[2], -p2);
+    const float s1 = p0 + p1;
+    const float s2 = s1 + p2;
+    const float err = two_sum_err(p0, p1, s1) + two_sum_err(s1, p2, s2);
+    const float cross = fmaf(a[0], d[3], fmaf(a[1], d[4], fmaf(a[2], d[5], fmaf(a[3], d[0], fmaf(a[4], d[1], a[5] * d[2])))));
+    return (s2 - rintf(s2)) + ((err + (e0 + e1 + e2)) + cross);
+}
+__device__ __forceinline__ void split_f(double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
 // Points to signature: M_b(s_k) = w_k sum_{j in b} exp(i k s_k . sign (p_j - c_b)) q_j.
 // S2M: sources, sign +1, no weights.  Transposed L2T: targets, sign -1, quadrature weights.
 // One thread per antipodal pair (k, k'): with E = C + iS the plane wave of s_k, it sums
@@ -194,18 +225,23 @@ __global__ void k_s2m(BoxView bx, QuadView qv, const int32_t* __restrict__ sstar
                       const double* __restrict__ sy, const double* __restrict__ sz,
                       const cxd* __restrict__ qs, int R_, double kappa_turns, cx<R>* __restrict__ M,
                       double sign, const double* __restrict__ wk) {
+    constexpr bool kF32 = std::is_same<R, float>::value;   // float32 level: float-only phases
     __shared__ double shd[kS2MThreads * 3];
+    __shared__ float shf[kS2MThreads * 6];
     __shared__ cxd shq[kS2MThreads * kRC];
     const int b = blockIdx.x;
     const int64_t p = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
     const bool active = p < qv.npair;
     int2 kk2 = make_int2(0, 0);
     double s[3] = {0, 0, 0};
+    float af[6] = {0, 0, 0, 0, 0, 0};
     if (active) {
         kk2 = qv.pair[p];
         s[0] = qv.shat[3 * kk2.x];
         s[1] = qv.shat[3 * kk2.x + 1];
         s[2] = qv.shat[3 * kk2.x + 2];
+        if (kF32)
+            for (int c = 0; c < 6; ++c) af[c] = qv.asplit[6 * (int64_t)kk2.x + c];
     }
     const int s0 = sstart[b], sc = scount[b];
     const double cxx = bx.center[3 * b], cyy = bx.center[3 * b + 1], czz = bx.center[3 * b + 2];
@@ -218,16 +254,24 @@ __global__ void k_s2m(BoxView bx, QuadView qv, const int32_t* __restrict__ sstar
             __syncthreads();
             if (threadIdx.x < jn) {
                 const int j = s0 + jb + threadIdx.x;
-                shd[3 * threadIdx.x] = sign * (sx[j] - cxx);
-                shd[3 * threadIdx.x + 1] = sign * (sy[j] - cyy);
-                shd[3 * threadIdx.x + 2] = sign * (sz[j] - czz);
+                const double dd[3] = {sign * (sx[j] - cxx), sign * (sy[j] - cyy), sign * (sz[j] - czz)};
+                for (int c = 0; c < 3; ++c) {
+                    shd[3 * threadIdx.x + c] = dd[c];
+                    split_f(dd[c], shf[6 * threadIdx.x + c], shf[6 * threadIdx.x + 3 + c]);
+                }
                 for (int r = 0; r < rn; ++r) shq[threadIdx.x * kRC + r] = qs[(int64_t)j * R_ + r0 + r];
             }
             __syncthreads();
             if (active)
                 for (int jj = 0; jj < jn; ++jj) {
-                    const double t = turns(kappa_turns, s, shd[3 * jj], shd[3 * jj + 1], shd[3 * jj + 2]);
-                    const cx<R> e = plane_wave<R>(t);
+                    cx<R> e;
+                    if (kF32) {
+                        float sn, cs;
+                        sincospif(2.0f * turns_f(af, &shf[6 * jj]), &sn, &cs);
+                        e = mk<R>(cs, sn);
+                    } else {
+                        e = plane_wave<R>(turns(kappa_turns, s, shd[3 * jj], shd[3 * jj + 1], shd[3 * jj + 2]));
+                    }
                     for (int r = 0; r < rn; ++r) {
                         const cx<R> q = cvt<R>(shq[jj * kRC + r]);
                         U[r] = U[r] + e.x * q;
@@ -264,7 +308,9 @@ __global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstar
                       const double* __restrict__ ty, const double* __restrict__ tz,
                       const cx<R>* __restrict__ L, int R_, double kappa_turns, cxd* __restrict__ phis,
                       double sign, const double* __restrict__ wk) {
+    constexpr bool kF32 = std::is_same<R, float>::value;   // float32 level: float-only phases
     __shared__ double shs[kL2TThreads * 3];
+    __shared__ float shf[kL2TThreads * 6];
     __shared__ cx<R> shp[kL2TThreads * kRC], shq[kL2TThreads * kRC];
     const int b = blockIdx.x;
     const int t0 = tstart[b], tc = tcount[b];
@@ -273,10 +319,14 @@ __global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstar
     const int ti = blockIdx.y * kL2TThreads + threadIdx.x;
     const bool active = ti < tc;
     double dx = 0, dy = 0, dz = 0;
+    float df6[6] = {0, 0, 0, 0, 0, 0};
     if (active) {
         dx = sign * (cxx - tx[t0 + ti]);
         dy = sign * (cyy - ty[t0 + ti]);
         dz = sign * (czz - tz[t0 + ti]);
+        split_f(dx, df6[0], df6[3]);
+        split_f(dy, df6[1], df6[4]);
+        split_f(dz, df6[2], df6[5]);
     }
     for (int r0 = 0; r0 < R_; r0 += kRC) {
         const int rn = kRC == 1 ? 1 : min(kRC, R_ - r0);
@@ -290,6 +340,8 @@ __global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstar
                 shs[3 * threadIdx.x] = qv.shat[3 * kk2.x];
                 shs[3 * threadIdx.x + 1] = qv.shat[3 * kk2.x + 1];
                 shs[3 * threadIdx.x + 2] = qv.shat[3 * kk2.x + 2];
+                if (kF32)
+                    for (int c = 0; c < 6; ++c) shf[6 * threadIdx.x + c] = qv.asplit[6 * (int64_t)kk2.x + c];
                 for (int r = 0; r < rn; ++r) {
                     const cx<R>* Lb = L + ((int64_t)b * R_ + r0 + r) * qv.K;
                     const cx<R> A = wk ? (R)wk[kk2.x] * Lb[kk2.x] : Lb[kk2.x];
@@ -301,8 +353,14 @@ __global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstar
             __syncthreads();
             if (active)
                 for (int kk = 0; kk < pn; ++kk) {
-                    const double t = turns(kappa_turns, &shs[3 * kk], dx, dy, dz);
-                    const cx<R> e = plane_wave<R>(t);
+                    cx<R> e;
+                    if (kF32) {
+                        float sn, cs;
+                        sincospif(2.0f * turns_f(&shf[6 * kk], df6), &sn, &cs);
+                        e = mk<R>(cs, sn);
+                    } else {
+                        e = plane_wave<R>(turns(kappa_turns, &shs[3 * kk], dx, dy, dz));
+                    }
                     for (int r = 0; r < rn; ++r) {
                         const cx<R> P = shp[kk * kRC + r], Q = shq[kk * kRC + r];
                         acc[r].x += P.x * e.x - Q.y * e.y;
@@ -447,9 +505,9 @@ __global__ void __launch_bounds__(32 * kL2TabWarps) k_l2t_tab(
                 for (int r = 0; r < rn; ++r) {
                     const cxd P = shp[pp * kRC + r], Q = shq[pp * kRC + r];
 #pragma unroll
-                    for (int i = 0; i < kPts; ++i) {
-                        acc[i][r].x += P.x * e[i].x - Q.y * e[i].y;
-                        acc[i][r].y += P.y * e[i].x + Q.x * e[i].y;
+                    for (int i = 0; i < kPts; ++i) {   // four FMA, no separate product or sum
+                        acc[i][r].x = fma(P.x, e[i].x, fma(-Q.y, e[i].y, acc[i][r].x));
+                        acc[i][r].y = fma(P.y, e[i].x, fma(Q.x, e[i].y, acc[i][r].y));
                     }
                 }
             }
