@@ -35,7 +35,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "FMM apply Mpoints*RHS/s at stated rel. err; mixed vs FP64 on one GB300"
 HEADLINE = dict(workload="ellipsoid2m", points=2097152, surface="(1, 0.5, 0.25) ellipsoid, uniform by area",
-                kappa=200.0, eps=1e-4, nrhs=1, charges="complex64 N(0,1)", precision="mixed")
+                kappa=200.0, eps=1e-4, nrhs=1, charges="complex64 N(0,1)", precision="mixed",
+                plan_shape="tuned (buffer boxes and leaf level chosen by the plan's cost model)")
+AUTO = dict(buffer=0)     # plan shape chosen by the library's cost model
 TIGHT_EPS = 1e-8
 REL_ERR_TARGETS = 1000
 ORACLE_DIRECT_TARGETS = 64
@@ -164,10 +166,11 @@ class OracleFmmSampler:
     Signatures fed to the sampled stages are zeros of the right shapes (the arithmetic does not
     depend on their values)."""
 
-    def __init__(self, s, t, q, kappa, eps, precision="mixed", leaf_boxes=12, level_boxes=3, seed=0):
+    def __init__(self, s, t, q, kappa, eps, precision="mixed", leaf_boxes=12, level_boxes=3, seed=0,
+                 buffer=1, depth=0):
         from oracle import fmm as ofmm
         self.ofmm = ofmm
-        self.plan = ofmm.Plan(s, t, kappa, eps, precision=precision)
+        self.plan = ofmm.Plan(s, t, kappa, eps, precision=precision, buffer=buffer, depth=depth)
         self.q = np.asarray(q, dtype=np.complex128).reshape(len(s), -1)
         self.nt = len(t)
         tr = self.plan.tree
@@ -230,7 +233,8 @@ class OracleFmmSampler:
 
     def sample_text(self):
         lf = self.plan.tree.depth
-        return (f"oracle float64 Fourier FMM at the same plan (L_f = {lf}), timed on {len(self.leaf)} seeded leaf "
+        return (f"oracle float64 Fourier FMM (buffer boxes {self.plan.buffer}, L_f = {lf}), timed on "
+                f"{len(self.leaf)} seeded leaf "
                 f"boxes (near field, S2M, L2T) and {max(len(v) for v in self.level.values()) if self.level else 0} "
                 f"boxes per level (M2M, M2L, L2L), extrapolated per stage by pairs / points / boxes / list "
                 f"entries; plan and transfer tables excluded")
@@ -418,23 +422,25 @@ def extras_run(timer, dev, steps):
     o = torch.empty((len(t), 1), dtype=torch.complex64, device=dev)
     sph = {}
     for prec in ("mixed", "fp64"):
-        p = FmmPlan(s, t, 64.0, 1e-6, precision=prec)
+        p = FmmPlan(s, t, 64.0, 1e-6, precision=prec, **AUTO)
         ms = timer.run(lambda: p.apply(q, out=o), max(3, steps // 2), 2)
         sph[prec] = {"ms_per_step": ms, "value": len(t) / (ms * 1e-3) / 1e6}
         if prec == "mixed":
             sph["stage_ms"] = timer.stages(p, lambda: p.apply(q, out=o), 3)
             sph["lf"] = p.info()["lf"]
+            sph["buffer"] = p.info()["buffer"]
         del p
     out["sphere262k"] = dict(sph, unit="Mpoints*RHS/s", kappa=64.0, eps=1e-6, charges="complex64")
     # 524,288 points in the unit cube, 64 right-hand sides, kappa 40, eps 1e-5
     cs, ct = wl.points("cube512k_rhs64")
-    cplan = FmmPlan(cs, ct, 40.0, 1e-5, precision="mixed", max_rhs=64)
+    cplan = FmmPlan(cs, ct, 40.0, 1e-5, precision="mixed", max_rhs=64, **AUTO)
     cq = torch.as_tensor(wl.charges(len(cs), 64, wl.rng(3, salt=1)).astype(np.complex64)).to(dev)
     cout = torch.empty((len(ct), 64), dtype=torch.complex64, device=dev)
     cms = timer.run(lambda: cplan.apply(cq, out=cout), 2, 1)
     ci = cplan.info()
     out["cube512k_rhs64"] = {"ms_per_step": cms, "value": len(ct) * 64 / (cms * 1e-3) / 1e6,
                              "unit": "Mpoints*RHS/s", "nrhs": 64, "kappa": 40.0, "eps": 1e-5, "lf": ci["lf"],
+                             "buffer": ci["buffer"],
                              "p2p_pairs": ci["p2p_pairs"],
                              "stage_ms": timer.stages(cplan, lambda: cplan.apply(cq, out=cout), 1),
                              "levels": {str(l): v["precision"] for l, v in ci["levels"].items()}}
@@ -444,7 +450,7 @@ def extras_run(timer, dev, steps):
     sizes = np.exp(g.uniform(np.log(8192), np.log(131072), 32)).astype(int)
     kappas = g.uniform(10.0, 60.0, 32)
     probs = [(wl.cube(int(n), g), float(k)) for n, k in zip(sizes, kappas)]
-    batch = FmmBatch([(x, x, k, 1e-5) for x, k in probs], precision="mixed", max_rhs=4)
+    batch = FmmBatch([(x, x, k, 1e-5) for x, k in probs], precision="mixed", max_rhs=4, **AUTO)
     qs = [torch.as_tensor(wl.charges(len(x), 4, g).astype(np.complex64)).to(dev) for x, _ in probs]
     outs = [torch.empty((len(x), 4), dtype=torch.complex64, device=dev) for x, _ in probs]
     bms = timer.run(lambda: batch.apply(qs, outs), max(3, steps // 2), 2)
@@ -477,7 +483,7 @@ def main():
     o128 = torch.empty((nt, 1), dtype=torch.complex128, device=dev)
 
     t0 = time.perf_counter()
-    mp = FmmPlan(s, t, kappa, eps, precision="mixed")
+    mp = FmmPlan(s, t, kappa, eps, precision="mixed", **AUTO)
     plan_seconds = time.perf_counter() - t0
     info = mp.info()
 
@@ -511,10 +517,11 @@ def main():
 
     fp64 = None
     if not args.no_fp64:
-        p = FmmPlan(s, t, kappa, eps, precision="fp64")
+        p = FmmPlan(s, t, kappa, eps, precision="fp64", **AUTO)
         ms = timer.run(lambda: p.apply(q64, out=o64), 2, 1)
         errs["fp64"] = rel(o64[:, 0].cpu().numpy().astype(np.complex128)[idx], ref)
         fp64 = {"value": nt / (ms * 1e-3) / 1e6, "ms_per_step": ms, "rel_err": errs["fp64"], "lf": p.info()["lf"],
+                "buffer": p.info()["buffer"],
                 "stage_ms": timer.stages(p, lambda: p.apply(q64, out=o64), 1)}
         del p
 
@@ -522,11 +529,11 @@ def main():
     if not args.no_tight:
         tight = {"eps": TIGHT_EPS, "charges": "complex128 (the complex64 values)"}
         for prec in (("mixed",) if args.no_fp64 else ("mixed", "fp64")):
-            p = FmmPlan(s, t, kappa, TIGHT_EPS, precision=prec)
+            p = FmmPlan(s, t, kappa, TIGHT_EPS, precision=prec, **AUTO)
             ms = timer.run(lambda: p.apply(q128, out=o128), 1 if prec == "fp64" else 2, 1)
             got = o128[:, 0].cpu().numpy()[idx]
             tight[prec] = {"value": nt / (ms * 1e-3) / 1e6, "ms_per_step": ms, "rel_err": rel(got, ref),
-                           "lf": p.info()["lf"]}
+                           "lf": p.info()["lf"], "buffer": p.info()["buffer"]}
             if prec == "mixed":
                 tight[prec]["stage_ms"] = timer.stages(p, lambda: p.apply(q128, out=o128), 1)
             del p
@@ -542,7 +549,8 @@ def main():
         oidx, ovals, osecs = oracle_direct_sample(s, t, q_host.astype(np.complex128), kappa,
                                                   ORACLE_DIRECT_TARGETS, 20260103)
         errs["mixed_vs_oracle_direct"] = rel(head_out[oidx], ovals)
-        smp = OracleFmmSampler(s, t, q_host.astype(np.complex128), kappa, eps)
+        smp = OracleFmmSampler(s, t, q_host.astype(np.complex128), kappa, eps, buffer=info["buffer"],
+                               depth=info["lf"])   # the GPU run's plan shape
         fmm_secs, parts = smp.time_once()
         cpu = {"value": nt / fmm_secs / 1e6, "unit": "Mpoints*RHS/s", "cores": oracle_threads(), "kind": "oracle",
                "sample": smp.sample_text(), "seconds_per_apply_extrapolated": fmm_secs,
@@ -576,8 +584,10 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+df+f64", "data": "synthetic",
             "config": dict(HEADLINE, points=nt, parallelism="replicas" if world > 1 else "single",
                            l2="flushed before every timed apply (512 MiB write)",
-                           lf=info["lf"], levels={str(l): v for l, v in info["levels"].items()},
-                           p2p_pairs=info["p2p_pairs"]),
+                           lf=info["lf"], buffer=info["buffer"],
+                           levels={str(l): v for l, v in info["levels"].items()},
+                           p2p_pairs=info["p2p_pairs"],
+                           predicted_ms={f"b{b}_L{l}": round(v, 2) for (b, l), v in info["predicted_ms"].items()}),
             "rel_err": errs["mixed"],
             "rel_err_ref": f"float64 direct sum at {len(idx)} seeded targets (library float64 kernel); "
                            f"mixed_vs_oracle_direct: oracle direct sum at {ORACLE_DIRECT_TARGETS} targets",

@@ -94,9 +94,14 @@ typedef struct {
      * double-float never use tables. */
     int64_t leaf_table_bytes;
     /* buffer boxes between a box and its interaction list (Section 3.3.3): 1 (default, the
-     * common case: |r0| >= 2 a_l, neighbour lists of 3^3 boxes, 316 transfer vectors) or 2
+     * common case: |r0| >= 2 a_l, neighbour lists of 3^3 boxes, 316 transfer vectors), 2
      * (|r0| >= 3 a_l: a smaller truncation l and more stable levels for the same eps,
-     * neighbour lists of 5^3 boxes, 1206 transfer vectors) */
+     * neighbour lists of 5^3 boxes, 1206 transfer vectors; no kappa a_l >= 6 limit), or 0:
+     * the plan-shape tuner chooses the buffer and the leaf level (at most the deepest stable
+     * level) that minimise a cost model of one apply (near-field pairs, plane-wave products,
+     * interaction-list entries and re-quadrature samples weighed with per-unit times measured
+     * on a GB300, for max_rhs right-hand sides); hfmm_query reports the choice and the
+     * predicted times.  The tuned plan equals the plan with that buffer and depth = lf. */
     int buffer;
 } hfmm_options;
 
@@ -138,6 +143,9 @@ typedef struct {
     int leaf_tables;
     int64_t leaf_table_bytes;   /* device bytes of those tables (0 without) */
     int buffer;                 /* buffer boxes of the plan (1 or 2) */
+    int tuned;                  /* 1 when the plan-shape tuner chose buffer and lf */
+    /* the tuner's predicted apply time in ms for [buffer][leaf level] (0: not a candidate) */
+    double predicted_ms[3][HFMM_MAX_LEVELS];
 } hfmm_info;
 
 /* Fill *opt with the defaults listed above. */

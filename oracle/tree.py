@@ -164,60 +164,88 @@ class Tree:
         self.tgt_start = np.searchsorted(tkey_sorted, lk, side='left')
         self.tgt_count = np.searchsorted(tkey_sorted, lk, side='right') - self.tgt_start
 
-        # lists
+        # lists, built per box on first use (ilist[l][a], vlist[l][a], nlist[a])
+        self._where = {}
+        self._ilists = {}
         self.ilist = [None] * (D + 1)
         self.vlist = [None] * (D + 1)
         for l in range(2, D + 1):
-            self.ilist[l], self.vlist[l] = self._interaction_lists(l)
-        self.nlist = self._neighbour_lists(D)
+            n = len(self.levels[l]['key'])
+            self.ilist[l] = _PerBox(n, lambda a, l=l: self._interaction_list(l, a)[0])
+            self.vlist[l] = _PerBox(n, lambda a, l=l: self._interaction_list(l, a)[1])
+        self.nlist = _PerBox(len(self.levels[D]['key']), lambda a: self._neighbour_list(D, a))
 
     def _lookup(self, l):
-        return {tuple(int(c) for c in self.levels[l]['idx'][i]): i
-                for i in range(len(self.levels[l]['key']))}
+        if l not in self._where:
+            self._where[l] = {tuple(int(c) for c in self.levels[l]['idx'][i]): i
+                              for i in range(len(self.levels[l]['key']))}
+        return self._where[l]
 
-    def _interaction_lists(self, l):
+    def _interaction_list(self, l, a):
+        """(box positions, transfer-vector indices) of I(box a at level l), by Morton key."""
+        if (l, a) in self._ilists:
+            return self._ilists[(l, a)]
         lev = self.levels[l]
         where = self._lookup(l)
         nb = 2 ** l
         bw = self.buffer
         span = 2 * bw + 1
-        il, vl = [], []
-        for a in range(len(lev['key'])):
-            ia = lev['idx'][a]
-            pa = ia >> 1
-            found = []
-            # children of the parent's neighbours (Chebyshev distance <= buffer)
-            for dp in np.ndindex(span, span, span):
-                pn = pa + np.array(dp) - bw
-                for dc in np.ndindex(2, 2, 2):
-                    ib = pn * 2 + np.array(dc)
-                    if np.any(ib < 0) or np.any(ib >= nb):
-                        continue
-                    d = ib - ia
-                    if np.max(np.abs(d)) <= bw:
-                        continue
-                    b = where.get(tuple(int(c) for c in ib))
-                    if b is not None:
-                        found.append((lev['key'][b], b, transfer_index(d, bw)))
-            found.sort()
-            il.append(np.array([f[1] for f in found], dtype=np.int64))
-            vl.append(np.array([f[2] for f in found], dtype=np.int64))
-        return il, vl
+        ia = lev['idx'][a]
+        pa = ia >> 1
+        found = []
+        # children of the parent's neighbours (Chebyshev distance <= buffer)
+        for dp in np.ndindex(span, span, span):
+            pn = pa + np.array(dp) - bw
+            for dc in np.ndindex(2, 2, 2):
+                ib = pn * 2 + np.array(dc)
+                if np.any(ib < 0) or np.any(ib >= nb):
+                    continue
+                d = ib - ia
+                if np.max(np.abs(d)) <= bw:
+                    continue
+                b = where.get(tuple(int(c) for c in ib))
+                if b is not None:
+                    found.append((lev['key'][b], b, transfer_index(d, bw)))
+        found.sort()
+        out = (np.array([f[1] for f in found], dtype=np.int64),
+               np.array([f[2] for f in found], dtype=np.int64))
+        self._ilists[(l, a)] = out
+        return out
 
-    def _neighbour_lists(self, l):
+    def _neighbour_list(self, l, a):
         lev = self.levels[l]
         where = self._lookup(l)
         bw = self.buffer
         span = 2 * bw + 1
-        out = []
-        for a in range(len(lev['key'])):
-            ia = lev['idx'][a]
-            found = []
-            for d in np.ndindex(span, span, span):
-                ib = ia + np.array(d) - bw
-                b = where.get(tuple(int(c) for c in ib))
-                if b is not None:
-                    found.append((lev['key'][b], b))
-            found.sort()
-            out.append(np.array([f[1] for f in found], dtype=np.int64))
-        return out
+        ia = lev['idx'][a]
+        found = []
+        for d in np.ndindex(span, span, span):
+            ib = ia + np.array(d) - bw
+            b = where.get(tuple(int(c) for c in ib))
+            if b is not None:
+                found.append((lev['key'][b], b))
+        found.sort()
+        return np.array([f[1] for f in found], dtype=np.int64)
+
+
+class _PerBox:
+    """Per-box lists computed by `fn(box)` on first access and kept (indexable, iterable)."""
+
+    def __init__(self, n, fn):
+        self.n, self.fn, self.cache = n, fn, {}
+
+    def __len__(self):
+        return self.n
+
+    def __getitem__(self, a):
+        a = int(a)
+        if a < 0:
+            a += self.n
+        if not 0 <= a < self.n:
+            raise IndexError(a)
+        if a not in self.cache:
+            self.cache[a] = self.fn(a)
+        return self.cache[a]
+
+    def __iter__(self):
+        return (self[a] for a in range(self.n))

@@ -901,7 +901,7 @@ hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, 
         return fail(HFMM_ERR_ARG, "unknown precision policy");
     if (opt.flags & ~HFMM_FLAG_REQUIRE_FAR) return fail(HFMM_ERR_ARG, "unknown flag bits");
     if (opt.leaf_table_bytes < -1) return fail(HFMM_ERR_ARG, "leaf_table_bytes must be -1, 0 or positive");
-    if (opt.buffer != 1 && opt.buffer != 2) return fail(HFMM_ERR_ARG, "buffer must be 1 or 2");
+    if (opt.buffer < 0 || opt.buffer > 2) return fail(HFMM_ERR_ARG, "buffer must be 0 (chosen by the plan), 1 or 2");
     std::vector<double> alphas;
     // default ladder: (0.8, 0.6), or (0.9, 0.8) below eps = 1e-7, where the few terms that
     // l(0.8) keeps beyond k|r| of a corner pair no longer reach eps
@@ -946,6 +946,11 @@ hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, 
         hp.depth_req = opt.depth;
         hp.precision = opt.precision;
         hp.buffer = opt.buffer;
+        // inputs of the plan-shape tuner (buffer = 0)
+        hp.model_rhs = opt.max_rhs;
+        hp.model_near = opt.precision == HFMM_PREC_MIXED ? (eps >= 1e-6 ? kFP32 : (eps >= 1e-11 ? kDF : kFP64)) : kFP64;
+        hp.model_sym = ns == nt && (sources == targets || std::memcmp(sources, targets, sizeof(double) * 3 * ns) == 0);
+        hp.model_table_bytes = opt.leaf_table_bytes;
         hp.has_root = opt.has_root;
         for (int k = 0; k < 4; ++k) hp.root[k] = opt.root[k];
         std::string e = build_host_plan(hp);
@@ -1288,6 +1293,9 @@ hfmm_status hfmm_query(hfmm_plan_t P, hfmm_info* info) {
     info->near_precision = P->near_prec == kFP32 ? HFMM_LEVEL_FP32 : (P->near_prec == kDF ? HFMM_LEVEL_DF : HFMM_LEVEL_FP64);
     info->leaf_tables = P->tab_s != nullptr;
     info->buffer = hp.buffer;
+    info->tuned = hp.tuned;
+    for (int b = 0; b < 3; ++b)
+        for (int l = 0; l < HFMM_MAX_LEVELS; ++l) info->predicted_ms[b][l] = hp.predicted_ms[b][l];
     info->leaf_table_bytes = P->tab_bytes;
     if (P->ev_recorded) {
         if (cudaEventSynchronize(P->ev[HFMM_N_STAGES]) != cudaSuccess)

@@ -60,7 +60,17 @@ struct HostPlan {
     std::vector<double> alphas;
     double eps_scale = 0.25;
     int max_leaf = 64, depth_req = 0, precision = 0;
-    int buffer = 1;      // buffer boxes between a box and its interaction list (Section 3.3.3)
+    int buffer = 1;      // buffer boxes between a box and its interaction list (Section 3.3.3);
+                         // 0 on input: chosen by the plan-shape tuner (1 or 2 on output)
+    // inputs of the plan-shape tuner's cost model: right-hand sides, near-field arithmetic,
+    // sources = targets, bytes allowed for float64 leaf tables (-1: no explicit limit)
+    int model_rhs = 1, model_near = 0;
+    bool model_sym = false;
+    int64_t model_table_bytes = -1;
+    // tuner result: 1 when the buffer / leaf level were chosen by the cost model, and the
+    // predicted apply time (ms) of every candidate [buffer][leaf level] (0 = not a candidate)
+    int tuned = 0;
+    double predicted_ms[3][kMaxLevels] = {};
     int has_root = 0;
     double root[4] = {0, 0, 0, 1};
     // tree

@@ -631,6 +631,207 @@ static void build_tree(HostPlan& hp) {
 }
 
 // ---------------------------------------------------------------------------
+// active levels for one buffer choice: alpha ladder outer, precision inner, precision never
+// decreasing with depth; *lf = the deepest accepted level (levels stop at the first failure)
+static std::vector<LevelPlan> plan_levels(const HostPlan& hp, int buffer, int dmax, int* lf_out) {
+    std::vector<LevelPlan> lps(kMaxLevels);
+    std::vector<int> allowed = (hp.precision == 1) ? std::vector<int>{kFP32, kDF, kFP64}
+                                                   : std::vector<int>{kFP64};
+    int lf = 1;
+    for (int l = 2; l <= dmax && l < kMaxLevels; ++l) {
+        // one buffer box: only boxes of about a wavelength or larger use the diagonal form
+        if (hp.kappa * (hp.side / (double)(1u << l)) < min_ka(buffer)) break;
+        bool ok = false;
+        for (double alpha : hp.alphas) {
+            LevelPlan cand;
+            plan_level(hp.kappa, hp.side / (double)(1u << l), hp.eps_l, alpha, buffer, cand);
+            for (int p : allowed) {
+                const double u = std::ldexp(1.0, p == kFP32 ? -24 : (p == kDF ? -48 : -53));
+                const double f = (p == kFP32) ? 1.0 : 1.0 / 16.0;
+                double est = round_off_estimate(cand.quad.ell, hp.kappa, cand.r0, cand.quad.K, u);
+                if (est <= hp.eps_l * f) {
+                    cand.prec = p;
+                    cand.est = est;
+                    lps[l] = cand;
+                    ok = true;
+                    allowed.erase(allowed.begin(), std::find(allowed.begin(), allowed.end(), p));
+                    break;
+                }
+            }
+            if (ok) break;
+        }
+        if (!ok) break;
+        lf = l;
+    }
+    if (dmax < 2) lf = dmax;
+    *lf_out = lf;
+    return lps;
+}
+
+// ---------------------------------------------------------------------------
+// Plan-shape tuner: the number of buffer boxes (1 or 2, Section 3.3.3) and the leaf level
+// L_f <= the deepest stable level, chosen by a cost model of one apply.  Two buffer boxes
+// shrink l and keep deeper levels stable (smaller near field, cheaper leaf precision) but
+// lengthen interaction lists (up to 875 entries) and neighbour lists (5^3 boxes); a shallower
+// leaf trades far-field work for near-field pairs.  The model counts, for each candidate,
+// near-field pairs, (point, antipodal sample pair) products of S2M and L2T, interaction-list
+// entries x samples of M2L and boxes x samples of the re-quadratures, and weighs them with
+// per-unit times measured on a GB300 (stage times of the benchmark workloads).
+// ---------------------------------------------------------------------------
+namespace {
+
+// seconds per unit on a GB300 (2070 MHz); R = right-hand sides
+struct UnitCost {
+    double near_f32_sym = 1.32e-12, near_f32_boxpair = 0.65e-9;  // symmetric float32, R = 1: per
+                                                                 // ordered pair, ordered box pair
+    double near_f32 = 2.7e-12;        // per pair and group of four RHS (one-way float32)
+    double near_tc = 0.27e-12;        // per pair and RHS (tensor-core form, R >= 8)
+    double near_df = 7.3e-12;         // per pair and group of four RHS
+    double near_f64 = 1.0e-10;        // per pair and RHS
+    double pw_f32 = 1.5e-12, pw_f32_rhs = 0.4e-12;   // per (point, antipodal pair) [+ per RHS]
+    double pw_df = 2.9e-12, pw_df_rhs = 3.15e-12;
+    double pw_f64_tab = 6.5e-12;      // per (point, pair, RHS), float64 tables
+    double pw_f64 = 67e-12, pw_f64_rhs = 6.5e-12;
+    double m2l_f32 = 1.28e-12, m2l_df = 2.5e-12, m2l_f64 = 11e-12;   // per (entry, sample, RHS)
+    double requad = 1.1e-10;          // per (box, sample, RHS) of M2M and again of L2L
+};
+
+struct LevelCounts {
+    std::vector<uint64_t> key;     // nonempty boxes, ascending
+    std::vector<int64_t> ns, nt;   // sources / targets per box
+};
+
+// boxes of one level with their point counts, from sorted depth-20 keys
+LevelCounts level_counts(const std::vector<uint64_t>& ks, const std::vector<uint64_t>& kt, int l) {
+    LevelCounts c;
+    const int sh = 3 * (kTreeBits - l);
+    size_t i = 0, j = 0;
+    while (i < ks.size() || j < kt.size()) {
+        const uint64_t a = i < ks.size() ? ks[i] >> sh : ~uint64_t(0);
+        const uint64_t b = j < kt.size() ? kt[j] >> sh : ~uint64_t(0);
+        const uint64_t k = std::min(a, b);
+        int64_t ns = 0, nt = 0;
+        while (i < ks.size() && (ks[i] >> sh) == k) ++i, ++ns;
+        while (j < kt.size() && (kt[j] >> sh) == k) ++j, ++nt;
+        c.key.push_back(k);
+        c.ns.push_back(ns);
+        c.nt.push_back(nt);
+    }
+    return c;
+}
+
+// sum over boxes of f(box, neighbour) for neighbours within Chebyshev distance bw
+template <typename F>
+void for_neighbours(const std::vector<uint64_t>& keys, int l, int bw, F f) {
+    const int n1 = 1 << l;
+#pragma omp parallel for schedule(static)
+    for (int64_t a = 0; a < (int64_t)keys.size(); ++a) {
+        int32_t ia[3];
+        demorton(keys[a], l, ia);
+        for (int dx = -bw; dx <= bw; ++dx)
+            for (int dy = -bw; dy <= bw; ++dy)
+                for (int dz = -bw; dz <= bw; ++dz) {
+                    const int ib[3] = {ia[0] + dx, ia[1] + dy, ia[2] + dz};
+                    if (ib[0] < 0 || ib[1] < 0 || ib[2] < 0 || ib[0] >= n1 || ib[1] >= n1 || ib[2] >= n1) continue;
+                    const int64_t b = find_key(keys, morton(ib[0], ib[1], ib[2], l));
+                    if (b >= 0) f(a, b);
+                }
+    }
+}
+
+}  // namespace
+
+static void tune_plan_shape(HostPlan& hp) {
+    const UnitCost uc;
+    const double R = hp.model_rhs;
+    std::vector<uint64_t> ks, kt;
+    leaf_keys(hp.src, hp.ns, hp.corner, hp.side, ks);
+    leaf_keys(hp.tgt, hp.nt, hp.corner, hp.side, kt);
+    std::sort(ks.begin(), ks.end());
+    std::sort(kt.begin(), kt.end());
+    std::vector<LevelPlan> lps[3];
+    int lfb[3] = {1, 1, 1};
+    for (int b = 1; b <= 2; ++b) lps[b] = plan_levels(hp, b, hp.occ_depth, &lfb[b]);
+    const int lmax = std::max(lfb[1], lfb[2]);
+    std::vector<LevelCounts> lc(lmax + 1);
+    for (int l = 1; l <= lmax; ++l) lc[l] = level_counts(ks, kt, l);
+    double best = -1.0;
+    int bb = 1, bl = lfb[1];
+    for (int b = 1; b <= 2; ++b) {
+        if (lfb[b] < 2) continue;
+        // interaction-list lengths: children of the parent's neighbours minus own neighbours
+        std::vector<double> ilist(lfb[b] + 1, 0.0);
+        for (int l = 2; l <= lfb[b]; ++l) {
+            const LevelCounts& P = lc[l - 1];
+            const LevelCounts& C = lc[l];
+            std::vector<int64_t> nchild(P.key.size(), 0), cand(P.key.size(), 0), own(C.key.size(), 0);
+            for (uint64_t k : C.key) nchild[find_key(P.key, k >> 3)]++;
+            for_neighbours(P.key, l - 1, b, [&](int64_t a, int64_t n) { cand[a] += nchild[n]; });
+            for_neighbours(C.key, l, b, [&](int64_t a, int64_t) { own[a]++; });
+            double tot = 0.0;
+            for (size_t a = 0; a < C.key.size(); ++a) tot += (double)(cand[find_key(P.key, C.key[a] >> 3)] - own[a]);
+            ilist[l] = tot;
+        }
+        for (int L = 2; L <= lfb[b]; ++L) {
+            // near field at leaf level L
+            const LevelCounts& F = lc[L];
+            std::vector<double> pr(F.key.size(), 0.0), bpr(F.key.size(), 0.0);
+            for_neighbours(F.key, L, b, [&](int64_t a, int64_t n) {
+                pr[a] += (double)F.nt[a] * (double)F.ns[n];
+                bpr[a] += 1.0;
+            });
+            double pairs = 0.0, boxpairs = 0.0;
+            for (size_t a = 0; a < F.key.size(); ++a) {
+                pairs += pr[a];
+                boxpairs += bpr[a];
+            }
+            double t = 0.0;
+            const double g4 = std::ceil(R / 4.0);
+            if (hp.model_near == kFP32) {
+                if (hp.model_sym && R == 1) t += pairs * uc.near_f32_sym + boxpairs * uc.near_f32_boxpair;
+                else if (R >= 8) t += pairs * R * uc.near_tc;
+                else t += pairs * g4 * uc.near_f32;
+            } else if (hp.model_near == kDF) {
+                t += pairs * g4 * uc.near_df;
+            } else {
+                t += pairs * R * uc.near_f64;
+            }
+            // S2M and L2T at the leaf
+            const LevelPlan& leaf = lps[b][L];
+            const double npair = (double)leaf.quad.K / 2.0, pts = (double)(hp.ns + hp.nt);
+            if (leaf.prec == kFP32) {
+                t += pts * npair * (uc.pw_f32 + R * uc.pw_f32_rhs);
+            } else if (leaf.prec == kDF) {
+                t += pts * npair * (uc.pw_df + R * uc.pw_df_rhs);
+            } else {
+                const double bytes = npair * 16.0 * (double)(hp.ns + (hp.model_sym ? 0 : hp.nt));
+                const double cap = hp.model_table_bytes > 0 ? (double)hp.model_table_bytes : 96.0 * 1073741824.0;
+                if (hp.model_table_bytes != 0 && bytes <= cap) t += pts * npair * R * uc.pw_f64_tab;
+                else t += pts * npair * (uc.pw_f64 + R * uc.pw_f64_rhs);
+            }
+            // M2L and the re-quadratures of levels 2..L
+            for (int l = 2; l <= L; ++l) {
+                const LevelPlan& lp = lps[b][l];
+                const double c = lp.prec == kFP32 ? uc.m2l_f32 : (lp.prec == kDF ? uc.m2l_df : uc.m2l_f64);
+                t += ilist[l] * (double)lp.quad.K * R * c;
+                if (l >= 3) t += 2.0 * uc.requad * R * (double)lc[l].key.size() * (double)lp.quad.K;
+            }
+            hp.predicted_ms[b][L] = 1e3 * t;
+            if (best < 0.0 || t < best) {
+                best = t;
+                bb = b;
+                bl = L;
+            }
+        }
+    }
+    hp.buffer = bb;
+    hp.lp = lps[bb];
+    hp.lf = lfb[bb] >= 2 ? bl : lfb[bb];
+    hp.tuned = lfb[bb] >= 2 ? 1 : 0;
+    if (hp.lf < lfb[bb]) hp.occ_depth = hp.lf;   // capped below the deepest stable level
+}
+
+// ---------------------------------------------------------------------------
 std::string build_host_plan(HostPlan& hp) {
     // root cube
     std::vector<double> lo(3), hi(3);
@@ -675,39 +876,12 @@ std::string build_host_plan(HostPlan& hp) {
             }
         }
     }
-    // active levels: alpha ladder outer, precision inner, precision never decreasing with depth
     hp.eps_l = hp.eps_scale * hp.eps;
-    hp.lp.assign(kMaxLevels, LevelPlan());
-    std::vector<int> allowed = (hp.precision == 1) ? std::vector<int>{kFP32, kDF, kFP64}
-                                                   : std::vector<int>{kFP64};
-    int lf = 1;
-    for (int l = 2; l <= hp.occ_depth && l < kMaxLevels; ++l) {
-        // only boxes of about a wavelength or larger (k a_l >= 6) use the diagonal form
-        if (hp.kappa * (hp.side / (double)(1u << l)) < min_ka(hp.buffer)) break;
-        bool ok = false;
-        for (double alpha : hp.alphas) {
-            LevelPlan cand;
-            plan_level(hp.kappa, hp.side / (double)(1u << l), hp.eps_l, alpha, hp.buffer, cand);
-            for (int p : allowed) {
-                const double u = std::ldexp(1.0, p == kFP32 ? -24 : (p == kDF ? -48 : -53));
-                const double f = (p == kFP32) ? 1.0 : 1.0 / 16.0;
-                double est = round_off_estimate(cand.quad.ell, hp.kappa, cand.r0, cand.quad.K, u);
-                if (est <= hp.eps_l * f) {
-                    cand.prec = p;
-                    cand.est = est;
-                    hp.lp[l] = cand;
-                    ok = true;
-                    allowed.erase(allowed.begin(), std::find(allowed.begin(), allowed.end(), p));
-                    break;
-                }
-            }
-            if (ok) break;
-        }
-        if (!ok) break;
-        lf = l;
+    if (hp.buffer == 0) {
+        tune_plan_shape(hp);
+    } else {
+        hp.lp = plan_levels(hp, hp.buffer, hp.occ_depth, &hp.lf);
     }
-    if (hp.occ_depth < 2) lf = hp.occ_depth;
-    hp.lf = lf;
     // the device transforms work on lengths up to 1024: refuse before the costly tables
     for (int l = 2; l <= hp.lf; ++l) {
         if (hp.lp[l].quad.ntheta > 1024) return "N_theta above 1024 is not supported";

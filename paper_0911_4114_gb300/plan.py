@@ -8,6 +8,7 @@ import ctypes
 import numpy as np
 
 from . import _native as nat
+from ._native import MAX_LEVELS
 
 
 _PREC_NAMES = {0: "fp64", 1: "fp32", 2: "df"}   # hfmm_level_precision codes
@@ -44,7 +45,8 @@ class FmmPlan:
     require_far: raise (HFMM_ERR_UNSTABLE) instead of planning a pure near field.
     leaf_table_bytes: device bytes allowed for the plane-wave tables of a float64 leaf level
     (-1: up to half the free device memory, 0: none).
-    buffer: buffer boxes between a box and its interaction list, 1 or 2 (Section 3.3.3).
+    buffer: buffer boxes between a box and its interaction list, 1 or 2 (Section 3.3.3), or 0:
+    chosen with the leaf level by the plan's cost model (the "auto" plan shape).
     """
 
     def __init__(self, sources, targets, kappa, eps, precision="fp64", alphas=None,
@@ -161,7 +163,9 @@ class FmmPlan:
                     near_precision=_PREC_NAMES[inf.near_precision],
                     p2p_self_pairs=inf.p2p_self_pairs, near_symmetric=bool(inf.near_symmetric),
                     leaf_tables=bool(inf.leaf_tables), leaf_table_bytes=inf.leaf_table_bytes,
-                    buffer=inf.buffer)
+                    buffer=inf.buffer, tuned=bool(inf.tuned),
+                    predicted_ms={(b, l): inf.predicted_ms[b][l] for b in (1, 2)
+                                  for l in range(MAX_LEVELS) if inf.predicted_ms[b][l] > 0})
 
     def debug_get(self, what, level=0, arg=0):
         L = nat.lib()

@@ -40,23 +40,30 @@ def _apply(plan, q):
 
 @pytest.mark.parametrize("eps,dtype", [(1e-4, np.complex64), (1e-8, np.complex128)])
 def test_ellipsoid_2m(eps, dtype):
+    """One buffer box (default) and the tuned plan shape (buffer = 0, the benchmark's plan)."""
     s, t = wl.points("ellipsoid2m")
     q = wl.charges(len(s), 0, wl.rng(2, salt=1)).astype(dtype)
-    plan = FmmPlan(s, t, 200.0, eps, precision="mixed")
-    got = _apply(plan, q)
     idx = np.sort(wl.rng(2, salt=2).choice(len(t), 500, replace=False))
     want = direct.direct(s, t[idx], q.astype(np.complex128), 200.0, block=8)
-    assert rel(got[idx], want) <= eps
+    for buffer in (1, 0):
+        plan = FmmPlan(s, t, 200.0, eps, precision="mixed", buffer=buffer)
+        got = _apply(plan, q)
+        assert rel(got[idx], want) <= eps, buffer
+        del plan
 
 
 def test_cube_512k_64_rhs():
+    """One buffer box (a float64 level 2) and the tuned plan shape (two buffer boxes, leaf
+    level 4)."""
     s, t = wl.points("cube512k_rhs64")
     q = wl.charges(len(s), 64, wl.rng(3, salt=1)).astype(np.complex64)
-    plan = FmmPlan(s, t, 40.0, 1e-5, precision="mixed", max_rhs=64)
-    got = _apply(plan, q)
     idx = np.sort(wl.rng(3, salt=2).choice(len(t), 100, replace=False))
     want = direct.direct(s, t[idx], q.astype(np.complex128), 40.0, block=16)
-    assert rel(got[idx], want) <= 1e-5
+    for buffer in (1, 0):
+        plan = FmmPlan(s, t, 40.0, 1e-5, precision="mixed", max_rhs=64, buffer=buffer)
+        got = _apply(plan, q)
+        assert rel(got[idx], want) <= 1e-5, buffer
+        del plan
 
 
 def test_batch_32_uneven_problems():
@@ -65,7 +72,7 @@ def test_batch_32_uneven_problems():
     sizes = np.exp(g.uniform(np.log(8192), np.log(131072), 32)).astype(int)
     kappas = g.uniform(10.0, 60.0, 32)
     pts = [wl.cube(int(n), g) for n in sizes]
-    batch = FmmBatch([(x, x, k, 1e-5) for x, k in zip(pts, kappas)], precision="mixed", max_rhs=4)
+    batch = FmmBatch([(x, x, k, 1e-5) for x, k in zip(pts, kappas)], precision="mixed", max_rhs=4, buffer=0)
     qs = [wl.charges(len(x), 4, g).astype(np.complex64) for x in pts]
     outs = batch.apply([torch.as_tensor(q, device="cuda") for q in qs])
     torch.cuda.synchronize()

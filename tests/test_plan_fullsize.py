@@ -6,7 +6,9 @@ right-hand sides, the two-sphere gradient problem -- are planned by both sides w
 plans.  Point permutations, every level's box coordinates and parents, every interaction
 list with its transfer vectors, every leaf neighbour list, the leaf point ranges, and the
 plan integers (active levels, l, N_theta, N_phi(theta_n), K, alpha, level precision) must be
-identical.
+identical.  The plans the benchmark runs with the plan-shape tuner (buffer = 0) are compared
+the same way against the oracle planned with the tuner's choice (buffer, depth = lf), the
+interaction and neighbour lists of two-buffer-box trees on a Morton-strided sample of boxes.
 """
 import functools
 
@@ -78,3 +80,49 @@ def test_fullsize_plan_bit_exact(cfg):
     assert np.array_equal(ls[nz, 0], tr.src_start[nz])
     nz = tr.tgt_count > 0
     assert np.array_equal(lt[nz, 0], tr.tgt_start[nz])
+
+
+TUNED = [
+    ("ellipsoid2m", 200.0, 1e-4, 1),
+    ("ellipsoid2m", 200.0, 1e-8, 1),
+    ("cube512k_rhs64", 40.0, 1e-5, 64),
+    ("sphere262k", 64.0, 1e-6, 1),
+]
+
+
+@pytest.mark.parametrize("cfg", TUNED, ids=[f"{c[0]}-{c[2]:g}-R{c[3]}" for c in TUNED])
+def test_tuned_fullsize_plan_bit_exact(cfg):
+    name, kappa, eps, nrhs = cfg
+    s, t = _points(name)
+    lib = FmmPlan(s, t, kappa, eps, precision="mixed", device=-1, buffer=0, max_rhs=nrhs)
+    info = lib.info()
+    assert info["tuned"] and info["buffer"] in (1, 2)
+    pred = info["predicted_ms"]
+    assert pred[(info["buffer"], info["lf"])] == min(pred.values())
+    orc = ofmm.Plan(s, t, kappa, eps, precision="mixed", buffer=info["buffer"], depth=info["lf"])
+    assert info["lf"] == orc.lf
+    for l, lp in orc.levels.items():
+        li = info["levels"][l]
+        assert (li["ell"], li["ntheta"], li["K"]) == (lp.ell, lp.ntheta, lp.K), (name, l)
+        assert li["alpha"] == lp.alpha and li["precision"] == orc.level_precision[l], (name, l)
+        assert np.array_equal(lib.debug_get("NPHI", l), lp.nphi), (name, l)
+    tr = orc.tree
+    assert np.array_equal(lib.debug_get("SRC_PERM"), tr.src_perm)
+    assert np.array_equal(lib.debug_get("TGT_PERM"), tr.tgt_perm)
+    for l in range(tr.depth + 1):
+        assert np.array_equal(lib.debug_get("BOX_IDX", l), tr.levels[l]["idx"]), (name, l)
+        if l > 0:
+            assert np.array_equal(lib.debug_get("BOX_PARENT", l), tr.levels[l]["parent"]), (name, l)
+    # lists on a Morton-strided sample of boxes (about 300 per level)
+    for l in range(2, tr.depth + 1):
+        off, idx, v = (lib.debug_get(k, l) for k in ("ILIST_OFF", "ILIST_IDX", "ILIST_V"))
+        n = len(tr.levels[l]["key"])
+        for a in range(0, n, max(1, n // 300)):
+            assert np.array_equal(idx[off[a]:off[a + 1]], tr.ilist[l][a]), (name, l, a)
+            assert np.array_equal(v[off[a]:off[a + 1]], tr.vlist[l][a]), (name, l, a)
+    off, idx = lib.debug_get("NLIST_OFF"), lib.debug_get("NLIST_IDX")
+    n = len(tr.nlist)
+    for a in range(0, n, max(1, n // 300)):
+        assert np.array_equal(idx[off[a]:off[a + 1]], tr.nlist[a]), (name, a)
+    ls = lib.debug_get("LEAF_SRC")
+    assert np.array_equal(ls[:, 1], tr.src_count)

@@ -193,3 +193,23 @@ def test_plan_independent_of_thread_count(tmp_path):
     assert a.keys() == b.keys() and a["lf"] >= 2
     for k in a:
         assert np.array_equal(a[k], b[k]), k
+
+
+def test_tuned_plan_equals_forced_plan():
+    """buffer = 0: the plan-shape tuner picks the candidate (buffer, leaf level) of least
+    predicted time, and the plan is exactly the plan with that buffer and depth = lf."""
+    rng = np.random.default_rng(zlib.crc32(b"tuner"))
+    x = rng.random((6000, 3))
+    for kappa, eps in ((70.0, 1e-4), (24.0, 1e-6)):
+        auto = FmmPlan(x, x, kappa, eps, precision="mixed", max_leaf=32, buffer=0, device=-1)
+        ia = auto.info()
+        assert ia["tuned"] and ia["lf"] >= 2
+        assert ia["predicted_ms"][(ia["buffer"], ia["lf"])] == min(ia["predicted_ms"].values())
+        forced = FmmPlan(x, x, kappa, eps, precision="mixed", buffer=ia["buffer"], depth=ia["lf"], device=-1)
+        fi = forced.info()
+        assert fi["lf"] == ia["lf"] and fi["levels"] == ia["levels"]
+        for what in ("SRC_PERM", "NLIST_OFF", "NLIST_IDX"):
+            assert np.array_equal(auto.debug_get(what), forced.debug_get(what))
+        for l in range(2, ia["lf"] + 1):
+            for what in ("BOX_IDX", "ILIST_OFF", "ILIST_IDX", "ILIST_V", "NPHI"):
+                assert np.array_equal(auto.debug_get(what, l), forced.debug_get(what, l)), (what, l)
