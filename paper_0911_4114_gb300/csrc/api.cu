@@ -46,9 +46,12 @@ struct DevLevel {
     QuadView qv{};
     BoxView bv{};
     int32_t* octant = nullptr;
-    int32_t *ioff = nullptr, *iidx = nullptr, *iv = nullptr;
-    int32_t* tslot = nullptr;
-    int32_t* tslot_t = nullptr;  // slot of the opposite vector (342 - v): transposed M2L
+    // M2L by sibling groups (k_m2l_sib): parents at level l-1 with their first child and child
+    // count, and per parent the union of the children's lists (box, child mask, slot per child
+    // for the forward and the transposed M2L)
+    int npar = 0;
+    int32_t *pfirst = nullptr, *pnch = nullptr, *poff = nullptr, *pu = nullptr, *pmask = nullptr;
+    int32_t *pslot = nullptr, *pslot_t = nullptr;
     void* table = nullptr;      // compact T^{s,LL} tables in the level precision
     df* sdf = nullptr;          // (K, 3) s_k * kappa / 2 pi as double-float pairs
     cxd* shift64 = nullptr;     // [8][K] exp(i k s.d_o), d_o = child-centre offsets of level l+1
@@ -227,19 +230,55 @@ hfmm_status upload_level(hfmm_plan_s* P, int l) {
     for (int b = 0; b < d.nbox; ++b)
         oct[b] = 4 * (T.idx[3 * b] & 1) + 2 * (T.idx[3 * b + 1] & 1) + (T.idx[3 * b + 2] & 1);
     TRY(upload(P, &d.octant, oct));
-    TRY(upload(P, &d.ioff, T.ioff));
-    TRY(upload(P, &d.iidx, T.iidx));
-    TRY(upload(P, &d.iv, T.iv));
     // transfer tables, compact: slot of every used vector (the lists are symmetric, so the
-    // opposite vector W^3 - 1 - v of a used v is used too)
+    // opposite vector W^3 - 1 - v of a used v is used too; the transposed M2L takes its slot)
     const int nslots = transfer_slots(hp.buffer);
     std::vector<int32_t> slot(nslots, 0);
     int ns = 0;
     for (int v = 0; v < nslots; ++v) slot[v] = lp.table[v].empty() ? 0 : ns++;
-    TRY(upload(P, &d.tslot, slot));
     std::vector<int32_t> slot_t(nslots, 0);
     for (int v = 0; v < nslots; ++v) slot_t[v] = slot[nslots - 1 - v];
-    TRY(upload(P, &d.tslot_t, slot_t));
+    {
+        // sibling groups: the children of each parent are contiguous at this level
+        const TreeLevel& PL = hp.levels[l - 1];
+        std::vector<int32_t> pf, pn, po(1, 0), pu, pm, ps, pst;
+        std::vector<int32_t> mark(d.nbox, -1);
+        for (int64_t pp = 0; pp < PL.nbox(); ++pp) {
+            const int c0 = PL.child_start[pp], nc = PL.child_count[pp];
+            if (nc == 0) continue;
+            if (nc > 8) return fail(HFMM_ERR_STATE, "internal: more than 8 children");
+            pf.push_back(c0);
+            pn.push_back(nc);
+            // union of the children's lists, in box order (= Morton order)
+            std::vector<int32_t> us;
+            for (int c = 0; c < nc; ++c)
+                for (int32_t t = T.ioff[c0 + c]; t < T.ioff[c0 + c + 1]; ++t) us.push_back(T.iidx[t]);
+            std::sort(us.begin(), us.end());
+            us.erase(std::unique(us.begin(), us.end()), us.end());
+            const size_t base = pu.size();
+            for (size_t i = 0; i < us.size(); ++i) mark[us[i]] = (int32_t)(base + i);
+            pu.insert(pu.end(), us.begin(), us.end());
+            pm.resize(pu.size(), 0);
+            ps.resize(8 * pu.size(), 0);
+            pst.resize(8 * pu.size(), 0);
+            for (int c = 0; c < nc; ++c)
+                for (int32_t t = T.ioff[c0 + c]; t < T.ioff[c0 + c + 1]; ++t) {
+                    const int32_t e = mark[T.iidx[t]];
+                    pm[e] |= 1 << c;
+                    ps[8 * (size_t)e + c] = slot[T.iv[t]];
+                    pst[8 * (size_t)e + c] = slot_t[T.iv[t]];
+                }
+            po.push_back((int32_t)pu.size());
+        }
+        d.npar = (int)pf.size();
+        TRY(upload(P, &d.pfirst, pf));
+        TRY(upload(P, &d.pnch, pn));
+        TRY(upload(P, &d.poff, po));
+        TRY(upload(P, &d.pu, pu));
+        TRY(upload(P, &d.pmask, pm));
+        TRY(upload(P, &d.pslot, ps));
+        TRY(upload(P, &d.pslot_t, pst));
+    }
     if (d.prec == kDF) {
         std::vector<cx<df>> t((size_t)ns * q.K);
         for (int v = 0; v < transfer_slots(hp.buffer); ++v)
@@ -656,13 +695,17 @@ void launch_m2m_t(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
 template <typename S, typename C>
 void launch_m2l(hfmm_plan_s* P, int l, int R, cudaStream_t st, bool transposed) {
     DevLevel& d = P->lev[l];
-    dim3 grid(d.nbox, nblk(d.K, 256));
-    if (!transposed)
-        k_m2l<S, C><<<grid, 256, 0, st>>>(d.nbox, d.K, d.ioff, d.iidx, d.iv, d.tslot, (const cx<S>*)d.table,
-                                          (const cx<S>*)d.M, R, (cx<S>*)d.IL);
+    const dim3 g(d.npar, nblk(d.K, 128));
+    const int32_t* ps = transposed ? d.pslot_t : d.pslot;
+    const cx<S>* in = (const cx<S>*)(transposed ? d.IL : d.M);
+    cx<S>* out = (cx<S>*)(transposed ? d.M : d.IL);
+    if (d.npar == 0) return;
+    if (R == 1)
+        k_m2l_sib<S, C, 1><<<g, 128, 0, st>>>(d.K, d.pfirst, d.pnch, d.poff, d.pu, d.pmask, ps,
+                                              (const cx<S>*)d.table, in, R, out);
     else
-        k_m2l<S, C><<<grid, 256, 0, st>>>(d.nbox, d.K, d.ioff, d.iidx, d.iv, d.tslot_t, (const cx<S>*)d.table,
-                                          (const cx<S>*)d.IL, R, (cx<S>*)d.M);
+        k_m2l_sib<S, C, 2><<<g, 128, 0, st>>>(d.K, d.pfirst, d.pnch, d.poff, d.pu, d.pmask, ps,
+                                              (const cx<S>*)d.table, in, R, out);
 }
 
 // type codes of a level's signatures and arithmetic: 0 float, 1 double, 2 double-float

@@ -1343,23 +1343,52 @@ struct M2LAcc<df> {
     __device__ __forceinline__ cx<df> get() const { return mk<df>(dfacc_get(x), dfacc_get(y)); }
 };
 
-template <typename S, typename C>
-__global__ void k_m2l(int nbox, int64_t K, const int32_t* __restrict__ ioff, const int32_t* __restrict__ iidx,
-                      const int32_t* __restrict__ iv, const int32_t* __restrict__ tslot,
-                      const cx<S>* __restrict__ T, const cx<S>* __restrict__ M, int R_,
-                      cx<S>* __restrict__ I) {
-    const int a = blockIdx.x;
+// M2L by sibling groups: one block per (parent box, tile of samples) evaluates the lists of
+// all children of the parent together.  The children's lists are subsets of one union (the
+// children of the parent's neighbours), so each partner signature is read once for all
+// siblings that list it (a per-entry mask) instead of once per sibling: with two buffer
+// boxes (lists up to 875 entries) the partner reads drop about sevenfold.  Each child still
+// sums its own entries in Morton order (the order of its list), as a per-box loop would.
+// Union entry e of parent p: box pu[e], children mask pmask[e] (bit c = child c lists it),
+// table slot pslot[8 e + c] of child c's transfer vector.
+template <typename S, typename C, int kRC>
+__global__ void k_m2l_sib(int64_t K, const int32_t* __restrict__ pfirst, const int32_t* __restrict__ pnch,
+                          const int32_t* __restrict__ poff, const int32_t* __restrict__ pu,
+                          const int32_t* __restrict__ pmask, const int32_t* __restrict__ pslot,
+                          const cx<S>* __restrict__ T, const cx<S>* __restrict__ M, int R_,
+                          cx<S>* __restrict__ I) {
+    const int p = blockIdx.x;
     const int64_t k = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
     if (k >= K) return;
-    const int l0 = ioff[a], l1 = ioff[a + 1];
-    for (int r = 0; r < R_; ++r) {
-        M2LAcc<C> acc;
-        acc.zero();
-        for (int t = l0; t < l1; ++t) {
-            const int b = iidx[t];
-            acc.mac(cvt<C>(T[(int64_t)tslot[iv[t]] * K + k]), cvt<C>(M[((int64_t)b * R_ + r) * K + k]));
+    const int c0 = pfirst[p], nc = pnch[p];
+    const int e0 = poff[p], e1 = poff[p + 1];
+    for (int r0 = 0; r0 < R_; r0 += kRC) {
+        const int rn = min(kRC, R_ - r0);
+        M2LAcc<C> acc[8][kRC];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+#pragma unroll
+            for (int r = 0; r < kRC; ++r) acc[c][r].zero();
+        for (int e = e0; e < e1; ++e) {
+            const int u = pu[e], mask = pmask[e];
+            cx<C> m[kRC];
+#pragma unroll
+            for (int r = 0; r < kRC; ++r)
+                m[r] = r < rn ? cvt<C>(M[((int64_t)u * R_ + r0 + r) * K + k]) : mk<C>(rval<C>(0.0), rval<C>(0.0));
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (mask & (1 << c)) {                 // uniform across the block
+                    const cx<C> t = cvt<C>(T[(int64_t)pslot[8 * e + c] * K + k]);
+#pragma unroll
+                    for (int r = 0; r < kRC; ++r) acc[c][r].mac(t, m[r]);
+                }
         }
-        I[((int64_t)a * R_ + r) * K + k] = cvt<S>(acc.get());
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (c < nc)
+#pragma unroll
+                for (int r = 0; r < kRC; ++r)
+                    if (r < rn) I[((int64_t)(c0 + c) * R_ + r0 + r) * K + k] = cvt<S>(acc[c][r].get());
     }
 }
 
