@@ -146,6 +146,9 @@ typedef struct {
     int tuned;                  /* 1 when the plan-shape tuner chose buffer and lf */
     /* the tuner's predicted apply time in ms for [buffer][leaf level] (0: not a candidate) */
     double predicted_ms[3][HFMM_MAX_LEVELS];
+    /* symmetric near field: the register budget (resident blocks per SM, 5-8) the plan timed
+     * fastest on its own near field at plan time (0: not the symmetric kernel) */
+    int near_variant;
 } hfmm_info;
 
 /* Fill *opt with the defaults listed above. */

@@ -97,6 +97,7 @@ struct hfmm_plan_s {
     int ntunits = 0, nsunits = 0;
     int2* symunits = nullptr;                   // the same chunks, heaviest first (symmetric near field)
     int nsymunits = 0;
+    int sym_variant = 7;      // resident-block target of the symmetric near-field kernel (tuned)
     int2 *tunits64 = nullptr, *sunits64 = nullptr;  // 64-point chunks (tensor-core near field)
     int ntunits64 = 0, nsunits64 = 0;
     double* gsort = nullptr;    // sorted position gradient (ns, 3)
@@ -708,6 +709,49 @@ void launch_m2l(hfmm_plan_s* P, int l, int R, cudaStream_t st, bool transposed) 
                                               (const cx<S>*)d.table, in, R, out);
 }
 
+// symmetric float32 near field; `variant` selects the register budget (resident blocks per SM)
+void launch_sym(int variant, int nunits, const int2* units, const int32_t* start, const int32_t* count,
+                const int32_t* noff, const int32_t* nidx, const P2PMixedArgs& a, const cxd* q, cxd* phi,
+                cudaStream_t st) {
+    const unsigned g = nblk(nunits, 4);
+    switch (variant) {
+        case 5: k_p2p_mixed_sym_warp<5><<<g, 128, 0, st>>>(units, nunits, start, count, noff, nidx, a, q, phi); break;
+        case 6: k_p2p_mixed_sym_warp<6><<<g, 128, 0, st>>>(units, nunits, start, count, noff, nidx, a, q, phi); break;
+        case 8: k_p2p_mixed_sym_warp<8><<<g, 128, 0, st>>>(units, nunits, start, count, noff, nidx, a, q, phi); break;
+        default: k_p2p_mixed_sym_warp<7><<<g, 128, 0, st>>>(units, nunits, start, count, noff, nidx, a, q, phi); break;
+    }
+}
+
+// Kernel tuner: time each register budget of the symmetric near field on the plan's own units
+// (two launches each into the plan's workspace, after one warm-up) and keep the fastest.
+hfmm_status tune_sym_variant(hfmm_plan_s* P) {
+    if (!(P->sym && P->near_prec == kFP32) || P->nsymunits == 0) return HFMM_OK;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaMemset(P->qs, 0, sizeof(cxd) * (size_t)P->hp.ns));
+    float best = -1.f;
+    for (int v : {5, 6, 7, 8}) {
+        launch_sym(v, P->nsymunits, P->symunits, P->tstart, P->tcount, P->noff, P->nidx, P->mixed, P->qs, P->phis, 0);
+        CK(cudaEventRecord(e0, 0));
+        for (int i = 0; i < 2; ++i)
+            launch_sym(v, P->nsymunits, P->symunits, P->tstart, P->tcount, P->noff, P->nidx, P->mixed, P->qs,
+                       P->phis, 0);
+        CK(cudaEventRecord(e1, 0));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (best < 0.f || ms < best) {
+            best = ms;
+            P->sym_variant = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaGetLastError());
+    return HFMM_OK;
+}
+
 // type codes of a level's signatures and arithmetic: 0 float, 1 double, 2 double-float
 // (float64 levels of the mixed policy store and compute in double-float pairs)
 int store_code(hfmm_plan_s* P, int l) {
@@ -1039,6 +1083,7 @@ hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, 
              P->hp.src_perm == P->hp.tgt_perm && P->hp.src_count == P->hp.tgt_count;
     if (opt.device >= 0) {
         hfmm_status s = upload_plan(P);
+        if (s == HFMM_OK) s = tune_sym_variant(P);
         if (s != HFMM_OK) {
             std::string msg = g_err;
             hfmm_destroy(P);
@@ -1095,9 +1140,8 @@ hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_d
     if (P->near_prec == kFP32 && P->sym && R == 1) {
         CK(cudaMemsetAsync(P->phis, 0, sizeof(cxd) * (size_t)hp.nt, st));
         if (P->nsymunits > 0)
-            k_p2p_mixed_sym_warp<<<nblk(P->nsymunits, 4), 128, 0, st>>>(P->symunits, P->nsymunits, P->tstart,
-                                                                       P->tcount, P->noff, P->nidx, P->mixed, P->qs,
-                                                                       P->phis);
+            launch_sym(P->sym_variant, P->nsymunits, P->symunits, P->tstart, P->tcount, P->noff, P->nidx, P->mixed,
+                       P->qs, P->phis, st);
     } else if (P->near_prec == kFP32 && R >= hfmm_plan_s::kTcMinRhs) {
         // static + dynamic shared memory exceeds 48 KiB: opt in explicitly
         cudaFuncSetAttribute(k_p2p_mixed_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcDynSmem);
@@ -1189,9 +1233,8 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t P, const void* w, void* out, int nrhs
     if (P->near_prec == kFP32 && P->sym && R == 1) {
         CK(cudaMemsetAsync(P->qs, 0, sizeof(cxd) * (size_t)hp.ns, st));
         if (P->nsymunits > 0)
-            k_p2p_mixed_sym_warp<<<nblk(P->nsymunits, 4), 128, 0, st>>>(P->symunits, P->nsymunits, P->sstart,
-                                                                       P->scount, P->noff, P->nidx, P->mixed, P->phis,
-                                                                       P->qs);
+            launch_sym(P->sym_variant, P->nsymunits, P->symunits, P->sstart, P->scount, P->noff, P->nidx, P->mixed,
+                       P->phis, P->qs, st);
     } else if (P->near_prec == kFP32 && R >= hfmm_plan_s::kTcMinRhs) {
         P2PMixedArgs a = P->mixed;
         std::swap(a.tpt, a.spt);
@@ -1337,6 +1380,7 @@ hfmm_status hfmm_query(hfmm_plan_t P, hfmm_info* info) {
     info->leaf_tables = P->tab_s != nullptr;
     info->buffer = hp.buffer;
     info->tuned = hp.tuned;
+    info->near_variant = (P->sym && P->near_prec == kFP32) ? P->sym_variant : 0;
     for (int b = 0; b < 3; ++b)
         for (int l = 0; l < HFMM_MAX_LEVELS; ++l) info->predicted_ms[b][l] = hp.predicted_ms[b][l];
     info->leaf_table_bytes = P->tab_bytes;

@@ -836,8 +836,11 @@ __device__ __forceinline__ cxf green_grid(float4 gp, float4 op, float4 sp, float
     return mk<float>(cs * rho, sn * rho);
 }
 
-// one warp per (box, 32-target chunk)
-__global__ void __launch_bounds__(128, 7) k_p2p_mixed_sym_warp(
+// one warp per (box, 32-target chunk).  kMinBlocks: resident blocks per SM the register
+// allocation is sized for (the plan times the instantiations on its own near field and keeps
+// the fastest; the arithmetic is the same in all of them)
+template <int kMinBlocks>
+__global__ void __launch_bounds__(128, kMinBlocks) k_p2p_mixed_sym_warp(
     const int2* __restrict__ units, int nunits, const int32_t* __restrict__ start,
     const int32_t* __restrict__ count, const int32_t* __restrict__ noff, const int32_t* __restrict__ nidx,
     P2PMixedArgs a, const cxd* __restrict__ qs, cxd* __restrict__ phis) {
@@ -878,16 +881,25 @@ __global__ void __launch_bounds__(128, 7) k_p2p_mixed_sym_warp(
             __syncwarp();
             cxf tile = mk<float>(0, 0);
             for (int jg = 0; jg < sn; jg += 8) {
+                // inactive lanes have qi = 0 (and a finite g), so their reverse terms vanish
                 cxf rv[8];
+                if (jg + 8 <= sn) {                // full group: no per-source bound test
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    rv[k] = mk<float>(0, 0);
-                    const int jj = jg + k;
-                    if (jj < sn) {                 // warp-uniform
-                        cxf g = green_grid(gp, op, wp[jj], wo[jj], a.tau_hi, a.tau_lo);
-                        if (!active) g = mk<float>(0, 0);
-                        mac(tile, g, wq[jj]);
+                    for (int k = 0; k < 8; ++k) {
+                        const cxf g = green_grid(gp, op, wp[jg + k], wo[jg + k], a.tau_hi, a.tau_lo);
+                        mac(tile, g, wq[jg + k]);
                         rv[k] = g * qi;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        rv[k] = mk<float>(0, 0);
+                        const int jj = jg + k;
+                        if (jj < sn) {             // warp-uniform
+                            const cxf g = green_grid(gp, op, wp[jj], wo[jj], a.tau_hi, a.tau_lo);
+                            mac(tile, g, wq[jj]);
+                            rv[k] = g * qi;
+                        }
                     }
                 }
                 if (both) {                        // warp-uniform

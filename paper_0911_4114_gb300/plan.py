@@ -165,7 +165,8 @@ class FmmPlan:
                     leaf_tables=bool(inf.leaf_tables), leaf_table_bytes=inf.leaf_table_bytes,
                     buffer=inf.buffer, tuned=bool(inf.tuned),
                     predicted_ms={(b, l): inf.predicted_ms[b][l] for b in (1, 2)
-                                  for l in range(MAX_LEVELS) if inf.predicted_ms[b][l] > 0})
+                                  for l in range(MAX_LEVELS) if inf.predicted_ms[b][l] > 0},
+                    near_variant=inf.near_variant)
 
     def debug_get(self, what, level=0, arg=0):
         L = nat.lib()
