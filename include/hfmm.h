@@ -110,6 +110,10 @@ typedef struct {
  * round-off rule rejects level 2 in every allowed precision and alpha, or the occupancy
  * depth is below 2. */
 #define HFMM_FLAG_REQUIRE_FAR 1
+/* hfmm_options.flags: compute the T^{s,LL} transfer tables on the host (OpenMP) instead of on
+ * the device (the default when a device is given).  Both follow Algorithm BMTF and the
+ * per-row anterpolation of Section 3.3.2 in float64 and agree to round-off. */
+#define HFMM_FLAG_HOST_TABLES 2
 
 typedef struct {
     int64_t ns, nt;
@@ -269,7 +273,8 @@ typedef enum {
     HFMM_GET_SRC_PERM = 7,     /* int64 (ns) original index of each sorted source */
     HFMM_GET_TGT_PERM = 8,     /* int64 (nt) original index of each sorted target */
     HFMM_GET_NPHI = 9,         /* int32 (ntheta/2+1) N_phi(theta_n) of `level` */
-    HFMM_GET_TABLE = 10,       /* float64 (K, 2) T^{s,LL} of `level` for vector `arg` */
+    HFMM_GET_TABLE = 10,       /* float64 (K, 2) T^{s,LL} of `level` for vector `arg` (device-computed
+                                  tables are copied back and converted) */
     HFMM_GET_LEAF_SRC = 11,    /* int32 (nbox, 2) first sorted source and count per leaf box */
     HFMM_GET_LEAF_TGT = 12     /* int32 (nbox, 2) first sorted target and count per leaf box */
 } hfmm_get;

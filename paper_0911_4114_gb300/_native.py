@@ -16,6 +16,7 @@ STAGES = ("permute_in", "near_field", "s2m", "m2m", "m2l", "l2l", "l2t", "permut
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_UNSTABLE, ERR_TIMEOUT, ERR_STATE = range(7)
 C64, C128 = 0, 1
 FLAG_REQUIRE_FAR = 1
+FLAG_HOST_TABLES = 2
 PREC_FP64, PREC_MIXED = 0, 1
 
 GET = dict(BOX_IDX=0, BOX_PARENT=1, ILIST_OFF=2, ILIST_IDX=3, ILIST_V=4, NLIST_OFF=5, NLIST_IDX=6,

@@ -33,7 +33,7 @@ def build(verbose=False, extra_nvcc=()):
         obj = os.path.join(BUILD, src + ".o")
         objs.append(obj)
         jobs.append(["g++", *host, "-c", os.path.join(CSRC, src), "-o", obj])
-    for src in ("api.cu", "noalloc.cu"):
+    for src in ("api.cu", "noalloc.cu", "tables.cu"):
         obj = os.path.join(BUILD, src + ".o")
         objs.append(obj)
         jobs.append([nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",

@@ -49,6 +49,7 @@ struct DevLevel {
     // M2L by sibling groups (k_m2l_sib): parents at level l-1 with their first child and child
     // count, and per parent the union of the children's lists (box, child mask, slot per child
     // for the forward and the transposed M2L)
+    std::vector<int32_t> slot_host;   // compact table slot of every transfer vector
     int npar = 0;
     int32_t *pfirst = nullptr, *pnch = nullptr, *poff = nullptr, *pu = nullptr, *pmask = nullptr;
     int32_t *pslot = nullptr, *pslot_t = nullptr;
@@ -234,11 +235,14 @@ hfmm_status upload_level(hfmm_plan_s* P, int l) {
     // transfer tables, compact: slot of every used vector (the lists are symmetric, so the
     // opposite vector W^3 - 1 - v of a used v is used too; the transposed M2L takes its slot)
     const int nslots = transfer_slots(hp.buffer);
+    std::vector<char> used(nslots, 0);
+    for (int32_t v : T.iv) used[v] = 1;
     std::vector<int32_t> slot(nslots, 0);
     int ns = 0;
-    for (int v = 0; v < nslots; ++v) slot[v] = lp.table[v].empty() ? 0 : ns++;
+    for (int v = 0; v < nslots; ++v) slot[v] = used[v] ? ns++ : 0;
     std::vector<int32_t> slot_t(nslots, 0);
     for (int v = 0; v < nslots; ++v) slot_t[v] = slot[nslots - 1 - v];
+    d.slot_host = slot;
     {
         // sibling groups: the children of each parent are contiguous at this level
         const TreeLevel& PL = hp.levels[l - 1];
@@ -280,7 +284,19 @@ hfmm_status upload_level(hfmm_plan_s* P, int l) {
         TRY(upload(P, &d.pslot, ps));
         TRY(upload(P, &d.pslot_t, pst));
     }
-    if (d.prec == kDF) {
+    if (!hp.host_tables) {
+        // T^{s,LL} on the device (tables.cu), in the level's storage
+        void* dt = nullptr;
+        size_t bytes = 0;
+        const std::string e = device_tables(make_table_job(lp, hp.kappa, hp.buffer, used), q,
+                                            d.prec == kFP32 ? 0 : (d.prec == kFP64 ? 1 : 2), &dt, &bytes);
+        if (!e.empty()) return fail(HFMM_ERR_CUDA, e);
+        if (dt) {
+            P->allocs.push_back(dt);
+            P->workspace += (int64_t)bytes;
+        }
+        d.table = dt;
+    } else if (d.prec == kDF) {
         std::vector<cx<df>> t((size_t)ns * q.K);
         for (int v = 0; v < transfer_slots(hp.buffer); ++v)
             if (!lp.table[v].empty())
@@ -986,7 +1002,7 @@ hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, 
     if (!(opt.eps_scale > 0.0 && opt.eps_scale <= 1.0)) return fail(HFMM_ERR_ARG, "eps_scale must be in (0, 1]");
     if (opt.precision != HFMM_PREC_FP64 && opt.precision != HFMM_PREC_MIXED)
         return fail(HFMM_ERR_ARG, "unknown precision policy");
-    if (opt.flags & ~HFMM_FLAG_REQUIRE_FAR) return fail(HFMM_ERR_ARG, "unknown flag bits");
+    if (opt.flags & ~(HFMM_FLAG_REQUIRE_FAR | HFMM_FLAG_HOST_TABLES)) return fail(HFMM_ERR_ARG, "unknown flag bits");
     if (opt.leaf_table_bytes < -1) return fail(HFMM_ERR_ARG, "leaf_table_bytes must be -1, 0 or positive");
     if (opt.buffer < 0 || opt.buffer > 2) return fail(HFMM_ERR_ARG, "buffer must be 0 (chosen by the plan), 1 or 2");
     std::vector<double> alphas;
@@ -1038,6 +1054,8 @@ hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, 
         hp.model_near = opt.precision == HFMM_PREC_MIXED ? (eps >= 1e-6 ? kFP32 : (eps >= 1e-11 ? kDF : kFP64)) : kFP64;
         hp.model_sym = ns == nt && (sources == targets || std::memcmp(sources, targets, sizeof(double) * 3 * ns) == 0);
         hp.model_table_bytes = opt.leaf_table_bytes;
+        // transfer tables on the device unless asked for on the host (or no device)
+        hp.host_tables = opt.device < 0 || (opt.flags & HFMM_FLAG_HOST_TABLES);
         hp.has_root = opt.has_root;
         for (int k = 0; k < 4; ++k) hp.root[k] = opt.root[k];
         std::string e = build_host_plan(hp);
@@ -1565,6 +1583,39 @@ int64_t hfmm_debug_get(hfmm_plan_t P, int what, int level, int64_t arg, void* ou
             return give(hp.lp[level].quad.nphi.data(), (int64_t)hp.lp[level].quad.nphi.size(), 4);
         case HFMM_GET_TABLE: {
             if (!lev_ok || level < 2 || arg < 0 || arg >= transfer_slots(hp.buffer)) return -1;
+            if (!hp.host_tables) {
+                // computed on the device: copy the vector's slot back, converted to float64
+                const DevLevel& d = P->lev[level];
+                bool used = false;
+                for (int32_t v : hp.levels[level].iv) used |= (v == arg);
+                if (!used || !d.table) return -1;
+                const int64_t K = hp.lp[level].quad.K;
+                if (out) {
+                    const size_t e = d.prec == kFP32 ? sizeof(cxf) : (d.prec == kFP64 ? sizeof(cxd) : sizeof(cx<df>));
+                    std::vector<unsigned char> buf(e * (size_t)K);
+                    if (cudaSetDevice(P->device) != cudaSuccess ||
+                        cudaMemcpy(buf.data(), (const unsigned char*)d.table + e * (size_t)d.slot_host[arg] * K, buf.size(),
+                                   cudaMemcpyDeviceToHost) != cudaSuccess)
+                        return -1;
+                    double* o = static_cast<double*>(out);
+                    for (int64_t k = 0; k < std::min(K, cap / 2); ++k) {
+                        double re, im;
+                        if (d.prec == kFP32) {
+                            const cxf v = reinterpret_cast<const cxf*>(buf.data())[k];
+                            re = v.x, im = v.y;
+                        } else if (d.prec == kFP64) {
+                            const cxd v = reinterpret_cast<const cxd*>(buf.data())[k];
+                            re = v.x, im = v.y;
+                        } else {
+                            const cx<df> v = reinterpret_cast<const cx<df>*>(buf.data())[k];
+                            re = (double)v.x.hi + (double)v.x.lo, im = (double)v.y.hi + (double)v.y.lo;
+                        }
+                        o[2 * k] = re;
+                        o[2 * k + 1] = im;
+                    }
+                }
+                return 2 * K;
+            }
             const auto& t = hp.lp[level].table[arg];
             if (t.empty()) return -1;
             const int64_t n = (int64_t)t.size();

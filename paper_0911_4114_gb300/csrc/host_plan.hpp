@@ -60,6 +60,7 @@ struct HostPlan {
     std::vector<double> alphas;
     double eps_scale = 0.25;
     int max_leaf = 64, depth_req = 0, precision = 0;
+    bool host_tables = true;   // false: T^{s,LL} is computed on the device at upload
     int buffer = 1;      // buffer boxes between a box and its interaction list (Section 3.3.3);
                          // 0 on input: chosen by the plan-shape tuner (1 or 2 on output)
     // inputs of the plan-shape tuner's cost model: right-hand sides, near-field arithmetic,
@@ -89,6 +90,23 @@ struct HostPlan {
 
 // Builds everything on the host; returns "" on success or an error message.
 std::string build_host_plan(HostPlan& hp);
+
+// T^{s,LL} of one level computed on the device (tables.cu): the canonical vectors the level's
+// lists use with their Legendre coefficients (Eq. TransferFn), and for every used transfer
+// vector, in ascending index order (the compact slot order of the apply), its canonical
+// vector and reflection (bit 0: x -> -x, 1: y -> -y, 2: z -> -z, 3: x <-> y).
+struct TableJob {
+    int ell = 0, nfull = 0;
+    double kappa = 0;
+    std::vector<cd> coef;          // (ncanon, ell + 1)
+    std::vector<double> rhat;      // (ncanon, 3)
+    std::vector<int32_t> slot_canon, slot_flags;
+    int ncanon() const { return (int)(rhat.size() / 3); }
+};
+TableJob make_table_job(const LevelPlan& lp, double kappa, int buffer, const std::vector<char>& used);
+// Computes the compact table [slot][K] into a new device allocation in the given storage
+// (0 float32, 1 float64, 2 double-float pairs); the caller owns *out.  Returns "" or a message.
+std::string device_tables(const TableJob& job, const Quadrature& q, int store, void** out, size_t* bytes);
 
 // --- special functions (special.cpp) ----------------------------------------
 void sph_jn_all(int nmax, double x, double* out);     // j_0..j_nmax

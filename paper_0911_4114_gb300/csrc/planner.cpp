@@ -381,6 +381,41 @@ static std::array<int, 3> canonical(int di, int dj, int dk) {
     return {std::max(std::abs(di), std::abs(dj)), std::min(std::abs(di), std::abs(dj)), std::abs(dk)};
 }
 
+TableJob make_table_job(const LevelPlan& lp, double kappa, int buffer, const std::vector<char>& used) {
+    const int D = transfer_span(buffer), W = transfer_width(buffer);
+    TableJob job;
+    job.ell = lp.quad.ell;
+    job.nfull = 4 * ((2 * lp.quad.ell + 1 + 3) / 4);
+    job.kappa = kappa;
+    std::vector<std::array<int, 3>> canon;
+    for (int di = -D; di <= D; ++di)
+        for (int dj = -D; dj <= D; ++dj)
+            for (int dk = -D; dk <= D; ++dk) {
+                const int v = (di + D) * W * W + (dj + D) * W + (dk + D);
+                if (!used[v]) continue;
+                const std::array<int, 3> cv = canonical(di, dj, dk);
+                if (std::find(canon.begin(), canon.end(), cv) == canon.end()) canon.push_back(cv);
+            }
+    std::sort(canon.begin(), canon.end());
+    for (auto& cv : canon) {
+        const double r0v[3] = {cv[0] * lp.a, cv[1] * lp.a, cv[2] * lp.a};
+        Transfer T(lp.quad.ell, kappa, r0v);
+        job.coef.insert(job.coef.end(), T.c.begin(), T.c.end());
+        job.rhat.insert(job.rhat.end(), T.rhat, T.rhat + 3);
+    }
+    for (int di = -D; di <= D; ++di)
+        for (int dj = -D; dj <= D; ++dj)
+            for (int dk = -D; dk <= D; ++dk) {
+                const int v = (di + D) * W * W + (dj + D) * W + (dk + D);
+                if (!used[v]) continue;
+                job.slot_canon.push_back(
+                    (int32_t)(std::find(canon.begin(), canon.end(), canonical(di, dj, dk)) - canon.begin()));
+                job.slot_flags.push_back((di < 0 ? 1 : 0) | (dj < 0 ? 2 : 0) | (dk < 0 ? 4 : 0) |
+                                         (std::abs(di) < std::abs(dj) ? 8 : 0));
+            }
+    return job;
+}
+
 static void build_tables(LevelPlan& lp, double kappa, int buffer, const std::vector<char>& used) {
     const int D = transfer_span(buffer), W = transfer_width(buffer);
     lp.table.assign(transfer_slots(buffer), {});
@@ -889,7 +924,7 @@ std::string build_host_plan(HostPlan& hp) {
             if (v > 1024) return "N_phi above 1024 is not supported";
     }
     build_tree(hp);
-    for (int l = 2; l <= hp.lf; ++l) {
+    for (int l = 2; l <= hp.lf && hp.host_tables; ++l) {
         std::vector<char> used(transfer_slots(hp.buffer), 0);
         for (int32_t v : hp.levels[l].iv) used[v] = 1;
         build_tables(hp.lp[l], hp.kappa, hp.buffer, used);

@@ -14,7 +14,7 @@ from ._native import MAX_LEVELS
 _PREC_NAMES = {0: "fp64", 1: "fp32", 2: "df"}   # hfmm_level_precision codes
 
 def make_options(precision="fp64", alphas=None, eps_scale=0.25, max_leaf=64, depth=0, root=None,
-                 max_rhs=1, device=0, require_far=False, leaf_table_bytes=-1, buffer=1):
+                 max_rhs=1, device=0, require_far=False, leaf_table_bytes=-1, buffer=1, host_tables=False):
     opt = nat.Options()
     nat.lib().hfmm_default_options(ctypes.byref(opt))
     if alphas is not None:              # None keeps the library default ladder
@@ -30,7 +30,7 @@ def make_options(precision="fp64", alphas=None, eps_scale=0.25, max_leaf=64, dep
     opt.precision = {"fp64": nat.PREC_FP64, "mixed": nat.PREC_MIXED}[precision]
     opt.max_rhs = max_rhs
     opt.device = device
-    opt.flags = nat.FLAG_REQUIRE_FAR if require_far else 0
+    opt.flags = (nat.FLAG_REQUIRE_FAR if require_far else 0) | (nat.FLAG_HOST_TABLES if host_tables else 0)
     opt.leaf_table_bytes = int(leaf_table_bytes)
     opt.buffer = int(buffer)
     return opt
@@ -45,19 +45,20 @@ class FmmPlan:
     require_far: raise (HFMM_ERR_UNSTABLE) instead of planning a pure near field.
     leaf_table_bytes: device bytes allowed for the plane-wave tables of a float64 leaf level
     (-1: up to half the free device memory, 0: none).
+    host_tables: compute the transfer tables on the host (default: on the device when there is one).
     buffer: buffer boxes between a box and its interaction list, 1 or 2 (Section 3.3.3), or 0:
     chosen with the leaf level by the plan's cost model (the "auto" plan shape).
     """
 
     def __init__(self, sources, targets, kappa, eps, precision="fp64", alphas=None,
                  eps_scale=0.25, max_leaf=64, depth=0, root=None, max_rhs=1, device=0,
-                 require_far=False, leaf_table_bytes=-1, buffer=1):
+                 require_far=False, leaf_table_bytes=-1, buffer=1, host_tables=False):
         L = nat.lib()
         src = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 3)
         tgt = np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 3)
         self.same = sources is targets
         opt = make_options(precision, alphas, eps_scale, max_leaf, depth, root, max_rhs, device,
-                           require_far, leaf_table_bytes, buffer)
+                           require_far, leaf_table_bytes, buffer, host_tables)
         h = ctypes.c_void_p()
         nat.check(L.hfmm_plan(src.ctypes.data, src.shape[0], tgt.ctypes.data, tgt.shape[0],
                               float(kappa), float(eps), ctypes.byref(opt), ctypes.byref(h)))
