@@ -50,6 +50,9 @@ struct DevLevel {
     // count, and per parent the union of the children's lists (box, child mask, slot per child
     // for the forward and the transposed M2L)
     std::vector<int32_t> slot_host;   // compact table slot of every transfer vector
+    // M2L per box (k_m2l_box): CSR lists with the table slot of every entry (forward, transposed)
+    int32_t *ioff = nullptr, *iidx = nullptr, *islot = nullptr, *islot_t = nullptr;
+    bool m2l_sib = false;             // M2L kernel the plan timed faster on this level
     int npar = 0;
     int32_t *pfirst = nullptr, *pnch = nullptr, *poff = nullptr, *pu = nullptr, *pmask = nullptr;
     int32_t *pslot = nullptr, *pslot_t = nullptr;
@@ -243,6 +246,17 @@ hfmm_status upload_level(hfmm_plan_s* P, int l) {
     std::vector<int32_t> slot_t(nslots, 0);
     for (int v = 0; v < nslots; ++v) slot_t[v] = slot[nslots - 1 - v];
     d.slot_host = slot;
+    {
+        std::vector<int32_t> es(T.iv.size()), est(T.iv.size());
+        for (size_t t = 0; t < T.iv.size(); ++t) {
+            es[t] = slot[T.iv[t]];
+            est[t] = slot_t[T.iv[t]];
+        }
+        TRY(upload(P, &d.ioff, T.ioff));
+        TRY(upload(P, &d.iidx, T.iidx));
+        TRY(upload(P, &d.islot, es));
+        TRY(upload(P, &d.islot_t, est));
+    }
     {
         // sibling groups: the children of each parent are contiguous at this level
         const TreeLevel& PL = hp.levels[l - 1];
@@ -712,10 +726,19 @@ void launch_m2m_t(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
 template <typename S, typename C>
 void launch_m2l(hfmm_plan_s* P, int l, int R, cudaStream_t st, bool transposed) {
     DevLevel& d = P->lev[l];
-    const dim3 g(d.npar, nblk(d.K, 128));
-    const int32_t* ps = transposed ? d.pslot_t : d.pslot;
     const cx<S>* in = (const cx<S>*)(transposed ? d.IL : d.M);
     cx<S>* out = (cx<S>*)(transposed ? d.M : d.IL);
+    if (!d.m2l_sib) {
+        const dim3 g(d.nbox, nblk(d.K, 128));
+        const int32_t* es = transposed ? d.islot_t : d.islot;
+        if (R == 1)
+            k_m2l_box<S, C, 1><<<g, 128, 0, st>>>(d.K, d.ioff, d.iidx, es, (const cx<S>*)d.table, in, R, out);
+        else
+            k_m2l_box<S, C, 2><<<g, 128, 0, st>>>(d.K, d.ioff, d.iidx, es, (const cx<S>*)d.table, in, R, out);
+        return;
+    }
+    const dim3 g(d.npar, nblk(d.K, 128));
+    const int32_t* ps = transposed ? d.pslot_t : d.pslot;
     if (d.npar == 0) return;
     if (R == 1)
         k_m2l_sib<S, C, 1><<<g, 128, 0, st>>>(d.K, d.pfirst, d.pnch, d.poff, d.pu, d.pmask, ps,
@@ -736,6 +759,34 @@ void launch_sym(int variant, int nunits, const int2* units, const int32_t* start
         case 8: k_p2p_mixed_sym_warp<8><<<g, 128, 0, st>>>(units, nunits, start, count, noff, nidx, a, q, phi); break;
         default: k_p2p_mixed_sym_warp<7><<<g, 128, 0, st>>>(units, nunits, start, count, noff, nidx, a, q, phi); break;
     }
+}
+
+void run_m2l(hfmm_plan_s* P, int l, int R, cudaStream_t st, bool transposed);
+
+// Kernel tuner for M2L: time the per-box and the sibling-group kernels on each level (the
+// plan's own lists and tables, the apply's workspace, max_rhs right-hand sides; one warm-up
+// and one timed launch each) and keep the faster.  Both give the same result.
+hfmm_status tune_m2l(hfmm_plan_s* P) {
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int l = 2; l <= P->hp.lf; ++l) {
+        float t[2] = {0.f, 0.f};
+        for (int v = 0; v < 2; ++v) {
+            P->lev[l].m2l_sib = v == 1;
+            run_m2l(P, l, P->rmax, 0, false);
+            CK(cudaEventRecord(e0, 0));
+            run_m2l(P, l, P->rmax, 0, false);
+            CK(cudaEventRecord(e1, 0));
+            CK(cudaEventSynchronize(e1));
+            CK(cudaEventElapsedTime(&t[v], e0, e1));
+        }
+        P->lev[l].m2l_sib = t[1] < t[0];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaGetLastError());
+    return HFMM_OK;
 }
 
 // Kernel tuner: time each register budget of the symmetric near field on the plan's own units
@@ -1102,6 +1153,7 @@ hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, 
     if (opt.device >= 0) {
         hfmm_status s = upload_plan(P);
         if (s == HFMM_OK) s = tune_sym_variant(P);
+        if (s == HFMM_OK) s = tune_m2l(P);
         if (s != HFMM_OK) {
             std::string msg = g_err;
             hfmm_destroy(P);

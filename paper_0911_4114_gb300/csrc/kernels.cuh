@@ -1339,7 +1339,10 @@ template <typename C>
 struct M2LAcc {
     cx<C> v;
     __device__ __forceinline__ void zero() { v = mk<C>(rval<C>(0.0), rval<C>(0.0)); }
-    __device__ __forceinline__ void mac(cx<C> t, cx<C> m) { v = v + t * m; }
+    __device__ __forceinline__ void mac(cx<C> t, cx<C> m) {   // four FMA
+        v.x = fma(t.x, m.x, fma(-t.y, m.y, v.x));
+        v.y = fma(t.x, m.y, fma(t.y, m.x, v.y));
+    }
     __device__ __forceinline__ cx<C> get() const { return v; }
 };
 template <>
@@ -1355,12 +1358,41 @@ struct M2LAcc<df> {
     __device__ __forceinline__ cx<df> get() const { return mk<df>(dfacc_get(x), dfacc_get(y)); }
 };
 
+// M2L per box: one thread per (box, sample) sums its interaction list in list order
+// (Morton order); islot is the table slot of every list entry.
+template <typename S, typename C, int kRC>
+__global__ void k_m2l_box(int64_t K, const int32_t* __restrict__ ioff, const int32_t* __restrict__ iidx,
+                          const int32_t* __restrict__ islot, const cx<S>* __restrict__ T,
+                          const cx<S>* __restrict__ M, int R_, cx<S>* __restrict__ I) {
+    const int a = blockIdx.x;
+    const int64_t k = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const int l0 = ioff[a], l1 = ioff[a + 1];
+    for (int r0 = 0; r0 < R_; r0 += kRC) {
+        const int rn = min(kRC, R_ - r0);
+        M2LAcc<C> acc[kRC];
+#pragma unroll
+        for (int r = 0; r < kRC; ++r) acc[r].zero();
+        for (int t = l0; t < l1; ++t) {
+            const int b = iidx[t];
+            const cx<C> tv = cvt<C>(T[(int64_t)islot[t] * K + k]);
+#pragma unroll
+            for (int r = 0; r < kRC; ++r)
+                if (r < rn) acc[r].mac(tv, cvt<C>(M[((int64_t)b * R_ + r0 + r) * K + k]));
+        }
+#pragma unroll
+        for (int r = 0; r < kRC; ++r)
+            if (r < rn) I[((int64_t)a * R_ + r0 + r) * K + k] = cvt<S>(acc[r].get());
+    }
+}
+
 // M2L by sibling groups: one block per (parent box, tile of samples) evaluates the lists of
 // all children of the parent together.  The children's lists are subsets of one union (the
 // children of the parent's neighbours), so each partner signature is read once for all
 // siblings that list it (a per-entry mask) instead of once per sibling: with two buffer
 // boxes (lists up to 875 entries) the partner reads drop about sevenfold.  Each child still
-// sums its own entries in Morton order (the order of its list), as a per-box loop would.
+// sums its own entries in Morton order (the order of its list), as k_m2l_box does, so the two
+// give the same result; the plan times both on each level and keeps the faster.
 // Union entry e of parent p: box pu[e], children mask pmask[e] (bit c = child c lists it),
 // table slot pslot[8 e + c] of child c's transfer vector.
 template <typename S, typename C, int kRC>
