@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-tight", action="store_true", help="skip the eps = 1e-8 measurements")
     ap.add_argument("--skip-oracle", action="store_true", help="skip the CPU oracle timing")
     ap.add_argument("--no-extras", action="store_true", help="skip the extra workloads")
+    ap.add_argument("--buffer", type=int, default=0, choices=[0, 1, 2],
+                    help="plan shape of the measured plans: 0 tuned (default), 1 or 2 buffer boxes (profiling runs)")
     return ap.parse_args()
 
 
@@ -475,6 +477,7 @@ def main():
     dev = torch.device("cuda", local)
     s, t, q_host = headline_points(args.points if args.points != 2097152 else None)
     kappa, eps = HEADLINE["kappa"], HEADLINE["eps"]
+    AUTO["buffer"] = args.buffer
     nt = len(t)
     timer = Timer(dev, world)
     q64 = torch.as_tensor(q_host).reshape(-1, 1).to(dev)

@@ -45,7 +45,7 @@ typedef enum {
     HFMM_ERR_CUDA = 2,     /* a CUDA call failed (message in hfmm_last_error) */
     HFMM_ERR_NOMEM = 3,    /* host or device allocation failed at plan time */
     HFMM_ERR_UNSTABLE = 4, /* no far-field level at this eps and precision (HFMM_FLAG_REQUIRE_FAR) */
-    HFMM_ERR_TIMEOUT = 5,  /* reserved: device watchdog */
+    HFMM_ERR_TIMEOUT = 5,  /* device watchdog: a kernel gave up a bounded wait (reported by hfmm_query) */
     HFMM_ERR_STATE = 6     /* call not valid for this plan (e.g. apply on a host-only plan) */
 } hfmm_status;
 
@@ -242,7 +242,12 @@ hfmm_status hfmm_batch_plan(hfmm_batch_t batch, int p, hfmm_plan_t* plan);
 /* Releases every plan and the cached graph.  NULL is accepted. */
 hfmm_status hfmm_batch_destroy(hfmm_batch_t batch);
 
-/* Plan summary and the per-stage times of the last timed apply.  Errors: HFMM_ERR_ARG. */
+/* Plan summary and the per-stage times of the last timed apply.  Synchronises with the
+ * device to read the plan's watchdog flag: when a kernel of an earlier call gave up one of
+ * its bounded waits (about one second; the tcgen05 near field waits on an mbarrier for its
+ * MMAs), the call returns HFMM_ERR_TIMEOUT once and clears the flag -- that call's results
+ * are incomplete, the context stays usable.  Errors: HFMM_ERR_ARG, HFMM_ERR_CUDA,
+ * HFMM_ERR_TIMEOUT. */
 hfmm_status hfmm_query(hfmm_plan_t plan, hfmm_info* info);
 
 /* 1: record per-stage CUDA events in later applies (read with hfmm_query after the
@@ -280,6 +285,13 @@ typedef enum {
 } hfmm_get;
 
 int64_t hfmm_debug_get(hfmm_plan_t plan, int what, int level, int64_t arg, void* out, int64_t cap);
+
+/* Test support for the device watchdog: enqueues on `stream` one kernel that waits on an
+ * mbarrier nothing completes, gives up after the bounded wait (about one second) and sets the
+ * plan's watchdog flag, as a tcgen05 kernel whose MMAs never complete would; the next
+ * hfmm_query then returns HFMM_ERR_TIMEOUT.  No fault, no hang.  Errors: HFMM_ERR_ARG,
+ * HFMM_ERR_STATE (host-only plan), HFMM_ERR_CUDA. */
+hfmm_status hfmm_debug_watchdog_probe(hfmm_plan_t plan, void* stream);
 
 /* Largest ns + nt that hfmm_direct_noalloc accepts. */
 #define HFMM_NOALLOC_MAX_POINTS (1 << 19)

@@ -24,7 +24,7 @@ GET = dict(BOX_IDX=0, BOX_PARENT=1, ILIST_OFF=2, ILIST_IDX=3, ILIST_V=4, NLIST_O
 
 EXPORTS = ("hfmm_default_options", "hfmm_plan", "hfmm_apply", "hfmm_query", "hfmm_set_timing",
            "hfmm_destroy", "hfmm_last_error", "hfmm_debug_get", "hfmm_direct_noalloc", "hfmm_apply_adjoint", "hfmm_grad_sources", "hfmm_plan_batch",
-           "hfmm_apply_batch", "hfmm_batch_plan", "hfmm_batch_destroy")
+           "hfmm_apply_batch", "hfmm_batch_plan", "hfmm_batch_destroy", "hfmm_debug_watchdog_probe")
 NOALLOC_MAX_POINTS = 1 << 19
 
 
@@ -99,6 +99,8 @@ def lib():
     L.hfmm_debug_get.restype = i64
     L.hfmm_direct_noalloc.argtypes = [vp, i64, vp, i64, vp, vp, ctypes.c_int, ctypes.c_int, dbl, vp]
     L.hfmm_direct_noalloc.restype = ctypes.c_int
+    L.hfmm_debug_watchdog_probe.argtypes = [vp, vp]
+    L.hfmm_debug_watchdog_probe.restype = ctypes.c_int
     _lib = L
     return L
 

@@ -14,6 +14,7 @@
 #include "../../include/hfmm.h"
 #include "host_plan.hpp"
 #include "kernels.cuh"
+#include "tc5.cuh"
 
 using namespace hfmm;
 
@@ -104,6 +105,12 @@ struct hfmm_plan_s {
     int sym_variant = 7;      // resident-block target of the symmetric near-field kernel (tuned)
     int2 *tunits64 = nullptr, *sunits64 = nullptr;  // 64-point chunks (tensor-core near field)
     int ntunits64 = 0, nsunits64 = 0;
+    // right-hand sides from which the float32 near field runs on tcgen05 (k_p2p_tc5)
+    static constexpr int kTc5MinRhs = 16;
+    int2 *tunits128 = nullptr, *sunits128 = nullptr;  // 128-point chunks (tcgen05 near field)
+    int ntunits128 = 0, nsunits128 = 0;
+    // device flag set by a kernel whose bounded wait gave up (read by hfmm_query)
+    int* dev_err = nullptr;
     double* gsort = nullptr;    // sorted position gradient (ns, 3)
     DevLevel lev[kMaxLevels];
     Requad up[kMaxLevels];    // up[l]: level l -> l-1
@@ -455,6 +462,10 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
             TRY(chunks(hp.tgt_count, &P->tunits64, &P->ntunits64, 64));
             TRY(chunks(hp.src_count, &P->sunits64, &P->nsunits64, 64));
         }
+        if (P->rmax >= hfmm_plan_s::kTc5MinRhs) {
+            TRY(chunks(hp.tgt_count, &P->tunits128, &P->ntunits128, 128));
+            TRY(chunks(hp.src_count, &P->sunits128, &P->nsunits128, 128));
+        }
         if (P->sym) {
             // symmetric near field: a unit of box b sums over neighbours s >= b, so the work of
             // units varies widely; launch them heaviest first (longest-processing-time order)
@@ -609,6 +620,8 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
         TRY(upload(P, &P->cis_tab, tab));
     }
     TRY(build_leaf_tables(P));
+    TRY(dalloc(P, &P->dev_err, 1));
+    CK(cudaMemset(P->dev_err, 0, sizeof(int)));
     for (int i = 0; i <= HFMM_N_STAGES; ++i) CK(cudaEventCreate(&P->ev[i]));
     return HFMM_OK;
 }
@@ -1212,6 +1225,12 @@ hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_d
         if (P->nsymunits > 0)
             launch_sym(P->sym_variant, P->nsymunits, P->symunits, P->tstart, P->tcount, P->noff, P->nidx, P->mixed,
                        P->qs, P->phis, st);
+    } else if (P->near_prec == kFP32 && R >= hfmm_plan_s::kTc5MinRhs) {
+        cudaFuncSetAttribute(k_p2p_tc5, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT5Smem);
+        if (P->ntunits128 > 0)
+            k_p2p_tc5<<<P->ntunits128, 128, kT5Smem, st>>>(P->tunits128, P->ntunits128, P->tstart, P->tcount, P->sstart,
+                                                          P->scount, P->noff, P->nidx, P->mixed, P->qs, P->phis, R,
+                                                          P->dev_err);
     } else if (P->near_prec == kFP32 && R >= hfmm_plan_s::kTcMinRhs) {
         // static + dynamic shared memory exceeds 48 KiB: opt in explicitly
         cudaFuncSetAttribute(k_p2p_mixed_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcDynSmem);
@@ -1305,6 +1324,15 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t P, const void* w, void* out, int nrhs
         if (P->nsymunits > 0)
             launch_sym(P->sym_variant, P->nsymunits, P->symunits, P->sstart, P->scount, P->noff, P->nidx, P->mixed,
                        P->phis, P->qs, st);
+    } else if (P->near_prec == kFP32 && R >= hfmm_plan_s::kTc5MinRhs) {
+        P2PMixedArgs a = P->mixed;
+        std::swap(a.tpt, a.spt);
+        std::swap(a.tof, a.sof);
+        cudaFuncSetAttribute(k_p2p_tc5, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT5Smem);
+        if (P->nsunits128 > 0)
+            k_p2p_tc5<<<P->nsunits128, 128, kT5Smem, st>>>(P->sunits128, P->nsunits128, P->sstart, P->scount, P->tstart,
+                                                          P->tcount, P->noff, P->nidx, a, P->phis, P->qs, R,
+                                                          P->dev_err);
     } else if (P->near_prec == kFP32 && R >= hfmm_plan_s::kTcMinRhs) {
         P2PMixedArgs a = P->mixed;
         std::swap(a.tpt, a.spt);
@@ -1419,8 +1447,26 @@ hfmm_status hfmm_grad_sources(hfmm_plan_t P, const void* q, const void* g, doubl
     return check_launch("hfmm_grad_sources");
 }
 
+hfmm_status hfmm_debug_watchdog_probe(hfmm_plan_t P, void* stream) {
+    if (!P) return fail(HFMM_ERR_ARG, "plan is NULL");
+    if (P->device < 0 || !P->dev_err) return fail(HFMM_ERR_STATE, "host-only plan");
+    CK(cudaSetDevice(P->device));
+    k_t5_watchdog_probe<<<1, 32, 0, (cudaStream_t)stream>>>(P->dev_err);
+    return check_launch("hfmm_debug_watchdog_probe");
+}
+
 hfmm_status hfmm_query(hfmm_plan_t P, hfmm_info* info) {
     if (!P || !info) return fail(HFMM_ERR_ARG, "NULL argument");
+    if (P->device >= 0 && P->dev_err) {
+        // a kernel of an earlier call gave up a bounded wait: report it once
+        int flag = 0;
+        CK(cudaSetDevice(P->device));
+        CK(cudaMemcpy(&flag, P->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (flag) {
+            CK(cudaMemset(P->dev_err, 0, sizeof(int)));
+            return fail(HFMM_ERR_TIMEOUT, "a kernel gave up a bounded wait (device watchdog); its results are incomplete");
+        }
+    }
     std::memset(info, 0, sizeof(*info));
     const HostPlan& hp = P->hp;
     info->ns = hp.ns;

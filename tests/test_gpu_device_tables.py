@@ -41,13 +41,16 @@ def test_device_tables_match_host_and_oracle(name, kappa, eps, kw):
             a, b = dev.debug_get("TABLE", l, v), host.debug_get("TABLE", l, v)
             c = orc.table(l, v)
             scale = np.max(np.abs(c))
-            assert np.max(np.abs(a - b)) <= 1e-13 * scale, (name, l, v)
+            # two float64 evaluations of the same steps in different orders (sums of many
+            # terms of both signs): measured up to 8e-13 of max |T|
+            assert np.max(np.abs(a - b)) <= 1e-11 * scale, (name, l, v)
             assert np.max(np.abs(a - c)) <= max(1e-11, 1e3 * est) * scale, (name, l, v)
 
 
 def test_device_table_storage_precisions_and_apply():
     """Mixed policy (float32 and double-float levels store their tables in their own type):
-    the stored tables round the host's float64 tables to that type; the float64 and mixed
+    the stored tables equal the host's float64 tables rounded to that type (float32: 2e-7;
+    double-float and float64: the 1e-11 agreement of two float64 evaluations); the float64 and mixed
     applies with device tables agree with those with host tables to round-off."""
     g = wl.rng(141)
     x = wl.cube(4000, g)
@@ -59,7 +62,7 @@ def test_device_table_storage_precisions_and_apply():
         ref = FmmPlan(x, x, kappa, eps, precision=prec, device=-1, **kw)
         info = dev.info()
         for l, lev in info["levels"].items():
-            tol = {"fp32": 2e-7, "df": 1e-13, "fp64": 1e-13}[lev["precision"]]
+            tol = {"fp32": 2e-7, "df": 1e-11, "fp64": 1e-11}[lev["precision"]]
             v = int(ref.debug_get("ILIST_V", l)[0])
             a, b = dev.debug_get("TABLE", l, v), ref.debug_get("TABLE", l, v)
             assert np.max(np.abs(a - b)) <= tol * np.max(np.abs(b)), (prec, eps, l)
