@@ -12,10 +12,10 @@
 // grid form of the float32 near field) and the charge rows, store both operands in shared
 // memory in the canonical K-major layout without swizzle (8 x 16-byte core matrices; leading
 // byte offset 128 between core matrices along K, stride byte offset 1024 between 8-row
-// groups), and one thread issues the MMAs (M = 128, N = 128, K = 8 each) into a 128-column
-// tensor-memory accumulator.  Completion is tracked by an mbarrier (tcgen05.commit); every
-// 32 tiles (512 sources) the accumulator is read back (tcgen05.ld) and added to the float64
-// result, which bounds the float32 accumulation length.  Every wait on the mbarrier gives up
+// groups), and one thread issues the MMAs (M = 128, N = 128, K = 8 each) into one of two
+// 128-column tensor-memory accumulators.  Completion is tracked by an mbarrier
+// (tcgen05.commit); each tile's sums are read back (tcgen05.ld) and added in float32
+// registers, and every 64 tiles (1024 sources) into the float64 result.  Every wait on the mbarrier gives up
 // after about one second of wall time: the CTA then records HFMM's timeout flag, waits
 // (bounded again) for its own MMAs, frees its tensor memory and returns.
 #pragma once
@@ -31,7 +31,7 @@ constexpr int kT5Src = 16;         // sources per tile (K = 32: real and imagina
 constexpr int kT5Rhs = 64;         // right-hand sides per pass (MMA N = 128)
 constexpr int kT5K = 2 * kT5Src;
 constexpr int kT5N = 2 * kT5Rhs;
-constexpr int kT5Flush = 32;       // tiles accumulated in tensor memory between float64 flushes
+constexpr int kT5Flush = 64;       // tiles summed in float32 registers between float64 flushes
 constexpr uint32_t kT5Lbo = 128;   // bytes between core matrices along K
 constexpr uint32_t kT5Sbo = (kT5K / 4) * 128;   // bytes between 8-row groups (1024)
 constexpr size_t kT5Op = (size_t)kT5M * kT5K * 4;   // bytes of one operand part (16 KB)
@@ -154,6 +154,11 @@ __device__ __forceinline__ void t5_ld32(uint32_t taddr, float* v) {
 
 // One CTA (128 threads) per (target box, 128-target chunk).  phis rows of the chunk are
 // overwritten.  err: set to 1 when a wait gave up (the result is then incomplete).
+// Each tile's MMAs write a fresh accumulator (the tensor pipe's float32 accumulation over
+// many tiles loses accuracy: measured 7e-6 relative after 512 sources against 4e-7 per
+// tile); two accumulators alternate, so the CUDA cores add tile i - 1's sums into their
+// float32 registers while the MMAs of tile i run.  Every kT5Flush tiles the registers are
+// added to the float64 rows.
 __global__ void __launch_bounds__(128) k_p2p_tc5(
     const int2* __restrict__ units, int nunits, const int32_t* __restrict__ tstart,
     const int32_t* __restrict__ tcount, const int32_t* __restrict__ sstart, const int32_t* __restrict__ scount,
@@ -163,7 +168,6 @@ __global__ void __launch_bounds__(128) k_p2p_tc5(
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
     __shared__ float4 shp[kT5Src], sho[kT5Src];
-    __shared__ int abort_flag;
     const int u = blockIdx.x;
     if (u >= nunits) return;                                   // block-uniform
     unsigned char* base = t5_smem + ((1024 - (smem_u32(t5_smem) & 1023)) & 1023);
@@ -175,18 +179,18 @@ __global__ void __launch_bounds__(128) k_p2p_tc5(
     const uint32_t mb = smem_u32(&mbar);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"((uint32_t)kT5N));
+                     "r"((uint32_t)(2 * kT5N)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
         asm volatile("fence.mbarrier_init.release.cluster;");
-        abort_flag = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_slot;
+    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
     const int b = units[u].x, c0 = units[u].y;
     const int t0 = tstart[b], tc = tcount[b];
     const bool active = c0 + tid < tc;
@@ -197,64 +201,76 @@ __global__ void __launch_bounds__(128) k_p2p_tc5(
     }
     uint32_t phase = 0;
     bool inflight = false;
+    bool my_abort = false;   // one of this thread's waits gave up
+    bool aborted = false;    // some thread's did (block-uniform: from a barrier reduction)
     const uint32_t a_hi_s = smem_u32(a_hi), a_lo_s = smem_u32(a_lo), b_hi_s = smem_u32(b_hi), b_lo_s = smem_u32(b_lo);
-    // read the accumulator back and add it (scaled to length units) to the float64 rows
-    auto flush = [&](int r0, bool first) {
-        if (inflight) {
-            if (!t5_wait(mb, phase)) atomicExch(&abort_flag, 1);
-            phase ^= 1u;
-            inflight = false;
-        }
+    float accr[kT5Rhs], acci[kT5Rhs];   // this thread's row: float32 sums of the tiles since the last flush
+
+    // wait for the MMAs in flight (their operands and accumulator are then free)
+    auto wait_mma = [&]() {
+        if (!inflight) return;
+        if (!t5_wait(mb, phase)) my_abort = true;
+        phase ^= 1u;
+        inflight = false;
+    };
+    // add accumulator `slot` (after its MMAs completed) into the registers
+    auto gather = [&](int slot) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const int rn = min(kT5Rhs, R - r0);
-        const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+        const uint32_t col = tmem + lane_base + (uint32_t)(slot * kT5N);
+#pragma unroll
         for (int h = 0; h < kT5Rhs / 32; ++h) {
-            float re[32], im[32];
-            t5_ld32(tmem + lane_base + (uint32_t)(32 * h), re);
-            t5_ld32(tmem + lane_base + (uint32_t)(kT5Rhs + 32 * h), im);
-            if (active)
-                for (int i = 0; i < 32; ++i) {
-                    const int r = 32 * h + i;
-                    if (r < rn) {
-                        cxd& o = phis[(int64_t)(t0 + c0 + tid) * R + r0 + r];
-                        const double x = a.inv_unit * (double)re[i], y = a.inv_unit * (double)im[i];
-                        if (first) o = mk<double>(x, y);
-                        else o = mk<double>(o.x + x, o.y + y);
-                    }
+            float v[32];
+            t5_ld32(col + (uint32_t)(32 * h), v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) accr[32 * h + i] += v[i];
+            t5_ld32(col + (uint32_t)(kT5Rhs + 32 * h), v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) acci[32 * h + i] += v[i];
+        }
+    };
+    // registers into the float64 rows (scaled to length units); `first` overwrites them
+    auto flush = [&](int r0, bool first) {
+        if (active) {
+            const int rn = min(kT5Rhs, R - r0);
+#pragma unroll
+            for (int r = 0; r < kT5Rhs; ++r)
+                if (r < rn) {
+                    cxd& o = phis[(int64_t)(t0 + c0 + tid) * R + r0 + r];
+                    const double x = a.inv_unit * (double)accr[r], y = a.inv_unit * (double)acci[r];
+                    if (first) o = mk<double>(x, y);
+                    else o = mk<double>(o.x + x, o.y + y);
                 }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kT5Rhs; ++r) accr[r] = acci[r] = 0.f;
     };
+
     for (int r0 = 0; r0 < R; r0 += kT5Rhs) {
-        int tiles = 0;        // tiles in the accumulator since the last flush
-        bool first = true;    // the next flush overwrites the rows
-        for (int nb = noff[b]; nb < noff[b + 1]; ++nb) {
+#pragma unroll
+        for (int r = 0; r < kT5Rhs; ++r) accr[r] = acci[r] = 0.f;
+        int tile = 0;          // tiles issued in this pass
+        int since = 0;         // tiles gathered since the last flush
+        bool first = true;     // the next flush overwrites the rows
+        for (int nb = noff[b]; nb < noff[b + 1] && !aborted; ++nb) {
             const int s = nidx[nb];
             const int s0 = sstart[s], sc = scount[s];
             for (int sb = 0; sb < sc; sb += kT5Src) {
                 const int sn = min(kT5Src, sc - sb);
-                if (inflight) {                                  // the MMAs still read the operands
-                    if (!t5_wait(mb, phase)) atomicExch(&abort_flag, 1);
-                    phase ^= 1u;
-                    inflight = false;
-                }
                 if (tid < kT5Src) {
                     shp[tid] = tid < sn ? a.spt[s0 + sb + tid] : make_float4(0, 0, 0, 0);
                     sho[tid] = tid < sn ? a.sof[s0 + sb + tid] : make_float4(0, 0, 0, 0);
                 }
-                __syncthreads();
-                if (abort_flag) break;                           // block-uniform after the barrier
+                aborted = __syncthreads_or(my_abort) != 0;       // block-uniform
+                if (aborted) break;
+                float rowa[kT5K], rowb[kT5K];
                 // A row: kernel values of this thread's target against the tile's sources
-                float row[kT5K];
 #pragma unroll
                 for (int j = 0; j < kT5Src; ++j) {
                     cxf g = mk<float>(0.f, 0.f);
                     if (active && j < sn) g = t5_green(gp, op, shp[j], sho[j], a.tau_hi, a.tau_lo);
-                    row[j] = g.x;
-                    row[kT5Src + j] = g.y;
+                    rowa[j] = g.x;
+                    rowa[kT5Src + j] = g.y;
                 }
-                t5_store_row(a_hi, a_lo, tid, row);
                 // B row n = tid: right-hand side r = n mod 64, real (n < 64) or imaginary part
                 {
                     const int r = tid % kT5Rhs;
@@ -267,57 +283,58 @@ __global__ void __launch_bounds__(128) k_p2p_tc5(
                             qr = (float)q.x;
                             qi = (float)q.y;
                         }
-                        row[j] = im ? qi : qr;
-                        row[kT5Src + j] = im ? qr : -qi;
+                        rowb[j] = im ? qi : qr;
+                        rowb[kT5Src + j] = im ? qr : -qi;
                     }
                 }
-                t5_store_row(b_hi, b_lo, tid, row);
+                wait_mma();                                      // tile - 1 done: operands free
+                t5_store_row(a_hi, a_lo, tid, rowa);
+                t5_store_row(b_hi, b_lo, tid, rowb);
                 asm volatile("fence.proxy.async.shared::cta;");
                 asm volatile("tcgen05.fence::before_thread_sync;");
                 __syncthreads();
                 if (tid == 0) {
                     asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t dcol = tmem + (uint32_t)((tile & 1) * kT5N);
 #pragma unroll
                     for (int ks = 0; ks < kT5K / 8; ++ks) {
                         const uint32_t ko = (uint32_t)ks * 2u * kT5Lbo;
                         const uint64_t ah = t5_desc(a_hi_s + ko), al = t5_desc(a_lo_s + ko);
                         const uint64_t bh = t5_desc(b_hi_s + ko), bl = t5_desc(b_lo_s + ko);
-                        t5_mma(tmem, ah, bh, (tiles > 0 || ks > 0) ? 1u : 0u);
-                        t5_mma(tmem, ah, bl, 1u);
-                        t5_mma(tmem, al, bh, 1u);
+                        t5_mma(dcol, ah, bh, ks > 0 ? 1u : 0u);
+                        t5_mma(dcol, ah, bl, 1u);
+                        t5_mma(dcol, al, bh, 1u);
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb));
                 }
                 inflight = true;
-                if (++tiles == kT5Flush) {
-                    flush(r0, first);
-                    first = false;
-                    tiles = 0;
+                if (tile > 0) {                                  // tile - 1's sums, beside tile's MMAs
+                    gather((tile - 1) & 1);
+                    if (++since == kT5Flush) {
+                        flush(r0, first);
+                        first = false;
+                        since = 0;
+                    }
                 }
-            }
-            if (abort_flag) break;
-        }
-        if (abort_flag) break;
-        if (tiles > 0 || first) {
-            if (tiles == 0) {                                    // no source at all: zero rows
-                if (active)
-                    for (int r = 0; r < min(kT5Rhs, R - r0); ++r)
-                        phis[(int64_t)(t0 + c0 + tid) * R + r0 + r] = mk<double>(0.0, 0.0);
-            } else {
-                flush(r0, first);
+                ++tile;
             }
         }
+        if (aborted) break;
+        if (tile > 0) {
+            wait_mma();
+            gather((tile - 1) & 1);
+        }
+        flush(r0, first);                                        // also zero rows without sources
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
     }
-    if (inflight) {
-        if (!t5_wait(mb, phase)) atomicExch(&abort_flag, 1);
-        inflight = false;
-    }
+    wait_mma();
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    if (tid == 0 && abort_flag) atomicExch(err, 1);
+    aborted = __syncthreads_or(my_abort) != 0;
+    if (tid == 0 && aborted) atomicExch(err, 1);
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kT5N));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * kT5N)));
     }
 }
 
