@@ -263,7 +263,8 @@ def run_reference(args, rank, world):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(HEADLINE, points=len(t), l2="n/a (host)"),
+            "config": dict(HEADLINE, points=len(t), l2="n/a (host)",
+                           plan_shape=f"oracle plan, {smp.plan.buffer} buffer box(es), L_f = {smp.plan.lf}"),
             "cpu_baseline": {"value": value, "unit": "Mpoints*RHS/s", "cores": oracle_threads(), "kind": "oracle",
                              "sample": smp.sample_text()},
             "e2e": {"value": value, "unit": "Mpoints*RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
