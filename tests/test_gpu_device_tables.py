@@ -9,7 +9,7 @@ import pytest
 from oracle import fmm as ofmm
 from oracle import quadrature as oq
 from paper_0911_4114_gb300 import FmmPlan, workloads as wl
-from gpu_util import fp64_round_est, run_apply
+from gpu_util import fp64_parity_tol, run_apply
 
 pytestmark = pytest.mark.gpu
 
@@ -69,5 +69,7 @@ def test_device_table_storage_precisions_and_apply():
         q = wl.charges(len(x), 0, g)
         got, want = run_apply(dev, q), run_apply(hst, q)
         orc = ofmm.Plan(x, x, kappa, eps, precision=prec, **kw)
-        tol = max(1e-12, 16.0 * fp64_round_est(orc)) if prec == "fp64" else eps / 10
+        # float64: two sets of tables that agree to round-off give applies that agree to the
+        # float64 parity bound (the quadrature sums amplify the table differences)
+        tol = fp64_parity_tol(orc) if prec == "fp64" else eps / 10
         assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want)), (prec, eps)
