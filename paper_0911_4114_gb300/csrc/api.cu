@@ -109,6 +109,7 @@ struct hfmm_plan_s {
     static constexpr int kTc5MinRhs = 16;
     int2 *tunits128 = nullptr, *sunits128 = nullptr;  // 128-point chunks (tcgen05 near field)
     int ntunits128 = 0, nsunits128 = 0;
+    cxf* qf32 = nullptr;      // (max(ns, nt), max_rhs) charges in float32 for the tcgen05 near field
     // device flag set by a kernel whose bounded wait gave up (read by hfmm_query)
     int* dev_err = nullptr;
     double* gsort = nullptr;    // sorted position gradient (ns, 3)
@@ -465,6 +466,7 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
         if (P->rmax >= hfmm_plan_s::kTc5MinRhs) {
             TRY(chunks(hp.tgt_count, &P->tunits128, &P->ntunits128, 128));
             TRY(chunks(hp.src_count, &P->sunits128, &P->nsunits128, 128));
+            TRY(dalloc(P, &P->qf32, (size_t)std::max(hp.ns, hp.nt) * P->rmax));
         }
         if (P->sym) {
             // symmetric near field: a unit of box b sums over neighbours s >= b, so the work of
@@ -1227,9 +1229,10 @@ hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_d
                        P->qs, P->phis, st);
     } else if (P->near_prec == kFP32 && R >= hfmm_plan_s::kTc5MinRhs) {
         cudaFuncSetAttribute(k_p2p_tc5, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT5Smem);
+        k_charges_f32<<<nblk(hp.ns * R, 256), 256, 0, st>>>(P->qs, hp.ns * R, P->qf32);
         if (P->ntunits128 > 0)
             k_p2p_tc5<<<P->ntunits128, 128, kT5Smem, st>>>(P->tunits128, P->ntunits128, P->tstart, P->tcount, P->sstart,
-                                                          P->scount, P->noff, P->nidx, P->mixed, P->qs, P->phis, R,
+                                                          P->scount, P->noff, P->nidx, P->mixed, P->qf32, P->phis, R,
                                                           P->dev_err);
     } else if (P->near_prec == kFP32 && R >= hfmm_plan_s::kTcMinRhs) {
         // static + dynamic shared memory exceeds 48 KiB: opt in explicitly
@@ -1329,9 +1332,10 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t P, const void* w, void* out, int nrhs
         std::swap(a.tpt, a.spt);
         std::swap(a.tof, a.sof);
         cudaFuncSetAttribute(k_p2p_tc5, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT5Smem);
+        k_charges_f32<<<nblk(hp.nt * R, 256), 256, 0, st>>>(P->phis, hp.nt * R, P->qf32);
         if (P->nsunits128 > 0)
             k_p2p_tc5<<<P->nsunits128, 128, kT5Smem, st>>>(P->sunits128, P->nsunits128, P->sstart, P->scount, P->tstart,
-                                                          P->tcount, P->noff, P->nidx, a, P->phis, P->qs, R,
+                                                          P->tcount, P->noff, P->nidx, a, P->qf32, P->qs, R,
                                                           P->dev_err);
     } else if (P->near_prec == kFP32 && R >= hfmm_plan_s::kTcMinRhs) {
         P2PMixedArgs a = P->mixed;

@@ -152,8 +152,15 @@ __device__ __forceinline__ void t5_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// One CTA (128 threads) per (target box, 128-target chunk).  phis rows of the chunk are
-// overwritten.  err: set to 1 when a wait gave up (the result is then incomplete).
+// charges rounded to float32 once per apply (the float64 -> float32 conversion runs on the
+// float64 pipe, which the per-tile loads of the near field must not touch)
+__global__ void k_charges_f32(const cxd* __restrict__ q, int64_t n, cxf* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = mk<float>((float)q[i].x, (float)q[i].y);
+}
+
+// One CTA (128 threads) per (target box, 128-target chunk); qs: the charges in float32
+// (k_charges_f32).  phis rows of the chunk are overwritten.  err: set to 1 when a wait gave up (the result is then incomplete).
 // Each tile's MMAs write a fresh accumulator (the tensor pipe's float32 accumulation over
 // many tiles loses accuracy: measured 7e-6 relative after 512 sources against 4e-7 per
 // tile); two accumulators alternate, so the CUDA cores add tile i - 1's sums into their
@@ -163,7 +170,7 @@ __global__ void __launch_bounds__(128) k_p2p_tc5(
     const int2* __restrict__ units, int nunits, const int32_t* __restrict__ tstart,
     const int32_t* __restrict__ tcount, const int32_t* __restrict__ sstart, const int32_t* __restrict__ scount,
     const int32_t* __restrict__ noff, const int32_t* __restrict__ nidx, P2PMixedArgs a,
-    const cxd* __restrict__ qs, cxd* __restrict__ phis, int R, int* __restrict__ err) {
+    const cxf* __restrict__ qs, cxd* __restrict__ phis, int R, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char t5_smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
@@ -279,9 +286,9 @@ __global__ void __launch_bounds__(128) k_p2p_tc5(
                     for (int j = 0; j < kT5Src; ++j) {
                         float qr = 0.f, qi = 0.f;
                         if (j < sn && r0 + r < R) {
-                            const cxd q = qs[(int64_t)(s0 + sb + j) * R + r0 + r];
-                            qr = (float)q.x;
-                            qi = (float)q.y;
+                            const cxf q = qs[(int64_t)(s0 + sb + j) * R + r0 + r];
+                            qr = q.x;
+                            qi = q.y;
                         }
                         rowb[j] = im ? qi : qr;
                         rowb[kT5Src + j] = im ? qr : -qi;
