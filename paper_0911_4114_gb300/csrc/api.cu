@@ -107,9 +107,16 @@ struct hfmm_plan_s {
     int ntunits64 = 0, nsunits64 = 0;
     // right-hand sides from which the float32 near field runs on tcgen05 (k_p2p_tc5)
     static constexpr int kTc5MinRhs = 16;
-    int2 *tunits128 = nullptr, *sunits128 = nullptr;  // 128-point chunks (tcgen05 near field)
-    int ntunits128 = 0, nsunits128 = 0;
-    cxf* qf32 = nullptr;      // (max(ns, nt), max_rhs) charges in float32 for the tcgen05 near field
+    // tcgen05 near field, per side (s: sources, t: targets): 16-point tiles of every leaf box
+    // (first sorted point, count) and each box's first tile; units (box, first point of a
+    // 128-chunk, tiles over the neighbour list of the other side) grouped per CTA
+    int32_t *t5first_s = nullptr, *t5n_s = nullptr, *t5base_s = nullptr;
+    int32_t *t5first_t = nullptr, *t5n_t = nullptr, *t5base_t = nullptr;
+    int t5ntiles_s = 0, t5ntiles_t = 0;
+    int4 *t5units_fwd = nullptr, *t5units_adj = nullptr;   // forward: target chunks; adjoint: source chunks
+    int32_t *t5off_fwd = nullptr, *t5off_adj = nullptr;
+    int t5cta_fwd = 0, t5cta_adj = 0;
+    unsigned char* t5blk = nullptr;   // split charge operands, (tile, 64-RHS pass) blocks
     // device flag set by a kernel whose bounded wait gave up (read by hfmm_query)
     int* dev_err = nullptr;
     double* gsort = nullptr;    // sorted position gradient (ns, 3)
@@ -428,6 +435,98 @@ hfmm_status build_leaf_tables(hfmm_plan_s* P) {
     return HFMM_OK;
 }
 
+// tcgen05 near field (k_p2p_tc5): the 16-point tiles of both sides, the units of both
+// directions dealt round robin in Morton order to one persistent CTA per SM, and the
+// split-charge block buffer for max_rhs right-hand sides.  Round robin keeps the units that
+// the CTAs work on at one time next to each other, so their neighbour lists, and the charge
+// blocks they read, largely coincide (the blocks are then read from L2)
+hfmm_status build_t5(hfmm_plan_s* P) {
+    HostPlan& hp = P->hp;
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->device));
+    nsm = std::max(nsm, 1);
+    auto tiles = [&](const std::vector<int32_t>& start, const std::vector<int32_t>& count, int32_t** dfirst,
+                     int32_t** dn, int32_t** dbase, int* ntiles) -> hfmm_status {
+        std::vector<int32_t> first, n, base(count.size(), 0);
+        for (size_t b = 0; b < count.size(); ++b) {
+            base[b] = (int32_t)first.size();
+            for (int c = 0; c < count[b]; c += kT5Src) {
+                first.push_back(start[b] + c);
+                n.push_back(std::min(kT5Src, count[b] - c));
+            }
+        }
+        *ntiles = (int)first.size();
+        TRY(upload(P, dfirst, first));
+        TRY(upload(P, dn, n));
+        TRY(upload(P, dbase, base));
+        return HFMM_OK;
+    };
+    TRY(tiles(hp.src_start, hp.src_count, &P->t5first_s, &P->t5n_s, &P->t5base_s, &P->t5ntiles_s));
+    TRY(tiles(hp.tgt_start, hp.tgt_count, &P->t5first_t, &P->t5n_t, &P->t5base_t, &P->t5ntiles_t));
+    auto sched = [&](const std::vector<int32_t>& ucount, const std::vector<int32_t>& ocount, int4** du,
+                     int32_t** doff, int* ncta) -> hfmm_status {
+        std::vector<int4> u;
+        for (size_t b = 0; b < ucount.size(); ++b) {
+            int nt = 0;
+            for (int32_t t = hp.noff[b]; t < hp.noff[b + 1]; ++t) nt += (ocount[hp.nidx[t]] + kT5Src - 1) / kT5Src;
+            for (int c = 0; c < ucount[b]; c += kT5M) u.push_back(make_int4((int)b, c, nt, 0));
+        }
+        const int nc = std::max(1, std::min(nsm, (int)u.size()));
+        std::vector<std::vector<int4>> bins(nc);
+        for (size_t k = 0; k < u.size(); ++k) bins[k % nc].push_back(u[k]);
+        std::vector<int4> flat;
+        std::vector<int32_t> off(1, 0);
+        for (const auto& bin : bins) {
+            flat.insert(flat.end(), bin.begin(), bin.end());
+            off.push_back((int32_t)flat.size());
+        }
+        *ncta = nc;
+        TRY(upload(P, du, flat));
+        TRY(upload(P, doff, off));
+        return HFMM_OK;
+    };
+    TRY(sched(hp.tgt_count, hp.src_count, &P->t5units_fwd, &P->t5off_fwd, &P->t5cta_fwd));
+    TRY(sched(hp.src_count, hp.tgt_count, &P->t5units_adj, &P->t5off_adj, &P->t5cta_adj));
+    const size_t npass = (size_t)(P->rmax + kT5Rhs - 1) / kT5Rhs;
+    TRY(dalloc(P, &P->t5blk, (size_t)std::max(P->t5ntiles_s, P->t5ntiles_t) * npass * kT5Blk));
+    return HFMM_OK;
+}
+
+// tcgen05 near field of one direction: split the charge operands, then the persistent kernel
+// (forward: target chunks over source tiles, q -> phi; adjoint: source chunks over target
+// tiles, w -> A^H w)
+void launch_t5(hfmm_plan_s* P, bool adjoint, int R, cudaStream_t st) {
+    const int npass = (R + kT5Rhs - 1) / kT5Rhs;
+    const int ntiles = adjoint ? P->t5ntiles_t : P->t5ntiles_s;
+    const cxd* in = adjoint ? P->phis : P->qs;
+    if (ntiles > 0)
+        k_t5_bsplit<<<(unsigned)((int64_t)ntiles * npass), 256, 0, st>>>(adjoint ? P->t5first_t : P->t5first_s,
+                                                                         adjoint ? P->t5n_t : P->t5n_s, ntiles,
+                                                                         npass, in, R, P->t5blk);
+    T5Args g{};
+    g.units = adjoint ? P->t5units_adj : P->t5units_fwd;
+    g.cta_off = adjoint ? P->t5off_adj : P->t5off_fwd;
+    g.tstart = adjoint ? P->sstart : P->tstart;
+    g.tcount = adjoint ? P->scount : P->tcount;
+    g.sstart = adjoint ? P->tstart : P->sstart;
+    g.scount = adjoint ? P->tcount : P->scount;
+    g.noff = P->noff;
+    g.nidx = P->nidx;
+    g.stbase = adjoint ? P->t5base_t : P->t5base_s;
+    g.bblk = P->t5blk;
+    g.a = P->mixed;
+    if (adjoint) {
+        std::swap(g.a.tpt, g.a.spt);
+        std::swap(g.a.tof, g.a.sof);
+    }
+    g.phis = adjoint ? P->qs : P->phis;
+    g.R = R;
+    g.err = P->dev_err;
+    const int ncta = adjoint ? P->t5cta_adj : P->t5cta_fwd;
+    cudaFuncSetAttribute(k_p2p_tc5, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT5Smem);
+    k_p2p_tc5<<<ncta, kT5Threads, kT5Smem, st>>>(g);
+}
+
 hfmm_status upload_plan(hfmm_plan_s* P) {
     HostPlan& hp = P->hp;
     CK(cudaSetDevice(P->device));
@@ -463,11 +562,7 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
             TRY(chunks(hp.tgt_count, &P->tunits64, &P->ntunits64, 64));
             TRY(chunks(hp.src_count, &P->sunits64, &P->nsunits64, 64));
         }
-        if (P->rmax >= hfmm_plan_s::kTc5MinRhs) {
-            TRY(chunks(hp.tgt_count, &P->tunits128, &P->ntunits128, 128));
-            TRY(chunks(hp.src_count, &P->sunits128, &P->nsunits128, 128));
-            TRY(dalloc(P, &P->qf32, (size_t)std::max(hp.ns, hp.nt) * P->rmax));
-        }
+        if (P->rmax >= hfmm_plan_s::kTc5MinRhs) TRY(build_t5(P));
         if (P->sym) {
             // symmetric near field: a unit of box b sums over neighbours s >= b, so the work of
             // units varies widely; launch them heaviest first (longest-processing-time order)
@@ -1228,12 +1323,7 @@ hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_d
             launch_sym(P->sym_variant, P->nsymunits, P->symunits, P->tstart, P->tcount, P->noff, P->nidx, P->mixed,
                        P->qs, P->phis, st);
     } else if (P->near_prec == kFP32 && R >= hfmm_plan_s::kTc5MinRhs) {
-        cudaFuncSetAttribute(k_p2p_tc5, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT5Smem);
-        k_charges_f32<<<nblk(hp.ns * R, 256), 256, 0, st>>>(P->qs, hp.ns * R, P->qf32);
-        if (P->ntunits128 > 0)
-            k_p2p_tc5<<<P->ntunits128, 128, kT5Smem, st>>>(P->tunits128, P->ntunits128, P->tstart, P->tcount, P->sstart,
-                                                          P->scount, P->noff, P->nidx, P->mixed, P->qf32, P->phis, R,
-                                                          P->dev_err);
+        launch_t5(P, false, R, st);
     } else if (P->near_prec == kFP32 && R >= hfmm_plan_s::kTcMinRhs) {
         // static + dynamic shared memory exceeds 48 KiB: opt in explicitly
         cudaFuncSetAttribute(k_p2p_mixed_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcDynSmem);
@@ -1328,15 +1418,7 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t P, const void* w, void* out, int nrhs
             launch_sym(P->sym_variant, P->nsymunits, P->symunits, P->sstart, P->scount, P->noff, P->nidx, P->mixed,
                        P->phis, P->qs, st);
     } else if (P->near_prec == kFP32 && R >= hfmm_plan_s::kTc5MinRhs) {
-        P2PMixedArgs a = P->mixed;
-        std::swap(a.tpt, a.spt);
-        std::swap(a.tof, a.sof);
-        cudaFuncSetAttribute(k_p2p_tc5, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT5Smem);
-        k_charges_f32<<<nblk(hp.nt * R, 256), 256, 0, st>>>(P->phis, hp.nt * R, P->qf32);
-        if (P->nsunits128 > 0)
-            k_p2p_tc5<<<P->nsunits128, 128, kT5Smem, st>>>(P->sunits128, P->nsunits128, P->sstart, P->scount, P->tstart,
-                                                          P->tcount, P->noff, P->nidx, a, P->qf32, P->qs, R,
-                                                          P->dev_err);
+        launch_t5(P, true, R, st);
     } else if (P->near_prec == kFP32 && R >= hfmm_plan_s::kTcMinRhs) {
         P2PMixedArgs a = P->mixed;
         std::swap(a.tpt, a.spt);
