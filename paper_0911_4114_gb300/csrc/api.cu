@@ -108,14 +108,17 @@ struct hfmm_plan_s {
     // right-hand sides from which the float32 near field runs on tcgen05 (k_p2p_tc5)
     static constexpr int kTc5MinRhs = 16;
     // tcgen05 near field, per side (s: sources, t: targets): 16-point tiles of every leaf box
-    // (first sorted point, count) and each box's first tile; units (box, first point of a
-    // 128-chunk, tiles over the neighbour list of the other side) grouped per CTA
-    int32_t *t5first_s = nullptr, *t5n_s = nullptr, *t5base_s = nullptr;
-    int32_t *t5first_t = nullptr, *t5n_t = nullptr, *t5base_t = nullptr;
+    // (first sorted point, count); per direction the units (box, first point of a 128-chunk,
+    // tiles over the neighbour list of the other side) grouped per CTA with their tile records
+    int32_t *t5first_s = nullptr, *t5n_s = nullptr;
+    int32_t *t5first_t = nullptr, *t5n_t = nullptr;
     int t5ntiles_s = 0, t5ntiles_t = 0;
-    int4 *t5units_fwd = nullptr, *t5units_adj = nullptr;   // forward: target chunks; adjoint: source chunks
-    int32_t *t5off_fwd = nullptr, *t5off_adj = nullptr;
-    int t5cta_fwd = 0, t5cta_adj = 0;
+    struct T5Dir {            // one direction (forward: target chunks; adjoint: source chunks)
+        int4* units = nullptr;
+        int32_t *cta_off = nullptr, *rec_off = nullptr;
+        int2* recs = nullptr;
+        int ncta = 0;
+    } t5fwd, t5adj;
     unsigned char* t5blk = nullptr;   // split charge operands, (tile, 64-RHS pass) blocks
     // device flag set by a kernel whose bounded wait gave up (read by hfmm_query)
     int* dev_err = nullptr;
@@ -445,9 +448,10 @@ hfmm_status build_t5(hfmm_plan_s* P) {
     int nsm = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P->device));
     nsm = std::max(nsm, 1);
-    auto tiles = [&](const std::vector<int32_t>& start, const std::vector<int32_t>& count, int32_t** dfirst,
-                     int32_t** dn, int32_t** dbase, int* ntiles) -> hfmm_status {
-        std::vector<int32_t> first, n, base(count.size(), 0);
+    auto tiles = [&](const std::vector<int32_t>& start, const std::vector<int32_t>& count, std::vector<int32_t>& base,
+                     int32_t** dfirst, int32_t** dn, int* ntiles) -> hfmm_status {
+        std::vector<int32_t> first, n;
+        base.assign(count.size(), 0);
         for (size_t b = 0; b < count.size(); ++b) {
             base[b] = (int32_t)first.size();
             for (int c = 0; c < count[b]; c += kT5Src) {
@@ -455,16 +459,19 @@ hfmm_status build_t5(hfmm_plan_s* P) {
                 n.push_back(std::min(kT5Src, count[b] - c));
             }
         }
+        if (first.size() >= (size_t(1) << 27)) return fail(HFMM_ERR_ARG, "too many near-field tiles");
         *ntiles = (int)first.size();
         TRY(upload(P, dfirst, first));
         TRY(upload(P, dn, n));
-        TRY(upload(P, dbase, base));
         return HFMM_OK;
     };
-    TRY(tiles(hp.src_start, hp.src_count, &P->t5first_s, &P->t5n_s, &P->t5base_s, &P->t5ntiles_s));
-    TRY(tiles(hp.tgt_start, hp.tgt_count, &P->t5first_t, &P->t5n_t, &P->t5base_t, &P->t5ntiles_t));
-    auto sched = [&](const std::vector<int32_t>& ucount, const std::vector<int32_t>& ocount, int4** du,
-                     int32_t** doff, int* ncta) -> hfmm_status {
+    std::vector<int32_t> sbase, tbase;
+    TRY(tiles(hp.src_start, hp.src_count, sbase, &P->t5first_s, &P->t5n_s, &P->t5ntiles_s));
+    TRY(tiles(hp.tgt_start, hp.tgt_count, tbase, &P->t5first_t, &P->t5n_t, &P->t5ntiles_t));
+    // units of one side (128-point chunks of its boxes) dealt round robin, and for every unit
+    // the records of the other side's tiles over its neighbour list
+    auto sched = [&](const std::vector<int32_t>& ucount, const std::vector<int32_t>& ostart,
+                     const std::vector<int32_t>& ocount, const std::vector<int32_t>& obase, hfmm_plan_s::T5Dir* d) -> hfmm_status {
         std::vector<int4> u;
         for (size_t b = 0; b < ucount.size(); ++b) {
             int nt = 0;
@@ -475,18 +482,32 @@ hfmm_status build_t5(hfmm_plan_s* P) {
         std::vector<std::vector<int4>> bins(nc);
         for (size_t k = 0; k < u.size(); ++k) bins[k % nc].push_back(u[k]);
         std::vector<int4> flat;
-        std::vector<int32_t> off(1, 0);
+        std::vector<int32_t> off(1, 0), roff;
+        std::vector<int2> recs;
         for (const auto& bin : bins) {
-            flat.insert(flat.end(), bin.begin(), bin.end());
+            for (const int4& x : bin) {
+                if (recs.size() + (size_t)x.z >= (size_t)INT32_MAX) return fail(HFMM_ERR_ARG, "too many near-field tiles");
+                roff.push_back((int32_t)recs.size());
+                for (int32_t t = hp.noff[x.x]; t < hp.noff[x.x + 1]; ++t) {
+                    const int32_t s = hp.nidx[t];
+                    for (int c = 0; c < ocount[s]; c += kT5Src) {
+                        const int sn = std::min(kT5Src, ocount[s] - c);
+                        recs.push_back(make_int2(ostart[s] + c, (obase[s] + c / kT5Src) | ((sn - 1) << 27)));
+                    }
+                }
+                flat.push_back(x);
+            }
             off.push_back((int32_t)flat.size());
         }
-        *ncta = nc;
-        TRY(upload(P, du, flat));
-        TRY(upload(P, doff, off));
+        d->ncta = nc;
+        TRY(upload(P, &d->units, flat));
+        TRY(upload(P, &d->cta_off, off));
+        TRY(upload(P, &d->rec_off, roff));
+        TRY(upload(P, &d->recs, recs));
         return HFMM_OK;
     };
-    TRY(sched(hp.tgt_count, hp.src_count, &P->t5units_fwd, &P->t5off_fwd, &P->t5cta_fwd));
-    TRY(sched(hp.src_count, hp.tgt_count, &P->t5units_adj, &P->t5off_adj, &P->t5cta_adj));
+    TRY(sched(hp.tgt_count, hp.src_start, hp.src_count, sbase, &P->t5fwd));
+    TRY(sched(hp.src_count, hp.tgt_start, hp.tgt_count, tbase, &P->t5adj));
     const size_t npass = (size_t)(P->rmax + kT5Rhs - 1) / kT5Rhs;
     TRY(dalloc(P, &P->t5blk, (size_t)std::max(P->t5ntiles_s, P->t5ntiles_t) * npass * kT5Blk));
     return HFMM_OK;
@@ -503,16 +524,14 @@ void launch_t5(hfmm_plan_s* P, bool adjoint, int R, cudaStream_t st) {
         k_t5_bsplit<<<(unsigned)((int64_t)ntiles * npass), 256, 0, st>>>(adjoint ? P->t5first_t : P->t5first_s,
                                                                          adjoint ? P->t5n_t : P->t5n_s, ntiles,
                                                                          npass, in, R, P->t5blk);
+    const hfmm_plan_s::T5Dir& d = adjoint ? P->t5adj : P->t5fwd;
     T5Args g{};
-    g.units = adjoint ? P->t5units_adj : P->t5units_fwd;
-    g.cta_off = adjoint ? P->t5off_adj : P->t5off_fwd;
+    g.units = d.units;
+    g.cta_off = d.cta_off;
     g.tstart = adjoint ? P->sstart : P->tstart;
     g.tcount = adjoint ? P->scount : P->tcount;
-    g.sstart = adjoint ? P->tstart : P->sstart;
-    g.scount = adjoint ? P->tcount : P->scount;
-    g.noff = P->noff;
-    g.nidx = P->nidx;
-    g.stbase = adjoint ? P->t5base_t : P->t5base_s;
+    g.rec_off = d.rec_off;
+    g.recs = d.recs;
     g.bblk = P->t5blk;
     g.a = P->mixed;
     if (adjoint) {
@@ -522,9 +541,8 @@ void launch_t5(hfmm_plan_s* P, bool adjoint, int R, cudaStream_t st) {
     g.phis = adjoint ? P->qs : P->phis;
     g.R = R;
     g.err = P->dev_err;
-    const int ncta = adjoint ? P->t5cta_adj : P->t5cta_fwd;
     cudaFuncSetAttribute(k_p2p_tc5, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT5Smem);
-    k_p2p_tc5<<<ncta, kT5Threads, kT5Smem, st>>>(g);
+    k_p2p_tc5<<<d.ncta, kT5Threads, kT5Smem, st>>>(g);
 }
 
 hfmm_status upload_plan(hfmm_plan_s* P) {

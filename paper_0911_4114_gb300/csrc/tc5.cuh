@@ -2,40 +2,43 @@
 // (tcgen05.mma kind::tf32, accumulators in tensor memory), one persistent CTA per SM.
 //
 // The near-field sum phi_t,r = sum_s G(x_t, y_s) q_s,r over a target chunk's neighbour
-// sources is, for a chunk of 128 targets, a complex GEMM.  Per tile of 16 sources it is done
-// as two real GEMMs over K = 32 (the real and imaginary parts of the charges),
-//     Re phi[t][r] = sum_j Re G[t][j] Re q[j][r] + (-Im G[t][j]) Im q[j][r],
-//     Im phi[t][r] = sum_j Im G[t][j] Re q[j][r] +   Re G[t][j]  Im q[j][r],
-// with B[r] = [Re q_r | Im q_r] (64 right-hand sides x 32) shared by both and the A operand of
-// each K step of 8 taken from one of three 128 x 16 blocks [Re G | Im G | -Im G] held side by
-// side (128 x 48).  Each factor is split into two TF32 parts and three products (hi hi, hi
-// lo, lo hi) accumulate in float32 (3xTF32), which keeps float32 accuracy.
+// sources is, for a chunk of 128 targets, a complex GEMM.  Written as one real GEMM per tile
+// of 16 sources,
+//     C[t][n] = sum_k' A[t][k'] B[n][k'],   A = [Re G | Im G]           (128 x 32),
+//     B[r][.] = [Re q_r | -Im q_r], B[64 + r][.] = [Im q_r | Re q_r]    (128 x 32, 64 RHS),
+// so C[t][r] = Re phi and C[t][64 + r] = Im phi.  Each factor is split into two TF32 parts and
+// three products (hi hi, hi lo, lo hi) accumulate in float32 (3xTF32), which keeps float32
+// accuracy.  Both operands are K-major with 128-byte rows (32 TF32 values) in the 128-byte
+// swizzled layout: row r at byte 128 r, its 16-byte chunk c at position c ^ (r mod 8), so
+// the tensor core reads the 8 rows of a K step from 8 different bank groups.
 //
-// The charges do not depend on the target, so their split operand B of every (source tile,
-// 64-RHS pass) is written once per apply into global memory in the shared-memory layout
-// (k_t5_bsplit, 16 KB per block) and copied into shared memory by one bulk asynchronous copy
-// per tile.  The kernel values A depend on both points and are computed in the CTA.  The
-// CTA's warps have fixed roles around a ring of three shared-memory stages and three
-// tensor-memory accumulators:
-//   * 8 producer warps: for each tile wait until its stage is free, start the B copy (one
-//     thread), evaluate the 128 x 16 kernel values of the exact-grid float32 form (two threads
-//     per target row, 8 sources each), split them and store A hi / lo in the canonical K-major
-//     layout without swizzle (8 x 16-byte core matrices; 128 bytes between core matrices along
-//     K, one 8-row group after the other);
-//   * 1 MMA thread: when a stage's A and B are in and an accumulator is free, issue the 24
-//     MMAs (M = 128, N = 64, K = 8; four K steps, three products, real and imaginary part)
-//     into a fresh accumulator and commit to the stage's "free" barrier and the accumulator's
-//     "full" barrier;
+// The charges do not depend on the target, so the split charges of every (source tile,
+// 64-RHS pass), rows [Re q_r | Im q_r], are written once per apply into global memory in this
+// layout (k_t5_bsplit, 16 KB per block) and brought by bulk asynchronous copies into the
+// upper half of a B slot, which the producers then expand in place into the two row blocks of
+// B (a sign change and a swap of halves): B's redundancy never crosses the memory system.  The
+// kernel values A depend on both points and are computed in the CTA.  The CTA's warps have
+// fixed roles around two A slots, four B slots and three tensor-memory accumulators:
+//   * 1 loader warp: walks the CTA's tile records (first source, count, charge block; read 32
+//     at a time) and, as soon as a B slot is free, copies the tile's charges and its source
+//     positions into it, up to four tiles ahead of the producers;
+//   * 8 producer warps: for each tile wait for a free A slot and the tile's B slot, evaluate
+//     the 128 x 16 kernel values of the exact-grid float32 form (two threads per target row,
+//     8 sources each; branch-free, so a thread's eight evaluations interleave), split them,
+//     store A hi / lo and expand B;
+//   * 1 MMA thread: when a tile's A and B are ready and an accumulator is free, issue the 12
+//     MMAs (M = 128, N = 128, K = 8: four K steps of three products) into a fresh accumulator
+//     and commit to the A slot's, the B slot's and the accumulator's barriers;
 //   * 8 epilogue warps (two per 32-lane quarter of tensor memory, 32 right-hand sides each):
 //     read each tile's sums (tcgen05.ld) into float32 registers and release the accumulator;
 //     every 64 tiles the registers are added into a float32 block sum held in the last 128
 //     columns of tensor memory, and at the end of a (target chunk, pass) the total is written
 //     as float64.
 // A fresh accumulator per tile keeps the tensor pipe's float32 accumulation short (12
-// products per sum; summed over 512 sources in one accumulator it measured 7e-6 relative).
-// Every wait gives up after about one second or when another thread of the CTA gave up: the
-// CTA then records HFMM's timeout flag, waits (bounded again) for its own copies and MMAs in
-// flight, frees its tensor memory and returns.
+// products; summed over 512 sources in one accumulator it measured 7e-6 relative).  Every wait
+// gives up after about one second or when another thread of the CTA gave up: the CTA then
+// records HFMM's timeout flag, waits (bounded again) for its own copies and MMAs in flight,
+// frees its tensor memory and returns.
 #pragma once
 #include <stdint.h>
 
@@ -47,24 +50,22 @@ namespace hfmm {
 constexpr int kT5M = 128;          // targets per CTA tile (MMA M)
 constexpr int kT5Src = 16;         // sources per tile (K = 32: real and imaginary parts)
 constexpr int kT5Rhs = 64;         // right-hand sides per pass (MMA N = 128)
-constexpr int kT5K = 2 * kT5Src;     // B columns: real parts, then imaginary parts
-constexpr int kT5AK = 3 * kT5Src;    // A columns: Re G, Im G, -Im G
-constexpr int kT5N = 2 * kT5Rhs;     // accumulator columns: Re phi (64), Im phi (64)
-constexpr int kT5Stages = 3;       // shared-memory ring
+constexpr int kT5K = 2 * kT5Src;   // operand row: 32 TF32 values = 128 bytes
+constexpr int kT5N = 2 * kT5Rhs;
+constexpr int kT5ASlots = 2;       // A (kernel values) ring
+constexpr int kT5BSlots = 4;       // B (charges + source positions) ring, filled ahead by the loader
 constexpr int kT5Acc = 3;          // tensor-memory accumulators of 128 columns
 constexpr uint32_t kT5SumCol = 384;   // float32 block sums: columns 384..511
 constexpr uint32_t kT5Cols = 512;     // tensor-memory columns allocated
 constexpr int kT5Flush = 64;       // tiles summed in registers between block-sum updates
-constexpr int kT5Prod = 8, kT5Epi = 8;   // producer and epilogue warps (then one MMA warp)
-constexpr int kT5Threads = 32 * (kT5Prod + kT5Epi + 1);
-constexpr uint32_t kT5Lbo = 128;   // bytes between core matrices along K
-constexpr uint32_t kT5SboA = (kT5AK / 4) * 128;   // bytes between 8-row groups of A (1536)
-constexpr uint32_t kT5SboB = (kT5K / 4) * 128;    // of B (1024)
-constexpr size_t kT5OpA = (size_t)kT5M * kT5AK * 4;     // one part of A (24 KB)
-constexpr size_t kT5OpB = (size_t)kT5Rhs * kT5K * 4;    // one part of B (8 KB)
-constexpr size_t kT5Blk = 2 * kT5OpB;                   // B hi + lo of one (source tile, pass)
-constexpr size_t kT5Stage = 2 * kT5OpA + kT5Blk;        // A hi, A lo, B hi, B lo (64 KB)
-constexpr size_t kT5Smem = kT5Stages * kT5Stage + 1024;   // + alignment slack
+constexpr int kT5Prod = 8, kT5Epi = 8;   // producer and epilogue warps, then the MMA and loader warps
+constexpr int kT5MmaWarp = kT5Prod + kT5Epi, kT5LoadWarp = kT5MmaWarp + 1;
+constexpr int kT5Threads = 32 * (kT5LoadWarp + 1);
+constexpr size_t kT5Op = (size_t)kT5M * kT5K * 4;   // one operand part (16 KB)
+constexpr size_t kT5Blk = kT5Op;                    // split charges (hi, lo: 64 rows each) of one (tile, pass)
+constexpr size_t kT5Slot = 2 * kT5Op;               // hi and lo part of an A or B slot
+constexpr size_t kT5PosBytes = 2 * kT5Src * 16;     // grid points then offsets (float4)
+constexpr size_t kT5Smem = (kT5ASlots + kT5BSlots) * kT5Slot + kT5BSlots * kT5PosBytes + 1024;   // + alignment
 constexpr unsigned long long kT5WaitNs = 1000000000ull;   // give up a wait after 1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -77,17 +78,20 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// shared-memory matrix descriptor: start >> 4 (bits 0-13), leading byte offset >> 4 (16-29),
-// stride byte offset >> 4 (32-45), fixed 0b001 (46-48), no swizzle
-__device__ __forceinline__ uint64_t t5_desc(uint32_t saddr, uint32_t sbo) {
-    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(kT5Lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
-           (1ull << 46);
+// shared-memory matrix descriptor of a K-major operand in the 128-byte swizzled layout:
+// start >> 4 (bits 0-13), leading byte offset (unused by this layout; 16 >> 4) (16-29),
+// stride byte offset 1024 >> 4 between 8-row groups (32-45), fixed 0b001 (46-48), base offset
+// 0 (49-51: the operands start on 1024-byte boundaries and K steps move the start only
+// within a 128-byte row), swizzle mode 2 = 128-byte (61-63)
+__device__ __forceinline__ uint64_t t5_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
 }
 
 // instruction descriptor of kind::tf32: D float32 (bits 4-5 = 1), A and B TF32 (bits 7-9,
-// 10-12 = 2), both K-major, N >> 3 (bits 17-22), M >> 4 (bits 24-28); N = 64
+// 10-12 = 2), both K-major, N >> 3 (bits 17-22), M >> 4 (bits 24-28)
 __host__ __device__ constexpr uint32_t t5_idesc() {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kT5Rhs >> 3) << 17) | ((uint32_t)(kT5M >> 4) << 24);
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kT5N >> 3) << 17) | ((uint32_t)(kT5M >> 4) << 24);
 }
 
 __device__ __forceinline__ void t5_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
@@ -136,19 +140,31 @@ __device__ __forceinline__ void t5_arrive(uint32_t mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
+__device__ __forceinline__ void t5_expect(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// bulk copy global -> shared (16-byte aligned addresses, a size that is a multiple of 16),
+// completing `bytes` transactions on mbar
+__device__ __forceinline__ void t5_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
 __device__ __forceinline__ uint32_t t5_tf32(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return r;
 }
 
-// byte offset of chunk (row, 4 consecutive K values) in a K-major operand (no swizzle) whose
-// 8-row groups are sbo bytes apart
-__host__ __device__ __forceinline__ uint32_t t5_off(int row, int chunk, uint32_t sbo) {
-    return (uint32_t)(row >> 3) * sbo + (uint32_t)chunk * kT5Lbo + (uint32_t)(row & 7) * 16u;
+// byte offset of 16-byte chunk c (TF32 values 4c .. 4c + 3) of row r in the 128-byte swizzled
+// K-major layout (the operand starts on a 1024-byte boundary)
+__host__ __device__ __forceinline__ uint32_t t5_off(int r, int c) {
+    return (uint32_t)r * 128u + ((uint32_t)(c ^ (r & 7)) << 4);
 }
 
-// four values as TF32 hi and lo parts at chunk offset `off` of the hi and lo operands
+// four values as TF32 hi and lo parts at offset `off` of the hi and lo operands
 __device__ __forceinline__ void t5_store4(unsigned char* hi, unsigned char* lo, uint32_t off, float a, float b,
                                           float c, float d) {
     const uint32_t ha = t5_tf32(a), hb = t5_tf32(b), hc = t5_tf32(c), hd = t5_tf32(d);
@@ -157,22 +173,6 @@ __device__ __forceinline__ void t5_store4(unsigned char* hi, unsigned char* lo, 
                          t5_tf32(c - __uint_as_float(hc)), t5_tf32(d - __uint_as_float(hd)));
     *reinterpret_cast<uint4*>(hi + off) = h;
     *reinterpret_cast<uint4*>(lo + off) = l;
-}
-
-// the same four values negated (the TF32 parts of -x are those of x negated)
-__device__ __forceinline__ void t5_store4_pair(unsigned char* hi, unsigned char* lo, uint32_t off, uint32_t offneg,
-                                               const float* v) {
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        h[i] = t5_tf32(v[i]);
-        l[i] = t5_tf32(v[i] - __uint_as_float(h[i]));
-    }
-    *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-    const uint32_t sg = 0x80000000u;
-    *reinterpret_cast<uint4*>(hi + offneg) = make_uint4(h[0] ^ sg, h[1] ^ sg, h[2] ^ sg, h[3] ^ sg);
-    *reinterpret_cast<uint4*>(lo + offneg) = make_uint4(l[0] ^ sg, l[1] ^ sg, l[2] ^ sg, l[3] ^ sg);
 }
 
 // float32 kernel value of the exact-grid form (as green_grid in kernels.cuh)
@@ -227,11 +227,11 @@ __device__ __forceinline__ void t5_st32(uint32_t taddr, const float* v) {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-// Split charge operand B of every (source tile g, pass p) in the shared-memory layout:
-// block (g, p) at blk + (g * npass + p) * kT5Blk, hi part then lo part, row r = right-hand side
-// p * 64 + r, columns [Re q_j | Im q_j] over the tile's 16 sources.  Tile g covers sources
-// tfirst[g] .. tfirst[g] + tn[g] - 1 (tn <= 16); absent sources and right-hand sides are zero.
-// One block of 256 threads per (g, p); q: the sorted charges (nsrc, R) in float64.
+// Split charges of every (source tile g, pass p) in the swizzled shared-memory layout: block
+// (g, p) at blk + (g * npass + p) * kT5Blk, 64 rows of hi parts then 64 rows of lo parts; row r
+// is [Re q | Im q] of right-hand side p * 64 + r over the tile's 16 sources.  Tile g covers
+// sources tfirst[g] .. tfirst[g] + tn[g] - 1 (tn <= 16); absent sources and right-hand sides
+// are zero.  One block of 256 threads per (g, p); q: the sorted charges (nsrc, R) in float64.
 __global__ void __launch_bounds__(256) k_t5_bsplit(const int32_t* __restrict__ tfirst, const int32_t* __restrict__ tn,
                                                    int ntiles, int npass, const cxd* __restrict__ q, int R,
                                                    unsigned char* __restrict__ blk) {
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(256) k_t5_bsplit(const int32_t* __restrict__ t
     const int g = (int)(gp / npass), p = (int)(gp % npass);
     const int f = tfirst[g], sn = tn[g];
     unsigned char* hi = blk + (size_t)gp * kT5Blk;
-    unsigned char* lo = hi + kT5OpB;
+    unsigned char* lo = hi + kT5Blk / 2;
     for (int e = threadIdx.x; e < kT5Rhs * (kT5K / 4); e += blockDim.x) {
         const int n = e % kT5Rhs, c = e / kT5Rhs;      // row fastest: coalesced charge reads
         const int r = p * kT5Rhs + n;
@@ -255,17 +255,19 @@ __global__ void __launch_bounds__(256) k_t5_bsplit(const int32_t* __restrict__ t
             }
             v[i] = x;
         }
-        t5_store4(hi, lo, t5_off(n, c, kT5SboB), v[0], v[1], v[2], v[3]);
+        t5_store4(hi, lo, t5_off(n, c), v[0], v[1], v[2], v[3]);
     }
 }
 
-// Arguments of k_p2p_tc5.  A unit is (target box, first target of its 128-chunk, tiles over
-// its neighbour list, 0); CTA c takes units cta_off[c] .. cta_off[c + 1] - 1 in order.
-// stbase[s]: index of source box s's first tile in the B blocks.
+// Arguments of k_p2p_tc5.  A unit is (target box, first target of its 128-chunk, number of
+// tiles, 0); CTA c takes units cta_off[c] .. cta_off[c + 1] - 1 in order.  The tiles of unit u
+// (its neighbour boxes' 16-source tiles in list order) are recs[rec_off[u] ..], each (first
+// sorted source, tile index g + (count - 1) << 27); a pass p reads charge block g * npass + p.
 struct T5Args {
     const int4* units;
     const int32_t* cta_off;
-    const int32_t *tstart, *tcount, *sstart, *scount, *noff, *nidx, *stbase;
+    const int32_t *tstart, *tcount, *rec_off;
+    const int2* recs;
     const unsigned char* bblk;
     P2PMixedArgs a;
     cxd* phis;    // (nt, R) sorted: overwritten rows of every unit
@@ -274,36 +276,43 @@ struct T5Args {
 };
 
 struct T5Ctl {
-    uint64_t afull[kT5Stages], bfull[kT5Stages], empty[kT5Stages];
+    uint64_t afull[kT5ASlots], aempty[kT5ASlots], bfull[kT5BSlots], bempty[kT5BSlots];
     uint64_t accfull[kT5Acc], accempty[kT5Acc];
+    int bsn[kT5BSlots];   // sources in the tile of each B slot
     uint32_t tmem;
     int abort;
-    int b_issued, b_used, mma_issued;
+    int b_issued, mma_issued;
 };
 
 __global__ void __launch_bounds__(kT5Threads, 1) k_p2p_tc5(T5Args g) {
     extern __shared__ __align__(1024) unsigned char t5_smem[];
     __shared__ T5Ctl ctl;
     unsigned char* base = t5_smem + ((1024 - (smem_u32(t5_smem) & 1023)) & 1023);
+    unsigned char* aslot = base;                                   // [kT5ASlots][hi, lo]
+    unsigned char* bslot = base + kT5ASlots * kT5Slot;             // [kT5BSlots][hi, lo]
+    float4* pos = reinterpret_cast<float4*>(base + (kT5ASlots + kT5BSlots) * kT5Slot);   // [kT5BSlots][32]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     volatile int* abort = &ctl.abort;
     const int u0 = g.cta_off[blockIdx.x], u1 = g.cta_off[blockIdx.x + 1];
     const int npass = (g.R + kT5Rhs - 1) / kT5Rhs;
     if (tid == 0) {
-        for (int s = 0; s < kT5Stages; ++s) {
+        for (int s = 0; s < kT5ASlots; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&ctl.afull[s])), "r"(kT5Prod));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&ctl.aempty[s])));
+        }
+        for (int s = 0; s < kT5BSlots; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&ctl.bfull[s])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&ctl.empty[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&ctl.bempty[s])));
         }
         for (int a = 0; a < kT5Acc; ++a) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&ctl.accfull[a])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&ctl.accempty[a])), "r"(kT5Epi));
         }
         ctl.abort = 0;
-        ctl.b_issued = ctl.b_used = ctl.mma_issued = 0;
+        ctl.b_issued = ctl.mma_issued = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    if (warp == kT5Prod + kT5Epi) {
+    if (warp == kT5MmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl.tmem)),
                      "r"(kT5Cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -313,75 +322,106 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_p2p_tc5(T5Args g) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = ctl.tmem;
 
-    if (warp < kT5Prod) {
+    if (warp == kT5LoadWarp) {
+        // ---------------- loader: charges and positions of tile i into B slot i mod 4 ----------
+        int i = 0;
+        bool ok = true;
+        for (int u = u0; u < u1 && ok; ++u) {
+            const int nt = g.units[u].z, r0 = g.rec_off[u];
+            for (int p = 0; p < npass && ok; ++p)
+                for (int k0 = 0; k0 < nt && ok; k0 += 32) {
+                    const int2 mine = k0 + lane < nt ? g.recs[r0 + k0 + lane] : make_int2(0, 0);
+                    const int kn = min(32, nt - k0);
+                    for (int k = 0; k < kn; ++k, ++i) {
+                        const int src = __shfl_sync(0xffffffffu, mine.x, k);
+                        const int gt = __shfl_sync(0xffffffffu, mine.y, k);
+                        const int bs = i % kT5BSlots;
+                        ok = t5_wait_ab(smem_u32(&ctl.bempty[bs]), ((i / kT5BSlots) & 1) ^ 1, abort);
+                        ok = __all_sync(0xffffffffu, ok);
+                        if (!ok) break;
+                        if (lane == 0) {
+                            const int sn = (gt >> 27) + 1;
+                            const unsigned char* blk = g.bblk + ((size_t)(gt & ((1 << 27) - 1)) * npass + p) * kT5Blk;
+                            unsigned char* b = bslot + bs * kT5Slot;
+                            const uint32_t fb = smem_u32(&ctl.bfull[bs]);
+                            const uint32_t pb = 16u * (uint32_t)sn;
+                            ctl.bsn[bs] = sn;
+                            t5_expect(fb, (uint32_t)kT5Blk + 2 * pb);
+                            // hi rows into rows 64..127 of B hi, lo rows into rows 64..127 of B lo
+                            t5_copy(smem_u32(b + kT5Op / 2), blk, (uint32_t)(kT5Blk / 2), fb);
+                            t5_copy(smem_u32(b + kT5Op + kT5Op / 2), blk + kT5Blk / 2, (uint32_t)(kT5Blk / 2), fb);
+                            t5_copy(smem_u32(pos + bs * 2 * kT5Src), g.a.spt + src, pb, fb);
+                            t5_copy(smem_u32(pos + bs * 2 * kT5Src + kT5Src), g.a.sof + src, pb, fb);
+                            ctl.b_issued = i + 1;
+                        }
+                    }
+                }
+        }
+    } else if (warp < kT5Prod) {
         // ---------------- producers: kernel values of row `row`, sources 8 h .. 8 h + 7 ----
         const int row = tid & (kT5M - 1), h = tid >> 7;
-        int i = 0;   // tile counter of this CTA
+        int i = 0;
         bool ok = true;
         for (int u = u0; u < u1 && ok; ++u) {
             const int4 un = g.units[u];
-            const int b = un.x, c0 = un.y;
-            const int t0 = g.tstart[b], tc = g.tcount[b];
-            const bool active = c0 + row < tc;
+            if (un.z == 0) continue;
+            const int t0 = g.tstart[un.x], tc = g.tcount[un.x];
+            const bool active = un.y + row < tc;
             float4 gp = make_float4(0, 0, 0, 0), op = gp;
             if (active) {
-                gp = g.a.tpt[t0 + c0 + row];
-                op = g.a.tof[t0 + c0 + row];
+                gp = g.a.tpt[t0 + un.y + row];
+                op = g.a.tof[t0 + un.y + row];
             }
-            for (int p = 0; p < npass && ok; ++p) {
-                for (int nb = g.noff[b]; nb < g.noff[b + 1] && ok; ++nb) {
-                    const int s = g.nidx[nb];
-                    const int s0 = g.sstart[s], sc = g.scount[s], tb = g.stbase[s];
-                    for (int sb = 0; sb < sc; sb += kT5Src, ++i) {
-                        const int st = i % kT5Stages;
-                        ok = t5_wait_ab(smem_u32(&ctl.empty[st]), ((i / kT5Stages) & 1) ^ 1, abort);
-                        ok = __all_sync(0xffffffffu, ok);
-                        if (!ok) break;
-                        unsigned char* stage = base + st * kT5Stage;
-                        if (tid == 0) {
-                            const uint32_t fb = smem_u32(&ctl.bfull[st]);
-                            const unsigned char* src = g.bblk + ((size_t)(tb + sb / kT5Src) * npass + p) * kT5Blk;
-                            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
-                                         "r"((uint32_t)kT5Blk)
-                                         : "memory");
-                            asm volatile(
-                                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
-                                "[%3];" ::"r"(smem_u32(stage + 2 * kT5OpA)),
-                                "l"(src), "r"((uint32_t)kT5Blk), "r"(fb)
-                                : "memory");
-                            ctl.b_issued = i + 1;
-                        }
-                        const int sn = min(kT5Src, sc - sb);
-                        float re[8], imv[8];
+            for (int t = 0; t < npass * un.z; ++t, ++i) {
+                const int as = i % kT5ASlots, bs = i % kT5BSlots;
+                ok = t5_wait_ab(smem_u32(&ctl.aempty[as]), ((i / kT5ASlots) & 1) ^ 1, abort);
+                ok = ok && t5_wait_ab(smem_u32(&ctl.bfull[bs]), (i / kT5BSlots) & 1, abort);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                const float4* sp = pos + bs * 2 * kT5Src;
+                const int sn = ctl.bsn[bs];
+                float re[8], imv[8];
 #pragma unroll
-                        for (int jj = 0; jj < 8; ++jj) {
-                            const int j = 8 * h + jj;
-                            cxf v = mk<float>(0.f, 0.f);
-                            if (active && j < sn) {
-                                const float4 sp = __ldg(&g.a.spt[s0 + sb + j]);
-                                const float4 so = __ldg(&g.a.sof[s0 + sb + j]);
-                                v = t5_green(gp, op, sp, so, g.a.tau_hi, g.a.tau_lo);
-                            }
-                            re[jj] = v.x;
-                            imv[jj] = v.y;
-                        }
-                        unsigned char* ahi = stage;
-                        unsigned char* alo = stage + kT5OpA;
-                        // Re G: chunks 2 h, 2 h + 1; Im G: 4 + 2 h, ...; -Im G: 8 + 2 h, ...
-                        t5_store4(ahi, alo, t5_off(row, 2 * h, kT5SboA), re[0], re[1], re[2], re[3]);
-                        t5_store4(ahi, alo, t5_off(row, 2 * h + 1, kT5SboA), re[4], re[5], re[6], re[7]);
-                        t5_store4_pair(ahi, alo, t5_off(row, 4 + 2 * h, kT5SboA), t5_off(row, 8 + 2 * h, kT5SboA),
-                                       imv);
-                        t5_store4_pair(ahi, alo, t5_off(row, 5 + 2 * h, kT5SboA), t5_off(row, 9 + 2 * h, kT5SboA),
-                                       imv + 4);
-                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        __syncwarp();
-                        if (lane == 0) t5_arrive(smem_u32(&ctl.afull[st]));
+                for (int jj = 0; jj < 8; ++jj) {
+                    const int j = 8 * h + jj;
+                    const int jc = j < sn ? j : 0;        // slot 0 always holds a source
+                    const cxf v = t5_green(gp, op, sp[jc], sp[kT5Src + jc], g.a.tau_hi, g.a.tau_lo);
+                    const bool use = active && j < sn;
+                    re[jj] = use ? v.x : 0.f;
+                    imv[jj] = use ? v.y : 0.f;
+                }
+                unsigned char* ahi = aslot + as * kT5Slot;
+                unsigned char* alo = ahi + kT5Op;
+                // columns 8 h .. 8 h + 7 (real parts: chunks 2 h, 2 h + 1), 16 + 8 h .. (imaginary)
+                t5_store4(ahi, alo, t5_off(row, 2 * h), re[0], re[1], re[2], re[3]);
+                t5_store4(ahi, alo, t5_off(row, 2 * h + 1), re[4], re[5], re[6], re[7]);
+                t5_store4(ahi, alo, t5_off(row, 4 + 2 * h), imv[0], imv[1], imv[2], imv[3]);
+                t5_store4(ahi, alo, t5_off(row, 5 + 2 * h), imv[4], imv[5], imv[6], imv[7]);
+                // expand B: charge row r = [Re q | Im q] (copied to row 64 + r) becomes row r =
+                // [Re q | -Im q] and row 64 + r = [Im q | Re q]; thread (part, r) of the first
+                // four warps
+                if (tid < 2 * kT5Rhs) {
+                    const int r = tid & (kT5Rhs - 1);
+                    unsigned char* bp = bslot + bs * kT5Slot + (tid >> 6) * kT5Op;
+                    uint4 v[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) v[c] = *reinterpret_cast<const uint4*>(bp + t5_off(kT5Rhs + r, c));
+                    const uint32_t sg = 0x80000000u;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        *reinterpret_cast<uint4*>(bp + t5_off(r, c)) = v[c];
+                        *reinterpret_cast<uint4*>(bp + t5_off(r, 4 + c)) =
+                            make_uint4(v[4 + c].x ^ sg, v[4 + c].y ^ sg, v[4 + c].z ^ sg, v[4 + c].w ^ sg);
+                        *reinterpret_cast<uint4*>(bp + t5_off(kT5Rhs + r, c)) = v[4 + c];
+                        *reinterpret_cast<uint4*>(bp + t5_off(kT5Rhs + r, 4 + c)) = v[c];
                     }
                 }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) t5_arrive(smem_u32(&ctl.afull[as]));
             }
         }
-    } else if (warp < kT5Prod + kT5Epi) {
+    } else if (warp < kT5MmaWarp) {
         // ---------------- epilogue: rows 32 q .. 32 q + 31, right-hand sides 32 e .. 32 e + 31 ----
         const int w = warp - kT5Prod, q = w & 3, e = w >> 2;
         const uint32_t lanes = (uint32_t)(32 * q) << 16;
@@ -441,59 +481,49 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_p2p_tc5(T5Args g) {
             }
         }
     } else if (lane == 0) {
-        // ---------------- MMA issue ----------------
+        // ---------------- MMA issue (warp kT5MmaWarp) ----------------
         int i = 0;
         bool ok = true;
         for (int u = u0; u < u1 && ok; ++u) {
             const int nt = g.units[u].z;
-            for (int p = 0; p < npass && ok; ++p)
-                for (int t = 0; t < nt; ++t, ++i) {
-                    const int st = i % kT5Stages, a = i % kT5Acc;
-                    const uint32_t ph = (i / kT5Stages) & 1;
-                    ok = t5_wait_ab(smem_u32(&ctl.bfull[st]), ph, abort);
-                    if (ok) ctl.b_used = i + 1;
-                    ok = ok && t5_wait_ab(smem_u32(&ctl.afull[st]), ph, abort);
-                    ok = ok && t5_wait_ab(smem_u32(&ctl.accempty[a]), ((i / kT5Acc) & 1) ^ 1, abort);
-                    if (!ok) break;
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t s_a = smem_u32(base + st * kT5Stage);
-                    const uint32_t ahi = s_a, alo = s_a + kT5OpA, bhi = s_a + 2 * kT5OpA, blo = bhi + kT5OpB;
-                    const uint32_t d = tmem + (uint32_t)(a * kT5N);
-                    // K step ks covers B chunks 2 ks, 2 ks + 1 (ks < 2: Re q, else Im q).  Re phi
-                    // takes A chunks of Re G then -Im G, Im phi those of Im G then Re G.
+            for (int t = 0; t < npass * nt; ++t, ++i) {
+                const int as = i % kT5ASlots, bs = i % kT5BSlots, a = i % kT5Acc;
+                ok = t5_wait_ab(smem_u32(&ctl.afull[as]), (i / kT5ASlots) & 1, abort);
+                ok = ok && t5_wait_ab(smem_u32(&ctl.accempty[a]), ((i / kT5Acc) & 1) ^ 1, abort);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t ahi = smem_u32(aslot + as * kT5Slot), alo = ahi + kT5Op;
+                const uint32_t bhi = smem_u32(bslot + bs * kT5Slot), blo = bhi + kT5Op;
+                const uint32_t d = tmem + (uint32_t)(a * kT5N);
+                // K step ks: bytes 32 ks .. 32 ks + 31 of every 128-byte row
 #pragma unroll
-                    for (int ks = 0; ks < kT5K / 8; ++ks) {
-                        const uint32_t kb = (uint32_t)ks * 2u * kT5Lbo;
-                        const uint32_t kre = (uint32_t)(ks < 2 ? 2 * ks : 8 + 2 * (ks - 2)) * kT5Lbo;
-                        const uint32_t kim = (uint32_t)(ks < 2 ? 4 + 2 * ks : 2 * (ks - 2)) * kT5Lbo;
-                        const uint64_t bh = t5_desc(bhi + kb, kT5SboB), bl = t5_desc(blo + kb, kT5SboB);
-                        const uint32_t acc = ks > 0 ? 1u : 0u;
-                        t5_mma(d, t5_desc(ahi + kre, kT5SboA), bh, acc);
-                        t5_mma(d, t5_desc(ahi + kre, kT5SboA), bl, 1u);
-                        t5_mma(d, t5_desc(alo + kre, kT5SboA), bh, 1u);
-                        t5_mma(d + kT5Rhs, t5_desc(ahi + kim, kT5SboA), bh, acc);
-                        t5_mma(d + kT5Rhs, t5_desc(ahi + kim, kT5SboA), bl, 1u);
-                        t5_mma(d + kT5Rhs, t5_desc(alo + kim, kT5SboA), bh, 1u);
-                    }
-                    t5_commit(smem_u32(&ctl.empty[st]));
-                    t5_commit(smem_u32(&ctl.accfull[a]));
-                    ctl.mma_issued = i + 1;
+                for (int ks = 0; ks < kT5K / 8; ++ks) {
+                    const uint32_t ko = (uint32_t)ks * 32u;
+                    t5_mma(d, t5_desc(ahi + ko), t5_desc(bhi + ko), ks > 0 ? 1u : 0u);
+                    t5_mma(d, t5_desc(ahi + ko), t5_desc(blo + ko), 1u);
+                    t5_mma(d, t5_desc(alo + ko), t5_desc(bhi + ko), 1u);
                 }
+                t5_commit(smem_u32(&ctl.aempty[as]));
+                t5_commit(smem_u32(&ctl.bempty[bs]));
+                t5_commit(smem_u32(&ctl.accfull[a]));
+                ctl.mma_issued = i + 1;
+            }
         }
     }
     __syncthreads();
     if (ctl.abort) {
-        // drain what this CTA still has in flight before its shared and tensor memory go
+        // drain what this CTA still has in flight before its shared and tensor memory go: the
+        // latest copy of every B slot, then the MMAs (their last commit covers all before it)
         if (tid == 0) {
-            for (int i = ctl.b_used; i < ctl.b_issued; ++i)
-                t5_wait(smem_u32(&ctl.bfull[i % kT5Stages]), (i / kT5Stages) & 1);
+            for (int i = max(0, ctl.b_issued - kT5BSlots); i < ctl.b_issued; ++i)
+                t5_wait(smem_u32(&ctl.bfull[i % kT5BSlots]), (i / kT5BSlots) & 1);
             const int m = ctl.mma_issued;
             if (m > 0) t5_wait(smem_u32(&ctl.accfull[(m - 1) % kT5Acc]), ((m - 1) / kT5Acc) & 1);
             atomicExch(g.err, 1);
         }
         __syncthreads();
     }
-    if (warp == kT5Prod + kT5Epi) {
+    if (warp == kT5MmaWarp) {
         __syncwarp();
         asm volatile("tcgen05.fence::after_thread_sync;");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kT5Cols));
