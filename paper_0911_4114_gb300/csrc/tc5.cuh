@@ -8,9 +8,11 @@
 //     B[r][.] = [Re q_r | -Im q_r], B[64 + r][.] = [Im q_r | Re q_r]    (128 x 32, 64 RHS),
 // so C[t][r] = Re phi and C[t][64 + r] = Im phi.  Each factor is split into two TF32 parts and
 // three products (hi hi, hi lo, lo hi) accumulate in float32 (3xTF32), which keeps float32
-// accuracy.  Both operands are K-major with 128-byte rows (32 TF32 values) in the 128-byte
-// swizzled layout: row r at byte 128 r, its 16-byte chunk c at position c ^ (r mod 8), so
-// the tensor core reads the 8 rows of a K step from 8 different bank groups.
+// accuracy.  A is read by the MMAs from tensor memory (row t in lane t, one TF32 value per
+// column), so neither its stores nor its reads take shared-memory bandwidth, which the MMAs'
+// B reads and the charge copies need.  B is K-major with 128-byte rows (32 TF32 values) in the
+// 128-byte swizzled shared-memory layout: row r at byte 128 r, its 16-byte chunk c at position
+// c ^ (r mod 8), so the tensor core reads the 8 rows of a K step from 8 different bank groups.
 //
 // The charges do not depend on the target, so the split charges of every (source tile,
 // 64-RHS pass), rows [Re q_r | Im q_r], are written once per apply into global memory in this
@@ -18,14 +20,15 @@
 // upper half of a B slot, which the producers then expand in place into the two row blocks of
 // B (a sign change and a swap of halves): B's redundancy never crosses the memory system.  The
 // kernel values A depend on both points and are computed in the CTA.  The CTA's warps have
-// fixed roles around two A slots, four B slots and three tensor-memory accumulators:
+// fixed roles around two tensor-memory A slots, six shared-memory B slots and two
+// tensor-memory accumulators:
 //   * 1 loader warp: walks the CTA's tile records (first source, count, charge block; read 32
 //     at a time) and, as soon as a B slot is free, copies the tile's charges and its source
-//     positions into it, up to four tiles ahead of the producers;
+//     positions into it, up to six tiles ahead of the producers;
 //   * 8 producer warps: for each tile wait for a free A slot and the tile's B slot, evaluate
 //     the 128 x 16 kernel values of the exact-grid float32 form (two threads per target row,
 //     8 sources each; branch-free, so a thread's eight evaluations interleave), split them,
-//     store A hi / lo and expand B;
+//     store A hi / lo into tensor memory (tcgen05.st) and expand B;
 //   * 1 MMA thread: when a tile's A and B are ready and an accumulator is free, issue the 12
 //     MMAs (M = 128, N = 128, K = 8: four K steps of three products) into a fresh accumulator
 //     and commit to the A slot's, the B slot's and the accumulator's barriers;
@@ -52,9 +55,12 @@ constexpr int kT5Src = 16;         // sources per tile (K = 32: real and imagina
 constexpr int kT5Rhs = 64;         // right-hand sides per pass (MMA N = 128)
 constexpr int kT5K = 2 * kT5Src;   // operand row: 32 TF32 values = 128 bytes
 constexpr int kT5N = 2 * kT5Rhs;
-constexpr int kT5ASlots = 2;       // A (kernel values) ring
-constexpr int kT5BSlots = 4;       // B (charges + source positions) ring, filled ahead by the loader
-constexpr int kT5Acc = 3;          // tensor-memory accumulators of 128 columns
+// tensor memory (512 columns): accumulators at 0 and 128, A slots (hi: 32 columns, lo: 32)
+// at 256 and 320, float32 block sums at 384
+constexpr int kT5ASlots = 2;       // A (kernel values) ring in tensor memory
+constexpr int kT5BSlots = 6;       // B (charges + source positions) ring, filled ahead by the loader
+constexpr int kT5Acc = 2;          // tensor-memory accumulators of 128 columns
+constexpr uint32_t kT5ACol = 256;     // A slot s: columns 256 + 64 s .. (hi), + 32 .. (lo)
 constexpr uint32_t kT5SumCol = 384;   // float32 block sums: columns 384..511
 constexpr uint32_t kT5Cols = 512;     // tensor-memory columns allocated
 constexpr int kT5Flush = 64;       // tiles summed in registers between block-sum updates
@@ -63,9 +69,9 @@ constexpr int kT5MmaWarp = kT5Prod + kT5Epi, kT5LoadWarp = kT5MmaWarp + 1;
 constexpr int kT5Threads = 32 * (kT5LoadWarp + 1);
 constexpr size_t kT5Op = (size_t)kT5M * kT5K * 4;   // one operand part (16 KB)
 constexpr size_t kT5Blk = kT5Op;                    // split charges (hi, lo: 64 rows each) of one (tile, pass)
-constexpr size_t kT5Slot = 2 * kT5Op;               // hi and lo part of an A or B slot
+constexpr size_t kT5Slot = 2 * kT5Op;               // hi and lo part of a B slot
 constexpr size_t kT5PosBytes = 2 * kT5Src * 16;     // grid points then offsets (float4)
-constexpr size_t kT5Smem = (kT5ASlots + kT5BSlots) * kT5Slot + kT5BSlots * kT5PosBytes + 1024;   // + alignment
+constexpr size_t kT5Smem = kT5BSlots * kT5Slot + kT5BSlots * kT5PosBytes + 1024;   // + alignment
 constexpr unsigned long long kT5WaitNs = 1000000000ull;   // give up a wait after 1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -99,6 +105,21 @@ __device__ __forceinline__ void t5_mma(uint32_t tmem, uint64_t a, uint64_t b, ui
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
         "l"(a), "l"(b), "r"(t5_idesc()), "r"(accumulate));
+}
+
+// the same with A in tensor memory (TMEM address of its first column)
+__device__ __forceinline__ void t5_mma_ta(uint32_t tmem, uint32_t a_tmem, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem),
+        "r"(a_tmem), "l"(b), "r"(t5_idesc()), "r"(accumulate));
+}
+
+// 8 consecutive columns of tensor memory for this warp's 32 lanes
+__device__ __forceinline__ void t5_st8(uint32_t taddr, const uint32_t* v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
 }
 
 __device__ __forceinline__ void t5_commit(uint32_t mbar) {
@@ -288,9 +309,8 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_p2p_tc5(T5Args g) {
     extern __shared__ __align__(1024) unsigned char t5_smem[];
     __shared__ T5Ctl ctl;
     unsigned char* base = t5_smem + ((1024 - (smem_u32(t5_smem) & 1023)) & 1023);
-    unsigned char* aslot = base;                                   // [kT5ASlots][hi, lo]
-    unsigned char* bslot = base + kT5ASlots * kT5Slot;             // [kT5BSlots][hi, lo]
-    float4* pos = reinterpret_cast<float4*>(base + (kT5ASlots + kT5BSlots) * kT5Slot);   // [kT5BSlots][32]
+    unsigned char* bslot = base;                                   // [kT5BSlots][hi, lo]
+    float4* pos = reinterpret_cast<float4*>(base + kT5BSlots * kT5Slot);   // [kT5BSlots][32]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     volatile int* abort = &ctl.abort;
     const int u0 = g.cta_off[blockIdx.x], u1 = g.cta_off[blockIdx.x + 1];
@@ -390,13 +410,24 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_p2p_tc5(T5Args g) {
                     re[jj] = use ? v.x : 0.f;
                     imv[jj] = use ? v.y : 0.f;
                 }
-                unsigned char* ahi = aslot + as * kT5Slot;
-                unsigned char* alo = ahi + kT5Op;
-                // columns 8 h .. 8 h + 7 (real parts: chunks 2 h, 2 h + 1), 16 + 8 h .. (imaginary)
-                t5_store4(ahi, alo, t5_off(row, 2 * h), re[0], re[1], re[2], re[3]);
-                t5_store4(ahi, alo, t5_off(row, 2 * h + 1), re[4], re[5], re[6], re[7]);
-                t5_store4(ahi, alo, t5_off(row, 4 + 2 * h), imv[0], imv[1], imv[2], imv[3]);
-                t5_store4(ahi, alo, t5_off(row, 5 + 2 * h), imv[4], imv[5], imv[6], imv[7]);
+                {
+                    // lane `row` of A slot as: columns 8 h .. 8 h + 7 (real parts), 16 + 8 h ..
+                    // (imaginary parts); the lo parts 32 columns further
+                    uint32_t hr[8], hm[8], lr[8], lm[8];
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+                        hr[jj] = t5_tf32(re[jj]);
+                        hm[jj] = t5_tf32(imv[jj]);
+                        lr[jj] = t5_tf32(re[jj] - __uint_as_float(hr[jj]));
+                        lm[jj] = t5_tf32(imv[jj] - __uint_as_float(hm[jj]));
+                    }
+                    const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + kT5ACol + (uint32_t)(64 * as + 8 * h);
+                    t5_st8(ta, hr);
+                    t5_st8(ta + 16, hm);
+                    t5_st8(ta + 32, lr);
+                    t5_st8(ta + 48, lm);
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                }
                 // expand B: charge row r = [Re q | Im q] (copied to row 64 + r) becomes row r =
                 // [Re q | -Im q] and row 64 + r = [Im q | Re q]; thread (part, r) of the first
                 // four warps
@@ -417,6 +448,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_p2p_tc5(T5Args g) {
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) t5_arrive(smem_u32(&ctl.afull[as]));
             }
@@ -492,16 +524,16 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_p2p_tc5(T5Args g) {
                 ok = ok && t5_wait_ab(smem_u32(&ctl.accempty[a]), ((i / kT5Acc) & 1) ^ 1, abort);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t ahi = smem_u32(aslot + as * kT5Slot), alo = ahi + kT5Op;
+                const uint32_t ahi = tmem + kT5ACol + (uint32_t)(64 * as), alo = ahi + 32;
                 const uint32_t bhi = smem_u32(bslot + bs * kT5Slot), blo = bhi + kT5Op;
                 const uint32_t d = tmem + (uint32_t)(a * kT5N);
-                // K step ks: bytes 32 ks .. 32 ks + 31 of every 128-byte row
+                // K step ks: A columns 8 ks .. 8 ks + 7, B bytes 32 ks .. 32 ks + 31 of every row
 #pragma unroll
                 for (int ks = 0; ks < kT5K / 8; ++ks) {
                     const uint32_t ko = (uint32_t)ks * 32u;
-                    t5_mma(d, t5_desc(ahi + ko), t5_desc(bhi + ko), ks > 0 ? 1u : 0u);
-                    t5_mma(d, t5_desc(ahi + ko), t5_desc(blo + ko), 1u);
-                    t5_mma(d, t5_desc(alo + ko), t5_desc(bhi + ko), 1u);
+                    t5_mma_ta(d, ahi + 8 * ks, t5_desc(bhi + ko), ks > 0 ? 1u : 0u);
+                    t5_mma_ta(d, ahi + 8 * ks, t5_desc(blo + ko), 1u);
+                    t5_mma_ta(d, alo + 8 * ks, t5_desc(bhi + ko), 1u);
                 }
                 t5_commit(smem_u32(&ctl.aempty[as]));
                 t5_commit(smem_u32(&ctl.bempty[bs]));
