@@ -617,7 +617,8 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
         const double scale = cells / hp.side;
         auto grid = [&](const std::vector<double>& pts, const std::vector<int64_t>& perm, const float4** g,
                         const float4** o) -> hfmm_status {
-            std::vector<float4> gg(perm.size()), oo(perm.size());
+            // 16 zero points past the end: the tcgen05 near field copies whole 16-point tiles
+            std::vector<float4> gg(perm.size() + 16, make_float4(0.f, 0.f, 0.f, 0.f)), oo(gg);
             for (size_t i = 0; i < perm.size(); ++i) {
                 float gv[3], ov[3];
                 for (int k = 0; k < 3; ++k) {

@@ -141,6 +141,19 @@ __global__ void k_p2p_fp64(int nbox, const int32_t* __restrict__ tstart, const i
 // square root, phase reduced in turns with a split constant; float64 accumulation of
 // float32 tile sums.
 // ---------------------------------------------------------------------------
+// hardware approximations without subnormal handling, for arguments that are zero or normal:
+// reciprocal square root, and sine and cosine of |x| <= pi (the approximations that rsqrtf
+// and __sincosf reach after their subnormal checks, which these arguments never need)
+__device__ __forceinline__ float rsqrt_hw(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ void sincos_hw(float x, float* s, float* c) {
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(*s) : "f"(x));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(*c) : "f"(x));
+}
+
 struct P2PMixedArgs {
     const float4* tpt;   // (gx, gy, gz, 0) per sorted target
     const float4* tof;   // (ox, oy, oz, 0)
@@ -750,7 +763,7 @@ __global__ void __launch_bounds__(128) k_p2p_mixed_warp(
                                          fmaf(ey, fmaf(2.0f, Dy, ey), ez * fmaf(2.0f, Dz, ez)));
                     const float s2 = A + B;
                     if (s2 <= 0.0f) continue;
-                    const float rho = rsqrtf(s2);
+                    const float rho = rsqrt_hw(s2);
                     const float r0f = s2 * rho;
                     const float e = fmaf(-r0f, r0f, A);
                     const float c = (e + B) * (0.5f * rho);
@@ -760,7 +773,7 @@ __global__ void __launch_bounds__(128) k_p2p_mixed_warp(
                     te = fmaf(a.tau_lo, r0f, te);
                     const float f = (th - rintf(th)) + te;
                     float sn_, cs_;
-                    __sincosf(two_pi * f, &sn_, &cs_);
+                    sincos_hw(two_pi * f, &sn_, &cs_);
                     const cxf g = mk<float>(cs_ * rho, sn_ * rho);
                     if (kRC == 1) mac(tile[0], g, wq[jj]);
                     else
@@ -822,7 +835,7 @@ __device__ __forceinline__ cxf green_grid(float4 gp, float4 op, float4 sp, float
     const float A = fmaf(Dx, Dx, fmaf(Dy, Dy, Dz * Dz));           // exact
     const float B = fmaf(ex, fmaf(2.0f, Dx, ex), fmaf(ey, fmaf(2.0f, Dy, ey), ez * fmaf(2.0f, Dz, ez)));
     const float s2 = A + B;
-    const float rho = s2 > 0.0f ? rsqrtf(s2) : 0.0f;
+    const float rho = s2 > 0.0f ? rsqrt_hw(s2) : 0.0f;
     const float r0f = s2 * rho;
     const float e = fmaf(-r0f, r0f, A);
     const float c = (e + B) * (0.5f * rho);
@@ -832,7 +845,7 @@ __device__ __forceinline__ cxf green_grid(float4 gp, float4 op, float4 sp, float
     te = fmaf(tau_lo, r0f, te);
     const float f = (th - rintf(th)) + te;
     float sn, cs;
-    __sincosf(6.28318530717958647692f * f, &sn, &cs);
+    sincos_hw(6.28318530717958647692f * f, &sn, &cs);
     return mk<float>(cs * rho, sn * rho);
 }
 

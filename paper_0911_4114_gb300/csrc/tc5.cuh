@@ -73,6 +73,7 @@ constexpr size_t kT5Slot = 2 * kT5Op;               // hi and lo part of a B slo
 constexpr size_t kT5PosBytes = 2 * kT5Src * 16;     // grid points then offsets (float4)
 constexpr size_t kT5Smem = kT5BSlots * kT5Slot + kT5BSlots * kT5PosBytes + 1024;   // + alignment
 constexpr unsigned long long kT5WaitNs = 1000000000ull;   // give up a wait after 1 s
+constexpr uint32_t kT5SuspendNs = 100000;                 // longest suspension of one mbarrier test
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -126,17 +127,20 @@ __device__ __forceinline__ void t5_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar));
 }
 
+// test the mbarrier phase; a thread whose phase is not complete is suspended until it
+// completes or kT5SuspendNs pass (so waiting warps do not take issue slots from working ones)
 __device__ __forceinline__ bool t5_try_wait(uint32_t mbar, uint32_t phase) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(mbar), "r"(phase));
+        : "r"(mbar), "r"(phase), "r"(kT5SuspendNs));
     return ok != 0;
 }
 
 // bounded wait for the mbarrier phase; false after about kT5WaitNs
 __device__ __forceinline__ bool t5_wait(uint32_t mbar, uint32_t phase) {
+    if (t5_try_wait(mbar, phase)) return true;
     const unsigned long long t0 = global_ns();
     while (!t5_try_wait(mbar, phase))
         if (global_ns() - t0 > kT5WaitNs) return false;
@@ -146,6 +150,7 @@ __device__ __forceinline__ bool t5_wait(uint32_t mbar, uint32_t phase) {
 // bounded wait that also gives up when another thread of the CTA has (*abort set); a wait
 // that runs out of time sets *abort
 __device__ __forceinline__ bool t5_wait_ab(uint32_t mbar, uint32_t phase, volatile int* abort) {
+    if (t5_try_wait(mbar, phase)) return true;
     const unsigned long long t0 = global_ns();
     while (!t5_try_wait(mbar, phase)) {
         if (*abort) return false;
@@ -203,7 +208,7 @@ __device__ __forceinline__ cxf t5_green(float4 gp, float4 op, float4 sp, float4 
     const float A = fmaf(Dx, Dx, fmaf(Dy, Dy, Dz * Dz));
     const float B = fmaf(ex, fmaf(2.0f, Dx, ex), fmaf(ey, fmaf(2.0f, Dy, ey), ez * fmaf(2.0f, Dz, ez)));
     const float s2 = A + B;
-    const float rho = s2 > 0.0f ? rsqrtf(s2) : 0.0f;
+    const float rho = s2 > 0.0f ? rsqrt_hw(s2) : 0.0f;
     const float r0f = s2 * rho;
     const float e = fmaf(-r0f, r0f, A);
     const float c = (e + B) * (0.5f * rho);
@@ -211,9 +216,9 @@ __device__ __forceinline__ cxf t5_green(float4 gp, float4 op, float4 sp, float4 
     float te = fmaf(tau_hi, r0f, -th);
     te = fmaf(tau_hi, c, te);
     te = fmaf(tau_lo, r0f, te);
-    const float f = (th - rintf(th)) + te;
+    const float x = 6.28318530717958647692f * ((th - rintf(th)) + te);
     float sn, cs;
-    __sincosf(6.28318530717958647692f * f, &sn, &cs);
+    sincos_hw(x, &sn, &cs);
     return mk<float>(cs * rho, sn * rho);
 }
 
@@ -299,7 +304,6 @@ struct T5Args {
 struct T5Ctl {
     uint64_t afull[kT5ASlots], aempty[kT5ASlots], bfull[kT5BSlots], bempty[kT5BSlots];
     uint64_t accfull[kT5Acc], accempty[kT5Acc];
-    int bsn[kT5BSlots];   // sources in the tile of each B slot
     uint32_t tmem;
     int abort;
     int b_issued, mma_issued;
@@ -360,12 +364,10 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_p2p_tc5(T5Args g) {
                         ok = __all_sync(0xffffffffu, ok);
                         if (!ok) break;
                         if (lane == 0) {
-                            const int sn = (gt >> 27) + 1;
                             const unsigned char* blk = g.bblk + ((size_t)(gt & ((1 << 27) - 1)) * npass + p) * kT5Blk;
                             unsigned char* b = bslot + bs * kT5Slot;
                             const uint32_t fb = smem_u32(&ctl.bfull[bs]);
-                            const uint32_t pb = 16u * (uint32_t)sn;
-                            ctl.bsn[bs] = sn;
+                            const uint32_t pb = 16u * kT5Src;   // whole tiles (the arrays are padded)
                             t5_expect(fb, (uint32_t)kT5Blk + 2 * pb);
                             // hi rows into rows 64..127 of B hi, lo rows into rows 64..127 of B lo
                             t5_copy(smem_u32(b + kT5Op / 2), blk, (uint32_t)(kT5Blk / 2), fb);
@@ -380,6 +382,11 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_p2p_tc5(T5Args g) {
     } else if (warp < kT5Prod) {
         // ---------------- producers: kernel values of row `row`, sources 8 h .. 8 h + 7 ----
         const int row = tid & (kT5M - 1), h = tid >> 7;
+        // B expansion: charge row r = [Re q | Im q] (copied to row 64 + r) becomes row r =
+        // [Re q | -Im q] and row 64 + r = [Im q | Re q]; thread (k, r) moves chunks k, 4 + k of
+        // that row in both parts (rows r and 64 + r share the swizzle, 64 rows lie 8 KB apart)
+        const int xr = tid & (kT5Rhs - 1), xk = tid >> 6;
+        const uint32_t xo_r = t5_off(kT5Rhs + xr, xk), xo_i = t5_off(kT5Rhs + xr, 4 + xk);
         int i = 0;
         bool ok = true;
         for (int u = u0; u < u1 && ok; ++u) {
@@ -387,6 +394,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_p2p_tc5(T5Args g) {
             if (un.z == 0) continue;
             const int t0 = g.tstart[un.x], tc = g.tcount[un.x];
             const bool active = un.y + row < tc;
+            const bool warp_rows = un.y + 32 * (warp & 3) < tc;   // some row of this warp is a target
             float4 gp = make_float4(0, 0, 0, 0), op = gp;
             if (active) {
                 gp = g.a.tpt[t0 + un.y + row];
@@ -399,18 +407,21 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_p2p_tc5(T5Args g) {
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
                 const float4* sp = pos + bs * 2 * kT5Src;
-                const int sn = ctl.bsn[bs];
-                float re[8], imv[8];
+                // a warp whose 32 rows all lie past the chunk's end (the short last chunk of a
+                // box) leaves its A rows as they are: those rows' sums are never written, and
+                // rows of a GEMM do not mix
+                if (warp_rows) {
+                    float re[8], imv[8];
 #pragma unroll
-                for (int jj = 0; jj < 8; ++jj) {
-                    const int j = 8 * h + jj;
-                    const int jc = j < sn ? j : 0;        // slot 0 always holds a source
-                    const cxf v = t5_green(gp, op, sp[jc], sp[kT5Src + jc], g.a.tau_hi, g.a.tau_lo);
-                    const bool use = active && j < sn;
-                    re[jj] = use ? v.x : 0.f;
-                    imv[jj] = use ? v.y : 0.f;
-                }
-                {
+                    for (int jj = 0; jj < 8; ++jj) {
+                        // sources past the tile's end are the next points (or the zero padding):
+                        // finite values that meet zero charges in B; rows past the chunk's end
+                        // are finite too and never written
+                        const int j = 8 * h + jj;
+                        const cxf v = t5_green(gp, op, sp[j], sp[kT5Src + j], g.a.tau_hi, g.a.tau_lo);
+                        re[jj] = v.x;
+                        imv[jj] = v.y;
+                    }
                     // lane `row` of A slot as: columns 8 h .. 8 h + 7 (real parts), 16 + 8 h ..
                     // (imaginary parts); the lo parts 32 columns further
                     uint32_t hr[8], hm[8], lr[8], lm[8];
@@ -426,27 +437,21 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_p2p_tc5(T5Args g) {
                     t5_st8(ta + 16, hm);
                     t5_st8(ta + 32, lr);
                     t5_st8(ta + 48, lm);
-                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 }
-                // expand B: charge row r = [Re q | Im q] (copied to row 64 + r) becomes row r =
-                // [Re q | -Im q] and row 64 + r = [Im q | Re q]; thread (part, r) of the first
-                // four warps
-                if (tid < 2 * kT5Rhs) {
-                    const int r = tid & (kT5Rhs - 1);
-                    unsigned char* bp = bslot + bs * kT5Slot + (tid >> 6) * kT5Op;
-                    uint4 v[8];
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) v[c] = *reinterpret_cast<const uint4*>(bp + t5_off(kT5Rhs + r, c));
+                {   // expand B (while the tensor-memory stores complete)
+                    unsigned char* bp = bslot + bs * kT5Slot;
                     const uint32_t sg = 0x80000000u;
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        *reinterpret_cast<uint4*>(bp + t5_off(r, c)) = v[c];
-                        *reinterpret_cast<uint4*>(bp + t5_off(r, 4 + c)) =
-                            make_uint4(v[4 + c].x ^ sg, v[4 + c].y ^ sg, v[4 + c].z ^ sg, v[4 + c].w ^ sg);
-                        *reinterpret_cast<uint4*>(bp + t5_off(kT5Rhs + r, c)) = v[4 + c];
-                        *reinterpret_cast<uint4*>(bp + t5_off(kT5Rhs + r, 4 + c)) = v[c];
+                    for (int part = 0; part < 2; ++part, bp += kT5Op) {
+                        const uint4 vr = *reinterpret_cast<const uint4*>(bp + xo_r);
+                        const uint4 vi = *reinterpret_cast<const uint4*>(bp + xo_i);
+                        *reinterpret_cast<uint4*>(bp + xo_r - kT5Op / 2) = vr;
+                        *reinterpret_cast<uint4*>(bp + xo_i - kT5Op / 2) = make_uint4(vi.x ^ sg, vi.y ^ sg, vi.z ^ sg, vi.w ^ sg);
+                        *reinterpret_cast<uint4*>(bp + xo_r) = vi;
+                        *reinterpret_cast<uint4*>(bp + xo_i) = vr;
                     }
                 }
+                if (warp_rows) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
