@@ -1047,6 +1047,9 @@ void launch_s2m(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false)
     if (R == 1)
         k_s2m<T, 1><<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt,
                                                   (cx<T>*)out, sign, wk);
+    else if (std::is_same<T, float>::value && R >= 16)
+        k_s2m<float, 16><<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt,
+                                                       (cxf*)out, sign, wk);
     else
         k_s2m<T, 4><<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt,
                                                   (cx<T>*)out, sign, wk);
@@ -1104,6 +1107,9 @@ void launch_l2t(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false)
     if (R == 1)
         k_l2t<T, 1><<<grid, kL2TThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, (const cx<T>*)in, R, kt,
                                                   out, sign, wk);
+    else if (std::is_same<T, float>::value && R >= 16)
+        k_l2t<float, 16><<<grid, kL2TThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, (const cxf*)in, R, kt,
+                                                       out, sign, wk);
     else
         k_l2t<T, 4><<<grid, kL2TThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, (const cx<T>*)in, R, kt,
                                                   out, sign, wk);

@@ -231,7 +231,9 @@ __device__ __forceinline__ void split_f(double v, float& hi, float& lo) {
 // S2M: sources, sign +1, no weights.  Transposed L2T: targets, sign -1, quadrature weights.
 // One thread per antipodal pair (k, k'): with E = C + iS the plane wave of s_k, it sums
 // U = sum q C and V = sum q S; then M(k) = U + iV and M(k') = U - iV.  kRC right-hand
-// sides per plane-wave evaluation (1, or 4 when R > 1).
+// sides per plane-wave evaluation (1, 4, or 16 at float32 levels with many right-hand
+// sides).  The charges are rounded to the level's precision once, as they enter shared
+// memory (a float64 -> float32 conversion per use would run on the slow float64 pipe).
 template <typename R, int kRC>
 __global__ void k_s2m(BoxView bx, QuadView qv, const int32_t* __restrict__ sstart,
                       const int32_t* __restrict__ scount, const double* __restrict__ sx,
@@ -241,7 +243,7 @@ __global__ void k_s2m(BoxView bx, QuadView qv, const int32_t* __restrict__ sstar
     constexpr bool kF32 = std::is_same<R, float>::value;   // float32 level: float-only phases
     __shared__ double shd[kS2MThreads * 3];
     __shared__ float shf[kS2MThreads * 6];
-    __shared__ cxd shq[kS2MThreads * kRC];
+    __shared__ cx<R> shq[kS2MThreads * kRC];
     const int b = blockIdx.x;
     const int64_t p = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
     const bool active = p < qv.npair;
@@ -272,7 +274,7 @@ __global__ void k_s2m(BoxView bx, QuadView qv, const int32_t* __restrict__ sstar
                     shd[3 * threadIdx.x + c] = dd[c];
                     split_f(dd[c], shf[6 * threadIdx.x + c], shf[6 * threadIdx.x + 3 + c]);
                 }
-                for (int r = 0; r < rn; ++r) shq[threadIdx.x * kRC + r] = qs[(int64_t)j * R_ + r0 + r];
+                for (int r = 0; r < rn; ++r) shq[threadIdx.x * kRC + r] = cvt<R>(qs[(int64_t)j * R_ + r0 + r]);
             }
             __syncthreads();
             if (active)
@@ -285,15 +287,19 @@ __global__ void k_s2m(BoxView bx, QuadView qv, const int32_t* __restrict__ sstar
                     } else {
                         e = plane_wave<R>(turns(kappa_turns, s, shd[3 * jj], shd[3 * jj + 1], shd[3 * jj + 2]));
                     }
-                    for (int r = 0; r < rn; ++r) {
-                        const cx<R> q = cvt<R>(shq[jj * kRC + r]);
-                        U[r] = U[r] + e.x * q;
-                        V[r] = V[r] + e.y * q;
-                    }
+#pragma unroll
+                    for (int r = 0; r < kRC; ++r)
+                        if (r < rn) {
+                            const cx<R> q = shq[jj * kRC + r];
+                            U[r] = U[r] + e.x * q;
+                            V[r] = V[r] + e.y * q;
+                        }
                 }
         }
         if (active)
-            for (int r = 0; r < rn; ++r) {
+#pragma unroll
+            for (int r = 0; r < kRC; ++r) {
+                if (r >= rn) break;
                 cx<R> a = mk<R>(U[r].x - V[r].y, U[r].y + V[r].x), c = mk<R>(U[r].x + V[r].y, U[r].y - V[r].x);
                 if (wk) {
                     a = (R)wk[kk2.x] * a;
@@ -314,7 +320,8 @@ constexpr int kL2TThreads = 128;
 // L2T: targets, sign +1, quadrature weights.  Transposed S2M: sources, sign -1, no weights.
 // Over antipodal pairs (k, k') with A = w_k L(k), B = w_k' L(k'), E = C + iS the plane wave
 // of s_k: A E + B conj(E) = (P.x C - Q.y S) + i (P.y C + Q.x S), P = A + B, Q = A - B.
-// kRC right-hand sides per plane-wave evaluation.
+// kRC right-hand sides per plane-wave evaluation (1, 4, or 16 at float32 levels with many
+// right-hand sides).
 template <typename R, int kRC>
 __global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstart,
                       const int32_t* __restrict__ tcount, const double* __restrict__ tx,
@@ -374,15 +381,19 @@ __global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstar
                     } else {
                         e = plane_wave<R>(turns(kappa_turns, &shs[3 * kk], dx, dy, dz));
                     }
-                    for (int r = 0; r < rn; ++r) {
-                        const cx<R> P = shp[kk * kRC + r], Q = shq[kk * kRC + r];
-                        acc[r].x += P.x * e.x - Q.y * e.y;
-                        acc[r].y += P.y * e.x + Q.x * e.y;
-                    }
+#pragma unroll
+                    for (int r = 0; r < kRC; ++r)
+                        if (r < rn) {
+                            const cx<R> P = shp[kk * kRC + r], Q = shq[kk * kRC + r];
+                            acc[r].x += P.x * e.x - Q.y * e.y;
+                            acc[r].y += P.y * e.x + Q.x * e.y;
+                        }
                 }
         }
         if (active)
-            for (int r = 0; r < rn; ++r) {
+#pragma unroll
+            for (int r = 0; r < kRC; ++r) {
+                if (r >= rn) break;
                 cxd& o = phis[(int64_t)(t0 + ti) * R_ + r0 + r];
                 o.x += (double)acc[r].x;
                 o.y += (double)acc[r].y;
