@@ -720,10 +720,12 @@ struct UnitCost {
     double near_f32_sym = 1.32e-12, near_f32_boxpair = 0.65e-9;  // symmetric float32, R = 1: per
                                                                  // ordered pair, ordered box pair
     double near_f32 = 2.7e-12;        // per pair and group of four RHS (one-way float32)
-    double near_tc = 0.27e-12;        // per pair and RHS (tensor-core form, R >= 8)
+    double near_tc = 0.27e-12;        // per pair and RHS (mma.sync tensor-core form, 8 <= R < 16)
+    double near_tc5 = 8.0e-9;         // per (128-target chunk, 16-source tile, 64-RHS pass), tcgen05 form
     double near_df = 7.3e-12;         // per pair and group of four RHS
     double near_f64 = 1.0e-10;        // per pair and RHS
-    double pw_f32 = 1.5e-12, pw_f32_rhs = 0.4e-12;   // per (point, antipodal pair) [+ per RHS]
+    double pw_f32 = 1.5e-12, pw_f32_rhs = 0.42e-12;  // per (point, antipodal pair): per plane
+                                                      // wave (one per 1, 4 or 16 RHS) + per RHS
     double pw_df = 2.9e-12, pw_df_rhs = 3.15e-12;
     double pw_f64_tab = 6.5e-12;      // per (point, pair, RHS), float64 tables
     double pw_f64 = 67e-12, pw_f64_rhs = 6.5e-12;
@@ -810,20 +812,23 @@ static void tune_plan_shape(HostPlan& hp) {
         for (int L = 2; L <= lfb[b]; ++L) {
             // near field at leaf level L
             const LevelCounts& F = lc[L];
-            std::vector<double> pr(F.key.size(), 0.0), bpr(F.key.size(), 0.0);
+            std::vector<double> pr(F.key.size(), 0.0), bpr(F.key.size(), 0.0), tl(F.key.size(), 0.0);
             for_neighbours(F.key, L, b, [&](int64_t a, int64_t n) {
                 pr[a] += (double)F.nt[a] * (double)F.ns[n];
                 bpr[a] += 1.0;
+                tl[a] += (double)((F.ns[n] + 15) / 16);
             });
-            double pairs = 0.0, boxpairs = 0.0;
+            double pairs = 0.0, boxpairs = 0.0, unit_tiles = 0.0;
             for (size_t a = 0; a < F.key.size(); ++a) {
                 pairs += pr[a];
                 boxpairs += bpr[a];
+                unit_tiles += (double)((F.nt[a] + 127) / 128) * tl[a];
             }
             double t = 0.0;
             const double g4 = std::ceil(R / 4.0);
             if (hp.model_near == kFP32) {
                 if (hp.model_sym && R == 1) t += pairs * uc.near_f32_sym + boxpairs * uc.near_f32_boxpair;
+                else if (R >= 16) t += unit_tiles * std::ceil(R / 64.0) * uc.near_tc5;
                 else if (R >= 8) t += pairs * R * uc.near_tc;
                 else t += pairs * g4 * uc.near_f32;
             } else if (hp.model_near == kDF) {
@@ -835,7 +840,8 @@ static void tune_plan_shape(HostPlan& hp) {
             const LevelPlan& leaf = lps[b][L];
             const double npair = (double)leaf.quad.K / 2.0, pts = (double)(hp.ns + hp.nt);
             if (leaf.prec == kFP32) {
-                t += pts * npair * (uc.pw_f32 + R * uc.pw_f32_rhs);
+                const double rc = R >= 16 ? 16.0 : (R > 1 ? 4.0 : 1.0);   // RHS per plane wave
+                t += pts * npair * (std::ceil(R / rc) * uc.pw_f32 + R * uc.pw_f32_rhs);
             } else if (leaf.prec == kDF) {
                 t += pts * npair * (uc.pw_df + R * uc.pw_df_rhs);
             } else {

@@ -53,8 +53,8 @@ def test_ellipsoid_2m(eps, dtype):
 
 
 def test_cube_512k_64_rhs():
-    """One buffer box (a float64 level 2) and the tuned plan shape (two buffer boxes, leaf
-    level 4)."""
+    """One buffer box (a float64 level 2) and the tuned plan shape (two buffer boxes; the
+    leaf level the cost model picks for 64 right-hand sides)."""
     s, t = wl.points("cube512k_rhs64")
     q = wl.charges(len(s), 64, wl.rng(3, salt=1)).astype(np.complex64)
     idx = np.sort(wl.rng(3, salt=2).choice(len(t), 100, replace=False))
