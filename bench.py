@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-tight", action="store_true", help="skip the eps = 1e-8 measurements")
     ap.add_argument("--skip-oracle", action="store_true", help="skip the CPU oracle timing")
     ap.add_argument("--no-extras", action="store_true", help="skip the extra workloads")
+    ap.add_argument("--cube-only", type=int, default=0, metavar="N",
+                    help="time only the 64-RHS cube workload on its first N points and print its line (profiling runs)")
     ap.add_argument("--buffer", type=int, default=0, choices=[0, 1, 2],
                     help="plan shape of the measured plans: 0 tuned (default), 1 or 2 buffer boxes (profiling runs)")
     return ap.parse_args()
@@ -414,6 +416,49 @@ def gpu_direct_reference(s, t_sub, q, kappa, dev):
     return out[:, 0].cpu().numpy()
 
 
+def cube_run(timer, dev, n=524288):
+    """The cube workload with 64 right-hand sides (kappa 40, eps 1e-5, tuned plan): time per
+    apply, stage times and the tensor-pipe roofline of its tcgen05 near field.  n < 524,288
+    takes the first n points of the same cloud (profiling runs)."""
+    import torch
+    from paper_0911_4114_gb300 import FmmPlan, workloads as wl
+    cs, ct = wl.points("cube512k_rhs64", n=n)
+    cplan = FmmPlan(cs, ct, 40.0, 1e-5, precision="mixed", max_rhs=64, **AUTO)
+    cq = torch.as_tensor(wl.charges(len(cs), 64, wl.rng(3, salt=1)).astype(np.complex64)).to(dev)
+    cout = torch.empty((len(ct), 64), dtype=torch.complex64, device=dev)
+    cms = timer.run(lambda: cplan.apply(cq, out=cout), 2, 1)
+    ci = cplan.info()
+    cst = timer.stages(cplan, lambda: cplan.apply(cq, out=cout), 1)
+    res = {"ms_per_step": cms, "value": len(ct) * 64 / (cms * 1e-3) / 1e6, "unit": "Mpoints*RHS/s",
+           "points": len(ct), "nrhs": 64, "kappa": 40.0, "eps": 1e-5, "lf": ci["lf"], "buffer": ci["buffer"],
+           "p2p_pairs": ci["p2p_pairs"], "stage_ms": cst,
+           "levels": {str(l): v["precision"] for l, v in ci["levels"].items()}}
+    tiles = ci.get("near_mma_tiles", 0)
+    if tiles and cst.get("near_field", 0.0) > 0.0:
+        # tensor-pipe roofline of the tcgen05 near field: the MMAs it issues (12 of 128 x 128 x 8
+        # per chunk-tile pair and 64-RHS pass) against the TF32 peak, and the algorithmic complex
+        # multiply-adds (8 flops per pair and RHS) against the same peak
+        try:
+            bf16 = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+            src = "of measured"
+        except (OSError, KeyError):
+            bf16, src = 1900.0, "of fallback"
+        tf32 = bf16 * 1.1 / 2.25
+        sec = cst["near_field"] * 1e-3
+        issued = tiles * 12 * 2.0 * 128 * 128 * 8
+        algo = ci["p2p_pairs"] * 64 * 8.0
+        res["near_field_roofline"] = {
+            "kernel": "k_p2p_tc5", "bound": "tensor", "unit": "TFLOP/s", "peak": tf32,
+            "peak_note": "TF32: measured bf16 GEMM peak x nominal TF32/bf16 ratio 1.1/2.25", "peak_source": src,
+            "achieved": issued / sec / 1e12, "frac": issued / sec / 1e12 / tf32,
+            "unit_work": "12 tcgen05.mma kind::tf32 M128 N128 K8 (three split products) per (128-target chunk, "
+                         "16-source tile, 64-RHS pass)",
+            "algorithmic": {"achieved": algo / sec / 1e12, "frac": algo / sec / 1e12 / tf32,
+                            "unit_work": "8 flops per near-field pair and right-hand side"}}
+    del cplan, cq, cout
+    return res
+
+
 def extras_run(timer, dev, steps):
     """Device-timed extra workloads: the sphere, the 64-RHS cube and the 32-problem batch."""
     import torch
@@ -435,19 +480,7 @@ def extras_run(timer, dev, steps):
         del p
     out["sphere262k"] = dict(sph, unit="Mpoints*RHS/s", kappa=64.0, eps=1e-6, charges="complex64")
     # 524,288 points in the unit cube, 64 right-hand sides, kappa 40, eps 1e-5
-    cs, ct = wl.points("cube512k_rhs64")
-    cplan = FmmPlan(cs, ct, 40.0, 1e-5, precision="mixed", max_rhs=64, **AUTO)
-    cq = torch.as_tensor(wl.charges(len(cs), 64, wl.rng(3, salt=1)).astype(np.complex64)).to(dev)
-    cout = torch.empty((len(ct), 64), dtype=torch.complex64, device=dev)
-    cms = timer.run(lambda: cplan.apply(cq, out=cout), 2, 1)
-    ci = cplan.info()
-    out["cube512k_rhs64"] = {"ms_per_step": cms, "value": len(ct) * 64 / (cms * 1e-3) / 1e6,
-                             "unit": "Mpoints*RHS/s", "nrhs": 64, "kappa": 40.0, "eps": 1e-5, "lf": ci["lf"],
-                             "buffer": ci["buffer"],
-                             "p2p_pairs": ci["p2p_pairs"],
-                             "stage_ms": timer.stages(cplan, lambda: cplan.apply(cq, out=cout), 1),
-                             "levels": {str(l): v["precision"] for l, v in ci["levels"].items()}}
-    del cplan, cq, cout
+    out["cube512k_rhs64"] = cube_run(timer, dev)
     # 32 uneven cube problems, 4 RHS each, one graph launch per apply
     g = wl.rng(5)
     sizes = np.exp(g.uniform(np.log(8192), np.log(131072), 32)).astype(int)
@@ -476,6 +509,11 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    AUTO["buffer"] = args.buffer
+    if args.cube_only:
+        if rank == 0:
+            print(json.dumps(dict(cube_run(Timer(dev, world), dev, args.cube_only), workload="cube_rhs64")))
+        return
     s, t, q_host = headline_points(args.points if args.points != 2097152 else None)
     kappa, eps = HEADLINE["kappa"], HEADLINE["eps"]
     AUTO["buffer"] = args.buffer

@@ -153,6 +153,9 @@ typedef struct {
     /* symmetric near field: the register budget (resident blocks per SM, 5-8) the plan timed
      * fastest on its own near field at plan time (0: not the symmetric kernel) */
     int near_variant;
+    /* tcgen05 near field (float32, 16 or more right-hand sides): (128-target chunk, 16-source
+     * tile) pairs of the apply per 64-RHS pass, each 12 MMAs of 128 x 128 x 8 (0: not built) */
+    int64_t near_mma_tiles;
 } hfmm_info;
 
 /* Fill *opt with the defaults listed above. */

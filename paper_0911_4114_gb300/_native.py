@@ -54,7 +54,7 @@ class Info(ctypes.Structure):
                 ("near_precision", ctypes.c_int), ("p2p_self_pairs", ctypes.c_int64),
                 ("near_symmetric", ctypes.c_int), ("leaf_tables", ctypes.c_int),
                 ("leaf_table_bytes", ctypes.c_int64), ("buffer", ctypes.c_int), ("tuned", ctypes.c_int),
-                ("predicted_ms", (ctypes.c_double * MAX_LEVELS) * 3), ("near_variant", ctypes.c_int)]
+                ("predicted_ms", (ctypes.c_double * MAX_LEVELS) * 3), ("near_variant", ctypes.c_int), ("near_mma_tiles", ctypes.c_int64)]
 
 
 _lib = None

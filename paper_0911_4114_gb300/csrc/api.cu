@@ -119,6 +119,7 @@ struct hfmm_plan_s {
         int2* recs = nullptr;
         int ncta = 0;
     } t5fwd, t5adj;
+    int64_t t5tiles_fwd = 0;  // (chunk, tile) pairs of the forward direction per 64-RHS pass
     unsigned char* t5blk = nullptr;   // split charge operands, (tile, 64-RHS pass) blocks
     // device flag set by a kernel whose bounded wait gave up (read by hfmm_query)
     int* dev_err = nullptr;
@@ -500,6 +501,7 @@ hfmm_status build_t5(hfmm_plan_s* P) {
             off.push_back((int32_t)flat.size());
         }
         d->ncta = nc;
+        if (d == &P->t5fwd) P->t5tiles_fwd = (int64_t)recs.size();
         TRY(upload(P, &d->units, flat));
         TRY(upload(P, &d->cta_off, off));
         TRY(upload(P, &d->rec_off, roff));
@@ -1608,6 +1610,7 @@ hfmm_status hfmm_query(hfmm_plan_t P, hfmm_info* info) {
     info->buffer = hp.buffer;
     info->tuned = hp.tuned;
     info->near_variant = (P->sym && P->near_prec == kFP32) ? P->sym_variant : 0;
+    info->near_mma_tiles = P->near_prec == kFP32 ? P->t5tiles_fwd : 0;
     for (int b = 0; b < 3; ++b)
         for (int l = 0; l < HFMM_MAX_LEVELS; ++l) info->predicted_ms[b][l] = hp.predicted_ms[b][l];
     info->leaf_table_bytes = P->tab_bytes;

@@ -519,6 +519,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_p2p_tc5(T5Args g) {
         }
     } else if (lane == 0) {
         // ---------------- MMA issue (warp kT5MmaWarp) ----------------
+        const uint64_t bdesc0 = t5_desc(smem_u32(bslot));   // B slot 0; slots and parts move its start
         int i = 0;
         bool ok = true;
         for (int u = u0; u < u1 && ok; ++u) {
@@ -530,15 +531,15 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_p2p_tc5(T5Args g) {
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t ahi = tmem + kT5ACol + (uint32_t)(64 * as), alo = ahi + 32;
-                const uint32_t bhi = smem_u32(bslot + bs * kT5Slot), blo = bhi + kT5Op;
+                const uint64_t bh = bdesc0 + (uint64_t)((bs * kT5Slot) >> 4), bl = bh + (kT5Op >> 4);
                 const uint32_t d = tmem + (uint32_t)(a * kT5N);
                 // K step ks: A columns 8 ks .. 8 ks + 7, B bytes 32 ks .. 32 ks + 31 of every row
+                // (2 ks in the descriptor's 16-byte start-address field)
 #pragma unroll
                 for (int ks = 0; ks < kT5K / 8; ++ks) {
-                    const uint32_t ko = (uint32_t)ks * 32u;
-                    t5_mma_ta(d, ahi + 8 * ks, t5_desc(bhi + ko), ks > 0 ? 1u : 0u);
-                    t5_mma_ta(d, ahi + 8 * ks, t5_desc(blo + ko), 1u);
-                    t5_mma_ta(d, alo + 8 * ks, t5_desc(bhi + ko), 1u);
+                    t5_mma_ta(d, ahi + 8 * ks, bh + 2 * ks, ks > 0 ? 1u : 0u);
+                    t5_mma_ta(d, ahi + 8 * ks, bl + 2 * ks, 1u);
+                    t5_mma_ta(d, alo + 8 * ks, bh + 2 * ks, 1u);
                 }
                 t5_commit(smem_u32(&ctl.aempty[as]));
                 t5_commit(smem_u32(&ctl.bempty[bs]));

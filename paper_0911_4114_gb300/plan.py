@@ -167,7 +167,7 @@ class FmmPlan:
                     buffer=inf.buffer, tuned=bool(inf.tuned),
                     predicted_ms={(b, l): inf.predicted_ms[b][l] for b in (1, 2)
                                   for l in range(MAX_LEVELS) if inf.predicted_ms[b][l] > 0},
-                    near_variant=inf.near_variant)
+                    near_variant=inf.near_variant, near_mma_tiles=inf.near_mma_tiles)
 
     def debug_get(self, what, level=0, arg=0):
         L = nat.lib()
