@@ -50,6 +50,13 @@ using cxd = cx<double>;
 using cxf = cx<float>;
 
 #ifdef __CUDACC__
+// a / b as a real scalar of type R for positive integers a, b (FFT normalisations); float32:
+// the correctly rounded quotient, without the float64 division (the slow float64 pipe)
+template <typename R>
+__device__ __forceinline__ R rratio(int a, int b) { return rval<R>((double)a / (double)b); }
+template <>
+__device__ __forceinline__ float rratio<float>(int a, int b) { return __fdiv_rn((float)a, (float)b); }
+
 // read-only (non-coherent cache) load of a float64 complex value
 __device__ __forceinline__ cxd ldg_cx(const cxd* p) {
     const double2 v = __ldg(reinterpret_cast<const double2*>(p));

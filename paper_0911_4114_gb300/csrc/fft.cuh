@@ -117,7 +117,7 @@ __device__ cx<R>* warp_resample(cx<R>* a, cx<R>* b, int n, int np, const Twiddle
     cx<R>* s = warp_fft(a, b, n, false, pool + tv.off[n], lane);
     cx<R>* o = (s == a) ? b : a;
     const int band = min((n + 1) / 2, (np + 1) / 2) - 1;
-    const R scale = rval<R>(1.0 / (double)n);
+    const R scale = rratio<R>(1, n);
     for (int j = lane; j < np; j += 32) {
         int f = (2 * j <= np) ? j : j - np;
         cx<R> v = mk<R>(rval<R>(0.0), rval<R>(0.0));

@@ -1520,7 +1520,7 @@ __global__ void k_requad_spec_a(RequadArgs ra, int nbox_seq, int R_, const cx<Ti
     const cx<Tc>* pool = reinterpret_cast<const cx<Tc>*>(ra.tw.pool);
     const cx<Tc>* sp = warp_fft(buf0, buf1, len, false, pool + ra.tw.off[len], lane);
     const int band = min((len + 1) / 2, (ra.big + 1) / 2) - 1;
-    const Tc scale = rval<Tc>(1.0 / (double)len);
+    const Tc scale = rratio<Tc>(1, len);
     cx<Tc>* dst = GA + seq * ra.big;
     for (int j = lane; j < ra.big; j += 32) {
         const int f = (2 * j <= ra.big) ? j : j - ra.big;
@@ -1715,7 +1715,7 @@ __global__ void k_requad_spec_cols_t(RequadArgs ra, int nbox_seq, int R_, const 
     }
     __syncwarp();
     cx<Tc>* res = warp_resample(buf0, buf1, ntb, nta, ra.tw, lane);
-    const Tc sc = rval<Tc>((double)ntb / (double)nta);
+    const Tc sc = rratio<Tc>(ntb, nta);
     cx<Tc>* ga = GA + br * (int64_t)ra.qa.nrows * ra.big;
     // transposed gather: row u collects t = u and t = ntheta_a - u (odd slot with a sign flip)
     for (int u = lane; u <= ha; u += 32) {
@@ -1758,7 +1758,7 @@ __global__ void k_requad_spec_at_add(RequadArgs ra, int nbox_seq, int R_, const 
     const int64_t br = seq / rows;
     const int len = ra.qa.nphi[t];
     const cx<Tc>* res = spec_at_row(GA + seq * ra.big, ra.big, len, buf0, buf1, ra, lane);
-    const Tc sc = rval<Tc>(1.0 / (double)len);
+    const Tc sc = rratio<Tc>(1, len);
     cx<Tout>* dst = out + br * ra.qa.K + ra.qa.off[t];
     for (int j = lane; j < len; j += 32) dst[j] = dst[j] + cvt<Tout>(sc * res[j]);
 }
@@ -1783,7 +1783,7 @@ __global__ void k_requad_spec_at_sum(RequadArgs ra, int nparent, int R_, const i
     const int p = (int)(pr / R_), r = (int)(pr % R_);
     const int len = ra.qa.nphi[t];
     const int64_t o = ra.qa.off[t];
-    const Tc sc = rval<Tc>(1.0 / (double)len);
+    const Tc sc = rratio<Tc>(1, len);
     for (int j = lane; j < len; j += 32) acc[j] = mk<Tc>(rval<Tc>(0.0), rval<Tc>(0.0));
     const int c0 = child_start[p], cn = child_count[p];
     for (int c = c0; c < c0 + cn; ++c) {
