@@ -1388,25 +1388,39 @@ template <typename S, typename C, int kRC>
 __global__ void k_m2l_box(int64_t K, const int32_t* __restrict__ ioff, const int32_t* __restrict__ iidx,
                           const int32_t* __restrict__ islot, const cx<S>* __restrict__ T,
                           const cx<S>* __restrict__ M, int R_, cx<S>* __restrict__ I) {
+    // the box's list passes through shared memory in chunks (one broadcast read per entry
+    // instead of two global loads), so the signature loads of several entries can be in flight
+    constexpr int kChunk = 256;
+    __shared__ int2 sl[kChunk];   // (partner box, table slot)
     const int a = blockIdx.x;
     const int64_t k = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= K) return;
+    const bool active = k < K;
     const int l0 = ioff[a], l1 = ioff[a + 1];
     for (int r0 = 0; r0 < R_; r0 += kRC) {
         const int rn = min(kRC, R_ - r0);
         M2LAcc<C> acc[kRC];
 #pragma unroll
         for (int r = 0; r < kRC; ++r) acc[r].zero();
-        for (int t = l0; t < l1; ++t) {
-            const int b = iidx[t];
-            const cx<C> tv = cvt<C>(T[(int64_t)islot[t] * K + k]);
+        for (int t0 = l0; t0 < l1; t0 += kChunk) {
+            const int tn = min(kChunk, l1 - t0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < tn; e += blockDim.x) sl[e] = make_int2(iidx[t0 + e], islot[t0 + e]);
+            __syncthreads();
+            if (active) {
+#pragma unroll 4
+                for (int e = 0; e < tn; ++e) {
+                    const int2 bs = sl[e];
+                    const cx<C> tv = cvt<C>(T[(int64_t)bs.y * K + k]);
+#pragma unroll
+                    for (int r = 0; r < kRC; ++r)
+                        if (r < rn) acc[r].mac(tv, cvt<C>(M[((int64_t)bs.x * R_ + r0 + r) * K + k]));
+                }
+            }
+        }
+        if (active)
 #pragma unroll
             for (int r = 0; r < kRC; ++r)
-                if (r < rn) acc[r].mac(tv, cvt<C>(M[((int64_t)b * R_ + r0 + r) * K + k]));
-        }
-#pragma unroll
-        for (int r = 0; r < kRC; ++r)
-            if (r < rn) I[((int64_t)a * R_ + r0 + r) * K + k] = cvt<S>(acc[r].get());
+                if (r < rn) I[((int64_t)a * R_ + r0 + r) * K + k] = cvt<S>(acc[r].get());
     }
 }
 
@@ -1425,9 +1439,12 @@ __global__ void k_m2l_sib(int64_t K, const int32_t* __restrict__ pfirst, const i
                           const int32_t* __restrict__ pmask, const int32_t* __restrict__ pslot,
                           const cx<S>* __restrict__ T, const cx<S>* __restrict__ M, int R_,
                           cx<S>* __restrict__ I) {
+    // the union entries pass through shared memory in chunks (broadcast reads)
+    constexpr int kChunk = 64;
+    __shared__ int su[kChunk], smask[kChunk], sslot[8 * kChunk];
     const int p = blockIdx.x;
     const int64_t k = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= K) return;
+    const bool active = k < K;
     const int c0 = pfirst[p], nc = pnch[p];
     const int e0 = poff[p], e1 = poff[p + 1];
     for (int r0 = 0; r0 < R_; r0 += kRC) {
@@ -1437,20 +1454,32 @@ __global__ void k_m2l_sib(int64_t K, const int32_t* __restrict__ pfirst, const i
         for (int c = 0; c < 8; ++c)
 #pragma unroll
             for (int r = 0; r < kRC; ++r) acc[c][r].zero();
-        for (int e = e0; e < e1; ++e) {
-            const int u = pu[e], mask = pmask[e];
-            cx<C> m[kRC];
+        for (int q0 = e0; q0 < e1; q0 += kChunk) {
+            const int qn = min(kChunk, e1 - q0);
+            __syncthreads();
+            for (int x = threadIdx.x; x < 8 * qn; x += blockDim.x) sslot[x] = pslot[8 * q0 + x];
+            for (int x = threadIdx.x; x < qn; x += blockDim.x) {
+                su[x] = pu[q0 + x];
+                smask[x] = pmask[q0 + x];
+            }
+            __syncthreads();
+            if (!active) continue;
+            for (int e = 0; e < qn; ++e) {
+                const int u = su[e], mask = smask[e];
+                cx<C> m[kRC];
 #pragma unroll
-            for (int r = 0; r < kRC; ++r)
-                m[r] = r < rn ? cvt<C>(M[((int64_t)u * R_ + r0 + r) * K + k]) : mk<C>(rval<C>(0.0), rval<C>(0.0));
+                for (int r = 0; r < kRC; ++r)
+                    m[r] = r < rn ? cvt<C>(M[((int64_t)u * R_ + r0 + r) * K + k]) : mk<C>(rval<C>(0.0), rval<C>(0.0));
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-                if (mask & (1 << c)) {                 // uniform across the block
-                    const cx<C> t = cvt<C>(T[(int64_t)pslot[8 * e + c] * K + k]);
+                for (int c = 0; c < 8; ++c)
+                    if (mask & (1 << c)) {                 // uniform across the block
+                        const cx<C> t = cvt<C>(T[(int64_t)sslot[8 * e + c] * K + k]);
 #pragma unroll
-                    for (int r = 0; r < kRC; ++r) acc[c][r].mac(t, m[r]);
-                }
+                        for (int r = 0; r < kRC; ++r) acc[c][r].mac(t, m[r]);
+                    }
+            }
         }
+        if (!active) continue;
 #pragma unroll
         for (int c = 0; c < 8; ++c)
             if (c < nc)
