@@ -69,6 +69,10 @@ struct DevLevel {
 struct Requad {
     RequadArgs args{};
     int64_t ga_elems = 0, gb_elems = 0;
+    // pass B' as a dense product (k_requad_theta_dense) for short circles: the 2 x 2 blocks
+    // (Lee, Leo, Loe, Loo)[n][u], nrb x nra, or null
+    const float4* theta_w = nullptr;
+    int nra = 0, nrb = 0;
 };
 
 }  // namespace
@@ -403,6 +407,40 @@ Requad make_requad(const Quadrature& a, const Quadrature& b, int nbox_seq, int r
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// The theta pass of k_requad_spec_cols for one coefficient pair as matrices, in float64: the
+// even circle of column u (rows 0 .. nta/2 of the grid a) is 1 at t = u and t = nta - u, the
+// odd one +1 at t = u and -1 at t = nta - u (t > nta/2); each is band-limited re-sampled to
+// length ntb (forward DFT, |f| <= min(ceil(nta/2), ceil(ntb/2)) - 1, 1/nta, inverse DFT) and
+// split into its even (y[n] + y[-n]) / 2 and odd (y[n] - y[-n]) / 2 parts, n = 0 .. ntb/2.
+// Entry n * nra + u: (even part of the even circle, of the odd circle; odd part of the even
+// circle, of the odd circle).
+std::vector<float4> theta_matrices(int nta, int ntb) {
+    const int ha = nta / 2, nra = ha + 1, nrb = ntb / 2 + 1;
+    const int band = std::min((nta + 1) / 2, (ntb + 1) / 2) - 1;
+    const double two_pi = 2.0 * 3.14159265358979323846;
+    auto resample = [&](const std::vector<std::pair<int, double>>& x, int m) {
+        double y = 0.0;
+        for (int f = -band; f <= band; ++f)
+            for (const auto& tv : x) y += tv.second * std::cos(two_pi * f * ((double)m / ntb - (double)tv.first / nta));
+        return y / nta;
+    };
+    std::vector<float4> w((size_t)nrb * nra);
+    for (int u = 0; u < nra; ++u) {
+        std::vector<std::pair<int, double>> ev{{u, 1.0}}, od{{u, 1.0}};
+        if (u != 0 && u != ha) {
+            ev.push_back({nta - u, 1.0});
+            od.push_back({nta - u, -1.0});
+        }
+        for (int n = 0; n < nrb; ++n) {
+            const int mn = (ntb - n) % ntb;
+            const double ye = resample(ev, n), yem = resample(ev, mn), yo = resample(od, n), yom = resample(od, mn);
+            w[(size_t)n * nra + u] = make_float4((float)(0.5 * (ye + yem)), (float)(0.5 * (yo + yom)),
+                                                 (float)(0.5 * (ye - yem)), (float)(0.5 * (yo - yom)));
+        }
+    }
+    return w;
+}
+
 // Plane-wave tables of a float64 leaf level (see k_pw_table), when they fit the budget.
 hfmm_status build_leaf_tables(hfmm_plan_s* P) {
     const HostPlan& hp = P->hp;
@@ -679,6 +717,16 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
     for (int l = 3; l <= hp.lf; ++l) {
         P->up[l] = make_requad(hp.lp[l].quad, hp.lp[l - 1].quad, P->lev[l].nbox, P->rmax);
         P->down[l - 1] = make_requad(hp.lp[l - 1].quad, hp.lp[l].quad, P->lev[l].nbox, P->rmax);
+        for (auto rq : {std::make_pair(&P->up[l], std::make_pair(l, l - 1)), std::make_pair(&P->down[l - 1], std::make_pair(l - 1, l))}) {
+            const int nta = hp.lp[rq.second.first].quad.ntheta, ntb = hp.lp[rq.second.second].quad.ntheta;
+            if (nta / 2 + 1 <= kThetaDenseMax && ntb / 2 + 1 <= kThetaDenseMax) {
+                float4* dw;
+                TRY(upload(P, &dw, theta_matrices(nta, ntb)));
+                rq.first->theta_w = dw;
+                rq.first->nra = nta / 2 + 1;
+                rq.first->nrb = ntb / 2 + 1;
+            }
+        }
         for (Requad* r : {&P->up[l], &P->down[l - 1]}) {
             ga = std::max(ga, r->ga_elems);
             gb = std::max(gb, r->gb_elems);
@@ -763,6 +811,30 @@ template <> const cx<float>* shift_of<float>(const DevLevel& d) { return d.shift
 template <> const cx<double>* shift_of<double>(const DevLevel& d) { return d.shift64; }
 template <> const cx<df>* shift_of<df>(const DevLevel& d) { return d.shiftdf; }
 
+// pass B' (theta re-sampling) of a forward re-quadrature: the dense form for float32 short
+// circles, else the warp-FFT form
+template <typename Tc>
+void launch_theta(const Requad& rq, const RequadArgs& ra, int nbox, int R, const cx<Tc>* GA, cx<Tc>* GB,
+                  size_t sm, cudaStream_t st) {
+    if (std::is_same<Tc, float>::value && rq.theta_w) {
+        const int64_t nseq = (int64_t)nbox * R;
+        const int64_t work = nseq * ra.big;
+        const unsigned g = (unsigned)std::min<int64_t>((work + 127) / 128, 152 * 32);
+        const int knr = rq.nra <= 9 ? 9 : (rq.nra <= 17 ? 17 : (rq.nra <= 25 ? 25 : 33));
+        const size_t smw = (size_t)rq.nrb * knr * sizeof(float4);
+        const cxf* ga = (const cxf*)GA;
+        cxf* gb = (cxf*)GB;
+        switch (knr) {
+            case 9: k_requad_theta_dense<9><<<g, 128, smw, st>>>(ra, nseq, rq.theta_w, rq.nra, rq.nrb, ga, gb); break;
+            case 17: k_requad_theta_dense<17><<<g, 128, smw, st>>>(ra, nseq, rq.theta_w, rq.nra, rq.nrb, ga, gb); break;
+            case 25: k_requad_theta_dense<25><<<g, 128, smw, st>>>(ra, nseq, rq.theta_w, rq.nra, rq.nrb, ga, gb); break;
+            default: k_requad_theta_dense<33><<<g, 128, smw, st>>>(ra, nseq, rq.theta_w, rq.nra, rq.nrb, ga, gb); break;
+        }
+        return;
+    }
+    k_requad_spec_cols<Tc><<<nblk((int64_t)nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(ra, nbox, R, GA, GB);
+}
+
 // Re-quadrature launches.  Tin / Tout: storage types of the input and output levels;
 // Tc: compute type, always the parent's (the coarser of the two; precision never decreases
 // with depth).  Going up, the parent's signature needs no more.  Going down, the parent's
@@ -785,8 +857,7 @@ void launch_up(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
     smem_opt_in(k_requad_spec_c_m2m<Tc, Tout>, sm3);
     k_requad_spec_a<Tin, Tc, kNoShift><<<nblk((int64_t)c.nbox * R * ra.qa.nrows, kWarps), 32 * kWarps, sm, st>>>(
         ra, c.nbox, R, (const cx<Tin>*)c.M, nullptr, nullptr, nullptr, GA);
-    k_requad_spec_cols<Tc><<<nblk((int64_t)c.nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(
-        ra, c.nbox, R, GA, GB);
+    launch_theta<Tc>(P->up[l], ra, c.nbox, R, GA, GB, sm, st);
     k_requad_spec_c_m2m<Tc, Tout><<<nblk((int64_t)p.nbox * R * ra.qb.nrows, kWarps), 32 * kWarps, sm3, st>>>(
         ra, p.nbox, R, p.bv.child_start, p.bv.child_count, c.octant, shift_of<Tc>(p), GB, (cx<Tout>*)p.M);
 }
@@ -827,8 +898,7 @@ void launch_down(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
     smem_opt_in(k_requad_spec_c_l2l<Tc, Tout>, sm);
     k_requad_spec_a<Tin, Tc, kShiftConj><<<nblk((int64_t)c.nbox * R * ra.qa.nrows, kWarps), 32 * kWarps, sm, st>>>(
         ra, c.nbox, R, (const cx<Tin>*)p.IL, c.bv.parent, c.octant, shift_of<Tc>(p), GA);
-    k_requad_spec_cols<Tc><<<nblk((int64_t)c.nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(
-        ra, c.nbox, R, GA, GB);
+    launch_theta<Tc>(P->down[l], ra, c.nbox, R, GA, GB, sm, st);
     k_requad_spec_c_l2l<Tc, Tout><<<nblk((int64_t)c.nbox * R * ra.qb.nrows, kWarps), 32 * kWarps, sm, st>>>(
         ra, c.nbox, R, GB, (cx<Tout>*)c.IL);
 }

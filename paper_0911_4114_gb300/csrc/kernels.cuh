@@ -1595,6 +1595,59 @@ __global__ void k_requad_spec_cols(RequadArgs ra, int nbox_seq, int R_, const cx
     }
 }
 
+// Pass B' of float32 re-quadratures with short theta circles (both N_theta <= 64): the map
+// k_requad_spec_cols applies to a coefficient pair (slot se of even, so of odd parity) is
+// linear in the pair's two columns of GA, so it is applied as a dense product with 2 x 2 blocks
+// of real matrices, W[n][u] = (Lee, Leo, Loe, Loo), built at plan time in float64 by running
+// that pass on unit columns:
+//     GB[n][se] = sum_u Lee[n][u] GA[u][se] + Leo[n][u] GA[u][so],
+//     GB[n][so] = sum_u Loe[n][u] GA[u][se] + Loo[n][u] GA[u][so],   n <= N_theta^b / 2.
+// For circles this short a warp-wide FFT leaves most lanes idle; here one thread takes one
+// (box, pair, real or imaginary part).  W sits in shared memory, kNR columns per row (zeros
+// past nra).
+constexpr int kThetaDenseMax = 33;   // rows N_theta / 2 + 1 of either grid
+template <int kNR>
+__global__ void __launch_bounds__(128) k_requad_theta_dense(RequadArgs ra, int64_t nseq, const float4* __restrict__ W,
+                                                            int nra, int nrb, const cxf* __restrict__ GA,
+                                                            cxf* __restrict__ GB) {
+    extern __shared__ float4 sW[];   // [nrb][kNR]
+    for (int i = threadIdx.x; i < nrb * kNR; i += blockDim.x) {
+        const int n = i / kNR, u = i % kNR;
+        sW[i] = u < nra ? W[n * nra + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    const int hb = ra.big / 2;
+    const int64_t total = nseq * hb * 2;
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
+        const int part = (int)(w & 1);
+        const int64_t cb = w >> 1;
+        const int c = (int)(cb % hb);
+        const int64_t br = cb / hb;
+        const int s_even = (c % 2 == 0) ? c : ra.big - 1 - c;
+        const int s_odd = (c % 2 == 0) ? ra.big - 1 - c : c;
+        const float* ga = reinterpret_cast<const float*>(GA + br * (int64_t)ra.qa.nrows * ra.big) + part;
+        float ge[kNR], go[kNR];
+#pragma unroll
+        for (int u = 0; u < kNR; ++u) {
+            ge[u] = u < nra ? ga[2 * ((int64_t)u * ra.big + s_even)] : 0.f;
+            go[u] = u < nra ? ga[2 * ((int64_t)u * ra.big + s_odd)] : 0.f;
+        }
+        float* gb = reinterpret_cast<float*>(GB + br * (int64_t)ra.qb.nrows * ra.big) + part;
+        for (int n = 0; n < nrb; ++n) {
+            const float4* wr = sW + n * kNR;
+            float e = 0.f, o = 0.f;
+#pragma unroll
+            for (int u = 0; u < kNR; ++u) {
+                const float4 m = wr[u];
+                e = fmaf(m.x, ge[u], fmaf(m.y, go[u], e));
+                o = fmaf(m.z, ge[u], fmaf(m.w, go[u], o));
+            }
+            gb[2 * ((int64_t)n * ra.big + s_even)] = e;
+            gb[2 * ((int64_t)n * ra.big + s_odd)] = o;
+        }
+    }
+}
+
 // coefficients of a GB' row, limited to the band of a length-len output row, into buf (length len)
 template <typename Tc>
 __device__ __forceinline__ void spec_row_to_buf(const cx<Tc>* row, int big, int len, cx<Tc>* buf, int lane) {
