@@ -73,6 +73,7 @@ struct Requad {
     // (Lee, Leo, Loe, Loo)[n][u], nrb x nra, or null
     const float4* theta_w = nullptr;
     int nra = 0, nrb = 0;
+    const float4* theta_wt = nullptr;   // the transposed pass (k_requad_spec_cols_t), nra x nrb
 };
 
 }  // namespace
@@ -414,6 +415,41 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 // split into its even (y[n] + y[-n]) / 2 and odd (y[n] - y[-n]) / 2 parts, n = 0 .. ntb/2.
 // Entry n * nra + u: (even part of the even circle, of the odd circle; odd part of the even
 // circle, of the odd circle).
+// The transposed theta pass (k_requad_spec_cols_t, rows n of grid b -> rows u of grid a) the
+// same way: unit values at row n of the even slot spread half onto m = n and m = ntb - n (the
+// whole value at n = 0 and n = ntb/2), of the odd slot +-half (nothing at n = 0, ntb/2); the
+// circle is re-sampled from ntb to nta (1/ntb), row u collects t = u and t = nta - u (the odd
+// slot with a sign flip), scaled by ntb / nta.  Entry u * nrb + n as in theta_matrices.
+std::vector<float4> theta_matrices_t(int nta, int ntb) {
+    const int ha = nta / 2, hbr = ntb / 2, nra = ha + 1, nrb = hbr + 1;
+    const int band = std::min((nta + 1) / 2, (ntb + 1) / 2) - 1;
+    const double two_pi = 2.0 * 3.14159265358979323846, sc = (double)ntb / nta;
+    auto resample = [&](const std::vector<std::pair<int, double>>& y, int t) {
+        double r = 0.0;
+        for (int f = -band; f <= band; ++f)
+            for (const auto& mv : y) r += mv.second * std::cos(two_pi * f * ((double)t / nta - (double)mv.first / ntb));
+        return r / ntb;
+    };
+    std::vector<float4> w((size_t)nra * nrb);
+    for (int n = 0; n < nrb; ++n) {
+        std::vector<std::pair<int, double>> ev, od;
+        if (n == 0 || n == hbr) {
+            ev.push_back({n, 1.0});
+        } else {
+            ev = {{n, 0.5}, {ntb - n, 0.5}};
+            od = {{n, 0.5}, {ntb - n, -0.5}};
+        }
+        for (int u = 0; u < nra; ++u) {
+            const bool two = u != 0 && u != ha;
+            const double e0 = resample(ev, u), em = two ? resample(ev, nta - u) : 0.0;
+            const double o0 = od.empty() ? 0.0 : resample(od, u), om = (two && !od.empty()) ? resample(od, nta - u) : 0.0;
+            w[(size_t)u * nrb + n] = make_float4((float)(sc * (e0 + em)), (float)(sc * (o0 + om)), (float)(sc * (e0 - em)),
+                                                 (float)(sc * (o0 - om)));
+        }
+    }
+    return w;
+}
+
 std::vector<float4> theta_matrices(int nta, int ntb) {
     const int ha = nta / 2, nra = ha + 1, nrb = ntb / 2 + 1;
     const int band = std::min((nta + 1) / 2, (ntb + 1) / 2) - 1;
@@ -723,6 +759,9 @@ hfmm_status upload_plan(hfmm_plan_s* P) {
                 float4* dw;
                 TRY(upload(P, &dw, theta_matrices(nta, ntb)));
                 rq.first->theta_w = dw;
+                float4* dwt;
+                TRY(upload(P, &dwt, theta_matrices_t(nta, ntb)));
+                rq.first->theta_wt = dwt;
                 rq.first->nra = nta / 2 + 1;
                 rq.first->nrb = ntb / 2 + 1;
             }
@@ -835,6 +874,31 @@ void launch_theta(const Requad& rq, const RequadArgs& ra, int nbox, int R, const
     k_requad_spec_cols<Tc><<<nblk((int64_t)nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(ra, nbox, R, GA, GB);
 }
 
+// the transposed theta pass (GB -> GA): the dense form for float32 short circles, else the
+// warp-FFT form
+template <typename Tc>
+void launch_theta_t(const Requad& rq, const RequadArgs& ra, int nbox, int R, const cx<Tc>* GB, cx<Tc>* GA,
+                    size_t sm, cudaStream_t st) {
+    if (std::is_same<Tc, float>::value && rq.theta_wt) {
+        const int64_t nseq = (int64_t)nbox * R;
+        const int64_t work = nseq * ra.big;
+        const unsigned g = (unsigned)std::min<int64_t>((work + 127) / 128, 152 * 32);
+        const int nin = rq.nrb, nout = rq.nra;
+        const int knr = nin <= 9 ? 9 : (nin <= 17 ? 17 : (nin <= 25 ? 25 : 33));
+        const size_t smw = (size_t)nout * knr * sizeof(float4);
+        const cxf* in = (const cxf*)GB;
+        cxf* out = (cxf*)GA;
+        switch (knr) {
+            case 9: k_requad_theta_dense<9><<<g, 128, smw, st>>>(ra, nseq, rq.theta_wt, nin, nout, in, out); break;
+            case 17: k_requad_theta_dense<17><<<g, 128, smw, st>>>(ra, nseq, rq.theta_wt, nin, nout, in, out); break;
+            case 25: k_requad_theta_dense<25><<<g, 128, smw, st>>>(ra, nseq, rq.theta_wt, nin, nout, in, out); break;
+            default: k_requad_theta_dense<33><<<g, 128, smw, st>>>(ra, nseq, rq.theta_wt, nin, nout, in, out); break;
+        }
+        return;
+    }
+    k_requad_spec_cols_t<Tc><<<nblk((int64_t)nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(ra, nbox, R, GB, GA);
+}
+
 // Re-quadrature launches.  Tin / Tout: storage types of the input and output levels;
 // Tc: compute type, always the parent's (the coarser of the two; precision never decreases
 // with depth).  Going up, the parent's signature needs no more.  Going down, the parent's
@@ -878,8 +942,7 @@ void launch_l2l_t(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
     smem_opt_in(k_requad_spec_at_sum<Tc, Tout>, sm3);
     k_requad_spec_ct<Tin, Tc, kNoShift><<<nblk((int64_t)c.nbox * R * ra.qb.nrows, kWarps), 32 * kWarps, sm, st>>>(
         ra, c.nbox, R, (const cx<Tin>*)c.IL, nullptr, nullptr, nullptr, GB);
-    k_requad_spec_cols_t<Tc><<<nblk((int64_t)c.nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(
-        ra, c.nbox, R, GB, GA);
+    launch_theta_t<Tc>(P->down[l], ra, c.nbox, R, GB, GA, sm, st);
     k_requad_spec_at_sum<Tc, Tout><<<nblk((int64_t)p.nbox * R * ra.qa.nrows, kWarps), 32 * kWarps, sm3, st>>>(
         ra, p.nbox, R, p.bv.child_start, p.bv.child_count, c.octant, shift_of<Tc>(p), GA, (cx<Tout>*)p.IL);
 }
@@ -918,8 +981,7 @@ void launch_m2m_t(hfmm_plan_s* P, int l, int R, cudaStream_t st) {
     smem_opt_in(k_requad_spec_at_add<Tc, Tout>, sm);
     k_requad_spec_ct<Tin, Tc, kShiftPlain><<<nblk((int64_t)c.nbox * R * ra.qb.nrows, kWarps), 32 * kWarps, sm, st>>>(
         ra, c.nbox, R, (const cx<Tin>*)p.M, c.bv.parent, c.octant, shift_of<Tc>(p), GB);
-    k_requad_spec_cols_t<Tc><<<nblk((int64_t)c.nbox * R * (ra.big / 2), kWarps), 32 * kWarps, sm, st>>>(
-        ra, c.nbox, R, GB, GA);
+    launch_theta_t<Tc>(P->up[l], ra, c.nbox, R, GB, GA, sm, st);
     k_requad_spec_at_add<Tc, Tout><<<nblk((int64_t)c.nbox * R * ra.qa.nrows, kWarps), 32 * kWarps, sm, st>>>(
         ra, c.nbox, R, GA, (cx<Tout>*)c.M);
 }

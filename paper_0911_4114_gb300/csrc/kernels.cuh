@@ -1604,12 +1604,14 @@ __global__ void k_requad_spec_cols(RequadArgs ra, int nbox_seq, int R_, const cx
 //     GB[n][so] = sum_u Loe[n][u] GA[u][se] + Loo[n][u] GA[u][so],   n <= N_theta^b / 2.
 // For circles this short a warp-wide FFT leaves most lanes idle; here one thread takes one
 // (box, pair, real or imaginary part).  W sits in shared memory, kNR columns per row (zeros
-// past nra).
+// past nra).  The transposed pass (k_requad_spec_cols_t, GB -> GA) runs the same kernel with
+// its own matrices: `in` has nra rows per (box, RHS), `out` nrb, both big slots wide.
 constexpr int kThetaDenseMax = 33;   // rows N_theta / 2 + 1 of either grid
 template <int kNR>
 __global__ void __launch_bounds__(128) k_requad_theta_dense(RequadArgs ra, int64_t nseq, const float4* __restrict__ W,
                                                             int nra, int nrb, const cxf* __restrict__ GA,
                                                             cxf* __restrict__ GB) {
+    // GA: input rows (nra per box-RHS), GB: output rows (nrb)
     extern __shared__ float4 sW[];   // [nrb][kNR]
     for (int i = threadIdx.x; i < nrb * kNR; i += blockDim.x) {
         const int n = i / kNR, u = i % kNR;
@@ -1625,14 +1627,14 @@ __global__ void __launch_bounds__(128) k_requad_theta_dense(RequadArgs ra, int64
         const int64_t br = cb / hb;
         const int s_even = (c % 2 == 0) ? c : ra.big - 1 - c;
         const int s_odd = (c % 2 == 0) ? ra.big - 1 - c : c;
-        const float* ga = reinterpret_cast<const float*>(GA + br * (int64_t)ra.qa.nrows * ra.big) + part;
+        const float* ga = reinterpret_cast<const float*>(GA + br * (int64_t)nra * ra.big) + part;
         float ge[kNR], go[kNR];
 #pragma unroll
         for (int u = 0; u < kNR; ++u) {
             ge[u] = u < nra ? ga[2 * ((int64_t)u * ra.big + s_even)] : 0.f;
             go[u] = u < nra ? ga[2 * ((int64_t)u * ra.big + s_odd)] : 0.f;
         }
-        float* gb = reinterpret_cast<float*>(GB + br * (int64_t)ra.qb.nrows * ra.big) + part;
+        float* gb = reinterpret_cast<float*>(GB + br * (int64_t)nrb * ra.big) + part;
         for (int n = 0; n < nrb; ++n) {
             const float4* wr = sW + n * kNR;
             float e = 0.f, o = 0.f;
