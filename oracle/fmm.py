@@ -13,6 +13,11 @@ Fourier quadratures of Section 3 with the re-quadrature of Section 3.4:
         (the rows n > N_theta/2 fold onto N_theta - n by Eq. NumSphereSym)
 * P2P   phi_i += sum_{j in N(b), R_ij > 0} q_j exp(i k R_ij) / R_ij
 
+On an adaptive tree (tree.py) the leaves lie on several levels: S2M runs for the
+leaves of each level at that level's quadrature and is added to the M2M result
+(which is zero for a leaf), L2T runs for the leaves of each level, and P2P takes
+each leaf's list of directly interacting leaves.
+
 Levels 2..L_f are active (L_f = deepest level the stability rule accepts, never
 deeper than the occupancy depth, and only levels whose boxes are about a wavelength
 or larger, k a_l >= 6: below that the Gegenbauer series converges only
@@ -71,7 +76,7 @@ class Plan:
     """Everything the apply needs: tree to depth L_f, per-level quadrature, transfer tables."""
 
     def __init__(self, sources, targets, kappa, eps, alphas=None, max_leaf=64, depth=0,
-                 root=None, precision='fp64', eps_scale=0.25, buffer=1):
+                 root=None, precision='fp64', eps_scale=0.25, buffer=1, adaptive=False):
         self.sources = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 3)
         self.targets = np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 3)
         self.kappa = float(kappa)
@@ -112,7 +117,9 @@ class Plan:
             lf = dmax
         self.occupancy_depth = dmax
         self.lf = lf
-        self.tree = Tree(self.sources, self.targets, lf, root, self.buffer)
+        self.adaptive = bool(adaptive)
+        self.tree = Tree(self.sources, self.targets, lf, root, self.buffer,
+                         max_leaf if self.adaptive else None)
         self._tables = {}
 
     def table(self, l, v):
@@ -131,16 +138,22 @@ def _boxes(boxes, n):
     return range(n) if boxes is None else [int(b) for b in boxes]
 
 
-def s2m(plan, qs, boxes=None):
-    """Leaf signatures M[b, r, k] (boxes: optional subset; the others stay zero)."""
+def _leaves(lev, boxes):
+    """The leaf boxes of a level, or the given subset of its boxes."""
+    return np.nonzero(lev['leaf'])[0] if boxes is None else [int(b) for b in boxes]
+
+
+def s2m(plan, qs, boxes=None, l=None):
+    """Signatures M[b, r, k] of the leaves of level l (default: the depth; boxes: optional
+    subset; the other boxes stay zero)."""
     t = plan.tree
-    lf = t.depth
+    lf = t.depth if l is None else l
     quad = plan.levels[lf].quad
     lev = t.levels[lf]
     ys = plan.sources[t.src_perm]
     out = np.zeros((len(lev['key']), qs.shape[1], quad.K), dtype=np.complex128)
-    for b in _boxes(boxes, len(lev['key'])):
-        s0, sc = t.src_start[b], t.src_count[b]
+    for b in _leaves(lev, boxes):
+        s0, sc = lev['src_start'][b], lev['src_count'][b]
         if sc == 0:
             continue
         d = ys[s0:s0 + sc] - lev['center'][b]
@@ -188,15 +201,17 @@ def l2l(plan, lpar, ichild, l, boxes=None):
     return qd.requadrature(shifted, qa, qb) + ichild[kids]
 
 
-def l2t(plan, lleaf, nrhs, boxes=None):
+def l2t(plan, lleaf, nrhs, boxes=None, l=None):
+    """Far field at the targets of the leaves of level l (default: the depth); the other
+    targets stay zero."""
     t = plan.tree
-    lf = t.depth
+    lf = t.depth if l is None else l
     quad = plan.levels[lf].quad
     lev = t.levels[lf]
     xs = plan.targets[t.tgt_perm]
     out = np.zeros((xs.shape[0], nrhs), dtype=np.complex128)
-    for b in _boxes(boxes, len(lev['key'])):
-        t0, tc = t.tgt_start[b], t.tgt_count[b]
+    for b in _leaves(lev, boxes):
+        t0, tc = lev['tgt_start'][b], lev['tgt_count'][b]
         if tc == 0:
             continue
         d = lev['center'][b] - xs[t0:t0 + tc]
@@ -211,7 +226,7 @@ def p2p(plan, qs, boxes=None):
     ys = plan.sources[t.src_perm]
     xs = plan.targets[t.tgt_perm]
     out = np.zeros((xs.shape[0], qs.shape[1]), dtype=np.complex128)
-    for b in _boxes(boxes, len(t.levels[lf]['key'])):
+    for b in _boxes(boxes, len(t.leaf_level)):
         t0, tc = t.tgt_start[b], t.tgt_count[b]
         if tc == 0:
             continue
@@ -239,11 +254,16 @@ def apply(plan, q, return_stages=False):
         mlev = {lf: s2m(plan, qs)}
         for l in range(lf, 2, -1):
             mlev[l - 1] = m2m(plan, mlev[l], l)
+            if t.levels[l - 1]['leaf'].any():       # leaves above the depth (adaptive tree)
+                mlev[l - 1] = mlev[l - 1] + s2m(plan, qs, l=l - 1)
         ilev = {l: m2l(plan, mlev[l], l) for l in range(2, lf + 1)}
         llev = {2: ilev[2]}
         for l in range(2, lf):
             llev[l + 1] = l2l(plan, llev[l], ilev[l + 1], l)
         far = l2t(plan, llev[lf], nrhs)
+        for l in range(2, lf):
+            if t.levels[l]['leaf'].any():
+                far = far + l2t(plan, llev[l], nrhs, l=l)
         stages.update(M=mlev, I=ilev, L=llev, far=far, near=phi_s.copy())
         phi_s = phi_s + far
     phi = np.zeros_like(phi_s)

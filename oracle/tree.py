@@ -17,6 +17,17 @@ for bit:
   coarser levels take the index shifted right;
 * box centre c = corner + (idx + 1/2) * (side / 2^l), box size a_l = side / 2^l;
 * only boxes holding at least one source or target exist (sparse, level uniform);
+* adaptive trees (max_leaf given): a box of level l < depth is split into its
+  children only when l < 2 (the far field starts at level 2) or it holds more than
+  max_leaf sources or more than max_leaf targets; the other boxes are leaves, so
+  leaves lie on several levels and no box exists below a leaf.  A target leaf B
+  and a source leaf C interact directly (P2P) when their ancestors at the coarser
+  of their two levels, m = min(l_B, l_C), are neighbours; otherwise the ancestors
+  first stop being neighbours at some level l0 <= m, where the source ancestor is in
+  the interaction list of the target ancestor (M2L).  This takes the U list and the
+  W and X lists of adaptive FMMs as direct interactions and keeps M2L between boxes
+  of one level, so the diagonal transfer of Section 3 is used unchanged (the paper
+  treats uniform trees only);
 * boxes and points are ordered by Morton key (x bit above y bit above z bit),
   points by key and then by original index;
 * "neighbour" = Chebyshev distance of box indices <= b, b the number of buffer
@@ -104,7 +115,8 @@ def transfer_offset(v, buffer=1):
 
 
 class Tree:
-    """Sparse level-uniform octree over sources and targets, levels 0..depth.
+    """Sparse octree over sources and targets, levels 0..depth: level uniform, or adaptive
+    (leaves on several levels) when max_leaf is given.
 
     Attributes
     ----------
@@ -116,12 +128,19 @@ class Tree:
                 boxes inside the permuted point arrays
     ilist[l], vlist[l] : for l >= 2, per box, the interaction-list box positions
                 (ascending) and their transfer-vector indices
-    nlist : per depth-level box, the neighbour-list box positions (ascending)
+    nlist : per leaf, the leaves it interacts with directly (ascending)
     buffer : number of buffer boxes (1 or 2)
+    leaf_level, leaf_box : level and position in that level of every leaf, in Morton
+                order of their points (a uniform tree's leaves are the depth-level boxes)
+    levels[l] also holds per box 'src_start', 'src_count', 'tgt_start', 'tgt_count'
+                (the points of its whole subtree, contiguous in tree order), 'split'
+                (has children) and 'leaf'
     """
 
-    def __init__(self, sources, targets, depth, root=None, buffer=1):
+    def __init__(self, sources, targets, depth, root=None, buffer=1, max_leaf=None):
         self.buffer = int(buffer)
+        self.max_leaf = None if max_leaf is None else int(max_leaf)
+        adaptive = self.max_leaf is not None
         sources = np.asarray(sources, dtype=np.float64).reshape(-1, 3)
         targets = np.asarray(targets, dtype=np.float64).reshape(-1, 3)
         allp = np.concatenate([sources, targets], axis=0)
@@ -143,6 +162,11 @@ class Tree:
         self.levels = []
         for l in range(D + 1):
             keys_l = np.unique(leaf_keys >> (3 * (D - l)))
+            if adaptive and l > 0:
+                # boxes exist only below split boxes
+                up = self.levels[l - 1]
+                pos = np.minimum(np.searchsorted(up['key'], keys_l >> 3), len(up['key']) - 1)
+                keys_l = keys_l[(up['key'][pos] == (keys_l >> 3)) & up['split'][pos]]
             idx = np.zeros((len(keys_l), 3), dtype=np.int64)
             for b in range(l):
                 idx[:, 0] |= ((keys_l >> (3 * b + 2)) & 1) << b
@@ -155,14 +179,34 @@ class Tree:
             else:
                 pkeys = self.levels[l - 1]['key']
                 parent = np.searchsorted(pkeys, keys_l >> 3).astype(np.int64)
+            sh = 3 * (D - l)
+            s0 = np.searchsorted(skey_sorted >> sh, keys_l, side='left')
+            sc = np.searchsorted(skey_sorted >> sh, keys_l, side='right') - s0
+            t0 = np.searchsorted(tkey_sorted >> sh, keys_l, side='left')
+            tc = np.searchsorted(tkey_sorted >> sh, keys_l, side='right') - t0
+            if adaptive:
+                split = (l < D) & ((l < 2) | (sc > self.max_leaf) | (tc > self.max_leaf))
+            else:
+                split = np.full(len(keys_l), l < D)
             self.levels.append({'idx': idx, 'key': keys_l, 'center': center,
-                                'parent': parent, 'a': h})
+                                'parent': parent, 'a': h,
+                                'src_start': s0, 'src_count': sc, 'tgt_start': t0, 'tgt_count': tc,
+                                'split': split, 'leaf': ~split})
 
-        lk = self.levels[D]['key']
-        self.src_start = np.searchsorted(skey_sorted, lk, side='left')
-        self.src_count = np.searchsorted(skey_sorted, lk, side='right') - self.src_start
-        self.tgt_start = np.searchsorted(tkey_sorted, lk, side='left')
-        self.tgt_count = np.searchsorted(tkey_sorted, lk, side='right') - self.tgt_start
+        # leaves of all levels in Morton order of their first depth-level key
+        lv = np.concatenate([np.full(int(L['leaf'].sum()), l, dtype=np.int64)
+                             for l, L in enumerate(self.levels)])
+        bx = np.concatenate([np.nonzero(L['leaf'])[0] for L in self.levels]).astype(np.int64)
+        first = np.array([int(self.levels[l]['key'][b]) << (3 * (D - l)) for l, b in zip(lv, bx)],
+                         dtype=np.int64)
+        order = np.argsort(first, kind='stable')
+        self.leaf_level, self.leaf_box = lv[order], bx[order]
+        pick = lambda f: np.array([self.levels[l][f][b] for l, b in zip(self.leaf_level, self.leaf_box)],
+                                  dtype=np.int64)
+        self.src_start, self.src_count = pick('src_start'), pick('src_count')
+        self.tgt_start, self.tgt_count = pick('tgt_start'), pick('tgt_count')
+        self._leaf_idx = np.array([self.levels[l]['idx'][b] for l, b in zip(self.leaf_level, self.leaf_box)],
+                                  dtype=np.int64).reshape(-1, 3)
 
         # lists, built per box on first use (ilist[l][a], vlist[l][a], nlist[a])
         self._where = {}
@@ -173,7 +217,18 @@ class Tree:
             n = len(self.levels[l]['key'])
             self.ilist[l] = _PerBox(n, lambda a, l=l: self._interaction_list(l, a)[0])
             self.vlist[l] = _PerBox(n, lambda a, l=l: self._interaction_list(l, a)[1])
-        self.nlist = _PerBox(len(self.levels[D]['key']), lambda a: self._neighbour_list(D, a))
+        if adaptive:
+            self.nlist = _PerBox(len(self.leaf_level), self._adaptive_neighbours)
+        else:
+            self.nlist = _PerBox(len(self.levels[D]['key']), lambda a: self._neighbour_list(D, a))
+
+    def _adaptive_neighbours(self, g):
+        """Leaves C whose ancestor at level min(l_B, l_C) neighbours leaf g's ancestor there."""
+        lb, lc = int(self.leaf_level[g]), self.leaf_level
+        m = np.minimum(lb, lc)
+        ab = self._leaf_idx[g][None, :] >> (lb - m)[:, None]
+        ac = self._leaf_idx >> (lc - m)[:, None]
+        return np.nonzero(np.max(np.abs(ab - ac), axis=1) <= self.buffer)[0].astype(np.int64)
 
     def _lookup(self, l):
         if l not in self._where:
