@@ -114,6 +114,14 @@ typedef struct {
  * the device (the default when a device is given).  Both follow Algorithm BMTF and the
  * per-row anterpolation of Section 3.3.2 in float64 and agree to round-off. */
 #define HFMM_FLAG_HOST_TABLES 2
+/* hfmm_options.flags: adaptive octree.  A box above the leaf level lf splits only when it
+ * lies above level 2 or holds more than max_leaf sources or more than max_leaf targets, so
+ * leaves lie on several levels (Section 2's tree, refined only where the points are dense).
+ * S2M and L2T run for the leaves of each level at that level's quadrature; M2L stays between
+ * boxes of one level (Section 3's diagonal transfer, unchanged); a target leaf B and a source
+ * leaf C interact directly when their ancestors at level min(l_B, l_C) are neighbours.  The
+ * plane-wave tables of a float64 leaf level are not used. */
+#define HFMM_FLAG_ADAPTIVE 4
 
 typedef struct {
     int64_t ns, nt;
@@ -156,6 +164,11 @@ typedef struct {
     /* tcgen05 near field (float32, 16 or more right-hand sides): (128-target chunk, 16-source
      * tile) pairs of the apply per 64-RHS pass, each 12 MMAs of 128 x 128 x 8 (0: not built) */
     int64_t near_mma_tiles;
+    /* 1 for an adaptive tree (HFMM_FLAG_ADAPTIVE); leaves in all and per level (a uniform
+     * tree's leaves are the level-lf boxes) */
+    int adaptive;
+    int64_t nleaf;
+    int level_nleaf[HFMM_MAX_LEVELS];
 } hfmm_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -275,16 +288,18 @@ typedef enum {
     HFMM_GET_ILIST_IDX = 3,    /* int32 interaction-list box positions */
     HFMM_GET_ILIST_V = 4,      /* int32 transfer-vector indices (di+D)*W*W+(dj+D)*W+(dk+D), D = 2b+1,
                                   W = 2D+1 for b buffer boxes (b = 1: (di+3)*49+(dj+3)*7+(dk+3)) */
-    HFMM_GET_NLIST_OFF = 5,    /* int32 (nbox+1) CSR offsets of the leaf neighbour lists (Chebyshev
-                                  distance <= b) */
-    HFMM_GET_NLIST_IDX = 6,    /* int32 neighbour-list box positions */
+    HFMM_GET_NLIST_OFF = 5,    /* int32 (nleaf+1) CSR offsets of the leaf near lists (uniform tree:
+                                  the neighbours within Chebyshev distance <= b) */
+    HFMM_GET_NLIST_IDX = 6,    /* int32 near-list leaf indices */
     HFMM_GET_SRC_PERM = 7,     /* int64 (ns) original index of each sorted source */
     HFMM_GET_TGT_PERM = 8,     /* int64 (nt) original index of each sorted target */
     HFMM_GET_NPHI = 9,         /* int32 (ntheta/2+1) N_phi(theta_n) of `level` */
     HFMM_GET_TABLE = 10,       /* float64 (K, 2) T^{s,LL} of `level` for vector `arg` (device-computed
                                   tables are copied back and converted) */
-    HFMM_GET_LEAF_SRC = 11,    /* int32 (nbox, 2) first sorted source and count per leaf box */
-    HFMM_GET_LEAF_TGT = 12     /* int32 (nbox, 2) first sorted target and count per leaf box */
+    HFMM_GET_LEAF_SRC = 11,    /* int32 (nleaf, 2) first sorted source and count per leaf */
+    HFMM_GET_LEAF_TGT = 12,    /* int32 (nleaf, 2) first sorted target and count per leaf */
+    HFMM_GET_LEAF_BOX = 13     /* int32 (nleaf, 2) level and position in that level of every leaf,
+                                  in Morton order (the order of the near lists) */
 } hfmm_get;
 
 int64_t hfmm_debug_get(hfmm_plan_t plan, int what, int level, int64_t arg, void* out, int64_t cap);

@@ -17,10 +17,11 @@ OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_UNSTABLE, ERR_TIMEOUT, ERR_STATE = range(7
 C64, C128 = 0, 1
 FLAG_REQUIRE_FAR = 1
 FLAG_HOST_TABLES = 2
+FLAG_ADAPTIVE = 4
 PREC_FP64, PREC_MIXED = 0, 1
 
 GET = dict(BOX_IDX=0, BOX_PARENT=1, ILIST_OFF=2, ILIST_IDX=3, ILIST_V=4, NLIST_OFF=5, NLIST_IDX=6,
-           SRC_PERM=7, TGT_PERM=8, NPHI=9, TABLE=10, LEAF_SRC=11, LEAF_TGT=12)
+           SRC_PERM=7, TGT_PERM=8, NPHI=9, TABLE=10, LEAF_SRC=11, LEAF_TGT=12, LEAF_BOX=13)
 
 EXPORTS = ("hfmm_default_options", "hfmm_plan", "hfmm_apply", "hfmm_query", "hfmm_set_timing",
            "hfmm_destroy", "hfmm_last_error", "hfmm_debug_get", "hfmm_direct_noalloc", "hfmm_apply_adjoint", "hfmm_grad_sources", "hfmm_plan_batch",
@@ -54,7 +55,8 @@ class Info(ctypes.Structure):
                 ("near_precision", ctypes.c_int), ("p2p_self_pairs", ctypes.c_int64),
                 ("near_symmetric", ctypes.c_int), ("leaf_tables", ctypes.c_int),
                 ("leaf_table_bytes", ctypes.c_int64), ("buffer", ctypes.c_int), ("tuned", ctypes.c_int),
-                ("predicted_ms", (ctypes.c_double * MAX_LEVELS) * 3), ("near_variant", ctypes.c_int), ("near_mma_tiles", ctypes.c_int64)]
+                ("predicted_ms", (ctypes.c_double * MAX_LEVELS) * 3), ("near_variant", ctypes.c_int), ("near_mma_tiles", ctypes.c_int64),
+                ("adaptive", ctypes.c_int), ("nleaf", ctypes.c_int64), ("level_nleaf", ctypes.c_int * MAX_LEVELS)]
 
 
 _lib = None

@@ -1322,7 +1322,8 @@ hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, 
     if (!(opt.eps_scale > 0.0 && opt.eps_scale <= 1.0)) return fail(HFMM_ERR_ARG, "eps_scale must be in (0, 1]");
     if (opt.precision != HFMM_PREC_FP64 && opt.precision != HFMM_PREC_MIXED)
         return fail(HFMM_ERR_ARG, "unknown precision policy");
-    if (opt.flags & ~(HFMM_FLAG_REQUIRE_FAR | HFMM_FLAG_HOST_TABLES)) return fail(HFMM_ERR_ARG, "unknown flag bits");
+    if (opt.flags & ~(HFMM_FLAG_REQUIRE_FAR | HFMM_FLAG_HOST_TABLES | HFMM_FLAG_ADAPTIVE))
+        return fail(HFMM_ERR_ARG, "unknown flag bits");
     if (opt.leaf_table_bytes < -1) return fail(HFMM_ERR_ARG, "leaf_table_bytes must be -1, 0 or positive");
     if (opt.buffer < 0 || opt.buffer > 2) return fail(HFMM_ERR_ARG, "buffer must be 0 (chosen by the plan), 1 or 2");
     std::vector<double> alphas;
@@ -1373,7 +1374,9 @@ hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, 
         hp.model_rhs = opt.max_rhs;
         hp.model_near = opt.precision == HFMM_PREC_MIXED ? (eps >= 1e-6 ? kFP32 : (eps >= 1e-11 ? kDF : kFP64)) : kFP64;
         hp.model_sym = ns == nt && (sources == targets || std::memcmp(sources, targets, sizeof(double) * 3 * ns) == 0);
-        hp.model_table_bytes = opt.leaf_table_bytes;
+        hp.adaptive = (opt.flags & HFMM_FLAG_ADAPTIVE) ? 1 : 0;
+        // adaptive trees evaluate plane waves per leaf level: no float64 leaf tables
+        hp.model_table_bytes = hp.adaptive ? 0 : opt.leaf_table_bytes;
         // transfer tables on the device unless asked for on the host (or no device)
         hp.host_tables = opt.device < 0 || (opt.flags & HFMM_FLAG_HOST_TABLES);
         hp.has_root = opt.has_root;
@@ -1415,7 +1418,7 @@ hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, 
     }
     P->rmax = opt.max_rhs;
     P->device = opt.device;
-    P->tab_budget = opt.leaf_table_bytes;
+    P->tab_budget = hp.adaptive ? 0 : opt.leaf_table_bytes;
     if (opt.precision == HFMM_PREC_MIXED) P->near_prec = eps >= 1e-6 ? kFP32 : (eps >= 1e-11 ? kDF : kFP64);
     P->sym = ns == nt && (sources == targets || std::memcmp(sources, targets, sizeof(double) * 3 * ns) == 0) &&
              P->hp.src_perm == P->hp.tgt_perm && P->hp.src_count == P->hp.tgt_count;
@@ -1746,6 +1749,9 @@ hfmm_status hfmm_query(hfmm_plan_t P, hfmm_info* info) {
     for (int b = 0; b < 3; ++b)
         for (int l = 0; l < HFMM_MAX_LEVELS; ++l) info->predicted_ms[b][l] = hp.predicted_ms[b][l];
     info->leaf_table_bytes = P->tab_bytes;
+    info->adaptive = hp.adaptive;
+    info->nleaf = (int64_t)hp.leaf_level.size();
+    for (int l = 0; l <= hp.lf && l < HFMM_MAX_LEVELS; ++l) info->level_nleaf[l] = (int)hp.levels[l].leaf_pos.size();
     if (P->ev_recorded) {
         if (cudaEventSynchronize(P->ev[HFMM_N_STAGES]) != cudaSuccess)
             return fail(HFMM_ERR_CUDA, "event synchronize failed");
@@ -1968,6 +1974,17 @@ int64_t hfmm_debug_get(hfmm_plan_t P, int what, int level, int64_t arg, void* ou
                 for (int64_t k = 0; k < std::min(n, cap / 2); ++k) {
                     o[2 * k] = t[k].real();
                     o[2 * k + 1] = t[k].imag();
+                }
+            }
+            return 2 * n;
+        }
+        case HFMM_GET_LEAF_BOX: {
+            const int64_t n = (int64_t)hp.leaf_level.size();
+            if (out) {
+                int32_t* o = static_cast<int32_t*>(out);
+                for (int64_t i = 0; i < std::min(n, cap / 2); ++i) {
+                    o[2 * i] = hp.leaf_level[i];
+                    o[2 * i + 1] = hp.leaf_box[i];
                 }
             }
             return 2 * n;

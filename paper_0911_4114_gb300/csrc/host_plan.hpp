@@ -48,6 +48,10 @@ struct TreeLevel {
     std::vector<double> center;    // (n, 3)
     std::vector<int32_t> child_start, child_count;  // children in the level below (contiguous)
     std::vector<int32_t> ioff, iidx, iv;            // interaction lists (CSR), level >= 2
+    std::vector<char> split;                        // the box has children in the level below
+    std::vector<int32_t> leaf_pos;                  // positions of this level's leaf boxes
+    // adaptive trees: first sorted point and count of every box's subtree (per box)
+    std::vector<int32_t> s_start, s_count, t_start, t_count;
     int64_t nbox() const { return (int64_t)key.size(); }
 };
 
@@ -60,6 +64,9 @@ struct HostPlan {
     std::vector<double> alphas;
     double eps_scale = 0.25;
     int max_leaf = 64, depth_req = 0, precision = 0;
+    // adaptive tree: a box above the depth splits only when it lies above level 2 or holds
+    // more than max_leaf sources or targets, so leaves lie on several levels; 0 = level uniform
+    int adaptive = 0;
     bool host_tables = true;   // false: T^{s,LL} is computed on the device at upload
     int buffer = 1;      // buffer boxes between a box and its interaction list (Section 3.3.3);
                          // 0 on input: chosen by the plan-shape tuner (1 or 2 on output)
@@ -80,8 +87,12 @@ struct HostPlan {
     int lf = 0;          // deepest active level (tree depth used by the apply)
     std::vector<int64_t> src_perm, tgt_perm;
     std::vector<TreeLevel> levels;                  // 0..lf
-    std::vector<int32_t> src_start, src_count, tgt_start, tgt_count;  // per leaf box
-    std::vector<int32_t> noff, nidx;                // leaf neighbour lists (CSR)
+    // leaves in Morton order of their points (a uniform tree's leaves are the level-lf boxes):
+    // level and position in that level, point ranges, and the leaves each one interacts with
+    // directly (CSR; uniform: the neighbours within Chebyshev distance buffer)
+    std::vector<int32_t> leaf_level, leaf_box;
+    std::vector<int32_t> src_start, src_count, tgt_start, tgt_count;  // per leaf
+    std::vector<int32_t> noff, nidx;                // leaf near lists (CSR)
     int64_t p2p_pairs = 0;
     int64_t p2p_self_pairs = 0;   // pairs inside one leaf box (target count x source count)
     // per level l = 2..lf

@@ -549,11 +549,20 @@ static void build_tree(HostPlan& hp) {
     std::sort(allk.begin(), allk.end());
     allk.erase(std::unique(allk.begin(), allk.end()), allk.end());
     hp.levels.assign(D + 1, TreeLevel());
+    // adaptive trees: level-l keys of the sorted points (for the per-box subtree ranges)
+    std::vector<uint64_t> lks, lkt;
     for (int l = 0; l <= D; ++l) {
         TreeLevel& L = hp.levels[l];
         for (auto k : allk) {
             uint64_t kl = k >> (3 * (D - l));
-            if (L.key.empty() || L.key.back() != kl) L.key.push_back(kl);
+            if (!L.key.empty() && L.key.back() == kl) continue;
+            if (hp.adaptive && l > 0) {
+                // boxes exist only below split boxes
+                const TreeLevel& U = hp.levels[l - 1];
+                const int64_t pb = find_key(U.key, kl >> 3);
+                if (pb < 0 || !U.split[pb]) continue;
+            }
+            L.key.push_back(kl);
         }
         const int64_t nb = L.nbox();
         L.idx.resize(3 * nb);
@@ -575,6 +584,31 @@ static void build_tree(HostPlan& hp) {
                 P.child_count[L.parent[b]]++;
             }
         }
+        if (hp.adaptive) {
+            // subtree ranges: the sorted points whose level-l key is the box's key
+            auto sub = [&](const std::vector<uint64_t>& k, const std::vector<int64_t>& perm, std::vector<uint64_t>& lk,
+                           std::vector<int32_t>& start, std::vector<int32_t>& count) {
+                lk.resize(perm.size());
+                for (size_t p = 0; p < perm.size(); ++p) lk[p] = k[perm[p]] >> (shift + 3 * (D - l));
+                start.resize(nb);
+                count.resize(nb);
+                for (int64_t b = 0; b < nb; ++b) {
+                    auto lo = std::lower_bound(lk.begin(), lk.end(), L.key[b]);
+                    auto hi = std::upper_bound(lo, lk.end(), L.key[b]);
+                    start[b] = (int32_t)(lo - lk.begin());
+                    count[b] = (int32_t)(hi - lo);
+                }
+            };
+            sub(ks, hp.src_perm, lks, L.s_start, L.s_count);
+            sub(kt, hp.tgt_perm, lkt, L.t_start, L.t_count);
+            L.split.assign(nb, 0);
+            for (int64_t b = 0; b < nb; ++b)
+                L.split[b] = l < D && (l < 2 || L.s_count[b] > hp.max_leaf || L.t_count[b] > hp.max_leaf);
+        } else {
+            L.split.assign(nb, l < D ? 1 : 0);
+        }
+        for (int64_t b = 0; b < nb; ++b)
+            if (!L.split[b]) L.leaf_pos.push_back((int32_t)b);
     }
     // leaf point ranges
     TreeLevel& leaf = hp.levels[D];
@@ -593,8 +627,84 @@ static void build_tree(HostPlan& hp) {
         for (int64_t i = 0; i < nb; ++i)
             if (count[i] == 0) start[i] = (i > 0) ? start[i - 1] + count[i - 1] : 0;
     };
-    ranges(ks, hp.src_perm, hp.src_start, hp.src_count);
-    ranges(kt, hp.tgt_perm, hp.tgt_start, hp.tgt_count);
+    if (hp.adaptive) {
+        // leaves of all levels in Morton order of their first depth-D key
+        std::vector<std::array<int64_t, 3>> lv;
+        for (int l = 0; l <= D; ++l)
+            for (int32_t b : hp.levels[l].leaf_pos)
+                lv.push_back({(int64_t)(hp.levels[l].key[b] << (3 * (D - l))), l, b});
+        std::sort(lv.begin(), lv.end());
+        const int64_t nl = (int64_t)lv.size();
+        hp.leaf_level.resize(nl);
+        hp.leaf_box.resize(nl);
+        hp.src_start.resize(nl);
+        hp.src_count.resize(nl);
+        hp.tgt_start.resize(nl);
+        hp.tgt_count.resize(nl);
+        std::vector<uint64_t> first(nl);
+        for (int64_t g = 0; g < nl; ++g) {
+            const TreeLevel& L = hp.levels[lv[g][1]];
+            const int32_t b = (int32_t)lv[g][2];
+            first[g] = (uint64_t)lv[g][0];
+            hp.leaf_level[g] = (int32_t)lv[g][1];
+            hp.leaf_box[g] = b;
+            hp.src_start[g] = L.s_start[b];
+            hp.src_count[g] = L.s_count[b];
+            hp.tgt_start[g] = L.t_start[b];
+            hp.tgt_count[g] = L.t_count[b];
+        }
+        // near lists: leaves C whose ancestor at level m = min(l_B, l_C) neighbours leaf B's
+        // ancestor there: (i) every leaf under a level-l_B neighbour of B (l_C >= l_B);
+        // (ii) leaves of a coarser level m that neighbour B's level-m ancestor
+        const int bw = hp.buffer;
+        std::vector<std::vector<int32_t>> nf(nl);
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t g = 0; g < nl; ++g) {
+            const int lb = hp.leaf_level[g];
+            const int32_t* ib = &hp.levels[lb].idx[3 * hp.leaf_box[g]];
+            for (int m = 0; m <= lb; ++m) {
+                const TreeLevel& M = hp.levels[m];
+                const int n1 = 1 << m;
+                const int32_t a[3] = {ib[0] >> (lb - m), ib[1] >> (lb - m), ib[2] >> (lb - m)};
+                for (int dx = -bw; dx <= bw; ++dx)
+                    for (int dy = -bw; dy <= bw; ++dy)
+                        for (int dz = -bw; dz <= bw; ++dz) {
+                            const int c[3] = {a[0] + dx, a[1] + dy, a[2] + dz};
+                            if (c[0] < 0 || c[1] < 0 || c[2] < 0 || c[0] >= n1 || c[1] >= n1 || c[2] >= n1) continue;
+                            const int64_t nbx = find_key(M.key, morton(c[0], c[1], c[2], m));
+                            if (nbx < 0) continue;
+                            const uint64_t k0 = M.key[nbx] << (3 * (D - m));
+                            if (m == lb) {
+                                const uint64_t k1 = (M.key[nbx] + 1) << (3 * (D - m));
+                                auto lo = std::lower_bound(first.begin(), first.end(), k0);
+                                auto hi = std::lower_bound(lo, first.end(), k1);
+                                for (auto it = lo; it != hi; ++it) nf[g].push_back((int32_t)(it - first.begin()));
+                            } else if (!M.split[nbx]) {
+                                nf[g].push_back((int32_t)(std::lower_bound(first.begin(), first.end(), k0) - first.begin()));
+                            }
+                        }
+            }
+            std::sort(nf[g].begin(), nf[g].end());
+        }
+        hp.noff.assign(nl + 1, 0);
+        for (int64_t g = 0; g < nl; ++g) hp.noff[g + 1] = hp.noff[g] + (int32_t)nf[g].size();
+        hp.nidx.resize(hp.noff.back());
+        hp.p2p_pairs = 0;
+        hp.p2p_self_pairs = 0;
+        for (int64_t g = 0; g < nl; ++g) {
+            for (size_t t = 0; t < nf[g].size(); ++t) {
+                hp.nidx[hp.noff[g] + t] = nf[g][t];
+                hp.p2p_pairs += (int64_t)hp.tgt_count[g] * hp.src_count[nf[g][t]];
+            }
+            hp.p2p_self_pairs += (int64_t)hp.tgt_count[g] * hp.src_count[g];
+        }
+    } else {
+        ranges(ks, hp.src_perm, hp.src_start, hp.src_count);
+        ranges(kt, hp.tgt_perm, hp.tgt_start, hp.tgt_count);
+        hp.leaf_level.assign(nb, D);
+        hp.leaf_box.resize(nb);
+        std::iota(hp.leaf_box.begin(), hp.leaf_box.end(), 0);
+    }
     // interaction lists: children of the parent's neighbours (Chebyshev distance <= buffer)
     // that are not neighbours of the box itself
     const int bw = hp.buffer, TD = transfer_span(bw), TW = transfer_width(bw);
@@ -636,6 +746,7 @@ static void build_tree(HostPlan& hp) {
                 L.iv[L.ioff[a] + t] = (int32_t)found[a][t][2];
             }
     }
+    if (hp.adaptive) return;
     // neighbour lists at the leaf level
     hp.noff.assign(nb + 1, 0);
     std::vector<std::vector<std::pair<uint64_t, int64_t>>> nf(nb);

@@ -14,7 +14,8 @@ from ._native import MAX_LEVELS
 _PREC_NAMES = {0: "fp64", 1: "fp32", 2: "df"}   # hfmm_level_precision codes
 
 def make_options(precision="fp64", alphas=None, eps_scale=0.25, max_leaf=64, depth=0, root=None,
-                 max_rhs=1, device=0, require_far=False, leaf_table_bytes=-1, buffer=1, host_tables=False):
+                 max_rhs=1, device=0, require_far=False, leaf_table_bytes=-1, buffer=1, host_tables=False,
+                 adaptive=False):
     opt = nat.Options()
     nat.lib().hfmm_default_options(ctypes.byref(opt))
     if alphas is not None:              # None keeps the library default ladder
@@ -30,7 +31,8 @@ def make_options(precision="fp64", alphas=None, eps_scale=0.25, max_leaf=64, dep
     opt.precision = {"fp64": nat.PREC_FP64, "mixed": nat.PREC_MIXED}[precision]
     opt.max_rhs = max_rhs
     opt.device = device
-    opt.flags = (nat.FLAG_REQUIRE_FAR if require_far else 0) | (nat.FLAG_HOST_TABLES if host_tables else 0)
+    opt.flags = ((nat.FLAG_REQUIRE_FAR if require_far else 0) | (nat.FLAG_HOST_TABLES if host_tables else 0)
+                 | (nat.FLAG_ADAPTIVE if adaptive else 0))
     opt.leaf_table_bytes = int(leaf_table_bytes)
     opt.buffer = int(buffer)
     return opt
@@ -48,17 +50,20 @@ class FmmPlan:
     host_tables: compute the transfer tables on the host (default: on the device when there is one).
     buffer: buffer boxes between a box and its interaction list, 1 or 2 (Section 3.3.3), or 0:
     chosen with the leaf level by the plan's cost model (the "auto" plan shape).
+    adaptive: adaptive octree -- boxes split only where they hold more than max_leaf sources
+    or targets, so leaves lie on several levels (S2M / L2T per leaf level, same-level M2L,
+    direct interaction between leaves whose ancestors at the coarser leaf level neighbour).
     """
 
     def __init__(self, sources, targets, kappa, eps, precision="fp64", alphas=None,
                  eps_scale=0.25, max_leaf=64, depth=0, root=None, max_rhs=1, device=0,
-                 require_far=False, leaf_table_bytes=-1, buffer=1, host_tables=False):
+                 require_far=False, leaf_table_bytes=-1, buffer=1, host_tables=False, adaptive=False):
         L = nat.lib()
         src = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 3)
         tgt = np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 3)
         self.same = sources is targets
         opt = make_options(precision, alphas, eps_scale, max_leaf, depth, root, max_rhs, device,
-                           require_far, leaf_table_bytes, buffer, host_tables)
+                           require_far, leaf_table_bytes, buffer, host_tables, adaptive)
         h = ctypes.c_void_p()
         nat.check(L.hfmm_plan(src.ctypes.data, src.shape[0], tgt.ctypes.data, tgt.shape[0],
                               float(kappa), float(eps), ctypes.byref(opt), ctypes.byref(h)))
@@ -167,7 +172,9 @@ class FmmPlan:
                     buffer=inf.buffer, tuned=bool(inf.tuned),
                     predicted_ms={(b, l): inf.predicted_ms[b][l] for b in (1, 2)
                                   for l in range(MAX_LEVELS) if inf.predicted_ms[b][l] > 0},
-                    near_variant=inf.near_variant, near_mma_tiles=inf.near_mma_tiles)
+                    near_variant=inf.near_variant, near_mma_tiles=inf.near_mma_tiles,
+                    adaptive=bool(inf.adaptive), nleaf=inf.nleaf,
+                    level_nleaf=[inf.level_nleaf[l] for l in range(lf + 1)])
 
     def debug_get(self, what, level=0, arg=0):
         L = nat.lib()
@@ -182,7 +189,7 @@ class FmmPlan:
             return out[0::2] + 1j * out[1::2]
         if what == "BOX_IDX":
             return out.reshape(-1, 3)
-        if what in ("LEAF_SRC", "LEAF_TGT"):
+        if what in ("LEAF_SRC", "LEAF_TGT", "LEAF_BOX"):
             return out.reshape(-1, 2)
         return out
 

@@ -137,7 +137,7 @@ def test_require_far_flag_returns_unstable():
     assert status(60.0, nat.FLAG_REQUIRE_FAR, max_leaf=16) == nat.OK    # kappa a_2 = 15
     assert status(60.0, nat.FLAG_REQUIRE_FAR, max_leaf=4000) == nat.ERR_UNSTABLE   # depth 0
     assert b"occupancy depth" in L.hfmm_last_error()
-    assert status(60.0, 4, max_leaf=16) == nat.ERR_ARG                  # unknown flag bit
+    assert status(60.0, 8, max_leaf=16) == nat.ERR_ARG                  # unknown flag bit
     assert status(60.0, 0, max_leaf=16, leaf_table_bytes=-2) == nat.ERR_ARG
     with pytest.raises(nat.HfmmError) as e:
         FmmPlan(x, x, 5.0, 1e-6, max_leaf=16, device=-1, require_far=True)
