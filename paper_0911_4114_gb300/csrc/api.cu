@@ -64,6 +64,15 @@ struct DevLevel {
     cx<df>* shiftdf = nullptr;
     void* M = nullptr;          // nbox * Rmax * K
     void* IL = nullptr;         // incoming, then local expansions (in place)
+    // this level's leaves (a uniform tree's level-lf leaves are all its boxes, other levels
+    // none): count, positions (null: every box), subtree point ranges per box, 32-point chunks
+    // (box, first point) of the leaves' targets and sources, largest leaf point counts
+    int nleaf = 0;
+    const int32_t* leaf = nullptr;
+    const int32_t *sstart = nullptr, *scount = nullptr, *tstart = nullptr, *tcount = nullptr;
+    const int2 *tunits = nullptr, *sunits = nullptr;
+    int ntunits = 0, nsunits = 0;
+    int max_src = 1, max_tgt = 1;
 };
 
 struct Requad {
@@ -255,6 +264,49 @@ hfmm_status upload_level(hfmm_plan_s* P, int l) {
         TRY(upload(P, &cc, T.child_count));
     }
     d.bv = BoxView{d.nbox, center, idx, parent, cs, cc};
+    // leaves of this level
+    if (!hp.adaptive) {
+        if (l == hp.lf) {
+            d.nleaf = d.nbox;
+            d.sstart = P->sstart;
+            d.scount = P->scount;
+            d.tstart = P->tstart;
+            d.tcount = P->tcount;
+            d.tunits = P->tunits;
+            d.sunits = P->sunits;
+            d.ntunits = P->ntunits;
+            d.nsunits = P->nsunits;
+            d.max_src = P->max_src_leaf;
+            d.max_tgt = P->max_tgt_leaf;
+        }
+    } else if (!T.leaf_pos.empty()) {
+        d.nleaf = (int)T.leaf_pos.size();
+        int32_t *lp_, *ss, *sc, *ts, *tc;
+        TRY(upload(P, &lp_, T.leaf_pos));
+        TRY(upload(P, &ss, T.s_start));
+        TRY(upload(P, &sc, T.s_count));
+        TRY(upload(P, &ts, T.t_start));
+        TRY(upload(P, &tc, T.t_count));
+        d.leaf = lp_;
+        d.sstart = ss;
+        d.scount = sc;
+        d.tstart = ts;
+        d.tcount = tc;
+        std::vector<int2> tu, su;
+        for (int32_t b : T.leaf_pos) {
+            for (int c = 0; c < T.t_count[b]; c += 32) tu.push_back(make_int2(b, c));
+            for (int c = 0; c < T.s_count[b]; c += 32) su.push_back(make_int2(b, c));
+            d.max_src = std::max(d.max_src, (int)T.s_count[b]);
+            d.max_tgt = std::max(d.max_tgt, (int)T.t_count[b]);
+        }
+        int2 *dtu, *dsu;
+        TRY(upload(P, &dtu, tu));
+        TRY(upload(P, &dsu, su));
+        d.tunits = dtu;
+        d.sunits = dsu;
+        d.ntunits = (int)tu.size();
+        d.nsunits = (int)su.size();
+    }
     std::vector<int32_t> oct(d.nbox);
     for (int b = 0; b < d.nbox; ++b)
         oct[b] = 4 * (T.idx[3 * b] & 1) + 2 * (T.idx[3 * b + 1] & 1) + (T.idx[3 * b + 2] & 1);
@@ -1138,14 +1190,14 @@ void run_m2l(hfmm_plan_s* P, int l, int R, cudaStream_t st, bool transposed) {
 // double-float levels evaluate their plane waves in double-float
 bool use_df(hfmm_plan_s* P, int l) { return P->lev[l].prec == kDF; }
 
-// points -> signature at the leaf level: S2M (sources, sign +1) or transposed L2T
-// (targets, sign -1, weighted)
+// points -> signature at the leaves of level l: S2M (sources, sign +1) or transposed L2T
+// (targets, sign -1, weighted); other boxes of the level are left as they are
 template <typename T>
-void launch_s2m(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false) {
-    const int lf = P->hp.lf;
-    DevLevel& d = P->lev[lf];
-    const int32_t* start = transposed ? P->tstart : P->sstart;
-    const int32_t* count = transposed ? P->tcount : P->scount;
+void launch_s2m(hfmm_plan_s* P, int l, int R, cudaStream_t st, bool transposed = false) {
+    DevLevel& d = P->lev[l];
+    if (d.nleaf == 0) return;
+    const int32_t* start = transposed ? d.tstart : d.sstart;
+    const int32_t* count = transposed ? d.tcount : d.scount;
     const double* px = transposed ? P->tx : P->sx;
     const double* py = transposed ? P->ty : P->sy;
     const double* pz = transposed ? P->tz : P->sz;
@@ -1154,10 +1206,12 @@ void launch_s2m(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false)
     const double sign = transposed ? -1.0 : 1.0;
     const double* wk = transposed ? d.qv.w : nullptr;
     const double kt = P->hp.kappa / (2.0 * 3.14159265358979323846);
-    dim3 grid(d.nbox, nblk(d.qv.npair, kS2MThreads));
+    BoxView bl = d.bv;
+    bl.leaf = d.leaf;
+    dim3 grid(d.nleaf, nblk(d.qv.npair, kS2MThreads));
     if (std::is_same<T, double>::value && P->tab_s) {
-        // float64 leaf with plane-wave tables: S2M reads the sources' table as stored, the
-        // transposed L2T the targets' table conjugated
+        // float64 leaf with plane-wave tables (uniform trees): S2M reads the sources' table as
+        // stored, the transposed L2T the targets' table conjugated
         const cxd* E = transposed ? P->tab_t : P->tab_s;
         const dim3 g(d.nbox, nblk(d.qv.npair, kTabThreads));
         if (transposed) {
@@ -1169,34 +1223,34 @@ void launch_s2m(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false)
         }
         return;
     }
-    if (std::is_same<T, double>::value && use_df(P, lf)) {
+    if (std::is_same<T, double>::value && use_df(P, l)) {
         if (R == 1)
-            k_s2m_df<1><<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt,
+            k_s2m_df<1><<<grid, kS2MThreads, 0, st>>>(bl, d.qv, start, count, px, py, pz, charges, R, kt,
                                                       P->cis_tab, (cx<df>*)out, sign, wk);
         else
-            k_s2m_df<4><<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt,
+            k_s2m_df<4><<<grid, kS2MThreads, 0, st>>>(bl, d.qv, start, count, px, py, pz, charges, R, kt,
                                                       P->cis_tab, (cx<df>*)out, sign, wk);
         return;
     }
     if (R == 1)
-        k_s2m<T, 1><<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt,
+        k_s2m<T, 1><<<grid, kS2MThreads, 0, st>>>(bl, d.qv, start, count, px, py, pz, charges, R, kt,
                                                   (cx<T>*)out, sign, wk);
     else if (std::is_same<T, float>::value && R >= 16)
-        k_s2m<float, 16><<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt,
+        k_s2m<float, 16><<<grid, kS2MThreads, 0, st>>>(bl, d.qv, start, count, px, py, pz, charges, R, kt,
                                                        (cxf*)out, sign, wk);
     else
-        k_s2m<T, 4><<<grid, kS2MThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, charges, R, kt,
+        k_s2m<T, 4><<<grid, kS2MThreads, 0, st>>>(bl, d.qv, start, count, px, py, pz, charges, R, kt,
                                                   (cx<T>*)out, sign, wk);
 }
 
-// signature -> points at the leaf level: L2T (targets, sign +1, weighted) or transposed
-// S2M (sources, sign -1)
+// signature -> points at the leaves of level l: L2T (targets, sign +1, weighted) or
+// transposed S2M (sources, sign -1); adds to the points' values
 template <typename T>
-void launch_l2t(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false) {
-    const int lf = P->hp.lf;
-    DevLevel& d = P->lev[lf];
-    const int32_t* start = transposed ? P->sstart : P->tstart;
-    const int32_t* count = transposed ? P->scount : P->tcount;
+void launch_l2t(hfmm_plan_s* P, int l, int R, cudaStream_t st, bool transposed = false) {
+    DevLevel& d = P->lev[l];
+    if (d.nleaf == 0) return;
+    const int32_t* start = transposed ? d.sstart : d.tstart;
+    const int32_t* count = transposed ? d.scount : d.tcount;
     const double* px = transposed ? P->sx : P->tx;
     const double* py = transposed ? P->sy : P->ty;
     const double* pz = transposed ? P->sz : P->tz;
@@ -1205,13 +1259,15 @@ void launch_l2t(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false)
     const double sign = transposed ? -1.0 : 1.0;
     const double* wk = transposed ? nullptr : d.qv.w;
     const double kt = P->hp.kappa / (2.0 * 3.14159265358979323846);
-    const dim3 grid(d.nbox, nblk(transposed ? P->max_src_leaf : P->max_tgt_leaf, kL2TThreads));
+    BoxView bl = d.bv;
+    bl.leaf = d.leaf;
+    const dim3 grid(d.nleaf, nblk(transposed ? d.max_src : d.max_tgt, kL2TThreads));
+    const int2* units = transposed ? d.sunits : d.tunits;
+    const int nu = transposed ? d.nsunits : d.ntunits;
     if (std::is_same<T, double>::value && P->tab_s) {
-        // float64 leaf with plane-wave tables: L2T reads the targets' table conjugated, the
-        // transposed S2M the sources' table as stored
+        // float64 leaf with plane-wave tables (uniform trees): L2T reads the targets' table
+        // conjugated, the transposed S2M the sources' table as stored
         const cxd* E = transposed ? P->tab_s : P->tab_t;
-        const int2* units = transposed ? P->sunits : P->tunits;
-        const int nu = transposed ? P->nsunits : P->ntunits;
         if (nu > 0) {
             const unsigned th = 32 * kL2TabWarps;
             const cxd* Lin = (const cxd*)in;
@@ -1225,9 +1281,7 @@ void launch_l2t(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false)
         }
         return;
     }
-    if (std::is_same<T, double>::value && use_df(P, lf)) {
-        const int2* units = transposed ? P->sunits : P->tunits;
-        const int nu = transposed ? P->nsunits : P->ntunits;
+    if (std::is_same<T, double>::value && use_df(P, l)) {
         if (nu > 0) {
             if (R == 1)
                 k_l2t_df_warp<1><<<nblk(nu, 4), 128, 0, st>>>(units, nu, d.bv, d.qv, d.sdf, start, count, px, py, pz,
@@ -1239,14 +1293,24 @@ void launch_l2t(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false)
         return;
     }
     if (R == 1)
-        k_l2t<T, 1><<<grid, kL2TThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, (const cx<T>*)in, R, kt,
+        k_l2t<T, 1><<<grid, kL2TThreads, 0, st>>>(bl, d.qv, start, count, px, py, pz, (const cx<T>*)in, R, kt,
                                                   out, sign, wk);
     else if (std::is_same<T, float>::value && R >= 16)
-        k_l2t<float, 16><<<grid, kL2TThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, (const cxf*)in, R, kt,
+        k_l2t<float, 16><<<grid, kL2TThreads, 0, st>>>(bl, d.qv, start, count, px, py, pz, (const cxf*)in, R, kt,
                                                        out, sign, wk);
     else
-        k_l2t<T, 4><<<grid, kL2TThreads, 0, st>>>(d.bv, d.qv, start, count, px, py, pz, (const cx<T>*)in, R, kt,
+        k_l2t<T, 4><<<grid, kL2TThreads, 0, st>>>(bl, d.qv, start, count, px, py, pz, (const cx<T>*)in, R, kt,
                                                   out, sign, wk);
+}
+
+// S2M / L2T of every level that has leaves (a uniform tree: the leaf level only)
+void run_s2m(hfmm_plan_s* P, int l, int R, cudaStream_t st, bool transposed = false) {
+    if (P->lev[l].prec == kFP32) launch_s2m<float>(P, l, R, st, transposed);
+    else launch_s2m<double>(P, l, R, st, transposed);
+}
+void run_l2t(hfmm_plan_s* P, int l, int R, cudaStream_t st, bool transposed = false) {
+    if (P->lev[l].prec == kFP32) launch_l2t<float>(P, l, R, st, transposed);
+    else launch_l2t<double>(P, l, R, st, transposed);
 }
 
 // transposed far field up to (not including) the transposed S2M: conj(w) on the targets
@@ -1254,12 +1318,15 @@ void launch_l2t(hfmm_plan_s* P, int R, cudaStream_t st, bool transposed = false)
 template <typename Mark>
 void transposed_far_chain(hfmm_plan_s* P, int R, cudaStream_t st, Mark mark) {
     const int lf = P->hp.lf;
-    // transposed L2T: weighted plane-wave sums of the targets into Lambda_L at the leaf level
-    if (P->lev[lf].prec == kFP32) launch_s2m<float>(P, R, st, true);
-    else launch_s2m<double>(P, R, st, true);
+    // transposed L2T: weighted plane-wave sums of the targets into Lambda_L at the leaves
+    run_s2m(P, lf, R, st, true);
     mark(3);
-    // transposed L2L, leaf level up to level 2
-    for (int l = lf - 1; l >= 2; --l) run_l2l_t(P, l, R, st);
+    // transposed L2L, leaf level up to level 2 (it writes every parent; the leaves of an
+    // adaptive tree's coarser levels then take their transposed L2T)
+    for (int l = lf - 1; l >= 2; --l) {
+        run_l2l_t(P, l, R, st);
+        run_s2m(P, l, R, st, true);
+    }
     mark(4);
     // transposed M2L: the opposite transfer vectors
     for (int l = 2; l <= lf; ++l) run_m2l(P, l, R, st, true);
@@ -1476,7 +1543,7 @@ hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_d
     else
         k_permute_in<double, false><<<nblk(hp.ns * R, 256), 256, 0, st>>>((const cxd*)q, hp.ns, R, P->src_perm, P->qs);
     mark(1);
-    const int nleaf = (int)hp.levels[lf].nbox();
+    const int nleaf = (int)hp.leaf_level.size();
     const dim3 g_fwd(nleaf, nblk(P->max_tgt_leaf, kP2PThreads));
     const df kt_df = df_from_double(hp.kappa / (2.0 * 3.14159265358979323846));
     if (P->near_prec == kFP32 && P->sym && R == 1) {
@@ -1524,17 +1591,20 @@ hfmm_status hfmm_apply(hfmm_plan_t P, const void* q, void* phi, int nrhs, hfmm_d
     }
     mark(2);
     if (lf >= 2) {
-        if (P->lev[lf].prec == kFP32) launch_s2m<float>(P, R, st);
-        else launch_s2m<double>(P, R, st);
+        run_s2m(P, lf, R, st);
         mark(3);
-        for (int l = lf; l >= 3; --l) run_up(P, l, R, st);
+        // M2M writes every parent; the leaves of an adaptive tree's coarser levels then take
+        // their S2M
+        for (int l = lf; l >= 3; --l) {
+            run_up(P, l, R, st);
+            run_s2m(P, l - 1, R, st);
+        }
         mark(4);
         for (int l = 2; l <= lf; ++l) run_m2l(P, l, R, st, false);
         mark(5);
         for (int l = 2; l < lf; ++l) run_down(P, l, R, st);
         mark(6);
-        if (P->lev[lf].prec == kFP32) launch_l2t<float>(P, R, st);
-        else launch_l2t<double>(P, R, st);
+        for (int l = 2; l <= lf; ++l) run_l2t(P, l, R, st);
         mark(7);
     } else {
         for (int i = 3; i <= 7; ++i) mark(i);
@@ -1571,7 +1641,7 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t P, const void* w, void* out, int nrhs
         k_permute_in<double, true><<<nblk(hp.nt * R, 256), 256, 0, st>>>((const cxd*)w, hp.nt, R, P->tgt_perm, P->phis);
     mark(1);
     // transposed near field: source boxes gather the targets of their neighbours
-    const int nleaf = (int)hp.levels[lf].nbox();
+    const int nleaf = (int)hp.leaf_level.size();
     const dim3 g_adj(nleaf, nblk(P->max_src_leaf, kP2PThreads));
     const df kt_df = df_from_double(hp.kappa / (2.0 * 3.14159265358979323846));
     if (P->near_prec == kFP32 && P->sym && R == 1) {
@@ -1626,9 +1696,8 @@ hfmm_status hfmm_apply_adjoint(hfmm_plan_t P, const void* w, void* out, int nrhs
     mark(2);
     if (lf >= 2) {
         transposed_far_chain(P, R, st, mark);
-        // transposed S2M: plane-wave sums back onto the sources
-        if (P->lev[lf].prec == kFP32) launch_l2t<float>(P, R, st, true);
-        else launch_l2t<double>(P, R, st, true);
+        // transposed S2M: plane-wave sums back onto the sources of every level's leaves
+        for (int l = 2; l <= lf; ++l) run_l2t(P, l, R, st, true);
         mark(7);
     } else {
         for (int i = 3; i <= 7; ++i) mark(i);
@@ -1666,25 +1735,32 @@ hfmm_status hfmm_grad_sources(hfmm_plan_t P, const void* q, const void* g, doubl
         k_permute_in<double, true><<<nblk(hp.nt * R, 256), 256, 0, st>>>((const cxd*)g, hp.nt, R, P->tgt_perm, P->phis);
     }
     mark(1);
-    const int nleaf = (int)hp.levels[lf].nbox();
+    const int nleaf = (int)hp.leaf_level.size();
     k_grad_near<<<dim3(nleaf, nblk(P->max_src_leaf, kP2PThreads)), kP2PThreads, 0, st>>>(nleaf, P->sstart, P->scount, P->tstart, P->tcount, P->noff, P->nidx,
                                                P->sx, P->sy, P->sz, P->tx, P->ty, P->tz, P->qs, P->phis, R,
                                                hp.kappa, P->gsort);
     mark(2);
     if (lf >= 2) {
         transposed_far_chain(P, R, st, mark);
-        DevLevel& d = P->lev[lf];
-        const dim3 gg(d.nbox, nblk(P->max_src_leaf, kL2TThreads));
-        const int sc = store_code(P, lf);
-        if (sc == 1)
-            k_grad_far<double, double><<<gg, kL2TThreads, 0, st>>>(d.bv, d.qv, P->sstart, P->scount, P->sx, P->sy,
-                                                                   P->sz, (const cxd*)d.M, P->qs, R, hp.kappa, P->gsort);
-        else if (sc == 2)
-            k_grad_far<df, double><<<gg, kL2TThreads, 0, st>>>(d.bv, d.qv, P->sstart, P->scount, P->sx, P->sy,
-                                                               P->sz, (const cx<df>*)d.M, P->qs, R, hp.kappa, P->gsort);
-        else
-            k_grad_far<float, float><<<gg, kL2TThreads, 0, st>>>(d.bv, d.qv, P->sstart, P->scount, P->sx, P->sy,
-                                                                 P->sz, (const cxf*)d.M, P->qs, R, hp.kappa, P->gsort);
+        for (int l = 2; l <= lf; ++l) {
+            DevLevel& d = P->lev[l];
+            if (d.nleaf == 0) continue;
+            BoxView bl = d.bv;
+            bl.leaf = d.leaf;
+            const dim3 gg(d.nleaf, nblk(d.max_src, kL2TThreads));
+            const int sc = store_code(P, l);
+            if (sc == 1)
+                k_grad_far<double, double><<<gg, kL2TThreads, 0, st>>>(bl, d.qv, d.sstart, d.scount, P->sx, P->sy,
+                                                                       P->sz, (const cxd*)d.M, P->qs, R, hp.kappa,
+                                                                       P->gsort);
+            else if (sc == 2)
+                k_grad_far<df, double><<<gg, kL2TThreads, 0, st>>>(bl, d.qv, d.sstart, d.scount, P->sx, P->sy, P->sz,
+                                                                   (const cx<df>*)d.M, P->qs, R, hp.kappa, P->gsort);
+            else
+                k_grad_far<float, float><<<gg, kL2TThreads, 0, st>>>(bl, d.qv, d.sstart, d.scount, P->sx, P->sy,
+                                                                     P->sz, (const cxf*)d.M, P->qs, R, hp.kappa,
+                                                                     P->gsort);
+        }
         mark(7);
     } else {
         for (int i = 3; i <= 7; ++i) mark(i);

@@ -38,6 +38,9 @@ struct BoxView {
     const int32_t* parent;
     const int32_t* child_start;
     const int32_t* child_count;
+    // S2M / L2T / far gradient of an adaptive tree: block x works on box leaf[x] (the level's
+    // leaves); null: on box x
+    const int32_t* leaf = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -244,7 +247,7 @@ __global__ void k_s2m(BoxView bx, QuadView qv, const int32_t* __restrict__ sstar
     __shared__ double shd[kS2MThreads * 3];
     __shared__ float shf[kS2MThreads * 6];
     __shared__ cx<R> shq[kS2MThreads * kRC];
-    const int b = blockIdx.x;
+    const int b = bx.leaf ? bx.leaf[blockIdx.x] : (int)blockIdx.x;
     const int64_t p = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
     const bool active = p < qv.npair;
     int2 kk2 = make_int2(0, 0);
@@ -332,7 +335,7 @@ __global__ void k_l2t(BoxView bx, QuadView qv, const int32_t* __restrict__ tstar
     __shared__ double shs[kL2TThreads * 3];
     __shared__ float shf[kL2TThreads * 6];
     __shared__ cx<R> shp[kL2TThreads * kRC], shq[kL2TThreads * kRC];
-    const int b = blockIdx.x;
+    const int b = bx.leaf ? bx.leaf[blockIdx.x] : (int)blockIdx.x;
     const int t0 = tstart[b], tc = tcount[b];
     if ((int)blockIdx.y * kL2TThreads >= tc) return;
     const double cxx = bx.center[3 * b], cyy = bx.center[3 * b + 1], czz = bx.center[3 * b + 2];
@@ -572,7 +575,7 @@ __global__ void k_s2m_df(BoxView bx, QuadView qv, const int32_t* __restrict__ ss
     __shared__ cdf shq[kS2MTile * kRC];
     __shared__ cdf tab[kCisTableBig];
     for (int v = threadIdx.x; v < kCisTableBig; v += blockDim.x) tab[v] = cis_tab[v];
-    const int b = blockIdx.x;
+    const int b = bx.leaf ? bx.leaf[blockIdx.x] : (int)blockIdx.x;
     const int64_t p = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;   // antipodal pair
     const bool active = p < qv.npair;
     int2 kk2 = make_int2(0, 0);
@@ -1224,7 +1227,7 @@ __global__ void k_grad_far(BoxView bx, QuadView qv, const int32_t* __restrict__ 
                            double* __restrict__ grad) {
     __shared__ double shs[kL2TThreads * 3];
     __shared__ cx<R> shl[kL2TThreads];
-    const int b = blockIdx.x;
+    const int b = bx.leaf ? bx.leaf[blockIdx.x] : (int)blockIdx.x;
     const int s0 = sstart[b], sc = scount[b];
     if ((int)blockIdx.y * kL2TThreads >= sc) return;
     const double kt = kappa / (2.0 * 3.14159265358979323846);
