@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the extra workloads")
     ap.add_argument("--cube-only", type=int, default=0, metavar="N",
                     help="time only the 64-RHS cube workload on its first N points and print its line (profiling runs)")
+    ap.add_argument("--adaptive-only", action="store_true",
+                    help="time only the adaptive-tree comparisons and print their line (profiling runs)")
     ap.add_argument("--buffer", type=int, default=0, choices=[0, 1, 2],
                     help="plan shape of the measured plans: 0 tuned (default), 1 or 2 buffer boxes (profiling runs)")
     return ap.parse_args()
@@ -459,6 +461,37 @@ def cube_run(timer, dev, n=524288):
     return res
 
 
+def adaptive_run(timer, dev, steps):
+    """Adaptive octree (HFMM_FLAG_ADAPTIVE, max_leaf 64) against the uniform tree, both with the
+    tuned plan shape, mixed policy, eps 1e-4, one right-hand side: the clustered cloud
+    (1,048,576 points in 16 dense small cubes plus 10% uniform, kappa 72.5) and the headline
+    ellipsoid.  Time per apply, stage times, leaves per level, near-field pairs, boxes, and the
+    error against the float64 direct sum on 500 seeded targets."""
+    import torch
+    from paper_0911_4114_gb300 import FmmPlan, workloads as wl
+    out = {}
+    for name, kappa in (("clusters1m", 72.5), ("ellipsoid2m", 200.0)):
+        s, t = wl.points(name)
+        qh = wl.charges(len(s), 0, wl.rng(6, salt=1)).astype(np.complex64)
+        q = torch.as_tensor(qh).reshape(-1, 1).to(dev)
+        o = torch.empty((len(t), 1), dtype=torch.complex64, device=dev)
+        idx = np.sort(np.random.default_rng(20260105).choice(len(t), 500, replace=False))
+        ref = gpu_direct_reference(s, t[idx], qh.astype(np.complex128), kappa, dev)
+        res = {"points": len(t), "kappa": kappa, "eps": 1e-4, "unit": "Mpoints*RHS/s"}
+        for tree in ("uniform", "adaptive"):
+            p = FmmPlan(s, t, kappa, 1e-4, precision="mixed", max_leaf=64, adaptive=tree == "adaptive", **AUTO)
+            ms = timer.run(lambda: p.apply(q, out=o), max(3, steps // 2), 2)
+            err = rel(o[:, 0].cpu().numpy().astype(np.complex128)[idx], ref)
+            i = p.info()
+            res[tree] = {"ms_per_step": ms, "value": len(t) / (ms * 1e-3) / 1e6, "rel_err": err, "lf": i["lf"],
+                         "buffer": i["buffer"], "p2p_pairs": i["p2p_pairs"], "nbox": i["nbox"],
+                         "leaves": {str(l): n for l, n in enumerate(i["level_nleaf"]) if n},
+                         "stage_ms": timer.stages(p, lambda: p.apply(q, out=o), 1)}
+            del p
+        out[name] = res
+    return out
+
+
 def extras_run(timer, dev, steps):
     """Device-timed extra workloads: the sphere, the 64-RHS cube and the 32-problem batch."""
     import torch
@@ -495,6 +528,8 @@ def extras_run(timer, dev, steps):
                            "problems": 32, "points_total": npts, "nrhs": 4, "eps": 1e-5,
                            "launch": "one cudaGraphLaunch per apply (hfmm_apply_batch replay)"}
     del batch
+    # adaptive against uniform trees
+    out["adaptive_tree"] = adaptive_run(timer, dev, steps)
     return out
 
 
@@ -513,6 +548,10 @@ def main():
     if args.cube_only:
         if rank == 0:
             print(json.dumps(dict(cube_run(Timer(dev, world), dev, args.cube_only), workload="cube_rhs64")))
+        return
+    if args.adaptive_only:
+        if rank == 0:
+            print(json.dumps(dict(adaptive_run(Timer(dev, world), dev, args.steps), workload="adaptive_tree")))
         return
     s, t, q_host = headline_points(args.points if args.points != 2097152 else None)
     kappa, eps = HEADLINE["kappa"], HEADLINE["eps"]

@@ -36,6 +36,21 @@ def ellipsoid(n, g, axes=(1.0, 0.5, 0.25)):
     return out[:n]
 
 
+def clusters(n, g, nclusters=16, background=0.1):
+    """Strongly clustered cloud in [0, 1]^3: a fraction `background` uniform in the cube, the
+    rest split evenly over `nclusters` small cubes (sides uniform in [0.02, 0.08], centres
+    uniform in [0.1, 0.9]^3): densities differ by three to four orders of magnitude."""
+    nb = int(round(background * n))
+    parts = [cube(nb, g)]
+    sizes = np.full(nclusters, (n - nb) // nclusters)
+    sizes[: (n - nb) - int(sizes.sum())] += 1
+    for m in sizes:
+        c = g.uniform(0.1, 0.9, 3)
+        h = g.uniform(0.02, 0.08)
+        parts.append(c + h * (g.random((int(m), 3)) - 0.5))
+    return np.concatenate(parts)
+
+
 def charges(n, nrhs, g):
     """complex charges, re and im i.i.d. N(0,1), shape (n, nrhs) (or (n,) for nrhs=0)."""
     shape = (n,) if nrhs == 0 else (n, nrhs)
@@ -49,6 +64,7 @@ WORKLOADS = {
     "ellipsoid2m": 2,       # 2,097,152 on the (1, .5, .25) ellipsoid, kappa 200
     "cube512k_rhs64": 3,    # 524,288 uniform cube, kappa 40, 64 RHS, eps 1e-5
     "spheres131k_grad": 4,  # 131,072 on r=1 (sources) and r=1.5 (targets), kappa 32
+    "clusters1m": 5,        # 1,048,576 in 16 dense small cubes + 10% uniform, kappa 72.5
 }
 
 
@@ -66,6 +82,9 @@ def points(name, n=None):
         return x, x
     if name == "cube512k_rhs64":
         x = cube(n or 524288, g)
+        return x, x
+    if name == "clusters1m":
+        x = clusters(n or 1048576, g)
         return x, x
     if name == "spheres131k_grad":
         s = sphere(n or 131072, g)
