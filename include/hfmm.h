@@ -115,8 +115,11 @@ typedef struct {
  * per-row anterpolation of Section 3.3.2 in float64 and agree to round-off. */
 #define HFMM_FLAG_HOST_TABLES 2
 /* hfmm_options.flags: adaptive octree.  A box above the leaf level lf splits only when it
- * lies above level 2 or holds more than max_leaf sources or more than max_leaf targets, so
- * leaves lie on several levels (Section 2's tree, refined only where the points are dense).
+ * lies above level 2, holds more than max_leaf sources or more than max_leaf targets, or is
+ * crowded (it holds a point and the other cubes of its level within Chebyshev distance
+ * `buffer` hold more than (2 buffer + 1)^3 max_leaf sources or targets), so leaves lie on
+ * several levels (Section 2's tree, refined only where the points are dense) and no leaf
+ * interacts directly with more points than a leaf of a uniform tree at max_leaf per box.
  * S2M and L2T run for the leaves of each level at that level's quadrature; M2L stays between
  * boxes of one level (Section 3's diagonal transfer, unchanged); a target leaf B and a source
  * leaf C interact directly when their ancestors at level min(l_B, l_C) are neighbours.  The

@@ -18,8 +18,12 @@ for bit:
 * box centre c = corner + (idx + 1/2) * (side / 2^l), box size a_l = side / 2^l;
 * only boxes holding at least one source or target exist (sparse, level uniform);
 * adaptive trees (max_leaf given): a box of level l < depth is split into its
-  children only when l < 2 (the far field starts at level 2) or it holds more than
-  max_leaf sources or more than max_leaf targets; the other boxes are leaves, so
+  children only when l < 2 (the far field starts at level 2), when it holds more than
+  max_leaf sources or more than max_leaf targets, or when it is crowded: it holds a
+  point and the other cubes of level l within Chebyshev distance b of it (occupied or
+  not by boxes of the tree) hold more than (2b+1)^3 max_leaf sources or more than that
+  many targets -- a leaf then never interacts directly with more points than a leaf of
+  a uniform tree at max_leaf points per box would.  The other boxes are leaves, so
   leaves lie on several levels and no box exists below a leaf.  A target leaf B
   and a source leaf C interact directly (P2P) when their ancestors at the coarser
   of their two levels, m = min(l_B, l_C), are neighbours; otherwise the ancestors
@@ -185,7 +189,8 @@ class Tree:
             t0 = np.searchsorted(tkey_sorted >> sh, keys_l, side='left')
             tc = np.searchsorted(tkey_sorted >> sh, keys_l, side='right') - t0
             if adaptive:
-                split = (l < D) & ((l < 2) | (sc > self.max_leaf) | (tc > self.max_leaf))
+                crowd = self._crowded(idx, sc + tc, skey_sorted >> sh, tkey_sorted >> sh, l)
+                split = (l < D) & ((l < 2) | (sc > self.max_leaf) | (tc > self.max_leaf) | crowd)
             else:
                 split = np.full(len(keys_l), l < D)
             self.levels.append({'idx': idx, 'key': keys_l, 'center': center,
@@ -221,6 +226,29 @@ class Tree:
             self.nlist = _PerBox(len(self.leaf_level), self._adaptive_neighbours)
         else:
             self.nlist = _PerBox(len(self.levels[D]['key']), lambda a: self._neighbour_list(D, a))
+
+    def _crowded(self, idx, count, skeys, tkeys, l):
+        """Per box: holds a point and the other level-l cubes within Chebyshev distance b hold
+        more than (2b+1)^3 max_leaf sources or targets (skeys, tkeys: sorted level-l keys of
+        all sources and targets)."""
+        bw, nb = self.buffer, 2 ** l
+        lim = (2 * bw + 1) ** 3 * self.max_leaf
+
+        def points_in(keys, sorted_keys):
+            return np.searchsorted(sorted_keys, keys, side='right') - np.searchsorted(sorted_keys, keys, side='left')
+
+        cs = np.zeros(len(idx), dtype=np.int64)
+        ct = np.zeros(len(idx), dtype=np.int64)
+        for d in np.ndindex(2 * bw + 1, 2 * bw + 1, 2 * bw + 1):
+            off = np.array(d) - bw
+            if not off.any():
+                continue
+            c = idx + off
+            inside = np.all((c >= 0) & (c < nb), axis=1)
+            k = morton_key(np.clip(c, 0, nb - 1), l)
+            cs += np.where(inside, points_in(k, skeys), 0)
+            ct += np.where(inside, points_in(k, tkeys), 0)
+        return (count > 0) & ((cs > lim) | (ct > lim))
 
     def _adaptive_neighbours(self, g):
         """Leaves C whose ancestor at level min(l_B, l_C) neighbours leaf g's ancestor there."""

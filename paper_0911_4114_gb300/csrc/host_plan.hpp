@@ -64,8 +64,10 @@ struct HostPlan {
     std::vector<double> alphas;
     double eps_scale = 0.25;
     int max_leaf = 64, depth_req = 0, precision = 0;
-    // adaptive tree: a box above the depth splits only when it lies above level 2 or holds
-    // more than max_leaf sources or targets, so leaves lie on several levels; 0 = level uniform
+    // adaptive tree: a box above the depth splits only when it lies above level 2, holds more
+    // than max_leaf sources or targets, or is crowded (the other cubes of its level within
+    // Chebyshev distance buffer hold more than (2 buffer + 1)^3 max_leaf sources or targets),
+    // so leaves lie on several levels; 0 = level uniform
     int adaptive = 0;
     bool host_tables = true;   // false: T^{s,LL} is computed on the device at upload
     int buffer = 1;      // buffer boxes between a box and its interaction list (Section 3.3.3);

@@ -601,9 +601,33 @@ static void build_tree(HostPlan& hp) {
             };
             sub(ks, hp.src_perm, lks, L.s_start, L.s_count);
             sub(kt, hp.tgt_perm, lkt, L.t_start, L.t_count);
+            // split: above level 2, more than max_leaf sources or targets, or crowded (the
+            // other level-l cubes within Chebyshev distance buffer hold more than
+            // (2 buffer + 1)^3 max_leaf sources or targets)
+            const int bw = hp.buffer, n1 = 1 << l;
+            const int64_t lim = (int64_t)(2 * bw + 1) * (2 * bw + 1) * (2 * bw + 1) * hp.max_leaf;
             L.split.assign(nb, 0);
-            for (int64_t b = 0; b < nb; ++b)
-                L.split[b] = l < D && (l < 2 || L.s_count[b] > hp.max_leaf || L.t_count[b] > hp.max_leaf);
+#pragma omp parallel for schedule(static)
+            for (int64_t b = 0; b < nb; ++b) {
+                bool sp = l < 2 || L.s_count[b] > hp.max_leaf || L.t_count[b] > hp.max_leaf;
+                if (!sp && l < D && L.s_count[b] + L.t_count[b] > 0) {
+                    const int32_t* ib = &L.idx[3 * b];
+                    int64_t cs = 0, ct = 0;
+                    for (int dx = -bw; dx <= bw; ++dx)
+                        for (int dy = -bw; dy <= bw; ++dy)
+                            for (int dz = -bw; dz <= bw; ++dz) {
+                                const int c[3] = {ib[0] + dx, ib[1] + dy, ib[2] + dz};
+                                if ((dx | dy | dz) == 0 || c[0] < 0 || c[1] < 0 || c[2] < 0 || c[0] >= n1 ||
+                                    c[1] >= n1 || c[2] >= n1)
+                                    continue;
+                                const uint64_t k = morton(c[0], c[1], c[2], l);
+                                cs += std::upper_bound(lks.begin(), lks.end(), k) - std::lower_bound(lks.begin(), lks.end(), k);
+                                ct += std::upper_bound(lkt.begin(), lkt.end(), k) - std::lower_bound(lkt.begin(), lkt.end(), k);
+                            }
+                    sp = cs > lim || ct > lim;
+                }
+                L.split[b] = l < D && sp;
+            }
         } else {
             L.split.assign(nb, l < D ? 1 : 0);
         }

@@ -50,9 +50,10 @@ class FmmPlan:
     host_tables: compute the transfer tables on the host (default: on the device when there is one).
     buffer: buffer boxes between a box and its interaction list, 1 or 2 (Section 3.3.3), or 0:
     chosen with the leaf level by the plan's cost model (the "auto" plan shape).
-    adaptive: adaptive octree -- boxes split only where they hold more than max_leaf sources
-    or targets, so leaves lie on several levels (S2M / L2T per leaf level, same-level M2L,
-    direct interaction between leaves whose ancestors at the coarser leaf level neighbour).
+    adaptive: adaptive octree -- boxes split only where they or their neighbourhood hold more
+    than max_leaf points per box, so leaves lie on several levels (S2M / L2T per leaf level,
+    same-level M2L, direct interaction between leaves whose ancestors at the coarser leaf level
+    neighbour).
     """
 
     def __init__(self, sources, targets, kappa, eps, precision="fp64", alphas=None,

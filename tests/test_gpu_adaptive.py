@@ -61,7 +61,7 @@ CASES = {
     "tc5_r20": ("cube+cluster", 60.0, 1e-5, 20, 1, 64, True),
     "df_near": ("sphere+cluster", 50.0, 1e-7, 1, 2, 32, True),
     "src_tgt": ("cube+cluster", 60.0, 1e-6, 3, 1, 32, False),
-    "tuned": ("sphere+cluster", 100.0, 1e-4, 1, 0, 48, True),
+    "tuned": ("clusters", 40.0, 1e-4, 1, 0, 64, True),
 }
 
 
@@ -69,6 +69,8 @@ def _cloud(name, g):
     kind = CASES[name][0]
     if kind == "cube+cluster":
         x = _clustered(2000, 22000, g, side=0.3)
+    elif kind == "clusters":
+        x = wl.clusters(80000, g)
     else:
         x = np.concatenate([0.5 + 0.5 * wl.sphere(15000, g),
                             np.array([0.45, 0.5, 0.55]) + 0.04 * (g.random((10000, 3)) - 0.5)])

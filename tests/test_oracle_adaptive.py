@@ -6,8 +6,10 @@
   level-l ancestor -- counted by walking both ancestor chains, independently of how the
   lists were built;
 * the leaves partition the points and each point lies inside its leaf's cube;
-* the split rule: a box has children iff it is above level 2 or holds more than max_leaf
-  sources or targets (and is above the depth);
+* the split rule: a box has children iff it is above the depth and above level 2, holds
+  more than max_leaf sources or targets, or holds a point while the other cubes of its level
+  within Chebyshev distance b hold more than (2b+1)^3 max_leaf sources or targets (counted
+  here from the point coordinates);
 * max_leaf = 0 splits every box: the tree, lists and ranges equal the uniform tree's;
 * the adaptive FMM on strongly clustered clouds matches the float64 direct sum within eps.
 """
@@ -70,12 +72,24 @@ def test_leaves_partition_points_and_follow_the_split_rule():
         lo = t.corner + t.levels[l]['idx'][b] * h
         p = xs[t.src_start[a]:t.src_start[a] + t.src_count[a]]
         assert np.all(p >= lo - 1e-12) and np.all(p <= lo + h + 1e-12)
+    lim = 27 * max_leaf
+    crowd_only = 0          # boxes split only because they are crowded
     for l, L in enumerate(t.levels):
         big = (L['src_count'] > max_leaf) | (L['tgt_count'] > max_leaf)
-        assert np.array_equal(L['split'], (l < t.depth) & ((l < 2) | big))
+        # points in the other cubes within Chebyshev distance 1, from the coordinates
+        pc = np.clip(np.floor((x - t.corner) * (2 ** l / t.side)), 0, 2 ** l - 1).astype(np.int64)
+        crowd = np.zeros(len(L['key']), dtype=bool)
+        for b in range(len(L['key'])):
+            cheb = np.max(np.abs(pc - L['idx'][b]), axis=1)
+            around = int(np.count_nonzero((cheb >= 1) & (cheb <= 1)))
+            crowd[b] = L['src_count'][b] + L['tgt_count'][b] > 0 and around > lim
+        assert np.array_equal(L['split'], (l < t.depth) & ((l < 2) | big | crowd)), l
+        if 2 <= l < t.depth:
+            crowd_only += int(np.count_nonzero(crowd & ~big))
         if l > 0:   # boxes exist only below split boxes
             assert np.all(t.levels[l - 1]['split'][L['parent']])
             assert np.all(L['src_count'] + L['tgt_count'] > 0)
+    assert crowd_only > 0
 
 
 def test_max_leaf_zero_is_the_uniform_tree():
