@@ -71,7 +71,8 @@ typedef struct {
     /* per-level target eps_l = eps_scale * eps (default 0.25) */
     double eps_scale;
     /* the tree depth never exceeds the smallest depth at which no box holds more
-     * than max_leaf sources or max_leaf targets (default 64) */
+     * than max_leaf sources or max_leaf targets (default 64); with HFMM_FLAG_ADAPTIVE it
+     * also decides which boxes split */
     int max_leaf;
     /* > 0: requested depth (replaces the max_leaf rule; active levels may still stop
      * earlier where the stability rule rejects a level).  0 = use max_leaf. */
@@ -180,7 +181,8 @@ void hfmm_default_options(hfmm_options* opt);
 /* Plan stage (host, float64; Sections 2.1, 3.3, 3.4 and the tree of Section 2).
  * sources: host (ns, 3) float64, ns >= 1.  targets: host (nt, 3) float64, nt >= 1; it
  * may be the same pointer as sources.  kappa > 0; 0 < eps <= 0.1.  opt may be NULL.
- * Builds the octree, the interaction and neighbour lists, the per-level truncation
+ * Builds the octree (level uniform, or adaptive with HFMM_FLAG_ADAPTIVE), the interaction
+ * lists and the leaves' near lists, the per-level truncation
  * (Eq. EBF refined by Eq. CollinoError), N_theta (Algorithm Ntheta), N_phi(theta_n)
  * (Algorithm Nphi) and the T^{s,LL} tables of the vectors the lists use (Algorithm BMTF;
  * canonical vectors computed, reflected into the others), copies the points, and (device >= 0) uploads everything and allocates the apply
