@@ -41,10 +41,62 @@ def test_adaptive_host_plan_bit_exact(kind, kappa, eps, buffer, max_leaf):
     s, t = _cloud(kind, g)
     lib = FmmPlan(s, t, kappa, eps, precision="mixed", max_leaf=max_leaf, buffer=buffer, device=-1, adaptive=True)
     orc = ofmm.Plan(s, t, kappa, eps, precision="mixed", max_leaf=max_leaf, buffer=buffer, adaptive=True)
+    assert len(set(orc.tree.leaf_level.tolist())) >= 2
+    assert_same_plan(lib, orc)
+
+
+def _covered_once(tr):
+    """Every (target leaf, source leaf) pair holding points is covered exactly once: directly or
+    by M2L at one level of the two ancestor chains."""
+    where = [{tuple(int(c) for c in L['idx'][i]): i for i in range(len(L['key']))} for L in tr.levels]
+    anc = []
+    for l, b in zip(tr.leaf_level, tr.leaf_box):
+        i = tr.levels[l]['idx'][b]
+        anc.append({m: where[m][tuple(int(c) for c in (i >> (l - m)))] for m in range(2, int(l) + 1)})
+    for a in range(len(tr.leaf_level)):
+        near = set(tr.nlist[a].tolist())
+        for c in range(len(tr.leaf_level)):
+            if tr.tgt_count[a] == 0 or tr.src_count[c] == 0:
+                continue
+            m = min(int(tr.leaf_level[a]), int(tr.leaf_level[c]))
+            m2l = sum(anc[c][l] in set(tr.ilist[l][anc[a][l]].tolist()) for l in range(2, m + 1))
+            assert (c in near) + m2l == 1, (a, c)
+
+
+def _line(n, g):
+    x = np.zeros((n, 3))
+    x[:, 0] = g.random(n)
+    return x
+
+
+EDGES = {
+    # name: (sources, targets, kappa, eps, buffer, max_leaf)
+    "coincident": (lambda g: (np.full((300, 3), 0.25), np.full((300, 3), 0.25)), 30.0, 1e-5, 1, 16),
+    "one_point": (lambda g: (np.array([[0.1, 0.2, 0.3]]), np.array([[0.1, 0.2, 0.3]])), 30.0, 1e-5, 1, 16),
+    "disjoint_corners": (lambda g: (0.1 * g.random((1500, 3)), 0.9 + 0.1 * g.random((1200, 3))), 80.0, 1e-5, 2, 16),
+    "line": (lambda g: (_line(2000, g), _line(2000, g)), 60.0, 1e-5, 1, 8),
+    "cluster_max_leaf_1": (lambda g: (np.concatenate([g.random((200, 3)), 0.5 + 0.01 * g.random((300, 3))]),) * 2,
+                           40.0, 1e-4, 2, 1),
+}
+
+
+@pytest.mark.parametrize("name", sorted(EDGES))
+def test_adaptive_edge_cases(name):
+    make, kappa, eps, buffer, max_leaf = EDGES[name]
+    s, t = make(wl.rng(83, salt=sorted(EDGES).index(name)))
+    lib = FmmPlan(s, t, kappa, eps, precision="mixed", max_leaf=max_leaf, buffer=buffer, device=-1, adaptive=True)
+    orc = ofmm.Plan(s, t, kappa, eps, precision="mixed", max_leaf=max_leaf, buffer=buffer, adaptive=True)
+    assert_same_plan(lib, orc)
+    tr = orc.tree
+    assert tr.src_count.sum() == len(s) and tr.tgt_count.sum() == len(t)
+    _covered_once(tr)
+
+
+def assert_same_plan(lib, orc):
+    """Library host plan and oracle plan agree bit for bit (tree, leaves, lists, integers)."""
     tr = orc.tree
     inf = lib.info()
     assert inf["adaptive"] and inf["lf"] == orc.lf == tr.depth and inf["occupancy_depth"] == orc.occupancy_depth
-    assert len(set(tr.leaf_level.tolist())) >= 2
     assert np.array_equal(lib.debug_get("SRC_PERM"), tr.src_perm)
     assert np.array_equal(lib.debug_get("TGT_PERM"), tr.tgt_perm)
     for l in range(tr.depth + 1):
