@@ -9,6 +9,8 @@ plan integers (active levels, l, N_theta, N_phi(theta_n), K, alpha, level precis
 identical.  The plans the benchmark runs with the plan-shape tuner (buffer = 0) are compared
 the same way against the oracle planned with the tuner's choice (buffer, depth = lf), the
 interaction and neighbour lists of two-buffer-box trees on a Morton-strided sample of boxes.
+The adaptive plans of the benchmark (the clustered 1M-point cloud and the ellipsoid) are
+compared with the oracle's adaptive tree in the same way.
 """
 import functools
 
@@ -126,3 +128,48 @@ def test_tuned_fullsize_plan_bit_exact(cfg):
         assert np.array_equal(idx[off[a]:off[a + 1]], tr.nlist[a]), (name, a)
     ls = lib.debug_get("LEAF_SRC")
     assert np.array_equal(ls[:, 1], tr.src_count)
+
+
+ADAPTIVE = [
+    ("clusters1m", 72.5, 1e-4),
+    ("ellipsoid2m", 200.0, 1e-4),
+]
+
+
+@pytest.mark.parametrize("cfg", ADAPTIVE, ids=[f"{c[0]}-adaptive" for c in ADAPTIVE])
+def test_adaptive_fullsize_plan_bit_exact(cfg):
+    """The adaptive plans the benchmark runs (tuned shape, max_leaf 64) against the oracle's
+    adaptive tree planned with the tuner's choice: permutations, boxes and parents of every
+    level, the leaves (level, position, point ranges), and the interaction and near lists on a
+    Morton-strided sample."""
+    name, kappa, eps = cfg
+    s, t = _points(name)
+    lib = FmmPlan(s, t, kappa, eps, precision="mixed", device=-1, buffer=0, max_leaf=64, adaptive=True)
+    info = lib.info()
+    assert info["adaptive"] and info["tuned"]
+    orc = ofmm.Plan(s, t, kappa, eps, precision="mixed", buffer=info["buffer"], depth=info["lf"], max_leaf=64,
+                    adaptive=True)
+    tr = orc.tree
+    assert info["lf"] == orc.lf == tr.depth
+    assert np.array_equal(lib.debug_get("SRC_PERM"), tr.src_perm)
+    assert np.array_equal(lib.debug_get("TGT_PERM"), tr.tgt_perm)
+    for l in range(tr.depth + 1):
+        assert np.array_equal(lib.debug_get("BOX_IDX", l), tr.levels[l]["idx"]), (name, l)
+        if l > 0:
+            assert np.array_equal(lib.debug_get("BOX_PARENT", l), tr.levels[l]["parent"]), (name, l)
+        assert info["level_nleaf"][l] == int(tr.levels[l]["leaf"].sum()), (name, l)
+    lb = lib.debug_get("LEAF_BOX")
+    assert np.array_equal(lb[:, 0], tr.leaf_level) and np.array_equal(lb[:, 1], tr.leaf_box)
+    ls, lt = lib.debug_get("LEAF_SRC"), lib.debug_get("LEAF_TGT")
+    assert np.array_equal(ls[:, 0], tr.src_start) and np.array_equal(ls[:, 1], tr.src_count)
+    assert np.array_equal(lt[:, 0], tr.tgt_start) and np.array_equal(lt[:, 1], tr.tgt_count)
+    for l in range(2, tr.depth + 1):
+        off, idx, v = (lib.debug_get(k, l) for k in ("ILIST_OFF", "ILIST_IDX", "ILIST_V"))
+        n = len(tr.levels[l]["key"])
+        for a in range(0, n, max(1, n // 200)):
+            assert np.array_equal(idx[off[a]:off[a + 1]], tr.ilist[l][a]), (name, l, a)
+            assert np.array_equal(v[off[a]:off[a + 1]], tr.vlist[l][a]), (name, l, a)
+    off, idx = lib.debug_get("NLIST_OFF"), lib.debug_get("NLIST_IDX")
+    n = len(tr.nlist)
+    for a in range(0, n, max(1, n // 200)):
+        assert np.array_equal(idx[off[a]:off[a + 1]], tr.nlist[a]), (name, a)
