@@ -102,7 +102,9 @@ typedef struct {
      * level) that minimise a cost model of one apply (near-field pairs, plane-wave products,
      * interaction-list entries and re-quadrature samples weighed with per-unit times measured
      * on a GB300, for max_rhs right-hand sides); hfmm_query reports the choice and the
-     * predicted times.  The tuned plan equals the plan with that buffer and depth = lf. */
+     * predicted times.  The tuned plan equals the plan with that buffer and depth = lf.  With
+     * HFMM_FLAG_ADAPTIVE the adaptive trees at the uniform model's leaf level and one level
+     * deeper are built and costed, and the cheaper is kept. */
     int buffer;
 } hfmm_options;
 

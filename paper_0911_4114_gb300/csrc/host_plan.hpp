@@ -86,6 +86,7 @@ struct HostPlan {
     // tree
     double corner[3] = {0, 0, 0}, side = 1;
     int occ_depth = 0;   // depth bound (max_leaf rule or requested depth)
+    int tree_ready = 0;  // the tuner already built the tree of the chosen shape (adaptive trees)
     int lf = 0;          // deepest active level (tree depth used by the apply)
     std::vector<int64_t> src_perm, tgt_perm;
     std::vector<TreeLevel> levels;                  // 0..lf

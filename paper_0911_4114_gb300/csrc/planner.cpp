@@ -913,6 +913,69 @@ void for_neighbours(const std::vector<uint64_t>& keys, int l, int bw, F f) {
 
 }  // namespace
 
+// Predicted apply time (s) of the adaptive tree with b buffer boxes and leaf level L: the tree,
+// its near lists and interaction lists are built as for the apply; near-field pairs, leaf
+// plane-wave products per leaf level, list entries and re-quadrature samples are weighed as in
+// the uniform model (no float64 leaf tables: adaptive plans do not build them).
+static double adaptive_cost(const HostPlan& hp, const std::vector<LevelPlan>& lps, int b, int L, const UnitCost& uc,
+                            HostPlan& t) {
+    t = HostPlan();
+    t.src = hp.src;
+    t.tgt = hp.tgt;
+    t.ns = hp.ns;
+    t.nt = hp.nt;
+    t.max_leaf = hp.max_leaf;
+    t.adaptive = 1;
+    t.buffer = b;
+    t.lf = L;
+    for (int k = 0; k < 3; ++k) t.corner[k] = hp.corner[k];
+    t.side = hp.side;
+    build_tree(t);
+    const double R = hp.model_rhs;
+    const double g4 = std::ceil(R / 4.0);
+    double pairs = 0.0, unit_tiles = 0.0;
+    const double boxpairs = (double)t.nidx.size();
+    for (size_t g = 0; g < t.leaf_level.size(); ++g) {
+        double tl = 0.0;
+        for (int32_t k = t.noff[g]; k < t.noff[g + 1]; ++k) {
+            pairs += (double)t.tgt_count[g] * (double)t.src_count[t.nidx[k]];
+            tl += (double)((t.src_count[t.nidx[k]] + 15) / 16);
+        }
+        unit_tiles += (double)((t.tgt_count[g] + 127) / 128) * tl;
+    }
+    double c = 0.0;
+    if (hp.model_near == kFP32) {
+        if (hp.model_sym && R == 1) c += pairs * uc.near_f32_sym + boxpairs * uc.near_f32_boxpair;
+        else if (R >= 16) c += unit_tiles * std::ceil(R / 64.0) * uc.near_tc5;
+        else if (R >= 8) c += pairs * R * uc.near_tc;
+        else c += pairs * g4 * uc.near_f32;
+    } else if (hp.model_near == kDF) {
+        c += pairs * g4 * uc.near_df;
+    } else {
+        c += pairs * R * uc.near_f64;
+    }
+    for (int l = 2; l <= L; ++l) {
+        const LevelPlan& lp = lps[l];
+        const TreeLevel& T = t.levels[l];
+        // S2M and L2T of this level's leaves
+        double pts = 0.0;
+        for (int32_t bx : T.leaf_pos) pts += (double)T.s_count[bx] + (double)T.t_count[bx];
+        const double npair = (double)lp.quad.K / 2.0;
+        if (lp.prec == kFP32) {
+            const double rc = R >= 16 ? 16.0 : (R > 1 ? 4.0 : 1.0);
+            c += pts * npair * (std::ceil(R / rc) * uc.pw_f32 + R * uc.pw_f32_rhs);
+        } else if (lp.prec == kDF) {
+            c += pts * npair * (uc.pw_df + R * uc.pw_df_rhs);
+        } else {
+            c += pts * npair * (uc.pw_f64 + R * uc.pw_f64_rhs);
+        }
+        const double cm = lp.prec == kFP32 ? uc.m2l_f32 : (lp.prec == kDF ? uc.m2l_df : uc.m2l_f64);
+        c += (double)T.iidx.size() * (double)lp.quad.K * R * cm;
+        if (l >= 3) c += 2.0 * uc.requad * R * (double)T.nbox() * (double)lp.quad.K;
+    }
+    return c;
+}
+
 static void tune_plan_shape(HostPlan& hp) {
     const UnitCost uc;
     const double R = hp.model_rhs;
@@ -1000,6 +1063,55 @@ static void tune_plan_shape(HostPlan& hp) {
             }
         }
     }
+    if (hp.adaptive) {
+        // adaptive trees: the uniform counts above overstate the far field of sparse regions
+        // and understate the leaf levels; cost the adaptive tree itself (built as the apply
+        // would use it, with the same per-unit times) at the uniform choice of each buffer
+        // whose uniform prediction is within 2.5x of the best and one level deeper (sparse
+        // regions stop early, so deeper leaves cost less than in a uniform tree), choose among
+        // those, and keep the chosen candidate's tree for the plan (each candidate costs one
+        // tree build)
+        int best_l[3] = {0, 0, 0};
+        double best_t[3] = {-1.0, -1.0, -1.0};
+        for (int b = 1; b <= 2; ++b)
+            for (int L = 2; L <= lfb[b]; ++L)
+                if (hp.predicted_ms[b][L] > 0.0 && (best_t[b] < 0.0 || hp.predicted_ms[b][L] < best_t[b])) {
+                    best_t[b] = hp.predicted_ms[b][L];
+                    best_l[b] = L;
+                }
+        const double uni = 1e3 * best;
+        for (int b = 1; b <= 2; ++b)
+            for (int L = 0; L < kMaxLevels; ++L) hp.predicted_ms[b][L] = 0.0;
+        best = -1.0;
+        for (int b = 1; b <= 2; ++b) {
+            if (lfb[b] < 2 || best_t[b] < 0.0 || best_t[b] > 2.5 * uni) continue;
+            for (int L = best_l[b]; L <= std::min(lfb[b], best_l[b] + 1); ++L) {
+                HostPlan cand;
+                const double t = adaptive_cost(hp, lps[b], b, L, uc, cand);
+                hp.predicted_ms[b][L] = 1e3 * t;
+                if (best < 0.0 || t < best) {
+                    best = t;
+                    bb = b;
+                    bl = L;
+                    // the plan's tree: everything build_tree writes
+                    hp.src_perm = std::move(cand.src_perm);
+                    hp.tgt_perm = std::move(cand.tgt_perm);
+                    hp.levels = std::move(cand.levels);
+                    hp.leaf_level = std::move(cand.leaf_level);
+                    hp.leaf_box = std::move(cand.leaf_box);
+                    hp.src_start = std::move(cand.src_start);
+                    hp.src_count = std::move(cand.src_count);
+                    hp.tgt_start = std::move(cand.tgt_start);
+                    hp.tgt_count = std::move(cand.tgt_count);
+                    hp.noff = std::move(cand.noff);
+                    hp.nidx = std::move(cand.nidx);
+                    hp.p2p_pairs = cand.p2p_pairs;
+                    hp.p2p_self_pairs = cand.p2p_self_pairs;
+                    hp.tree_ready = 1;
+                }
+            }
+        }
+    }
     hp.buffer = bb;
     hp.lp = lps[bb];
     hp.lf = lfb[bb] >= 2 ? bl : lfb[bb];
@@ -1064,7 +1176,7 @@ std::string build_host_plan(HostPlan& hp) {
         for (int v : hp.lp[l].quad.nphi)
             if (v > 1024) return "N_phi above 1024 is not supported";
     }
-    build_tree(hp);
+    if (!hp.tree_ready) build_tree(hp);
     for (int l = 2; l <= hp.lf && hp.host_tables; ++l) {
         std::vector<char> used(transfer_slots(hp.buffer), 0);
         for (int32_t v : hp.levels[l].iv) used[v] = 1;

@@ -147,6 +147,10 @@ def test_adaptive_fullsize_plan_bit_exact(cfg):
     lib = FmmPlan(s, t, kappa, eps, precision="mixed", device=-1, buffer=0, max_leaf=64, adaptive=True)
     info = lib.info()
     assert info["adaptive"] and info["tuned"]
+    # the adaptive trees costed by the tuner: the uniform choice of each buffer in the running
+    # and one level deeper; the plan takes the cheapest (and keeps that candidate's tree)
+    pred = info["predicted_ms"]
+    assert 1 <= len(pred) <= 4 and pred[(info["buffer"], info["lf"])] == min(pred.values())
     orc = ofmm.Plan(s, t, kappa, eps, precision="mixed", buffer=info["buffer"], depth=info["lf"], max_leaf=64,
                     adaptive=True)
     tr = orc.tree
