@@ -22,6 +22,7 @@
 // Built with -ffp-contract=off so the tree arithmetic rounds exactly as written.
 #include <algorithm>
 #include <cmath>
+#include <parallel/algorithm>
 #include <cstring>
 #include <numeric>
 #include <stdexcept>
@@ -481,12 +482,17 @@ static void demorton(uint64_t k, int depth, int32_t out[3]) {
     }
 }
 
+// ascending sort on all threads (the values sorted here are plain integers, so the result is
+// the same as a serial sort)
+static void psort(std::vector<uint64_t>& v) { __gnu_parallel::sort(v.begin(), v.end()); }
+
 // keys at depth kTreeBits
 static void leaf_keys(const std::vector<double>& p, int64_t n, const double corner[3], double side,
                       std::vector<uint64_t>& key) {
     const double nb = (double)(1u << kTreeBits);
     const double scale = nb / side;
     key.resize(n);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         uint32_t c[3];
         for (int k = 0; k < 3; ++k) {
@@ -516,9 +522,12 @@ static int64_t find_key(const std::vector<uint64_t>& keys, uint64_t k) {
 }
 
 static void build_tree(HostPlan& hp) {
+    // sources and targets the same point set: one key array and one sort serve both
+    const bool same = hp.ns == hp.nt && hp.src == hp.tgt;
     std::vector<uint64_t> ks, kt;
     leaf_keys(hp.src, hp.ns, hp.corner, hp.side, ks);
-    leaf_keys(hp.tgt, hp.nt, hp.corner, hp.side, kt);
+    if (!same) leaf_keys(hp.tgt, hp.nt, hp.corner, hp.side, kt);
+    const std::vector<uint64_t>& ktr = same ? ks : kt;
     const int D = hp.lf;
     const int shift = 3 * (kTreeBits - D);
     // sort by depth-D key, ties by original index: one sort of packed (key, index) words when
@@ -531,7 +540,7 @@ static void build_tree(HostPlan& hp) {
         if (3 * D + ibits <= 64) {
             std::vector<uint64_t> w(n);
             for (int64_t i = 0; i < n; ++i) w[i] = ((k[i] >> shift) << ibits) | (uint64_t)i;
-            std::sort(w.begin(), w.end());
+            psort(w);   // the words are distinct: the order is unique
             const uint64_t mask = (ibits == 64) ? ~uint64_t(0) : ((uint64_t(1) << ibits) - 1);
             for (int64_t i = 0; i < n; ++i) perm[i] = (int64_t)(w[i] & mask);
         } else {
@@ -541,12 +550,14 @@ static void build_tree(HostPlan& hp) {
         }
     };
     sort_perm(ks, hp.src_perm);
-    sort_perm(kt, hp.tgt_perm);
+    if (same) hp.tgt_perm = hp.src_perm;
+    else sort_perm(kt, hp.tgt_perm);
     std::vector<uint64_t> allk;
-    allk.reserve(ks.size() + kt.size());
+    allk.reserve(ks.size() + (same ? 0 : kt.size()));
     for (auto k : ks) allk.push_back(k >> shift);
-    for (auto k : kt) allk.push_back(k >> shift);
-    std::sort(allk.begin(), allk.end());
+    if (!same)
+        for (auto k : kt) allk.push_back(k >> shift);
+    psort(allk);
     allk.erase(std::unique(allk.begin(), allk.end()), allk.end());
     hp.levels.assign(D + 1, TreeLevel());
     // adaptive trees: level-l keys of the sorted points (for the per-box subtree ranges)
@@ -600,7 +611,7 @@ static void build_tree(HostPlan& hp) {
                 }
             };
             sub(ks, hp.src_perm, lks, L.s_start, L.s_count);
-            sub(kt, hp.tgt_perm, lkt, L.t_start, L.t_count);
+            sub(ktr, hp.tgt_perm, lkt, L.t_start, L.t_count);
             // split: above level 2, more than max_leaf sources or targets, or crowded (the
             // other level-l cubes within Chebyshev distance buffer hold more than
             // (2 buffer + 1)^3 max_leaf sources or targets)
@@ -724,7 +735,7 @@ static void build_tree(HostPlan& hp) {
         }
     } else {
         ranges(ks, hp.src_perm, hp.src_start, hp.src_count);
-        ranges(kt, hp.tgt_perm, hp.tgt_start, hp.tgt_count);
+        ranges(ktr, hp.tgt_perm, hp.tgt_start, hp.tgt_count);
         hp.leaf_level.assign(nb, D);
         hp.leaf_box.resize(nb);
         std::iota(hp.leaf_box.begin(), hp.leaf_box.end(), 0);
@@ -976,14 +987,10 @@ static double adaptive_cost(const HostPlan& hp, const std::vector<LevelPlan>& lp
     return c;
 }
 
-static void tune_plan_shape(HostPlan& hp) {
+// ks, kt: depth-kTreeBits keys of the sources and targets, ascending
+static void tune_plan_shape(HostPlan& hp, const std::vector<uint64_t>& ks, const std::vector<uint64_t>& kt) {
     const UnitCost uc;
     const double R = hp.model_rhs;
-    std::vector<uint64_t> ks, kt;
-    leaf_keys(hp.src, hp.ns, hp.corner, hp.side, ks);
-    leaf_keys(hp.tgt, hp.nt, hp.corner, hp.side, kt);
-    std::sort(ks.begin(), ks.end());
-    std::sort(kt.begin(), kt.end());
     std::vector<LevelPlan> lps[3];
     int lfb[3] = {1, 1, 1};
     for (int b = 1; b <= 2; ++b) lps[b] = plan_levels(hp, b, hp.occ_depth, &lfb[b]);
@@ -1146,15 +1153,23 @@ std::string build_host_plan(HostPlan& hp) {
         hp.side = side;
         for (int k = 0; k < 3; ++k) hp.corner[k] = (lo[k] + hi[k]) / 2.0 - side / 2.0;
     }
+    // sorted depth-kTreeBits keys of the sources and targets (occupancy rule, plan-shape tuner)
+    std::vector<uint64_t> ks, kt;
+    const bool same = hp.ns == hp.nt && hp.src == hp.tgt;
+    if (hp.depth_req == 0 || hp.buffer == 0) {
+        leaf_keys(hp.src, hp.ns, hp.corner, hp.side, ks);
+        psort(ks);
+        if (same) {
+            kt = ks;
+        } else {
+            leaf_keys(hp.tgt, hp.nt, hp.corner, hp.side, kt);
+            psort(kt);
+        }
+    }
     // depth bound
     if (hp.depth_req > 0) {
         hp.occ_depth = hp.depth_req;
     } else {
-        std::vector<uint64_t> ks, kt;
-        leaf_keys(hp.src, hp.ns, hp.corner, hp.side, ks);
-        leaf_keys(hp.tgt, hp.nt, hp.corner, hp.side, kt);
-        std::sort(ks.begin(), ks.end());
-        std::sort(kt.begin(), kt.end());
         hp.occ_depth = kTreeBits;
         for (int d = 0; d <= kTreeBits; ++d) {
             int sh = 3 * (kTreeBits - d);
@@ -1166,7 +1181,7 @@ std::string build_host_plan(HostPlan& hp) {
     }
     hp.eps_l = hp.eps_scale * hp.eps;
     if (hp.buffer == 0) {
-        tune_plan_shape(hp);
+        tune_plan_shape(hp, ks, kt);
     } else {
         hp.lp = plan_levels(hp, hp.buffer, hp.occ_depth, &hp.lf);
     }
