@@ -560,8 +560,18 @@ static void build_tree(HostPlan& hp) {
     psort(allk);
     allk.erase(std::unique(allk.begin(), allk.end()), allk.end());
     hp.levels.assign(D + 1, TreeLevel());
-    // adaptive trees: level-l keys of the sorted points (for the per-box subtree ranges)
-    std::vector<uint64_t> lks, lkt;
+    // adaptive trees: depth-D keys of the points in tree order, and level-l keys of the sorted
+    // points (for the per-box subtree ranges)
+    std::vector<uint64_t> lks, lkt, sds, sdt;
+    if (hp.adaptive) {
+        auto sorted_keys = [&](const std::vector<uint64_t>& k, const std::vector<int64_t>& perm, std::vector<uint64_t>& out) {
+            out.resize(perm.size());
+#pragma omp parallel for schedule(static)
+            for (int64_t p = 0; p < (int64_t)perm.size(); ++p) out[p] = k[perm[p]] >> shift;
+        };
+        sorted_keys(ks, hp.src_perm, sds);
+        if (!same) sorted_keys(ktr, hp.tgt_perm, sdt);
+    }
     for (int l = 0; l <= D; ++l) {
         TreeLevel& L = hp.levels[l];
         for (auto k : allk) {
@@ -597,10 +607,11 @@ static void build_tree(HostPlan& hp) {
         }
         if (hp.adaptive) {
             // subtree ranges: the sorted points whose level-l key is the box's key
-            auto sub = [&](const std::vector<uint64_t>& k, const std::vector<int64_t>& perm, std::vector<uint64_t>& lk,
+            auto sub = [&](const std::vector<uint64_t>& sorted_d, std::vector<uint64_t>& lk,
                            std::vector<int32_t>& start, std::vector<int32_t>& count) {
-                lk.resize(perm.size());
-                for (size_t p = 0; p < perm.size(); ++p) lk[p] = k[perm[p]] >> (shift + 3 * (D - l));
+                lk.resize(sorted_d.size());
+#pragma omp parallel for schedule(static)
+                for (int64_t p = 0; p < (int64_t)sorted_d.size(); ++p) lk[p] = sorted_d[p] >> (3 * (D - l));
                 start.resize(nb);
                 count.resize(nb);
                 for (int64_t b = 0; b < nb; ++b) {
@@ -610,8 +621,14 @@ static void build_tree(HostPlan& hp) {
                     count[b] = (int32_t)(hi - lo);
                 }
             };
-            sub(ks, hp.src_perm, lks, L.s_start, L.s_count);
-            sub(ktr, hp.tgt_perm, lkt, L.t_start, L.t_count);
+            sub(sds, lks, L.s_start, L.s_count);
+            if (same) {
+                lkt = lks;
+                L.t_start = L.s_start;
+                L.t_count = L.s_count;
+            } else {
+                sub(sdt, lkt, L.t_start, L.t_count);
+            }
             // split: above level 2, more than max_leaf sources or targets, or crowded (the
             // other level-l cubes within Chebyshev distance buffer hold more than
             // (2 buffer + 1)^3 max_leaf sources or targets)
@@ -786,6 +803,7 @@ static void build_tree(HostPlan& hp) {
     hp.noff.assign(nb + 1, 0);
     std::vector<std::vector<std::pair<uint64_t, int64_t>>> nf(nb);
     const int n1 = 1 << D;
+#pragma omp parallel for schedule(static)
     for (int64_t a = 0; a < nb; ++a) {
         const int32_t* ia = &leaf.idx[3 * a];
         for (int dx = -bw; dx <= bw; ++dx)
@@ -798,8 +816,8 @@ static void build_tree(HostPlan& hp) {
                     if (b >= 0) nf[a].push_back({leaf.key[b], b});
                 }
         std::sort(nf[a].begin(), nf[a].end());
-        hp.noff[a + 1] = hp.noff[a] + (int32_t)nf[a].size();
     }
+    for (int64_t a = 0; a < nb; ++a) hp.noff[a + 1] = hp.noff[a] + (int32_t)nf[a].size();
     hp.nidx.resize(hp.noff.back());
     hp.p2p_pairs = 0;
     for (int64_t a = 0; a < nb; ++a)
