@@ -137,3 +137,31 @@ def test_uniform_plan_reports_its_leaves():
     assert inf["level_nleaf"] == [0] * lf + [inf["nbox"][lf]]
     lb = lib.debug_get("LEAF_BOX")
     assert np.all(lb[:, 0] == lf) and np.array_equal(lb[:, 1], np.arange(inf["nbox"][lf]))
+
+
+def _random_cloud(g):
+    """Uniform background plus one to four dense cubes of random size and place."""
+    parts = [g.random((int(g.integers(0, 400)), 3))]
+    for _ in range(int(g.integers(1, 5))):
+        c, h = g.uniform(0.05, 0.95, 3), g.uniform(0.005, 0.2)
+        parts.append(np.clip(c + h * (g.random((int(g.integers(20, 600)), 3)) - 0.5), 0.0, 1.0))
+    return np.concatenate(parts)
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_random_adaptive_plans(seed):
+    """Seeded random clouds, max_leaf, buffer, depth and point-set pairings: the library's adaptive
+    host plan equals the oracle's bit for bit and covers every leaf pair exactly once."""
+    g = wl.rng(84, salt=seed)
+    s = _random_cloud(g)
+    t = s if g.random() < 0.6 else _random_cloud(g)
+    max_leaf = int(g.integers(1, 48))
+    buffer = int(g.integers(1, 3))
+    depth = int(g.integers(2, 7))
+    kappa = float(g.uniform(5.0, 80.0))
+    lib = FmmPlan(s, t, kappa, 1e-4, precision="mixed", max_leaf=max_leaf, buffer=buffer, depth=depth,
+                  root=(0, 0, 0, 1.0), device=-1, adaptive=True)
+    orc = ofmm.Plan(s, t, kappa, 1e-4, precision="mixed", max_leaf=max_leaf, buffer=buffer, depth=depth,
+                    root=(0, 0, 0, 1.0), adaptive=True)
+    assert_same_plan(lib, orc)
+    _covered_once(orc.tree)
