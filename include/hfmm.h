@@ -121,8 +121,9 @@ typedef struct {
  * lies above level 2, holds more than max_leaf sources or more than max_leaf targets, or is
  * crowded (it holds a point and the other cubes of its level within Chebyshev distance
  * `buffer` hold more than (2 buffer + 1)^3 max_leaf sources or targets), so leaves lie on
- * several levels (Section 2's tree, refined only where the points are dense) and no leaf
- * interacts directly with more points than a leaf of a uniform tree at max_leaf per box.
+ * several levels (Section 2's tree, refined only where the points are dense).  A leaf of
+ * level l < lf then sums at most ((2 buffer + 1)^3 + 1 + l ((2 buffer + 1)^3 - 1)) max_leaf
+ * sources directly.
  * S2M and L2T run for the leaves of each level at that level's quadrature; M2L stays between
  * boxes of one level (Section 3's diagonal transfer, unchanged); a target leaf B and a source
  * leaf C interact directly when their ancestors at level min(l_B, l_C) are neighbours.  The

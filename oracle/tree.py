@@ -22,8 +22,9 @@ for bit:
   max_leaf sources or more than max_leaf targets, or when it is crowded: it holds a
   point and the other cubes of level l within Chebyshev distance b of it (occupied or
   not by boxes of the tree) hold more than (2b+1)^3 max_leaf sources or more than that
-  many targets -- a leaf then never interacts directly with more points than a leaf of
-  a uniform tree at max_leaf points per box would.  The other boxes are leaves, so
+  many targets -- a leaf of level l < depth then sums at most
+  ((2b+1)^3 + 1 + l ((2b+1)^3 - 1)) max_leaf sources directly (its own, the other cubes
+  around it, and at most (2b+1)^3 - 1 leaves per coarser level).  The other boxes are leaves, so
   leaves lie on several levels and no box exists below a leaf.  A target leaf B
   and a source leaf C interact directly (P2P) when their ancestors at the coarser
   of their two levels, m = min(l_B, l_C), are neighbours; otherwise the ancestors

@@ -124,3 +124,34 @@ def test_adaptive_fmm_matches_direct_sum(buffer, kappa, eps):
     want = direct.direct(x, x, q, kappa)
     err = np.linalg.norm(phi - want) / np.linalg.norm(want)
     assert err <= eps, err
+
+
+@pytest.mark.parametrize("seed", range(7))
+def test_direct_work_of_a_leaf_is_bounded(seed):
+    """The crowded-box rule bounds what a leaf above the depth sums directly: the leaves under its
+    level-l neighbours hold at most (2b+1)^3 max_leaf + max_leaf sources (itself and the other
+    cubes, which are not crowded), and each coarser level m < l adds at most (2b+1)^3 - 1 leaves of
+    at most max_leaf sources (leaves neighbouring the level-m ancestor)."""
+    g = wl.rng(75, salt=seed)
+    if seed == 6:
+        # a sparse background with a very dense small cube: without the rule, sparse leaves next to
+        # the cube would sum all of its points directly
+        x = np.concatenate([g.random((80, 3)), np.array([0.26, 0.26, 0.26]) + 0.02 * g.random((4000, 3))])
+    else:
+        parts = [g.random((int(g.integers(50, 400)), 3))]
+        for _ in range(int(g.integers(1, 4))):
+            c, h = g.uniform(0.1, 0.9, 3), g.uniform(0.01, 0.15)
+            parts.append(np.clip(c + h * (g.random((int(g.integers(100, 800)), 3)) - 0.5), 0.0, 1.0))
+        x = np.concatenate(parts)
+    buffer, max_leaf = 1 + seed % 2, int(g.integers(2, 30))
+    t = Tree(x, x, 6, root=(0, 0, 0, 1.0), buffer=buffer, max_leaf=max_leaf)
+    span = (2 * buffer + 1) ** 3
+    checked = 0
+    for a in range(len(t.leaf_level)):
+        l = int(t.leaf_level[a])
+        if l == t.depth:
+            continue
+        direct_src = int(t.src_count[t.nlist[a]].sum())
+        assert direct_src <= span * max_leaf + max_leaf + l * (span - 1) * max_leaf, (a, l, direct_src)
+        checked += 1
+    assert checked > 0
