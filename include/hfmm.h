@@ -319,6 +319,15 @@ int64_t hfmm_debug_get(hfmm_plan_t plan, int what, int level, int64_t arg, void*
  * HFMM_ERR_STATE (host-only plan), HFMM_ERR_CUDA. */
 hfmm_status hfmm_debug_watchdog_probe(hfmm_plan_t plan, void* stream);
 
+/* Test support for allocation failures: after `after` more allocation points of the host
+ * planner in the calling thread (the planning stages: bounding cube, occupancy depth, level
+ * plans, tree and lists, each level's transfer tables), the next one fails as a host
+ * allocation failure would, and hfmm_plan returns HFMM_ERR_NOMEM having released everything
+ * it allocated; the hook is then off again.  A countdown that has not fired carries over to
+ * the next plan.  after < 0 turns the hook off (the default).  No device call is made.
+ * Errors: none (always HFMM_OK). */
+hfmm_status hfmm_debug_fail_host_alloc(int after);
+
 /* Largest ns + nt that hfmm_direct_noalloc accepts. */
 #define HFMM_NOALLOC_MAX_POINTS (1 << 19)
 

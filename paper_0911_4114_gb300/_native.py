@@ -25,7 +25,8 @@ GET = dict(BOX_IDX=0, BOX_PARENT=1, ILIST_OFF=2, ILIST_IDX=3, ILIST_V=4, NLIST_O
 
 EXPORTS = ("hfmm_default_options", "hfmm_plan", "hfmm_apply", "hfmm_query", "hfmm_set_timing",
            "hfmm_destroy", "hfmm_last_error", "hfmm_debug_get", "hfmm_direct_noalloc", "hfmm_apply_adjoint", "hfmm_grad_sources", "hfmm_plan_batch",
-           "hfmm_apply_batch", "hfmm_batch_plan", "hfmm_batch_destroy", "hfmm_debug_watchdog_probe")
+           "hfmm_apply_batch", "hfmm_batch_plan", "hfmm_batch_destroy", "hfmm_debug_watchdog_probe",
+           "hfmm_debug_fail_host_alloc")
 NOALLOC_MAX_POINTS = 1 << 19
 
 
@@ -103,6 +104,8 @@ def lib():
     L.hfmm_direct_noalloc.restype = ctypes.c_int
     L.hfmm_debug_watchdog_probe.argtypes = [vp, vp]
     L.hfmm_debug_watchdog_probe.restype = ctypes.c_int
+    L.hfmm_debug_fail_host_alloc.argtypes = [ctypes.c_int]
+    L.hfmm_debug_fail_host_alloc.restype = ctypes.c_int
     _lib = L
     return L
 

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <new>
 #include <type_traits>
 #include <utility>
 #include <string>
@@ -21,6 +22,8 @@ using namespace hfmm;
 namespace {
 
 thread_local std::string g_err;
+// allocation points left before the planner's next one fails (hfmm_debug_fail_host_alloc)
+thread_local int g_fail_alloc_after = -1;
 
 hfmm_status fail(hfmm_status s, const std::string& msg) {
     g_err = msg;
@@ -30,6 +33,11 @@ hfmm_status fail(hfmm_status s, const std::string& msg) {
 }  // namespace
 
 void hfmm::set_last_error(const std::string& msg) { g_err = msg; }
+
+void hfmm::alloc_point() {
+    if (g_fail_alloc_after < 0) return;
+    if (g_fail_alloc_after-- == 0) throw std::bad_alloc();
+}
 
 namespace {
 
@@ -1370,6 +1378,11 @@ void hfmm_default_options(hfmm_options* opt) {
 }
 
 const char* hfmm_last_error(void) { return g_err.c_str(); }
+
+hfmm_status hfmm_debug_fail_host_alloc(int after) {
+    g_fail_alloc_after = after < 0 ? -1 : after;
+    return HFMM_OK;
+}
 
 hfmm_status hfmm_plan(const double* sources, int64_t ns, const double* targets, int64_t nt, double kappa,
                       double eps, const hfmm_options* opt_in, hfmm_plan_t* out) {

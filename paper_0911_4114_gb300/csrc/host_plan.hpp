@@ -130,6 +130,10 @@ void bessel_jn_all(int nmax, double x, double* out);  // J_0..J_nmax (integer or
 // thread-local message returned by hfmm_last_error (api.cu)
 void set_last_error(const std::string& msg);
 
+// allocation point of the planner: throws std::bad_alloc when the test hook
+// (hfmm_debug_fail_host_alloc) counts down to it in this thread
+void alloc_point();
+
 // --- helpers shared by the planner and the device-side setup -----------------
 bool is_235(int64_t k);
 int64_t round_fft(int64_t n, int64_t mult);

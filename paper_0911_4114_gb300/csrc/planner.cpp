@@ -1146,6 +1146,7 @@ static void tune_plan_shape(HostPlan& hp, const std::vector<uint64_t>& ks, const
 
 // ---------------------------------------------------------------------------
 std::string build_host_plan(HostPlan& hp) {
+    alloc_point();
     // root cube
     std::vector<double> lo(3), hi(3);
     for (int k = 0; k < 3; ++k) {
@@ -1184,6 +1185,7 @@ std::string build_host_plan(HostPlan& hp) {
             psort(kt);
         }
     }
+    alloc_point();
     // depth bound
     if (hp.depth_req > 0) {
         hp.occ_depth = hp.depth_req;
@@ -1198,6 +1200,7 @@ std::string build_host_plan(HostPlan& hp) {
         }
     }
     hp.eps_l = hp.eps_scale * hp.eps;
+    alloc_point();
     if (hp.buffer == 0) {
         tune_plan_shape(hp, ks, kt);
     } else {
@@ -1209,8 +1212,10 @@ std::string build_host_plan(HostPlan& hp) {
         for (int v : hp.lp[l].quad.nphi)
             if (v > 1024) return "N_phi above 1024 is not supported";
     }
+    alloc_point();
     if (!hp.tree_ready) build_tree(hp);
     for (int l = 2; l <= hp.lf && hp.host_tables; ++l) {
+        alloc_point();
         std::vector<char> used(transfer_slots(hp.buffer), 0);
         for (int32_t v : hp.levels[l].iv) used[v] = 1;
         build_tables(hp.lp[l], hp.kappa, hp.buffer, used);

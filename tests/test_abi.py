@@ -142,3 +142,37 @@ def test_require_far_flag_returns_unstable():
     with pytest.raises(nat.HfmmError) as e:
         FmmPlan(x, x, 5.0, 1e-6, max_leaf=16, device=-1, require_far=True)
     assert e.value.status == nat.ERR_UNSTABLE
+
+
+def test_host_allocation_failure_returns_nomem():
+    """A host allocation failure at any planning stage (simulated by the planner's test hook)
+    makes hfmm_plan return HFMM_ERR_NOMEM with a message and no plan; the hook is off afterwards
+    and the same plan then succeeds."""
+    L = nat.lib()
+    x = np.random.default_rng(3).random((2500, 3))
+    h = ctypes.c_void_p()
+
+    def plan():
+        opt = nat.Options()
+        L.hfmm_default_options(ctypes.byref(opt))
+        opt.device = -1
+        opt.precision = nat.PREC_MIXED
+        return L.hfmm_plan(x.ctypes.data, len(x), x.ctypes.data, len(x), 60.0, 1e-5, ctypes.byref(opt),
+                           ctypes.byref(h))
+
+    failed = 0
+    for after in range(12):
+        assert L.hfmm_debug_fail_host_alloc(after) == nat.OK
+        st = plan()
+        L.hfmm_debug_fail_host_alloc(-1)
+        if st == nat.ERR_NOMEM:
+            failed += 1
+            assert b"allocation" in L.hfmm_last_error()
+            assert not h.value
+        else:
+            assert st == nat.OK
+            L.hfmm_destroy(h)
+            break
+    assert failed >= 5            # bounding cube, occupancy, levels, tree, at least one table
+    assert plan() == nat.OK       # unaffected once the hook has fired
+    L.hfmm_destroy(h)
