@@ -104,10 +104,13 @@ def test_max_leaf_zero_is_the_uniform_tree():
     assert np.all(a.leaf_level == 5) and np.array_equal(a.leaf_box, np.arange(len(u.levels[5]['key'])))
     for f in ('src_start', 'src_count', 'tgt_start', 'tgt_count'):
         assert np.array_equal(getattr(u, f), getattr(a, f))
-    for b in range(len(u.nlist)):
+    # lists on a strided sample of about 150 boxes per level
+    n = len(u.nlist)
+    for b in range(0, n, max(1, n // 150)):
         assert np.array_equal(u.nlist[b], a.nlist[b])
     for l in range(2, 6):
-        for b in range(len(u.levels[l]['key'])):
+        n = len(u.levels[l]['key'])
+        for b in range(0, n, max(1, n // 150)):
             assert np.array_equal(u.ilist[l][b], a.ilist[l][b])
             assert np.array_equal(u.vlist[l][b], a.vlist[l][b])
 
